@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Throughput of the compact-stencil separation-of-variables solver on one GB300.
+
+Workload (default): 6th-order compact scheme for Lap(u) + k(z)^2 u = f on the
+unit cube, 255^3 interior points (h = 1/256), k(z) = 20 (1 + z^2/2), f = the
+manufactured right-hand side of u = sin(pi x) sin(2 pi y) sin(3 pi z) e^z plus
+seeded U[-1, 1] noise at interior nodes, face data d2f/dn2 analytic, FP64 f.
+
+A step is one complete solve of one right-hand side (RHS operator, forward
+DSTs, z-solves, inverse DSTs, and for the mixed path the FP64 residual and
+refinement sweeps) with f and u resident in HBM.  The headline value is the
+mixed path (FP32 transforms, FP64 z-solves, FP64 residual, 2 refinement
+sweeps) in Gunknowns/s; the FP64 path is timed beside it.  L2 is flushed
+(a 256 MB write) between timed steps.  N > 1 GPUs run independent replicas
+(weak scaling, no collective on the data path).
+
+--impl reference times the CPU oracle (plain FP64 numpy) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gunknowns/s per solve at <=1e-10 rel err, mixed vs FP64 GPU path; % HBM roofline"
+UNIT = "Gunknowns/s"
+
+# Algorithmic bytes per interior unknown for each stage of one solve, by path
+# (what the stage must read and write: inputs, outputs, cached factors).
+BYTES_MIXED = {
+    "rhs": 16.0,               # read f (FP64 nodes), write F (FP64)
+    "dst_x": None,             # 12 (FP64 F -> FP32) first sweep, 8 after
+    "dst_y": 8.0,              # FP32 read + write
+    "thomas": 32.0,            # FP32 r + FP32 w + 3 FP64 factors
+    "idst_y": 8.0,
+    "idst_x": None,            # 4 + 8 (write u) first sweep, 4 + 16 (u += ) after
+    "residual": 20.0,          # read F, U (FP64), write r (FP32)
+}
+BYTES_FP64 = {"rhs": 16.0, "dst_x": 16.0, "dst_y": 16.0, "thomas": 40.0, "idst_y": 16.0,
+              "idst_x": 16.0, "residual": 0.0}
+
+
+def stage_bytes(path: str, sweeps: int):
+    if path == "fp64":
+        return dict(BYTES_FP64)
+    b = dict(BYTES_MIXED)
+    n = sweeps + 1
+    b["dst_x"] = 12.0 + 8.0 * sweeps
+    b["idst_x"] = 12.0 + 20.0 * sweeps
+    b["dst_y"] *= n
+    b["thomas"] *= n
+    b["idst_y"] *= n
+    b["residual"] *= sweeps
+    return b
+
+
+def launches_per_solve(path: str, sweeps: int) -> int:
+    return 6 if path == "fp64" else 1 + 5 * (sweeps + 1) + sweeps
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def make_problem(N: int, seed: int):
+    import workloads as W
+    return W.workload_cube255_order6(seed=seed, N=N)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://")
+        if rank != 0:
+            dist.barrier()
+            dist.destroy_process_group()
+            return
+    from oracle import hs_oracle as O
+    p = make_problem(args.n, args.seed)
+    n = p.Nx * p.Ny * p.Nz
+    for _ in range(args.warmup):
+        O.solve(p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.solve(p)
+    dt = (time.perf_counter() - t0) / args.steps
+    val = n / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"cube{args.n}_o6: 6th-order compact Helmholtz, {args.n}^3 "
+                                   "interior, k=20(1+z^2/2), manufactured f + U[-1,1] noise, 1 RHS",
+                       "global_batch": 1, "parallelism": "cpu oracle, rank 0 only"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"full {args.n}^3 solve per step (numpy FP64, "
+                                       "matmul O(N^4) DSTs, textbook Thomas)"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hs", choices=["hs", "reference"])
+    ap.add_argument("--n", type=int, default=255)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--sweeps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "hs":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1912_03565_gb300 as H
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    p = make_problem(args.n, args.seed)
+    N3 = p.Nx * p.Ny * p.Nz
+    f = torch.from_numpy(p.f_nodes).cuda()
+    fnn = [None if a is None else torch.from_numpy(a).cuda() for a in p.fnn]
+    u = torch.zeros((p.Nz, p.Ny, p.Nx), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def solver(precision, sweeps):
+        s = H.Solver(p.Nx, p.Ny, p.Nz, p.Lx, p.Ly, p.Lz, p.order, H.HS_HELMHOLTZ, precision)
+        s.set_coeff(p.c0, p.c1, p.c2)
+        if precision == H.HS_MIXED:
+            H.hs_set_refinement(s.plan, sweeps)
+        return s
+
+    smix = solver(H.HS_MIXED, args.sweeps)
+    s64 = solver(H.HS_FP64, 0)
+
+    # ---- accuracy (untimed)
+    acc = {}
+    s64.solve(f, u, H.HS_F64, H.HS_RHS_NODAL, None, fnn, stream=stream)
+    torch.cuda.synchronize()
+    u64 = u.cpu().numpy()
+    _, inf = smix.solve(f, u, H.HS_F64, H.HS_RHS_NODAL, None, fnn, stream=stream, info=True)
+    umix = u.cpu().numpy()
+    s0 = solver(H.HS_MIXED, 0)
+    s0.solve(f, u, H.HS_F64, H.HS_RHS_NODAL, None, fnn, stream=stream)
+    torch.cuda.synchronize()
+    u0 = u.cpu().numpy()
+    s0.close()
+
+    def rel(a, b):
+        return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    acc["mixed_refined_vs_fp64_gpu"] = rel(umix, u64)
+    acc["mixed_unrefined_vs_fp64_gpu"] = rel(u0, u64)
+    acc["mixed_rel_residual_per_sweep"] = inf["rel_residual"]
+    acc["min_pivot_ratio"] = inf["min_pivot_ratio"]
+
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import hs_oracle as O
+        t0 = time.perf_counter()
+        ref, _ = O.solve(p)
+        dt = time.perf_counter() - t0
+        acc["fp64_vs_oracle"] = rel(u64, ref)
+        acc["mixed_refined_vs_oracle"] = rel(umix, ref)
+        acc["mixed_unrefined_vs_oracle"] = rel(u0, ref)
+        cpu_baseline = {"value": N3 / dt / 1e9, "unit": UNIT, "cores": cpu_cores(),
+                        "kind": "oracle",
+                        "sample": f"one full {args.n}^3 solve (numpy FP64, matmul O(N^4) DSTs, "
+                                  f"textbook Thomas): {dt:.2f} s"}
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB
+
+    def timed(s, path, sweeps, steps, warmup):
+        H.hs_set_stage_timing(s.plan, True)
+        for _ in range(warmup):
+            s.solve(f, u, H.HS_F64, H.HS_RHS_NODAL, None, fnn, stream=stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        stage_tot = {k: 0.0 for k in H.STAGES}
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            s.solve(f, u, H.HS_F64, H.HS_RHS_NODAL, None, fnn, stream=stream)
+            ev[k][1].record(stream)
+            st = H.hs_stage_times(s.plan)
+            for key, v in st.items():
+                stage_tot[key] += v
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        H.hs_set_stage_timing(s.plan, False)
+        return ms, {k: v / steps for k, v in stage_tot.items()}
+
+    clk = ClockSampler(local)
+    clk.start()
+    ms_mix, st_mix = timed(smix, "mixed", args.sweeps, args.steps, args.warmup)
+    ms_64, st_64 = timed(s64, "fp64", 0, max(3, args.steps // 2), args.warmup)
+    clocks = clk.stop()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms_mix = max_over_ranks(ms_mix)
+    ms_64 = max_over_ranks(ms_64)
+    steps64 = max(3, args.steps // 2)
+    value = world * args.steps * N3 / (ms_mix * 1e-3) / 1e9
+    value64 = world * steps64 * N3 / (ms_64 * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel of the mixed path
+    hbm_peak, peak_kind = load_peaks()
+    bmix = stage_bytes("mixed", args.sweeps)
+    kern = max((k for k in bmix if st_mix.get(k, 0) > 0), key=lambda k: st_mix[k])
+    nlaunch = {"dst_x": args.sweeps + 1, "dst_y": args.sweeps + 1, "thomas": args.sweeps + 1,
+               "idst_y": args.sweeps + 1, "idst_x": args.sweeps + 1, "rhs": 1,
+               "residual": args.sweeps}[kern]
+    bytes_per_launch = bmix[kern] * N3 / nlaunch
+    t_launch = st_mix[kern] / nlaunch * 1e-3
+    achieved = bytes_per_launch / t_launch / 1e9
+    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                "algorithmic_bytes_per_launch": bytes_per_launch}
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        fh = torch.from_numpy(p.f_nodes).pin_memory()
+        fnnh = [None if a is None else torch.from_numpy(a).pin_memory() for a in p.fnn]
+        uh = torch.zeros((p.Nz, p.Ny, p.Nx), dtype=torch.float64).pin_memory()
+        ke = max(3, args.steps // 2)
+        for _ in range(2):
+            smix.solve(fh, uh, H.HS_F64, H.HS_RHS_NODAL, None, fnnh, stream=stream)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ke):
+            smix.solve(fh, uh, H.HS_F64, H.HS_RHS_NODAL, None, fnnh, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1))
+        h2d = fh.numel() * 8 + sum(a.numel() * 8 for a in fnnh if a is not None)
+        e2e = {"value": world * ke * N3 / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": uh.numel() * 8,
+               "ms_per_step": ms_e2e / ke}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_mix / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+            "data": "synthetic",
+            "config": {"workload": f"cube{args.n}_o6: 6th-order compact Helmholtz, {args.n}^3 "
+                                   "interior, h=1/256, k=20(1+z^2/2), manufactured f + U[-1,1] "
+                                   "noise (seed), FP64 f, 1 RHS per step",
+                       "global_batch": world, "parallelism": f"replicas x{world}",
+                       "refinement_sweeps": args.sweeps,
+                       "l2": "256 MB buffer written between timed steps"},
+            "fp64_path": {"value": value64, "unit": UNIT, "ms_per_step": ms_64 / steps64,
+                          "stages_ms": st_64},
+            "stages_ms": st_mix,
+            "accuracy": acc,
+            "roofline": roofline,
+            "cpu_baseline": cpu_baseline,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": launches_per_solve("mixed", args.sweeps) * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    smix.close()
+    s64.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

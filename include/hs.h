@@ -1,0 +1,207 @@
+/*
+ * hs.h -- C ABI of the GB300 (sm_103a) separation-of-variables direct solver
+ * for 27-point compact schemes of
+ *
+ *     Laplacian(u) + k(z)^2 u = f            (Helmholtz, 2nd/4th/6th order)
+ *     Laplacian(u) + gamma(z) u_z = f        (convection-diffusion, 4th order)
+ *
+ * on a box with Dirichlet data on all six faces (arXiv 1912.03565: problem
+ * statement eqs. (problem), (bc); schemes Sections 2 and 3.2-3.5; solver
+ * Section 3.6).  A solve applies the compact right-hand-side operator, a 2-D
+ * discrete sine transform (DST-I) along x then y, one tridiagonal system in z
+ * per sine mode (p, q), and the inverse transform.
+ *
+ * Conventions shared by every entry point
+ *  - Grids.  N_a interior points per axis, h_a = L_a / (N_a + 1) (Section 2).
+ *    Interior arrays are C-ordered [l][j][i] (x fastest), the paper's row
+ *    order i + Nx j + Nx Ny l (Section 3.1).  Node-grid arrays include the
+ *    boundary nodes: [Nz+2][Ny+2][Nx+2].
+ *  - Faces are numbered x-lo, x-hi, y-lo, y-hi, z-lo, z-hi.  Face arrays are
+ *    full faces including edges: x-faces [Nz+2][Ny+2], y-faces [Nz+2][Nx+2],
+ *    z-faces [Ny+2][Nx+2].  Where faces share an edge or corner node, the
+ *    z-face value is used, then the y-face, then the x-face.
+ *  - Pointers to bulk data (f, u, faces) may be device pointers or host
+ *    pointers; host data are staged through plan-owned device buffers and
+ *    copied on the given stream.  The caller keeps every buffer valid until
+ *    the stream has passed the solve.
+ *  - Errors are returned, never raised: no entry point aborts, traps or
+ *    prints.  Negative codes are errors (the outputs are unspecified),
+ *    positive codes are warnings (the outputs are valid).
+ *  - Distinct plans may be used from distinct host threads concurrently; one
+ *    plan must not be used by two threads at once.  The library keeps no
+ *    global mutable state.
+ */
+#ifndef HS_H
+#define HS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int hs_status;
+
+enum {
+    HS_OK = 0,
+    HS_WARN_NEAR_SINGULAR = 1,   /* min |pivot| / max |diag| < 1e-13 in some z-system */
+    HS_WARN_NOT_CONVERGED = 2,   /* refinement ended above its tolerance (result valid) */
+    HS_ERR_INVALID_ARG = -1,
+    HS_ERR_UNSUPPORTED = -2,
+    HS_ERR_OOM = -3,
+    HS_ERR_CUDA = -4,
+    HS_ERR_NO_COEFF = -5,        /* hs_solve before hs_set_coeff */
+    HS_ERR_TIMEOUT = -6,         /* a bounded device-side wait gave up */
+    HS_ERR_NONFINITE = -7
+};
+
+enum { HS_HELMHOLTZ = 0, HS_CONVDIFF = 1 };                 /* equation */
+enum { HS_BC_DIRICHLET = 0 };                               /* boundary conditions */
+enum { HS_FP64 = 0, HS_MIXED = 1 };                          /* precision path */
+enum { HS_CD_PAPER = 0, HS_CD_CORRECTED = 1 };               /* CD coefficient variant */
+enum { HS_F64 = 0, HS_F32 = 1 };                             /* element type of f / faces */
+enum { HS_RHS_NODAL = 0, HS_RHS_ASSEMBLED = 1 };             /* meaning of f */
+
+typedef struct hs_plan_s *hs_plan_t;
+
+/* Dirichlet face values and, for the 6th-order right-hand side only, the
+ * normal second derivative of f on each face (d2f/dx2 on the x-faces, ...).
+ * Element type: the f_dtype of the solve.  NULL entries mean zero.  For a
+ * multi-RHS solve the same boundary data apply to every right-hand side. */
+typedef struct {
+    const void *face[6];
+    const void *fnn[6];
+} hs_boundary;
+
+#define HS_INFO_MAX_ITERS 8
+#define HS_INFO_STAGES 8
+
+/* Diagnostics of the last right-hand side of a solve.  Filling it makes the
+ * solve synchronise the stream. */
+typedef struct {
+    int iterations;                          /* inverse applications (1 + refinements) */
+    double rel_residual[HS_INFO_MAX_ITERS];  /* ||F - A U||_2 / ||F||_2 after each */
+    double min_pivot_ratio;                  /* min |pivot| / max |diag| of the z-systems */
+    float stage_ms[HS_INFO_STAGES];          /* device time per stage (stage timing on) */
+} hs_info;
+
+/* Stage indices of hs_info.stage_ms. */
+enum {
+    HS_STAGE_RHS = 0,        /* right-hand-side operator + Dirichlet lifting */
+    HS_STAGE_DST_X = 1,      /* forward DST along x (all iterations) */
+    HS_STAGE_DST_Y = 2,      /* forward DST along y */
+    HS_STAGE_THOMAS = 3,     /* z-direction tridiagonal solves */
+    HS_STAGE_IDST_Y = 4,     /* inverse DST along y */
+    HS_STAGE_IDST_X = 5,     /* inverse DST along x (+ write / update of u) */
+    HS_STAGE_RESIDUAL = 6,   /* FP64 residual F - A U (mixed path) */
+    HS_STAGE_TOTAL = 7
+};
+
+/*
+ * hs_plan -- create a solver plan for one grid and scheme (Section 2 grid,
+ * Sections 3.2-3.5 schemes).
+ *   out         receives the plan handle (caller frees it with hs_destroy).
+ *   Nx, Ny, Nz  interior points per axis, each >= 1.
+ *   Lx, Ly, Lz  box lengths (> 0); h_a = L_a / (N_a + 1).
+ *   order       2, 4 or 6 for HS_HELMHOLTZ; 4 for HS_CONVDIFF.  Order 6
+ *               needs hx = hy = hz (relative difference <= 1e-12).
+ *   equation    HS_HELMHOLTZ or HS_CONVDIFF.
+ *   bc          HS_BC_DIRICHLET (the only one).
+ *   precision   HS_FP64: every step in FP64.  HS_MIXED: FP32 transforms,
+ *               FP64 z-solves, FP64 residual and iterative refinement.
+ *   max_rhs     largest nrhs a solve will pass (>= 1).
+ * Allocates the plan's device tables and workspace on the current device.
+ * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED, HS_ERR_OOM, HS_ERR_CUDA.
+ */
+hs_status hs_plan(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, double Lz,
+                  int order, int equation, int bc, int precision, int max_rhs);
+
+/*
+ * hs_set_coeff -- set the z-dependent coefficient and build the per-row
+ * stencil coefficients {a,b,c,d} x {l-1,l,l+1} (Sections 3.2-3.5) and the
+ * cached factorization of every z-system (Section 3.6: eigenvalues
+ * lambda_nu(p,q) = 4 a_nu cos(th_p) cos(th_q) + 2 b_nu cos(th_p)
+ * + 2 c_nu cos(th_q) + d_nu, LU without pivoting).
+ *   c0, c1, c2  HOST arrays of length Nz+2 sampled at z_l = l hz, l = 0..Nz+1;
+ *               copied.  Helmholtz: c0 = k^2, c1 = (k^2)', c2 = (k^2)''
+ *               (c1, c2 may be NULL below order 6; for order 6 they are
+ *               required and should be the exact derivatives).  CD: c0 =
+ *               gamma, c1 = gamma', c2 = gamma'' (NULL = 0).
+ *   cd_variant  HS_CD_CORRECTED (variable-gamma corrections, 4th order for
+ *               gamma = gamma(z)) or HS_CD_PAPER (the printed coefficients
+ *               with gamma frozen at row l); ignored for Helmholtz.
+ * Synchronous.  Returns HS_WARN_NEAR_SINGULAR when some pivot ratio is
+ * below 1e-13.  Errors: HS_ERR_INVALID_ARG, HS_ERR_CUDA.
+ */
+hs_status hs_set_coeff(hs_plan_t plan, const double *c0, const double *c1, const double *c2,
+                       int cd_variant);
+
+/*
+ * hs_set_refinement -- number of refinement sweeps of the HS_MIXED path
+ * after its first solve (default 2; 0..HS_INFO_MAX_ITERS-1).  Each sweep
+ * computes the FP64 residual r = F - A U and adds the fast solve of r to U.
+ * Ignored by the HS_FP64 path.
+ */
+hs_status hs_set_refinement(hs_plan_t plan, int sweeps);
+
+/*
+ * hs_set_stage_timing -- when on (1), solves record CUDA events around each
+ * stage launch (no synchronisation is added); hs_stage_times and
+ * hs_info.stage_ms report them.  Off (0) by default.
+ */
+hs_status hs_set_stage_timing(hs_plan_t plan, int on);
+
+/*
+ * hs_solve -- solve A U = F for nrhs right-hand sides on `stream`.
+ *   f          rhs_kind HS_RHS_NODAL: f on the node grid, [nrhs][Nz+2][Ny+2][Nx+2];
+ *              the library applies the scheme's right-hand-side operator
+ *              (2nd: hz^2 f; 4th: hz^2 f^(IV), eq. (scheme4); 6th: hz^2 f^(VI),
+ *              eq. (scheme6) with explicit differences; CD: eq. (cd_rhs)).
+ *              HS_RHS_ASSEMBLED: F on the interior, [nrhs][Nz][Ny][Nx]
+ *              (the operator already applied).  Element type f_dtype.
+ *   bnd        Dirichlet and 6th-order face data (NULL = all zero).
+ *   u          output, FP64, interior [nrhs][Nz][Ny][Nx].
+ *   stream     a cudaStream_t (NULL = the legacy default stream).
+ *   info       NULL: the call is asynchronous.  Non-NULL: the call
+ *              synchronises and fills the diagnostics of the last RHS.
+ * nrhs must be between 1 and max_rhs.  Errors: HS_ERR_INVALID_ARG,
+ * HS_ERR_NO_COEFF, HS_ERR_CUDA, HS_ERR_OOM (host staging).
+ */
+hs_status hs_solve(hs_plan_t plan, const void *f, int f_dtype, int rhs_kind,
+                   const hs_boundary *bnd, double *u, int nrhs, void *stream, hs_info *info);
+
+/*
+ * hs_residual -- ||F - A U||_2 and ||F||_2 of a computed solution, in FP64,
+ * for one right-hand side given as in hs_solve (L2-res of Section 5.1).
+ * Synchronous.  Device or host pointers.
+ */
+hs_status hs_residual(hs_plan_t plan, const void *f, int f_dtype, int rhs_kind,
+                      const hs_boundary *bnd, const double *u, void *stream,
+                      double *res_norm, double *rhs_norm);
+
+/*
+ * hs_stage_times -- device time per stage (ms[HS_INFO_STAGES], indexed by
+ * HS_STAGE_*) summed over the last hs_solve on this plan, when stage timing
+ * was on; HS_STAGE_TOTAL is the whole call.  Waits for that solve's events.
+ * Errors: HS_ERR_INVALID_ARG.
+ */
+hs_status hs_stage_times(hs_plan_t plan, float *ms);
+
+/* hs_workspace_bytes -- device bytes owned by the plan (tables, cached
+ * factorization, workspace). */
+size_t hs_workspace_bytes(hs_plan_t plan);
+
+/* hs_destroy -- free a plan (NULL is accepted).  Synchronises the device. */
+hs_status hs_destroy(hs_plan_t plan);
+
+/* hs_status_str -- static text for a status code. */
+const char *hs_status_str(hs_status s);
+
+/* hs_last_error -- text of the last error seen on this plan (never NULL). */
+const char *hs_last_error(hs_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HS_H */

@@ -1,0 +1,262 @@
+"""Python binding of libhs, the GB300 separation-of-variables compact-stencil solver.
+
+The functions below carry the C ABI's names (include/hs.h) and only marshal
+arguments: every step of a solve runs in the CUDA library.  There is no CPU
+path: importing works without a GPU, but any call needs libhs.so (built by
+``paper_1912_03565_gb300.build``) and a CUDA device, and raises otherwise.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; CPU/host data are
+staged by the library itself (host-to-device copies on the given stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhs.so")
+
+# enums (include/hs.h)
+HS_OK = 0
+HS_WARN_NEAR_SINGULAR = 1
+HS_WARN_NOT_CONVERGED = 2
+HS_ERR_INVALID_ARG = -1
+HS_ERR_UNSUPPORTED = -2
+HS_ERR_OOM = -3
+HS_ERR_CUDA = -4
+HS_ERR_NO_COEFF = -5
+HS_ERR_TIMEOUT = -6
+HS_ERR_NONFINITE = -7
+HS_HELMHOLTZ, HS_CONVDIFF = 0, 1
+HS_BC_DIRICHLET = 0
+HS_FP64, HS_MIXED = 0, 1
+HS_CD_PAPER, HS_CD_CORRECTED = 0, 1
+HS_F64, HS_F32 = 0, 1
+HS_RHS_NODAL, HS_RHS_ASSEMBLED = 0, 1
+HS_INFO_MAX_ITERS = 8
+HS_INFO_STAGES = 8
+STAGES = ("rhs", "dst_x", "dst_y", "thomas", "idst_y", "idst_x", "residual", "total")
+
+EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_stage_timing", "hs_solve",
+            "hs_residual", "hs_stage_times", "hs_workspace_bytes", "hs_destroy",
+            "hs_status_str", "hs_last_error")
+
+
+class hs_boundary(ctypes.Structure):
+    _fields_ = [("face", ctypes.c_void_p * 6), ("fnn", ctypes.c_void_p * 6)]
+
+
+class hs_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int),
+                ("rel_residual", ctypes.c_double * HS_INFO_MAX_ITERS),
+                ("min_pivot_ratio", ctypes.c_double),
+                ("stage_ms", ctypes.c_float * HS_INFO_STAGES)]
+
+    def as_dict(self):
+        n = self.iterations
+        return {"iterations": n, "rel_residual": list(self.rel_residual[:max(n, 1)]),
+                "min_pivot_ratio": self.min_pivot_ratio,
+                "stage_ms": dict(zip(STAGES, list(self.stage_ms)))}
+
+
+class HsError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)} {detail}".strip())
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load libhs.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_1912_03565_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.hs_plan.argtypes = [ctypes.POINTER(vp), ci, ci, ci, cd, cd, cd, ci, ci, ci, ci, ci]
+    lib.hs_plan.restype = ci
+    lib.hs_set_coeff.argtypes = [vp, vp, vp, vp, ci]
+    lib.hs_set_coeff.restype = ci
+    lib.hs_set_refinement.argtypes = [vp, ci]
+    lib.hs_set_refinement.restype = ci
+    lib.hs_set_stage_timing.argtypes = [vp, ci]
+    lib.hs_set_stage_timing.restype = ci
+    lib.hs_solve.argtypes = [vp, vp, ci, ci, ctypes.POINTER(hs_boundary), vp, ci, vp,
+                             ctypes.POINTER(hs_info)]
+    lib.hs_solve.restype = ci
+    lib.hs_residual.argtypes = [vp, vp, ci, ci, ctypes.POINTER(hs_boundary), vp, vp,
+                                ctypes.POINTER(cd), ctypes.POINTER(cd)]
+    lib.hs_residual.restype = ci
+    lib.hs_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.hs_stage_times.restype = ci
+    lib.hs_workspace_bytes.argtypes = [vp]
+    lib.hs_workspace_bytes.restype = ctypes.c_size_t
+    lib.hs_destroy.argtypes = [vp]
+    lib.hs_destroy.restype = ci
+    lib.hs_status_str.argtypes = [ci]
+    lib.hs_status_str.restype = ctypes.c_char_p
+    lib.hs_last_error.argtypes = [vp]
+    lib.hs_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_str(s: int) -> str:
+    try:
+        return load().hs_status_str(int(s)).decode()
+    except Exception:  # library missing: still describe the code
+        return f"hs_status {s}"
+
+
+def _check(st, where, plan=None):
+    if st < 0:
+        detail = ""
+        if plan:
+            detail = load().hs_last_error(plan).decode()
+        raise HsError(st, where, detail)
+    return st
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("arrays must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return getattr(stream, "cuda_stream", None) or None
+
+
+# ------------------------------------------------------------------ C ABI calls
+
+
+def hs_plan(Nx, Ny, Nz, Lx, Ly, Lz, order, equation=HS_HELMHOLTZ, bc=HS_BC_DIRICHLET,
+            precision=HS_FP64, max_rhs=1):
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib.hs_plan(ctypes.byref(h), Nx, Ny, Nz, Lx, Ly, Lz, order, equation, bc,
+                       precision, max_rhs), "hs_plan")
+    return h.value
+
+
+def hs_set_coeff(plan, c0, c1=None, c2=None, cd_variant=HS_CD_CORRECTED):
+    """c0, c1, c2: host float64 arrays of length Nz+2 (numpy)."""
+    import numpy as np
+    arrs = [None if c is None else np.ascontiguousarray(c, dtype=np.float64) for c in (c0, c1, c2)]
+    return _check(load().hs_set_coeff(plan, *[_ptr(a) for a in arrs], cd_variant),
+                  "hs_set_coeff", plan)
+
+
+def hs_set_refinement(plan, sweeps):
+    return _check(load().hs_set_refinement(plan, sweeps), "hs_set_refinement", plan)
+
+
+def hs_set_stage_timing(plan, on):
+    return _check(load().hs_set_stage_timing(plan, 1 if on else 0), "hs_set_stage_timing", plan)
+
+
+def make_boundary(faces: Optional[Sequence] = None, fnn: Optional[Sequence] = None):
+    b = hs_boundary()
+    for k in range(6):
+        b.face[k] = _ptr(faces[k]) if faces is not None and faces[k] is not None else None
+        b.fnn[k] = _ptr(fnn[k]) if fnn is not None and fnn[k] is not None else None
+    return b
+
+
+def hs_solve(plan, f, f_dtype, rhs_kind, bnd, u, nrhs=1, stream=None, info=False):
+    """Returns (status, info dict or None).  bnd: hs_boundary or None."""
+    inf = hs_info() if info else None
+    st = load().hs_solve(plan, _ptr(f), f_dtype, rhs_kind,
+                         ctypes.byref(bnd) if bnd is not None else None, _ptr(u), nrhs,
+                         _stream_ptr(stream), ctypes.byref(inf) if inf is not None else None)
+    _check(st, "hs_solve", plan)
+    return st, (inf.as_dict() if inf is not None else None)
+
+
+def hs_residual(plan, f, f_dtype, rhs_kind, bnd, u, stream=None):
+    r = ctypes.c_double()
+    n = ctypes.c_double()
+    _check(load().hs_residual(plan, _ptr(f), f_dtype, rhs_kind,
+                              ctypes.byref(bnd) if bnd is not None else None, _ptr(u),
+                              _stream_ptr(stream), ctypes.byref(r), ctypes.byref(n)),
+           "hs_residual", plan)
+    return r.value, n.value
+
+
+def hs_stage_times(plan):
+    """Per-stage device ms of the last solve (stage timing on), keyed by STAGES."""
+    arr = (ctypes.c_float * HS_INFO_STAGES)()
+    _check(load().hs_stage_times(plan, arr), "hs_stage_times", plan)
+    return dict(zip(STAGES, list(arr)))
+
+
+def hs_workspace_bytes(plan):
+    return int(load().hs_workspace_bytes(plan))
+
+
+def hs_destroy(plan):
+    if plan:
+        return _check(load().hs_destroy(plan), "hs_destroy")
+    return HS_OK
+
+
+def hs_last_error(plan):
+    return load().hs_last_error(plan).decode()
+
+
+def hs_status_str(s):
+    return status_str(s)
+
+
+# ------------------------------------------------------------------ convenience
+
+
+class Solver:
+    """Owns one plan; marshals torch / numpy arrays to hs_solve."""
+
+    def __init__(self, Nx, Ny, Nz, Lx, Ly, Lz, order, equation=HS_HELMHOLTZ,
+                 precision=HS_FP64, max_rhs=1):
+        self.shape = (Nz, Ny, Nx)
+        self.order, self.equation, self.precision = order, equation, precision
+        self.plan = hs_plan(Nx, Ny, Nz, Lx, Ly, Lz, order, equation, HS_BC_DIRICHLET,
+                            precision, max_rhs)
+
+    def set_coeff(self, c0, c1=None, c2=None, cd_variant=HS_CD_CORRECTED):
+        return hs_set_coeff(self.plan, c0, c1, c2, cd_variant)
+
+    def solve(self, f, u, f_dtype=HS_F64, rhs_kind=HS_RHS_NODAL, faces=None, fnn=None, nrhs=1,
+              stream=None, info=False):
+        b = make_boundary(faces, fnn) if (faces is not None or fnn is not None) else None
+        self._keep = (f, u, faces, fnn)  # arrays stay alive until the next call
+        return hs_solve(self.plan, f, f_dtype, rhs_kind, b, u, nrhs, stream, info)
+
+    def close(self):
+        if getattr(self, "plan", None):
+            hs_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,713 @@
+// C ABI of the solver (declared in include/hs.h): plan creation, coefficient
+// tables, the solve pipeline and diagnostics.  Host code only; the kernels
+// live in k_dst.cu, k_rhs.cu and k_thomas.cu.
+//
+// Solve pipeline (Section 3.6 with Algorithm 1's three phases, per RHS):
+//   FP64 path:  F = R_h f - lift          (k_rhs, FP64)
+//               Fhat = DST_y DST_x F       (k_dst, FP64, in place)
+//               W = T_pq^{-1} Fhat         (k_thomas, FP64, cached LU)
+//               U = 4/((Nx+1)(Ny+1)) DST_x DST_y W
+//   Mixed path: F as above, kept in FP64; U_0 = 0; for m = 0..sweeps:
+//               r = F - A U_m (FP64 27-point; r = F for m = 0), rounded to FP32,
+//               U_{m+1} = U_m + (FP32 DSTs, FP64 z-solves) r.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "hs_internal.cuh"
+
+namespace {
+
+void set_err(hs_plan_s *P, const char *fmt, ...) {
+    if (!P) return;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(P->last_error, sizeof(P->last_error), fmt, ap);
+    va_end(ap);
+}
+
+#define HS_CK(P, call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            set_err(P, "%s failed: %s", #call, cudaGetErrorString(e_));                  \
+            return (e_ == cudaErrorMemoryAllocation) ? HS_ERR_OOM : HS_ERR_CUDA;         \
+        }                                                                                \
+    } while (0)
+
+#define HS_TRY(P, expr)                                                                  \
+    do {                                                                                 \
+        hs_status st_ = (expr);                                                          \
+        if (st_ < 0) {                                                                   \
+            if (!P->last_error[0]) set_err(P, "%s failed (%d): %s", #expr, st_,           \
+                                           cudaGetErrorString(cudaGetLastError()));      \
+            return st_;                                                                  \
+        }                                                                                \
+    } while (0)
+
+// Stages of M = 2^a 3^b (4s, then one 2, then 3s); 0 when M has another factor.
+int plan_radix(int M, int *radix, int *nst) {
+    int n = 0;
+    while (M % 4 == 0 && n < HS_MAX_STAGES) { radix[n++] = 4; M /= 4; }
+    while (M % 2 == 0 && n < HS_MAX_STAGES) { radix[n++] = 2; M /= 2; }
+    while (M % 3 == 0 && n < HS_MAX_STAGES) { radix[n++] = 3; M /= 3; }
+    *nst = n;
+    return M == 1 ? 1 : 0;
+}
+
+// sin(pi * num / den) with the argument reduced exactly to [0, pi/2]
+// before the FP64 sine (num, den integers, den > 0).
+double sin_pi_ratio(long num, long den) {
+    long m = num % (2 * den);
+    if (m < 0) m += 2 * den;
+    double sign = 1.0;
+    if (m >= den) { m -= den; sign = -1.0; }        // sin(x + pi) = -sin x
+    if (2 * m > den) m = den - m;                   // sin(pi - x) = sin x
+    return sign * sin(M_PI * (double)m / (double)den);
+}
+double cos_pi_ratio(long num, long den) { return sin_pi_ratio(2 * num + den, 2 * den); }
+
+bool is_device_ptr(const void *p) {
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+hs_status dev_alloc(hs_plan_s *P, T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) return HS_OK;
+    HS_CK(P, cudaMalloc((void **)p, n * sizeof(T)));
+    P->bytes += n * sizeof(T);
+    return HS_OK;
+}
+
+void free_plan(hs_plan_s *P) {
+    if (!P) return;
+    void *ptrs[] = {P->d_coef, P->d_c0, P->d_c1, P->d_cx, P->d_cy, P->d_fac, P->d_red,
+                    P->d_tables, P->d_w64, P->d_w32, P->d_dscr, P->d_stage_f, P->d_stage_u,
+                    P->d_stage_bnd};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    if (P->have_events) {
+        for (int k = 0; k < 2 * HS_EVENT_PAIRS; ++k) cudaEventDestroy(P->ev[k]);
+        cudaEventDestroy(P->ev_total[0]);
+        cudaEventDestroy(P->ev_total[1]);
+    }
+    delete P;
+}
+
+// Builds the FP64 and FP32 transform tables of both axes in one allocation.
+hs_status build_tables(hs_plan_s *P) {
+    const int Ns[2] = {P->Nx, P->Ny};
+    size_t tot = 0;
+    size_t off_d[2][3], off_f[2][3];
+    for (int a = 0; a < 2; ++a) {
+        const int M = Ns[a] + 1;
+        off_d[a][0] = tot; tot += (size_t)M * 16;
+        off_d[a][1] = tot; tot += (size_t)(M + 1) * 16;
+        off_d[a][2] = tot; tot += (size_t)2 * M * 8;
+        off_f[a][0] = tot; tot += (size_t)M * 8;
+        off_f[a][1] = tot; tot += (size_t)(M + 1) * 8;
+        off_f[a][2] = tot; tot += (size_t)2 * M * 4;
+        tot = (tot + 255) & ~(size_t)255;
+    }
+    std::vector<unsigned char> host(tot, 0);
+    for (int a = 0; a < 2; ++a) {
+        const int N = Ns[a], M = N + 1;
+        double *rd = reinterpret_cast<double *>(&host[off_d[a][0]]);
+        double *hd = reinterpret_cast<double *>(&host[off_d[a][1]]);
+        double *sd = reinterpret_cast<double *>(&host[off_d[a][2]]);
+        float *rf = reinterpret_cast<float *>(&host[off_f[a][0]]);
+        float *hf = reinterpret_cast<float *>(&host[off_f[a][1]]);
+        float *sf = reinterpret_cast<float *>(&host[off_f[a][2]]);
+        for (int k = 0; k < M; ++k) {   // exp(-2 pi i k / M)
+            rd[2 * k] = cos_pi_ratio(2L * k, M);
+            rd[2 * k + 1] = -sin_pi_ratio(2L * k, M);
+            rf[2 * k] = (float)rd[2 * k];
+            rf[2 * k + 1] = (float)rd[2 * k + 1];
+        }
+        for (int k = 0; k <= M; ++k) {  // (cos(pi k / M), sin(pi k / M))
+            hd[2 * k] = cos_pi_ratio(k, M);
+            hd[2 * k + 1] = sin_pi_ratio(k, M);
+            hf[2 * k] = (float)hd[2 * k];
+            hf[2 * k + 1] = (float)hd[2 * k + 1];
+        }
+        for (int m = 0; m < 2 * M; ++m) {
+            sd[m] = sin_pi_ratio(m, M);
+            sf[m] = (float)sd[m];
+        }
+    }
+    HS_TRY(P, dev_alloc(P, (unsigned char **)&P->d_tables, tot));
+    HS_CK(P, cudaMemcpy(P->d_tables, host.data(), tot, cudaMemcpyHostToDevice));
+    unsigned char *base = static_cast<unsigned char *>(P->d_tables);
+    for (int a = 0; a < 2; ++a) {
+        const int N = Ns[a], M = N + 1;
+        DstAxis ax;
+        memset(&ax, 0, sizeof(ax));
+        ax.N = N;
+        ax.M = M;
+        ax.fft = plan_radix(M, ax.radix, &ax.nst);
+        DstAxis af = ax;
+        ax.roots = base + off_d[a][0];
+        ax.half = base + off_d[a][1];
+        ax.sintab = base + off_d[a][2];
+        af.roots = base + off_f[a][0];
+        af.half = base + off_f[a][1];
+        af.sintab = base + off_f[a][2];
+        P->axd[a] = ax;
+        P->axf[a] = af;
+    }
+    return HS_OK;
+}
+
+// Per-row stencil coefficients C[l][nu][a,b,c,d] (Sections 3.2-3.5).
+void stencil_table(const hs_plan_s *P, const double *c0, const double *c1, const double *c2,
+                   int cd_variant, double *C) {
+    const int Nz = P->Nz;
+    const double hx = P->hx, hy = P->hy, hz = P->hz;
+    const double Rzx = hz * hz / (hx * hx), Rzy = hz * hz / (hy * hy);
+    memset(C, 0, sizeof(double) * 12 * (size_t)Nz);
+    for (int l = 1; l <= Nz; ++l) {
+        double *lo = C + (size_t)(l - 1) * 12, *mid = lo + 4, *up = lo + 8;
+        if (P->equation == HS_HELMHOLTZ) {
+            const double K = c0[l], Km = c0[l - 1], Kp = c0[l + 1];
+            if (P->order == 2) {
+                mid[1] = Rzx;
+                mid[2] = Rzy;
+                lo[3] = up[3] = 1.0;
+                mid[3] = -2.0 * (Rzx + Rzy + 1.0) + hz * hz * K;
+            } else if (P->order == 4) {
+                lo[1] = up[1] = (1.0 + Rzx) / 12.0;
+                lo[2] = up[2] = (1.0 + Rzy) / 12.0;
+                lo[3] = 2.0 / 3.0 - (Rzx + Rzy) / 6.0 + hz * hz * Km / 12.0;
+                up[3] = 2.0 / 3.0 - (Rzx + Rzy) / 6.0 + hz * hz * Kp / 12.0;
+                mid[0] = (Rzx + Rzy) / 12.0;
+                mid[1] = (4.0 * Rzx - Rzy - 1.0 + hz * hz * K / 2.0) / 6.0;
+                mid[2] = (4.0 * Rzy - Rzx - 1.0 + hz * hz * K / 2.0) / 6.0;
+                mid[3] = -4.0 * (1.0 + Rzx + Rzy) / 3.0 + hz * hz * K / 2.0;
+            } else {
+                const double h = hz, h2 = h * h, h3 = h2 * h, h4 = h2 * h2;
+                const double Kz = c1[l], Kzz = c2[l];
+                lo[0] = up[0] = 1.0 / 30.0;
+                lo[1] = lo[2] = 0.1 + h2 * Km / 90.0 - h3 * Kz / 120.0;
+                up[1] = up[2] = 0.1 + h2 * Kp / 90.0 + h3 * Kz / 120.0;
+                lo[3] = 7.0 / 15.0 - h2 * Km / 90.0 - (h3 * Kz / 20.0) * (1.0 / 3.0 + h2 * Km / 6.0);
+                up[3] = 7.0 / 15.0 - h2 * Kp / 90.0 + (h3 * Kz / 20.0) * (1.0 / 3.0 + h2 * Kp / 6.0);
+                mid[0] = 0.1 + h2 * K / 90.0;
+                mid[1] = mid[2] = 7.0 / 15.0 - h2 * K / 90.0;
+                mid[3] = -64.0 / 15.0 + 14.0 * h2 * K / 15.0 - h4 * K * K / 20.0 + h4 * Kzz / 20.0;
+            }
+        } else {
+            const double g = c0[l];
+            const double s[2] = {-1.0, 1.0};
+            double *rows[2] = {lo, up};
+            for (int k = 0; k < 2; ++k) {
+                rows[k][1] = (1.0 + Rzx) * (2.0 + s[k] * g * hz) / 24.0;
+                rows[k][2] = (1.0 + Rzy) * (2.0 + s[k] * g * hz) / 24.0;
+                rows[k][3] = 2.0 / 3.0 - (Rzx + Rzy) / 6.0 +
+                             s[k] * (hz * g / 12.0) * (4.0 - Rzx - Rzy + s[k] * hz * g);
+            }
+            mid[0] = (Rzx + Rzy) / 12.0;
+            mid[1] = (4.0 * Rzx - Rzy - 1.0) / 6.0;
+            mid[2] = (4.0 * Rzy - Rzx - 1.0) / 6.0;
+            mid[3] = -4.0 * (1.0 + Rzx + Rzy) / 3.0 - hz * hz * g * g / 6.0;
+            if (cd_variant == HS_CD_CORRECTED) {
+                const double g1 = c1 ? c1[l] : 0.0, g2 = c2 ? c2[l] : 0.0;
+                const double t3 = hz * hz * hz * (g2 + g * g1) / 24.0;
+                const double t2 = hz * hz * g1 / 6.0;
+                up[3] += t3 + t2;
+                lo[3] += -t3 + t2;
+                mid[3] += -hz * hz * g1 / 3.0;
+            }
+        }
+    }
+}
+
+size_t node_count(const hs_plan_s *P) {
+    return (size_t)(P->Nx + 2) * (P->Ny + 2) * (P->Nz + 2);
+}
+size_t interior_count(const hs_plan_s *P) { return (size_t)P->Nx * P->Ny * P->Nz; }
+size_t face_count(const hs_plan_s *P, int k) {
+    if (k < 2) return (size_t)(P->Nz + 2) * (P->Ny + 2);
+    if (k < 4) return (size_t)(P->Nz + 2) * (P->Nx + 2);
+    return (size_t)(P->Ny + 2) * (P->Nx + 2);
+}
+
+// Copies host-resident boundary arrays to the plan's staging buffer.
+hs_status stage_boundary(hs_plan_s *P, const hs_boundary *bnd, size_t esz, cudaStream_t s,
+                         DevBoundary *out) {
+    memset(out, 0, sizeof(*out));
+    if (!bnd) return HS_OK;
+    size_t need = 0;
+    for (int k = 0; k < 12; ++k) {
+        const void *p = (k < 6) ? bnd->face[k] : bnd->fnn[k - 6];
+        if (p && !is_device_ptr(p)) need += ((face_count(P, k % 6) * esz + 255) & ~(size_t)255);
+    }
+    if (need > P->stage_bnd_bytes) {
+        if (P->d_stage_bnd) {
+            cudaFree(P->d_stage_bnd);
+            P->bytes -= P->stage_bnd_bytes;
+        }
+        P->d_stage_bnd = nullptr;
+        P->stage_bnd_bytes = 0;
+        HS_TRY(P, dev_alloc(P, (unsigned char **)&P->d_stage_bnd, need));
+        P->stage_bnd_bytes = need;
+    }
+    size_t off = 0;
+    for (int k = 0; k < 12; ++k) {
+        const void *p = (k < 6) ? bnd->face[k] : bnd->fnn[k - 6];
+        const void **dst = (k < 6) ? &out->face[k] : &out->fnn[k - 6];
+        if (!p) continue;
+        if (is_device_ptr(p)) {
+            *dst = p;
+            continue;
+        }
+        const size_t nb = face_count(P, k % 6) * esz;
+        unsigned char *d = static_cast<unsigned char *>(P->d_stage_bnd) + off;
+        HS_CK(P, cudaMemcpyAsync(d, p, nb, cudaMemcpyHostToDevice, s));
+        *dst = d;
+        off += (nb + 255) & ~(size_t)255;
+    }
+    return HS_OK;
+}
+
+// Records an event pair around each stage launch without synchronising.  The
+// pairs live in the plan; hs_stage_times (or a solve with hs_info) reads them
+// once the stream has passed them, so timing does not change the launch
+// stream.  When the pool is full it is drained first (one synchronisation).
+void timer_drain(hs_plan_s *P) {
+    if (P->timer_used == 0) return;
+    cudaEventSynchronize(P->ev[2 * (P->timer_used - 1) + 1]);
+    for (int k = 0; k < P->timer_used; ++k) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, P->ev[2 * k], P->ev[2 * k + 1]);
+        P->timer_acc[P->timer_stage[k]] += ms;
+    }
+    P->timer_used = 0;
+}
+
+struct StageTimer {
+    hs_plan_s *P;
+    cudaStream_t s;
+    bool on;
+    StageTimer(hs_plan_s *p, cudaStream_t st, bool o) : P(p), s(st), on(o) {}
+    void begin(int k) {
+        if (!on) return;
+        if (P->timer_used == HS_EVENT_PAIRS) timer_drain(P);
+        P->timer_stage[P->timer_used] = k;
+        cudaEventRecord(P->ev[2 * P->timer_used], s);
+    }
+    void end(int k) {
+        if (!on) return;
+        (void)k;
+        cudaEventRecord(P->ev[2 * P->timer_used + 1], s);
+        ++P->timer_used;
+    }
+};
+
+void timer_reset(hs_plan_s *P) {
+    P->timer_used = 0;
+    for (int k = 0; k < HS_INFO_STAGES; ++k) P->timer_acc[k] = 0.f;
+    P->timer_total_pending = 0;
+}
+
+// Drains the pending pairs and the total; fills ms[HS_INFO_STAGES].
+void timer_read(hs_plan_s *P, float *ms) {
+    timer_drain(P);
+    if (P->timer_total_pending) {
+        cudaEventSynchronize(P->ev_total[1]);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, P->ev_total[0], P->ev_total[1]);
+        P->timer_acc[HS_STAGE_TOTAL] = t;
+        P->timer_total_pending = 0;
+    }
+    for (int k = 0; k < HS_INFO_STAGES; ++k) ms[k] = P->timer_acc[k];
+}
+
+// ||F - A U||_2^2 and ||F||^2 into d_red[2], d_red[3] (synchronous).
+hs_status residual_norms(hs_plan_s *P, const double *F, const double *U, cudaStream_t s,
+                         double *res2, double *f2) {
+    HS_CK(P, cudaMemsetAsync(P->d_red + 2, 0, 2 * sizeof(double), s));
+    HS_TRY(P, hs_launch_residual(P, F, U, nullptr, P->d_dscr, s));
+    HS_TRY(P, hs_launch_sumsq(P->d_dscr, nullptr, interior_count(P), P->d_red + 2, s));
+    HS_TRY(P, hs_launch_sumsq(F, nullptr, interior_count(P), P->d_red + 3, s));
+    double h[2];
+    HS_CK(P, cudaMemcpyAsync(h, P->d_red + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HS_CK(P, cudaStreamSynchronize(s));
+    *res2 = h[0];
+    *f2 = h[1];
+    return HS_OK;
+}
+
+// One right-hand side: F (lifted, FP64) is in P->d_w64 on entry.
+hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_info *info) {
+    const double sx = 2.0 / (P->Nx + 1), sy = 2.0 / (P->Ny + 1);
+    if (P->precision == HS_FP64) {
+        double *w = P->d_w64;
+        T.begin(HS_STAGE_DST_X);
+        HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F64, HS_T_F64, w, HS_T_F64, w, HS_MODE_WRITE, 1.0, s));
+        T.end(HS_STAGE_DST_X);
+        T.begin(HS_STAGE_DST_Y);
+        HS_TRY(P, hs_launch_dst(P, HS_AXIS_Y, HS_T_F64, HS_T_F64, w, HS_T_F64, w, HS_MODE_WRITE, 1.0, s));
+        T.end(HS_STAGE_DST_Y);
+        T.begin(HS_STAGE_THOMAS);
+        HS_TRY(P, hs_launch_thomas(P, HS_T_F64, w, nullptr, s));
+        T.end(HS_STAGE_THOMAS);
+        T.begin(HS_STAGE_IDST_Y);
+        HS_TRY(P, hs_launch_dst(P, HS_AXIS_Y, HS_T_F64, HS_T_F64, w, HS_T_F64, w, HS_MODE_WRITE, sy, s));
+        T.end(HS_STAGE_IDST_Y);
+        T.begin(HS_STAGE_IDST_X);
+        HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F64, HS_T_F64, w, HS_T_F64, u, HS_MODE_WRITE, sx, s));
+        T.end(HS_STAGE_IDST_X);
+        if (info) {
+            // residual norms use a copy of F: the FP64 path consumed it, so recompute
+            info->iterations = 1;
+        }
+        return HS_OK;
+    }
+    // mixed path
+    float *w = P->d_w32;
+    const double *F = P->d_w64;
+    const int sweeps = P->refine_sweeps;
+    for (int m = 0; m <= sweeps; ++m) {
+        T.begin(HS_STAGE_DST_X);
+        if (m == 0) {
+            HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F64, F, HS_T_F32, w, HS_MODE_WRITE, 1.0, s));
+            T.end(HS_STAGE_DST_X);
+        } else {
+            T.end(HS_STAGE_DST_X);
+            T.begin(HS_STAGE_RESIDUAL);
+            HS_TRY(P, hs_launch_residual(P, F, u, w, nullptr, s));
+            T.end(HS_STAGE_RESIDUAL);
+            T.begin(HS_STAGE_DST_X);
+            HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_F32, w, HS_MODE_WRITE, 1.0, s));
+            T.end(HS_STAGE_DST_X);
+        }
+        T.begin(HS_STAGE_DST_Y);
+        HS_TRY(P, hs_launch_dst(P, HS_AXIS_Y, HS_T_F32, HS_T_F32, w, HS_T_F32, w, HS_MODE_WRITE, 1.0, s));
+        T.end(HS_STAGE_DST_Y);
+        T.begin(HS_STAGE_THOMAS);
+        HS_TRY(P, hs_launch_thomas(P, HS_T_F32, w, P->d_dscr, s));
+        T.end(HS_STAGE_THOMAS);
+        T.begin(HS_STAGE_IDST_Y);
+        HS_TRY(P, hs_launch_dst(P, HS_AXIS_Y, HS_T_F32, HS_T_F32, w, HS_T_F32, w, HS_MODE_WRITE, sy, s));
+        T.end(HS_STAGE_IDST_Y);
+        T.begin(HS_STAGE_IDST_X);
+        HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_F64, u,
+                                m == 0 ? HS_MODE_WRITE : HS_MODE_ADD, sx, s));
+        T.end(HS_STAGE_IDST_X);
+        if (info && m < HS_INFO_MAX_ITERS) {
+            double r2, f2;
+            HS_TRY(P, residual_norms(P, F, u, s, &r2, &f2));
+            info->rel_residual[m] = f2 > 0 ? sqrt(r2 / f2) : sqrt(r2);
+            info->iterations = m + 1;
+        }
+    }
+    return HS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hs_status hs_plan(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, double Lz,
+                  int order, int equation, int bc, int precision, int max_rhs) {
+    if (!out) return HS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (Nx < 1 || Ny < 1 || Nz < 1 || !(Lx > 0) || !(Ly > 0) || !(Lz > 0) || max_rhs < 1)
+        return HS_ERR_INVALID_ARG;
+    if (bc != HS_BC_DIRICHLET) return HS_ERR_UNSUPPORTED;
+    if (equation != HS_HELMHOLTZ && equation != HS_CONVDIFF) return HS_ERR_INVALID_ARG;
+    if (equation == HS_HELMHOLTZ && order != 2 && order != 4 && order != 6)
+        return HS_ERR_INVALID_ARG;
+    if (equation == HS_CONVDIFF && order != 4) return HS_ERR_INVALID_ARG;
+    if (precision != HS_FP64 && precision != HS_MIXED) return HS_ERR_INVALID_ARG;
+    if ((double)Nx * Ny * Nz > 4.0e9 || Nx > 16383 || Ny > 16383) return HS_ERR_UNSUPPORTED;
+    const double hx = Lx / (Nx + 1), hy = Ly / (Ny + 1), hz = Lz / (Nz + 1);
+    if (order == 6) {
+        const double tol = 1e-12 * hz;
+        if (fabs(hx - hz) > tol || fabs(hy - hz) > tol) return HS_ERR_INVALID_ARG;
+    }
+    hs_plan_s *P = new (std::nothrow) hs_plan_s;
+    if (!P) return HS_ERR_OOM;
+    memset(P, 0, sizeof(*P));
+    P->Nx = Nx; P->Ny = Ny; P->Nz = Nz;
+    P->Lx = Lx; P->Ly = Ly; P->Lz = Lz;
+    P->hx = hx; P->hy = hy; P->hz = hz;
+    P->order = order; P->equation = equation; P->precision = precision; P->max_rhs = max_rhs;
+    P->refine_sweeps = 2;
+    P->cd_variant = HS_CD_CORRECTED;
+    if (cudaGetDevice(&P->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        return HS_ERR_CUDA;
+    }
+    for (int a = 0; a < 2; ++a) {
+        DstAxis ax;
+        memset(&ax, 0, sizeof(ax));
+        ax.N = a == 0 ? Nx : Ny;
+        ax.M = ax.N + 1;
+        ax.fft = plan_radix(ax.M, ax.radix, &ax.nst);
+        const int tc = precision == HS_FP64 ? HS_T_F64 : HS_T_F32;
+        if (!hs_dst_fits(ax, a, tc) || !hs_dst_fits(ax, a, HS_T_F64)) {
+            delete P;
+            return HS_ERR_UNSUPPORTED;
+        }
+    }
+    const size_t nint = (size_t)Nx * Ny * Nz;
+    hs_status st = HS_OK;
+    if ((st = dev_alloc(P, &P->d_coef, (size_t)Nz * 12)) ||
+        (st = dev_alloc(P, &P->d_c0, (size_t)Nz + 2)) ||
+        (st = dev_alloc(P, &P->d_c1, (size_t)Nz + 2)) ||
+        (st = dev_alloc(P, &P->d_cx, (size_t)Nx)) || (st = dev_alloc(P, &P->d_cy, (size_t)Ny)) ||
+        (st = dev_alloc(P, &P->d_fac, 3 * nint)) || (st = dev_alloc(P, &P->d_red, (size_t)64)) ||
+        (st = dev_alloc(P, &P->d_w64, nint)) || (st = dev_alloc(P, &P->d_dscr, nint)) ||
+        (precision == HS_MIXED && (st = dev_alloc(P, &P->d_w32, nint))) ||
+        (st = build_tables(P))) {
+        free_plan(P);
+        return st;
+    }
+    std::vector<double> cxh(Nx), cyh(Ny);
+    for (int p = 1; p <= Nx; ++p) cxh[p - 1] = cos_pi_ratio(p, Nx + 1);
+    for (int q = 1; q <= Ny; ++q) cyh[q - 1] = cos_pi_ratio(q, Ny + 1);
+    if (cudaMemcpy(P->d_cx, cxh.data(), Nx * sizeof(double), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(P->d_cy, cyh.data(), Ny * sizeof(double), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        free_plan(P);
+        return HS_ERR_CUDA;
+    }
+    {
+        int ok = 1, k = 0;
+        for (; k < 2 * HS_EVENT_PAIRS && ok; ++k) ok = cudaEventCreate(&P->ev[k]) == cudaSuccess;
+        ok = ok && cudaEventCreate(&P->ev_total[0]) == cudaSuccess;
+        ok = ok && cudaEventCreate(&P->ev_total[1]) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            free_plan(P);  // events are not destroyed: have_events is still 0
+            return HS_ERR_CUDA;
+        }
+        P->have_events = 1;
+    }
+    *out = P;
+    return HS_OK;
+}
+
+hs_status hs_set_coeff(hs_plan_t P, const double *c0, const double *c1, const double *c2,
+                       int cd_variant) {
+    if (!P || !c0) return HS_ERR_INVALID_ARG;
+    if (P->equation == HS_HELMHOLTZ && P->order == 6 && (!c1 || !c2)) {
+        set_err(P, "order 6 needs (k^2)' and (k^2)''");
+        return HS_ERR_INVALID_ARG;
+    }
+    if (P->equation == HS_CONVDIFF && cd_variant != HS_CD_PAPER && cd_variant != HS_CD_CORRECTED)
+        return HS_ERR_INVALID_ARG;
+    const int Nz = P->Nz;
+    for (int l = 0; l < Nz + 2; ++l)
+        if (!isfinite(c0[l]) || (c1 && !isfinite(c1[l])) || (c2 && !isfinite(c2[l])))
+            return HS_ERR_NONFINITE;
+    P->last_error[0] = 0;
+    std::vector<double> C((size_t)Nz * 12), c1v(Nz + 2, 0.0);
+    stencil_table(P, c0, c1, c2, cd_variant, C.data());
+    if (c1)
+        for (int l = 0; l < Nz + 2; ++l) c1v[l] = c1[l];
+    HS_CK(P, cudaMemcpy(P->d_coef, C.data(), C.size() * sizeof(double), cudaMemcpyHostToDevice));
+    HS_CK(P, cudaMemcpy(P->d_c0, c0, (Nz + 2) * sizeof(double), cudaMemcpyHostToDevice));
+    HS_CK(P, cudaMemcpy(P->d_c1, c1v.data(), (Nz + 2) * sizeof(double), cudaMemcpyHostToDevice));
+    const double init[2] = {__builtin_inf(), 0.0};
+    HS_CK(P, cudaMemcpy(P->d_red, init, sizeof(init), cudaMemcpyHostToDevice));
+    HS_TRY(P, hs_launch_factor(P, 0));
+    double red[2];
+    HS_CK(P, cudaMemcpy(red, P->d_red, sizeof(red), cudaMemcpyDeviceToHost));
+    P->min_pivot_ratio = red[1] > 0 ? red[0] / red[1] : 0.0;
+    P->cd_variant = cd_variant;
+    P->have_coeff = 1;
+    return P->min_pivot_ratio < 1e-13 ? HS_WARN_NEAR_SINGULAR : HS_OK;
+}
+
+hs_status hs_set_refinement(hs_plan_t P, int sweeps) {
+    if (!P || sweeps < 0 || sweeps >= HS_INFO_MAX_ITERS) return HS_ERR_INVALID_ARG;
+    P->refine_sweeps = sweeps;
+    return HS_OK;
+}
+
+hs_status hs_set_stage_timing(hs_plan_t P, int on) {
+    if (!P) return HS_ERR_INVALID_ARG;
+    P->stage_timing = on ? 1 : 0;
+    return HS_OK;
+}
+
+hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const hs_boundary *bnd,
+                   double *u, int nrhs, void *stream, hs_info *info) {
+    if (!P || !f || !u) return HS_ERR_INVALID_ARG;
+    if (f_dtype != HS_F64 && f_dtype != HS_F32) return HS_ERR_INVALID_ARG;
+    if (rhs_kind != HS_RHS_NODAL && rhs_kind != HS_RHS_ASSEMBLED) return HS_ERR_INVALID_ARG;
+    if (nrhs < 1 || nrhs > P->max_rhs) return HS_ERR_INVALID_ARG;
+    if (!P->have_coeff) return HS_ERR_NO_COEFF;
+    P->last_error[0] = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t esz = f_dtype == HS_F64 ? 8 : 4;
+    const size_t fcount = rhs_kind == HS_RHS_NODAL ? node_count(P) : interior_count(P);
+    const size_t ucount = interior_count(P);
+
+    // host staging
+    const unsigned char *fd = static_cast<const unsigned char *>(f);
+    if (!is_device_ptr(f)) {
+        const size_t nb = fcount * esz * nrhs;
+        if (nb > P->stage_f_bytes) {
+            if (P->d_stage_f) { cudaFree(P->d_stage_f); P->bytes -= P->stage_f_bytes; }
+            P->d_stage_f = nullptr;
+            P->stage_f_bytes = 0;
+            HS_TRY(P, dev_alloc(P, (unsigned char **)&P->d_stage_f, nb));
+            P->stage_f_bytes = nb;
+        }
+        HS_CK(P, cudaMemcpyAsync(P->d_stage_f, f, nb, cudaMemcpyHostToDevice, s));
+        fd = static_cast<const unsigned char *>(P->d_stage_f);
+    }
+    double *ud = u;
+    const bool u_host = !is_device_ptr(u);
+    if (u_host) {
+        const size_t nb = ucount * sizeof(double) * nrhs;
+        if (nb > P->stage_u_bytes) {
+            if (P->d_stage_u) { cudaFree(P->d_stage_u); P->bytes -= P->stage_u_bytes; }
+            P->d_stage_u = nullptr;
+            P->stage_u_bytes = 0;
+            HS_TRY(P, dev_alloc(P, (unsigned char **)&P->d_stage_u, nb / sizeof(double)));
+            P->stage_u_bytes = nb;
+        }
+        ud = P->d_stage_u;
+    }
+    DevBoundary db;
+    HS_TRY(P, stage_boundary(P, bnd, esz, s, &db));
+
+    StageTimer T(P, s, P->stage_timing != 0 && P->have_events);
+    timer_reset(P);
+    if (T.on) cudaEventRecord(P->ev_total[0], s);
+    for (int r = 0; r < nrhs; ++r) {
+        const void *fr = fd + (size_t)r * fcount * esz;
+        double *ur = ud + (size_t)r * ucount;
+        hs_info *ir = (info && r == nrhs - 1) ? info : nullptr;
+        if (ir) memset(ir, 0, sizeof(*ir));
+        T.begin(HS_STAGE_RHS);
+        HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db, P->d_w64, s));
+        T.end(HS_STAGE_RHS);
+        HS_TRY(P, solve_one(P, ur, s, T, ir));
+        if (ir && P->precision == HS_FP64) {
+            HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db, P->d_w64, s));
+            double r2, f2;
+            HS_TRY(P, residual_norms(P, P->d_w64, ur, s, &r2, &f2));
+            ir->rel_residual[0] = f2 > 0 ? sqrt(r2 / f2) : sqrt(r2);
+        }
+    }
+    if (u_host)
+        HS_CK(P, cudaMemcpyAsync(u, ud, ucount * sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    if (T.on) {
+        cudaEventRecord(P->ev_total[1], s);
+        P->timer_total_pending = 1;
+    }
+    if (info) {
+        info->min_pivot_ratio = P->min_pivot_ratio;
+        HS_CK(P, cudaStreamSynchronize(s));
+        if (T.on) timer_read(P, info->stage_ms);
+    }
+    HS_CK(P, cudaGetLastError());
+    return (P->min_pivot_ratio < 1e-13) ? HS_WARN_NEAR_SINGULAR : HS_OK;
+}
+
+hs_status hs_residual(hs_plan_t P, const void *f, int f_dtype, int rhs_kind,
+                      const hs_boundary *bnd, const double *u, void *stream, double *res_norm,
+                      double *rhs_norm) {
+    if (!P || !f || !u) return HS_ERR_INVALID_ARG;
+    if (!P->have_coeff) return HS_ERR_NO_COEFF;
+    if (f_dtype != HS_F64 && f_dtype != HS_F32) return HS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t esz = f_dtype == HS_F64 ? 8 : 4;
+    const size_t fcount = rhs_kind == HS_RHS_NODAL ? node_count(P) : interior_count(P);
+    const size_t ucount = interior_count(P);
+    const void *fd = f;
+    if (!is_device_ptr(f)) {
+        const size_t nb = fcount * esz;
+        if (nb > P->stage_f_bytes) {
+            if (P->d_stage_f) { cudaFree(P->d_stage_f); P->bytes -= P->stage_f_bytes; }
+            P->d_stage_f = nullptr;
+            P->stage_f_bytes = 0;
+            HS_TRY(P, dev_alloc(P, (unsigned char **)&P->d_stage_f, nb));
+            P->stage_f_bytes = nb;
+        }
+        HS_CK(P, cudaMemcpyAsync(P->d_stage_f, f, nb, cudaMemcpyHostToDevice, s));
+        fd = P->d_stage_f;
+    }
+    const double *ud = u;
+    if (!is_device_ptr(u)) {
+        const size_t nb = ucount * sizeof(double);
+        if (nb > P->stage_u_bytes) {
+            if (P->d_stage_u) { cudaFree(P->d_stage_u); P->bytes -= P->stage_u_bytes; }
+            P->d_stage_u = nullptr;
+            P->stage_u_bytes = 0;
+            HS_TRY(P, dev_alloc(P, (unsigned char **)&P->d_stage_u, ucount));
+            P->stage_u_bytes = nb;
+        }
+        HS_CK(P, cudaMemcpyAsync(P->d_stage_u, u, nb, cudaMemcpyHostToDevice, s));
+        ud = P->d_stage_u;
+    }
+    DevBoundary db;
+    HS_TRY(P, stage_boundary(P, bnd, esz, s, &db));
+    HS_TRY(P, hs_launch_rhs(P, fd, f_dtype, rhs_kind, db, P->d_w64, s));
+    double r2, f2;
+    HS_TRY(P, residual_norms(P, P->d_w64, ud, s, &r2, &f2));
+    if (res_norm) *res_norm = sqrt(r2);
+    if (rhs_norm) *rhs_norm = sqrt(f2);
+    return HS_OK;
+}
+
+hs_status hs_stage_times(hs_plan_t P, float *ms) {
+    if (!P || !ms) return HS_ERR_INVALID_ARG;
+    if (!P->have_events) return HS_ERR_CUDA;
+    timer_read(P, ms);
+    return HS_OK;
+}
+
+size_t hs_workspace_bytes(hs_plan_t P) { return P ? P->bytes : 0; }
+
+hs_status hs_destroy(hs_plan_t P) {
+    if (!P) return HS_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    const int dev = P->device;
+    if (cur != dev) cudaSetDevice(dev);
+    cudaDeviceSynchronize();
+    free_plan(P);
+    if (cur != dev) cudaSetDevice(cur);
+    return HS_OK;
+}
+
+const char *hs_status_str(hs_status s) {
+    switch (s) {
+        case HS_OK: return "HS_OK";
+        case HS_WARN_NEAR_SINGULAR: return "HS_WARN_NEAR_SINGULAR: a z-system has a pivot below 1e-13 of its diagonal";
+        case HS_WARN_NOT_CONVERGED: return "HS_WARN_NOT_CONVERGED: refinement ended above its tolerance";
+        case HS_ERR_INVALID_ARG: return "HS_ERR_INVALID_ARG: invalid argument";
+        case HS_ERR_UNSUPPORTED: return "HS_ERR_UNSUPPORTED: unsupported configuration";
+        case HS_ERR_OOM: return "HS_ERR_OOM: out of device memory";
+        case HS_ERR_CUDA: return "HS_ERR_CUDA: CUDA error";
+        case HS_ERR_NO_COEFF: return "HS_ERR_NO_COEFF: hs_set_coeff was not called";
+        case HS_ERR_TIMEOUT: return "HS_ERR_TIMEOUT: a bounded device wait gave up";
+        case HS_ERR_NONFINITE: return "HS_ERR_NONFINITE: non-finite input";
+        default: return "unknown hs_status";
+    }
+}
+
+const char *hs_last_error(hs_plan_t P) { return P ? P->last_error : "no plan"; }
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// z-direction tridiagonal solves, one per sine mode (p, q) (Section 3.6).
+//
+// Row l of the system of mode (p, q) is
+//     lambda_{l-1}(p,q) w_{l-1} + lambda_l(p,q) w_l + lambda_{l+1}(p,q) w_{l+1} = Fhat_l,
+//     lambda_nu(p,q) = 4 a_nu cos(th_p) cos(th_q) + 2 b_nu cos(th_p) + 2 c_nu cos(th_q) + d_nu,
+// with the coefficients of row l.  It is solved by LU without pivoting (the
+// paper's "LU decomposition"; the systems are indefinite for k^2 above the
+// mode's eigenvalue, so small pivots are reported, not avoided).
+//
+// The elimination factors do not depend on the right-hand side, so they are
+// computed once per coefficient set and cached in FP64:
+//     c'_l = upper_l / m_l,   alpha_l = 1 / m_l,   beta_l = lower_l / m_l,
+//     m_l  = diag_l - lower_l c'_{l-1}.
+// A solve is then d'_l = alpha_l F_l - beta_l d'_{l-1} (forward) and
+// w_l = d'_l - c'_l w_{l+1} (backward): three FP64 operations per unknown.
+// One thread owns one (p, q) column; threads of a warp own consecutive p, so
+// every plane access is coalesced.
+#include "hs_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ void atomic_min_pos(double *addr, double v) {
+    atomicMin(reinterpret_cast<unsigned long long *>(addr),
+              (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_max_pos(double *addr, double v) {
+    atomicMax(reinterpret_cast<unsigned long long *>(addr),
+              (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void __launch_bounds__(256) factor_kernel(int Nx, int Ny, int Nz,
+                                                      const double *__restrict__ coef,
+                                                      const double *__restrict__ cx,
+                                                      const double *__restrict__ cy,
+                                                      double *__restrict__ fac,
+                                                      double *__restrict__ red) {
+    const size_t plane = (size_t)Nx * Ny;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double minpiv = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    double maxdiag = 0.0;
+    if (idx < plane) {
+        const int q = (int)(idx / Nx);
+        const int p = (int)(idx - (size_t)q * Nx);
+        const double cp = cx[p], cq = cy[q];
+        const double P4 = 4.0 * cp * cq, Q2 = 2.0 * cp, R2 = 2.0 * cq;
+        double *cpr = fac;
+        double *alpha = fac + (size_t)Nz * plane;
+        double *beta = fac + 2 * (size_t)Nz * plane;
+        double cprev = 0.0;
+        for (int l = 0; l < Nz; ++l) {
+            const double *cf = coef + (size_t)l * 12;
+            const double lo = cf[0] * P4 + cf[1] * Q2 + cf[2] * R2 + cf[3];
+            const double di = cf[4] * P4 + cf[5] * Q2 + cf[6] * R2 + cf[7];
+            const double up = cf[8] * P4 + cf[9] * Q2 + cf[10] * R2 + cf[11];
+            const double m = (l == 0) ? di : di - lo * cprev;
+            const double inv = 1.0 / m;
+            const double c1 = up * inv;
+            const size_t o = (size_t)l * plane + idx;
+            cpr[o] = c1;
+            alpha[o] = inv;
+            beta[o] = (l == 0) ? 0.0 : lo * inv;
+            cprev = c1;
+            minpiv = fmin(minpiv, fabs(m));
+            maxdiag = fmax(maxdiag, fabs(di));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        minpiv = fmin(minpiv, __shfl_down_sync(0xffffffffu, minpiv, o));
+        maxdiag = fmax(maxdiag, __shfl_down_sync(0xffffffffu, maxdiag, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_min_pos(red + 0, minpiv);
+        atomic_max_pos(red + 1, maxdiag);
+    }
+}
+
+// FP64 path: data holds Fhat on entry and W on exit (forward sweep in place).
+__global__ void __launch_bounds__(256) thomas64_kernel(int Nx, int Ny, int Nz,
+                                                        double *__restrict__ data,
+                                                        const double *__restrict__ fac) {
+    const size_t plane = (size_t)Nx * Ny;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= plane) return;
+    const double *cpr = fac;
+    const double *alpha = fac + (size_t)Nz * plane;
+    const double *beta = fac + 2 * (size_t)Nz * plane;
+    double d = 0.0;
+#pragma unroll 4
+    for (int l = 0; l < Nz; ++l) {
+        const size_t o = (size_t)l * plane + idx;
+        d = alpha[o] * data[o] - beta[o] * d;
+        data[o] = d;
+    }
+    double w = d;
+#pragma unroll 4
+    for (int l = Nz - 2; l >= 0; --l) {
+        const size_t o = (size_t)l * plane + idx;
+        w = data[o] - cpr[o] * w;
+        data[o] = w;
+    }
+}
+
+// Mixed path: FP32 Fhat in, FP32 W out; the forward sweep is kept in FP64.
+__global__ void __launch_bounds__(256) thomas32_kernel(int Nx, int Ny, int Nz,
+                                                        float *__restrict__ data,
+                                                        double *__restrict__ scratch,
+                                                        const double *__restrict__ fac) {
+    const size_t plane = (size_t)Nx * Ny;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= plane) return;
+    const double *cpr = fac;
+    const double *alpha = fac + (size_t)Nz * plane;
+    const double *beta = fac + 2 * (size_t)Nz * plane;
+    double d = 0.0;
+#pragma unroll 4
+    for (int l = 0; l < Nz; ++l) {
+        const size_t o = (size_t)l * plane + idx;
+        d = alpha[o] * (double)data[o] - beta[o] * d;
+        scratch[o] = d;
+    }
+    double w = d;
+    data[(size_t)(Nz - 1) * plane + idx] = (float)w;
+#pragma unroll 4
+    for (int l = Nz - 2; l >= 0; --l) {
+        const size_t o = (size_t)l * plane + idx;
+        w = scratch[o] - cpr[o] * w;
+        data[o] = (float)w;
+    }
+}
+
+}  // namespace
+
+hs_status hs_launch_factor(const hs_plan_s *P, cudaStream_t s) {
+    const size_t plane = (size_t)P->Nx * P->Ny;
+    const unsigned blocks = (unsigned)((plane + 255) / 256);
+    factor_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef, P->d_cx, P->d_cy,
+                                         P->d_fac, P->d_red);
+    return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+hs_status hs_launch_thomas(const hs_plan_s *P, int tio, void *data, double *scratch,
+                           cudaStream_t s) {
+    const size_t plane = (size_t)P->Nx * P->Ny;
+    const unsigned blocks = (unsigned)((plane + 255) / 256);
+    if (tio == HS_T_F64)
+        thomas64_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, static_cast<double *>(data),
+                                               P->d_fac);
+    else
+        thomas32_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, static_cast<float *>(data),
+                                               scratch, P->d_fac);
+    return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}

@@ -1,0 +1,74 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares (no GPU).
+
+Only calls that return before touching the device are exercised here.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_1912_03565_gb300 as H
+from paper_1912_03565_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return H.load()
+
+
+def declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(hdr).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(hs_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "hs_solve" in names and "hs_plan" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_header():
+    assert set(H.EXPORTED) <= set(declared_functions())
+
+
+def test_status_strings(lib):
+    for s in (0, 1, 2, -1, -2, -3, -4, -5, -6, -7):
+        assert lib.hs_status_str(s).decode().startswith("HS_")
+
+
+def test_argument_validation_before_device(lib):
+    h = ctypes.c_void_p()
+    assert lib.hs_plan(None, 4, 4, 4, 1.0, 1.0, 1.0, 4, 0, 0, 0, 1) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_plan(ctypes.byref(h), 0, 4, 4, 1.0, 1.0, 1.0, 4, 0, 0, 0, 1) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_plan(ctypes.byref(h), 4, 4, 4, 1.0, 1.0, 1.0, 5, 0, 0, 0, 1) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_plan(ctypes.byref(h), 4, 4, 4, 1.0, 1.0, 1.0, 6, 1, 0, 0, 1) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_plan(ctypes.byref(h), 4, 4, 4, 1.0, 1.0, -1.0, 4, 0, 0, 0, 1) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_plan(ctypes.byref(h), 4, 4, 5, 1.0, 1.0, 1.0, 6, 0, 0, 0, 1) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_plan(ctypes.byref(h), 4, 4, 4, 1.0, 1.0, 1.0, 4, 0, 3, 0, 1) == H.HS_ERR_UNSUPPORTED
+    assert lib.hs_plan(ctypes.byref(h), 4, 4, 4, 1.0, 1.0, 1.0, 4, 0, 0, 0, 0) == H.HS_ERR_INVALID_ARG
+    assert h.value is None
+    assert lib.hs_destroy(None) == H.HS_OK
+    assert lib.hs_solve(None, None, 0, 0, None, None, 1, None, None) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_set_coeff(None, None, None, None, 0) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_workspace_bytes(None) == 0
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    with pytest.raises(RuntimeError):
+        H._lib_backup = H._lib
+        try:
+            H._lib = None
+            H.load(str(tmp_path / "missing.so"))
+        finally:
+            H._lib = H._lib_backup

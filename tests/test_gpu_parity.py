@@ -1,0 +1,259 @@
+"""GPU parity: the CUDA solver through the C ABI against the FP64 CPU oracle.
+
+Measure: max relative error ||U_gpu - U_oracle||_inf / ||U_oracle||_inf.
+Bars: <= 1e-12 for the FP64 path; <= 1e-10 for the mixed path after
+refinement (the unrefined mixed error is reported by the benchmark, not gated).
+"""
+import numpy as np
+import pytest
+
+import paper_1912_03565_gb300 as H
+import workloads as W
+from oracle import hs_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOLMIX = 1e-10
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def gpu_solve(p, precision=H.HS_FP64, sweeps=2, f_dtype=H.HS_F64, device=True,
+              cd_variant=H.HS_CD_CORRECTED, info=False):
+    torch = _torch()
+    eq = H.HS_CONVDIFF if p.equation == W.CONVDIFF else H.HS_HELMHOLTZ
+    s = H.Solver(p.Nx, p.Ny, p.Nz, p.Lx, p.Ly, p.Lz, p.order, eq, precision)
+    try:
+        s.set_coeff(p.c0, p.c1, p.c2, cd_variant)
+        if precision == H.HS_MIXED:
+            H.hs_set_refinement(s.plan, sweeps)
+        npdt = np.float64 if f_dtype == H.HS_F64 else np.float32
+        f = np.ascontiguousarray(p.f_nodes.astype(npdt))
+        faces = [None if a is None else np.ascontiguousarray(a.astype(npdt)) for a in p.faces]
+        fnn = [None if a is None else np.ascontiguousarray(a.astype(npdt)) for a in p.fnn]
+        if device:
+            f = torch.from_numpy(f).cuda()
+            faces = [None if a is None else torch.from_numpy(a).cuda() for a in faces]
+            fnn = [None if a is None else torch.from_numpy(a).cuda() for a in fnn]
+            u = torch.zeros((p.Nz, p.Ny, p.Nx), dtype=torch.float64, device="cuda")
+        else:
+            u = np.zeros((p.Nz, p.Ny, p.Nx))
+        st, inf = s.solve(f, u, f_dtype, H.HS_RHS_NODAL, faces, fnn, 1, None, info)
+        if device:
+            torch.cuda.synchronize()
+            u = u.cpu().numpy()
+        return u, inf
+    finally:
+        s.close()
+
+
+def oracle_solve(p, f_dtype=H.HS_F64, cd_variant=O.CD_CORRECTED):
+    if f_dtype == H.HS_F32:
+        q = W.Problem(**{**p.__dict__})
+        q.f_nodes = p.f_nodes.astype(np.float32).astype(np.float64)
+        q.faces = [None if a is None else a.astype(np.float32).astype(np.float64) for a in p.faces]
+        q.fnn = [None if a is None else a.astype(np.float32).astype(np.float64) for a in p.fnn]
+        p = q
+    return O.solve(p, cd_variant=cd_variant)[0]
+
+
+def random_problem(shape, order, eq, seed, faces=True):
+    rs = np.random.RandomState(seed)
+    Nx, Ny, Nz = shape
+    if order == 6:
+        h = 1.0 / (max(shape) + 1)
+        L = ((Nx + 1) * h, (Ny + 1) * h, (Nz + 1) * h)
+    else:
+        L = (1.0, 0.8, 1.2)
+    if eq == W.HELMHOLTZ:
+        k = W.k_linear(rs.uniform(3, 12), rs.uniform(0, 1))
+        prof = W.k_profile_to_k2(k)
+    else:
+        g = rs.uniform(-30, 30)
+        prof = W.Profile(lambda z: g + 3 * np.sin(2 * np.pi * z),
+                         lambda z: 6 * np.pi * np.cos(2 * np.pi * z),
+                         lambda z: -12 * np.pi ** 2 * np.sin(2 * np.pi * z))
+    p = W.random_interior_problem(shape, L, order, eq, prof, seed)
+    p.f_nodes = rs.uniform(-1, 1, p.f_nodes.shape)
+    if faces:
+        fc = W.faces_from_nodes(rs.uniform(-1, 1, p.f_nodes.shape))
+        p.faces = fc
+        if order == 6:
+            p.fnn = W.faces_from_nodes(rs.uniform(-1, 1, p.f_nodes.shape))
+    return p
+
+
+# ----------------------------------------------------------------- workloads
+
+
+def test_cube31_order4_fp64_and_mixed():
+    """31^3, 4th order, k = 10 + 5 sin(pi z), manufactured u (one RHS)."""
+    p = W.workload_cube31_order4()
+    ref = oracle_solve(p)
+    u64, _ = gpu_solve(p, H.HS_FP64)
+    assert O.max_rel_diff(u64, ref) <= TOL64
+    umx, inf = gpu_solve(p, H.HS_MIXED, sweeps=2, info=True)
+    assert O.max_rel_diff(umx, ref) <= TOLMIX, inf
+    # the discretisation error is the scheme's (4th order), not the solver's
+    assert O.error_measures(u64, p.u_exact)[0] < 1e-3
+
+
+def test_cube255_order6_fp64_and_mixed():
+    """255^3, 6th order, k = 20 (1 + z^2/2), manufactured f + U[-1,1] noise."""
+    p = W.workload_cube255_order6()
+    ref = oracle_solve(p)
+    u64, _ = gpu_solve(p, H.HS_FP64)
+    assert O.max_rel_diff(u64, ref) <= TOL64
+    umx, inf = gpu_solve(p, H.HS_MIXED, sweeps=2, info=True)
+    assert O.max_rel_diff(umx, ref) <= TOLMIX, inf
+
+
+# ------------------------------------------------------------ schemes, shapes
+
+
+SHAPES = [(17, 23, 11), (32, 7, 9), (10, 4, 6), (1, 2, 3), (63, 31, 20), (26, 35, 5)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("order,eq", [(2, W.HELMHOLTZ), (4, W.HELMHOLTZ), (6, W.HELMHOLTZ),
+                                      (4, W.CONVDIFF)])
+def test_random_problems_fp64(shape, order, eq):
+    """Random f, random Dirichlet faces (and face data for order 6), ragged shapes
+    including lengths without an FFT plan (N + 1 = 11, 5) and N = 1, 2."""
+    p = random_problem(shape, order, eq, seed=sum(shape) * 7 + order)
+    ref = oracle_solve(p)
+    u, _ = gpu_solve(p, H.HS_FP64)
+    assert O.max_rel_diff(u, ref) <= TOL64
+
+
+@pytest.mark.parametrize("shape", [(17, 23, 11), (63, 31, 20)])
+@pytest.mark.parametrize("order,eq", [(4, W.HELMHOLTZ), (6, W.HELMHOLTZ), (4, W.CONVDIFF)])
+def test_random_problems_mixed(shape, order, eq):
+    p = random_problem(shape, order, eq, seed=sum(shape) * 5 + order)
+    ref = oracle_solve(p)
+    u, inf = gpu_solve(p, H.HS_MIXED, sweeps=3, info=True)
+    assert O.max_rel_diff(u, ref) <= TOLMIX, inf
+
+
+@pytest.mark.parametrize("variant", [H.HS_CD_PAPER, H.HS_CD_CORRECTED])
+def test_convdiff_variants(variant):
+    p = random_problem((20, 18, 22), 4, W.CONVDIFF, seed=3)
+    ref = oracle_solve(p, cd_variant=variant)
+    u, _ = gpu_solve(p, H.HS_FP64, cd_variant=variant)
+    assert O.max_rel_diff(u, ref) <= TOL64
+
+
+def test_paper_convdiff_table10_on_gpu():
+    """The GPU reproduces Table 10's 64^3 max-err (gamma = -100, non-homogeneous z-faces)."""
+    p = W.paper_convdiff(64)
+    u, _ = gpu_solve(p, H.HS_FP64)
+    maxe, l2e = O.error_measures(u, p.u_exact)
+    assert maxe == pytest.approx(3.2612907e-03, rel=2e-7)
+    assert l2e == pytest.approx(4.6813690e-04, rel=2e-7)
+
+
+def test_paper_helmholtz_order6_faces():
+    p = W.paper_helmholtz(47, 6)
+    ref = oracle_solve(p)
+    u, _ = gpu_solve(p, H.HS_FP64)
+    assert O.max_rel_diff(u, ref) <= TOL64
+
+
+# ------------------------------------------------------------- interface paths
+
+
+def test_fp32_input():
+    p = random_problem((33, 31, 15), 6, W.HELMHOLTZ, seed=9)
+    ref = oracle_solve(p, f_dtype=H.HS_F32)
+    u, _ = gpu_solve(p, H.HS_FP64, f_dtype=H.HS_F32)
+    assert O.max_rel_diff(u, ref) <= TOL64
+    um, _ = gpu_solve(p, H.HS_MIXED, f_dtype=H.HS_F32)
+    assert O.max_rel_diff(um, ref) <= TOLMIX
+
+
+def test_host_pointers_match_device():
+    p = random_problem((24, 20, 18), 4, W.HELMHOLTZ, seed=4)
+    ud, _ = gpu_solve(p, H.HS_FP64, device=True)
+    uh, _ = gpu_solve(p, H.HS_FP64, device=False)
+    assert np.array_equal(ud, uh)
+
+
+def test_assembled_rhs_and_multi_rhs():
+    torch = _torch()
+    Nx, Ny, Nz = 30, 26, 21
+    rs = np.random.RandomState(2)
+    h = O.grid_steps((Nx, Ny, Nz), (1.0, 1.0, 1.0))
+    K = W.k_profile_to_k2(W.k_10_5sin())
+    c0, c1, c2 = K.sample(Nz, 1.0)
+    C = O.stencil_coefficients(4, W.HELMHOLTZ, h, c0)
+    F = rs.standard_normal((3, Nz, Ny, Nx))
+    refs = [O.solve_assembled(C, F[r])[0] for r in range(3)]
+    s = H.Solver(Nx, Ny, Nz, 1.0, 1.0, 1.0, 4, H.HS_HELMHOLTZ, H.HS_FP64, max_rhs=3)
+    try:
+        s.set_coeff(c0, c1, c2)
+        f = torch.from_numpy(F).cuda()
+        u = torch.zeros_like(f)
+        s.solve(f, u, H.HS_F64, H.HS_RHS_ASSEMBLED, nrhs=3)
+        torch.cuda.synchronize()
+        u = u.cpu().numpy()
+    finally:
+        s.close()
+    for r in range(3):
+        assert O.max_rel_diff(u[r], refs[r]) <= TOL64
+
+
+def test_residual_entry_point():
+    torch = _torch()
+    p = random_problem((31, 31, 31), 6, W.HELMHOLTZ, seed=8)
+    u, _ = gpu_solve(p, H.HS_FP64)
+    C = O.stencil_coefficients(6, W.HELMHOLTZ, p.h, p.c0, p.c1, p.c2)
+    F = O.assemble_rhs(6, W.HELMHOLTZ, p.h, p.f_nodes, C, p.c0, p.c1, p.faces, p.fnn)
+    ref_res = O.residual_l2(C, u, F)
+    s = H.Solver(31, 31, 31, p.Lx, p.Ly, p.Lz, 6)
+    try:
+        s.set_coeff(p.c0, p.c1, p.c2)
+        b = H.make_boundary(p.faces, p.fnn)
+        res, fn = H.hs_residual(s.plan, p.f_nodes, H.HS_F64, H.HS_RHS_NODAL, b, u)
+    finally:
+        s.close()
+    assert fn == pytest.approx(np.linalg.norm(F), rel=1e-12)
+    assert res < 1e-12 * fn
+    assert res == pytest.approx(ref_res, rel=0.5, abs=1e-14 * fn)
+
+
+def test_info_reports_refinement_and_stages():
+    p = random_problem((63, 63, 63), 6, W.HELMHOLTZ, seed=1, faces=False)
+    _, inf = gpu_solve(p, H.HS_MIXED, sweeps=2, info=True)
+    assert inf["iterations"] == 3
+    rr = inf["rel_residual"]
+    assert rr[2] < rr[1] < rr[0] < 1e-4
+    assert inf["min_pivot_ratio"] > 0
+
+
+def test_error_codes_without_touching_data():
+    torch = _torch()
+    with pytest.raises(H.HsError) as e:
+        H.hs_plan(0, 4, 4, 1, 1, 1, 4)
+    assert e.value.status == H.HS_ERR_INVALID_ARG
+    with pytest.raises(H.HsError):
+        H.hs_plan(8, 8, 9, 1.0, 1.0, 1.0, 6)   # order 6 needs a uniform h
+    s = H.Solver(8, 8, 8, 1, 1, 1, 4)
+    try:
+        f = torch.zeros((10, 10, 10), dtype=torch.float64, device="cuda")
+        u = torch.zeros((8, 8, 8), dtype=torch.float64, device="cuda")
+        with pytest.raises(H.HsError) as e:
+            s.solve(f, u)
+        assert e.value.status == H.HS_ERR_NO_COEFF
+        s.set_coeff(np.full(10, 25.0))
+        with pytest.raises(H.HsError) as e:
+            s.solve(f, u, nrhs=2)
+        assert e.value.status == H.HS_ERR_INVALID_ARG
+        with pytest.raises(H.HsError) as e:
+            H.hs_set_coeff(s.plan, np.array([1.0, np.nan] + [1.0] * 8))
+        assert e.value.status == H.HS_ERR_NONFINITE
+    finally:
+        s.close()
