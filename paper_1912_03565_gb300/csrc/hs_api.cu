@@ -583,7 +583,7 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
             if (P->d_stage_u) { cudaFree(P->d_stage_u); P->bytes -= P->stage_u_bytes; }
             P->d_stage_u = nullptr;
             P->stage_u_bytes = 0;
-            HS_TRY(P, dev_alloc(P, (unsigned char **)&P->d_stage_u, nb / sizeof(double)));
+            HS_TRY(P, dev_alloc(P, &P->d_stage_u, ucount * (size_t)nrhs));
             P->stage_u_bytes = nb;
         }
         ud = P->d_stage_u;
@@ -655,7 +655,7 @@ hs_status hs_residual(hs_plan_t P, const void *f, int f_dtype, int rhs_kind,
             if (P->d_stage_u) { cudaFree(P->d_stage_u); P->bytes -= P->stage_u_bytes; }
             P->d_stage_u = nullptr;
             P->stage_u_bytes = 0;
-            HS_TRY(P, dev_alloc(P, (unsigned char **)&P->d_stage_u, ucount));
+            HS_TRY(P, dev_alloc(P, &P->d_stage_u, ucount));
             P->stage_u_bytes = nb;
         }
         HS_CK(P, cudaMemcpyAsync(P->d_stage_u, u, nb, cudaMemcpyHostToDevice, s));
