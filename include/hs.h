@@ -28,8 +28,8 @@
  *    prints.  Negative codes are errors (the outputs are unspecified),
  *    positive codes are warnings (the outputs are valid).
  *  - Distinct plans may be used from distinct host threads concurrently; one
- *    plan must not be used by two threads at once.  The library keeps no
- *    global mutable state.
+ *    plan must not be used by two threads at once.  The only global state
+ *    is the fixed scratch of hs_residual_static and its per-device address.
  */
 #ifndef HS_H
 #define HS_H
@@ -186,6 +186,35 @@ hs_status hs_residual(hs_plan_t plan, const void *f, int f_dtype, int rhs_kind,
  * Errors: HS_ERR_INVALID_ARG.
  */
 hs_status hs_stage_times(hs_plan_t plan, float *ms);
+
+/*
+ * hs_residual_static -- ||F - A U||_2 and ||F||_2 for an assembled, lifted
+ * right-hand side F (zero Dirichlet data), WITHOUT allocating anything.
+ * The paper has no counterpart: this is a library convenience.  It exists for
+ * callers that cannot call cudaMalloc -- code whose device memory belongs to
+ * its own pool allocator or framework, plugins limited to the buffers they
+ * are handed, loops that must not allocate -- and that want to check an
+ * iterate without creating a plan (hs_plan allocates its workspace).
+ *   Nx..Lz, order, equation, cd_variant, c0..c2  as for hs_plan/hs_set_coeff
+ *               (c0..c2 HOST arrays of length Nz+2; order 6 uses h = Lz/(Nz+1)).
+ *   F, u       DEVICE arrays [Nz][Ny][Nx] (FP64); host pointers are rejected.
+ *   stream     cudaStream_t (NULL = legacy default stream).
+ *   res_norm, rhs_norm  host outputs.
+ * Scratch: one file-scope device array of fixed size (the coefficient table
+ * of up to HS_STATIC_MAX_NZ rows plus partial sums, about 0.8 MB) that every
+ * GPU loading the library holds until exit.  Nz > HS_STATIC_MAX_NZ returns
+ * HS_ERR_UNSUPPORTED.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Calls share the array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Synchronous: returns after the norms are read.
+ * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED, HS_ERR_CUDA.
+ */
+#define HS_STATIC_MAX_NZ 8192
+hs_status hs_residual_static(int Nx, int Ny, int Nz, double Lx, double Ly, double Lz, int order,
+                             int equation, int cd_variant, const double *c0, const double *c1,
+                             const double *c2, const double *F, const double *u, void *stream,
+                             double *res_norm, double *rhs_norm);
 
 /* hs_workspace_bytes -- device bytes owned by the plan (tables, cached
  * factorization, workspace). */

@@ -40,7 +40,8 @@ STAGES = ("rhs", "dst_x", "dst_y", "thomas", "idst_y", "idst_x", "residual", "to
 
 EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_stage_timing", "hs_solve",
             "hs_residual", "hs_stage_times", "hs_workspace_bytes", "hs_destroy",
-            "hs_status_str", "hs_last_error")
+            "hs_status_str", "hs_last_error", "hs_residual_static")
+HS_STATIC_MAX_NZ = 8192
 
 
 class hs_boundary(ctypes.Structure):
@@ -96,6 +97,9 @@ def load(path: Optional[str] = None):
     lib.hs_residual.restype = ci
     lib.hs_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.hs_stage_times.restype = ci
+    lib.hs_residual_static.argtypes = [ci, ci, ci, cd, cd, cd, ci, ci, ci, vp, vp, vp, vp, vp, vp,
+                                       ctypes.POINTER(cd), ctypes.POINTER(cd)]
+    lib.hs_residual_static.restype = ci
     lib.hs_workspace_bytes.argtypes = [vp]
     lib.hs_workspace_bytes.restype = ctypes.c_size_t
     lib.hs_destroy.argtypes = [vp]
@@ -208,6 +212,20 @@ def hs_stage_times(plan):
     arr = (ctypes.c_float * HS_INFO_STAGES)()
     _check(load().hs_stage_times(plan, arr), "hs_stage_times", plan)
     return dict(zip(STAGES, list(arr)))
+
+
+def hs_residual_static(Nx, Ny, Nz, Lx, Ly, Lz, order, equation, cd_variant, c0, c1, c2, F, u,
+                       stream=None):
+    """||F - A U||_2, ||F||_2 without any allocation in the library (F, u device arrays)."""
+    import numpy as np
+    arrs = [None if c is None else np.ascontiguousarray(c, dtype=np.float64) for c in (c0, c1, c2)]
+    r = ctypes.c_double()
+    n = ctypes.c_double()
+    _check(load().hs_residual_static(Nx, Ny, Nz, Lx, Ly, Lz, order, equation, cd_variant,
+                                     *[_ptr(a) for a in arrs], _ptr(F), _ptr(u),
+                                     _stream_ptr(stream), ctypes.byref(r), ctypes.byref(n)),
+           "hs_residual_static")
+    return r.value, n.value
 
 
 def hs_workspace_bytes(plan):

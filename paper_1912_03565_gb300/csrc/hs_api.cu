@@ -418,6 +418,12 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
 
 }  // namespace
 
+// Exposed for the fixed-scratch residual entry point (k_noalloc.cu).
+void hs_stencil_table(const hs_plan_s *P, const double *c0, const double *c1, const double *c2,
+                      int cd_variant, double *C) {
+    stencil_table(P, c0, c1, c2, cd_variant, C);
+}
+
 extern "C" {
 
 hs_status hs_plan(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, double Lz,

@@ -118,3 +118,9 @@ hs_status hs_launch_factor(const hs_plan_s *P, cudaStream_t s);
 // the FP64 scratch.
 hs_status hs_launch_thomas(const hs_plan_s *P, int tio, void *data, double *scratch,
                            cudaStream_t s);
+
+// Per-row stencil coefficients C[l][nu][a,b,c,d] for rows l = 1..P->Nz
+// (Sections 3.2-3.5).  Reads P's Nz, h, order and equation only; c0..c2 are
+// host arrays indexed l = 0..Nz+1.
+void hs_stencil_table(const hs_plan_s *P, const double *c0, const double *c1, const double *c2,
+                      int cd_variant, double *C);
