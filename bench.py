@@ -36,24 +36,26 @@ UNIT = "Gunknowns/s"
 # Algorithmic bytes per interior unknown for each stage of one solve, by path
 # (what the stage must read and write: inputs, outputs, cached factors).
 BYTES_MIXED = {
-    "rhs": 16.0,               # read f (FP64 nodes), write F (FP64)
-    "dst_x": None,             # 12 (FP64 F -> FP32) first sweep, 8 after
+    "rhs": 16.0,               # read f (FP64 nodes), write F (double-float pair)
+    "dst_x": 8.0,              # FP32 read (F_hi or r) + FP32 write
     "dst_y": 8.0,              # FP32 read + write
-    "thomas": 32.0,            # FP32 r + FP32 w + 3 FP64 factors
+    "thomas": 20.0,            # FP32 r + FP32 w + 3 FP32 factors (32 with FP64 factors)
     "idst_y": 8.0,
-    "idst_x": None,            # 4 + 8 (write u) first sweep, 4 + 16 (u += ) after
-    "residual": 20.0,          # read F, U (FP64), write r (FP32)
+    "idst_x": None,            # 4 + 8 (set U pair) first sweep, 4 + 16 (U pair += / u) after
+    "residual": 20.0,          # read F pair, U pair (27-point), write r (FP32)
 }
 BYTES_FP64 = {"rhs": 16.0, "dst_x": 16.0, "dst_y": 16.0, "thomas": 40.0, "idst_y": 16.0,
               "idst_x": 16.0, "residual": 0.0}
 
 
-def stage_bytes(path: str, sweeps: int):
+def stage_bytes(path: str, sweeps: int, thomas_fp32: bool = True):
     if path == "fp64":
         return dict(BYTES_FP64)
     b = dict(BYTES_MIXED)
     n = sweeps + 1
-    b["dst_x"] = 12.0 + 8.0 * sweeps
+    if not thomas_fp32:
+        b["thomas"] = 32.0
+    b["dst_x"] *= n
     b["idst_x"] = 12.0 + 20.0 * sweeps
     b["dst_y"] *= n
     b["thomas"] *= n
@@ -317,7 +319,7 @@ def main():
 
     # ---- roofline of the dominant kernel of the mixed path
     hbm_peak, peak_kind = load_peaks()
-    bmix = stage_bytes("mixed", args.sweeps)
+    bmix = stage_bytes("mixed", args.sweeps, inf["min_pivot_ratio"] >= 1e-4)
     kern = max((k for k in bmix if st_mix.get(k, 0) > 0), key=lambda k: st_mix[k])
     nlaunch = {"dst_x": args.sweeps + 1, "dst_y": args.sweeps + 1, "thomas": args.sweeps + 1,
                "idst_y": args.sweeps + 1, "idst_x": args.sweeps + 1, "rhs": 1,
@@ -357,7 +359,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_mix / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 + f32-pair (mixed)",
             "data": "synthetic",
             "config": {"workload": f"cube{args.n}_o6: 6th-order compact Helmholtz, {args.n}^3 "
                                    "interior, h=1/256, k=20(1+z^2/2), manufactured f + U[-1,1] "

@@ -95,7 +95,7 @@ void free_plan(hs_plan_s *P) {
     if (!P) return;
     void *ptrs[] = {P->d_coef, P->d_c0, P->d_c1, P->d_cx, P->d_cy, P->d_fac, P->d_red,
                     P->d_tables, P->d_w64, P->d_w32, P->d_dscr, P->d_stage_f, P->d_stage_u,
-                    P->d_stage_bnd};
+                    P->d_stage_bnd, P->d_fac32, P->d_coef_df, P->d_Fdf, P->d_Udf, P->d_rhs_df};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->have_events) {
@@ -375,24 +375,25 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
         }
         return HS_OK;
     }
-    // mixed path
+    // mixed path: F (double-float planes) in P->d_Fdf on entry; the iterate U
+    // is kept as double-float in P->d_Udf and written to u (FP64) at the end.
     float *w = P->d_w32;
-    const double *F = P->d_w64;
+    const float *F = P->d_Fdf;
+    float *U = P->d_Udf;
+    const size_t n = interior_count(P);
     const int sweeps = P->refine_sweeps;
     for (int m = 0; m <= sweeps; ++m) {
-        T.begin(HS_STAGE_DST_X);
-        if (m == 0) {
-            HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F64, F, HS_T_F32, w, HS_MODE_WRITE, 1.0, s));
-            T.end(HS_STAGE_DST_X);
-        } else {
-            T.end(HS_STAGE_DST_X);
+        const bool last = (m == sweeps);
+        if (m > 0) {
             T.begin(HS_STAGE_RESIDUAL);
-            HS_TRY(P, hs_launch_residual(P, F, u, w, nullptr, s));
+            HS_TRY(P, hs_launch_residual_df(P, F, U, w, s));
             T.end(HS_STAGE_RESIDUAL);
-            T.begin(HS_STAGE_DST_X);
-            HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_F32, w, HS_MODE_WRITE, 1.0, s));
-            T.end(HS_STAGE_DST_X);
         }
+        // m = 0 transforms F_hi (the first plane of F) directly
+        T.begin(HS_STAGE_DST_X);
+        HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, m == 0 ? F : w, HS_T_F32, w,
+                                HS_MODE_WRITE, 1.0, s));
+        T.end(HS_STAGE_DST_X);
         T.begin(HS_STAGE_DST_Y);
         HS_TRY(P, hs_launch_dst(P, HS_AXIS_Y, HS_T_F32, HS_T_F32, w, HS_T_F32, w, HS_MODE_WRITE, 1.0, s));
         T.end(HS_STAGE_DST_Y);
@@ -403,16 +404,31 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
         HS_TRY(P, hs_launch_dst(P, HS_AXIS_Y, HS_T_F32, HS_T_F32, w, HS_T_F32, w, HS_MODE_WRITE, sy, s));
         T.end(HS_STAGE_IDST_Y);
         T.begin(HS_STAGE_IDST_X);
-        HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_F64, u,
-                                m == 0 ? HS_MODE_WRITE : HS_MODE_ADD, sx, s));
+        if (sweeps == 0 && !info) {
+            HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_F64, u,
+                                    HS_MODE_WRITE, sx, s));
+        } else if (last && !info) {
+            HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_DF, U,
+                                    HS_MODE_DF_FINAL, sx, s, u));
+        } else {
+            HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_DF, U,
+                                    m == 0 ? HS_MODE_DF_SET : HS_MODE_DF_ADD, sx, s));
+        }
         T.end(HS_STAGE_IDST_X);
         if (info && m < HS_INFO_MAX_ITERS) {
-            double r2, f2;
-            HS_TRY(P, residual_norms(P, F, u, s, &r2, &f2));
-            info->rel_residual[m] = f2 > 0 ? sqrt(r2 / f2) : sqrt(r2);
+            // ||F - A U|| with the double-float residual, ||F|| from F_hi
+            HS_CK(P, cudaMemsetAsync(P->d_red + 2, 0, 2 * sizeof(double), s));
+            HS_TRY(P, hs_launch_residual_df(P, F, U, w, s));
+            HS_TRY(P, hs_launch_sumsq(nullptr, w, n, P->d_red + 2, s));
+            HS_TRY(P, hs_launch_sumsq(nullptr, F, n, P->d_red + 3, s));
+            double h[2];
+            HS_CK(P, cudaMemcpyAsync(h, P->d_red + 2, sizeof(h), cudaMemcpyDeviceToHost, s));
+            HS_CK(P, cudaStreamSynchronize(s));
+            info->rel_residual[m] = h[1] > 0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
             info->iterations = m + 1;
         }
     }
+    if (info) HS_TRY(P, hs_launch_df_to_f64(U, n, u, s));
     return HS_OK;
 }
 
@@ -479,6 +495,11 @@ hs_status hs_plan(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, 
         (st = dev_alloc(P, &P->d_fac, 3 * nint)) || (st = dev_alloc(P, &P->d_red, (size_t)64)) ||
         (st = dev_alloc(P, &P->d_w64, nint)) || (st = dev_alloc(P, &P->d_dscr, nint)) ||
         (precision == HS_MIXED && (st = dev_alloc(P, &P->d_w32, nint))) ||
+        (precision == HS_MIXED && (st = dev_alloc(P, &P->d_Fdf, 2 * nint))) ||
+        (precision == HS_MIXED && (st = dev_alloc(P, &P->d_Udf, 2 * nint))) ||
+        (precision == HS_MIXED && (st = dev_alloc(P, &P->d_fac32, 3 * nint))) ||
+        (precision == HS_MIXED && (st = dev_alloc(P, &P->d_coef_df, (size_t)Nz * 12))) ||
+        (precision == HS_MIXED && (st = dev_alloc(P, &P->d_rhs_df, (size_t)Nz + 2))) ||
         (st = build_tables(P))) {
         free_plan(P);
         return st;
@@ -529,6 +550,33 @@ hs_status hs_set_coeff(hs_plan_t P, const double *c0, const double *c1, const do
     if (c1)
         for (int l = 0; l < Nz + 2; ++l) c1v[l] = c1[l];
     HS_CK(P, cudaMemcpy(P->d_coef, C.data(), C.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (P->d_coef_df) {
+        std::vector<float2> Cdf(C.size());
+        for (size_t k = 0; k < C.size(); ++k) {
+            const float hi = (float)C[k];
+            Cdf[k] = make_float2(hi, (float)(C[k] - (double)hi));
+        }
+        HS_CK(P, cudaMemcpy(P->d_coef_df, Cdf.data(), Cdf.size() * sizeof(float2),
+                            cudaMemcpyHostToDevice));
+    }
+    if (P->d_rhs_df) {
+        // per-row weights of the double-float right-hand side, formed in FP64
+        std::vector<float4> w(Nz + 2);
+        const double h = P->hz, h2 = h * h;
+        for (int l = 0; l < Nz + 2; ++l) {
+            double a = 0.0, e = 0.0;
+            if (P->equation == HS_CONVDIFF) {
+                e = h * c0[l] / 24.0;
+            } else if (P->order == 6) {
+                a = 67.0 / 120.0 - h2 * c0[l] / 20.0;
+                e = h2 * h * (c1 ? c1[l] : 0.0) / 120.0;
+            }
+            const float ah = (float)a, eh = (float)e;
+            w[l] = make_float4(ah, (float)(a - (double)ah), eh, (float)(e - (double)eh));
+        }
+        HS_CK(P, cudaMemcpy(P->d_rhs_df, w.data(), w.size() * sizeof(float4),
+                            cudaMemcpyHostToDevice));
+    }
     HS_CK(P, cudaMemcpy(P->d_c0, c0, (Nz + 2) * sizeof(double), cudaMemcpyHostToDevice));
     HS_CK(P, cudaMemcpy(P->d_c1, c1v.data(), (Nz + 2) * sizeof(double), cudaMemcpyHostToDevice));
     const double init[2] = {__builtin_inf(), 0.0};
@@ -537,6 +585,8 @@ hs_status hs_set_coeff(hs_plan_t P, const double *c0, const double *c1, const do
     double red[2];
     HS_CK(P, cudaMemcpy(red, P->d_red, sizeof(red), cudaMemcpyDeviceToHost));
     P->min_pivot_ratio = red[1] > 0 ? red[0] / red[1] : 0.0;
+    // FP32 z-solves in the mixed path only when no z-system is close to singular
+    P->thomas32 = (P->precision == HS_MIXED && P->d_fac32 && P->min_pivot_ratio >= 1e-4) ? 1 : 0;
     P->cd_variant = cd_variant;
     P->have_coeff = 1;
     return P->min_pivot_ratio < 1e-13 ? HS_WARN_NEAR_SINGULAR : HS_OK;
@@ -606,11 +656,13 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
         hs_info *ir = (info && r == nrhs - 1) ? info : nullptr;
         if (ir) memset(ir, 0, sizeof(*ir));
         T.begin(HS_STAGE_RHS);
-        HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db, P->d_w64, s));
+        HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db,
+                                P->precision == HS_MIXED ? (void *)P->d_Fdf : (void *)P->d_w64,
+                                P->precision == HS_MIXED, s));
         T.end(HS_STAGE_RHS);
         HS_TRY(P, solve_one(P, ur, s, T, ir));
         if (ir && P->precision == HS_FP64) {
-            HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db, P->d_w64, s));
+            HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db, P->d_w64, 0, s));
             double r2, f2;
             HS_TRY(P, residual_norms(P, P->d_w64, ur, s, &r2, &f2));
             ir->rel_residual[0] = f2 > 0 ? sqrt(r2 / f2) : sqrt(r2);
@@ -669,7 +721,7 @@ hs_status hs_residual(hs_plan_t P, const void *f, int f_dtype, int rhs_kind,
     }
     DevBoundary db;
     HS_TRY(P, stage_boundary(P, bnd, esz, s, &db));
-    HS_TRY(P, hs_launch_rhs(P, fd, f_dtype, rhs_kind, db, P->d_w64, s));
+    HS_TRY(P, hs_launch_rhs(P, fd, f_dtype, rhs_kind, db, P->d_w64, 0, s));
     double r2, f2;
     HS_TRY(P, residual_norms(P, P->d_w64, ud, s, &r2, &f2));
     if (res_norm) *res_norm = sqrt(r2);

@@ -25,8 +25,12 @@ struct DstAxis {
 };
 
 enum { HS_AXIS_X = 0, HS_AXIS_Y = 1 };
-enum { HS_T_F64 = 0, HS_T_F32 = 1 };
-enum { HS_MODE_WRITE = 0, HS_MODE_ADD = 1 };
+enum { HS_T_F64 = 0, HS_T_F32 = 1, HS_T_DF = 2 };
+// Output modes of the inverse x-transform: write, accumulate, and the
+// double-float iterate updates of the mixed path (set hi = X, lo = 0; add X
+// to (hi, lo); add X and write hi + lo as FP64 to the auxiliary array u).
+enum { HS_MODE_WRITE = 0, HS_MODE_ADD = 1, HS_MODE_DF_SET = 2, HS_MODE_DF_ADD = 3,
+       HS_MODE_DF_FINAL = 4 };
 
 // Device views of the boundary data of one solve (pointers already on device).
 struct DevBoundary {
@@ -40,6 +44,7 @@ struct hs_plan_s {
     int order, equation, precision, max_rhs;
     int refine_sweeps;
     int stage_timing;
+    int dst_generic;    // 1: always use the runtime-sized transform kernels
     int have_coeff;
     int cd_variant;
     double min_pivot_ratio;
@@ -52,6 +57,11 @@ struct hs_plan_s {
     double *d_cx;       // [Nx]: cos(p pi / (Nx+1))
     double *d_cy;       // [Ny]
     double *d_fac;      // [3][Nz][Ny][Nx]: c'_l, 1/m_l, lower_l/m_l
+    float *d_fac32;     // the same rounded to FP32 (mixed path, well-conditioned plans)
+    float2 *d_coef_df;  // [Nz][12] coefficients as FP32 pairs (double-float residual)
+    float4 *d_rhs_df;   // [Nz+2] double-float RHS weights: 6th order (67/120 - h^2 K/20,
+                        // h^3 K_z/120); CD (0, h gamma/24)
+    int thomas32;       // mixed path: 1 = FP32 z-solves (min pivot ratio >= 1e-4)
     double *d_red;      // reduction scratch (64 doubles)
 
     // transform tables
@@ -62,6 +72,8 @@ struct hs_plan_s {
     // workspace
     double *d_w64;      // [Nz][Ny][Nx]: FP64 path data, or mixed-path lifted F
     float *d_w32;       // [Nz][Ny][Nx]: mixed-path FP32 work array
+    float *d_Fdf;       // [2][Nz][Ny][Nx]: mixed-path lifted F as double-float (hi, lo planes)
+    float *d_Udf;       // [2][Nz][Ny][Nx]: mixed-path iterate U as double-float
     double *d_dscr;     // [Nz][Ny][Nx]: mixed-path forward-sweep scratch
 
     // host staging (allocated on first use with host pointers)
@@ -89,16 +101,32 @@ struct hs_plan_s {
 
 // Forward/inverse DST-I along one axis of an interior array [Nz][Ny][Nx].
 // out = scale * DST(in) (MODE_WRITE) or out += scale * DST(in) (MODE_ADD,
-// FP64 out only).  `in` and `out` may alias (each block owns its tile).
+// FP64 out only), or a double-float mode (tout = HS_T_DF, out = float2 pairs,
+// aux = FP64 u for MODE_DF_FINAL).  `in` and `out` may alias (each block owns
+// its tile).
 hs_status hs_launch_dst(const hs_plan_s *P, int axis, int tc, int tin, const void *in, int tout,
-                        void *out, int mode, double scale, cudaStream_t s);
+                        void *out, int mode, double scale, cudaStream_t s, double *aux = nullptr);
+
+// Compile-time-sized transform kernels (k_dst_fast.cu): 1 when M = N + 1 has one.
+int hs_dst_fast_size(int M);
+hs_status hs_launch_dst_fast(const hs_plan_s *P, int axis, int tc, int tin, const void *in,
+                             int tout, void *out, int mode, double scale, cudaStream_t s,
+                             double *aux);
 
 // 1 when a line of this axis fits the transform kernel's shared memory.
 int hs_dst_fits(const DstAxis &ax, int axis, int tc);
 
-// Lifted right-hand side F (FP64, interior) from f.
+// Lifted right-hand side F (interior) from f: FP64 (out_df = 0) or a
+// double-float pair in two FP32 planes [2][Nz][Ny][Nx] (out_df = 1).
 hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_kind,
-                        const DevBoundary &b, double *F, cudaStream_t s);
+                        const DevBoundary &b, void *F, int out_df, cudaStream_t s);
+
+// r = F - A U in double-float arithmetic (F, U double-float pairs; r FP32).
+hs_status hs_launch_residual_df(const hs_plan_s *P, const float *F, const float *U, float *r,
+                                cudaStream_t s);
+
+// u = hi + lo in FP64 for a double-float array of n pairs (two planes).
+hs_status hs_launch_df_to_f64(const float *x, size_t n, double *u, cudaStream_t s);
 
 // r = F - A U on the interior (zero Dirichlet data: F is already lifted).
 // r is FP32 (r32 != NULL) or FP64 (r64 != NULL).
@@ -114,8 +142,9 @@ hs_status hs_launch_sumsq(const double *x64, const float *x32, size_t n, double 
 hs_status hs_launch_factor(const hs_plan_s *P, cudaStream_t s);
 
 // z-solves with the cached factorization.  FP64 path: data is FP64, in place
-// (scratch unused).  Mixed path: data is FP32 in place, forward sweep kept in
-// the FP64 scratch.
+// (scratch unused).  Mixed path: data is FP32 in place; with FP64 factors the
+// forward sweep is kept in the FP64 scratch, with FP32 factors (P->thomas32)
+// everything is FP32 and in place.
 hs_status hs_launch_thomas(const hs_plan_s *P, int tio, void *data, double *scratch,
                            cudaStream_t s);
 
@@ -124,3 +153,34 @@ hs_status hs_launch_thomas(const hs_plan_s *P, int tio, void *data, double *scra
 // host arrays indexed l = 0..Nz+1.
 void hs_stencil_table(const hs_plan_s *P, const double *c0, const double *c1, const double *c2,
                       int cd_variant, double *C);
+
+// Shared output step of the transform kernels (see HS_MODE_*).  For the
+// double-float modes Tout is float: the hi plane is out[0, lo_off) and the lo
+// plane out[lo_off, 2 lo_off); aux is the FP64 u of HS_MODE_DF_FINAL.
+#include "hs_df.cuh"
+template <typename Tout, int MODE>
+__device__ __forceinline__ void hs_emit(Tout *out, double *aux, size_t lo_off, size_t idx,
+                                        double v) {
+    if constexpr (MODE == HS_MODE_WRITE) {
+        out[idx] = (Tout)v;
+    } else if constexpr (MODE == HS_MODE_ADD) {
+        out[idx] += (Tout)v;
+    } else if constexpr (MODE == HS_MODE_DF_SET) {
+        out[idx] = (float)v;
+        out[idx + lo_off] = 0.f;
+    } else {
+        dfloat a;
+        a.hi = out[idx];
+        a.lo = out[idx + lo_off];
+        dfloat b;
+        b.hi = (float)v;
+        b.lo = 0.f;
+        const dfloat s = df_add(a, b);
+        if constexpr (MODE == HS_MODE_DF_ADD) {
+            out[idx] = s.hi;
+            out[idx + lo_off] = s.lo;
+        } else {
+            aux[idx] = (double)s.hi + (double)s.lo;
+        }
+    }
+}

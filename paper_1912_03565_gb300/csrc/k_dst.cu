@@ -97,20 +97,14 @@ __device__ __forceinline__ void stockham_stage(const typename Cplx<Tc>::t *src,
     }
 }
 
-template <typename Tout, int MODE>
-__device__ __forceinline__ void emit(Tout *out, size_t idx, double v) {
-    if (MODE == HS_MODE_ADD) {
-        out[idx] += (Tout)v;
-    } else {
-        out[idx] = (Tout)v;
-    }
-}
-
 template <typename Tc, typename Tin, typename Tout, int AXIS, int MODE>
 __global__ void __launch_bounds__(256)
-dst_fft_kernel(DstAxis ax, const Tin *in, Tout *out, int Nx, int Ny, int Nz, int S, Tc scale) {
+dst_fft_kernel(DstAxis ax, const Tin *in, Tout *out, double *aux, int Nx, int Ny, int Nz, int S,
+               Tc scale) {
     typedef typename Cplx<Tc>::t T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const size_t lo_off = (size_t)Nx * Ny * Nz;  // lo plane of a double-float output
+    (void)lo_off;
     const int N = ax.N, M = ax.M;
     const int LS = M + 1;  // padded line stride (complex elements): fewer bank conflicts
     T2 *roots = reinterpret_cast<T2 *>(smem_raw);
@@ -191,7 +185,7 @@ dst_fft_kernel(DstAxis ax, const Tin *in, Tout *out, int Nx, int Ny, int Nz, int
             const T2 Wm = src[(size_t)s * LS + (M - k)];
             const T2 cs = half[k];
             const Tc X = ((Wm.y - Wk.y) + cs.x * (Wk.x - Wm.x) + cs.y * (Wk.y + Wm.y)) * q;
-            emit<Tout, MODE>(out, base + t, (double)X);
+            hs_emit<Tout, MODE>(out, aux, lo_off, base + t, (double)X);
         }
     } else {
         for (int t = threadIdx.x; t < S * N; t += blockDim.x) {
@@ -203,7 +197,7 @@ dst_fft_kernel(DstAxis ax, const Tin *in, Tout *out, int Nx, int Ny, int Nz, int
             const T2 Wm = src[(size_t)s * LS + (M - k)];
             const T2 cs = half[k];
             const Tc X = ((Wm.y - Wk.y) + cs.x * (Wk.x - Wm.x) + cs.y * (Wk.y + Wm.y)) * q;
-            emit<Tout, MODE>(out, base + (size_t)kk * Nx + s, (double)X);
+            hs_emit<Tout, MODE>(out, aux, lo_off, base + (size_t)kk * Nx + s, (double)X);
         }
     }
 }
@@ -211,8 +205,11 @@ dst_fft_kernel(DstAxis ax, const Tin *in, Tout *out, int Nx, int Ny, int Nz, int
 // Direct sums X_k = sum_i x_i sin(pi k i / M) for lengths without an FFT plan.
 template <typename Tc, typename Tin, typename Tout, int AXIS, int MODE>
 __global__ void __launch_bounds__(256)
-dst_direct_kernel(DstAxis ax, const Tin *in, Tout *out, int Nx, int Ny, int Nz, int S, Tc scale) {
+dst_direct_kernel(DstAxis ax, const Tin *in, Tout *out, double *aux, int Nx, int Ny, int Nz, int S,
+                  Tc scale) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const size_t lo_off = (size_t)Nx * Ny * Nz;  // lo plane of a double-float output
+    (void)lo_off;
     const int N = ax.N, M = ax.M, twoM = 2 * M;
     Tc *sint = reinterpret_cast<Tc *>(smem_raw);
     Tc *xs = sint + twoM;
@@ -259,7 +256,7 @@ dst_direct_kernel(DstAxis ax, const Tin *in, Tout *out, int Nx, int Ny, int Nz, 
             acc += x[i - 1] * sint[m];
         }
         const size_t idx = (AXIS == HS_AXIS_X) ? base + t : base + (size_t)(k - 1) * Nx + s;
-        emit<Tout, MODE>(out, idx, (double)(acc * scale));
+        hs_emit<Tout, MODE>(out, aux, lo_off, idx, (double)(acc * scale));
     }
 }
 
@@ -293,7 +290,7 @@ int lines_per_cta(const DstAxis &ax, int axis, size_t *smem) {
 
 template <typename Tc, typename Tin, typename Tout, int MODE>
 hs_status launch_typed(const hs_plan_s *P, int axis, const void *in, void *out, double scale,
-                       cudaStream_t s) {
+                       cudaStream_t s, double *aux) {
     const DstAxis &ax = (sizeof(Tc) == 8) ? P->axd[axis] : P->axf[axis];
     size_t smem = 0;
     const int S = lines_per_cta<Tc>(ax, axis, &smem);
@@ -311,21 +308,21 @@ hs_status launch_typed(const hs_plan_s *P, int axis, const void *in, void *out, 
         if (axis == HS_AXIS_X) {
             auto k = dst_fft_kernel<Tc, Tin, Tout, HS_AXIS_X, MODE>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k<<<grid, 256, smem, s>>>(ax, pin, pout, P->Nx, P->Ny, P->Nz, S, (Tc)scale);
+            k<<<grid, 256, smem, s>>>(ax, pin, pout, aux, P->Nx, P->Ny, P->Nz, S, (Tc)scale);
         } else {
             auto k = dst_fft_kernel<Tc, Tin, Tout, HS_AXIS_Y, MODE>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k<<<grid, 256, smem, s>>>(ax, pin, pout, P->Nx, P->Ny, P->Nz, S, (Tc)scale);
+            k<<<grid, 256, smem, s>>>(ax, pin, pout, aux, P->Nx, P->Ny, P->Nz, S, (Tc)scale);
         }
     } else {
         if (axis == HS_AXIS_X) {
             auto k = dst_direct_kernel<Tc, Tin, Tout, HS_AXIS_X, MODE>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k<<<grid, 256, smem, s>>>(ax, pin, pout, P->Nx, P->Ny, P->Nz, S, (Tc)scale);
+            k<<<grid, 256, smem, s>>>(ax, pin, pout, aux, P->Nx, P->Ny, P->Nz, S, (Tc)scale);
         } else {
             auto k = dst_direct_kernel<Tc, Tin, Tout, HS_AXIS_Y, MODE>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k<<<grid, 256, smem, s>>>(ax, pin, pout, P->Nx, P->Ny, P->Nz, S, (Tc)scale);
+            k<<<grid, 256, smem, s>>>(ax, pin, pout, aux, P->Nx, P->Ny, P->Nz, S, (Tc)scale);
         }
     }
     return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
@@ -340,21 +337,29 @@ int hs_dst_fits(const DstAxis &ax, int axis, int tc) {
 }
 
 hs_status hs_launch_dst(const hs_plan_s *P, int axis, int tc, int tin, const void *in, int tout,
-                        void *out, int mode, double scale, cudaStream_t s) {
+                        void *out, int mode, double scale, cudaStream_t s, double *aux) {
+    if (P->dst_generic == 0 && hs_dst_fast_size(P->axd[axis].M))
+        return hs_launch_dst_fast(P, axis, tc, tin, in, tout, out, mode, scale, s, aux);
     if (tc == HS_T_F64) {
         if (tin == HS_T_F64 && tout == HS_T_F64 && mode == HS_MODE_WRITE)
-            return launch_typed<double, double, double, HS_MODE_WRITE>(P, axis, in, out, scale, s);
+            return launch_typed<double, double, double, HS_MODE_WRITE>(P, axis, in, out, scale, s, aux);
         if (tin == HS_T_F64 && tout == HS_T_F64 && mode == HS_MODE_ADD)
-            return launch_typed<double, double, double, HS_MODE_ADD>(P, axis, in, out, scale, s);
+            return launch_typed<double, double, double, HS_MODE_ADD>(P, axis, in, out, scale, s, aux);
         return HS_ERR_UNSUPPORTED;
     }
     if (tin == HS_T_F64 && tout == HS_T_F32 && mode == HS_MODE_WRITE)
-        return launch_typed<float, double, float, HS_MODE_WRITE>(P, axis, in, out, scale, s);
+        return launch_typed<float, double, float, HS_MODE_WRITE>(P, axis, in, out, scale, s, aux);
     if (tin == HS_T_F32 && tout == HS_T_F32 && mode == HS_MODE_WRITE)
-        return launch_typed<float, float, float, HS_MODE_WRITE>(P, axis, in, out, scale, s);
+        return launch_typed<float, float, float, HS_MODE_WRITE>(P, axis, in, out, scale, s, aux);
     if (tin == HS_T_F32 && tout == HS_T_F64 && mode == HS_MODE_WRITE)
-        return launch_typed<float, float, double, HS_MODE_WRITE>(P, axis, in, out, scale, s);
+        return launch_typed<float, float, double, HS_MODE_WRITE>(P, axis, in, out, scale, s, aux);
     if (tin == HS_T_F32 && tout == HS_T_F64 && mode == HS_MODE_ADD)
-        return launch_typed<float, float, double, HS_MODE_ADD>(P, axis, in, out, scale, s);
+        return launch_typed<float, float, double, HS_MODE_ADD>(P, axis, in, out, scale, s, aux);
+    if (tin == HS_T_F32 && tout == HS_T_DF && mode == HS_MODE_DF_SET)
+        return launch_typed<float, float, float, HS_MODE_DF_SET>(P, axis, in, out, scale, s, aux);
+    if (tin == HS_T_F32 && tout == HS_T_DF && mode == HS_MODE_DF_ADD)
+        return launch_typed<float, float, float, HS_MODE_DF_ADD>(P, axis, in, out, scale, s, aux);
+    if (tin == HS_T_F32 && tout == HS_T_DF && mode == HS_MODE_DF_FINAL)
+        return launch_typed<float, float, float, HS_MODE_DF_FINAL>(P, axis, in, out, scale, s, aux);
     return HS_ERR_UNSUPPORTED;
 }

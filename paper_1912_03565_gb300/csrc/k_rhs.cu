@@ -17,6 +17,7 @@
 // absent, the zero derivative data the paper mentions).
 // Lifting: every stencil neighbour on a boundary node contributes
 // -coef * g to F (the Dirichlet data of eq. (bc) moved to the right side).
+#include "hs_df.cuh"
 #include "hs_internal.cuh"
 
 namespace {
@@ -28,6 +29,7 @@ struct RhsArgs {
     const double *coef;  // [Nz][3][4]
     const double *c0;    // [Nz+2]
     const double *c1;    // [Nz+2]
+    const float4 *rc;    // [Nz+2]: per-row double-float RHS weights (see rhs_tiled_df_kernel)
     DevBoundary b;
 };
 
@@ -77,9 +79,10 @@ __device__ double lift_terms(const RhsArgs &a, int i, int j, int l) {
     return acc;
 }
 
-template <typename T>
+// OUT_DF = 0: F is FP64; OUT_DF = 1: F is stored as a double-float pair (hi, lo).
+template <typename T, int OUT_DF>
 __global__ void __launch_bounds__(256) rhs_kernel(RhsArgs a, const T *__restrict__ f,
-                                                   double *__restrict__ F) {
+                                                   void *__restrict__ Fout) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;  // node indices
     const int j = blockIdx.y * blockDim.y + threadIdx.y + 1;
     const int l = blockIdx.z + 1;
@@ -170,7 +173,298 @@ __global__ void __launch_bounds__(256) rhs_kernel(RhsArgs a, const T *__restrict
     }
     const bool near = (i == 1 || i == a.Nx || j == 1 || j == a.Ny || l == 1 || l == a.Nz);
     if (near) val -= lift_terms<T>(a, i, j, l);
-    F[out] = val;
+    if (OUT_DF) {
+        const dfloat d = df_from_double(val);
+        float *Fo = static_cast<float *>(Fout);
+        Fo[out] = d.hi;
+        Fo[out + (size_t)a.Nx * a.Ny * a.Nz] = d.lo;
+    } else {
+        static_cast<double *>(Fout)[out] = val;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tiled right-hand side for nodal f: a CTA owns a TX x TY patch of interior
+// points and marches over RZ planes in z with a ring of five f-planes in
+// shared memory (halo 2 in x and y; the second neighbours beyond a face are
+// the ghosts 2 f_0 - f_1 + h^2 (f_nn)_face, filled in at load time).  The
+// 6th-order operator is evaluated in the summed form
+//   F6 / h^2 = (67/120 - h^2 K_l / 20) f + S1 / 18 - S2 / 240 + E / 90
+//              + (h^3 K_{z,l} / 120) (f_{l+1} - f_{l-1}),
+// where S1 sums the 6 face neighbours, S2 the 6 second neighbours and E the 12
+// edge mid-points (the same operator as the expanded form above:
+// Dx+Dy+Dz = S1 - 6 f, Dx^2+Dy^2+Dz^2 = S2 - 4 S1 + 18 f,
+// DxDy+DxDz+DyDz = E - 4 S1 + 12 f).
+constexpr int RTX = 32, RTY = 8, RZ = 16;
+constexpr int RHX = RTX + 4, RHY = RTY + 4;
+
+template <typename T>
+__device__ double node_or_ghost(const RhsArgs &a, const T *f, int i, int j, int l) {
+    const int Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
+    const size_t sy = (size_t)(Nx + 2), sz = sy * (Ny + 2);
+    const double h2 = a.hz * a.hz;
+    const bool xin = i >= 0 && i <= Nx + 1, yin = j >= 0 && j <= Ny + 1, zin = l >= 0 && l <= Nz + 1;
+    if (xin && yin && zin) return ld(f, (size_t)l * sz + (size_t)j * sy + i);
+    // ghosts exist one node beyond a face, along that face's normal only
+    if (!xin && yin && zin && (i == -1 || i == Nx + 2)) {
+        const int i0 = (i == -1) ? 0 : Nx + 1, i1 = (i == -1) ? 1 : Nx;
+        const T *fnn = static_cast<const T *>(a.b.fnn[i == -1 ? 0 : 1]);
+        const size_t r = (size_t)l * sz + (size_t)j * sy;
+        return 2.0 * ld(f, r + i0) - ld(f, r + i1) +
+               (fnn ? h2 * ld(fnn, (size_t)l * (Ny + 2) + j) : 0.0);
+    }
+    if (xin && !yin && zin && (j == -1 || j == Ny + 2)) {
+        const int j0 = (j == -1) ? 0 : Ny + 1, j1 = (j == -1) ? 1 : Ny;
+        const T *fnn = static_cast<const T *>(a.b.fnn[j == -1 ? 2 : 3]);
+        const size_t r = (size_t)l * sz + i;
+        return 2.0 * ld(f, r + (size_t)j0 * sy) - ld(f, r + (size_t)j1 * sy) +
+               (fnn ? h2 * ld(fnn, (size_t)l * (Nx + 2) + i) : 0.0);
+    }
+    if (xin && yin && !zin && (l == -1 || l == Nz + 2)) {
+        const int l0 = (l == -1) ? 0 : Nz + 1, l1 = (l == -1) ? 1 : Nz;
+        const T *fnn = static_cast<const T *>(a.b.fnn[l == -1 ? 4 : 5]);
+        const size_t r = (size_t)j * sy + i;
+        return 2.0 * ld(f, (size_t)l0 * sz + r) - ld(f, (size_t)l1 * sz + r) +
+               (fnn ? h2 * ld(fnn, (size_t)j * (Nx + 2) + i) : 0.0);
+    }
+    return 0.0;  // never read by an interior point
+}
+
+template <typename T, int OUT_DF>
+__global__ void __launch_bounds__(RTX *RTY) rhs_tiled_kernel(RhsArgs a, const T *__restrict__ f,
+                                                             void *__restrict__ Fout) {
+    __shared__ double pl[5][RHY][RHX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RTX + tx;
+    const int i0 = 1 + blockIdx.x * RTX, j0 = 1 + blockIdx.y * RTY;
+    const int lbeg = 1 + blockIdx.z * RZ;
+    const int lend = min(lbeg + RZ - 1, a.Nz);
+    const size_t n = (size_t)a.Nx * a.Ny * a.Nz;
+    const double h = a.hz, h2 = h * h;
+
+    auto load_plane = [&](int l) {
+        double(*P)[RHX] = pl[(l + 10) % 5];
+        for (int e = tid; e < RHX * RHY; e += RTX * RTY) {
+            const int ey = e / RHX, ex = e - ey * RHX;
+            P[ey][ex] = node_or_ghost<T>(a, f, i0 - 2 + ex, j0 - 2 + ey, l);
+        }
+    };
+    for (int l = lbeg - 2; l <= lbeg + 1; ++l) load_plane(l);
+    const int i = i0 + tx, j = j0 + ty;
+    const int cx = tx + 2, cy = ty + 2;
+    for (int l = lbeg; l <= lend; ++l) {
+        load_plane(l + 2);
+        __syncthreads();
+        if (i <= a.Nx && j <= a.Ny) {
+            const double(*Pm2)[RHX] = pl[(l + 8) % 5];
+            const double(*Pm)[RHX] = pl[(l + 9) % 5];
+            const double(*P0)[RHX] = pl[(l + 10) % 5];
+            const double(*Pp)[RHX] = pl[(l + 11) % 5];
+            const double(*Pp2)[RHX] = pl[(l + 12) % 5];
+            const double fc = P0[cy][cx];
+            const double fzm = Pm[cy][cx], fzp = Pp[cy][cx];
+            const double S1 = (P0[cy][cx - 1] + P0[cy][cx + 1]) + (P0[cy - 1][cx] + P0[cy + 1][cx]) +
+                              (fzm + fzp);
+            double val;
+            if (a.equation == HS_CONVDIFF) {
+                const double g = a.c0[l];
+                val = h2 * (0.5 * fc + S1 * (1.0 / 12.0) + h * g * (fzp - fzm) * (1.0 / 24.0));
+            } else if (a.order == 2) {
+                val = h2 * fc;
+            } else if (a.order == 4) {
+                val = h2 * (0.5 * fc + S1 * (1.0 / 12.0));
+            } else {
+                const double S2 = (P0[cy][cx - 2] + P0[cy][cx + 2]) +
+                                  (P0[cy - 2][cx] + P0[cy + 2][cx]) + (Pm2[cy][cx] + Pp2[cy][cx]);
+                const double E = ((P0[cy - 1][cx - 1] + P0[cy - 1][cx + 1]) +
+                                  (P0[cy + 1][cx - 1] + P0[cy + 1][cx + 1])) +
+                                 ((Pm[cy][cx - 1] + Pm[cy][cx + 1]) + (Pm[cy - 1][cx] + Pm[cy + 1][cx])) +
+                                 ((Pp[cy][cx - 1] + Pp[cy][cx + 1]) + (Pp[cy - 1][cx] + Pp[cy + 1][cx]));
+                const double K = a.c0[l], Kz = a.c1[l];
+                const double F6 = (67.0 / 120.0 - h2 * K * (1.0 / 20.0)) * fc + S1 * (1.0 / 18.0) -
+                                  S2 * (1.0 / 240.0) + E * (1.0 / 90.0) +
+                                  h2 * h * Kz * (1.0 / 120.0) * (fzp - fzm);
+                val = h2 * F6;
+            }
+            const bool near = (i == 1 || i == a.Nx || j == 1 || j == a.Ny || l == 1 || l == a.Nz);
+            if (near) val -= lift_terms<T>(a, i, j, l);
+            const size_t out = ((size_t)(l - 1) * a.Ny + (j - 1)) * a.Nx + (i - 1);
+            if (OUT_DF) {
+                const dfloat d = df_from_double(val);
+                float *Fo = static_cast<float *>(Fout);
+                Fo[out] = d.hi;
+                Fo[out + n] = d.lo;
+            } else {
+                static_cast<double *>(Fout)[out] = val;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// The same tiled operator in double-float arithmetic (mixed path): f enters
+// shared memory as (hi, lo) pairs (FP64 f split with integer operations,
+// FP32 f exact), the sums and products use two_sum / two_prod, and F is
+// written as its two FP32 planes.  Ghost values and the Dirichlet lifting
+// (points next to a face only) are formed in FP64 and then split.
+template <typename T>
+__device__ __forceinline__ dfloat node_df(const RhsArgs &a, const T *f, int i, int j, int l) {
+    const bool in = i >= 0 && i <= a.Nx + 1 && j >= 0 && j <= a.Ny + 1 && l >= 0 && l <= a.Nz + 1;
+    if (in) {
+        const size_t sy = (size_t)(a.Nx + 2), sz = sy * (a.Ny + 2);
+        return df_of(__ldg(f + (size_t)l * sz + (size_t)j * sy + i));
+    }
+    return df_split_bits(node_or_ghost<T>(a, f, i, j, l));
+}
+
+__device__ __forceinline__ dfloat dsum(dfloat a, dfloat b) { return df_add(a, b); }
+
+template <typename T>
+__global__ void __launch_bounds__(RTX *RTY) rhs_tiled_df_kernel(RhsArgs a, const T *__restrict__ f,
+                                                                float *__restrict__ Fo) {
+    __shared__ float ph[5][RHY][RHX];
+    __shared__ float pq[5][RHY][RHX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RTX + tx;
+    const int i0 = 1 + blockIdx.x * RTX, j0 = 1 + blockIdx.y * RTY;
+    const int lbeg = 1 + blockIdx.z * RZ;
+    const int lend = min(lbeg + RZ - 1, a.Nz);
+    const size_t n = (size_t)a.Nx * a.Ny * a.Nz;
+    const dfloat H2 = df_from_double(a.hz * a.hz);
+    const dfloat C18 = df_from_double(1.0 / 18.0), C240 = df_from_double(-1.0 / 240.0);
+    const dfloat C90 = df_from_double(1.0 / 90.0), C12 = df_from_double(1.0 / 12.0);
+    const dfloat HALF = df_of(0.5f);
+
+    auto load_plane = [&](int l) {
+        const int slot = (l + 10) % 5;
+        for (int e = tid; e < RHX * RHY; e += RTX * RTY) {
+            const int ey = e / RHX, ex = e - ey * RHX;
+            const dfloat v = node_df<T>(a, f, i0 - 2 + ex, j0 - 2 + ey, l);
+            ph[slot][ey][ex] = v.hi;
+            pq[slot][ey][ex] = v.lo;
+        }
+    };
+    for (int l = lbeg - 2; l <= lbeg + 1; ++l) load_plane(l);
+    const int i = i0 + tx, j = j0 + ty;
+    const int cx = tx + 2, cy = ty + 2;
+    for (int l = lbeg; l <= lend; ++l) {
+        load_plane(l + 2);
+        __syncthreads();
+        if (i <= a.Nx && j <= a.Ny) {
+            const int sm2 = (l + 8) % 5, sm = (l + 9) % 5, s0 = (l + 10) % 5, sp = (l + 11) % 5,
+                      sp2 = (l + 12) % 5;
+#define HS_G(S, Y, X) dfloat{ph[S][Y][X], pq[S][Y][X]}
+            const dfloat fc = HS_G(s0, cy, cx);
+            const dfloat fzm = HS_G(sm, cy, cx), fzp = HS_G(sp, cy, cx);
+            const dfloat S1 = dsum(dsum(dsum(HS_G(s0, cy, cx - 1), HS_G(s0, cy, cx + 1)),
+                                        dsum(HS_G(s0, cy - 1, cx), HS_G(s0, cy + 1, cx))),
+                                   dsum(fzm, fzp));
+            dfloat val;
+            const float4 w = a.rc[l];
+            if (a.equation == HS_CONVDIFF) {
+                const dfloat g = dfloat{w.z, w.w};
+                const dfloat dz = df_add_accurate(fzp, df_neg(fzm));
+                val = df_mul(H2, dsum(dsum(df_mul(HALF, fc), df_mul(C12, S1)), df_mul(g, dz)));
+            } else if (a.order == 2) {
+                val = df_mul(H2, fc);
+            } else if (a.order == 4) {
+                val = df_mul(H2, dsum(df_mul(HALF, fc), df_mul(C12, S1)));
+            } else {
+                const dfloat S2 = dsum(dsum(dsum(HS_G(s0, cy, cx - 2), HS_G(s0, cy, cx + 2)),
+                                            dsum(HS_G(s0, cy - 2, cx), HS_G(s0, cy + 2, cx))),
+                                       dsum(HS_G(sm2, cy, cx), HS_G(sp2, cy, cx)));
+                const dfloat Exy = dsum(dsum(HS_G(s0, cy - 1, cx - 1), HS_G(s0, cy - 1, cx + 1)),
+                                        dsum(HS_G(s0, cy + 1, cx - 1), HS_G(s0, cy + 1, cx + 1)));
+                const dfloat Em = dsum(dsum(HS_G(sm, cy, cx - 1), HS_G(sm, cy, cx + 1)),
+                                       dsum(HS_G(sm, cy - 1, cx), HS_G(sm, cy + 1, cx)));
+                const dfloat Ep = dsum(dsum(HS_G(sp, cy, cx - 1), HS_G(sp, cy, cx + 1)),
+                                       dsum(HS_G(sp, cy - 1, cx), HS_G(sp, cy + 1, cx)));
+                const dfloat E = dsum(Exy, dsum(Em, Ep));
+                const dfloat alpha = dfloat{w.x, w.y};
+                const dfloat eps = dfloat{w.z, w.w};
+                const dfloat dz = df_add_accurate(fzp, df_neg(fzm));
+                dfloat F6 = df_mul(alpha, fc);
+                F6 = dsum(F6, df_mul(C18, S1));
+                F6 = dsum(F6, df_mul(C240, S2));
+                F6 = dsum(F6, df_mul(C90, E));
+                F6 = dsum(F6, df_mul(eps, dz));
+                val = df_mul(H2, F6);
+            }
+#undef HS_G
+            const bool near = (i == 1 || i == a.Nx || j == 1 || j == a.Ny || l == 1 || l == a.Nz);
+            if (near) val = df_add_accurate(val, df_neg(df_split_bits(lift_terms<T>(a, i, j, l))));
+            const size_t out = ((size_t)(l - 1) * a.Ny + (j - 1)) * a.Nx + (i - 1);
+            Fo[out] = val.hi;
+            Fo[out + n] = val.lo;
+        }
+        __syncthreads();
+    }
+}
+
+// r = F - A U in double-float arithmetic: F and U are (hi, lo) pairs, the
+// per-row coefficients are split into FP32 pairs, U = 0 outside the interior.
+// A U_hi is accumulated exactly enough (two_sum / two_prod); A U_lo, which is
+// ~2^-24 of it, in plain FP32.  r is rounded to FP32.
+__global__ void __launch_bounds__(256) residual_df_kernel(int Nx, int Ny, int Nz,
+                                                           const float2 *__restrict__ coef,
+                                                           const float *__restrict__ F,
+                                                           const float *__restrict__ U,
+                                                           float *__restrict__ r) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int l = blockIdx.z;
+    if (i >= Nx || j >= Ny) return;
+    const size_t plane = (size_t)Nx * Ny;
+    const size_t n = plane * Nz;
+    const float2 *cf = coef + (size_t)l * 12;
+    const bool im = i > 0, ip = i < Nx - 1, jm = j > 0, jp = j < Ny - 1;
+    const size_t c = (size_t)j * Nx + i;
+    dfloat acc;
+    acc.hi = 0.f;
+    acc.lo = 0.f;
+    float acc_lo = 0.f;
+#pragma unroll
+    for (int dl = -1; dl <= 1; ++dl) {
+        const int ll = l + dl;
+        if (ll < 0 || ll >= Nz) continue;
+        const float *P = U + (size_t)ll * plane;
+        const float *Q = P + n;  // lo plane
+        float h[9], q[9];
+        // 0: (i-1,j-1) 1: (i+1,j-1) 2: (i,j-1) 3: (i-1,j+1) 4: (i+1,j+1) 5: (i,j+1)
+        // 6: (i-1,j) 7: (i+1,j) 8: (i,j)
+        const bool ok[9] = {jm && im, jm && ip, jm, jp && im, jp && ip, jp, im, ip, true};
+        const long off[9] = {-(long)Nx - 1, -(long)Nx + 1, -(long)Nx, (long)Nx - 1, (long)Nx + 1,
+                             (long)Nx, -1, 1, 0};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            h[k] = ok[k] ? __ldg(P + (long)c + off[k]) : 0.f;
+            q[k] = ok[k] ? __ldg(Q + (long)c + off[k]) : 0.f;
+        }
+        const dfloat C = df_add(df_make(h[0], h[1]), df_make(h[3], h[4]));
+        const dfloat X = df_make(h[6], h[7]);
+        const dfloat Y = df_make(h[2], h[5]);
+        dfloat ce;
+        ce.hi = h[8];
+        ce.lo = 0.f;
+        const float2 ka = cf[(dl + 1) * 4 + 0], kb = cf[(dl + 1) * 4 + 1];
+        const float2 kc = cf[(dl + 1) * 4 + 2], kd = cf[(dl + 1) * 4 + 3];
+        dfloat t = df_mul(dfloat{ka.x, ka.y}, C);
+        t = df_add(t, df_mul(dfloat{kb.x, kb.y}, X));
+        t = df_add(t, df_mul(dfloat{kc.x, kc.y}, Y));
+        t = df_add(t, df_mul(dfloat{kd.x, kd.y}, ce));
+        acc = df_add(acc, t);
+        acc_lo += ka.x * ((q[0] + q[1]) + (q[3] + q[4])) + kb.x * (q[6] + q[7]) +
+                  kc.x * (q[2] + q[5]) + kd.x * q[8];
+    }
+    const size_t o = (size_t)l * plane + c;
+    const dfloat res = df_add_accurate(dfloat{F[o], F[o + n]}, df_neg(acc));
+    r[o] = res.hi + (res.lo - acc_lo);
+}
+
+// u (FP64) = hi + lo of a double-float array.
+__global__ void __launch_bounds__(256) df_to_f64_kernel(const float *__restrict__ x, size_t n,
+                                                         double *__restrict__ u) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        u[k] = (double)x[k] + (double)x[k + n];
 }
 
 // r = F - A U with U = 0 outside the interior.
@@ -239,7 +533,7 @@ __global__ void __launch_bounds__(256) sumsq_kernel(const T *__restrict__ x, siz
 }  // namespace
 
 hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_kind,
-                        const DevBoundary &b, double *F, cudaStream_t s) {
+                        const DevBoundary &b, void *F, int out_df, cudaStream_t s) {
     RhsArgs a;
     a.Nx = P->Nx;
     a.Ny = P->Ny;
@@ -251,13 +545,53 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
     a.coef = P->d_coef;
     a.c0 = P->d_c0;
     a.c1 = P->d_c1;
+    a.rc = P->d_rhs_df;
     a.b = b;
+    if (rhs_kind == HS_RHS_NODAL) {
+        dim3 tb(RTX, RTY, 1);
+        dim3 tg((P->Nx + RTX - 1) / RTX, (P->Ny + RTY - 1) / RTY, (P->Nz + RZ - 1) / RZ);
+        if (f_dtype == HS_F64) {
+            if (out_df)
+                rhs_tiled_df_kernel<double><<<tg, tb, 0, s>>>(a, static_cast<const double *>(f),
+                                                              static_cast<float *>(F));
+            else
+                rhs_tiled_kernel<double, 0><<<tg, tb, 0, s>>>(a, static_cast<const double *>(f), F);
+        } else {
+            if (out_df)
+                rhs_tiled_df_kernel<float><<<tg, tb, 0, s>>>(a, static_cast<const float *>(f),
+                                                             static_cast<float *>(F));
+            else
+                rhs_tiled_kernel<float, 0><<<tg, tb, 0, s>>>(a, static_cast<const float *>(f), F);
+        }
+        return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+    }
     dim3 block(32, 8, 1);
     dim3 grid((P->Nx + 31) / 32, (P->Ny + 7) / 8, P->Nz);
-    if (f_dtype == HS_F64)
-        rhs_kernel<double><<<grid, block, 0, s>>>(a, static_cast<const double *>(f), F);
-    else
-        rhs_kernel<float><<<grid, block, 0, s>>>(a, static_cast<const float *>(f), F);
+    if (f_dtype == HS_F64) {
+        if (out_df)
+            rhs_kernel<double, 1><<<grid, block, 0, s>>>(a, static_cast<const double *>(f), F);
+        else
+            rhs_kernel<double, 0><<<grid, block, 0, s>>>(a, static_cast<const double *>(f), F);
+    } else {
+        if (out_df)
+            rhs_kernel<float, 1><<<grid, block, 0, s>>>(a, static_cast<const float *>(f), F);
+        else
+            rhs_kernel<float, 0><<<grid, block, 0, s>>>(a, static_cast<const float *>(f), F);
+    }
+    return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+hs_status hs_launch_residual_df(const hs_plan_s *P, const float *F, const float *U, float *r,
+                                cudaStream_t s) {
+    dim3 block(32, 8, 1);
+    dim3 grid((P->Nx + 31) / 32, (P->Ny + 7) / 8, P->Nz);
+    residual_df_kernel<<<grid, block, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df, F, U, r);
+    return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+hs_status hs_launch_df_to_f64(const float *x, size_t n, double *u, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((n + 255) / 256 < 4864 ? (n + 255) / 256 : 4864);
+    df_to_f64_kernel<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(x, n, u);
     return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 

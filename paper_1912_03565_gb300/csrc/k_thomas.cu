@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(256) factor_kernel(int Nx, int Ny, int Nz,
                                                       const double *__restrict__ cx,
                                                       const double *__restrict__ cy,
                                                       double *__restrict__ fac,
+                                                      float *__restrict__ fac32,
                                                       double *__restrict__ red) {
     const size_t plane = (size_t)Nx * Ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -56,9 +57,15 @@ __global__ void __launch_bounds__(256) factor_kernel(int Nx, int Ny, int Nz,
             const double inv = 1.0 / m;
             const double c1 = up * inv;
             const size_t o = (size_t)l * plane + idx;
+            const double b1 = (l == 0) ? 0.0 : lo * inv;
             cpr[o] = c1;
             alpha[o] = inv;
-            beta[o] = (l == 0) ? 0.0 : lo * inv;
+            beta[o] = b1;
+            if (fac32) {
+                fac32[o] = (float)c1;
+                fac32[(size_t)Nz * plane + o] = (float)inv;
+                fac32[2 * (size_t)Nz * plane + o] = (float)b1;
+            }
             cprev = c1;
             minpiv = fmin(minpiv, fabs(m));
             maxdiag = fmax(maxdiag, fabs(di));
@@ -74,6 +81,79 @@ __global__ void __launch_bounds__(256) factor_kernel(int Nx, int Ny, int Nz,
     }
 }
 
+// The sweeps walk the column CH planes at a time: all loads of a chunk are
+// issued before its dependent chain and its stores (the in-place stores would
+// otherwise keep the next plane's load from starting early), so each thread has
+// 2-3 x CH loads in flight.
+constexpr int CH = 8;
+
+// One z-solve with cached factors.  Td: data type (in place); Tf: factor type;
+// Ts: type of the forward-sweep values (kept in `scratch` when it is not null,
+// else in `data`); Ta: arithmetic type.
+template <typename Td, typename Tf, typename Ta>
+__device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, Td *data,
+                                              Ta *scratch, const Tf *cpr, const Tf *alpha,
+                                              const Tf *beta) {
+    Ta d = (Ta)0;
+    int l = 0;
+    for (; l + CH <= Nz; l += CH) {
+        Ta r[CH], a[CH], b[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            const size_t o = (size_t)(l + k) * plane + idx;
+            r[k] = (Ta)data[o];
+            a[k] = (Ta)alpha[o];
+            b[k] = (Ta)beta[o];
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            d = a[k] * r[k] - b[k] * d;
+            r[k] = d;
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            const size_t o = (size_t)(l + k) * plane + idx;
+            if (scratch)
+                scratch[o] = r[k];
+            else
+                data[o] = (Td)r[k];
+        }
+    }
+    for (; l < Nz; ++l) {
+        const size_t o = (size_t)l * plane + idx;
+        d = (Ta)alpha[o] * (Ta)data[o] - (Ta)beta[o] * d;
+        if (scratch)
+            scratch[o] = d;
+        else
+            data[o] = (Td)d;
+    }
+    Ta w = d;
+    data[(size_t)(Nz - 1) * plane + idx] = (Td)w;
+    int top = Nz - 2;  // next plane to solve, going down
+    for (; top - CH + 1 >= 0; top -= CH) {
+        Ta dv[CH], c[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            const size_t o = (size_t)(top - k) * plane + idx;
+            dv[k] = scratch ? scratch[o] : (Ta)data[o];
+            c[k] = (Ta)cpr[o];
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            w = dv[k] - c[k] * w;
+            dv[k] = w;
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k) data[(size_t)(top - k) * plane + idx] = (Td)dv[k];
+    }
+    for (; top >= 0; --top) {
+        const size_t o = (size_t)top * plane + idx;
+        const Ta dd = scratch ? scratch[o] : (Ta)data[o];
+        w = dd - (Ta)cpr[o] * w;
+        data[o] = (Td)w;
+    }
+}
+
 // FP64 path: data holds Fhat on entry and W on exit (forward sweep in place).
 __global__ void __launch_bounds__(256) thomas64_kernel(int Nx, int Ny, int Nz,
                                                         double *__restrict__ data,
@@ -81,26 +161,12 @@ __global__ void __launch_bounds__(256) thomas64_kernel(int Nx, int Ny, int Nz,
     const size_t plane = (size_t)Nx * Ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= plane) return;
-    const double *cpr = fac;
-    const double *alpha = fac + (size_t)Nz * plane;
-    const double *beta = fac + 2 * (size_t)Nz * plane;
-    double d = 0.0;
-#pragma unroll 4
-    for (int l = 0; l < Nz; ++l) {
-        const size_t o = (size_t)l * plane + idx;
-        d = alpha[o] * data[o] - beta[o] * d;
-        data[o] = d;
-    }
-    double w = d;
-#pragma unroll 4
-    for (int l = Nz - 2; l >= 0; --l) {
-        const size_t o = (size_t)l * plane + idx;
-        w = data[o] - cpr[o] * w;
-        data[o] = w;
-    }
+    thomas_column<double, double, double>(Nz, plane, idx, data, (double *)nullptr, fac,
+                                          fac + (size_t)Nz * plane, fac + 2 * (size_t)Nz * plane);
 }
 
-// Mixed path: FP32 Fhat in, FP32 W out; the forward sweep is kept in FP64.
+// Mixed path, FP64 factors (plans with small pivots): FP32 Fhat in, FP32 W
+// out; the forward sweep is kept in FP64 scratch.
 __global__ void __launch_bounds__(256) thomas32_kernel(int Nx, int Ny, int Nz,
                                                         float *__restrict__ data,
                                                         double *__restrict__ scratch,
@@ -108,24 +174,22 @@ __global__ void __launch_bounds__(256) thomas32_kernel(int Nx, int Ny, int Nz,
     const size_t plane = (size_t)Nx * Ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= plane) return;
-    const double *cpr = fac;
-    const double *alpha = fac + (size_t)Nz * plane;
-    const double *beta = fac + 2 * (size_t)Nz * plane;
-    double d = 0.0;
-#pragma unroll 4
-    for (int l = 0; l < Nz; ++l) {
-        const size_t o = (size_t)l * plane + idx;
-        d = alpha[o] * (double)data[o] - beta[o] * d;
-        scratch[o] = d;
-    }
-    double w = d;
-    data[(size_t)(Nz - 1) * plane + idx] = (float)w;
-#pragma unroll 4
-    for (int l = Nz - 2; l >= 0; --l) {
-        const size_t o = (size_t)l * plane + idx;
-        w = scratch[o] - cpr[o] * w;
-        data[o] = (float)w;
-    }
+    thomas_column<float, double, double>(Nz, plane, idx, data, scratch, fac,
+                                         fac + (size_t)Nz * plane, fac + 2 * (size_t)Nz * plane);
+}
+
+// Mixed path, well-conditioned plans: the factors rounded to FP32 and an FP32
+// recurrence, in place (Fhat in, W out).  The error this adds to the fast
+// solve, ~2^-24 times the condition of the z-system, is removed by the
+// refinement sweeps like the FP32 transform error.
+__global__ void __launch_bounds__(256) thomas_f32_kernel(int Nx, int Ny, int Nz,
+                                                          float *__restrict__ data,
+                                                          const float *__restrict__ fac) {
+    const size_t plane = (size_t)Nx * Ny;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= plane) return;
+    thomas_column<float, float, float>(Nz, plane, idx, data, (float *)nullptr, fac,
+                                       fac + (size_t)Nz * plane, fac + 2 * (size_t)Nz * plane);
 }
 
 }  // namespace
@@ -134,7 +198,7 @@ hs_status hs_launch_factor(const hs_plan_s *P, cudaStream_t s) {
     const size_t plane = (size_t)P->Nx * P->Ny;
     const unsigned blocks = (unsigned)((plane + 255) / 256);
     factor_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef, P->d_cx, P->d_cy,
-                                         P->d_fac, P->d_red);
+                                         P->d_fac, P->d_fac32, P->d_red);
     return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
@@ -145,6 +209,9 @@ hs_status hs_launch_thomas(const hs_plan_s *P, int tio, void *data, double *scra
     if (tio == HS_T_F64)
         thomas64_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, static_cast<double *>(data),
                                                P->d_fac);
+    else if (P->thomas32)
+        thomas_f32_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, static_cast<float *>(data),
+                                                 P->d_fac32);
     else
         thomas32_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, static_cast<float *>(data),
                                                scratch, P->d_fac);

@@ -257,3 +257,21 @@ def test_error_codes_without_touching_data():
         assert e.value.status == H.HS_ERR_NONFINITE
     finally:
         s.close()
+
+
+FAST_N = [31, 63, 95, 127, 191, 255, 383, 511, 767, 1023]
+
+
+@pytest.mark.parametrize("N", FAST_N)
+@pytest.mark.parametrize("precision", [H.HS_FP64, H.HS_MIXED])
+def test_transform_lengths(N, precision):
+    """Every compile-time-sized transform length, along x and along y (ragged tiles).
+
+    Uniform h (6th order) keeps these thin boxes well conditioned (min pivot ratio
+    ~0.25): FP64 parity is bounded by eps * kappa, and random anisotropic boxes reach
+    pivot ratios of 1e-7, where two exact-in-theory FP64 solvers differ by ~1e-11."""
+    for shape in ((N, 9, 5), (7, N, 4)):
+        p = random_problem(shape, 6, W.HELMHOLTZ, seed=N + shape[1])
+        ref = oracle_solve(p)
+        u, _ = gpu_solve(p, precision, sweeps=3)
+        assert O.max_rel_diff(u, ref) <= (TOL64 if precision == H.HS_FP64 else TOLMIX)
