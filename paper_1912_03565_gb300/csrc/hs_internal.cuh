@@ -45,6 +45,7 @@ struct hs_plan_s {
     int refine_sweeps;
     int stage_timing;
     int dst_generic;    // 1: always use the runtime-sized transform kernels
+    int residual_simple;  // 1: one-thread-per-point residual instead of the z-marching one
     int have_coeff;
     int cd_variant;
     double min_pivot_ratio;

@@ -268,8 +268,10 @@ __device__ __forceinline__ void fstages(typename Cx<Tc>::t *&src, typename Cx<Tc
 // Real element m of a line's odd extension, stored inside the padded complex layout.
 __device__ __forceinline__ int ZPAD(int m) { return 2 * PAD(m >> 1) + (m & 1); }
 
+// FP32 tiles use up to ~74 KB of shared memory, so three CTAs fit an SM; the
+// register cap keeps the third one resident.
 template <typename Tc, typename Tin, typename Tout, int AXIS, int MODE, int M, int S, int... Rs>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (sizeof(Tc) == 4 ? 3 : 1))
 dst_fast_kernel(const Tin *in, Tout *out, double *aux, const typename Cx<Tc>::t *roots_g,
                 const typename Cx<Tc>::t *half_g, int Nx, int Ny, int Nz, Tc scale) {
     typedef typename Cx<Tc>::t T2;

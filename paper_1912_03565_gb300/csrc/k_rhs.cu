@@ -30,6 +30,7 @@ struct RhsArgs {
     const double *c0;    // [Nz+2]
     const double *c1;    // [Nz+2]
     const float4 *rc;    // [Nz+2]: per-row double-float RHS weights (see rhs_tiled_df_kernel)
+    int has_faces;       // 0: every Dirichlet face is zero, so the lifting vanishes
     DevBoundary b;
 };
 
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(256) rhs_kernel(RhsArgs a, const T *__restrict
         }
     }
     const bool near = (i == 1 || i == a.Nx || j == 1 || j == a.Ny || l == 1 || l == a.Nz);
-    if (near) val -= lift_terms<T>(a, i, j, l);
+    if (a.has_faces && near) val -= lift_terms<T>(a, i, j, l);
     if (OUT_DF) {
         const dfloat d = df_from_double(val);
         float *Fo = static_cast<float *>(Fout);
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_kernel(RhsArgs a, const T 
                 val = h2 * F6;
             }
             const bool near = (i == 1 || i == a.Nx || j == 1 || j == a.Ny || l == 1 || l == a.Nz);
-            if (near) val -= lift_terms<T>(a, i, j, l);
+            if (a.has_faces && near) val -= lift_terms<T>(a, i, j, l);
             const size_t out = ((size_t)(l - 1) * a.Ny + (j - 1)) * a.Nx + (i - 1);
             if (OUT_DF) {
                 const dfloat d = df_from_double(val);
@@ -318,11 +319,31 @@ __device__ __forceinline__ dfloat node_df(const RhsArgs &a, const T *f, int i, i
 
 __device__ __forceinline__ dfloat dsum(dfloat a, dfloat b) { return df_add(a, b); }
 
+// Sum of double-float terms without renormalising after each one: the hi parts
+// go through two_sum (exact), their errors and the lo parts are added in FP32.
+struct LeanSum {
+    float s, e;
+    __device__ __forceinline__ LeanSum(dfloat a) : s(a.hi), e(a.lo) {}
+    __device__ __forceinline__ void add(dfloat a) {
+        float t, err;
+        df_two_sum(s, a.hi, t, err);
+        s = t;
+        e += err + a.lo;
+    }
+    __device__ __forceinline__ dfloat get() const {
+        dfloat r;
+        df_fast_two_sum(s, e, r.hi, r.lo);
+        return r;
+    }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_df_kernel(RhsArgs a, const T *__restrict__ f,
                                                                 float *__restrict__ Fo) {
     __shared__ float ph[5][RHY][RHX];
     __shared__ float pq[5][RHY][RHX];
+    constexpr int NT = RTX * RTY;
+    constexpr int PER = (RHX * RHY + NT - 1) / NT;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RTX + tx;
     const int i0 = 1 + blockIdx.x * RTX, j0 = 1 + blockIdx.y * RTY;
     const int lbeg = 1 + blockIdx.z * RZ;
@@ -333,30 +354,52 @@ __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_df_kernel(RhsArgs a, const
     const dfloat C90 = df_from_double(1.0 / 90.0), C12 = df_from_double(1.0 / 12.0);
     const dfloat HALF = df_of(0.5f);
 
-    auto load_plane = [&](int l) {
-        const int slot = (l + 10) % 5;
-        for (int e = tid; e < RHX * RHY; e += RTX * RTY) {
+    dfloat reg[PER];
+    auto fetch = [&](int l) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * NT;
             const int ey = e / RHX, ex = e - ey * RHX;
-            const dfloat v = node_df<T>(a, f, i0 - 2 + ex, j0 - 2 + ey, l);
-            ph[slot][ey][ex] = v.hi;
-            pq[slot][ey][ex] = v.lo;
+            reg[k] = (e < RHX * RHY) ? node_df<T>(a, f, i0 - 2 + ex, j0 - 2 + ey, l)
+                                     : df_of(0.f);
         }
     };
-    for (int l = lbeg - 2; l <= lbeg + 1; ++l) load_plane(l);
+    auto store = [&](int l) {
+        const int slot = (l + 10) % 5;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * NT;
+            if (e < RHX * RHY) {
+                const int ey = e / RHX, ex = e - ey * RHX;
+                ph[slot][ey][ex] = reg[k].hi;
+                pq[slot][ey][ex] = reg[k].lo;
+            }
+        }
+    };
+    for (int l = lbeg - 2; l <= lbeg + 1; ++l) {
+        fetch(l);
+        store(l);
+    }
+    fetch(lbeg + 2);
     const int i = i0 + tx, j = j0 + ty;
     const int cx = tx + 2, cy = ty + 2;
     for (int l = lbeg; l <= lend; ++l) {
-        load_plane(l + 2);
+        store(l + 2);               // slot of plane l - 3, last read in the previous step
         __syncthreads();
+        if (l + 3 <= lend + 2) fetch(l + 3);   // in flight during this plane's arithmetic
         if (i <= a.Nx && j <= a.Ny) {
             const int sm2 = (l + 8) % 5, sm = (l + 9) % 5, s0 = (l + 10) % 5, sp = (l + 11) % 5,
                       sp2 = (l + 12) % 5;
 #define HS_G(S, Y, X) dfloat{ph[S][Y][X], pq[S][Y][X]}
             const dfloat fc = HS_G(s0, cy, cx);
             const dfloat fzm = HS_G(sm, cy, cx), fzp = HS_G(sp, cy, cx);
-            const dfloat S1 = dsum(dsum(dsum(HS_G(s0, cy, cx - 1), HS_G(s0, cy, cx + 1)),
-                                        dsum(HS_G(s0, cy - 1, cx), HS_G(s0, cy + 1, cx))),
-                                   dsum(fzm, fzp));
+            LeanSum a1(HS_G(s0, cy, cx - 1));
+            a1.add(HS_G(s0, cy, cx + 1));
+            a1.add(HS_G(s0, cy - 1, cx));
+            a1.add(HS_G(s0, cy + 1, cx));
+            a1.add(fzm);
+            a1.add(fzp);
+            const dfloat S1 = a1.get();
             dfloat val;
             const float4 w = a.rc[l];
             if (a.equation == HS_CONVDIFF) {
@@ -368,16 +411,26 @@ __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_df_kernel(RhsArgs a, const
             } else if (a.order == 4) {
                 val = df_mul(H2, dsum(df_mul(HALF, fc), df_mul(C12, S1)));
             } else {
-                const dfloat S2 = dsum(dsum(dsum(HS_G(s0, cy, cx - 2), HS_G(s0, cy, cx + 2)),
-                                            dsum(HS_G(s0, cy - 2, cx), HS_G(s0, cy + 2, cx))),
-                                       dsum(HS_G(sm2, cy, cx), HS_G(sp2, cy, cx)));
-                const dfloat Exy = dsum(dsum(HS_G(s0, cy - 1, cx - 1), HS_G(s0, cy - 1, cx + 1)),
-                                        dsum(HS_G(s0, cy + 1, cx - 1), HS_G(s0, cy + 1, cx + 1)));
-                const dfloat Em = dsum(dsum(HS_G(sm, cy, cx - 1), HS_G(sm, cy, cx + 1)),
-                                       dsum(HS_G(sm, cy - 1, cx), HS_G(sm, cy + 1, cx)));
-                const dfloat Ep = dsum(dsum(HS_G(sp, cy, cx - 1), HS_G(sp, cy, cx + 1)),
-                                       dsum(HS_G(sp, cy - 1, cx), HS_G(sp, cy + 1, cx)));
-                const dfloat E = dsum(Exy, dsum(Em, Ep));
+                LeanSum a2(HS_G(s0, cy, cx - 2));
+                a2.add(HS_G(s0, cy, cx + 2));
+                a2.add(HS_G(s0, cy - 2, cx));
+                a2.add(HS_G(s0, cy + 2, cx));
+                a2.add(HS_G(sm2, cy, cx));
+                a2.add(HS_G(sp2, cy, cx));
+                const dfloat S2 = a2.get();
+                LeanSum a3(HS_G(s0, cy - 1, cx - 1));
+                a3.add(HS_G(s0, cy - 1, cx + 1));
+                a3.add(HS_G(s0, cy + 1, cx - 1));
+                a3.add(HS_G(s0, cy + 1, cx + 1));
+                a3.add(HS_G(sm, cy, cx - 1));
+                a3.add(HS_G(sm, cy, cx + 1));
+                a3.add(HS_G(sm, cy - 1, cx));
+                a3.add(HS_G(sm, cy + 1, cx));
+                a3.add(HS_G(sp, cy, cx - 1));
+                a3.add(HS_G(sp, cy, cx + 1));
+                a3.add(HS_G(sp, cy - 1, cx));
+                a3.add(HS_G(sp, cy + 1, cx));
+                const dfloat E = a3.get();
                 const dfloat alpha = dfloat{w.x, w.y};
                 const dfloat eps = dfloat{w.z, w.w};
                 const dfloat dz = df_add_accurate(fzp, df_neg(fzm));
@@ -390,7 +443,8 @@ __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_df_kernel(RhsArgs a, const
             }
 #undef HS_G
             const bool near = (i == 1 || i == a.Nx || j == 1 || j == a.Ny || l == 1 || l == a.Nz);
-            if (near) val = df_add_accurate(val, df_neg(df_split_bits(lift_terms<T>(a, i, j, l))));
+            if (a.has_faces && near)
+                val = df_add_accurate(val, df_neg(df_split_bits(lift_terms<T>(a, i, j, l))));
             const size_t out = ((size_t)(l - 1) * a.Ny + (j - 1)) * a.Nx + (i - 1);
             Fo[out] = val.hi;
             Fo[out + n] = val.lo;
@@ -457,6 +511,146 @@ __global__ void __launch_bounds__(256) residual_df_kernel(int Nx, int Ny, int Nz
     const size_t o = (size_t)l * plane + c;
     const dfloat res = df_add_accurate(dfloat{F[o], F[o + n]}, df_neg(acc));
     r[o] = res.hi + (res.lo - acc_lo);
+}
+
+// z-marching double-float residual.  A CTA owns a RTX x RTY patch and RZ
+// planes; a ring of three U-planes (hi and lo, halo 1) sits in shared memory.
+// For every plane each thread forms the in-plane sums of its column once --
+// corners C, x-neighbours X, y-neighbours Y (exact pair sums of the FP32 hi
+// parts, plain FP32 sums of the lo parts) -- and keeps the last three planes'
+// sums in registers, so output row l costs 12 products
+//     A U_l = sum_nu a_nu C_nu + b_nu X_nu + c_nu Y_nu + d_nu U_nu,
+// accumulated as an unnormalised pair (two_prod into two_sum; cross terms and
+// lo parts in FP32), and one accurate pair subtraction F - A U.
+struct PlaneSums {
+    float C, Ce, X, Xe, Y, Ye, U;   // hi sums with their two_sum errors; U = centre hi
+    float L;                        // lo parts: C_lo etc. folded per coefficient below
+    float Clo, Xlo, Ylo, Ulo;
+};
+
+__device__ __forceinline__ void acc_term(float &S, float &E, float2 k, float v, float ve,
+                                         float vlo) {
+    // S + E += (k.x + k.y) * (v + ve + vlo)
+    const float p = k.x * v;
+    const float pe = fmaf(k.x, v, -p);
+    float s, t;
+    df_two_sum(S, p, s, t);
+    S = s;
+    E += t + pe + fmaf(k.x, ve + vlo, k.y * v);
+}
+
+constexpr int QTX = 32, QTY = 8, QZ = 16;
+constexpr int QHX = QTX + 2, QHY = QTY + 2;
+
+__global__ void __launch_bounds__(QTX *QTY) residual_zmarch_kernel(int Nx, int Ny, int Nz,
+                                                                    const float2 *__restrict__ coef,
+                                                                    const float *__restrict__ F,
+                                                                    const float *__restrict__ U,
+                                                                    float *__restrict__ r) {
+    // two plane slots: the plane whose sums are being formed and the next one,
+    // whose global loads are issued into registers before the current plane's
+    // arithmetic (so their latency overlaps it)
+    __shared__ float uh[2][QHY][QHX];
+    __shared__ float ul[2][QHY][QHX];
+    constexpr int NT = QTX * QTY;
+    constexpr int PER = (QHX * QHY + NT - 1) / NT;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * QTX + tx;
+    const int i0 = blockIdx.x * QTX, j0 = blockIdx.y * QTY;  // 0-based interior indices
+    const int lbeg = blockIdx.z * QZ;
+    const int lend = min(lbeg + QZ, Nz);                      // exclusive
+    const size_t plane = (size_t)Nx * Ny;
+    const size_t n = plane * Nz;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = i < Nx && j < Ny;
+
+    float rh[PER], rl[PER];
+    auto fetch = [&](int l) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * NT;
+            const int ey = e / QHX, ex = e - ey * QHX;
+            const int ii = i0 - 1 + ex, jj = j0 - 1 + ey;
+            rh[k] = 0.f;
+            rl[k] = 0.f;
+            if (e < QHX * QHY && l >= 0 && l < Nz && ii >= 0 && ii < Nx && jj >= 0 && jj < Ny) {
+                const size_t o = (size_t)l * plane + (size_t)jj * Nx + ii;
+                rh[k] = __ldg(U + o);
+                rl[k] = __ldg(U + n + o);
+            }
+        }
+    };
+    auto store = [&](int l) {
+        const int slot = (l + 2) & 1;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * NT;
+            if (e < QHX * QHY) {
+                const int ey = e / QHX, ex = e - ey * QHX;
+                uh[slot][ey][ex] = rh[k];
+                ul[slot][ey][ex] = rl[k];
+            }
+        }
+    };
+    auto sums = [&](int l, PlaneSums &ps) {
+        const int sl = (l + 2) & 1;
+        const int cx = tx + 1, cy = ty + 1;
+        float s, e, s2, e2;
+        df_two_sum(uh[sl][cy - 1][cx - 1], uh[sl][cy - 1][cx + 1], s, e);
+        df_two_sum(uh[sl][cy + 1][cx - 1], uh[sl][cy + 1][cx + 1], s2, e2);
+        float s3, e3;
+        df_two_sum(s, s2, s3, e3);
+        ps.C = s3;
+        ps.Ce = e3 + (e + e2);
+        df_two_sum(uh[sl][cy][cx - 1], uh[sl][cy][cx + 1], ps.X, ps.Xe);
+        df_two_sum(uh[sl][cy - 1][cx], uh[sl][cy + 1][cx], ps.Y, ps.Ye);
+        ps.U = uh[sl][cy][cx];
+        ps.Clo = (ul[sl][cy - 1][cx - 1] + ul[sl][cy - 1][cx + 1]) +
+                 (ul[sl][cy + 1][cx - 1] + ul[sl][cy + 1][cx + 1]);
+        ps.Xlo = ul[sl][cy][cx - 1] + ul[sl][cy][cx + 1];
+        ps.Ylo = ul[sl][cy - 1][cx] + ul[sl][cy + 1][cx];
+        ps.Ulo = ul[sl][cy][cx];
+    };
+
+    PlaneSums pm, p0, pp;
+    fetch(lbeg - 1);
+    store(lbeg - 1);
+    __syncthreads();
+    sums(lbeg - 1, pm);
+    fetch(lbeg);
+    __syncthreads();
+    store(lbeg);
+    __syncthreads();
+    sums(lbeg, p0);
+    fetch(lbeg + 1);
+    for (int l = lbeg; l < lend; ++l) {
+        __syncthreads();          // slot of plane l + 1 (= that of l - 1) is free
+        store(l + 1);
+        __syncthreads();
+        fetch(l + 2);             // in flight during the arithmetic below
+        sums(l + 1, pp);
+        if (active) {
+            const float2 *cf = coef + (size_t)l * 12;
+            float S = 0.f, E = 0.f;
+            const PlaneSums *q[3] = {&pm, &p0, &pp};
+#pragma unroll
+            for (int nu = 0; nu < 3; ++nu) {
+                const int ll = l + nu - 1;
+                if (ll < 0 || ll >= Nz) continue;
+                const PlaneSums &ps = *q[nu];
+                acc_term(S, E, cf[nu * 4 + 0], ps.C, ps.Ce, ps.Clo);
+                acc_term(S, E, cf[nu * 4 + 1], ps.X, ps.Xe, ps.Xlo);
+                acc_term(S, E, cf[nu * 4 + 2], ps.Y, ps.Ye, ps.Ylo);
+                acc_term(S, E, cf[nu * 4 + 3], ps.U, 0.f, ps.Ulo);
+            }
+            const size_t o = (size_t)l * plane + (size_t)j * Nx + i;
+            dfloat au;
+            df_fast_two_sum(S, E, au.hi, au.lo);
+            const dfloat res = df_add_accurate(dfloat{F[o], F[o + n]}, df_neg(au));
+            r[o] = res.hi + res.lo;
+        }
+        pm = p0;
+        p0 = pp;
+    }
 }
 
 // u (FP64) = hi + lo of a double-float array.
@@ -547,6 +741,9 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
     a.c1 = P->d_c1;
     a.rc = P->d_rhs_df;
     a.b = b;
+    a.has_faces = 0;
+    for (int k = 0; k < 6; ++k)
+        if (b.face[k]) a.has_faces = 1;
     if (rhs_kind == HS_RHS_NODAL) {
         dim3 tb(RTX, RTY, 1);
         dim3 tg((P->Nx + RTX - 1) / RTX, (P->Ny + RTY - 1) / RTY, (P->Nz + RZ - 1) / RZ);
@@ -585,7 +782,13 @@ hs_status hs_launch_residual_df(const hs_plan_s *P, const float *F, const float 
                                 cudaStream_t s) {
     dim3 block(32, 8, 1);
     dim3 grid((P->Nx + 31) / 32, (P->Ny + 7) / 8, P->Nz);
-    residual_df_kernel<<<grid, block, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df, F, U, r);
+    if (P->residual_simple) {
+        residual_df_kernel<<<grid, block, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df, F, U, r);
+    } else {
+        dim3 qb(QTX, QTY, 1);
+        dim3 qg((P->Nx + QTX - 1) / QTX, (P->Ny + QTY - 1) / QTY, (P->Nz + QZ - 1) / QZ);
+        residual_zmarch_kernel<<<qg, qb, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df, F, U, r);
+    }
     return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 

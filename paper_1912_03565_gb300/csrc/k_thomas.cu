@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) factor_kernel(int Nx, int Ny, int Nz,
 // issued before its dependent chain and its stores (the in-place stores would
 // otherwise keep the next plane's load from starting early), so each thread has
 // 2-3 x CH loads in flight.
-constexpr int CH = 8;
+constexpr int CH = 16;
 
 // One z-solve with cached factors.  Td: data type (in place); Tf: factor type;
 // Ts: type of the forward-sweep values (kept in `scratch` when it is not null,
