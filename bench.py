@@ -28,6 +28,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -138,9 +140,14 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def make_problem(N: int, seed: int):
-    import workloads as W
-    return W.workload_cube255_order6(seed=seed, N=N)
+def reduce_max(x, dist, device):
+    """Max of a per-rank float over all ranks (identity without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def cpu_cores():
@@ -148,6 +155,97 @@ def cpu_cores():
         return len(os.sched_getaffinity(0))
     except Exception:
         return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- workloads
+
+WORKLOADS = {
+    "cube255_o6": dict(
+        steps=100,
+        desc="6th-order compact Helmholtz on the unit cube, 255^3 interior (h=1/256), "
+             "k=20(1+z^2/2), f = manufactured (u=sin(pi x)sin(2pi y)sin(3pi z)e^z) "
+             "+ U[-1,1] noise at interior nodes (seed 2), FP64 f, 1 RHS per step"),
+    "cube31_o4": dict(
+        steps=200,
+        desc="4th-order compact Helmholtz on the unit cube, 31^3 interior (h=1/32), "
+             "k=10+5 sin(pi z), manufactured u, FP64 f, 1 RHS per step"),
+    "cube1023_o6": dict(
+        steps=10,
+        desc="6th-order compact Helmholtz on the unit cube, 1023^3 interior (h=1/1024), "
+             "k=40+20 tanh(10(z-1/2)), f = 16 seeded sine modes, amplitudes N(0,1), "
+             "stored FP32, 1 RHS per step"),
+    "cd511x8": dict(
+        steps=10,
+        desc="4th-order compact convection-diffusion Lap(u)+b(z)u_z=f, 511^3 interior, "
+             "b=2+sin(2pi z) (variable-b corrected coefficients), 8 right-hand sides "
+             "U[-1,1] stored FP32 per step, nonsymmetric z-systems"),
+}
+
+
+class Work:
+    """One benchmark workload: plan parameters, device inputs and its CPU-oracle sample."""
+
+    def __init__(self, name, torch, W, want_oracle):
+        self.name = name
+        self.desc = WORKLOADS[name]["desc"]
+        self.fnn = None
+        self.ref = None            # oracle solution of the first RHS (numpy) when affordable
+        self.cpu = None            # (seconds, unknowns, sample text) of the oracle run
+        self.nrhs = 1
+        self.cd = 1
+        from oracle import hs_oracle as O
+        if name in ("cube255_o6", "cube31_o4"):
+            p = W.workload_cube255_order6(seed=2) if name == "cube255_o6" else W.workload_cube31_order4()
+            self.N, self.L, self.order, self.eq = (p.Nx, p.Ny, p.Nz), (p.Lx, p.Ly, p.Lz), p.order, 0
+            self.c = (p.c0, p.c1, p.c2)
+            self.f = torch.from_numpy(p.f_nodes).cuda()
+            self.f_host = p.f_nodes
+            self.f_dtype = 0
+            self.fnn = [None if a is None else torch.from_numpy(a).cuda() for a in p.fnn]
+            self.fnn_host = p.fnn
+            if want_oracle:
+                t0 = time.perf_counter()
+                self.ref, _ = O.solve(p)
+                dt = time.perf_counter() - t0
+                n = p.Nx * p.Ny * p.Nz
+                self.cpu = (dt, n, f"one full {p.Nx}^3 oracle solve (numpy FP64, matmul O(N^4) "
+                                   f"DSTs, textbook Thomas): {dt:.2f} s")
+        elif name == "cube1023_o6":
+            N = 1023
+            modes, amps = W.sine_modes(N, 16, 4)
+            K = W.k_profile_to_k2(W.k_tanh())
+            self.N, self.L, self.order, self.eq = (N, N, N), (1.0, 1.0, 1.0), 6, 0
+            self.c = K.sample(N, 1.0)
+            self.f = W.sine_mode_nodes_torch(N, modes, amps, torch.float32)
+            self.f_host = None
+            self.f_dtype = 1
+            if want_oracle:
+                q = W.sine_mode_problem(255, 6, W.k_tanh(), nmodes=16, seed=4)
+                t0 = time.perf_counter()
+                O.solve(q)
+                dt = time.perf_counter() - t0
+                self.cpu = (dt, 255 ** 3, f"bounded sample: one full 255^3 oracle solve of the "
+                                           f"same recipe (16 sine modes, FP32 f): {dt:.2f} s")
+        elif name == "cd511x8":
+            N, R = 511, 8
+            probs = [W.workload_convdiff511(r) for r in range(R)]
+            self.N, self.L, self.order, self.eq = (N, N, N), (1.0, 1.0, 1.0), 4, 1
+            self.c = (probs[0].c0, probs[0].c1, probs[0].c2)
+            self.f_host = np.stack([q.f_nodes.astype(np.float32) for q in probs])
+            self.f = torch.from_numpy(self.f_host).cuda()
+            self.f_dtype = 1
+            self.nrhs = R
+            if want_oracle:
+                t0 = time.perf_counter()
+                self.ref, _ = O.solve(probs[0])
+                dt = time.perf_counter() - t0
+                self.cpu = (dt, N ** 3, f"bounded sample: the oracle on 1 of the 8 right-hand "
+                                        f"sides (511^3): {dt:.2f} s")
+        else:
+            raise ValueError(name)
+        Nx, Ny, Nz = self.N
+        self.n = Nx * Ny * Nz
+        self.fnn_host = getattr(self, "fnn_host", None)
 
 
 def run_reference(args):
@@ -159,26 +257,37 @@ def run_reference(args):
             dist.barrier()
             dist.destroy_process_group()
             return
+    import workloads as W
     from oracle import hs_oracle as O
-    p = make_problem(args.n, args.seed)
-    n = p.Nx * p.Ny * p.Nz
+    name = args.workload
+    # each step is the oracle on the workload's bounded sample (the full problem when
+    # it takes seconds, else a smaller instance of the same recipe or one RHS)
+    if name == "cube255_o6":
+        p, n, sample = W.workload_cube255_order6(seed=2), 255 ** 3, "full 255^3 solve per step"
+    elif name == "cube31_o4":
+        p, n, sample = W.workload_cube31_order4(), 31 ** 3, "full 31^3 solve per step"
+    elif name == "cube1023_o6":
+        p = W.sine_mode_problem(255, 6, W.k_tanh(), nmodes=16, seed=4)
+        n, sample = 255 ** 3, "255^3 instance of the same recipe per step"
+    else:
+        p, n, sample = W.workload_convdiff511(0), 511 ** 3, "1 of the 8 right-hand sides per step"
+    steps = args.steps if args.steps is not None else 5
     for _ in range(args.warmup):
         O.solve(p)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         O.solve(p)
-    dt = (time.perf_counter() - t0) / args.steps
+    dt = (time.perf_counter() - t0) / steps
     val = n / dt / 1e9
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"cube{args.n}_o6: 6th-order compact Helmholtz, {args.n}^3 "
-                                   "interior, k=20(1+z^2/2), manufactured f + U[-1,1] noise, 1 RHS",
-                       "global_batch": 1, "parallelism": "cpu oracle, rank 0 only"},
+            "config": {"workload": f"{name}: {WORKLOADS[name]['desc']}", "global_batch": 1,
+                       "parallelism": "cpu oracle, rank 0 only"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                             "sample": f"full {args.n}^3 solve per step (numpy FP64, "
-                                       "matmul O(N^4) DSTs, textbook Thomas)"},
+                             "sample": sample + " (numpy FP64, matmul O(N^4) DSTs, textbook "
+                                                "Thomas)"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -190,13 +299,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hs", choices=["hs", "reference"])
-    ap.add_argument("--n", type=int, default=255)
-    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--workload", default="cube255_o6", choices=sorted(WORKLOADS))
     ap.add_argument("--sweeps", type=int, default=-1,
-                    help="refinement sweeps; -1 = the fewest whose error vs the oracle is <= 1e-10")
+                    help="refinement sweeps; -1 = the fewest whose error is <= 1e-10")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -205,11 +313,13 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.steps is None:
+        args.steps = WORKLOADS[args.workload]["steps"]
 
-    import numpy as np
     import torch
 
     import paper_1912_03565_gb300 as H
+    import workloads as W
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -222,53 +332,54 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    p = make_problem(args.n, args.seed)
-    N3 = p.Nx * p.Ny * p.Nz
-    f = torch.from_numpy(p.f_nodes).cuda()
-    fnn = [None if a is None else torch.from_numpy(a).cuda() for a in p.fnn]
-    u = torch.zeros((p.Nz, p.Ny, p.Nx), dtype=torch.float64, device="cuda")
+    want_oracle = rank == 0 and world == 1 and not args.no_cpu_baseline
+    wk = Work(args.workload, torch, W, want_oracle)
+    Nx, Ny, Nz = wk.N
+    N3 = wk.n
+    R = wk.nrhs
+    ushape = (Nz, Ny, Nx) if R == 1 else (R, Nz, Ny, Nx)
+    u = torch.zeros(ushape, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
     def solver(precision, sweeps):
-        s = H.Solver(p.Nx, p.Ny, p.Nz, p.Lx, p.Ly, p.Lz, p.order, H.HS_HELMHOLTZ, precision)
-        s.set_coeff(p.c0, p.c1, p.c2)
+        s = H.Solver(Nx, Ny, Nz, *wk.L, wk.order, wk.eq, precision, max_rhs=R)
+        s.set_coeff(*wk.c, wk.cd)
         if precision == H.HS_MIXED:
             H.hs_set_refinement(s.plan, sweeps)
         return s
 
-    s64 = solver(H.HS_FP64, 0)
+    def run(s, f, uu, fnn=None, info=False):
+        return s.solve(f, uu, wk.f_dtype, H.HS_RHS_NODAL, None, fnn, R, stream, info)
 
     def rel(a, b):
-        return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        return float((a - b).abs().max()) / float(b.abs().max())
 
     # ---- accuracy (untimed): FP64 path, and the mixed path after 0..3 sweeps
     acc = {}
-    s64.solve(f, u, H.HS_F64, H.HS_RHS_NODAL, None, fnn, stream=stream)
+    s64 = solver(H.HS_FP64, 0)
+    u64 = torch.zeros_like(u)
+    run(s64, wk.f, u64, wk.fnn)
     torch.cuda.synchronize()
-    u64 = u.cpu().numpy()
     ref = None
-    cpu_baseline = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import hs_oracle as O
-        t0 = time.perf_counter()
-        ref, _ = O.solve(p)
-        dt = time.perf_counter() - t0
-        acc["fp64_vs_oracle"] = rel(u64, ref)
-        cpu_baseline = {"value": N3 / dt / 1e9, "unit": UNIT, "cores": cpu_cores(),
-                        "kind": "oracle",
-                        "sample": f"one full {args.n}^3 solve (numpy FP64, matmul O(N^4) DSTs, "
-                                  f"textbook Thomas): {dt:.2f} s"}
-    judge = ref if ref is not None else u64
+    if wk.ref is not None:
+        ref = torch.from_numpy(wk.ref).cuda()
+        acc["fp64_vs_oracle"] = rel(u64 if R == 1 else u64[0], ref)
     acc["judged_against"] = "oracle" if ref is not None else "fp64 GPU path"
     by_sweeps = []
     for sw in range(0, 4):
         ss = solver(H.HS_MIXED, sw)
-        ss.solve(f, u, H.HS_F64, H.HS_RHS_NODAL, None, fnn, stream=stream)
+        run(ss, wk.f, u, wk.fnn)
         torch.cuda.synchronize()
-        by_sweeps.append(rel(u.cpu().numpy(), judge))
+        if ref is not None:
+            e = rel(u if R == 1 else u[0], ref)
+            if R > 1:
+                e = max(e, rel(u, u64))
+        else:
+            e = rel(u, u64)
+        by_sweeps.append(e)
         ss.close()
+        torch.cuda.empty_cache()
     acc["mixed_error_by_sweeps"] = by_sweeps
-    # the fewest refinement sweeps that meet the 1e-10 bar (args.sweeps < 0: choose)
     sweeps = args.sweeps
     if sweeps < 0:
         ok = [k for k in range(1, 4) if by_sweeps[k] <= 1e-10]
@@ -276,17 +387,24 @@ def main():
     acc["sweeps_used"] = sweeps
     acc["mixed_error"] = by_sweeps[sweeps] if sweeps < 4 else None
     smix = solver(H.HS_MIXED, sweeps)
-    _, inf = smix.solve(f, u, H.HS_F64, H.HS_RHS_NODAL, None, fnn, stream=stream, info=True)
+    _, inf = run(smix, wk.f, u, wk.fnn, info=True)
     acc["mixed_rel_residual_per_sweep"] = inf["rel_residual"]
     acc["min_pivot_ratio"] = inf["min_pivot_ratio"]
-    args.sweeps = sweeps
+    del u64
+    torch.cuda.empty_cache()
+
+    cpu_baseline = None
+    if wk.cpu is not None:
+        dt, n, sample = wk.cpu
+        cpu_baseline = {"value": n / dt / 1e9, "unit": UNIT, "cores": cpu_cores(),
+                        "kind": "oracle", "sample": sample}
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB
 
-    def timed(s, path, sweeps, steps, warmup):
+    def timed(s, steps, warmup):
         H.hs_set_stage_timing(s.plan, True)
         for _ in range(warmup):
-            s.solve(f, u, H.HS_F64, H.HS_RHS_NODAL, None, fnn, stream=stream)
+            run(s, wk.f, u, wk.fnn)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
@@ -296,7 +414,7 @@ def main():
         for k in range(steps):
             flush.fill_(float(k))
             ev[k][0].record(stream)
-            s.solve(f, u, H.HS_F64, H.HS_RHS_NODAL, None, fnn, stream=stream)
+            run(s, wk.f, u, wk.fnn)
             ev[k][1].record(stream)
             st = H.hs_stage_times(s.plan)
             for key, v in st.items():
@@ -308,33 +426,29 @@ def main():
         H.hs_set_stage_timing(s.plan, False)
         return ms, {k: v / steps for k, v in stage_tot.items()}
 
+    steps64 = max(3, args.steps // 2)
     clk = ClockSampler(local)
     clk.start()
-    ms_mix, st_mix = timed(smix, "mixed", args.sweeps, args.steps, args.warmup)
-    ms_64, st_64 = timed(s64, "fp64", 0, max(3, args.steps // 2), args.warmup)
+    ms_mix, st_mix = timed(smix, args.steps, args.warmup)
+    ms_64, st_64 = timed(s64, steps64, args.warmup)
     clocks = clk.stop()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dist, "cuda")
 
     ms_mix = max_over_ranks(ms_mix)
     ms_64 = max_over_ranks(ms_64)
-    steps64 = max(3, args.steps // 2)
-    value = world * args.steps * N3 / (ms_mix * 1e-3) / 1e9
-    value64 = world * steps64 * N3 / (ms_64 * 1e-3) / 1e9
+    value = world * args.steps * R * N3 / (ms_mix * 1e-3) / 1e9
+    value64 = world * steps64 * R * N3 / (ms_64 * 1e-3) / 1e9
 
     # ---- roofline of the dominant kernel of the mixed path
     hbm_peak, peak_kind = load_peaks()
-    bmix = stage_bytes("mixed", args.sweeps, inf["min_pivot_ratio"] >= 1e-4)
+    bmix = stage_bytes("mixed", sweeps, inf["min_pivot_ratio"] >= 1e-4)
     kern = max((k for k in bmix if st_mix.get(k, 0) > 0), key=lambda k: st_mix[k])
-    nlaunch = {"dst_x": args.sweeps + 1, "dst_y": args.sweeps + 1, "thomas": args.sweeps + 1,
-               "idst_y": args.sweeps + 1, "idst_x": args.sweeps + 1, "rhs": 1,
-               "residual": args.sweeps}[kern]
-    bytes_per_launch = bmix[kern] * N3 / nlaunch
+    nlaunch = {"dst_x": sweeps + 1, "dst_y": sweeps + 1, "thomas": sweeps + 1,
+               "idst_y": sweeps + 1, "idst_x": sweeps + 1, "rhs": 1, "residual": sweeps}[kern]
+    nlaunch *= R
+    bytes_per_launch = bmix[kern] * N3 * R / nlaunch
     t_launch = st_mix[kern] / nlaunch * 1e-3
     achieved = bytes_per_launch / t_launch / 1e9
     roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": hbm_peak,
@@ -345,23 +459,26 @@ def main():
     # ---- end to end through the C ABI with host buffers (pinned)
     e2e = None
     if not args.no_e2e:
-        fh = torch.from_numpy(p.f_nodes).pin_memory()
-        fnnh = [None if a is None else torch.from_numpy(a).pin_memory() for a in p.fnn]
-        uh = torch.zeros((p.Nz, p.Ny, p.Nx), dtype=torch.float64).pin_memory()
+        fh = wk.f.cpu().pin_memory()
+        fnnh = None if wk.fnn is None else [None if a is None else a.cpu().pin_memory()
+                                            for a in wk.fnn]
+        uh = torch.zeros(ushape, dtype=torch.float64).pin_memory()
         ke = max(3, args.steps // 2)
         for _ in range(2):
-            smix.solve(fh, uh, H.HS_F64, H.HS_RHS_NODAL, None, fnnh, stream=stream)
+            run(smix, fh, uh, fnnh)
         torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(ke):
-            smix.solve(fh, uh, H.HS_F64, H.HS_RHS_NODAL, None, fnnh, stream=stream)
+            run(smix, fh, uh, fnnh)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = max_over_ranks(e0.elapsed_time(e1))
-        h2d = fh.numel() * 8 + sum(a.numel() * 8 for a in fnnh if a is not None)
-        e2e = {"value": world * ke * N3 / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
+        h2d = fh.numel() * fh.element_size()
+        if fnnh is not None:
+            h2d += sum(a.numel() * a.element_size() for a in fnnh if a is not None)
+        e2e = {"value": world * ke * R * N3 / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": uh.numel() * 8,
                "ms_per_step": ms_e2e / ke}
 
@@ -371,11 +488,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_mix / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 + f32-pair (mixed)",
             "data": "synthetic",
-            "config": {"workload": f"cube{args.n}_o6: 6th-order compact Helmholtz, {args.n}^3 "
-                                   "interior, h=1/256, k=20(1+z^2/2), manufactured f + U[-1,1] "
-                                   "noise (seed), FP64 f, 1 RHS per step",
-                       "global_batch": world, "parallelism": f"replicas x{world}",
-                       "refinement_sweeps": args.sweeps,
+            "config": {"workload": f"{args.workload}: {wk.desc}",
+                       "global_batch": world * R, "parallelism": f"replicas x{world}",
+                       "refinement_sweeps": sweeps,
                        "l2": "256 MB buffer written between timed steps"},
             "fp64_path": {"value": value64, "unit": UNIT, "ms_per_step": ms_64 / steps64,
                           "stages_ms": st_64},
@@ -385,7 +500,7 @@ def main():
             "cpu_baseline": cpu_baseline,
             "e2e": e2e,
             "clocks": clocks,
-            "gpu_launches": launches_per_solve("mixed", args.sweeps) * args.steps,
+            "gpu_launches": launches_per_solve("mixed", sweeps) * R * args.steps,
         }
         print(json.dumps(line), flush=True)
     smix.close()

@@ -387,6 +387,70 @@ def solve(prob, cd_variant=CD_CORRECTED, return_all=False):
 
 
 # --------------------------------------------------------------------------
+# separable right-hand sides: exact discrete solution without 3-D transforms
+
+
+def solve_sine_modes(modes, amps, N, L, order, c0, c1=None, c2=None, sample=None):
+    """Discrete solution for f = sum_m A_m sin(p_m pi x/Lx) sin(q_m pi y/Ly) sin(r_m pi z/Lz).
+
+    Each term is separable: on the grid, sin(p pi x_i/Lx) is an eigenvector of
+    the undivided second difference D_x (eigenvalue mu_p = 2 cos(p pi/(Nx+1)) - 2),
+    also with the 6th-order ghosts, which for a sine mode with zero face data
+    are its odd extension.  So R_h f = A sin_p sin_q phi(l) with a 1-D profile
+    phi, the 2-D transform of sin_p sin_q is a single mode, and the solution
+    is sin_p sin_q times the solution of the one tridiagonal system T_pq w = phi
+    (Section 3.6).  Homogeneous Dirichlet data; order 6 uses zero face data.
+    Returns U on the interior, or U at the points `sample` = (i, j, l) arrays
+    of 1-based interior indices when given.
+    """
+    Nx, Ny, Nz = N
+    h = grid_steps(N, L)
+    hx, hy, hz = h
+    C = stencil_coefficients(order, HELMHOLTZ, h, c0, c1, c2)
+    K = np.asarray(c0, dtype=np.float64)
+    Kz = None if c1 is None else np.asarray(c1, dtype=np.float64)
+    lz = np.arange(0, Nz + 2)
+    ix = np.arange(1, Nx + 1)
+    jy = np.arange(1, Ny + 1)
+    groups = {}
+    for (p, q, r), A in zip(modes, amps):
+        s = A * np.sin(np.pi * ((r * lz) % (2 * (Nz + 1))) / (Nz + 1))   # s_l, l = 0..Nz+1
+        mux = 2.0 * np.cos(np.pi * p / (Nx + 1)) - 2.0
+        muy = 2.0 * np.cos(np.pi * q / (Ny + 1)) - 2.0
+        muz = 2.0 * np.cos(np.pi * r / (Nz + 1)) - 2.0
+        si = s[1:-1]
+        if order == 2:
+            phi = hz * hz * si
+        elif order == 4:
+            phi = hz * hz * si * (1.0 + (mux + muy + muz) / 12.0)
+        else:
+            hh = hz
+            base = (1.0 + (mux + muy + muz) / 12.0 - (mux ** 2 + muy ** 2 + muz ** 2) / 240.0
+                    + (mux * muy + mux * muz + muy * muz) / 90.0)
+            phi = hh * hh * (base * si - hh * hh * K[1:-1] * si / 20.0
+                             + hh ** 3 * Kz[1:-1] * (s[2:] - s[:-2]) / 120.0)
+        key = (int(p), int(q))
+        groups[key] = groups.get(key, 0.0) + phi
+    if sample is None:
+        U = np.zeros((Nz, Ny, Nx))
+    else:
+        si_, sj_, sl_ = (np.asarray(a) for a in sample)
+        U = np.zeros(si_.shape)
+    for (p, q), phi in groups.items():
+        cp, cq = np.cos(np.pi * p / (Nx + 1)), np.cos(np.pi * q / (Ny + 1))
+        lam = (4.0 * C[:, :, A_] * cp * cq + 2.0 * C[:, :, B_] * cp + 2.0 * C[:, :, C_] * cq
+               + C[:, :, D_])                                           # (Nz, 3)
+        w, _ = thomas(lam[:, LOW], lam[:, MID], lam[:, UPP], phi)
+        Sx = np.sin(np.pi * ((p * ix) % (2 * (Nx + 1))) / (Nx + 1))
+        Sy = np.sin(np.pi * ((q * jy) % (2 * (Ny + 1))) / (Ny + 1))
+        if sample is None:
+            U += w[:, None, None] * Sy[None, :, None] * Sx[None, None, :]
+        else:
+            U += w[sl_ - 1] * Sy[sj_ - 1] * Sx[si_ - 1]
+    return U
+
+
+# --------------------------------------------------------------------------
 # diagnostics (Section 5.1 error measures)
 
 

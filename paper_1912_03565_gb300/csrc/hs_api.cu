@@ -334,6 +334,15 @@ void timer_read(hs_plan_s *P, float *ms) {
     for (int k = 0; k < HS_INFO_STAGES; ++k) ms[k] = P->timer_acc[k];
 }
 
+// FP64 work arrays (lifted F and a residual/forward-sweep scratch): always
+// present in FP64 plans, allocated on first need in mixed plans.
+hs_status ensure_f64_work(hs_plan_s *P) {
+    const size_t nint = interior_count(P);
+    if (!P->d_w64) HS_TRY(P, dev_alloc(P, &P->d_w64, nint));
+    if (!P->d_dscr) HS_TRY(P, dev_alloc(P, &P->d_dscr, nint));
+    return HS_OK;
+}
+
 // ||F - A U||_2^2 and ||F||^2 into d_red[2], d_red[3] (synchronous).
 hs_status residual_norms(hs_plan_s *P, const double *F, const double *U, cudaStream_t s,
                          double *res2, double *f2) {
@@ -492,8 +501,10 @@ hs_status hs_plan(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, 
         (st = dev_alloc(P, &P->d_c0, (size_t)Nz + 2)) ||
         (st = dev_alloc(P, &P->d_c1, (size_t)Nz + 2)) ||
         (st = dev_alloc(P, &P->d_cx, (size_t)Nx)) || (st = dev_alloc(P, &P->d_cy, (size_t)Ny)) ||
-        (st = dev_alloc(P, &P->d_fac, 3 * nint)) || (st = dev_alloc(P, &P->d_red, (size_t)64)) ||
-        (st = dev_alloc(P, &P->d_w64, nint)) || (st = dev_alloc(P, &P->d_dscr, nint)) ||
+        (precision == HS_FP64 && (st = dev_alloc(P, &P->d_fac, 3 * nint))) ||
+        (st = dev_alloc(P, &P->d_red, (size_t)64)) ||
+        (precision == HS_FP64 && (st = dev_alloc(P, &P->d_w64, nint))) ||
+        (precision == HS_FP64 && (st = dev_alloc(P, &P->d_dscr, nint))) ||
         (precision == HS_MIXED && (st = dev_alloc(P, &P->d_w32, nint))) ||
         (precision == HS_MIXED && (st = dev_alloc(P, &P->d_Fdf, 2 * nint))) ||
         (precision == HS_MIXED && (st = dev_alloc(P, &P->d_Udf, 2 * nint))) ||
@@ -585,8 +596,16 @@ hs_status hs_set_coeff(hs_plan_t P, const double *c0, const double *c1, const do
     double red[2];
     HS_CK(P, cudaMemcpy(red, P->d_red, sizeof(red), cudaMemcpyDeviceToHost));
     P->min_pivot_ratio = red[1] > 0 ? red[0] / red[1] : 0.0;
-    // FP32 z-solves in the mixed path only when no z-system is close to singular
-    P->thomas32 = (P->precision == HS_MIXED && P->d_fac32 && P->min_pivot_ratio >= 1e-4) ? 1 : 0;
+    // FP32 z-solves in the mixed path only when no z-system is close to
+    // singular; otherwise the FP64 factors are built (and kept) as well.
+    P->thomas32 = (P->precision == HS_MIXED && P->min_pivot_ratio >= 1e-4) ? 1 : 0;
+    if (P->precision == HS_MIXED && !P->thomas32) {
+        if (!P->d_fac) HS_TRY(P, dev_alloc(P, &P->d_fac, 3 * interior_count(P)));
+        HS_TRY(P, ensure_f64_work(P));
+        HS_CK(P, cudaMemcpy(P->d_red, init, sizeof(init), cudaMemcpyHostToDevice));
+        HS_TRY(P, hs_launch_factor(P, 0));
+        HS_CK(P, cudaDeviceSynchronize());
+    }
     P->cd_variant = cd_variant;
     P->have_coeff = 1;
     return P->min_pivot_ratio < 1e-13 ? HS_WARN_NEAR_SINGULAR : HS_OK;
@@ -721,6 +740,7 @@ hs_status hs_residual(hs_plan_t P, const void *f, int f_dtype, int rhs_kind,
     }
     DevBoundary db;
     HS_TRY(P, stage_boundary(P, bnd, esz, s, &db));
+    HS_TRY(P, ensure_f64_work(P));
     HS_TRY(P, hs_launch_rhs(P, fd, f_dtype, rhs_kind, db, P->d_w64, 0, s));
     double r2, f2;
     HS_TRY(P, residual_norms(P, P->d_w64, ud, s, &r2, &f2));

@@ -45,8 +45,8 @@ __global__ void __launch_bounds__(256) factor_kernel(int Nx, int Ny, int Nz,
         const double cp = cx[p], cq = cy[q];
         const double P4 = 4.0 * cp * cq, Q2 = 2.0 * cp, R2 = 2.0 * cq;
         double *cpr = fac;
-        double *alpha = fac + (size_t)Nz * plane;
-        double *beta = fac + 2 * (size_t)Nz * plane;
+        double *alpha = fac ? fac + (size_t)Nz * plane : nullptr;
+        double *beta = fac ? fac + 2 * (size_t)Nz * plane : nullptr;
         double cprev = 0.0;
         for (int l = 0; l < Nz; ++l) {
             const double *cf = coef + (size_t)l * 12;
@@ -58,9 +58,11 @@ __global__ void __launch_bounds__(256) factor_kernel(int Nx, int Ny, int Nz,
             const double c1 = up * inv;
             const size_t o = (size_t)l * plane + idx;
             const double b1 = (l == 0) ? 0.0 : lo * inv;
-            cpr[o] = c1;
-            alpha[o] = inv;
-            beta[o] = b1;
+            if (fac) {
+                cpr[o] = c1;
+                alpha[o] = inv;
+                beta[o] = b1;
+            }
             if (fac32) {
                 fac32[o] = (float)c1;
                 fac32[(size_t)Nz * plane + o] = (float)inv;

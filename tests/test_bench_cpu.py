@@ -1,0 +1,60 @@
+"""Host-side logic of bench.py on CPU: the multi-rank reductions (gloo, 2 ranks),
+the reference arm under torchrun, and the bookkeeping helpers."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        out[rank] = bench.reduce_max(10.0 * (rank + 1), dist, "cpu")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_reduce_max_two_ranks_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    procs = [ctx.Process(target=_worker, args=(r, 2, 29531, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert dict(out) == {0: 20.0, 1: 20.0}
+    assert bench.reduce_max(3.5, None, "cpu") == 3.5
+
+
+def test_reference_arm_two_ranks_prints_one_line():
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", "29533", os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--workload", "cube31_o4", "--steps", "1", "--warmup", "1",
+           "--gpus", "2"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
+    assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_stage_bytes_and_launch_counts():
+    b = bench.stage_bytes("mixed", 1)
+    assert b["residual"] == 20.0 and b["dst_x"] == 16.0 and b["idst_x"] == 32.0
+    assert bench.stage_bytes("mixed", 1, thomas_fp32=False)["thomas"] == 64.0
+    assert bench.launches_per_solve("mixed", 1) == 12
+    assert bench.launches_per_solve("fp64", 0) == 6
+    assert set(bench.WORKLOADS) >= {"cube255_o6", "cube1023_o6", "cd511x8"}

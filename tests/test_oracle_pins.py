@@ -368,3 +368,34 @@ def test_planted_transposed_eigen_index_is_caught(monkeypatch):
     A_int, _ = assemble_matrix(C, Nx, Ny, Nz)
     U_lu = spla.splu(A_int).solve(F.ravel()).reshape(Nz, Ny, Nx)
     assert O.max_rel_diff(U, U_lu) > 1e-3
+
+
+# ------------------------------------------------- separable right-hand sides
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+def test_sine_mode_solution_matches_full_oracle(order):
+    """The 1-D reduction for sums of sine modes equals the full 3-D oracle solve."""
+    N = (20, 17, 23) if order != 6 else (23, 23, 23)
+    L = (1.0, 0.9, 1.2) if order != 6 else (1.0, 1.0, 1.0)
+    rs = np.random.RandomState(order)
+    modes = rs.randint(1, 12, size=(6, 3))
+    amps = rs.standard_normal(6)
+
+    def f(x, y, z):
+        out = 0.0 * (x + y + z)
+        for (p, q, r), A in zip(modes, amps):
+            out = out + A * (np.sin(p * np.pi * x / L[0]) * np.sin(q * np.pi * y / L[1])
+                             * np.sin(r * np.pi * z / L[2]))
+        return out
+
+    K = W.k_profile_to_k2(W.k_tanh(20.0, 10.0))
+    c0, c1, c2 = K.sample(N[2], L[2])
+    fn = W.sample_nodes(f, *N, *L)
+    p = W.Problem(*N, *L, order, W.HELMHOLTZ, c0, c1, c2, fn)
+    U, _ = O.solve(p)
+    U2 = O.solve_sine_modes(modes, amps, N, L, order, c0, c1, c2)
+    assert O.max_rel_diff(U2, U) < 1e-12
+    pts = (np.array([1, 5, N[0]]), np.array([2, N[1], 7]), np.array([N[2], 3, 1]))
+    Us = O.solve_sine_modes(modes, amps, N, L, order, c0, c1, c2, sample=pts)
+    assert np.allclose(Us, U[pts[2] - 1, pts[1] - 1, pts[0] - 1], rtol=0, atol=1e-12 * np.abs(U).max())

@@ -389,6 +389,19 @@ def batch_problem(spec: dict, rhs_index: int, seed: int = 3, dtype=np.float32) -
                                    name=f"batch{spec['N']}r{rhs_index}")
 
 
+def sine_mode_nodes_torch(N: int, modes, amps, dtype=None, device="cuda"):
+    """The sum of sine modes on the node grid, built on a torch device (the
+    1023^3 FP64 grid is 8.6 GB, too slow to fill with numpy).  Input generation
+    only: f(x,y,z) = sum_m A_m sin(p pi x) sin(q pi y) sin(r pi z) on [0,1]^3."""
+    import torch
+    x = torch.arange(N + 2, dtype=torch.float64, device=device) * (np.pi / (N + 1))
+    f = torch.zeros((N + 2, N + 2, N + 2), dtype=torch.float64, device=device)
+    for (p, q, r), A in zip(modes, amps):
+        zy = torch.outer(torch.sin(float(r) * x), torch.sin(float(q) * x))
+        f.addcmul_(zy[:, :, None], torch.sin(float(p) * x)[None, None, :], value=float(A))
+    return f if dtype is None else f.to(dtype)
+
+
 def workload_cube1023_order6(seed: int = 4, N: int = 1023) -> Problem:
     """6th order, N^3 (default 1023^3), k = 40 + 20 tanh(10 (z - 1/2)), 16 sine modes, FP32 f."""
     return sine_mode_problem(N, 6, k_tanh(), nmodes=16, seed=seed, dtype=np.float32,
