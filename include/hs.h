@@ -145,6 +145,17 @@ hs_status hs_set_coeff(hs_plan_t plan, const double *c0, const double *c1, const
 hs_status hs_set_refinement(hs_plan_t plan, int sweeps);
 
 /*
+ * hs_set_refinement_tol -- tolerance-controlled refinement of the HS_MIXED
+ * path (iterative refinement U_{m+1} = U_m + M (F - A U_m), stopped once
+ * ||F - A U_m||_2 / ||F||_2 <= tol or after the hs_set_refinement count).
+ * tol = 0 (default) runs the fixed count.  The decision is taken on the device
+ * (no host synchronisation): the kernels of sweeps after convergence return
+ * at once.  With hs_info the same test is made on the host.
+ * Errors: HS_ERR_INVALID_ARG (tol < 0 or NaN).
+ */
+hs_status hs_set_refinement_tol(hs_plan_t plan, double tol);
+
+/*
  * hs_set_stage_timing -- when on (1), solves record CUDA events around each
  * stage launch (no synchronisation is added); hs_stage_times and
  * hs_info.stage_ms report them.  Off (0) by default.

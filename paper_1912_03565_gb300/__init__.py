@@ -38,7 +38,8 @@ HS_INFO_MAX_ITERS = 8
 HS_INFO_STAGES = 8
 STAGES = ("rhs", "dst_x", "dst_y", "thomas", "idst_y", "idst_x", "residual", "total")
 
-EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_stage_timing", "hs_solve",
+EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_tol",
+            "hs_set_stage_timing", "hs_solve",
             "hs_residual", "hs_stage_times", "hs_workspace_bytes", "hs_destroy",
             "hs_status_str", "hs_last_error", "hs_residual_static")
 HS_STATIC_MAX_NZ = 8192
@@ -87,6 +88,8 @@ def load(path: Optional[str] = None):
     lib.hs_set_coeff.restype = ci
     lib.hs_set_refinement.argtypes = [vp, ci]
     lib.hs_set_refinement.restype = ci
+    lib.hs_set_refinement_tol.argtypes = [vp, cd]
+    lib.hs_set_refinement_tol.restype = ci
     lib.hs_set_stage_timing.argtypes = [vp, ci]
     lib.hs_set_stage_timing.restype = ci
     lib.hs_solve.argtypes = [vp, vp, ci, ci, ctypes.POINTER(hs_boundary), vp, ci, vp,
@@ -173,6 +176,10 @@ def hs_set_coeff(plan, c0, c1=None, c2=None, cd_variant=HS_CD_CORRECTED):
 
 def hs_set_refinement(plan, sweeps):
     return _check(load().hs_set_refinement(plan, sweeps), "hs_set_refinement", plan)
+
+
+def hs_set_refinement_tol(plan, tol):
+    return _check(load().hs_set_refinement_tol(plan, float(tol)), "hs_set_refinement_tol", plan)
 
 
 def hs_set_stage_timing(plan, on):

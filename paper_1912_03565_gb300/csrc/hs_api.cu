@@ -95,7 +95,8 @@ void free_plan(hs_plan_s *P) {
     if (!P) return;
     void *ptrs[] = {P->d_coef, P->d_c0, P->d_c1, P->d_cx, P->d_cy, P->d_fac, P->d_red,
                     P->d_tables, P->d_w64, P->d_w32, P->d_dscr, P->d_stage_f, P->d_stage_u,
-                    P->d_stage_bnd, P->d_fac32, P->d_coef_df, P->d_Fdf, P->d_Udf, P->d_rhs_df};
+                    P->d_stage_bnd, P->d_fac32, P->d_coef_df, P->d_Fdf, P->d_Udf, P->d_rhs_df,
+                    P->d_skip};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->have_events) {
@@ -391,12 +392,18 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
     float *U = P->d_Udf;
     const size_t n = interior_count(P);
     const int sweeps = P->refine_sweeps;
+    // tolerance mode (no info): the device decides after each residual whether to
+    // go on; converged sweeps' kernels return at once and u is written at the end
+    const bool tol_mode = P->refine_tol > 0 && sweeps > 0 && !info;
     for (int m = 0; m <= sweeps; ++m) {
         const bool last = (m == sweeps);
         if (m > 0) {
+            if (tol_mode) P->cur_skip = P->d_skip;
             T.begin(HS_STAGE_RESIDUAL);
-            HS_TRY(P, hs_launch_residual_df(P, F, U, w, s));
+            HS_TRY(P, hs_launch_residual_df(P, F, U, w, s, tol_mode ? P->d_red + 4 + m : nullptr));
             T.end(HS_STAGE_RESIDUAL);
+            if (tol_mode)
+                HS_TRY(P, hs_launch_gate(P->d_red + 4 + m, P->d_red + 4, P->refine_tol, P->d_skip, s));
         }
         // m = 0 transforms F_hi (the first plane of F) directly
         T.begin(HS_STAGE_DST_X);
@@ -413,7 +420,10 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
         HS_TRY(P, hs_launch_dst(P, HS_AXIS_Y, HS_T_F32, HS_T_F32, w, HS_T_F32, w, HS_MODE_WRITE, sy, s));
         T.end(HS_STAGE_IDST_Y);
         T.begin(HS_STAGE_IDST_X);
-        if (sweeps == 0 && !info) {
+        if (tol_mode) {
+            HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_DF, U,
+                                    m == 0 ? HS_MODE_DF_SET : HS_MODE_DF_ADD, sx, s));
+        } else if (sweeps == 0 && !info) {
             HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_F64, u,
                                     HS_MODE_WRITE, sx, s));
         } else if (last && !info) {
@@ -435,9 +445,11 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
             HS_CK(P, cudaStreamSynchronize(s));
             info->rel_residual[m] = h[1] > 0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
             info->iterations = m + 1;
+            if (P->refine_tol > 0 && info->rel_residual[m] <= P->refine_tol) break;
         }
     }
-    if (info) HS_TRY(P, hs_launch_df_to_f64(U, n, u, s));
+    P->cur_skip = nullptr;
+    if (info || tol_mode) HS_TRY(P, hs_launch_df_to_f64(U, n, u, s));
     return HS_OK;
 }
 
@@ -502,7 +514,7 @@ hs_status hs_plan(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, 
         (st = dev_alloc(P, &P->d_c1, (size_t)Nz + 2)) ||
         (st = dev_alloc(P, &P->d_cx, (size_t)Nx)) || (st = dev_alloc(P, &P->d_cy, (size_t)Ny)) ||
         (precision == HS_FP64 && (st = dev_alloc(P, &P->d_fac, 3 * nint))) ||
-        (st = dev_alloc(P, &P->d_red, (size_t)64)) ||
+        (st = dev_alloc(P, &P->d_red, (size_t)64)) || (st = dev_alloc(P, &P->d_skip, (size_t)1)) ||
         (precision == HS_FP64 && (st = dev_alloc(P, &P->d_w64, nint))) ||
         (precision == HS_FP64 && (st = dev_alloc(P, &P->d_dscr, nint))) ||
         (precision == HS_MIXED && (st = dev_alloc(P, &P->d_w32, nint))) ||
@@ -617,6 +629,12 @@ hs_status hs_set_refinement(hs_plan_t P, int sweeps) {
     return HS_OK;
 }
 
+hs_status hs_set_refinement_tol(hs_plan_t P, double tol) {
+    if (!P || !(tol >= 0.0)) return HS_ERR_INVALID_ARG;
+    P->refine_tol = tol;
+    return HS_OK;
+}
+
 hs_status hs_set_stage_timing(hs_plan_t P, int on) {
     if (!P) return HS_ERR_INVALID_ARG;
     P->stage_timing = on ? 1 : 0;
@@ -674,10 +692,16 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
         double *ur = ud + (size_t)r * ucount;
         hs_info *ir = (info && r == nrhs - 1) ? info : nullptr;
         if (ir) memset(ir, 0, sizeof(*ir));
+        const bool tol_mode = P->precision == HS_MIXED && P->refine_tol > 0 &&
+                              P->refine_sweeps > 0 && !ir;
+        if (tol_mode) {
+            HS_CK(P, cudaMemsetAsync(P->d_red + 4, 0, (HS_INFO_MAX_ITERS + 1) * sizeof(double), s));
+            HS_CK(P, cudaMemsetAsync(P->d_skip, 0, sizeof(int), s));
+        }
         T.begin(HS_STAGE_RHS);
         HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db,
                                 P->precision == HS_MIXED ? (void *)P->d_Fdf : (void *)P->d_w64,
-                                P->precision == HS_MIXED, s));
+                                P->precision == HS_MIXED, s, tol_mode ? P->d_red + 4 : nullptr));
         T.end(HS_STAGE_RHS);
         HS_TRY(P, solve_one(P, ur, s, T, ir));
         if (ir && P->precision == HS_FP64) {

@@ -43,6 +43,9 @@ struct hs_plan_s {
     double Lx, Ly, Lz, hx, hy, hz;
     int order, equation, precision, max_rhs;
     int refine_sweeps;
+    double refine_tol;  // > 0: stop refining once ||F - A U|| / ||F|| <= refine_tol
+    int *d_skip;        // device flag: 1 once refinement has converged (later kernels return)
+    const int *cur_skip;  // the flag the launchers pass on (NULL outside tolerance mode)
     int stage_timing;
     int dst_generic;    // 1: always use the runtime-sized transform kernels
     int residual_simple;  // 1: one-thread-per-point residual instead of the z-marching one
@@ -120,11 +123,16 @@ int hs_dst_fits(const DstAxis &ax, int axis, int tc);
 // Lifted right-hand side F (interior) from f: FP64 (out_df = 0) or a
 // double-float pair in two FP32 planes [2][Nz][Ny][Nx] (out_df = 1).
 hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_kind,
-                        const DevBoundary &b, void *F, int out_df, cudaStream_t s);
+                        const DevBoundary &b, void *F, int out_df, cudaStream_t s,
+                        double *f2 = nullptr);
 
-// r = F - A U in double-float arithmetic (F, U double-float pairs; r FP32).
+// r = F - A U in double-float arithmetic (F, U double-float pairs; r FP32);
+// adds ||r||^2 to *r2 when r2 is not NULL.
 hs_status hs_launch_residual_df(const hs_plan_s *P, const float *F, const float *U, float *r,
-                                cudaStream_t s);
+                                cudaStream_t s, double *r2 = nullptr);
+
+// Sets *skip = 1 when *r2 <= tol^2 * *f2 (refinement converged).
+hs_status hs_launch_gate(const double *r2, const double *f2, double tol, int *skip, cudaStream_t s);
 
 // u = hi + lo in FP64 for a double-float array of n pairs (two planes).
 hs_status hs_launch_df_to_f64(const float *x, size_t n, double *u, cudaStream_t s);

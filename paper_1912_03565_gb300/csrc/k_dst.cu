@@ -100,7 +100,8 @@ __device__ __forceinline__ void stockham_stage(const typename Cplx<Tc>::t *src,
 template <typename Tc, typename Tin, typename Tout, int AXIS, int MODE>
 __global__ void __launch_bounds__(256)
 dst_fft_kernel(DstAxis ax, const Tin *in, Tout *out, double *aux, int Nx, int Ny, int Nz, int S,
-               Tc scale) {
+               Tc scale, const int *skip) {
+    if (skip && *skip) return;
     typedef typename Cplx<Tc>::t T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const size_t lo_off = (size_t)Nx * Ny * Nz;  // lo plane of a double-float output
@@ -206,7 +207,8 @@ dst_fft_kernel(DstAxis ax, const Tin *in, Tout *out, double *aux, int Nx, int Ny
 template <typename Tc, typename Tin, typename Tout, int AXIS, int MODE>
 __global__ void __launch_bounds__(256)
 dst_direct_kernel(DstAxis ax, const Tin *in, Tout *out, double *aux, int Nx, int Ny, int Nz, int S,
-                  Tc scale) {
+                  Tc scale, const int *skip) {
+    if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const size_t lo_off = (size_t)Nx * Ny * Nz;  // lo plane of a double-float output
     (void)lo_off;
@@ -308,21 +310,25 @@ hs_status launch_typed(const hs_plan_s *P, int axis, const void *in, void *out, 
         if (axis == HS_AXIS_X) {
             auto k = dst_fft_kernel<Tc, Tin, Tout, HS_AXIS_X, MODE>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k<<<grid, 256, smem, s>>>(ax, pin, pout, aux, P->Nx, P->Ny, P->Nz, S, (Tc)scale);
+            k<<<grid, 256, smem, s>>>(ax, pin, pout, aux, P->Nx, P->Ny, P->Nz, S, (Tc)scale,
+                                      P->cur_skip);
         } else {
             auto k = dst_fft_kernel<Tc, Tin, Tout, HS_AXIS_Y, MODE>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k<<<grid, 256, smem, s>>>(ax, pin, pout, aux, P->Nx, P->Ny, P->Nz, S, (Tc)scale);
+            k<<<grid, 256, smem, s>>>(ax, pin, pout, aux, P->Nx, P->Ny, P->Nz, S, (Tc)scale,
+                                      P->cur_skip);
         }
     } else {
         if (axis == HS_AXIS_X) {
             auto k = dst_direct_kernel<Tc, Tin, Tout, HS_AXIS_X, MODE>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k<<<grid, 256, smem, s>>>(ax, pin, pout, aux, P->Nx, P->Ny, P->Nz, S, (Tc)scale);
+            k<<<grid, 256, smem, s>>>(ax, pin, pout, aux, P->Nx, P->Ny, P->Nz, S, (Tc)scale,
+                                      P->cur_skip);
         } else {
             auto k = dst_direct_kernel<Tc, Tin, Tout, HS_AXIS_Y, MODE>;
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k<<<grid, 256, smem, s>>>(ax, pin, pout, aux, P->Nx, P->Ny, P->Nz, S, (Tc)scale);
+            k<<<grid, 256, smem, s>>>(ax, pin, pout, aux, P->Nx, P->Ny, P->Nz, S, (Tc)scale,
+                                      P->cur_skip);
         }
     }
     return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;

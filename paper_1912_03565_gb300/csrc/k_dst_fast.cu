@@ -273,7 +273,9 @@ __device__ __forceinline__ int ZPAD(int m) { return 2 * PAD(m >> 1) + (m & 1); }
 template <typename Tc, typename Tin, typename Tout, int AXIS, int MODE, int M, int S, int... Rs>
 __global__ void __launch_bounds__(256, (sizeof(Tc) == 4 ? 3 : 1))
 dst_fast_kernel(const Tin *in, Tout *out, double *aux, const typename Cx<Tc>::t *roots_g,
-                const typename Cx<Tc>::t *half_g, int Nx, int Ny, int Nz, Tc scale) {
+                const typename Cx<Tc>::t *half_g, int Nx, int Ny, int Nz, Tc scale,
+                const int *skip) {
+    if (skip && *skip) return;
     typedef typename Cx<Tc>::t T2;
     constexpr int N = M - 1;
     constexpr int LS = LineStride<M>::value;
@@ -450,7 +452,7 @@ hs_status launch_m(const hs_plan_s *P, int axis, const DstAxis &ax, const void *
         const long nrows = (long)P->Ny * P->Nz;
         k<<<(unsigned)((nrows + S - 1) / S), 256, smem, st>>>(
             static_cast<const Tin *>(in), static_cast<Tout *>(out), aux, roots, half, P->Nx,
-            P->Ny, P->Nz, (Tc)scale);
+            P->Ny, P->Nz, (Tc)scale, P->cur_skip);
     } else {
         constexpr int S = Lines<Tc, M, HS_AXIS_Y>::value;
         constexpr size_t smem = fast_smem<Tc, M, S>();
@@ -461,7 +463,7 @@ hs_status launch_m(const hs_plan_s *P, int axis, const DstAxis &ax, const void *
             return HS_ERR_CUDA;
         dim3 grid((unsigned)((P->Nx + S - 1) / S), (unsigned)P->Nz, 1);
         k<<<grid, 256, smem, st>>>(static_cast<const Tin *>(in), static_cast<Tout *>(out), aux,
-                                   roots, half, P->Nx, P->Ny, P->Nz, (Tc)scale);
+                                   roots, half, P->Nx, P->Ny, P->Nz, (Tc)scale, P->cur_skip);
     }
     return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }

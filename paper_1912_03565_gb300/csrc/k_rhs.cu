@@ -57,6 +57,22 @@ __device__ double boundary_value(const RhsArgs &a, int i, int j, int l) {
     return p ? ld(p, idx) : 0.0;
 }
 
+// Adds a per-thread value over the CTA and atomically to *out (thread 0).
+__device__ __forceinline__ void block_sum_to(double v, double *out) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __shared__ double part[32];
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    __syncthreads();
+    if ((tid & 31) == 0) part[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += part[w];
+        atomicAdd(out, s);
+    }
+}
+
 // Subtract the boundary-node terms of row (i, j, l) (node indices, interior).
 template <typename T>
 __device__ double lift_terms(const RhsArgs &a, int i, int j, int l) {
@@ -339,7 +355,8 @@ struct LeanSum {
 
 template <typename T>
 __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_df_kernel(RhsArgs a, const T *__restrict__ f,
-                                                                float *__restrict__ Fo) {
+                                                                float *__restrict__ Fo,
+                                                                double *f2out) {
     __shared__ float ph[5][RHY][RHX];
     __shared__ float pq[5][RHY][RHX];
     constexpr int NT = RTX * RTY;
@@ -381,6 +398,7 @@ __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_df_kernel(RhsArgs a, const
         store(l);
     }
     fetch(lbeg + 2);
+    float fsq = 0.f;
     const int i = i0 + tx, j = j0 + ty;
     const int cx = tx + 2, cy = ty + 2;
     for (int l = lbeg; l <= lend; ++l) {
@@ -448,9 +466,11 @@ __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_df_kernel(RhsArgs a, const
             const size_t out = ((size_t)(l - 1) * a.Ny + (j - 1)) * a.Nx + (i - 1);
             Fo[out] = val.hi;
             Fo[out + n] = val.lo;
+            fsq = fmaf(val.hi, val.hi, fsq);
         }
         __syncthreads();
     }
+    if (f2out) block_sum_to((double)fsq, f2out);
 }
 
 // r = F - A U in double-float arithmetic: F and U are (hi, lo) pairs, the
@@ -546,7 +566,9 @@ __global__ void __launch_bounds__(QTX *QTY) residual_zmarch_kernel(int Nx, int N
                                                                     const float2 *__restrict__ coef,
                                                                     const float *__restrict__ F,
                                                                     const float *__restrict__ U,
-                                                                    float *__restrict__ r) {
+                                                                    float *__restrict__ r,
+                                                                    const int *skip, double *r2out) {
+    if (skip && *skip) return;
     // two plane slots: the plane whose sums are being formed and the next one,
     // whose global loads are issued into registers before the current plane's
     // arithmetic (so their latency overlaps it)
@@ -612,6 +634,7 @@ __global__ void __launch_bounds__(QTX *QTY) residual_zmarch_kernel(int Nx, int N
     };
 
     PlaneSums pm, p0, pp;
+    float rsq = 0.f;
     fetch(lbeg - 1);
     store(lbeg - 1);
     __syncthreads();
@@ -646,11 +669,18 @@ __global__ void __launch_bounds__(QTX *QTY) residual_zmarch_kernel(int Nx, int N
             dfloat au;
             df_fast_two_sum(S, E, au.hi, au.lo);
             const dfloat res = df_add_accurate(dfloat{F[o], F[o + n]}, df_neg(au));
-            r[o] = res.hi + res.lo;
+            const float rv = res.hi + res.lo;
+            r[o] = rv;
+            rsq = fmaf(rv, rv, rsq);
         }
         pm = p0;
         p0 = pp;
     }
+    if (r2out) block_sum_to((double)rsq, r2out);
+}
+
+__global__ void refine_gate_kernel(const double *r2, const double *f2, double tol2, int *skip) {
+    if (*skip == 0 && *r2 <= tol2 * *f2) *skip = 1;
 }
 
 // u (FP64) = hi + lo of a double-float array.
@@ -727,7 +757,7 @@ __global__ void __launch_bounds__(256) sumsq_kernel(const T *__restrict__ x, siz
 }  // namespace
 
 hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_kind,
-                        const DevBoundary &b, void *F, int out_df, cudaStream_t s) {
+                        const DevBoundary &b, void *F, int out_df, cudaStream_t s, double *f2) {
     RhsArgs a;
     a.Nx = P->Nx;
     a.Ny = P->Ny;
@@ -750,13 +780,13 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
         if (f_dtype == HS_F64) {
             if (out_df)
                 rhs_tiled_df_kernel<double><<<tg, tb, 0, s>>>(a, static_cast<const double *>(f),
-                                                              static_cast<float *>(F));
+                                                              static_cast<float *>(F), f2);
             else
                 rhs_tiled_kernel<double, 0><<<tg, tb, 0, s>>>(a, static_cast<const double *>(f), F);
         } else {
             if (out_df)
                 rhs_tiled_df_kernel<float><<<tg, tb, 0, s>>>(a, static_cast<const float *>(f),
-                                                             static_cast<float *>(F));
+                                                             static_cast<float *>(F), f2);
             else
                 rhs_tiled_kernel<float, 0><<<tg, tb, 0, s>>>(a, static_cast<const float *>(f), F);
         }
@@ -779,7 +809,7 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
 }
 
 hs_status hs_launch_residual_df(const hs_plan_s *P, const float *F, const float *U, float *r,
-                                cudaStream_t s) {
+                                cudaStream_t s, double *r2) {
     dim3 block(32, 8, 1);
     dim3 grid((P->Nx + 31) / 32, (P->Ny + 7) / 8, P->Nz);
     if (P->residual_simple) {
@@ -787,8 +817,15 @@ hs_status hs_launch_residual_df(const hs_plan_s *P, const float *F, const float 
     } else {
         dim3 qb(QTX, QTY, 1);
         dim3 qg((P->Nx + QTX - 1) / QTX, (P->Ny + QTY - 1) / QTY, (P->Nz + QZ - 1) / QZ);
-        residual_zmarch_kernel<<<qg, qb, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df, F, U, r);
+        residual_zmarch_kernel<<<qg, qb, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df, F, U, r,
+                                                 P->cur_skip, r2);
     }
+    return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
+
+hs_status hs_launch_gate(const double *r2, const double *f2, double tol, int *skip,
+                         cudaStream_t s) {
+    refine_gate_kernel<<<1, 1, 0, s>>>(r2, f2, tol * tol, skip);
     return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 

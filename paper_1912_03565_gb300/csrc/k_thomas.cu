@@ -159,7 +159,9 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
 // FP64 path: data holds Fhat on entry and W on exit (forward sweep in place).
 __global__ void __launch_bounds__(256) thomas64_kernel(int Nx, int Ny, int Nz,
                                                         double *__restrict__ data,
-                                                        const double *__restrict__ fac) {
+                                                        const double *__restrict__ fac,
+                                                        const int *skip) {
+    if (skip && *skip) return;
     const size_t plane = (size_t)Nx * Ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= plane) return;
@@ -172,7 +174,9 @@ __global__ void __launch_bounds__(256) thomas64_kernel(int Nx, int Ny, int Nz,
 __global__ void __launch_bounds__(256) thomas32_kernel(int Nx, int Ny, int Nz,
                                                         float *__restrict__ data,
                                                         double *__restrict__ scratch,
-                                                        const double *__restrict__ fac) {
+                                                        const double *__restrict__ fac,
+                                                        const int *skip) {
+    if (skip && *skip) return;
     const size_t plane = (size_t)Nx * Ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= plane) return;
@@ -186,7 +190,9 @@ __global__ void __launch_bounds__(256) thomas32_kernel(int Nx, int Ny, int Nz,
 // refinement sweeps like the FP32 transform error.
 __global__ void __launch_bounds__(256) thomas_f32_kernel(int Nx, int Ny, int Nz,
                                                           float *__restrict__ data,
-                                                          const float *__restrict__ fac) {
+                                                          const float *__restrict__ fac,
+                                                          const int *skip) {
+    if (skip && *skip) return;
     const size_t plane = (size_t)Nx * Ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= plane) return;
@@ -210,12 +216,12 @@ hs_status hs_launch_thomas(const hs_plan_s *P, int tio, void *data, double *scra
     const unsigned blocks = (unsigned)((plane + 255) / 256);
     if (tio == HS_T_F64)
         thomas64_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, static_cast<double *>(data),
-                                               P->d_fac);
+                                               P->d_fac, P->cur_skip);
     else if (P->thomas32)
         thomas_f32_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, static_cast<float *>(data),
-                                                 P->d_fac32);
+                                                 P->d_fac32, P->cur_skip);
     else
         thomas32_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, static_cast<float *>(data),
-                                               scratch, P->d_fac);
+                                               scratch, P->d_fac, P->cur_skip);
     return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }

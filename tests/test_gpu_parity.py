@@ -275,3 +275,40 @@ def test_transform_lengths(N, precision):
         ref = oracle_solve(p)
         u, _ = gpu_solve(p, precision, sweeps=3)
         assert O.max_rel_diff(u, ref) <= (TOL64 if precision == H.HS_FP64 else TOLMIX)
+
+
+def test_refinement_tolerance_stops_on_device():
+    """With a tolerance the device stops refining once ||F - A U|| / ||F|| <= tol:
+    the result equals the fixed-count solve with the count the residuals imply."""
+    torch = _torch()
+    p = W.workload_cube255_order6(N=127)
+    ref = oracle_solve(p)
+    f = torch.from_numpy(p.f_nodes).cuda()
+    fnn = [None if a is None else torch.from_numpy(a).cuda() for a in p.fnn]
+
+    def run(sweeps, tol, info=False):
+        s = H.Solver(p.Nx, p.Ny, p.Nz, p.Lx, p.Ly, p.Lz, 6, H.HS_HELMHOLTZ, H.HS_MIXED)
+        try:
+            s.set_coeff(p.c0, p.c1, p.c2)
+            H.hs_set_refinement(s.plan, sweeps)
+            H.hs_set_refinement_tol(s.plan, tol)
+            u = torch.zeros((p.Nz, p.Ny, p.Nx), dtype=torch.float64, device="cuda")
+            _, inf = s.solve(f, u, H.HS_F64, H.HS_RHS_NODAL, None, fnn, info=info)
+            torch.cuda.synchronize()
+            return u.cpu().numpy(), inf
+        finally:
+            s.close()
+
+    _, inf = run(4, 0.0, info=True)
+    rr = inf["rel_residual"]            # residual after 0, 1, ..., 4 sweeps
+    tol = 1e-9
+    need = next(m for m in range(5) if rr[m] <= tol)
+    u_tol, _ = run(4, tol)
+    u_fix, _ = run(need, 0.0)
+    assert O.max_rel_diff(u_tol, u_fix) <= 1e-15
+    assert O.max_rel_diff(u_tol, ref) <= TOLMIX
+    u_all, _ = run(3, 1e-30)             # never met: all sweeps run
+    u_3, _ = run(3, 0.0)
+    assert O.max_rel_diff(u_all, u_3) <= 1e-15
+    _, inf_t = run(4, tol, info=True)    # host-side test with diagnostics
+    assert inf_t["iterations"] == need + 1
