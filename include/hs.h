@@ -227,6 +227,63 @@ hs_status hs_residual_static(int Nx, int Ny, int Nz, double Lx, double Ly, doubl
                              const double *c2, const double *F, const double *u, void *stream,
                              double *res_norm, double *rhs_norm);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent problems solved by the HS_MIXED path in ONE persistent
+ * kernel launch (captured in a CUDA graph): uneven sizes, their own
+ * coefficient profiles and 1..16 right-hand sides each.  Persistent CTAs take
+ * (problem, RHS, stage, tile) work items from a queue and wait -- bounded --
+ * for the previous stage of the same problem and RHS.  No paper counterpart
+ * (the paper solves one problem at a time); Section 3.6 is the per-problem
+ * solve.  Transform lengths N_x + 1 and N_y + 1 must be in
+ * {32, 64, 96, 128, 192, 256, 384}. */
+typedef struct hs_batch_s *hs_batch_t;
+
+typedef struct {
+    int Nx, Ny, Nz;          /* as hs_plan */
+    double Lx, Ly, Lz;
+    int order, equation, cd_variant;
+    const double *c0, *c1, *c2;   /* HOST profiles (as hs_set_coeff), copied */
+    int nrhs;                /* 1..16 */
+    const void *f;           /* DEVICE, [nrhs][Nz+2][Ny+2][Nx+2] nodal f of the batch's f_dtype */
+    double *u;               /* DEVICE, [nrhs][Nz][Ny][Nx] FP64 output */
+} hs_problem_desc;
+
+/*
+ * hs_batch_create -- plan every problem (tables, cached factorization,
+ * workspace per RHS) and the work-item list.  sweeps: refinement sweeps of
+ * every solve (0..HS_INFO_MAX_ITERS-1).  Synchronous; allocates.
+ * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED (a transform length outside
+ * the set above), HS_ERR_OOM, HS_ERR_CUDA.
+ */
+hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int nprob, int f_dtype,
+                          int sweeps);
+
+/* hs_batch_set_io -- new f and u device pointers of problem k (same layout). */
+hs_status hs_batch_set_io(hs_batch_t batch, int k, const void *f, double *u);
+
+/*
+ * hs_batch_solve -- one graph launch solving every problem of the batch on
+ * `stream` (the graph is built on the first call for a stream).  sync = 0:
+ * asynchronous; sync = 1: waits and returns HS_ERR_TIMEOUT if a bounded wait
+ * inside the launch gave up (the results are then incomplete).
+ */
+hs_status hs_batch_solve(hs_batch_t batch, void *stream, int sync);
+
+/* hs_batch_set_wait_limit -- spin iterations (about 100 ns each) before a wait
+ * inside the launch gives up (default 2e7). */
+hs_status hs_batch_set_wait_limit(hs_batch_t batch, long long spins);
+
+/* hs_batch_debug_stall -- test hook: on = 1 makes one dependency of the first
+ * problem unsatisfiable, so the next solve must end with HS_ERR_TIMEOUT; on =
+ * 0 restores it. */
+hs_status hs_batch_debug_stall(hs_batch_t batch, int on);
+
+/* hs_batch_workspace_bytes -- device bytes owned by the batch. */
+size_t hs_batch_workspace_bytes(hs_batch_t batch);
+
+/* hs_batch_destroy -- free a batch (NULL accepted).  Synchronises the device. */
+hs_status hs_batch_destroy(hs_batch_t batch);
+
 /* hs_workspace_bytes -- device bytes owned by the plan (tables, cached
  * factorization, workspace). */
 size_t hs_workspace_bytes(hs_plan_t plan);

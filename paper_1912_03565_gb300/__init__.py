@@ -41,12 +41,22 @@ STAGES = ("rhs", "dst_x", "dst_y", "thomas", "idst_y", "idst_x", "residual", "to
 EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_tol",
             "hs_set_stage_timing", "hs_solve",
             "hs_residual", "hs_stage_times", "hs_workspace_bytes", "hs_destroy",
-            "hs_status_str", "hs_last_error", "hs_residual_static")
+            "hs_status_str", "hs_last_error", "hs_residual_static", "hs_batch_create",
+            "hs_batch_set_io", "hs_batch_solve", "hs_batch_set_wait_limit", "hs_batch_debug_stall",
+            "hs_batch_workspace_bytes", "hs_batch_destroy")
 HS_STATIC_MAX_NZ = 8192
 
 
 class hs_boundary(ctypes.Structure):
     _fields_ = [("face", ctypes.c_void_p * 6), ("fnn", ctypes.c_void_p * 6)]
+
+
+class hs_problem_desc(ctypes.Structure):
+    _fields_ = [("Nx", ctypes.c_int), ("Ny", ctypes.c_int), ("Nz", ctypes.c_int),
+                ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
+                ("order", ctypes.c_int), ("equation", ctypes.c_int), ("cd_variant", ctypes.c_int),
+                ("c0", ctypes.c_void_p), ("c1", ctypes.c_void_p), ("c2", ctypes.c_void_p),
+                ("nrhs", ctypes.c_int), ("f", ctypes.c_void_p), ("u", ctypes.c_void_p)]
 
 
 class hs_info(ctypes.Structure):
@@ -103,6 +113,20 @@ def load(path: Optional[str] = None):
     lib.hs_residual_static.argtypes = [ci, ci, ci, cd, cd, cd, ci, ci, ci, vp, vp, vp, vp, vp, vp,
                                        ctypes.POINTER(cd), ctypes.POINTER(cd)]
     lib.hs_residual_static.restype = ci
+    lib.hs_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(hs_problem_desc), ci, ci, ci]
+    lib.hs_batch_create.restype = ci
+    lib.hs_batch_set_io.argtypes = [vp, ci, vp, vp]
+    lib.hs_batch_set_io.restype = ci
+    lib.hs_batch_solve.argtypes = [vp, vp, ci]
+    lib.hs_batch_solve.restype = ci
+    lib.hs_batch_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    lib.hs_batch_set_wait_limit.restype = ci
+    lib.hs_batch_debug_stall.argtypes = [vp, ci]
+    lib.hs_batch_debug_stall.restype = ci
+    lib.hs_batch_workspace_bytes.argtypes = [vp]
+    lib.hs_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.hs_batch_destroy.argtypes = [vp]
+    lib.hs_batch_destroy.restype = ci
     lib.hs_workspace_bytes.argtypes = [vp]
     lib.hs_workspace_bytes.restype = ctypes.c_size_t
     lib.hs_destroy.argtypes = [vp]
@@ -251,6 +275,58 @@ def hs_last_error(plan):
 
 def hs_status_str(s):
     return status_str(s)
+
+
+def hs_batch_create(problems, f_dtype=HS_F32, sweeps=1):
+    """problems: list of dicts with N (Nx,Ny,Nz), L, order, equation, cd_variant, c0, c1, c2,
+    nrhs, f (device array), u (device array).  Returns (handle, keepalive)."""
+    import numpy as np
+    arr = (hs_problem_desc * len(problems))()
+    keep = []
+    for k, p in enumerate(problems):
+        cs = [None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+              for c in (p["c0"], p.get("c1"), p.get("c2"))]
+        keep.append(cs)
+        d = arr[k]
+        d.Nx, d.Ny, d.Nz = p["N"]
+        d.Lx, d.Ly, d.Lz = p["L"]
+        d.order, d.equation = p["order"], p.get("equation", HS_HELMHOLTZ)
+        d.cd_variant = p.get("cd_variant", HS_CD_CORRECTED)
+        d.c0, d.c1, d.c2 = [_ptr(c) for c in cs]
+        d.nrhs = p["nrhs"]
+        d.f, d.u = _ptr(p["f"]), _ptr(p["u"])
+    h = ctypes.c_void_p()
+    _check(load().hs_batch_create(ctypes.byref(h), arr, len(problems), f_dtype, sweeps),
+           "hs_batch_create")
+    return h.value
+
+
+def hs_batch_set_io(batch, k, f, u):
+    return _check(load().hs_batch_set_io(batch, k, _ptr(f), _ptr(u)), "hs_batch_set_io")
+
+
+def hs_batch_solve(batch, stream=None, sync=True):
+    st = load().hs_batch_solve(batch, _stream_ptr(stream), 1 if sync else 0)
+    _check(st, "hs_batch_solve")
+    return st
+
+
+def hs_batch_set_wait_limit(batch, spins):
+    return _check(load().hs_batch_set_wait_limit(batch, int(spins)), "hs_batch_set_wait_limit")
+
+
+def hs_batch_debug_stall(batch, on):
+    return _check(load().hs_batch_debug_stall(batch, 1 if on else 0), "hs_batch_debug_stall")
+
+
+def hs_batch_workspace_bytes(batch):
+    return int(load().hs_batch_workspace_bytes(batch))
+
+
+def hs_batch_destroy(batch):
+    if batch:
+        return _check(load().hs_batch_destroy(batch), "hs_batch_destroy")
+    return HS_OK
 
 
 # ------------------------------------------------------------------ convenience

@@ -1,0 +1,957 @@
+// Tile functions shared by the stand-alone kernels and the batched persistent
+// kernel: one CTA's work for the transforms (k_dst_fast.cu), the double-float
+// right-hand side and residual (k_rhs.cu) and the z-solves (k_thomas.cu).
+// Each takes its tile index and, where it needs one, a pointer to the CTA's
+// shared memory instead of reading blockIdx or declaring shared arrays, so a
+// persistent CTA can run tiles of different stages one after another.
+#pragma once
+
+#include "hs_internal.cuh"
+
+namespace hs_tiles {
+
+// Load that bypasses L1 when COH: data written by other CTAs earlier in the
+// same launch must not be served from a stale L1 line.
+template <bool COH, typename T>
+__device__ __forceinline__ T ldc(const T *p) {
+    if constexpr (COH)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
+// =================================================================== transforms
+__device__ __forceinline__ double cos48(int k) {
+    switch (k) {
+        case 0: return 1.0;
+        case 1: return 0.9914448613738104;
+        case 2: return 0.9659258262890683;
+        case 3: return 0.9238795325112867;
+        case 4: return 0.8660254037844387;
+        case 5: return 0.7933533402912352;
+        case 6: return 0.7071067811865476;
+        case 7: return 0.6087614290087207;
+        case 8: return 0.5000000000000001;
+        case 9: return 0.38268343236508984;
+        case 10: return 0.25881904510252074;
+        case 11: return 0.1305261922200517;
+        case 12: return 0.0;
+        case 13: return -0.1305261922200516;
+        case 14: return -0.25881904510252063;
+        case 15: return -0.3826834323650895;
+        case 16: return -0.4999999999999998;
+        case 17: return -0.6087614290087207;
+        case 18: return -0.7071067811865475;
+        case 19: return -0.793353340291235;
+        case 20: return -0.8660254037844387;
+        case 21: return -0.9238795325112867;
+        case 22: return -0.9659258262890682;
+        case 23: return -0.9914448613738104;
+        case 24: return -1.0;
+        case 25: return -0.9914448613738104;
+        case 26: return -0.9659258262890683;
+        case 27: return -0.9238795325112868;
+        case 28: return -0.8660254037844388;
+        case 29: return -0.7933533402912352;
+        case 30: return -0.7071067811865479;
+        case 31: return -0.6087614290087209;
+        case 32: return -0.5000000000000004;
+        case 33: return -0.3826834323650895;
+        case 34: return -0.25881904510252063;
+        case 35: return -0.13052619222005163;
+        case 36: return 0.0;
+        case 37: return 0.13052619222005127;
+        case 38: return 0.2588190451025203;
+        case 39: return 0.38268343236508917;
+        case 40: return 0.5000000000000001;
+        case 41: return 0.6087614290087199;
+        case 42: return 0.7071067811865474;
+        case 43: return 0.7933533402912349;
+        case 44: return 0.8660254037844384;
+        case 45: return 0.9238795325112868;
+        case 46: return 0.9659258262890681;
+        case 47: return 0.9914448613738104;
+        default: return 0.0;
+    }
+}
+__device__ __forceinline__ double sin48(int k) {
+    switch (k) {
+        case 0: return 0.0;
+        case 1: return 0.13052619222005157;
+        case 2: return 0.25881904510252074;
+        case 3: return 0.3826834323650898;
+        case 4: return 0.49999999999999994;
+        case 5: return 0.6087614290087207;
+        case 6: return 0.7071067811865475;
+        case 7: return 0.7933533402912352;
+        case 8: return 0.8660254037844386;
+        case 9: return 0.9238795325112867;
+        case 10: return 0.9659258262890683;
+        case 11: return 0.9914448613738104;
+        case 12: return 1.0;
+        case 13: return 0.9914448613738104;
+        case 14: return 0.9659258262890683;
+        case 15: return 0.9238795325112868;
+        case 16: return 0.8660254037844387;
+        case 17: return 0.7933533402912352;
+        case 18: return 0.7071067811865476;
+        case 19: return 0.6087614290087209;
+        case 20: return 0.49999999999999994;
+        case 21: return 0.3826834323650899;
+        case 22: return 0.258819045102521;
+        case 23: return 0.130526192220052;
+        case 24: return 0.0;
+        case 25: return -0.13052619222005177;
+        case 26: return -0.2588190451025208;
+        case 27: return -0.38268343236508967;
+        case 28: return -0.4999999999999997;
+        case 29: return -0.6087614290087207;
+        case 30: return -0.7071067811865471;
+        case 31: return -0.7933533402912349;
+        case 32: return -0.8660254037844384;
+        case 33: return -0.9238795325112868;
+        case 34: return -0.9659258262890683;
+        case 35: return -0.9914448613738104;
+        case 36: return -1.0;
+        case 37: return -0.9914448613738105;
+        case 38: return -0.9659258262890684;
+        case 39: return -0.923879532511287;
+        case 40: return -0.8660254037844386;
+        case 41: return -0.7933533402912357;
+        case 42: return -0.7071067811865477;
+        case 43: return -0.6087614290087209;
+        case 44: return -0.5000000000000004;
+        case 45: return -0.38268343236508956;
+        case 46: return -0.25881904510252157;
+        case 47: return -0.13052619222005168;
+        default: return 0.0;
+    }
+}
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { typedef double2 t; };
+template <> struct Cx<float> { typedef float2 t; };
+
+template <typename T2, typename T>
+__device__ __forceinline__ T2 mk2(T x, T y) {
+    T2 r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+
+// y * W_R^m (forward sign): W = cos(2 pi m/R) - i sin(2 pi m/R)
+template <typename Tc, int R>
+__device__ __forceinline__ typename Cx<Tc>::t twiddle_const(typename Cx<Tc>::t y, int m) {
+    const int k = (m % R) * (48 / R);
+    if (k == 0) return y;
+    if (k == 12) return mk2<typename Cx<Tc>::t>(y.y, -y.x);     // -i
+    if (k == 24) return mk2<typename Cx<Tc>::t>(-y.x, -y.y);    // -1
+    if (k == 36) return mk2<typename Cx<Tc>::t>(-y.y, y.x);     // +i
+    const Tc c = (Tc)cos48(k), s = (Tc)sin48(k);
+    return mk2<typename Cx<Tc>::t>(y.x * c + y.y * s, y.y * c - y.x * s);
+}
+
+template <typename Tc, int R> struct Dft;
+
+template <typename Tc> struct Dft<Tc, 2> {
+    typedef typename Cx<Tc>::t T2;
+    static __device__ __forceinline__ void run(T2 *v) {
+        const T2 a = v[0], b = v[1];
+        v[0] = mk2<T2>(a.x + b.x, a.y + b.y);
+        v[1] = mk2<T2>(a.x - b.x, a.y - b.y);
+    }
+};
+
+template <typename Tc> struct Dft<Tc, 3> {
+    typedef typename Cx<Tc>::t T2;
+    static __device__ __forceinline__ void run(T2 *v) {
+        const Tc k3 = (Tc)0.86602540378443864676;
+        const T2 a = v[0];
+        const T2 s = mk2<T2>(v[1].x + v[2].x, v[1].y + v[2].y);
+        const T2 d = mk2<T2>(v[1].x - v[2].x, v[1].y - v[2].y);
+        const T2 t = mk2<T2>(a.x - (Tc)0.5 * s.x, a.y - (Tc)0.5 * s.y);
+        v[0] = mk2<T2>(a.x + s.x, a.y + s.y);
+        v[1] = mk2<T2>(t.x + k3 * d.y, t.y - k3 * d.x);
+        v[2] = mk2<T2>(t.x - k3 * d.y, t.y + k3 * d.x);
+    }
+};
+
+template <typename Tc> struct Dft<Tc, 4> {
+    typedef typename Cx<Tc>::t T2;
+    static __device__ __forceinline__ void run(T2 *v) {
+        const T2 s02 = mk2<T2>(v[0].x + v[2].x, v[0].y + v[2].y);
+        const T2 d02 = mk2<T2>(v[0].x - v[2].x, v[0].y - v[2].y);
+        const T2 s13 = mk2<T2>(v[1].x + v[3].x, v[1].y + v[3].y);
+        const T2 d13 = mk2<T2>(v[1].y - v[3].y, v[3].x - v[1].x);  // -i (v1 - v3)
+        v[0] = mk2<T2>(s02.x + s13.x, s02.y + s13.y);
+        v[2] = mk2<T2>(s02.x - s13.x, s02.y - s13.y);
+        v[1] = mk2<T2>(d02.x + d13.x, d02.y + d13.y);
+        v[3] = mk2<T2>(d02.x - d13.x, d02.y - d13.y);
+    }
+};
+
+// R = R1 * R2 with R1 = 4 when possible, else 2, else 3.
+template <typename Tc, int R> struct Dft {
+    typedef typename Cx<Tc>::t T2;
+    static constexpr int R1 = (R % 4 == 0) ? 4 : ((R % 2 == 0) ? 2 : 3);
+    static constexpr int R2 = R / R1;
+    static __device__ __forceinline__ void run(T2 *x) {
+        T2 y[R];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) {
+            T2 t[R1];
+#pragma unroll
+            for (int n1 = 0; n1 < R1; ++n1) t[n1] = x[R2 * n1 + n2];
+            Dft<Tc, R1>::run(t);
+#pragma unroll
+            for (int k1 = 0; k1 < R1; ++k1) y[n2 * R1 + k1] = twiddle_const<Tc, R>(t[k1], n2 * k1);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+            T2 t[R2];
+#pragma unroll
+            for (int n2 = 0; n2 < R2; ++n2) t[n2] = y[n2 * R1 + k1];
+            Dft<Tc, R2>::run(t);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = t[k2];
+        }
+    }
+};
+
+// Shared-memory layout of a line: complex element i lives at PAD(i) = i + i/16,
+// so the stride-16 writes of a first radix-16 stage fall in distinct banks.
+__device__ __forceinline__ int PAD(int i) { return i + (i >> 4); }
+template <int M> struct LineStride { static constexpr int value = M + (M >> 4) + 1; };
+
+// One Stockham stage of radix R on S lines of length M (line stride LS).
+template <typename Tc, int M, int S, int R, int Ns>
+__device__ __forceinline__ void fstage(const typename Cx<Tc>::t *__restrict__ src,
+                                       typename Cx<Tc>::t *__restrict__ dst,
+                                       const typename Cx<Tc>::t *__restrict__ roots) {
+    typedef typename Cx<Tc>::t T2;
+    constexpr int LS = LineStride<M>::value;
+    constexpr int MR = M / R;
+    constexpr int stride = M / (Ns * R);
+    for (int t = threadIdx.x; t < S * MR; t += blockDim.x) {
+        const int s = t / MR;
+        const int j = t - s * MR;
+        const int k = j % Ns;
+        const T2 *x = src + s * LS;
+        T2 *y = dst + s * LS;
+        T2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = x[PAD(j + r * MR)];
+        if (Ns > 1 && k > 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const T2 w = roots[k * r * stride];
+                const T2 a = v[r];
+                v[r] = mk2<T2>(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+            }
+        }
+        Dft<Tc, R>::run(v);
+        const int idxD = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) y[PAD(idxD + r * Ns)] = v[r];
+    }
+}
+
+template <typename Tc, int M, int S, int Ns>
+__device__ __forceinline__ void fstages(typename Cx<Tc>::t *&src, typename Cx<Tc>::t *&dst,
+                                        const typename Cx<Tc>::t *roots) {}
+
+template <typename Tc, int M, int S, int Ns, int R, int... Rest>
+__device__ __forceinline__ void fstages(typename Cx<Tc>::t *&src, typename Cx<Tc>::t *&dst,
+                                        const typename Cx<Tc>::t *roots) {
+    fstage<Tc, M, S, R, Ns>(src, dst, roots);
+    __syncthreads();
+    typename Cx<Tc>::t *t = src;
+    src = dst;
+    dst = t;
+    fstages<Tc, M, S, Ns * R, Rest...>(src, dst, roots);
+}
+
+// Real element m of a line's odd extension, stored inside the padded complex layout.
+__device__ __forceinline__ int ZPAD(int m) { return 2 * PAD(m >> 1) + (m & 1); }
+
+// FP32 tiles use up to ~74 KB of shared memory, so three CTAs fit an SM; the
+// register cap keeps the third one resident.
+// One CTA's work of the transform: S whole lines (see the file comment of
+// k_dst_fast.cu).  COH: loads of data written earlier in the same launch go
+// through L2 only (the batched persistent kernel); smem_raw is the CTA's
+// dynamic shared memory; (bx, by) the tile index.
+template <typename Tc, typename Tin, typename Tout, int AXIS, int MODE, int M, int S, bool COH,
+          int... Rs>
+__device__ __forceinline__ void dst_fast_tile(const Tin *in, Tout *out, double *aux,
+                                              const typename Cx<Tc>::t *roots_g,
+                                              const typename Cx<Tc>::t *half_g, int Nx, int Ny,
+                                              int Nz, Tc scale, unsigned char *smem_raw, int bx,
+                                              int by) {
+    typedef typename Cx<Tc>::t T2;
+    constexpr int N = M - 1;
+    constexpr int LS = LineStride<M>::value;
+    constexpr int twoM = 2 * M;
+    constexpr int NT = 256;
+    constexpr int ITER = (S * N + NT - 1) / NT;  // elements per thread in load/store phases
+    const size_t lo_off = (size_t)Nx * Ny * Nz;  // lo plane of a double-float output
+    (void)lo_off;
+    T2 *roots = reinterpret_cast<T2 *>(smem_raw);
+    T2 *half = roots + M;
+    T2 *buf0 = half + (M + 1);
+    T2 *buf1 = buf0 + S * LS;
+    for (int t = threadIdx.x; t < M; t += NT) roots[t] = roots_g[t];
+    for (int t = threadIdx.x; t <= M; t += NT) half[t] = half_g[t];
+
+    Tc *z = reinterpret_cast<Tc *>(buf0);
+    for (int s = threadIdx.x; s < S; s += NT) {
+        z[s * 2 * LS + ZPAD(0)] = (Tc)0;
+        z[s * 2 * LS + ZPAD(M)] = (Tc)0;
+    }
+    size_t base;
+    int nvalid;
+    // all global loads of the tile are issued before any shared-memory store
+    Tc v[ITER];
+    if (AXIS == HS_AXIS_X) {
+        const long nrows = (long)Ny * Nz;
+        const long row0 = (long)bx * S;
+        base = (size_t)row0 * N;
+        nvalid = (int)min((long)S, nrows - row0);
+        const int nel = nvalid * N;
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) {
+            const int e = threadIdx.x + it * NT;
+            v[it] = (e < nel) ? (Tc)ldc<COH>(in + base + e) : (Tc)0;
+        }
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) {
+            const int e = threadIdx.x + it * NT;
+            if (e < S * N) {
+                const int s = e / N;
+                const int i = e - s * N;
+                z[s * 2 * LS + ZPAD(i + 1)] = v[it];
+                z[s * 2 * LS + ZPAD(twoM - 1 - i)] = -v[it];
+            }
+        }
+    } else {
+        const int p0 = bx * S;
+        base = (size_t)by * N * Nx + p0;
+        nvalid = min(S, Nx - p0);
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) {
+            const int e = threadIdx.x + it * NT;
+            const int j = e / S;
+            const int s = e - j * S;
+            v[it] = (e < S * N && s < nvalid) ? (Tc)ldc<COH>(in + base + (size_t)j * Nx + s) : (Tc)0;
+        }
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) {
+            const int e = threadIdx.x + it * NT;
+            if (e < S * N) {
+                const int j = e / S;
+                const int s = e - j * S;
+                z[s * 2 * LS + ZPAD(j + 1)] = v[it];
+                z[s * 2 * LS + ZPAD(twoM - 1 - j)] = -v[it];
+            }
+        }
+    }
+    __syncthreads();
+
+    T2 *src = buf0, *dst = buf1;
+    fstages<Tc, M, S, 1, Rs...>(src, dst, roots);
+
+    const Tc q = scale * (Tc)0.25;
+    if (AXIS == HS_AXIS_X) {
+        const int nel = nvalid * N;
+        if constexpr (MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL) {
+            // read every (hi, lo) of the tile before any store
+            float uh[ITER], ul[ITER];
+#pragma unroll
+            for (int it = 0; it < ITER; ++it) {
+                const int e = threadIdx.x + it * NT;
+                uh[it] = (e < nel) ? ldc<COH>(out + base + e) : 0.f;
+                ul[it] = (e < nel) ? ldc<COH>(out + base + e + lo_off) : 0.f;
+            }
+#pragma unroll
+            for (int it = 0; it < ITER; ++it) {
+                const int e = threadIdx.x + it * NT;
+                if (e < nel) {
+                    const int s = e / N;
+                    const int k = e - s * N + 1;
+                    const T2 Wk = src[s * LS + PAD(k)];
+                    const T2 Wm = src[s * LS + PAD(M - k)];
+                    const T2 cs = half[k];
+                    const Tc X = ((Wm.y - Wk.y) + cs.x * (Wk.x - Wm.x) + cs.y * (Wk.y + Wm.y)) * q;
+                    dfloat a;
+                    a.hi = uh[it];
+                    a.lo = ul[it];
+                    const dfloat r = df_add(a, df_of((float)X));
+                    if constexpr (MODE == HS_MODE_DF_ADD) {
+                        out[base + e] = r.hi;
+                        out[base + e + lo_off] = r.lo;
+                    } else {
+                        aux[base + e] = (double)r.hi + (double)r.lo;
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int it = 0; it < ITER; ++it) {
+                const int e = threadIdx.x + it * NT;
+                if (e < nel) {
+                    const int s = e / N;
+                    const int k = e - s * N + 1;
+                    const T2 Wk = src[s * LS + PAD(k)];
+                    const T2 Wm = src[s * LS + PAD(M - k)];
+                    const T2 cs = half[k];
+                    const Tc X = ((Wm.y - Wk.y) + cs.x * (Wk.x - Wm.x) + cs.y * (Wk.y + Wm.y)) * q;
+                    hs_emit<Tout, MODE>(out, aux, lo_off, base + e, (double)X);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) {
+            const int e = threadIdx.x + it * NT;
+            const int kk = e / S;
+            const int s = e - kk * S;
+            if (e < S * N && s < nvalid) {
+                const int k = kk + 1;
+                const T2 Wk = src[s * LS + PAD(k)];
+                const T2 Wm = src[s * LS + PAD(M - k)];
+                const T2 cs = half[k];
+                const Tc X = ((Wm.y - Wk.y) + cs.x * (Wk.x - Wm.x) + cs.y * (Wk.y + Wm.y)) * q;
+                hs_emit<Tout, MODE>(out, aux, lo_off, base + (size_t)kk * Nx + s, (double)X);
+            }
+        }
+    }
+}
+
+
+// Lines per CTA: about 4096 (FP32) or 2048 (FP64) complex points per buffer;
+// y-lines at least 16 (FP32) / 8 (FP64) so each row segment is 64 bytes; never
+// more than fits in 227 KB of shared memory.
+template <typename Tc, int M, int AXIS>
+struct Lines {
+    static constexpr int pts = (sizeof(Tc) == 4) ? 4096 : 2048;
+    static constexpr int base = (pts / M) > 0 ? (pts / M) : 1;
+    static constexpr int ymin = (sizeof(Tc) == 4) ? 16 : 8;
+    static constexpr int want = (AXIS == HS_AXIS_Y && base < ymin) ? ymin : base;
+    static constexpr int fit = (int)((227 * 1024 / (2 * sizeof(Tc)) - (2 * M + 1)) /
+                                     (2 * (M + (M >> 4) + 1)));
+    static constexpr int value = want < fit ? want : fit;
+};
+
+template <typename Tc, int M, int S>
+constexpr size_t fast_smem() {
+    return sizeof(typename Cx<Tc>::t) * ((size_t)2 * M + 1 + (size_t)2 * S * LineStride<M>::value);
+}
+
+
+// ============================================================ right-hand side
+struct RhsArgs {
+    int Nx, Ny, Nz;
+    double hz;           // h_z (the uniform h for order 6)
+    int order, equation, rhs_kind;
+    const double *coef;  // [Nz][3][4]
+    const double *c0;    // [Nz+2]
+    const double *c1;    // [Nz+2]
+    const float4 *rc;    // [Nz+2]: per-row double-float RHS weights (see rhs_tiled_df_kernel)
+    int has_faces;       // 0: every Dirichlet face is zero, so the lifting vanishes
+    DevBoundary b;
+};
+
+template <typename T>
+__device__ __forceinline__ double ld(const T *p, size_t i) {
+    return (double)__ldg(p + i);
+}
+
+template <typename T>
+__device__ double boundary_value(const RhsArgs &a, int i, int j, int l) {
+    const int Nx2 = a.Nx + 2, Ny2 = a.Ny + 2;
+    const T *p;
+    size_t idx;
+    if (l == 0 || l == a.Nz + 1) {
+        p = static_cast<const T *>(a.b.face[l == 0 ? 4 : 5]);
+        idx = (size_t)j * Nx2 + i;
+    } else if (j == 0 || j == a.Ny + 1) {
+        p = static_cast<const T *>(a.b.face[j == 0 ? 2 : 3]);
+        idx = (size_t)l * Nx2 + i;
+    } else {
+        p = static_cast<const T *>(a.b.face[i == 0 ? 0 : 1]);
+        idx = (size_t)l * Ny2 + j;
+    }
+    return p ? ld(p, idx) : 0.0;
+}
+
+// Adds a per-thread value over the CTA and atomically to *out (thread 0).
+__device__ __forceinline__ void block_sum_to(double v, double *out) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __shared__ double part[32];
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    __syncthreads();
+    if ((tid & 31) == 0) part[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += part[w];
+        atomicAdd(out, s);
+    }
+}
+
+// Subtract the boundary-node terms of row (i, j, l) (node indices, interior).
+template <typename T>
+__device__ double lift_terms(const RhsArgs &a, int i, int j, int l) {
+    double acc = 0.0;
+    const double *cf = a.coef + (size_t)(l - 1) * 12;
+    for (int dl = -1; dl <= 1; ++dl) {
+        const int ll = l + dl;
+        for (int dj = -1; dj <= 1; ++dj) {
+            const int jj = j + dj;
+            for (int di = -1; di <= 1; ++di) {
+                const int ii = i + di;
+                const bool bnd = (ll == 0 || ll == a.Nz + 1 || jj == 0 || jj == a.Ny + 1 ||
+                                  ii == 0 || ii == a.Nx + 1);
+                if (!bnd) continue;
+                const int m = (di != 0 && dj != 0) ? 0 : (di != 0 ? 1 : (dj != 0 ? 2 : 3));
+                const double c = cf[(dl + 1) * 4 + m];
+                if (c != 0.0) acc += c * boundary_value<T>(a, ii, jj, ll);
+            }
+        }
+    }
+    return acc;
+}
+
+// OUT_DF = 0: F is FP64; OUT_DF = 1: F is stored as a double-float pair (hi, lo).
+// ---------------------------------------------------------------------------
+// Tiled right-hand side for nodal f: a CTA owns a TX x TY patch of interior
+// points and marches over RZ planes in z with a ring of five f-planes in
+// shared memory (halo 2 in x and y; the second neighbours beyond a face are
+// the ghosts 2 f_0 - f_1 + h^2 (f_nn)_face, filled in at load time).  The
+// 6th-order operator is evaluated in the summed form
+//   F6 / h^2 = (67/120 - h^2 K_l / 20) f + S1 / 18 - S2 / 240 + E / 90
+//              + (h^3 K_{z,l} / 120) (f_{l+1} - f_{l-1}),
+// where S1 sums the 6 face neighbours, S2 the 6 second neighbours and E the 12
+// edge mid-points (the same operator as the expanded form above:
+// Dx+Dy+Dz = S1 - 6 f, Dx^2+Dy^2+Dz^2 = S2 - 4 S1 + 18 f,
+// DxDy+DxDz+DyDz = E - 4 S1 + 12 f).
+constexpr int RTX = 32, RTY = 8, RZ = 16;
+constexpr int RHX = RTX + 4, RHY = RTY + 4;
+
+template <typename T>
+__device__ double node_or_ghost(const RhsArgs &a, const T *f, int i, int j, int l) {
+    const int Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
+    const size_t sy = (size_t)(Nx + 2), sz = sy * (Ny + 2);
+    const double h2 = a.hz * a.hz;
+    const bool xin = i >= 0 && i <= Nx + 1, yin = j >= 0 && j <= Ny + 1, zin = l >= 0 && l <= Nz + 1;
+    if (xin && yin && zin) return ld(f, (size_t)l * sz + (size_t)j * sy + i);
+    // ghosts exist one node beyond a face, along that face's normal only
+    if (!xin && yin && zin && (i == -1 || i == Nx + 2)) {
+        const int i0 = (i == -1) ? 0 : Nx + 1, i1 = (i == -1) ? 1 : Nx;
+        const T *fnn = static_cast<const T *>(a.b.fnn[i == -1 ? 0 : 1]);
+        const size_t r = (size_t)l * sz + (size_t)j * sy;
+        return 2.0 * ld(f, r + i0) - ld(f, r + i1) +
+               (fnn ? h2 * ld(fnn, (size_t)l * (Ny + 2) + j) : 0.0);
+    }
+    if (xin && !yin && zin && (j == -1 || j == Ny + 2)) {
+        const int j0 = (j == -1) ? 0 : Ny + 1, j1 = (j == -1) ? 1 : Ny;
+        const T *fnn = static_cast<const T *>(a.b.fnn[j == -1 ? 2 : 3]);
+        const size_t r = (size_t)l * sz + i;
+        return 2.0 * ld(f, r + (size_t)j0 * sy) - ld(f, r + (size_t)j1 * sy) +
+               (fnn ? h2 * ld(fnn, (size_t)l * (Nx + 2) + i) : 0.0);
+    }
+    if (xin && yin && !zin && (l == -1 || l == Nz + 2)) {
+        const int l0 = (l == -1) ? 0 : Nz + 1, l1 = (l == -1) ? 1 : Nz;
+        const T *fnn = static_cast<const T *>(a.b.fnn[l == -1 ? 4 : 5]);
+        const size_t r = (size_t)j * sy + i;
+        return 2.0 * ld(f, (size_t)l0 * sz + r) - ld(f, (size_t)l1 * sz + r) +
+               (fnn ? h2 * ld(fnn, (size_t)j * (Nx + 2) + i) : 0.0);
+    }
+    return 0.0;  // never read by an interior point
+}
+
+// The same tiled operator in double-float arithmetic (mixed path): f enters
+// shared memory as (hi, lo) pairs (FP64 f split with integer operations,
+// FP32 f exact), the sums and products use two_sum / two_prod, and F is
+// written as its two FP32 planes.  Ghost values and the Dirichlet lifting
+// (points next to a face only) are formed in FP64 and then split.
+template <typename T>
+__device__ __forceinline__ dfloat node_df(const RhsArgs &a, const T *f, int i, int j, int l) {
+    const bool in = i >= 0 && i <= a.Nx + 1 && j >= 0 && j <= a.Ny + 1 && l >= 0 && l <= a.Nz + 1;
+    if (in) {
+        const size_t sy = (size_t)(a.Nx + 2), sz = sy * (a.Ny + 2);
+        return df_of(__ldg(f + (size_t)l * sz + (size_t)j * sy + i));
+    }
+    return df_split_bits(node_or_ghost<T>(a, f, i, j, l));
+}
+
+__device__ __forceinline__ dfloat dsum(dfloat a, dfloat b) { return df_add(a, b); }
+
+// Sum of double-float terms without renormalising after each one: the hi parts
+// go through two_sum (exact), their errors and the lo parts are added in FP32.
+struct LeanSum {
+    float s, e;
+    __device__ __forceinline__ LeanSum(dfloat a) : s(a.hi), e(a.lo) {}
+    __device__ __forceinline__ void add(dfloat a) {
+        float t, err;
+        df_two_sum(s, a.hi, t, err);
+        s = t;
+        e += err + a.lo;
+    }
+    __device__ __forceinline__ dfloat get() const {
+        dfloat r;
+        df_fast_two_sum(s, e, r.hi, r.lo);
+        return r;
+    }
+};
+
+// One CTA's work of the double-float right-hand side: a RTX x RTY patch and RZ
+// planes; smem holds 2 x 5 planes of (RTY + 4) x (RTX + 4) floats.
+template <typename T>
+__device__ __forceinline__ void rhs_df_tile(const RhsArgs &a, const T *__restrict__ f,
+                                            float *__restrict__ Fo, double *f2out,
+                                            unsigned char *smem, int bx, int by, int bz) {
+    float(*ph)[RHY][RHX] = reinterpret_cast<float(*)[RHY][RHX]>(smem);
+    float(*pq)[RHY][RHX] = ph + 5;
+    constexpr int NT = RTX * RTY;
+    constexpr int PER = (RHX * RHY + NT - 1) / NT;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int tx = tid & (RTX - 1), ty = tid / RTX;
+    const int i0 = 1 + bx * RTX, j0 = 1 + by * RTY;
+    const int lbeg = 1 + bz * RZ;
+    const int lend = min(lbeg + RZ - 1, a.Nz);
+    const size_t n = (size_t)a.Nx * a.Ny * a.Nz;
+    const dfloat H2 = df_from_double(a.hz * a.hz);
+    const dfloat C18 = df_from_double(1.0 / 18.0), C240 = df_from_double(-1.0 / 240.0);
+    const dfloat C90 = df_from_double(1.0 / 90.0), C12 = df_from_double(1.0 / 12.0);
+    const dfloat HALF = df_of(0.5f);
+
+    dfloat reg[PER];
+    auto fetch = [&](int l) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * NT;
+            const int ey = e / RHX, ex = e - ey * RHX;
+            reg[k] = (e < RHX * RHY) ? node_df<T>(a, f, i0 - 2 + ex, j0 - 2 + ey, l)
+                                     : df_of(0.f);
+        }
+    };
+    auto store = [&](int l) {
+        const int slot = (l + 10) % 5;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * NT;
+            if (e < RHX * RHY) {
+                const int ey = e / RHX, ex = e - ey * RHX;
+                ph[slot][ey][ex] = reg[k].hi;
+                pq[slot][ey][ex] = reg[k].lo;
+            }
+        }
+    };
+    for (int l = lbeg - 2; l <= lbeg + 1; ++l) {
+        fetch(l);
+        store(l);
+    }
+    fetch(lbeg + 2);
+    float fsq = 0.f;
+    const int i = i0 + tx, j = j0 + ty;
+    const int cx = tx + 2, cy = ty + 2;
+    for (int l = lbeg; l <= lend; ++l) {
+        store(l + 2);               // slot of plane l - 3, last read in the previous step
+        __syncthreads();
+        if (l + 3 <= lend + 2) fetch(l + 3);   // in flight during this plane's arithmetic
+        if (i <= a.Nx && j <= a.Ny) {
+            const int sm2 = (l + 8) % 5, sm = (l + 9) % 5, s0 = (l + 10) % 5, sp = (l + 11) % 5,
+                      sp2 = (l + 12) % 5;
+#define HS_G(S, Y, X) dfloat{ph[S][Y][X], pq[S][Y][X]}
+            const dfloat fc = HS_G(s0, cy, cx);
+            const dfloat fzm = HS_G(sm, cy, cx), fzp = HS_G(sp, cy, cx);
+            LeanSum a1(HS_G(s0, cy, cx - 1));
+            a1.add(HS_G(s0, cy, cx + 1));
+            a1.add(HS_G(s0, cy - 1, cx));
+            a1.add(HS_G(s0, cy + 1, cx));
+            a1.add(fzm);
+            a1.add(fzp);
+            const dfloat S1 = a1.get();
+            dfloat val;
+            const float4 w = a.rc[l];
+            if (a.equation == HS_CONVDIFF) {
+                const dfloat g = dfloat{w.z, w.w};
+                const dfloat dz = df_add_accurate(fzp, df_neg(fzm));
+                val = df_mul(H2, dsum(dsum(df_mul(HALF, fc), df_mul(C12, S1)), df_mul(g, dz)));
+            } else if (a.order == 2) {
+                val = df_mul(H2, fc);
+            } else if (a.order == 4) {
+                val = df_mul(H2, dsum(df_mul(HALF, fc), df_mul(C12, S1)));
+            } else {
+                LeanSum a2(HS_G(s0, cy, cx - 2));
+                a2.add(HS_G(s0, cy, cx + 2));
+                a2.add(HS_G(s0, cy - 2, cx));
+                a2.add(HS_G(s0, cy + 2, cx));
+                a2.add(HS_G(sm2, cy, cx));
+                a2.add(HS_G(sp2, cy, cx));
+                const dfloat S2 = a2.get();
+                LeanSum a3(HS_G(s0, cy - 1, cx - 1));
+                a3.add(HS_G(s0, cy - 1, cx + 1));
+                a3.add(HS_G(s0, cy + 1, cx - 1));
+                a3.add(HS_G(s0, cy + 1, cx + 1));
+                a3.add(HS_G(sm, cy, cx - 1));
+                a3.add(HS_G(sm, cy, cx + 1));
+                a3.add(HS_G(sm, cy - 1, cx));
+                a3.add(HS_G(sm, cy + 1, cx));
+                a3.add(HS_G(sp, cy, cx - 1));
+                a3.add(HS_G(sp, cy, cx + 1));
+                a3.add(HS_G(sp, cy - 1, cx));
+                a3.add(HS_G(sp, cy + 1, cx));
+                const dfloat E = a3.get();
+                const dfloat alpha = dfloat{w.x, w.y};
+                const dfloat eps = dfloat{w.z, w.w};
+                const dfloat dz = df_add_accurate(fzp, df_neg(fzm));
+                dfloat F6 = df_mul(alpha, fc);
+                F6 = dsum(F6, df_mul(C18, S1));
+                F6 = dsum(F6, df_mul(C240, S2));
+                F6 = dsum(F6, df_mul(C90, E));
+                F6 = dsum(F6, df_mul(eps, dz));
+                val = df_mul(H2, F6);
+            }
+#undef HS_G
+            const bool near = (i == 1 || i == a.Nx || j == 1 || j == a.Ny || l == 1 || l == a.Nz);
+            if (a.has_faces && near)
+                val = df_add_accurate(val, df_neg(df_split_bits(lift_terms<T>(a, i, j, l))));
+            const size_t out = ((size_t)(l - 1) * a.Ny + (j - 1)) * a.Nx + (i - 1);
+            Fo[out] = val.hi;
+            Fo[out + n] = val.lo;
+            fsq = fmaf(val.hi, val.hi, fsq);
+        }
+        __syncthreads();
+    }
+    if (f2out) block_sum_to((double)fsq, f2out);
+}
+
+
+// =================================================================== residual
+// z-marching double-float residual.  A CTA owns a RTX x RTY patch and RZ
+// planes; a ring of three U-planes (hi and lo, halo 1) sits in shared memory.
+// For every plane each thread forms the in-plane sums of its column once --
+// corners C, x-neighbours X, y-neighbours Y (exact pair sums of the FP32 hi
+// parts, plain FP32 sums of the lo parts) -- and keeps the last three planes'
+// sums in registers, so output row l costs 12 products
+//     A U_l = sum_nu a_nu C_nu + b_nu X_nu + c_nu Y_nu + d_nu U_nu,
+// accumulated as an unnormalised pair (two_prod into two_sum; cross terms and
+// lo parts in FP32), and one accurate pair subtraction F - A U.
+struct PlaneSums {
+    float C, Ce, X, Xe, Y, Ye, U;   // hi sums with their two_sum errors; U = centre hi
+    float L;                        // lo parts: C_lo etc. folded per coefficient below
+    float Clo, Xlo, Ylo, Ulo;
+};
+
+__device__ __forceinline__ void acc_term(float &S, float &E, float2 k, float v, float ve,
+                                         float vlo) {
+    // S + E += (k.x + k.y) * (v + ve + vlo)
+    const float p = k.x * v;
+    const float pe = fmaf(k.x, v, -p);
+    float s, t;
+    df_two_sum(S, p, s, t);
+    S = s;
+    E += t + pe + fmaf(k.x, ve + vlo, k.y * v);
+}
+
+constexpr int QTX = 32, QTY = 8, QZ = 16;
+constexpr int QHX = QTX + 2, QHY = QTY + 2;
+
+// One CTA's work of the double-float residual: a QTX x QTY patch and QZ planes;
+// smem holds 2 x 2 planes of (QTY + 2) x (QTX + 2) floats.
+template <bool COH>
+__device__ __forceinline__ void residual_tile(int Nx, int Ny, int Nz, const float2 *__restrict__ coef,
+                                              const float *__restrict__ F,
+                                              const float *__restrict__ U, float *__restrict__ r,
+                                              double *r2out, unsigned char *smem, int bx, int by,
+                                              int bz) {
+    // two plane slots: the plane whose sums are being formed and the next one,
+    // whose global loads are issued into registers before the current plane's
+    // arithmetic (so their latency overlaps it)
+    float(*uh)[QHY][QHX] = reinterpret_cast<float(*)[QHY][QHX]>(smem);
+    float(*ul)[QHY][QHX] = uh + 2;
+    constexpr int NT = QTX * QTY;
+    constexpr int PER = (QHX * QHY + NT - 1) / NT;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int tx = tid & (QTX - 1), ty = tid / QTX;
+    const int i0 = bx * QTX, j0 = by * QTY;  // 0-based interior indices
+    const int lbeg = bz * QZ;
+    const int lend = min(lbeg + QZ, Nz);                      // exclusive
+    const size_t plane = (size_t)Nx * Ny;
+    const size_t n = plane * Nz;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = i < Nx && j < Ny;
+
+    float rh[PER], rl[PER];
+    auto fetch = [&](int l) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * NT;
+            const int ey = e / QHX, ex = e - ey * QHX;
+            const int ii = i0 - 1 + ex, jj = j0 - 1 + ey;
+            rh[k] = 0.f;
+            rl[k] = 0.f;
+            if (e < QHX * QHY && l >= 0 && l < Nz && ii >= 0 && ii < Nx && jj >= 0 && jj < Ny) {
+                const size_t o = (size_t)l * plane + (size_t)jj * Nx + ii;
+                rh[k] = ldc<COH>(U + o);
+                rl[k] = ldc<COH>(U + n + o);
+            }
+        }
+    };
+    auto store = [&](int l) {
+        const int slot = (l + 2) & 1;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * NT;
+            if (e < QHX * QHY) {
+                const int ey = e / QHX, ex = e - ey * QHX;
+                uh[slot][ey][ex] = rh[k];
+                ul[slot][ey][ex] = rl[k];
+            }
+        }
+    };
+    auto sums = [&](int l, PlaneSums &ps) {
+        const int sl = (l + 2) & 1;
+        const int cx = tx + 1, cy = ty + 1;
+        float s, e, s2, e2;
+        df_two_sum(uh[sl][cy - 1][cx - 1], uh[sl][cy - 1][cx + 1], s, e);
+        df_two_sum(uh[sl][cy + 1][cx - 1], uh[sl][cy + 1][cx + 1], s2, e2);
+        float s3, e3;
+        df_two_sum(s, s2, s3, e3);
+        ps.C = s3;
+        ps.Ce = e3 + (e + e2);
+        df_two_sum(uh[sl][cy][cx - 1], uh[sl][cy][cx + 1], ps.X, ps.Xe);
+        df_two_sum(uh[sl][cy - 1][cx], uh[sl][cy + 1][cx], ps.Y, ps.Ye);
+        ps.U = uh[sl][cy][cx];
+        ps.Clo = (ul[sl][cy - 1][cx - 1] + ul[sl][cy - 1][cx + 1]) +
+                 (ul[sl][cy + 1][cx - 1] + ul[sl][cy + 1][cx + 1]);
+        ps.Xlo = ul[sl][cy][cx - 1] + ul[sl][cy][cx + 1];
+        ps.Ylo = ul[sl][cy - 1][cx] + ul[sl][cy + 1][cx];
+        ps.Ulo = ul[sl][cy][cx];
+    };
+
+    PlaneSums pm, p0, pp;
+    float rsq = 0.f;
+    fetch(lbeg - 1);
+    store(lbeg - 1);
+    __syncthreads();
+    sums(lbeg - 1, pm);
+    fetch(lbeg);
+    __syncthreads();
+    store(lbeg);
+    __syncthreads();
+    sums(lbeg, p0);
+    fetch(lbeg + 1);
+    for (int l = lbeg; l < lend; ++l) {
+        __syncthreads();          // slot of plane l + 1 (= that of l - 1) is free
+        store(l + 1);
+        __syncthreads();
+        fetch(l + 2);             // in flight during the arithmetic below
+        sums(l + 1, pp);
+        if (active) {
+            const float2 *cf = coef + (size_t)l * 12;
+            float S = 0.f, E = 0.f;
+            const PlaneSums *q[3] = {&pm, &p0, &pp};
+#pragma unroll
+            for (int nu = 0; nu < 3; ++nu) {
+                const int ll = l + nu - 1;
+                if (ll < 0 || ll >= Nz) continue;
+                const PlaneSums &ps = *q[nu];
+                acc_term(S, E, cf[nu * 4 + 0], ps.C, ps.Ce, ps.Clo);
+                acc_term(S, E, cf[nu * 4 + 1], ps.X, ps.Xe, ps.Xlo);
+                acc_term(S, E, cf[nu * 4 + 2], ps.Y, ps.Ye, ps.Ylo);
+                acc_term(S, E, cf[nu * 4 + 3], ps.U, 0.f, ps.Ulo);
+            }
+            const size_t o = (size_t)l * plane + (size_t)j * Nx + i;
+            dfloat au;
+            df_fast_two_sum(S, E, au.hi, au.lo);
+            const dfloat res = df_add_accurate(dfloat{ldc<COH>(F + o), ldc<COH>(F + o + n)}, df_neg(au));
+            const float rv = res.hi + res.lo;
+            r[o] = rv;
+            rsq = fmaf(rv, rv, rsq);
+        }
+        pm = p0;
+        p0 = pp;
+    }
+    if (r2out) block_sum_to((double)rsq, r2out);
+}
+
+
+// ==================================================================== z-solves
+// The sweeps walk the column CH planes at a time: all loads of a chunk are
+// issued before its dependent chain and its stores (the in-place stores would
+// otherwise keep the next plane's load from starting early), so each thread has
+// 2-3 x CH loads in flight.
+constexpr int CH = 16;
+
+// One z-solve with cached factors.  Td: data type (in place); Tf: factor type;
+// Ts: type of the forward-sweep values (kept in `scratch` when it is not null,
+// else in `data`); Ta: arithmetic type.
+template <typename Td, typename Tf, typename Ta, bool COH = false>
+__device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, Td *data,
+                                              Ta *scratch, const Tf *cpr, const Tf *alpha,
+                                              const Tf *beta) {
+    Ta d = (Ta)0;
+    int l = 0;
+    for (; l + CH <= Nz; l += CH) {
+        Ta r[CH], a[CH], b[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            const size_t o = (size_t)(l + k) * plane + idx;
+            r[k] = (Ta)ldc<COH>(data + o);
+            a[k] = (Ta)alpha[o];
+            b[k] = (Ta)beta[o];
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            d = a[k] * r[k] - b[k] * d;
+            r[k] = d;
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            const size_t o = (size_t)(l + k) * plane + idx;
+            if (scratch)
+                scratch[o] = r[k];
+            else
+                data[o] = (Td)r[k];
+        }
+    }
+    for (; l < Nz; ++l) {
+        const size_t o = (size_t)l * plane + idx;
+        d = (Ta)alpha[o] * (Ta)ldc<COH>(data + o) - (Ta)beta[o] * d;
+        if (scratch)
+            scratch[o] = d;
+        else
+            data[o] = (Td)d;
+    }
+    Ta w = d;
+    data[(size_t)(Nz - 1) * plane + idx] = (Td)w;
+    int top = Nz - 2;  // next plane to solve, going down
+    for (; top - CH + 1 >= 0; top -= CH) {
+        Ta dv[CH], c[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            const size_t o = (size_t)(top - k) * plane + idx;
+            dv[k] = scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o);
+            c[k] = (Ta)cpr[o];
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            w = dv[k] - c[k] * w;
+            dv[k] = w;
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k) data[(size_t)(top - k) * plane + idx] = (Td)dv[k];
+    }
+    for (; top >= 0; --top) {
+        const size_t o = (size_t)top * plane + idx;
+        const Ta dd = scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o);
+        w = dd - (Ta)cpr[o] * w;
+        data[o] = (Td)w;
+    }
+}
+
+}  // namespace hs_tiles

@@ -15,9 +15,11 @@
 // w_l = d'_l - c'_l w_{l+1} (backward): three FP64 operations per unknown.
 // One thread owns one (p, q) column; threads of a warp own consecutive p, so
 // every plane access is coalesced.
-#include "hs_internal.cuh"
+#include "hs_tiles.cuh"
 
 namespace {
+
+using namespace hs_tiles;
 
 __device__ __forceinline__ void atomic_min_pos(double *addr, double v) {
     atomicMin(reinterpret_cast<unsigned long long *>(addr),
@@ -80,79 +82,6 @@ __global__ void __launch_bounds__(256) factor_kernel(int Nx, int Ny, int Nz,
     if ((threadIdx.x & 31) == 0) {
         atomic_min_pos(red + 0, minpiv);
         atomic_max_pos(red + 1, maxdiag);
-    }
-}
-
-// The sweeps walk the column CH planes at a time: all loads of a chunk are
-// issued before its dependent chain and its stores (the in-place stores would
-// otherwise keep the next plane's load from starting early), so each thread has
-// 2-3 x CH loads in flight.
-constexpr int CH = 16;
-
-// One z-solve with cached factors.  Td: data type (in place); Tf: factor type;
-// Ts: type of the forward-sweep values (kept in `scratch` when it is not null,
-// else in `data`); Ta: arithmetic type.
-template <typename Td, typename Tf, typename Ta>
-__device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, Td *data,
-                                              Ta *scratch, const Tf *cpr, const Tf *alpha,
-                                              const Tf *beta) {
-    Ta d = (Ta)0;
-    int l = 0;
-    for (; l + CH <= Nz; l += CH) {
-        Ta r[CH], a[CH], b[CH];
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            const size_t o = (size_t)(l + k) * plane + idx;
-            r[k] = (Ta)data[o];
-            a[k] = (Ta)alpha[o];
-            b[k] = (Ta)beta[o];
-        }
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            d = a[k] * r[k] - b[k] * d;
-            r[k] = d;
-        }
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            const size_t o = (size_t)(l + k) * plane + idx;
-            if (scratch)
-                scratch[o] = r[k];
-            else
-                data[o] = (Td)r[k];
-        }
-    }
-    for (; l < Nz; ++l) {
-        const size_t o = (size_t)l * plane + idx;
-        d = (Ta)alpha[o] * (Ta)data[o] - (Ta)beta[o] * d;
-        if (scratch)
-            scratch[o] = d;
-        else
-            data[o] = (Td)d;
-    }
-    Ta w = d;
-    data[(size_t)(Nz - 1) * plane + idx] = (Td)w;
-    int top = Nz - 2;  // next plane to solve, going down
-    for (; top - CH + 1 >= 0; top -= CH) {
-        Ta dv[CH], c[CH];
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            const size_t o = (size_t)(top - k) * plane + idx;
-            dv[k] = scratch ? scratch[o] : (Ta)data[o];
-            c[k] = (Ta)cpr[o];
-        }
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            w = dv[k] - c[k] * w;
-            dv[k] = w;
-        }
-#pragma unroll
-        for (int k = 0; k < CH; ++k) data[(size_t)(top - k) * plane + idx] = (Td)dv[k];
-    }
-    for (; top >= 0; --top) {
-        const size_t o = (size_t)top * plane + idx;
-        const Ta dd = scratch ? scratch[o] : (Ta)data[o];
-        w = dd - (Ta)cpr[o] * w;
-        data[o] = (Td)w;
     }
 }
 
