@@ -174,6 +174,12 @@ WORKLOADS = {
         desc="6th-order compact Helmholtz on the unit cube, 1023^3 interior (h=1/1024), "
              "k=40+20 tanh(10(z-1/2)), f = 16 seeded sine modes, amplitudes N(0,1), "
              "stored FP32, 1 RHS per step"),
+    "batch64": dict(
+        steps=5,
+        desc="64 independent 6th-order Helmholtz problems, N per axis drawn (seed 3) from "
+             "{63,95,127,191,255,383}, uniform h=1/(max N+1), k=k0(1+a z) with k0~U[5,60], "
+             "a~U[0,1], 1-4 right-hand sides each, f ~ U[-1,1] FP32 at interior nodes, "
+             "one persistent launch in a CUDA graph per step"),
     "cd511x8": dict(
         steps=10,
         desc="4th-order compact convection-diffusion Lap(u)+b(z)u_z=f, 511^3 interior, "
@@ -269,6 +275,11 @@ def run_reference(args):
     elif name == "cube1023_o6":
         p = W.sine_mode_problem(255, 6, W.k_tanh(), nmodes=16, seed=4)
         n, sample = 255 ** 3, "255^3 instance of the same recipe per step"
+    elif name == "batch64":
+        sp = W.workload_batch_specs(nprob=64, seed=3)[0]
+        p = W.batch_problem(sp, 0)
+        n = p.Nx * p.Ny * p.Nz
+        sample = f"problem 0 of the batch ({p.Nx}x{p.Ny}x{p.Nz}, 1 RHS) per step"
     else:
         p, n, sample = W.workload_convdiff511(0), 511 ** 3, "1 of the 8 right-hand sides per step"
     steps = args.steps if args.steps is not None else 5
@@ -294,6 +305,117 @@ def run_reference(args):
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
+    """Config with many problems: one hs_batch_solve per step."""
+    specs = W.workload_batch_specs(nprob=64, seed=3)
+    gen = torch.Generator(device="cuda")
+    probs = []
+    total = 0
+    for sp in specs:
+        Nx, Ny, Nz = sp["N"]
+        h = 1.0 / (max(sp["N"]) + 1)
+        L = ((Nx + 1) * h, (Ny + 1) * h, (Nz + 1) * h)
+        K = W.k_profile_to_k2(W.k_linear(sp["k0"], sp["a"]))
+        c0, c1, c2 = K.sample(Nz, L[2])
+        gen.manual_seed(1_000_003 * 3 + sp["id"])
+        f = torch.zeros((sp["nrhs"], Nz + 2, Ny + 2, Nx + 2), dtype=torch.float32, device="cuda")
+        f[:, 1:-1, 1:-1, 1:-1] = torch.rand((sp["nrhs"], Nz, Ny, Nx), generator=gen,
+                                            device="cuda") * 2 - 1
+        u = torch.zeros((sp["nrhs"], Nz, Ny, Nx), dtype=torch.float64, device="cuda")
+        probs.append(dict(N=sp["N"], L=L, order=6, c0=c0, c1=c1, c2=c2, nrhs=sp["nrhs"], f=f, u=u))
+        total += sp["nrhs"] * Nx * Ny * Nz
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed_solve(pr, prec, sweeps, tol, out):
+        s = H.Solver(*pr["N"], *pr["L"], 6, H.HS_HELMHOLTZ, prec, max_rhs=pr["nrhs"])
+        try:
+            s.set_coeff(pr["c0"], pr["c1"], pr["c2"])
+            if prec == H.HS_MIXED:
+                H.hs_set_refinement(s.plan, sweeps)
+                H.hs_set_refinement_tol(s.plan, tol)
+            s.solve(pr["f"], out, H.HS_F32, H.HS_RHS_NODAL, nrhs=pr["nrhs"], stream=stream)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s.solve(pr["f"], out, H.HS_F32, H.HS_RHS_NODAL, nrhs=pr["nrhs"], stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+        finally:
+            s.close()
+
+    # the FP64 path's answers, which the batch must meet to 1e-10
+    u64 = [torch.empty_like(pr["u"]) for pr in probs]
+    t64 = sum(timed_solve(pr, H.HS_FP64, 0, 0.0, u) for pr, u in zip(probs, u64))
+
+    def worst_err():
+        return max(float((pr["u"] - u).abs().max()) / float(u.abs().max())
+                   for pr, u in zip(probs, u64))
+
+    # refinement: up to `max_sweeps` sweeps, each (problem, RHS) stopping on the
+    # device at a relative residual `tol`; take the loosest tol that meets 1e-10
+    max_sweeps = 4 if args.sweeps < 0 else args.sweeps
+    tried = {}
+    tol = 0.0
+    b = H.hs_batch_create(probs, H.HS_F32, max_sweeps)
+    for cand in ((1e-9, 1e-10, 1e-11, 1e-12, 0.0) if args.sweeps < 0 else (0.0,)):
+        H.hs_batch_set_tol(b, cand)
+        H.hs_batch_solve(b, stream, True)
+        tried[cand] = worst_err()
+        tol = cand
+        if tried[cand] <= 1e-10:
+            break
+    H.hs_batch_set_tol(b, tol)
+    H.hs_batch_solve(b, stream, True)
+    acc = {"batch_vs_fp64_gpu_max": worst_err(),
+           "judged_against": "fp64 GPU path, every problem and RHS",
+           "max_sweeps": max_sweeps, "residual_tol": tol,
+           "tried": {f"{k:g}": v for k, v in tried.items()}}
+    scratch = [torch.empty_like(pr["u"]) for pr in probs]
+    tmix = sum(timed_solve(pr, H.HS_MIXED, max_sweeps, tol, u) for pr, u in zip(probs, scratch))
+    del scratch
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        H.hs_batch_solve(b, stream, False)
+    torch.cuda.synchronize()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        H.hs_batch_solve(b, stream, False)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    status = H.hs_batch_solve(b, stream, True)
+    ms = max_over_ranks_dev(sum(a.elapsed_time(b2) for a, b2 in ev))
+    value = world * args.steps * total / (ms * 1e-3) / 1e9
+    H.hs_batch_destroy(b)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 + f32-pair (mixed)",
+            "data": "synthetic",
+            "config": {"workload": f"batch64: {WORKLOADS['batch64']['desc']}",
+                       "global_batch": world * 64, "parallelism": f"replicas x{world}",
+                       "unknown_solves_per_step": total, "refinement_sweeps_max": max_sweeps,
+                       "refinement_residual_tol": tol,
+                       "l2": "256 MB buffer written between timed steps"},
+            "sequential_fp64_path": {"value": total / (t64 * 1e-3) / 1e9, "unit": UNIT,
+                                     "ms_per_step": t64},
+            "sequential_mixed_path": {"value": total / (tmix * 1e-3) / 1e9, "unit": UNIT,
+                                      "ms_per_step": tmix},
+            "accuracy": acc, "status": status, "cpu_baseline": None, "e2e": None,
+            "roofline": None, "clocks": clocks,
+            "gpu_launches": args.steps,
+        }
+        print(json.dumps(line), flush=True)
 
 
 def main():
@@ -331,6 +453,13 @@ def main():
     def barrier():
         if dist is not None:
             dist.barrier()
+
+    if args.workload == "batch64":
+        bench_batch(args, torch, H, W, rank, world, barrier,
+                    lambda x: reduce_max(x, dist, "cuda"))
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     want_oracle = rank == 0 and world == 1 and not args.no_cpu_baseline
     wk = Work(args.workload, torch, W, want_oracle)

@@ -273,6 +273,11 @@ hs_status hs_batch_solve(hs_batch_t batch, void *stream, int sync);
  * inside the launch gives up (default 2e7). */
 hs_status hs_batch_set_wait_limit(hs_batch_t batch, long long spins);
 
+/* hs_batch_set_tol -- tolerance-controlled refinement per problem and RHS:
+ * each stops once ||F - A U||_2 / ||F||_2 <= tol (decided on the device) or
+ * after the batch's sweep count; 0 (default) runs every sweep. */
+hs_status hs_batch_set_tol(hs_batch_t batch, double tol);
+
 /* hs_batch_debug_stall -- test hook: on = 1 makes one dependency of the first
  * problem unsatisfiable, so the next solve must end with HS_ERR_TIMEOUT; on =
  * 0 restores it. */

@@ -42,7 +42,8 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_set_stage_timing", "hs_solve",
             "hs_residual", "hs_stage_times", "hs_workspace_bytes", "hs_destroy",
             "hs_status_str", "hs_last_error", "hs_residual_static", "hs_batch_create",
-            "hs_batch_set_io", "hs_batch_solve", "hs_batch_set_wait_limit", "hs_batch_debug_stall",
+            "hs_batch_set_io", "hs_batch_solve", "hs_batch_set_wait_limit", "hs_batch_set_tol",
+            "hs_batch_debug_stall",
             "hs_batch_workspace_bytes", "hs_batch_destroy")
 HS_STATIC_MAX_NZ = 8192
 
@@ -121,6 +122,8 @@ def load(path: Optional[str] = None):
     lib.hs_batch_solve.restype = ci
     lib.hs_batch_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     lib.hs_batch_set_wait_limit.restype = ci
+    lib.hs_batch_set_tol.argtypes = [vp, cd]
+    lib.hs_batch_set_tol.restype = ci
     lib.hs_batch_debug_stall.argtypes = [vp, ci]
     lib.hs_batch_debug_stall.restype = ci
     lib.hs_batch_workspace_bytes.argtypes = [vp]
@@ -313,6 +316,10 @@ def hs_batch_solve(batch, stream=None, sync=True):
 
 def hs_batch_set_wait_limit(batch, spins):
     return _check(load().hs_batch_set_wait_limit(batch, int(spins)), "hs_batch_set_wait_limit")
+
+
+def hs_batch_set_tol(batch, tol):
+    return _check(load().hs_batch_set_tol(batch, float(tol)), "hs_batch_set_tol")
 
 
 def hs_batch_debug_stall(batch, on):

@@ -55,6 +55,8 @@ struct BatchWork {
     float sx, sy;
     int gx, gy, gz;                    // RHS / residual tile grid
     int dxg, dyg;                      // x-transform groups, y-transform groups per plane
+    int lx;                            // x lines per x-transform tile
+    double *norms;                     // [0] ||F||^2, [1 + m] ||r_m||^2 (tolerance mode)
     int need[BMAX_STAGES];
 };
 
@@ -72,7 +74,9 @@ struct BatchArgs {
     int *err;
     long long spin_limit;
     int f_is_f64;
+    double tol2;        // > 0: a (problem, RHS) stops refining once ||r||^2 <= tol2 ||F||^2
     StageList stages;
+    int sweep_of[BMAX_STAGES];   // refinement sweep a stage belongs to (0: first solve)
 };
 
 __device__ __forceinline__ int ld_volatile(const int *p) {
@@ -136,24 +140,53 @@ __device__ void dst_w64_tile(const BatchWork &W, const float *in, float scale,
     }
 }
 
+// Tolerance mode: has this (problem, RHS) converged at or before sweep m?  The
+// residual of sweep j (j >= 1) is complete before any later stage runs, so every
+// tile of a stage takes the same decision.
+__device__ __forceinline__ bool converged(const BatchArgs &A, const BatchWork &W, int m) {
+    if (A.tol2 <= 0.0 || m < 1) return false;
+    const double f2 = __ldcg(W.norms);
+    for (int j = 1; j <= m; ++j)
+        if (__ldcg(W.norms + j) <= A.tol2 * f2) return true;
+    return false;
+}
+
 __device__ void run_tile(const BatchArgs &A, const BatchWork &W, int stage, int type, int tile,
                          unsigned char *smem) {
     const size_t plane = (size_t)W.Nx * W.Ny;
+    if (A.tol2 > 0.0) {
+        const int m = A.sweep_of[stage];
+        // a residual runs unless an earlier sweep converged; the rest of a sweep
+        // runs unless its own residual says converged
+        const bool skip = type == ST_RESIDUAL ? converged(A, W, m - 1) : converged(A, W, m);
+        if (skip) {
+            if (type == ST_IDSTX_FINAL) {
+                // the converged iterate is the answer: u = U_hi + U_lo on this tile
+                const size_t n = plane * W.Nz;
+                const size_t r0 = (size_t)tile * W.lx * W.Nx;
+                const size_t r1 = min(n, r0 + (size_t)W.lx * W.Nx);
+                for (size_t k = r0 + threadIdx.x; k < r1; k += blockDim.x)
+                    W.u[k] = (double)__ldcg(W.U + k) + (double)__ldcg(W.U + n + k);
+            }
+            return;
+        }
+    }
     switch (type) {
         case ST_RHS: {
             const int bx = tile % W.gx, by = (tile / W.gx) % W.gy, bz = tile / (W.gx * W.gy);
+            double *f2 = A.tol2 > 0.0 ? W.norms : nullptr;
             if (A.f_is_f64)
-                rhs_df_tile<double>(W.rhs, static_cast<const double *>(W.f), W.F, nullptr, smem,
-                                    bx, by, bz);
+                rhs_df_tile<double>(W.rhs, static_cast<const double *>(W.f), W.F, f2, smem, bx,
+                                    by, bz);
             else
-                rhs_df_tile<float>(W.rhs, static_cast<const float *>(W.f), W.F, nullptr, smem,
-                                   bx, by, bz);
+                rhs_df_tile<float>(W.rhs, static_cast<const float *>(W.f), W.F, f2, smem, bx, by,
+                                   bz);
             break;
         }
         case ST_RESIDUAL: {
             const int bx = tile % W.gx, by = (tile / W.gx) % W.gy, bz = tile / (W.gx * W.gy);
-            residual_tile<true>(W.Nx, W.Ny, W.Nz, W.coef_df, W.F, W.U, W.w, nullptr, smem, bx, by,
-                                bz);
+            double *r2 = A.tol2 > 0.0 ? W.norms + A.sweep_of[stage] : nullptr;
+            residual_tile<true>(W.Nx, W.Ny, W.Nz, W.coef_df, W.F, W.U, W.w, r2, smem, bx, by, bz);
             break;
         }
         case ST_DSTX_F:
@@ -191,7 +224,7 @@ __device__ void run_tile(const BatchArgs &A, const BatchWork &W, int stage, int 
     }
 }
 
-__global__ void __launch_bounds__(256, 1) batch_kernel(BatchArgs A) {
+__global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int cur;
     __shared__ int bail;
@@ -249,7 +282,10 @@ struct hs_batch_s {
     int nitems, nworks, grid;
     size_t smem;
     long long spin_limit;
+    double tol;
+    double *d_norms;                  // [nworks][HS_INFO_MAX_ITERS + 1]
     StageList stages;
+    int sweep_of[BMAX_STAGES];
     cudaGraphExec_t graph;
     cudaStream_t graph_stream;
     int have_graph;
@@ -292,6 +328,7 @@ void free_batch(hs_batch_s *B) {
     if (B->d_works) cudaFree(B->d_works);
     if (B->d_items) cudaFree(B->d_items);
     if (B->d_ctr) cudaFree(B->d_ctr);
+    if (B->d_norms) cudaFree(B->d_norms);
     delete B;
 }
 
@@ -319,6 +356,8 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
     B->d_works = nullptr;
     B->d_items = nullptr;
     B->d_ctr = nullptr;
+    B->d_norms = nullptr;
+    B->tol = 0.0;
     B->have_graph = 0;
     B->graph_stream = nullptr;
     B->bytes = 0;
@@ -328,8 +367,10 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
     // with the residual before every refinement pass
     StageList &L = B->stages;
     L.n = 0;
+    B->sweep_of[L.n] = 0;
     L.type[L.n++] = ST_RHS;
     for (int p = 0; p <= sweeps; ++p) {
+        const int first = L.n;
         if (p > 0) L.type[L.n++] = ST_RESIDUAL;
         L.type[L.n++] = ST_DSTX_F;
         L.type[L.n++] = ST_DSTY;
@@ -338,6 +379,7 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
         L.type[L.n++] = sweeps == 0 ? ST_IDSTX_W64
                                     : (p == 0 ? ST_IDSTX_SET
                                               : (p == sweeps ? ST_IDSTX_FINAL : ST_IDSTX_ADD));
+        for (int k = first; k < L.n; ++k) B->sweep_of[k] = p;
     }
 
     hs_status st = HS_OK;
@@ -398,8 +440,14 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
                 W.w = P->d_w32;
                 W.scr64 = P->d_dscr;
             } else {
+                // F (2n floats), U (2n floats), w (n floats) and, with FP64 factors,
+                // the FP64 forward-sweep scratch (n doubles), each 256-byte aligned
+                auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+                const size_t oF = 0, oU = up(oF + 2 * n * sizeof(float));
+                const size_t ow = up(oU + 2 * n * sizeof(float));
+                const size_t os = up(ow + n * sizeof(float));
+                const size_t bytes = os + (W.thomas32 ? 0 : n * sizeof(double));
                 void *buf = nullptr;
-                const size_t bytes = (5 * n) * sizeof(float) + (W.thomas32 ? 0 : n * sizeof(double));
                 if (cudaMalloc(&buf, bytes) != cudaSuccess) {
                     cudaGetLastError();
                     st = HS_ERR_OOM;
@@ -407,11 +455,11 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
                 }
                 B->extra.push_back(buf);
                 B->bytes += bytes;
-                float *fb = static_cast<float *>(buf);
-                W.F = fb;
-                W.U = fb + 2 * n;
-                W.w = fb + 4 * n;
-                W.scr64 = W.thomas32 ? nullptr : reinterpret_cast<double *>(fb + 5 * n);
+                unsigned char *base = static_cast<unsigned char *>(buf);
+                W.F = reinterpret_cast<float *>(base + oF);
+                W.U = reinterpret_cast<float *>(base + oU);
+                W.w = reinterpret_cast<float *>(base + ow);
+                W.scr64 = W.thomas32 ? nullptr : reinterpret_cast<double *>(base + os);
             }
             W.sx = (float)(2.0 / (d.Nx + 1));
             W.sy = (float)(2.0 / (d.Ny + 1));
@@ -420,6 +468,7 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
             W.gz = (d.Nz + RZ - 1) / RZ;
             const int Sx = lines_for(W.Mx, HS_AXIS_X), Sy = lines_for(W.My, HS_AXIS_Y);
             W.dxg = (int)(((long)d.Ny * d.Nz + Sx - 1) / Sx);
+            W.lx = Sx;
             W.dyg = (d.Nx + Sy - 1) / Sy;
             for (int s = 0; s < L.n; ++s) {
                 int t = 0;
@@ -452,6 +501,13 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
         return HS_ERR_UNSUPPORTED;
     }
     B->smem = smem;
+    const size_t nslots = (size_t)B->nworks * (HS_INFO_MAX_ITERS + 1);
+    if (cudaMalloc((void **)&B->d_norms, nslots * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        free_batch(B);
+        return HS_ERR_OOM;
+    }
+    for (int w = 0; w < B->nworks; ++w) B->works[w].norms = B->d_norms + (size_t)w * (HS_INFO_MAX_ITERS + 1);
     if (cudaMalloc((void **)&B->d_works, B->works.size() * sizeof(BatchWork)) != cudaSuccess ||
         cudaMalloc((void **)&B->d_items, items.size() * sizeof(int2)) != cudaSuccess ||
         cudaMalloc((void **)&B->d_ctr, (2 + (size_t)B->nworks * BMAX_STAGES) * sizeof(int)) !=
@@ -517,6 +573,16 @@ hs_status hs_batch_set_wait_limit(hs_batch_t B, long long spins) {
     return HS_OK;
 }
 
+hs_status hs_batch_set_tol(hs_batch_t B, double tol) {
+    if (!B || !(tol >= 0.0)) return HS_ERR_INVALID_ARG;
+    B->tol = tol;
+    if (B->have_graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->have_graph = 0;
+    }
+    return HS_OK;
+}
+
 hs_status hs_batch_debug_stall(hs_batch_t B, int on) {
     // test hook: one dependency of the first (problem, RHS) asks for one tile
     // more than its stage has, so the wait for it can only end by timing out
@@ -547,7 +613,9 @@ hs_status hs_batch_solve(hs_batch_t B, void *stream, int sync) {
         A.done = B->d_ctr + 2;
         A.spin_limit = B->spin_limit;
         A.f_is_f64 = B->f_dtype == HS_F64;
+        A.tol2 = B->tol * B->tol;
         A.stages = B->stages;
+        for (int k = 0; k < BMAX_STAGES; ++k) A.sweep_of[k] = B->sweep_of[k];
         cudaStream_t cs;
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
@@ -557,6 +625,8 @@ hs_status hs_batch_solve(hs_batch_t B, void *stream, int sync) {
         bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         if (ok) {
             cudaMemsetAsync(B->d_ctr, 0, (2 + (size_t)B->nworks * BMAX_STAGES) * sizeof(int), cs);
+            cudaMemsetAsync(B->d_norms, 0,
+                            (size_t)B->nworks * (HS_INFO_MAX_ITERS + 1) * sizeof(double), cs);
             batch_kernel<<<B->grid, 256, B->smem, cs>>>(A);
             ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && g;
         }

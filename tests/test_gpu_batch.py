@@ -110,3 +110,72 @@ def test_batch_rejects_unsupported_lengths():
         H.hs_batch_create([dict(N=(10, 10, 10), L=(1, 1, 1), order=4, c0=c, nrhs=1, f=f, u=u)],
                           H.HS_F32, 1)
     assert e.value.status == H.HS_ERR_UNSUPPORTED
+
+
+def test_batch_fp64_factor_path_odd_sizes():
+    """Problems whose z-systems need FP64 factors (min pivot ratio < 1e-4), odd unknown
+    counts and several right-hand sides: the per-RHS FP64 scratch of the batch."""
+    torch = pytest.importorskip("torch")
+    specs = [dict(id=0, N=(31, 31, 63), k0=60.0, a=1.0, nrhs=3),
+             dict(id=1, N=(63, 31, 31), k0=55.0, a=0.9, nrhs=2),
+             dict(id=2, N=(95, 31, 63), k0=45.0, a=1.0, nrhs=2)]
+    probs, _ = _make(torch, specs)
+    b = H.hs_batch_create(probs, H.HS_F32, 1)
+    try:
+        H.hs_batch_solve(b, sync=True)
+        for k, pr in enumerate(probs):
+            for r in range(pr["nrhs"]):
+                ref = _single(torch, pr, r, 1)
+                d = float((pr["u"][r] - ref).abs().max()) / float(ref.abs().max())
+                assert d <= 1e-14, (k, r, d)
+    finally:
+        H.hs_batch_destroy(b)
+
+
+def _single_info(torch, pr, r, sweeps):
+    s = H.Solver(*pr["N"], *pr["L"], 6, H.HS_HELMHOLTZ, H.HS_MIXED)
+    try:
+        s.set_coeff(pr["c0"], pr["c1"], pr["c2"])
+        H.hs_set_refinement(s.plan, sweeps)
+        u = torch.empty(pr["u"].shape[1:], dtype=torch.float64, device="cuda")
+        _, inf = s.solve(pr["f"][r].contiguous(), u, H.HS_F32, H.HS_RHS_NODAL, info=True)
+        torch.cuda.synchronize()
+        return inf["rel_residual"]
+    finally:
+        s.close()
+
+
+def test_batch_tolerance_stops_each_problem():
+    """With a tolerance every (problem, RHS) stops refining on its own once
+    ||F - A U|| / ||F|| <= tol: its result equals the stand-alone solve with the
+    sweep count its own residual history implies."""
+    torch = pytest.importorskip("torch")
+    specs = _specs(seed=13, n=5)
+    probs, _ = _make(torch, specs)
+    tol = 1e-9
+    b = H.hs_batch_create(probs, H.HS_F32, 4)
+    try:
+        H.hs_batch_set_tol(b, tol)
+        H.hs_batch_solve(b, sync=True)
+        H.hs_batch_solve(b, sync=True)
+        counts = set()
+        for k, pr in enumerate(probs):
+            for r in range(pr["nrhs"]):
+                rr = _single_info(torch, pr, r, 4)
+                need = next((m for m in range(5) if rr[m] <= tol), 4)
+                counts.add(need)
+                ref = _single(torch, pr, r, need)
+                got = pr["u"][r]
+                d = float((got - ref).abs().max()) / float(ref.abs().max())
+                assert d <= 1e-14, (k, r, need, d)
+        # a tolerance never met runs every sweep
+        H.hs_batch_set_tol(b, 1e-30)
+        H.hs_batch_solve(b, sync=True)
+        pr = probs[2]
+        ref = _single(torch, pr, 0, 4)
+        d = float((pr["u"][0] - ref).abs().max()) / float(ref.abs().max())
+        assert d <= 1e-14, d
+        with pytest.raises(H.HsError):
+            H.hs_batch_set_tol(b, -1.0)
+    finally:
+        H.hs_batch_destroy(b)
