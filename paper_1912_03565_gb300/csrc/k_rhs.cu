@@ -205,76 +205,30 @@ __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_df_kernel(RhsArgs a, const
     rhs_df_tile<T>(a, f, Fo, f2out, smem, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
-// r = F - A U in double-float arithmetic: F and U are (hi, lo) pairs, the
-// per-row coefficients are split into FP32 pairs, U = 0 outside the interior.
-// A U_hi is accumulated exactly enough (two_sum / two_prod); A U_lo, which is
-// ~2^-24 of it, in plain FP32.  r is rounded to FP32.
-__global__ void __launch_bounds__(256) residual_df_kernel(int Nx, int Ny, int Nz,
-                                                           const float2 *__restrict__ coef,
-                                                           const float *__restrict__ F,
-                                                           const float *__restrict__ U,
-                                                           float *__restrict__ r) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int l = blockIdx.z;
-    if (i >= Nx || j >= Ny) return;
-    const size_t plane = (size_t)Nx * Ny;
-    const size_t n = plane * Nz;
-    const float2 *cf = coef + (size_t)l * 12;
-    const bool im = i > 0, ip = i < Nx - 1, jm = j > 0, jp = j < Ny - 1;
-    const size_t c = (size_t)j * Nx + i;
-    dfloat acc;
-    acc.hi = 0.f;
-    acc.lo = 0.f;
-    float acc_lo = 0.f;
-#pragma unroll
-    for (int dl = -1; dl <= 1; ++dl) {
-        const int ll = l + dl;
-        if (ll < 0 || ll >= Nz) continue;
-        const float *P = U + (size_t)ll * plane;
-        const float *Q = P + n;  // lo plane
-        float h[9], q[9];
-        // 0: (i-1,j-1) 1: (i+1,j-1) 2: (i,j-1) 3: (i-1,j+1) 4: (i+1,j+1) 5: (i,j+1)
-        // 6: (i-1,j) 7: (i+1,j) 8: (i,j)
-        const bool ok[9] = {jm && im, jm && ip, jm, jp && im, jp && ip, jp, im, ip, true};
-        const long off[9] = {-(long)Nx - 1, -(long)Nx + 1, -(long)Nx, (long)Nx - 1, (long)Nx + 1,
-                             (long)Nx, -1, 1, 0};
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            h[k] = ok[k] ? __ldg(P + (long)c + off[k]) : 0.f;
-            q[k] = ok[k] ? __ldg(Q + (long)c + off[k]) : 0.f;
-        }
-        const dfloat C = df_add(df_make(h[0], h[1]), df_make(h[3], h[4]));
-        const dfloat X = df_make(h[6], h[7]);
-        const dfloat Y = df_make(h[2], h[5]);
-        dfloat ce;
-        ce.hi = h[8];
-        ce.lo = 0.f;
-        const float2 ka = cf[(dl + 1) * 4 + 0], kb = cf[(dl + 1) * 4 + 1];
-        const float2 kc = cf[(dl + 1) * 4 + 2], kd = cf[(dl + 1) * 4 + 3];
-        dfloat t = df_mul(dfloat{ka.x, ka.y}, C);
-        t = df_add(t, df_mul(dfloat{kb.x, kb.y}, X));
-        t = df_add(t, df_mul(dfloat{kc.x, kc.y}, Y));
-        t = df_add(t, df_mul(dfloat{kd.x, kd.y}, ce));
-        acc = df_add(acc, t);
-        acc_lo += ka.x * ((q[0] + q[1]) + (q[3] + q[4])) + kb.x * (q[6] + q[7]) +
-                  kc.x * (q[2] + q[5]) + kd.x * q[8];
-    }
-    const size_t o = (size_t)l * plane + c;
-    const dfloat res = df_add_accurate(dfloat{F[o], F[o + n]}, df_neg(acc));
-    r[o] = res.hi + (res.lo - acc_lo);
-}
-
 __global__ void __launch_bounds__(QTX *QTY) residual_zmarch_kernel(int Nx, int Ny, int Nz,
                                                                     const float2 *__restrict__ coef,
                                                                     const float *__restrict__ F,
                                                                     const float *__restrict__ U,
                                                                     float *__restrict__ r,
-                                                                    const int *skip, double *r2out) {
+                                                                    const int *skip, double *r2out,
+                                                                    const double *norms, int m,
+                                                                    int sel) {
     if (skip && *skip) return;
+    if (sel == HS_RESID_SEL_DF && residual_use_f64(norms, m)) return;
     __shared__ __align__(16) unsigned char smem[2 * 2 * QHY * QHX * sizeof(float)];
     residual_tile<false>(Nx, Ny, Nz, coef, F, U, r, r2out, smem, blockIdx.x, blockIdx.y,
                          blockIdx.z);
+}
+
+__global__ void __launch_bounds__(QTX *QTY) residual64_zmarch_kernel(
+    int Nx, int Ny, int Nz, const double *__restrict__ coef, const float *__restrict__ F,
+    const float *__restrict__ U, float *__restrict__ r, const int *skip, double *r2out,
+    const double *norms, int m, int sel) {
+    if (skip && *skip) return;
+    if (sel == HS_RESID_SEL_F64 && !residual_use_f64(norms, m)) return;
+    __shared__ __align__(16) unsigned char smem[2 * QHY * QHX * sizeof(double)];
+    residual64_tile<false>(Nx, Ny, Nz, coef, F, U, r, r2out, smem, blockIdx.x, blockIdx.y,
+                           blockIdx.z);
 }
 
 __global__ void refine_gate_kernel(const double *r2, const double *f2, double tol2, int *skip) {
@@ -407,17 +361,16 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
 }
 
 hs_status hs_launch_residual_df(const hs_plan_s *P, const float *F, const float *U, float *r,
-                                cudaStream_t s, double *r2) {
-    dim3 block(32, 8, 1);
-    dim3 grid((P->Nx + 31) / 32, (P->Ny + 7) / 8, P->Nz);
-    if (P->residual_simple) {
-        residual_df_kernel<<<grid, block, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df, F, U, r);
-    } else {
-        dim3 qb(QTX, QTY, 1);
-        dim3 qg((P->Nx + QTX - 1) / QTX, (P->Ny + QTY - 1) / QTY, (P->Nz + QZ - 1) / QZ);
+                                cudaStream_t s, double *r2, int prec, const double *norms,
+                                int m) {
+    dim3 qb(QTX, QTY, 1);
+    dim3 qg((P->Nx + QTX - 1) / QTX, (P->Ny + QTY - 1) / QTY, (P->Nz + QZ - 1) / QZ);
+    if (prec == HS_RESID_DF || prec == HS_RESID_SEL_DF)
         residual_zmarch_kernel<<<qg, qb, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df, F, U, r,
-                                                 P->cur_skip, r2);
-    }
+                                                 P->cur_skip, r2, norms, m, prec);
+    if (prec == HS_RESID_F64 || prec == HS_RESID_SEL_F64)
+        residual64_zmarch_kernel<<<qg, qb, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef, F, U, r,
+                                                   P->cur_skip, r2, norms, m, prec);
     return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 

@@ -179,3 +179,35 @@ def test_batch_tolerance_stops_each_problem():
             H.hs_batch_set_tol(b, -1.0)
     finally:
         H.hs_batch_destroy(b)
+
+
+def test_batch_residual_precision_auto():
+    """The batch takes the automatic residual decision per (problem, RHS): an
+    ill-conditioned problem next to well-conditioned ones gives, for each, the
+    stand-alone solve's result in the same mode."""
+    torch = pytest.importorskip("torch")
+    allspecs = W.workload_batch_specs(nprob=64, seed=3)
+    specs = [dict(sp, nrhs=1) for sp in allspecs if sp["id"] == 0]
+    specs += [dict(id=1, N=(63, 31, 95), k0=20.0, a=0.5, nrhs=2)]
+    probs, _ = _make(torch, specs)
+    for mode in (H.HS_RESID_AUTO, H.HS_RESID_F64):
+        b = H.hs_batch_create(probs, H.HS_F32, 4)
+        try:
+            H.hs_batch_set_residual_precision(b, mode)
+            H.hs_batch_solve(b, sync=True)
+            for k, pr in enumerate(probs):
+                for r in range(pr["nrhs"]):
+                    s = H.Solver(*pr["N"], *pr["L"], 6, H.HS_HELMHOLTZ, H.HS_MIXED)
+                    try:
+                        s.set_coeff(pr["c0"], pr["c1"], pr["c2"])
+                        H.hs_set_refinement(s.plan, 4)
+                        H.hs_set_residual_precision(s.plan, mode)
+                        ref = torch.empty(pr["u"].shape[1:], dtype=torch.float64, device="cuda")
+                        s.solve(pr["f"][r].contiguous(), ref, H.HS_F32, H.HS_RHS_NODAL)
+                        torch.cuda.synchronize()
+                    finally:
+                        s.close()
+                    d = float((pr["u"][r] - ref).abs().max()) / float(ref.abs().max())
+                    assert d <= 1e-14, (mode, k, r, d)
+        finally:
+            H.hs_batch_destroy(b)

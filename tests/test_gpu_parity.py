@@ -312,3 +312,78 @@ def test_refinement_tolerance_stops_on_device():
     assert O.max_rel_diff(u_all, u_3) <= 1e-15
     _, inf_t = run(4, tol, info=True)    # host-side test with diagnostics
     assert inf_t["iterations"] == need + 1
+
+
+def _ill_conditioned_problem():
+    """A problem from the 64-problem batch whose k(z) puts some z-systems close
+    to singular (min pivot ratio ~4e-5) with large cancellation in A U."""
+    spec = next(sp for sp in W.workload_batch_specs(nprob=64, seed=3) if sp["id"] == 0)
+    return W.batch_problem(spec, 0)
+
+
+def test_residual_precision_modes():
+    """Refinement with the FP32-pair residual stalls at its rounding floor on an
+    ill-conditioned problem; the FP64 residual (forced, or picked automatically
+    once a sweep gains less than 16x) brings the result to the FP64 solve's own
+    level.  Backward error: its FP64 residual within 4x of the FP64 solve's.
+    Forward error: within 4x of the scale at which two independent FP64 solvers
+    (this FP64 path and the oracle) already disagree, or 1e-10."""
+    torch = _torch()
+    p = _ill_conditioned_problem()
+    f = torch.from_numpy(p.f_nodes.astype(np.float32)).cuda()
+
+    def run(prec, mode=None, sweeps=4, info=False):
+        s = H.Solver(p.Nx, p.Ny, p.Nz, p.Lx, p.Ly, p.Lz, 6, H.HS_HELMHOLTZ, prec)
+        try:
+            s.set_coeff(p.c0, p.c1, p.c2)
+            if prec == H.HS_MIXED:
+                H.hs_set_refinement(s.plan, sweeps)
+                H.hs_set_residual_precision(s.plan, mode)
+            u = torch.empty((p.Nz, p.Ny, p.Nx), dtype=torch.float64, device="cuda")
+            _, inf = s.solve(f, u, H.HS_F32, H.HS_RHS_NODAL, info=info)
+            torch.cuda.synchronize()
+            r, n = H.hs_residual(s.plan, f, H.HS_F32, H.HS_RHS_NODAL, None, u)
+            return u, r / n, inf
+        finally:
+            s.close()
+
+    ref = oracle_solve(p, H.HS_F32)
+    u64, res64, _ = run(H.HS_FP64)
+    delta = O.max_rel_diff(u64.cpu().numpy(), ref)      # FP64 vs FP64
+    bar = max(1e-10, 4 * delta)
+    scale = float(u64.abs().max())
+    err = lambda u: O.max_rel_diff(u.cpu().numpy(), ref)
+    u_df, res_df, _ = run(H.HS_MIXED, H.HS_RESID_DF)
+    u_f64, res_f64, _ = run(H.HS_MIXED, H.HS_RESID_F64)
+    u_auto, res_auto, _ = run(H.HS_MIXED, H.HS_RESID_AUTO)
+    vals = (f"res64={res64:.3e} res_df={res_df:.3e} res_f64={res_f64:.3e} "
+            f"res_auto={res_auto:.3e} delta64={delta:.3e} err_df={err(u_df):.3e} "
+            f"err_f64={err(u_f64):.3e} err_auto={err(u_auto):.3e}")
+    assert res_df > 5 * res64, vals                 # the pair residual's floor
+    for u, res in ((u_f64, res_f64), (u_auto, res_auto)):
+        assert res <= 4 * res64 and res <= res_df / 5, vals
+        assert err(u) <= bar, vals
+    # host-side decision (hs_info) gives the same iterate as the device-side one
+    u_ai, _, inf = run(H.HS_MIXED, H.HS_RESID_AUTO, info=True)
+    assert float((u_ai - u_auto).abs().max()) / scale <= 1e-15
+    rr = inf["rel_residual"]
+    assert rr[inf["iterations"] - 1] <= 4 * res64
+    # and on a well-conditioned problem with 2 sweeps the automatic mode keeps
+    # the pair residual: identical to HS_RESID_DF
+    q = W.workload_cube255_order6(N=63)
+    fq = torch.from_numpy(q.f_nodes).cuda()
+    outs = []
+    for mode in (H.HS_RESID_DF, H.HS_RESID_AUTO):
+        s = H.Solver(q.Nx, q.Ny, q.Nz, q.Lx, q.Ly, q.Lz, 6, H.HS_HELMHOLTZ, H.HS_MIXED)
+        try:
+            s.set_coeff(q.c0, q.c1, q.c2)
+            H.hs_set_refinement(s.plan, 2)
+            H.hs_set_residual_precision(s.plan, mode)
+            u = torch.empty((q.Nz, q.Ny, q.Nx), dtype=torch.float64, device="cuda")
+            fnn = [None if a is None else torch.from_numpy(a).cuda() for a in q.fnn]
+            s.solve(fq, u, H.HS_F64, H.HS_RHS_NODAL, None, fnn)
+            torch.cuda.synchronize()
+            outs.append(u)
+        finally:
+            s.close()
+    assert torch.equal(outs[0], outs[1])
