@@ -51,6 +51,25 @@ BYTES_FP64 = {"rhs": 16.0, "dst_x": 16.0, "dst_y": 16.0, "thomas": 40.0, "idst_y
               "idst_x": 16.0, "residual": 0.0}
 
 
+# Counters of one ncu capture (--set full) of a kernel at a workload's full size,
+# per launch: DRAM bytes read + written, warp instructions.  Valid only while the
+# kernel is unchanged since the capture (the profile named records the command).
+NCU_COUNTS = {
+    ("cube255_o6", "rhs"): {"bound": "alu", "dram_bytes": 139.165696e6 + 89.344e6,
+                            "warp_inst": 355172572,
+                            "profile": "profiles/rhs_df_cube255_o6.md"},
+}
+
+
+def sm_max_mhz():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                               "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh).get("sm_max_mhz", 2070.0))
+    except (OSError, ValueError):
+        return 2070.0
+
+
 def stage_bytes(path: str, sweeps: int, thomas_fp32: bool = True):
     if path == "fp64":
         return dict(BYTES_FP64)
@@ -619,10 +638,27 @@ def main():
     bytes_per_launch = bmix[kern] * N3 * R / nlaunch
     t_launch = st_mix[kern] / nlaunch * 1e-3
     achieved = bytes_per_launch / t_launch / 1e9
-    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-                "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                "algorithmic_bytes_per_launch": bytes_per_launch}
+    hbm = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": hbm_peak,
+           "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+           "peak_kind": f"{peak_kind} HBM copy bandwidth",
+           "algorithmic_bytes_per_launch": bytes_per_launch}
+    counts = NCU_COUNTS.get((args.workload, kern))
+    if counts is not None:
+        hbm["traffic"] = counts["dram_bytes"]
+    if counts is not None and counts.get("bound") == "alu":
+        # instruction-issue bound: warp instructions per launch (ncu) over the live
+        # launch time, against 4 schedulers x SMs x the maximum SM clock
+        props = torch.cuda.get_device_properties(local)
+        issue_peak = 4 * props.multi_processor_count * sm_max_mhz() * 1e6 / 1e9
+        ach = counts["warp_inst"] / t_launch / 1e9
+        roofline = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": issue_peak,
+                    "unit": "G warp-inst/s", "frac": ach / issue_peak,
+                    "traffic": counts["dram_bytes"],
+                    "peak_kind": "issue rate: 4 warp-instructions/clock/SM x SMs x max SM clock",
+                    "warp_inst_per_launch": counts["warp_inst"], "profile": counts["profile"],
+                    "hbm": hbm}
+    else:
+        roofline = hbm
 
     # ---- end to end through the C ABI with host buffers (pinned)
     e2e = None

@@ -297,6 +297,21 @@ hs_status hs_batch_set_tol(hs_batch_t batch, double tol);
  * (problem, RHS) of the batch, each deciding on its own (default AUTO). */
 hs_status hs_batch_set_residual_precision(hs_batch_t batch, int mode);
 
+/* hs_batch_set_variant / hs_batch_get_variant -- the persistent kernel
+ * variant: 0 = registers capped for 2 resident CTAs (256 threads) per SM,
+ * 1 = for 3 (fewer registers, more latency hiding).  The grid is every CTA
+ * the variant can keep resident.  Default: the first variant that fits.
+ * Errors: HS_ERR_INVALID_ARG; HS_ERR_UNSUPPORTED (variant cannot be resident
+ * with this batch's shared memory). */
+hs_status hs_batch_set_variant(hs_batch_t batch, int variant);
+hs_status hs_batch_get_variant(hs_batch_t batch, int *variant, int *grid);
+
+/* hs_batch_autotune -- times `reps` solves of the batch (after one warm-up)
+ * with each kernel variant on `stream` and keeps the fastest; *ms (may be
+ * NULL) receives its mean time per solve.  The solves write the outputs u.
+ * Synchronous. */
+hs_status hs_batch_autotune(hs_batch_t batch, void *stream, int reps, float *ms);
+
 /* hs_batch_debug_stall -- test hook: on = 1 makes one dependency of the first
  * problem unsatisfiable, so the next solve must end with HS_ERR_TIMEOUT; on =
  * 0 restores it. */

@@ -45,6 +45,7 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_status_str", "hs_last_error", "hs_residual_static", "hs_batch_create",
             "hs_batch_set_io", "hs_batch_solve", "hs_batch_set_wait_limit", "hs_batch_set_tol",
             "hs_batch_set_residual_precision", "hs_batch_debug_stall", "hs_set_residual_precision",
+            "hs_batch_set_variant", "hs_batch_get_variant", "hs_batch_autotune",
             "hs_batch_workspace_bytes", "hs_batch_destroy")
 HS_STATIC_MAX_NZ = 8192
 
@@ -123,6 +124,12 @@ def load(path: Optional[str] = None):
     lib.hs_batch_solve.restype = ci
     lib.hs_batch_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     lib.hs_batch_set_wait_limit.restype = ci
+    lib.hs_batch_set_variant.argtypes = [vp, ci]
+    lib.hs_batch_set_variant.restype = ci
+    lib.hs_batch_get_variant.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    lib.hs_batch_get_variant.restype = ci
+    lib.hs_batch_autotune.argtypes = [vp, vp, ci, ctypes.POINTER(ctypes.c_float)]
+    lib.hs_batch_autotune.restype = ci
     lib.hs_batch_set_residual_precision.argtypes = [vp, ci]
     lib.hs_batch_set_residual_precision.restype = ci
     lib.hs_set_residual_precision.argtypes = [vp, ci]
@@ -331,6 +338,26 @@ def hs_set_residual_precision(plan, mode):
 def hs_batch_set_residual_precision(batch, mode):
     return _check(load().hs_batch_set_residual_precision(batch, int(mode)),
                   "hs_batch_set_residual_precision")
+
+
+def hs_batch_set_variant(batch, variant):
+    return _check(load().hs_batch_set_variant(batch, int(variant)), "hs_batch_set_variant")
+
+
+def hs_batch_get_variant(batch):
+    """(variant, grid) of the batch's persistent kernel."""
+    v, g = ctypes.c_int(), ctypes.c_int()
+    _check(load().hs_batch_get_variant(batch, ctypes.byref(v), ctypes.byref(g)),
+           "hs_batch_get_variant")
+    return v.value, g.value
+
+
+def hs_batch_autotune(batch, stream=None, reps=2):
+    """Times each kernel variant on the batch, keeps the fastest; returns its ms per solve."""
+    ms = ctypes.c_float()
+    _check(load().hs_batch_autotune(batch, _stream_ptr(stream), int(reps), ctypes.byref(ms)),
+           "hs_batch_autotune")
+    return ms.value
 
 
 def hs_batch_set_tol(batch, tol):

@@ -47,11 +47,12 @@ def build(verbose: bool = False, extra=()) -> str:
     """Compile every csrc/*.cu and link libhs.so; returns the library path."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
-    newest = max(os.path.getmtime(p) for p in srcs + [os.path.join(INCLUDE, "hs.h"),
-                                                       os.path.join(CSRC, "hs_internal.cuh")])
+    deps = srcs + [os.path.join(INCLUDE, "hs.h")] + sorted(
+        os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh"))
+    newest = max(os.path.getmtime(p) for p in deps)
     if os.path.exists(LIB) and os.path.getmtime(LIB) > newest and not extra:
         return LIB
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 8))) as ex:
         objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
     cmd = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -1,281 +1,14 @@
-// Batched solves in one persistent launch.
-//
-// Many independent problems (uneven sizes, their own k(z), 1..4 right-hand
-// sides each) are solved by the mixed path in ONE kernel launch: a grid of
-// persistent CTAs (as many as can be resident) takes work items from a queue
-// (an atomic counter over an item list).  An item is one tile of one stage of
-// one (problem, right-hand side): the right-hand side, a transform pass, the
-// z-solves, the residual, ... -- the same tile code as the stand-alone
-// kernels (hs_tiles.cuh), reading data produced earlier in the launch through
-// L2 only.  Items are listed stage by stage, so every item depends only on
-// items earlier in the list; a CTA waits (bounded) until all tiles of the
-// previous stage of its own (problem, RHS) are done, counted per stage with
-// atomics.  Since CTAs take items in list order and all CTAs are resident,
-// the items a CTA waits for are already running: no deadlock.  A wait that
-// exceeds its limit sets an error flag that the host reads (HS_ERR_TIMEOUT);
-// later waits then give up at once, so the launch always ends.
-// The launch (counter resets + kernel) is captured in a CUDA graph per stream.
+// Batched solves in one persistent launch: host side (plans, work and item
+// lists, kernel variant and grid, graph capture).  The device side and the
+// scheduling scheme are in hs_batch.cuh.
 #include <string.h>
 
 #include <new>
 #include <vector>
 
-#include "hs_tiles.cuh"
+#include "hs_batch.cuh"
 
-using namespace hs_tiles;
-
-namespace {
-
-enum StageType : int {
-    ST_RHS = 0,
-    ST_DSTX_F = 1,       // forward x: F_hi (pass 0) or r -> w
-    ST_DSTY = 2,         // forward or inverse y, in place, with a scale
-    ST_THOMAS = 3,
-    ST_IDSTX_SET = 4,    // inverse x into U (double-float), first pass
-    ST_IDSTX_ADD = 5,    // inverse x, U += correction
-    ST_IDSTX_FINAL = 6,  // inverse x, u = U + correction (FP64)
-    ST_IDSTX_W64 = 7,    // inverse x straight into u (no refinement)
-    ST_RESIDUAL = 8
-};
-
-constexpr int BMAX_STAGES = 6 + 6 * HS_INFO_MAX_ITERS;
-
-struct BatchWork {
-    int Nx, Ny, Nz, Mx, My;
-    int thomas32;
-    const float2 *coef_df;
-    const float *fac32;
-    const double *fac64;
-    double *scr64;
-    const float2 *rx, *hx, *ry, *hy;   // FP32 transform tables of x and y
-    RhsArgs rhs;
-    const void *f;
-    double *u;
-    float *F, *U, *w;
-    float sx, sy;
-    int gx, gy, gz;                    // RHS / residual tile grid
-    int dxg, dyg;                      // x-transform groups, y-transform groups per plane
-    int lx;                            // x lines per x-transform tile
-    const double *coef64;              // FP64 stencil rows (FP64 residual)
-    double *norms;                     // [0] ||F||^2, [m] ||r_m||^2 (when norms_on)
-    int need[BMAX_STAGES];
-};
-
-struct StageList {
-    int n;
-    int type[BMAX_STAGES];
-};
-
-struct BatchArgs {
-    const BatchWork *works;
-    const int2 *items;  // x: work index + 65536 * stage, y: tile
-    int nitems;
-    int *next;
-    int *done;          // [nworks][BMAX_STAGES]
-    int *err;
-    long long spin_limit;
-    int f_is_f64;
-    double tol2;        // > 0: a (problem, RHS) stops refining once ||r||^2 <= tol2 ||F||^2
-    int norms_on;       // accumulate the squared norms (tolerance or automatic residual)
-    int resid_mode;     // HS_RESID_DF / HS_RESID_F64 / HS_RESID_AUTO
-    StageList stages;
-    int sweep_of[BMAX_STAGES];   // refinement sweep a stage belongs to (0: first solve)
-};
-
-__device__ __forceinline__ int ld_volatile(const int *p) {
-    return *reinterpret_cast<const volatile int *>(p);
-}
-
-template <int AXIS, int MODE, int M, int... Rs>
-__device__ __forceinline__ void dst_tile_m(const BatchWork &W, const float *in, void *out,
-                                           float scale, unsigned char *smem, int tile) {
-    constexpr int S = Lines<float, M, AXIS>::value;
-    const float2 *roots = AXIS == HS_AXIS_X ? W.rx : W.ry;
-    const float2 *half = AXIS == HS_AXIS_X ? W.hx : W.hy;
-    const int bx = AXIS == HS_AXIS_X ? tile : tile % W.dyg;
-    const int by = AXIS == HS_AXIS_X ? 0 : tile / W.dyg;
-    if constexpr (MODE == HS_MODE_DF_SET || MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL) {
-        dst_fast_tile<float, float, float, AXIS, MODE, M, S, true, Rs...>(
-            in, static_cast<float *>(out), W.u, roots, half, W.Nx, W.Ny, W.Nz, scale, smem, bx, by);
-    } else {
-        dst_fast_tile<float, float, float, AXIS, MODE, M, S, true, Rs...>(
-            in, static_cast<float *>(out), nullptr, roots, half, W.Nx, W.Ny, W.Nz, scale, smem,
-            bx, by);
-    }
-}
-
-template <int M, int... Rs>
-__device__ __forceinline__ void dst_w64_m(const BatchWork &W, const float *in, float scale,
-                                          unsigned char *smem, int tile) {
-    constexpr int S = Lines<float, M, HS_AXIS_X>::value;
-    dst_fast_tile<float, float, double, HS_AXIS_X, HS_MODE_WRITE, M, S, true, Rs...>(
-        in, W.u, nullptr, W.rx, W.hx, W.Nx, W.Ny, W.Nz, scale, smem, tile, 0);
-}
-
-// Dispatch a transform tile on the line length.
-template <int AXIS, int MODE>
-__device__ void dst_tile(const BatchWork &W, const float *in, void *out, float scale,
-                         unsigned char *smem, int tile) {
-    const int M = AXIS == HS_AXIS_X ? W.Mx : W.My;
-    switch (M) {
-        case 32: dst_tile_m<AXIS, MODE, 32, 8, 4>(W, in, out, scale, smem, tile); break;
-        case 64: dst_tile_m<AXIS, MODE, 64, 16, 4>(W, in, out, scale, smem, tile); break;
-        case 96: dst_tile_m<AXIS, MODE, 96, 16, 6>(W, in, out, scale, smem, tile); break;
-        case 128: dst_tile_m<AXIS, MODE, 128, 16, 8>(W, in, out, scale, smem, tile); break;
-        case 192: dst_tile_m<AXIS, MODE, 192, 16, 12>(W, in, out, scale, smem, tile); break;
-        case 256: dst_tile_m<AXIS, MODE, 256, 16, 16>(W, in, out, scale, smem, tile); break;
-        case 384: dst_tile_m<AXIS, MODE, 384, 16, 8, 3>(W, in, out, scale, smem, tile); break;
-        default: break;
-    }
-}
-
-__device__ void dst_w64_tile(const BatchWork &W, const float *in, float scale,
-                             unsigned char *smem, int tile) {
-    switch (W.Mx) {
-        case 32: dst_w64_m<32, 8, 4>(W, in, scale, smem, tile); break;
-        case 64: dst_w64_m<64, 16, 4>(W, in, scale, smem, tile); break;
-        case 96: dst_w64_m<96, 16, 6>(W, in, scale, smem, tile); break;
-        case 128: dst_w64_m<128, 16, 8>(W, in, scale, smem, tile); break;
-        case 192: dst_w64_m<192, 16, 12>(W, in, scale, smem, tile); break;
-        case 256: dst_w64_m<256, 16, 16>(W, in, scale, smem, tile); break;
-        case 384: dst_w64_m<384, 16, 8, 3>(W, in, scale, smem, tile); break;
-        default: break;
-    }
-}
-
-// Tolerance mode: has this (problem, RHS) converged at or before sweep m?  The
-// residual of sweep j (j >= 1) is complete before any later stage runs, so every
-// tile of a stage takes the same decision.
-__device__ __forceinline__ bool converged(const BatchArgs &A, const BatchWork &W, int m) {
-    if (A.tol2 <= 0.0 || m < 1) return false;
-    const double f2 = __ldcg(W.norms);
-    for (int j = 1; j <= m; ++j)
-        if (__ldcg(W.norms + j) <= A.tol2 * f2) return true;
-    return false;
-}
-
-__device__ void run_tile(const BatchArgs &A, const BatchWork &W, int stage, int type, int tile,
-                         unsigned char *smem) {
-    const size_t plane = (size_t)W.Nx * W.Ny;
-    if (A.tol2 > 0.0) {
-        const int m = A.sweep_of[stage];
-        // a residual runs unless an earlier sweep converged; the rest of a sweep
-        // runs unless its own residual says converged
-        const bool skip = type == ST_RESIDUAL ? converged(A, W, m - 1) : converged(A, W, m);
-        if (skip) {
-            if (type == ST_IDSTX_FINAL) {
-                // the converged iterate is the answer: u = U_hi + U_lo on this tile
-                const size_t n = plane * W.Nz;
-                const size_t r0 = (size_t)tile * W.lx * W.Nx;
-                const size_t r1 = min(n, r0 + (size_t)W.lx * W.Nx);
-                for (size_t k = r0 + threadIdx.x; k < r1; k += blockDim.x)
-                    W.u[k] = (double)__ldcg(W.U + k) + (double)__ldcg(W.U + n + k);
-            }
-            return;
-        }
-    }
-    switch (type) {
-        case ST_RHS: {
-            const int bx = tile % W.gx, by = (tile / W.gx) % W.gy, bz = tile / (W.gx * W.gy);
-            double *f2 = A.norms_on ? W.norms : nullptr;
-            if (A.f_is_f64)
-                rhs_df_tile<double>(W.rhs, static_cast<const double *>(W.f), W.F, f2, smem, bx,
-                                    by, bz);
-            else
-                rhs_df_tile<float>(W.rhs, static_cast<const float *>(W.f), W.F, f2, smem, bx, by,
-                                   bz);
-            break;
-        }
-        case ST_RESIDUAL: {
-            const int bx = tile % W.gx, by = (tile / W.gx) % W.gy, bz = tile / (W.gx * W.gy);
-            const int m = A.sweep_of[stage];
-            double *r2 = A.norms_on ? W.norms + m : nullptr;
-            const bool f64 = A.resid_mode == HS_RESID_F64 ||
-                             (A.resid_mode == HS_RESID_AUTO && residual_use_f64(W.norms, m));
-            if (f64)
-                residual64_tile<true>(W.Nx, W.Ny, W.Nz, W.coef64, W.F, W.U, W.w, r2, smem, bx, by,
-                                      bz);
-            else
-                residual_tile<true>(W.Nx, W.Ny, W.Nz, W.coef_df, W.F, W.U, W.w, r2, smem, bx, by,
-                                    bz);
-            break;
-        }
-        case ST_DSTX_F:
-            // the first pass transforms F_hi (the first plane of F); later ones the residual
-            dst_tile<HS_AXIS_X, HS_MODE_WRITE>(W, stage == 1 ? W.F : W.w, W.w, 1.f, smem, tile);
-            break;
-        case ST_DSTY: {
-            // forward y follows a forward x (stage type of the previous stage)
-            const bool inverse = A.stages.type[stage - 1] == ST_THOMAS;
-            dst_tile<HS_AXIS_Y, HS_MODE_WRITE>(W, W.w, W.w, inverse ? W.sy : 1.f, smem, tile);
-            break;
-        }
-        case ST_THOMAS: {
-            const size_t idx = (size_t)tile * blockDim.x + threadIdx.x;
-            if (idx < plane) {
-                const size_t nz = (size_t)W.Nz * plane;
-                if (W.thomas32)
-                    thomas_column<float, float, float, true>(W.Nz, plane, idx, W.w, (float *)nullptr,
-                                                             W.fac32, W.fac32 + nz,
-                                                             W.fac32 + 2 * nz);
-                else
-                    thomas_column<float, double, double, true>(W.Nz, plane, idx, W.w, W.scr64,
-                                                               W.fac64, W.fac64 + nz,
-                                                               W.fac64 + 2 * nz);
-            }
-            break;
-        }
-        case ST_IDSTX_SET: dst_tile<HS_AXIS_X, HS_MODE_DF_SET>(W, W.w, W.U, W.sx, smem, tile); break;
-        case ST_IDSTX_ADD: dst_tile<HS_AXIS_X, HS_MODE_DF_ADD>(W, W.w, W.U, W.sx, smem, tile); break;
-        case ST_IDSTX_FINAL:
-            dst_tile<HS_AXIS_X, HS_MODE_DF_FINAL>(W, W.w, W.U, W.sx, smem, tile);
-            break;
-        case ST_IDSTX_W64: dst_w64_tile(W, W.w, W.sx, smem, tile); break;
-        default: break;
-    }
-}
-
-__global__ void __launch_bounds__(256, 2) batch_kernel(BatchArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int cur;
-    __shared__ int bail;
-    for (;;) {
-        if (threadIdx.x == 0) cur = atomicAdd(A.next, 1);
-        __syncthreads();
-        const int it = cur;
-        if (it >= A.nitems) break;
-        const int2 item = A.items[it];
-        const int wi = item.x & 0xFFFF, stage = item.x >> 16, tile = item.y;
-        const BatchWork &W = A.works[wi];
-        if (threadIdx.x == 0) {
-            bail = 0;
-            if (stage > 0) {
-                const int *cnt = A.done + (size_t)wi * BMAX_STAGES + (stage - 1);
-                const int need = W.need[stage - 1];
-                long long spins = 0;
-                while (ld_volatile(cnt) < need) {
-                    if (ld_volatile(A.err) || ++spins > A.spin_limit) {
-                        atomicExch(A.err, 1);
-                        bail = 1;
-                        break;
-                    }
-                    __nanosleep(100);
-                }
-                __threadfence();
-            }
-            if (ld_volatile(A.err)) bail = 1;
-        }
-        __syncthreads();
-        if (!bail) run_tile(A, W, stage, A.stages.type[stage], tile, smem);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(A.done + (size_t)wi * BMAX_STAGES + stage, 1);
-        }
-    }
-}
-
-}  // namespace
+using namespace hs_batch;
 
 // ------------------------------------------------------------------- host side
 
@@ -290,7 +23,9 @@ struct hs_batch_s {
     BatchWork *d_works;
     int2 *d_items;
     int *d_ctr;                       // [0] next, [1] err, then done counters
-    int nitems, nworks, grid;
+    int nitems, nworks;
+    int variant;                      // index into kVariants
+    int grid[2];                      // resident CTAs of each variant
     size_t smem;
     long long spin_limit;
     double tol;
@@ -305,6 +40,17 @@ struct hs_batch_s {
 };
 
 namespace {
+
+// The kernel variants: CTAs per SM the registers are capped for.
+constexpr int kNumVariants = 2;
+const void *variant_fn(int v) { return v == 0 ? batch_kernel_v2() : batch_kernel_v3(); }
+
+void drop_graph(hs_batch_s *B) {
+    if (B->have_graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->have_graph = 0;
+    }
+}
 
 size_t dst_smem_for(int M, int axis) {
     switch (M) {
@@ -535,24 +281,32 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
     if (cudaMemcpy(B->d_works, B->works.data(), B->works.size() * sizeof(BatchWork),
                    cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(B->d_items, items.data(), items.size() * sizeof(int2),
-                   cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         free_batch(B);
         return HS_ERR_CUDA;
     }
-    int dev = 0, sms = 0, per = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel, 256, smem) !=
-            cudaSuccess ||
-        per < 1) {
-        cudaGetLastError();
+    B->variant = -1;
+    for (int v = 0; v < kNumVariants; ++v) {
+        int per = 0;
+        B->grid[v] = 0;
+        if (cudaFuncSetAttribute(variant_fn(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, variant_fn(v), 256, smem) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        B->grid[v] = sms * per;  // every CTA resident: waits only on items already taken
+        if (per >= 1 && B->variant < 0) B->variant = v;
+    }
+    if (B->variant < 0) {
         free_batch(B);
         return HS_ERR_UNSUPPORTED;
     }
-    B->grid = sms * per;  // every CTA resident: waits only on items already taken
     *out = B;
     return HS_OK;
 }
@@ -580,20 +334,14 @@ hs_status hs_batch_set_io(hs_batch_t B, int k, const void *f, double *u) {
 hs_status hs_batch_set_wait_limit(hs_batch_t B, long long spins) {
     if (!B || spins < 1) return HS_ERR_INVALID_ARG;
     B->spin_limit = spins;
-    if (B->have_graph) {
-        cudaGraphExecDestroy(B->graph);
-        B->have_graph = 0;
-    }
+    drop_graph(B);
     return HS_OK;
 }
 
 hs_status hs_batch_set_tol(hs_batch_t B, double tol) {
     if (!B || !(tol >= 0.0)) return HS_ERR_INVALID_ARG;
     B->tol = tol;
-    if (B->have_graph) {
-        cudaGraphExecDestroy(B->graph);
-        B->have_graph = 0;
-    }
+    drop_graph(B);
     return HS_OK;
 }
 
@@ -601,11 +349,61 @@ hs_status hs_batch_set_residual_precision(hs_batch_t B, int mode) {
     if (!B || (mode != HS_RESID_DF && mode != HS_RESID_F64 && mode != HS_RESID_AUTO))
         return HS_ERR_INVALID_ARG;
     B->resid_mode = mode;
-    if (B->have_graph) {
-        cudaGraphExecDestroy(B->graph);
-        B->have_graph = 0;
-    }
+    drop_graph(B);
     return HS_OK;
+}
+
+hs_status hs_batch_set_variant(hs_batch_t B, int variant) {
+    if (!B || variant < 0 || variant >= kNumVariants) return HS_ERR_INVALID_ARG;
+    if (B->grid[variant] < 1) return HS_ERR_UNSUPPORTED;
+    if (variant != B->variant) drop_graph(B);
+    B->variant = variant;
+    return HS_OK;
+}
+
+hs_status hs_batch_get_variant(hs_batch_t B, int *variant, int *grid) {
+    if (!B) return HS_ERR_INVALID_ARG;
+    if (variant) *variant = B->variant;
+    if (grid) *grid = B->grid[B->variant];
+    return HS_OK;
+}
+
+hs_status hs_batch_autotune(hs_batch_t B, void *stream, int reps, float *ms_out) {
+    if (!B || reps < 1) return HS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return HS_ERR_CUDA;
+    }
+    int best = -1;
+    float best_ms = 0.f;
+    hs_status st = HS_OK;
+    for (int v = 0; v < kNumVariants && st == HS_OK; ++v) {
+        if (B->grid[v] < 1) continue;
+        if ((st = hs_batch_set_variant(B, v)) != HS_OK) break;
+        if ((st = hs_batch_solve(B, stream, 1)) != HS_OK) break;  // capture + warm-up
+        float tot = 0.f;
+        for (int r = 0; r < reps && st == HS_OK; ++r) {
+            cudaEventRecord(e0, s);
+            st = hs_batch_solve(B, stream, 0);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = HS_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tot += ms;
+        }
+        if (st == HS_OK && (best < 0 || tot < best_ms)) {
+            best = v;
+            best_ms = tot;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HS_OK) return st;
+    if (best < 0) return HS_ERR_UNSUPPORTED;
+    if (ms_out) *ms_out = best_ms / reps;
+    return hs_batch_set_variant(B, best);
 }
 
 hs_status hs_batch_debug_stall(hs_batch_t B, int on) {
@@ -655,7 +453,9 @@ hs_status hs_batch_solve(hs_batch_t B, void *stream, int sync) {
             cudaMemsetAsync(B->d_ctr, 0, (2 + (size_t)B->nworks * BMAX_STAGES) * sizeof(int), cs);
             cudaMemsetAsync(B->d_norms, 0,
                             (size_t)B->nworks * (HS_INFO_MAX_ITERS + 1) * sizeof(double), cs);
-            batch_kernel<<<B->grid, 256, B->smem, cs>>>(A);
+            void *args[] = {&A};
+            cudaLaunchKernel(variant_fn(B->variant), dim3(B->grid[B->variant]), dim3(256), args,
+                             B->smem, cs);
             ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && g;
         }
         ok = ok && cudaGraphInstantiate(&B->graph, g, 0) == cudaSuccess;

@@ -1,0 +1,10 @@
+// Persistent batch kernel, register cap for 3 resident CTAs of 256 threads per SM.
+#include "hs_batch.cuh"
+
+namespace hs_batch {
+
+__global__ void __launch_bounds__(256, 3) batch_kernel3(BatchArgs A) { batch_body(A); }
+
+const void *batch_kernel_v3() { return reinterpret_cast<const void *>(&batch_kernel3); }
+
+}  // namespace hs_batch
