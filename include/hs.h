@@ -62,6 +62,8 @@ enum { HS_CD_PAPER = 0, HS_CD_CORRECTED = 1 };               /* CD coefficient v
 enum { HS_F64 = 0, HS_F32 = 1 };                             /* element type of f / faces */
 enum { HS_RHS_NODAL = 0, HS_RHS_ASSEMBLED = 1 };             /* meaning of f */
 enum { HS_RESID_DF = 0, HS_RESID_F64 = 1, HS_RESID_AUTO = 2 }; /* refinement residual */
+enum { HS_DST_STAGED = 0, HS_DST_FUSED = 1, HS_DST_GENERIC = 2 };  /* transform kernels */
+enum { HS_AXIS_X = 0, HS_AXIS_Y = 1 };                       /* transform axis */
 
 typedef struct hs_plan_s *hs_plan_t;
 
@@ -169,6 +171,32 @@ hs_status hs_set_residual_precision(hs_plan_t plan, int mode);
  * Errors: HS_ERR_INVALID_ARG (tol < 0 or NaN).
  */
 hs_status hs_set_refinement_tol(hs_plan_t plan, double tol);
+
+/*
+ * hs_set_transform_variant / hs_get_transform_variant -- the DST-I kernels of
+ * one axis (HS_AXIS_X = 0, HS_AXIS_Y = 1; Section 3.6's transforms):
+ *   HS_DST_STAGED  compile-time-sized FFT, every radix stage through shared
+ *                  memory (line lengths N + 1 in {32,..,1024} of 2^a 3^b);
+ *   HS_DST_FUSED   the same lengths, first stage loaded straight from global
+ *                  memory and (x) the last stage paired by warp shuffles
+ *                  (HS_MIXED plans only);
+ *   HS_DST_GENERIC runtime-sized kernels (any length; the only choice for
+ *                  lengths without compiled kernels).
+ * Results agree to rounding.  Default: HS_DST_STAGED where compiled.
+ * Errors: HS_ERR_INVALID_ARG; HS_ERR_UNSUPPORTED (variant not built for this
+ * length or precision).
+ */
+hs_status hs_set_transform_variant(hs_plan_t plan, int axis, int variant);
+hs_status hs_get_transform_variant(hs_plan_t plan, int axis, int *variant);
+
+/*
+ * hs_autotune -- times one forward transform pass per supported variant and
+ * axis (`reps` launches after one untimed) on the plan's own work buffer
+ * (overwritten) on `stream`, and keeps the fastest variant of each axis;
+ * *ms_x, *ms_y (may be NULL) receive the kept variants' times per pass.
+ * Synchronous.  Call after hs_plan, before solves (not during capture).
+ */
+hs_status hs_autotune(hs_plan_t plan, void *stream, int reps, float *ms_x, float *ms_y);
 
 /*
  * hs_set_stage_timing -- when on (1), solves record CUDA events around each

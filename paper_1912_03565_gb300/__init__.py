@@ -35,6 +35,8 @@ HS_CD_PAPER, HS_CD_CORRECTED = 0, 1
 HS_F64, HS_F32 = 0, 1
 HS_RHS_NODAL, HS_RHS_ASSEMBLED = 0, 1
 HS_RESID_DF, HS_RESID_F64, HS_RESID_AUTO = 0, 1, 2
+HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC = 0, 1, 2
+HS_AXIS_X, HS_AXIS_Y = 0, 1
 HS_INFO_MAX_ITERS = 8
 HS_INFO_STAGES = 8
 STAGES = ("rhs", "dst_x", "dst_y", "thomas", "idst_y", "idst_x", "residual", "total")
@@ -46,6 +48,7 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_batch_set_io", "hs_batch_solve", "hs_batch_set_wait_limit", "hs_batch_set_tol",
             "hs_batch_set_residual_precision", "hs_batch_debug_stall", "hs_set_residual_precision",
             "hs_batch_set_variant", "hs_batch_get_variant", "hs_batch_autotune",
+            "hs_set_transform_variant", "hs_get_transform_variant", "hs_autotune",
             "hs_batch_workspace_bytes", "hs_batch_destroy")
 HS_STATIC_MAX_NZ = 8192
 
@@ -124,6 +127,13 @@ def load(path: Optional[str] = None):
     lib.hs_batch_solve.restype = ci
     lib.hs_batch_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     lib.hs_batch_set_wait_limit.restype = ci
+    lib.hs_set_transform_variant.argtypes = [vp, ci, ci]
+    lib.hs_set_transform_variant.restype = ci
+    lib.hs_get_transform_variant.argtypes = [vp, ci, ctypes.POINTER(ci)]
+    lib.hs_get_transform_variant.restype = ci
+    lib.hs_autotune.argtypes = [vp, vp, ci, ctypes.POINTER(ctypes.c_float),
+                                ctypes.POINTER(ctypes.c_float)]
+    lib.hs_autotune.restype = ci
     lib.hs_batch_set_variant.argtypes = [vp, ci]
     lib.hs_batch_set_variant.restype = ci
     lib.hs_batch_get_variant.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]
@@ -338,6 +348,26 @@ def hs_set_residual_precision(plan, mode):
 def hs_batch_set_residual_precision(batch, mode):
     return _check(load().hs_batch_set_residual_precision(batch, int(mode)),
                   "hs_batch_set_residual_precision")
+
+
+def hs_set_transform_variant(plan, axis, variant):
+    return _check(load().hs_set_transform_variant(plan, int(axis), int(variant)),
+                  "hs_set_transform_variant", plan)
+
+
+def hs_get_transform_variant(plan, axis):
+    v = ctypes.c_int()
+    _check(load().hs_get_transform_variant(plan, int(axis), ctypes.byref(v)),
+           "hs_get_transform_variant", plan)
+    return v.value
+
+
+def hs_autotune(plan, stream=None, reps=3):
+    """Keeps the fastest transform variant per axis; returns (ms_x, ms_y) per pass."""
+    mx, my = ctypes.c_float(), ctypes.c_float()
+    _check(load().hs_autotune(plan, _stream_ptr(stream), int(reps), ctypes.byref(mx),
+                              ctypes.byref(my)), "hs_autotune", plan)
+    return mx.value, my.value
 
 
 def hs_batch_set_variant(batch, variant):

@@ -672,6 +672,74 @@ hs_status hs_set_residual_precision(hs_plan_t P, int mode) {
     return HS_OK;
 }
 
+hs_status hs_set_transform_variant(hs_plan_t P, int axis, int variant) {
+    if (!P || (axis != HS_AXIS_X && axis != HS_AXIS_Y)) return HS_ERR_INVALID_ARG;
+    if (variant != HS_DST_STAGED && variant != HS_DST_FUSED && variant != HS_DST_GENERIC)
+        return HS_ERR_INVALID_ARG;
+    const bool fast = hs_dst_fast_size(P->axd[axis].M) != 0;
+    if (variant == HS_DST_FUSED && (!fast || P->precision != HS_MIXED)) return HS_ERR_UNSUPPORTED;
+    if (variant == HS_DST_STAGED && !fast) return HS_ERR_UNSUPPORTED;
+    P->dst_variant[axis] = variant;
+    return HS_OK;
+}
+
+hs_status hs_get_transform_variant(hs_plan_t P, int axis, int *variant) {
+    if (!P || !variant || (axis != HS_AXIS_X && axis != HS_AXIS_Y)) return HS_ERR_INVALID_ARG;
+    *variant = P->dst_variant[axis];
+    return HS_OK;
+}
+
+hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *ms_y) {
+    if (!P || reps < 1) return HS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool mixed = P->precision == HS_MIXED;
+    const int tc = mixed ? HS_T_F32 : HS_T_F64;
+    void *w = mixed ? (void *)P->d_w32 : (void *)P->d_w64;
+    if (!w) return HS_ERR_INVALID_ARG;
+    const size_t n = interior_count(P);
+    HS_CK(P, cudaMemsetAsync(w, 0, n * (mixed ? sizeof(float) : sizeof(double)), s));
+    cudaEvent_t e0, e1;
+    HS_CK(P, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return HS_ERR_CUDA;
+    }
+    hs_status st = HS_OK;
+    float best_ms[2] = {0.f, 0.f};
+    for (int axis = 0; axis < 2 && st == HS_OK; ++axis) {
+        const int saved = P->dst_variant[axis];
+        int best = -1;
+        for (int v = HS_DST_STAGED; v <= HS_DST_GENERIC && st == HS_OK; ++v) {
+            if (hs_set_transform_variant(P, axis, v) != HS_OK) continue;
+            // one untimed pass (first launch, attribute set-up), then `reps` timed
+            st = hs_launch_dst(P, axis, tc, tc, w, tc, w, HS_MODE_WRITE, 1.0, s);
+            if (st != HS_OK) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && st == HS_OK; ++r)
+                st = hs_launch_dst(P, axis, tc, tc, w, tc, w, HS_MODE_WRITE, 1.0, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = HS_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (st == HS_OK && (best < 0 || ms < best_ms[axis])) {
+                best = v;
+                best_ms[axis] = ms;
+            }
+        }
+        P->dst_variant[axis] = best >= 0 ? best : saved;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HS_OK) {
+        cudaGetLastError();
+        return st;
+    }
+    if (ms_x) *ms_x = best_ms[0];
+    if (ms_y) *ms_y = best_ms[1];
+    return HS_OK;
+}
+
 hs_status hs_set_stage_timing(hs_plan_t P, int on) {
     if (!P) return HS_ERR_INVALID_ARG;
     P->stage_timing = on ? 1 : 0;

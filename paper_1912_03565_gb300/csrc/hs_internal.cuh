@@ -24,7 +24,7 @@ struct DstAxis {
     const void *sintab; // 2M reals: sin(pi m / M) (direct path)
 };
 
-enum { HS_AXIS_X = 0, HS_AXIS_Y = 1 };
+// HS_AXIS_X / HS_AXIS_Y come from hs.h
 enum { HS_T_F64 = 0, HS_T_F32 = 1, HS_T_DF = 2 };
 // Output modes of the inverse x-transform: write, accumulate, and the
 // double-float iterate updates of the mixed path (set hi = X, lo = 0; add X
@@ -47,7 +47,7 @@ struct hs_plan_s {
     int *d_skip;        // device flag: 1 once refinement has converged (later kernels return)
     const int *cur_skip;  // the flag the launchers pass on (NULL outside tolerance mode)
     int stage_timing;
-    int dst_generic;    // 1: always use the runtime-sized transform kernels
+    int dst_variant[2];   // per axis: HS_DST_STAGED / HS_DST_FUSED / HS_DST_GENERIC
     int resid_mode;       // HS_RESID_DF / HS_RESID_F64 / HS_RESID_AUTO
     int have_coeff;
     int cd_variant;
@@ -116,6 +116,13 @@ int hs_dst_fast_size(int M);
 hs_status hs_launch_dst_fast(const hs_plan_s *P, int axis, int tc, int tin, const void *in,
                              int tout, void *out, int mode, double scale, cudaStream_t s,
                              double *aux);
+
+// Fused FP32 transform tiles (k_dst_fused_x.cu, k_dst_fused_y.cu); HS_ERR_UNSUPPORTED
+// for a length or type combination they do not cover.
+hs_status hs_launch_dst_fused_x(const hs_plan_s *P, int tin, const void *in, int tout, void *out,
+                                int mode, double scale, cudaStream_t s, double *aux);
+hs_status hs_launch_dst_fused_y(const hs_plan_s *P, int tin, const void *in, int tout, void *out,
+                                int mode, double scale, cudaStream_t s, double *aux);
 
 // 1 when a line of this axis fits the transform kernel's shared memory.
 int hs_dst_fits(const DstAxis &ax, int axis, int tc);

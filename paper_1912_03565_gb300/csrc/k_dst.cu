@@ -344,7 +344,14 @@ int hs_dst_fits(const DstAxis &ax, int axis, int tc) {
 
 hs_status hs_launch_dst(const hs_plan_s *P, int axis, int tc, int tin, const void *in, int tout,
                         void *out, int mode, double scale, cudaStream_t s, double *aux) {
-    if (P->dst_generic == 0 && hs_dst_fast_size(P->axd[axis].M))
+    const int v = P->dst_variant[axis];
+    if (v == HS_DST_FUSED && tc == HS_T_F32 && hs_dst_fast_size(P->axd[axis].M)) {
+        const hs_status st =
+            axis == HS_AXIS_X ? hs_launch_dst_fused_x(P, tin, in, tout, out, mode, scale, s, aux)
+                              : hs_launch_dst_fused_y(P, tin, in, tout, out, mode, scale, s, aux);
+        if (st != HS_ERR_UNSUPPORTED) return st;
+    }
+    if (v != HS_DST_GENERIC && hs_dst_fast_size(P->axd[axis].M))
         return hs_launch_dst_fast(P, axis, tc, tin, in, tout, out, mode, scale, s, aux);
     if (tc == HS_T_F64) {
         if (tin == HS_T_F64 && tout == HS_T_F64 && mode == HS_MODE_WRITE)

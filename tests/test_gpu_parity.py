@@ -23,12 +23,19 @@ def _torch():
 
 
 def gpu_solve(p, precision=H.HS_FP64, sweeps=2, f_dtype=H.HS_F64, device=True,
-              cd_variant=H.HS_CD_CORRECTED, info=False):
+              cd_variant=H.HS_CD_CORRECTED, info=False, variant=None):
     torch = _torch()
     eq = H.HS_CONVDIFF if p.equation == W.CONVDIFF else H.HS_HELMHOLTZ
     s = H.Solver(p.Nx, p.Ny, p.Nz, p.Lx, p.Ly, p.Lz, p.order, eq, precision)
     try:
         s.set_coeff(p.c0, p.c1, p.c2, cd_variant)
+        if variant is not None:
+            for axis in (H.HS_AXIS_X, H.HS_AXIS_Y):
+                try:   # lengths without compiled kernels keep the runtime-sized ones
+                    H.hs_set_transform_variant(s.plan, axis, variant)
+                except H.HsError as e:
+                    if e.status != H.HS_ERR_UNSUPPORTED:
+                        raise
         if precision == H.HS_MIXED:
             H.hs_set_refinement(s.plan, sweeps)
         npdt = np.float64 if f_dtype == H.HS_F64 else np.float32
@@ -263,18 +270,63 @@ FAST_N = [31, 63, 95, 127, 191, 255, 383, 511, 767, 1023]
 
 
 @pytest.mark.parametrize("N", FAST_N)
-@pytest.mark.parametrize("precision", [H.HS_FP64, H.HS_MIXED])
-def test_transform_lengths(N, precision):
-    """Every compile-time-sized transform length, along x and along y (ragged tiles).
+@pytest.mark.parametrize("precision,variant", [(H.HS_FP64, H.HS_DST_STAGED),
+                                               (H.HS_MIXED, H.HS_DST_STAGED),
+                                               (H.HS_MIXED, H.HS_DST_FUSED)])
+def test_transform_lengths(N, precision, variant):
+    """Every compile-time-sized transform length and kernel variant, along x and along
+    y (ragged tiles: 9 x-lines over 5 planes, 7-column y-tiles).
 
     Uniform h (6th order) keeps these thin boxes well conditioned (min pivot ratio
     ~0.25): FP64 parity is bounded by eps * kappa, and random anisotropic boxes reach
-    pivot ratios of 1e-7, where two exact-in-theory FP64 solvers differ by ~1e-11."""
+    pivot ratios of 1e-7, where two exact-in-theory FP64 solvers differ by ~1e-11.
+    The unrefined mixed solve (FP32 transforms) must be as accurate with either
+    variant: both are FP32 FFTs of the same length."""
     for shape in ((N, 9, 5), (7, N, 4)):
         p = random_problem(shape, 6, W.HELMHOLTZ, seed=N + shape[1])
         ref = oracle_solve(p)
-        u, _ = gpu_solve(p, precision, sweeps=3)
+        u, _ = gpu_solve(p, precision, sweeps=3, variant=variant)
         assert O.max_rel_diff(u, ref) <= (TOL64 if precision == H.HS_FP64 else TOLMIX)
+        if precision == H.HS_MIXED:
+            u0, _ = gpu_solve(p, precision, sweeps=0, variant=variant)
+            u0s, _ = gpu_solve(p, precision, sweeps=0, variant=H.HS_DST_STAGED)
+            e, es = O.max_rel_diff(u0, ref), O.max_rel_diff(u0s, ref)
+            assert e <= 4 * es + 1e-7 and e <= 1e-4, (e, es)
+
+
+def test_autotune_keeps_a_valid_variant():
+    """hs_autotune times the transform variants of each axis and keeps one; solves
+    afterwards still meet the parity bar; variants that do not exist are refused."""
+    torch = _torch()
+    p = random_problem((127, 95, 33), 6, W.HELMHOLTZ, seed=5)
+    ref = oracle_solve(p)
+    s = H.Solver(p.Nx, p.Ny, p.Nz, p.Lx, p.Ly, p.Lz, 6, H.HS_HELMHOLTZ, H.HS_MIXED)
+    try:
+        s.set_coeff(p.c0, p.c1, p.c2)
+        mx, my = H.hs_autotune(s.plan, reps=2)
+        assert mx > 0 and my > 0
+        for axis in (H.HS_AXIS_X, H.HS_AXIS_Y):
+            assert H.hs_get_transform_variant(s.plan, axis) in (
+                H.HS_DST_STAGED, H.HS_DST_FUSED, H.HS_DST_GENERIC)
+        H.hs_set_refinement(s.plan, 2)
+        f = torch.from_numpy(p.f_nodes).cuda()
+        faces = [None if a is None else torch.from_numpy(a).cuda() for a in p.faces]
+        fnn = [None if a is None else torch.from_numpy(a).cuda() for a in p.fnn]
+        u = torch.zeros((p.Nz, p.Ny, p.Nx), dtype=torch.float64, device="cuda")
+        s.solve(f, u, H.HS_F64, H.HS_RHS_NODAL, faces, fnn)
+        torch.cuda.synchronize()
+        assert O.max_rel_diff(u.cpu().numpy(), ref) <= TOLMIX
+        with pytest.raises(H.HsError):
+            H.hs_set_transform_variant(s.plan, H.HS_AXIS_X, 7)
+    finally:
+        s.close()
+    q = H.Solver(100, 20, 10, 1.0, 1.0, 1.0, 4, H.HS_HELMHOLTZ, H.HS_MIXED)   # N + 1 = 101
+    try:
+        with pytest.raises(H.HsError):
+            H.hs_set_transform_variant(q.plan, H.HS_AXIS_X, H.HS_DST_FUSED)
+        H.hs_set_transform_variant(q.plan, H.HS_AXIS_X, H.HS_DST_GENERIC)
+    finally:
+        q.close()
 
 
 def test_refinement_tolerance_stops_on_device():
