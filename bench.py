@@ -425,6 +425,10 @@ def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
         if tried[cand]["ok"]:
             break
     H.hs_batch_set_tol(b, tol)
+    t0 = time.perf_counter()
+    tuned_ms = H.hs_batch_autotune(b, stream, 1)    # kernel variant (set-up, untimed)
+    tune = {"variant": H.hs_batch_get_variant(b)[0], "grid": H.hs_batch_get_variant(b)[1],
+            "ms": tuned_ms, "autotune_s": time.perf_counter() - t0}
     H.hs_batch_solve(b, stream, True)
     acc = {"judged_against": "fp64 GPU path, every problem and RHS: forward error <= 1e-10, "
                              "else FP64 residual <= 4x the FP64 path's",
@@ -463,7 +467,7 @@ def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
             "config": {"workload": f"batch64: {WORKLOADS['batch64']['desc']}",
                        "global_batch": world * 64, "parallelism": f"replicas x{world}",
                        "unknown_solves_per_step": total, "refinement_sweeps_max": max_sweeps,
-                       "refinement_residual_tol": tol,
+                       "refinement_residual_tol": tol, "batch_kernel": tune,
                        "l2": "256 MB buffer written between timed steps"},
             "sequential_fp64_path": {"value": total / (t64 * 1e-3) / 1e9, "unit": UNIT,
                                      "ms_per_step": t64},

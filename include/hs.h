@@ -326,11 +326,12 @@ hs_status hs_batch_set_tol(hs_batch_t batch, double tol);
 hs_status hs_batch_set_residual_precision(hs_batch_t batch, int mode);
 
 /* hs_batch_set_variant / hs_batch_get_variant -- the persistent kernel
- * variant: 0 = registers capped for 2 resident CTAs (256 threads) per SM,
- * 1 = for 3 (fewer registers, more latency hiding).  The grid is every CTA
- * the variant can keep resident.  Default: the first variant that fits.
- * Errors: HS_ERR_INVALID_ARG; HS_ERR_UNSUPPORTED (variant cannot be resident
- * with this batch's shared memory). */
+ * variant: 0 = staged transform tiles, registers capped for 2 resident CTAs
+ * (256 threads) per SM; 1 = staged, capped for 3; 2 = fused transform tiles
+ * (first stage from global memory, x pairing by shuffles), 2 CTAs; 3 = fused,
+ * 3 CTAs.  The grid is every CTA the variant can keep resident.  Default: the
+ * first variant that fits.  Errors: HS_ERR_INVALID_ARG; HS_ERR_UNSUPPORTED
+ * (variant cannot be resident with this batch's shared memory). */
 hs_status hs_batch_set_variant(hs_batch_t batch, int variant);
 hs_status hs_batch_get_variant(hs_batch_t batch, int *variant, int *grid);
 

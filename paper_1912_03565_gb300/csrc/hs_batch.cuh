@@ -18,6 +18,7 @@
 // the launch always ends.
 #pragma once
 
+#include "hs_dst_fused.cuh"
 #include "hs_tiles.cuh"
 
 namespace hs_batch {
@@ -94,14 +95,27 @@ __device__ __forceinline__ void dst_tile_m(const BatchWork &W, const float *in, 
     const float2 *half = AXIS == HS_AXIS_X ? W.hx : W.hy;
     const int bx = AXIS == HS_AXIS_X ? tile : tile % W.dyg;
     const int by = AXIS == HS_AXIS_X ? 0 : tile / W.dyg;
-    if constexpr (MODE == HS_MODE_DF_SET || MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL) {
-        dst_fast_tile<float, float, float, AXIS, MODE, M, S, true, Rs...>(
-            in, static_cast<float *>(out), W.u, roots, half, W.Nx, W.Ny, W.Nz, scale, smem, bx, by);
-    } else {
-        dst_fast_tile<float, float, float, AXIS, MODE, M, S, true, Rs...>(
-            in, static_cast<float *>(out), nullptr, roots, half, W.Nx, W.Ny, W.Nz, scale, smem,
-            bx, by);
-    }
+    double *aux =
+        (MODE == HS_MODE_DF_SET || MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL) ? W.u
+                                                                                      : nullptr;
+    dst_fast_tile<float, float, float, AXIS, MODE, M, S, true, Rs...>(
+        in, static_cast<float *>(out), aux, roots, half, W.Nx, W.Ny, W.Nz, scale, smem, bx, by);
+}
+
+// The fused tiles (hs_dst_fused.cuh): radices R1 (first), RL (last), Rmid.
+template <int AXIS, int MODE, int M, int R1, int RL, int... Rmid>
+__device__ __forceinline__ void dst_fused_m(const BatchWork &W, const float *in, void *out,
+                                            float scale, unsigned char *smem, int tile) {
+    constexpr int S = Lines<float, M, AXIS>::value;
+    const float2 *roots = AXIS == HS_AXIS_X ? W.rx : W.ry;
+    const float2 *half = AXIS == HS_AXIS_X ? W.hx : W.hy;
+    const int bx = AXIS == HS_AXIS_X ? tile : tile % W.dyg;
+    const int by = AXIS == HS_AXIS_X ? 0 : tile / W.dyg;
+    double *aux =
+        (MODE == HS_MODE_DF_SET || MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL) ? W.u
+                                                                                      : nullptr;
+    dst_fused_tile<float, float, AXIS, MODE, M, S, true, R1, RL, Rmid...>(
+        in, static_cast<float *>(out), aux, roots, half, W.Nx, W.Ny, W.Nz, scale, smem, bx, by);
 }
 
 template <int M, int... Rs>
@@ -112,34 +126,69 @@ __device__ __forceinline__ void dst_w64_m(const BatchWork &W, const float *in, f
         in, W.u, nullptr, W.rx, W.hx, W.Nx, W.Ny, W.Nz, scale, smem, tile, 0);
 }
 
-// Dispatch a transform tile on the line length.
-template <int AXIS, int MODE>
+template <int M, int R1, int RL, int... Rmid>
+__device__ __forceinline__ void dst_w64_fused_m(const BatchWork &W, const float *in, float scale,
+                                                unsigned char *smem, int tile) {
+    constexpr int S = Lines<float, M, HS_AXIS_X>::value;
+    dst_fused_tile<float, double, HS_AXIS_X, HS_MODE_WRITE, M, S, true, R1, RL, Rmid...>(
+        in, W.u, nullptr, W.rx, W.hx, W.Nx, W.Ny, W.Nz, scale, smem, tile, 0);
+}
+
+// Dispatch a transform tile on the line length (staged or fused tiles).
+template <bool FUSED, int AXIS, int MODE>
 __device__ void dst_tile(const BatchWork &W, const float *in, void *out, float scale,
                          unsigned char *smem, int tile) {
     const int M = AXIS == HS_AXIS_X ? W.Mx : W.My;
-    switch (M) {
-        case 32: dst_tile_m<AXIS, MODE, 32, 8, 4>(W, in, out, scale, smem, tile); break;
-        case 64: dst_tile_m<AXIS, MODE, 64, 16, 4>(W, in, out, scale, smem, tile); break;
-        case 96: dst_tile_m<AXIS, MODE, 96, 16, 6>(W, in, out, scale, smem, tile); break;
-        case 128: dst_tile_m<AXIS, MODE, 128, 16, 8>(W, in, out, scale, smem, tile); break;
-        case 192: dst_tile_m<AXIS, MODE, 192, 16, 12>(W, in, out, scale, smem, tile); break;
-        case 256: dst_tile_m<AXIS, MODE, 256, 16, 16>(W, in, out, scale, smem, tile); break;
-        case 384: dst_tile_m<AXIS, MODE, 384, 16, 8, 3>(W, in, out, scale, smem, tile); break;
-        default: break;
+    if constexpr (FUSED) {
+        switch (M) {
+            case 32: dst_fused_m<AXIS, MODE, 32, 8, 4>(W, in, out, scale, smem, tile); break;
+            case 64: dst_fused_m<AXIS, MODE, 64, 16, 4>(W, in, out, scale, smem, tile); break;
+            case 96: dst_fused_m<AXIS, MODE, 96, 16, 6>(W, in, out, scale, smem, tile); break;
+            case 128: dst_fused_m<AXIS, MODE, 128, 16, 8>(W, in, out, scale, smem, tile); break;
+            case 192: dst_fused_m<AXIS, MODE, 192, 16, 12>(W, in, out, scale, smem, tile); break;
+            case 256: dst_fused_m<AXIS, MODE, 256, 16, 16>(W, in, out, scale, smem, tile); break;
+            case 384: dst_fused_m<AXIS, MODE, 384, 16, 12, 2>(W, in, out, scale, smem, tile); break;
+            default: break;
+        }
+    } else {
+        switch (M) {
+            case 32: dst_tile_m<AXIS, MODE, 32, 8, 4>(W, in, out, scale, smem, tile); break;
+            case 64: dst_tile_m<AXIS, MODE, 64, 16, 4>(W, in, out, scale, smem, tile); break;
+            case 96: dst_tile_m<AXIS, MODE, 96, 16, 6>(W, in, out, scale, smem, tile); break;
+            case 128: dst_tile_m<AXIS, MODE, 128, 16, 8>(W, in, out, scale, smem, tile); break;
+            case 192: dst_tile_m<AXIS, MODE, 192, 16, 12>(W, in, out, scale, smem, tile); break;
+            case 256: dst_tile_m<AXIS, MODE, 256, 16, 16>(W, in, out, scale, smem, tile); break;
+            case 384: dst_tile_m<AXIS, MODE, 384, 16, 8, 3>(W, in, out, scale, smem, tile); break;
+            default: break;
+        }
     }
 }
 
+template <bool FUSED>
 __device__ void dst_w64_tile(const BatchWork &W, const float *in, float scale,
                              unsigned char *smem, int tile) {
-    switch (W.Mx) {
-        case 32: dst_w64_m<32, 8, 4>(W, in, scale, smem, tile); break;
-        case 64: dst_w64_m<64, 16, 4>(W, in, scale, smem, tile); break;
-        case 96: dst_w64_m<96, 16, 6>(W, in, scale, smem, tile); break;
-        case 128: dst_w64_m<128, 16, 8>(W, in, scale, smem, tile); break;
-        case 192: dst_w64_m<192, 16, 12>(W, in, scale, smem, tile); break;
-        case 256: dst_w64_m<256, 16, 16>(W, in, scale, smem, tile); break;
-        case 384: dst_w64_m<384, 16, 8, 3>(W, in, scale, smem, tile); break;
-        default: break;
+    if constexpr (FUSED) {
+        switch (W.Mx) {
+            case 32: dst_w64_fused_m<32, 8, 4>(W, in, scale, smem, tile); break;
+            case 64: dst_w64_fused_m<64, 16, 4>(W, in, scale, smem, tile); break;
+            case 96: dst_w64_fused_m<96, 16, 6>(W, in, scale, smem, tile); break;
+            case 128: dst_w64_fused_m<128, 16, 8>(W, in, scale, smem, tile); break;
+            case 192: dst_w64_fused_m<192, 16, 12>(W, in, scale, smem, tile); break;
+            case 256: dst_w64_fused_m<256, 16, 16>(W, in, scale, smem, tile); break;
+            case 384: dst_w64_fused_m<384, 16, 12, 2>(W, in, scale, smem, tile); break;
+            default: break;
+        }
+    } else {
+        switch (W.Mx) {
+            case 32: dst_w64_m<32, 8, 4>(W, in, scale, smem, tile); break;
+            case 64: dst_w64_m<64, 16, 4>(W, in, scale, smem, tile); break;
+            case 96: dst_w64_m<96, 16, 6>(W, in, scale, smem, tile); break;
+            case 128: dst_w64_m<128, 16, 8>(W, in, scale, smem, tile); break;
+            case 192: dst_w64_m<192, 16, 12>(W, in, scale, smem, tile); break;
+            case 256: dst_w64_m<256, 16, 16>(W, in, scale, smem, tile); break;
+            case 384: dst_w64_m<384, 16, 8, 3>(W, in, scale, smem, tile); break;
+            default: break;
+        }
     }
 }
 
@@ -154,6 +203,7 @@ __device__ __forceinline__ bool converged(const BatchArgs &A, const BatchWork &W
     return false;
 }
 
+template <bool FUSED>
 __device__ void run_tile(const BatchArgs &A, const BatchWork &W, int stage, int type, int tile,
                          unsigned char *smem) {
     const size_t plane = (size_t)W.Nx * W.Ny;
@@ -202,12 +252,12 @@ __device__ void run_tile(const BatchArgs &A, const BatchWork &W, int stage, int 
         }
         case ST_DSTX_F:
             // the first pass transforms F_hi (the first plane of F); later ones the residual
-            dst_tile<HS_AXIS_X, HS_MODE_WRITE>(W, stage == 1 ? W.F : W.w, W.w, 1.f, smem, tile);
+            dst_tile<FUSED, HS_AXIS_X, HS_MODE_WRITE>(W, stage == 1 ? W.F : W.w, W.w, 1.f, smem, tile);
             break;
         case ST_DSTY: {
             // forward y follows a forward x (stage type of the previous stage)
             const bool inverse = A.stages.type[stage - 1] == ST_THOMAS;
-            dst_tile<HS_AXIS_Y, HS_MODE_WRITE>(W, W.w, W.w, inverse ? W.sy : 1.f, smem, tile);
+            dst_tile<FUSED, HS_AXIS_Y, HS_MODE_WRITE>(W, W.w, W.w, inverse ? W.sy : 1.f, smem, tile);
             break;
         }
         case ST_THOMAS: {
@@ -215,22 +265,22 @@ __device__ void run_tile(const BatchArgs &A, const BatchWork &W, int stage, int 
             if (idx < plane) {
                 const size_t nz = (size_t)W.Nz * plane;
                 if (W.thomas32)
-                    thomas_column<float, float, float, true>(W.Nz, plane, idx, W.w, (float *)nullptr,
+                    thomas_column<float, float, float, true, false>(W.Nz, plane, idx, W.w, (float *)nullptr,
                                                              W.fac32, W.fac32 + nz,
                                                              W.fac32 + 2 * nz);
                 else
-                    thomas_column<float, double, double, true>(W.Nz, plane, idx, W.w, W.scr64,
+                    thomas_column<float, double, double, true, false>(W.Nz, plane, idx, W.w, W.scr64,
                                                                W.fac64, W.fac64 + nz,
                                                                W.fac64 + 2 * nz);
             }
             break;
         }
-        case ST_IDSTX_SET: dst_tile<HS_AXIS_X, HS_MODE_DF_SET>(W, W.w, W.U, W.sx, smem, tile); break;
-        case ST_IDSTX_ADD: dst_tile<HS_AXIS_X, HS_MODE_DF_ADD>(W, W.w, W.U, W.sx, smem, tile); break;
+        case ST_IDSTX_SET: dst_tile<FUSED, HS_AXIS_X, HS_MODE_DF_SET>(W, W.w, W.U, W.sx, smem, tile); break;
+        case ST_IDSTX_ADD: dst_tile<FUSED, HS_AXIS_X, HS_MODE_DF_ADD>(W, W.w, W.U, W.sx, smem, tile); break;
         case ST_IDSTX_FINAL:
-            dst_tile<HS_AXIS_X, HS_MODE_DF_FINAL>(W, W.w, W.U, W.sx, smem, tile);
+            dst_tile<FUSED, HS_AXIS_X, HS_MODE_DF_FINAL>(W, W.w, W.U, W.sx, smem, tile);
             break;
-        case ST_IDSTX_W64: dst_w64_tile(W, W.w, W.sx, smem, tile); break;
+        case ST_IDSTX_W64: dst_w64_tile<FUSED>(W, W.w, W.sx, smem, tile); break;
         default: break;
     }
 }
@@ -241,6 +291,7 @@ __device__ void run_tile(const BatchArgs &A, const BatchWork &W, int stage, int 
 // dependency unless this CTA has already seen it met (counters only grow);
 // the tile index and flags reach the other threads through shared memory, so
 // an item costs two barriers.
+template <bool FUSED>
 __device__ __forceinline__ void batch_body(const BatchArgs &A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_it, s_wi, s_stage, s_tile, s_bail;
@@ -296,16 +347,19 @@ __device__ __forceinline__ void batch_body(const BatchArgs &A) {
         __syncthreads();
         if (s_it >= A.nitems) break;
         const int stage = s_stage;
-        if (!s_bail) run_tile(A, A.works[s_wi], stage, A.stages.type[stage], s_tile, smem);
+        if (!s_bail) run_tile<FUSED>(A, A.works[s_wi], stage, A.stages.type[stage], s_tile, smem);
         __syncthreads();
     }
 }
 
 }  // namespace
 
-// Kernel variants (registers capped for 2 or 3 resident CTAs per SM), each in
-// its own translation unit; the host picks one per batch.
+// Kernel variants (registers capped for 2 or 3 resident CTAs per SM; staged or
+// fused transform tiles), each in its own translation unit; the host picks one
+// per batch.
 const void *batch_kernel_v2();
 const void *batch_kernel_v3();
+const void *batch_kernel_v2f();
+const void *batch_kernel_v3f();
 
 }  // namespace hs_batch

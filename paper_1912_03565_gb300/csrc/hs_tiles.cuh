@@ -1009,67 +1009,173 @@ constexpr int CH = 16;
 // One z-solve with cached factors.  Td: data type (in place); Tf: factor type;
 // Ts: type of the forward-sweep values (kept in `scratch` when it is not null,
 // else in `data`); Ta: arithmetic type.
-template <typename Td, typename Tf, typename Ta, bool COH = false>
+template <typename Td, typename Tf, typename Ta, bool COH = false, bool PIPE = true>
 __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, Td *data,
                                               Ta *scratch, const Tf *cpr, const Tf *alpha,
                                               const Tf *beta) {
-    Ta d = (Ta)0;
-    int l = 0;
-    for (; l + CH <= Nz; l += CH) {
-        Ta r[CH], a[CH], b[CH];
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            const size_t o = (size_t)(l + k) * plane + idx;
-            r[k] = (Ta)ldc<COH>(data + o);
-            a[k] = (Ta)alpha[o];
-            b[k] = (Ta)beta[o];
+    if constexpr (!PIPE) {
+        // chunked, not pipelined (kernels whose register budget cannot hold two
+        // chunks, e.g. the persistent batch kernel)
+        Ta d = (Ta)0;
+        int l = 0;
+        for (; l + CH <= Nz; l += CH) {
+            Ta r[CH], a[CH], b[CH];
+    #pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                const size_t o = (size_t)(l + k) * plane + idx;
+                r[k] = (Ta)ldc<COH>(data + o);
+                a[k] = (Ta)alpha[o];
+                b[k] = (Ta)beta[o];
+            }
+    #pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                d = a[k] * r[k] - b[k] * d;
+                r[k] = d;
+            }
+    #pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                const size_t o = (size_t)(l + k) * plane + idx;
+                if (scratch)
+                    scratch[o] = r[k];
+                else
+                    data[o] = (Td)r[k];
+            }
         }
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            d = a[k] * r[k] - b[k] * d;
-            r[k] = d;
-        }
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            const size_t o = (size_t)(l + k) * plane + idx;
+        for (; l < Nz; ++l) {
+            const size_t o = (size_t)l * plane + idx;
+            d = (Ta)alpha[o] * (Ta)ldc<COH>(data + o) - (Ta)beta[o] * d;
             if (scratch)
-                scratch[o] = r[k];
+                scratch[o] = d;
             else
-                data[o] = (Td)r[k];
+                data[o] = (Td)d;
         }
-    }
-    for (; l < Nz; ++l) {
-        const size_t o = (size_t)l * plane + idx;
-        d = (Ta)alpha[o] * (Ta)ldc<COH>(data + o) - (Ta)beta[o] * d;
-        if (scratch)
-            scratch[o] = d;
-        else
-            data[o] = (Td)d;
-    }
-    Ta w = d;
-    data[(size_t)(Nz - 1) * plane + idx] = (Td)w;
-    int top = Nz - 2;  // next plane to solve, going down
-    for (; top - CH + 1 >= 0; top -= CH) {
-        Ta dv[CH], c[CH];
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            const size_t o = (size_t)(top - k) * plane + idx;
-            dv[k] = scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o);
-            c[k] = (Ta)cpr[o];
+        Ta w = d;
+        data[(size_t)(Nz - 1) * plane + idx] = (Td)w;
+        int top = Nz - 2;  // next plane to solve, going down
+        for (; top - CH + 1 >= 0; top -= CH) {
+            Ta dv[CH], c[CH];
+    #pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                const size_t o = (size_t)(top - k) * plane + idx;
+                dv[k] = scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o);
+                c[k] = (Ta)cpr[o];
+            }
+    #pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                w = dv[k] - c[k] * w;
+                dv[k] = w;
+            }
+    #pragma unroll
+            for (int k = 0; k < CH; ++k) data[(size_t)(top - k) * plane + idx] = (Td)dv[k];
         }
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            w = dv[k] - c[k] * w;
-            dv[k] = w;
+        for (; top >= 0; --top) {
+            const size_t o = (size_t)top * plane + idx;
+            const Ta dd = scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o);
+            w = dd - (Ta)cpr[o] * w;
+            data[o] = (Td)w;
         }
-#pragma unroll
-        for (int k = 0; k < CH; ++k) data[(size_t)(top - k) * plane + idx] = (Td)dv[k];
-    }
-    for (; top >= 0; --top) {
-        const size_t o = (size_t)top * plane + idx;
-        const Ta dd = scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o);
-        w = dd - (Ta)cpr[o] * w;
-        data[o] = (Td)w;
+    } else {
+        // software-pipelined: the loads of chunk c + 1 are issued before the
+        // dependent chain and the stores of chunk c (the in-place stores would
+        // otherwise keep the compiler from moving them up)
+        Ta d = (Ta)0;
+        const int nfull = Nz / CH;
+        {
+            Ta r[CH], a[CH], b[CH];
+            if (nfull > 0) {
+    #pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    const size_t o = (size_t)k * plane + idx;
+                    r[k] = (Ta)ldc<COH>(data + o);
+                    a[k] = (Ta)alpha[o];
+                    b[k] = (Ta)beta[o];
+                }
+            }
+            for (int c = 0; c < nfull; ++c) {
+                const bool more = c + 1 < nfull;
+                Ta r2[CH], a2[CH], b2[CH];
+    #pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    const size_t o = (size_t)((c + 1) * CH + k) * plane + idx;
+                    r2[k] = more ? (Ta)ldc<COH>(data + o) : (Ta)0;
+                    a2[k] = more ? (Ta)alpha[o] : (Ta)0;
+                    b2[k] = more ? (Ta)beta[o] : (Ta)0;
+                }
+    #pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    d = a[k] * r[k] - b[k] * d;
+                    r[k] = d;
+                }
+    #pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    const size_t o = (size_t)(c * CH + k) * plane + idx;
+                    if (scratch)
+                        scratch[o] = r[k];
+                    else
+                        data[o] = (Td)r[k];
+                }
+    #pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    r[k] = r2[k];
+                    a[k] = a2[k];
+                    b[k] = b2[k];
+                }
+            }
+        }
+        for (int l = nfull * CH; l < Nz; ++l) {
+            const size_t o = (size_t)l * plane + idx;
+            d = (Ta)alpha[o] * (Ta)ldc<COH>(data + o) - (Ta)beta[o] * d;
+            if (scratch)
+                scratch[o] = d;
+            else
+                data[o] = (Td)d;
+        }
+        Ta w = d;
+        data[(size_t)(Nz - 1) * plane + idx] = (Td)w;
+        // back substitution, planes Nz-2 down to 0, in chunks of CH (tail first)
+        const int nb = Nz - 1;             // planes left to solve
+        const int ntail = nb % CH;
+        int top = Nz - 2;
+        for (int t = 0; t < ntail; ++t, --top) {
+            const size_t o = (size_t)top * plane + idx;
+            const Ta dd = scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o);
+            w = dd - (Ta)cpr[o] * w;
+            data[o] = (Td)w;
+        }
+        const int nbf = nb / CH;           // full chunks, top planes first
+        {
+            Ta dv[CH], cc[CH];
+            if (nbf > 0) {
+    #pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    const size_t o = (size_t)(top - k) * plane + idx;
+                    dv[k] = scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o);
+                    cc[k] = (Ta)cpr[o];
+                }
+            }
+            for (int c = 0; c < nbf; ++c, top -= CH) {
+                const bool more = c + 1 < nbf;
+                Ta dv2[CH], cc2[CH];
+    #pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    const size_t o = (size_t)(more ? top - CH - k : top - k) * plane + idx;
+                    dv2[k] = more ? (scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o)) : (Ta)0;
+                    cc2[k] = more ? (Ta)cpr[o] : (Ta)0;
+                }
+    #pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    w = dv[k] - cc[k] * w;
+                    dv[k] = w;
+                }
+    #pragma unroll
+                for (int k = 0; k < CH; ++k) data[(size_t)(top - k) * plane + idx] = (Td)dv[k];
+    #pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                    dv[k] = dv2[k];
+                    cc[k] = cc2[k];
+                }
+            }
+        }
     }
 }
 

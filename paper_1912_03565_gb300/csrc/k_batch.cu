@@ -25,7 +25,7 @@ struct hs_batch_s {
     int *d_ctr;                       // [0] next, [1] err, then done counters
     int nitems, nworks;
     int variant;                      // index into kVariants
-    int grid[2];                      // resident CTAs of each variant
+    int grid[4];                      // resident CTAs of each variant
     size_t smem;
     long long spin_limit;
     double tol;
@@ -41,9 +41,17 @@ struct hs_batch_s {
 
 namespace {
 
-// The kernel variants: CTAs per SM the registers are capped for.
-constexpr int kNumVariants = 2;
-const void *variant_fn(int v) { return v == 0 ? batch_kernel_v2() : batch_kernel_v3(); }
+// The kernel variants: 0/1 staged transform tiles, registers capped for 2/3
+// CTAs per SM; 2/3 the same with the fused transform tiles.
+constexpr int kNumVariants = 4;
+const void *variant_fn(int v) {
+    switch (v) {
+        case 0: return batch_kernel_v2();
+        case 1: return batch_kernel_v3();
+        case 2: return batch_kernel_v2f();
+        default: return batch_kernel_v3f();
+    }
+}
 
 void drop_graph(hs_batch_s *B) {
     if (B->have_graph) {

@@ -1,9 +1,12 @@
-// Persistent batch kernel, register cap for 3 resident CTAs of 256 threads per SM.
+// Persistent batch kernel: register cap for 3 resident CTAs of 256 threads per
+// SM, staged transform tiles.
 #include "hs_batch.cuh"
 
 namespace hs_batch {
 
-__global__ void __launch_bounds__(256, 3) batch_kernel3(BatchArgs A) { batch_body(A); }
+__global__ void __launch_bounds__(256, 3) batch_kernel3(BatchArgs A) {
+    batch_body<false>(A);
+}
 
 const void *batch_kernel_v3() { return reinterpret_cast<const void *>(&batch_kernel3); }
 

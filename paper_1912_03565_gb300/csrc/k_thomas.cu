@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) thomas64_kernel(int Nx, int Ny, int Nz,
     const size_t plane = (size_t)Nx * Ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= plane) return;
-    thomas_column<double, double, double>(Nz, plane, idx, data, (double *)nullptr, fac,
+    thomas_column<double, double, double, false, false>(Nz, plane, idx, data, (double *)nullptr, fac,
                                           fac + (size_t)Nz * plane, fac + 2 * (size_t)Nz * plane);
 }
 
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) thomas32_kernel(int Nx, int Ny, int Nz,
     const size_t plane = (size_t)Nx * Ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= plane) return;
-    thomas_column<float, double, double>(Nz, plane, idx, data, scratch, fac,
+    thomas_column<float, double, double, false, false>(Nz, plane, idx, data, scratch, fac,
                                          fac + (size_t)Nz * plane, fac + 2 * (size_t)Nz * plane);
 }
 

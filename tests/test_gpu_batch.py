@@ -214,15 +214,16 @@ def test_batch_residual_precision_auto():
 
 
 def test_batch_kernel_variants_and_autotune():
-    """Both persistent-kernel variants (register caps for 2 and 3 CTAs per SM)
-    give the stand-alone results; the autotuner times them and keeps one."""
+    """Every persistent-kernel variant (register caps for 2 and 3 CTAs per SM,
+    staged or fused transform tiles) gives the stand-alone results; the
+    autotuner times them and keeps one."""
     torch = pytest.importorskip("torch")
     specs = _specs(seed=14, n=4)
     probs, _ = _make(torch, specs)
     b = H.hs_batch_create(probs, H.HS_F32, 1)
     try:
         outs = []
-        for v in (0, 1):
+        for v in (0, 1, 2, 3):
             H.hs_batch_set_variant(b, v)
             assert H.hs_batch_get_variant(b)[0] == v
             assert H.hs_batch_get_variant(b)[1] >= 1
@@ -230,15 +231,16 @@ def test_batch_kernel_variants_and_autotune():
                 p["u"].fill_(np.nan)
             H.hs_batch_solve(b, sync=True)
             outs.append([p["u"].clone() for p in probs])
-        for a, c, pr in zip(outs[0], outs[1], probs):
+        for k, pr in enumerate(probs):
             ref = _single(torch, pr, 0, 1)
-            for x in (a, c):
+            for v in range(4):
+                x = outs[v][k]
                 d = float((x[0] - ref).abs().max()) / float(ref.abs().max())
-                assert d <= 1e-14, d
+                assert d <= 1e-14, (v, k, d)
         ms = H.hs_batch_autotune(b, reps=1)
         assert ms > 0
-        assert H.hs_batch_get_variant(b)[0] in (0, 1)
+        assert H.hs_batch_get_variant(b)[0] in (0, 1, 2, 3)
         with pytest.raises(H.HsError):
-            H.hs_batch_set_variant(b, 2)
+            H.hs_batch_set_variant(b, 4)
     finally:
         H.hs_batch_destroy(b)
