@@ -329,11 +329,18 @@ hs_status hs_batch_set_residual_precision(hs_batch_t batch, int mode);
  * variant: 0 = staged transform tiles, registers capped for 2 resident CTAs
  * (256 threads) per SM; 1 = staged, capped for 3; 2 = fused transform tiles
  * (first stage from global memory, x pairing by shuffles), 2 CTAs; 3 = fused,
- * 3 CTAs.  The grid is every CTA the variant can keep resident.  Default: the
- * first variant that fits.  Errors: HS_ERR_INVALID_ARG; HS_ERR_UNSUPPORTED
- * (variant cannot be resident with this batch's shared memory). */
+ * 3 CTAs; 4 = no persistent kernel: every problem's stand-alone mixed solve
+ * (one per RHS) captured into one graph on up to 8 parallel branches, each
+ * stage at its own kernel's occupancy (grid reported as 1).  For 0-3 the grid
+ * is every CTA the variant can keep resident.  Default: the first persistent
+ * variant that fits.  Errors: HS_ERR_INVALID_ARG; HS_ERR_UNSUPPORTED (variant
+ * cannot be resident with this batch's shared memory). */
 hs_status hs_batch_set_variant(hs_batch_t batch, int variant);
 hs_status hs_batch_get_variant(hs_batch_t batch, int *variant, int *grid);
+
+/* hs_batch_graph_kernels -- kernel launches per hs_batch_solve: the kernel
+ * nodes of the captured graph (0 before the first solve of the variant). */
+hs_status hs_batch_graph_kernels(hs_batch_t batch, int *kernels);
 
 /* hs_batch_autotune -- times `reps` solves of the batch (after one warm-up)
  * with each kernel variant on `stream` and keeps the fastest; *ms (may be

@@ -48,6 +48,7 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_batch_set_io", "hs_batch_solve", "hs_batch_set_wait_limit", "hs_batch_set_tol",
             "hs_batch_set_residual_precision", "hs_batch_debug_stall", "hs_set_residual_precision",
             "hs_batch_set_variant", "hs_batch_get_variant", "hs_batch_autotune",
+            "hs_batch_graph_kernels",
             "hs_set_transform_variant", "hs_get_transform_variant", "hs_autotune",
             "hs_batch_workspace_bytes", "hs_batch_destroy")
 HS_STATIC_MAX_NZ = 8192
@@ -138,6 +139,8 @@ def load(path: Optional[str] = None):
     lib.hs_batch_set_variant.restype = ci
     lib.hs_batch_get_variant.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci)]
     lib.hs_batch_get_variant.restype = ci
+    lib.hs_batch_graph_kernels.argtypes = [vp, ctypes.POINTER(ci)]
+    lib.hs_batch_graph_kernels.restype = ci
     lib.hs_batch_autotune.argtypes = [vp, vp, ci, ctypes.POINTER(ctypes.c_float)]
     lib.hs_batch_autotune.restype = ci
     lib.hs_batch_set_residual_precision.argtypes = [vp, ci]
@@ -380,6 +383,13 @@ def hs_batch_get_variant(batch):
     _check(load().hs_batch_get_variant(batch, ctypes.byref(v), ctypes.byref(g)),
            "hs_batch_get_variant")
     return v.value, g.value
+
+
+def hs_batch_graph_kernels(batch):
+    """Kernel launches per hs_batch_solve (kernel nodes of the captured graph)."""
+    k = ctypes.c_int()
+    _check(load().hs_batch_graph_kernels(batch, ctypes.byref(k)), "hs_batch_graph_kernels")
+    return k.value
 
 
 def hs_batch_autotune(batch, stream=None, reps=2):

@@ -3,6 +3,7 @@
 // scheduling scheme are in hs_batch.cuh.
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -25,7 +26,9 @@ struct hs_batch_s {
     int *d_ctr;                       // [0] next, [1] err, then done counters
     int nitems, nworks;
     int variant;                      // index into kVariants
-    int grid[4];                      // resident CTAs of each variant
+    int grid[5];                      // resident CTAs of each variant (graph mode: 1)
+    int graph_warm;                   // graph mode: plans have solved once outside capture
+    int graph_kernels;                // kernel nodes in the captured graph
     size_t smem;
     long long spin_limit;
     double tol;
@@ -43,13 +46,16 @@ namespace {
 
 // The kernel variants: 0/1 staged transform tiles, registers capped for 2/3
 // CTAs per SM; 2/3 the same with the fused transform tiles.
-constexpr int kNumVariants = 4;
+constexpr int kNumVariants = 5;
+constexpr int kGraphVariant = 4;   // stand-alone solves in one graph (no persistent kernel)
+constexpr int kGraphBranches = 8;
 const void *variant_fn(int v) {
     switch (v) {
         case 0: return batch_kernel_v2();
         case 1: return batch_kernel_v3();
         case 2: return batch_kernel_v2f();
-        default: return batch_kernel_v3f();
+        case 3: return batch_kernel_v3f();
+        default: return nullptr;
     }
 }
 
@@ -98,6 +104,154 @@ void free_batch(hs_batch_s *B) {
     delete B;
 }
 
+
+int count_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return -1;
+    int k = 0;
+    for (cudaGraphNode_t v : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(v, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
+// The persistent launch: counter resets and one kernel, captured as a graph.
+hs_status capture_persistent(hs_batch_s *B) {
+    BatchArgs A;
+    A.works = B->d_works;
+    A.items = B->d_items;
+    A.nitems = B->nitems;
+    A.next = B->d_ctr;
+    A.err = B->d_ctr + 1;
+    A.done = B->d_ctr + 2;
+    A.spin_limit = B->spin_limit;
+    A.f_is_f64 = B->f_dtype == HS_F64;
+    A.tol2 = B->tol * B->tol;
+    A.resid_mode = B->resid_mode;
+    A.norms_on = B->sweeps >= 1 && (B->tol > 0.0 ||
+                                     (B->resid_mode == HS_RESID_AUTO && B->sweeps >= 2));
+    A.stages = B->stages;
+    for (int k = 0; k < BMAX_STAGES; ++k) A.sweep_of[k] = B->sweep_of[k];
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return HS_ERR_CUDA;
+    }
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        cudaMemsetAsync(B->d_ctr, 0, (2 + (size_t)B->nworks * BMAX_STAGES) * sizeof(int), cs);
+        cudaMemsetAsync(B->d_norms, 0,
+                        (size_t)B->nworks * (HS_INFO_MAX_ITERS + 1) * sizeof(double), cs);
+        void *args[] = {&A};
+        cudaLaunchKernel(variant_fn(B->variant), dim3(B->grid[B->variant]), dim3(256), args,
+                         B->smem, cs);
+        ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && g;
+    }
+    if (ok) B->graph_kernels = count_kernel_nodes(g);
+    ok = ok && cudaGraphInstantiate(&B->graph, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (!ok) {
+        cudaGetLastError();
+        return HS_ERR_CUDA;
+    }
+    B->have_graph = 1;
+    return HS_OK;
+}
+
+// The other execution: every problem's stand-alone mixed solve (one per RHS,
+// the plans the batch already holds) captured into one graph on up to 8
+// parallel branches, problems assigned largest first to the least-loaded
+// branch.  Each stage then runs at its own kernel's occupancy and small
+// problems overlap; the queue, counters and waits are not used.
+hs_status capture_solves(hs_batch_s *B) {
+    const int nb = B->n < kGraphBranches ? B->n : kGraphBranches;
+    for (hs_plan_t P : B->plans) {
+        hs_status st;
+        if ((st = hs_set_refinement(P, B->sweeps)) != HS_OK ||
+            (st = hs_set_refinement_tol(P, B->tol)) != HS_OK ||
+            (st = hs_set_residual_precision(P, B->resid_mode)) != HS_OK)
+            return st;
+    }
+    if (!B->graph_warm) {
+        // one solve per problem outside capture: first-launch attributes and any
+        // lazily created buffers exist before the capture
+        for (int k = 0; k < B->n; ++k) {
+            const BatchWork &W = B->works[B->work_of[k]];
+            const hs_status st = hs_solve(B->plans[k], W.f, B->f_dtype, HS_RHS_NODAL, nullptr,
+                                          W.u, 1, nullptr, nullptr);
+            if (st < 0) return st;
+        }
+        if (cudaDeviceSynchronize() != cudaSuccess) {
+            cudaGetLastError();
+            return HS_ERR_CUDA;
+        }
+        B->graph_warm = 1;
+    }
+    std::vector<int> order(B->n);
+    for (int k = 0; k < B->n; ++k) order[k] = k;
+    auto work = [&](int k) {
+        const hs_plan_s *P = B->plans[k];
+        return (double)P->Nx * P->Ny * P->Nz * B->nrhs[k];
+    };
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    std::vector<double> load(nb, 0.0);
+    std::vector<int> branch_of(B->n, 0);
+    for (int k : order) {
+        int best = 0;
+        for (int b = 1; b < nb; ++b)
+            if (load[b] < load[best]) best = b;
+        branch_of[k] = best;
+        load[best] += work(k);
+    }
+    cudaStream_t cs;
+    std::vector<cudaStream_t> br(nb, nullptr);
+    std::vector<cudaEvent_t> ev(nb + 1, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; ok && b < nb; ++b)
+        ok = cudaStreamCreateWithFlags(&br[b], cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; ok && b <= nb; ++b)
+        ok = cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming) == cudaSuccess;
+    cudaGraph_t g = nullptr;
+    hs_status st = HS_OK;
+    if (ok) ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        cudaMemsetAsync(B->d_ctr + 1, 0, sizeof(int), cs);   // no stale timeout flag
+        cudaEventRecord(ev[nb], cs);
+        for (int b = 0; b < nb; ++b) cudaStreamWaitEvent(br[b], ev[nb], 0);
+        for (int k : order) {
+            for (int r = 0; r < B->nrhs[k] && st >= 0; ++r) {
+                const BatchWork &W = B->works[B->work_of[k] + r];
+                st = hs_solve(B->plans[k], W.f, B->f_dtype, HS_RHS_NODAL, nullptr, W.u, 1,
+                              br[branch_of[k]], nullptr);
+            }
+        }
+        for (int b = 0; b < nb; ++b) {
+            cudaEventRecord(ev[b], br[b]);
+            cudaStreamWaitEvent(cs, ev[b], 0);
+        }
+        ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && g && st >= 0;
+    }
+    if (ok) B->graph_kernels = count_kernel_nodes(g);
+    ok = ok && cudaGraphInstantiate(&B->graph, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    for (int b = 0; b <= nb; ++b)
+        if (ev[b]) cudaEventDestroy(ev[b]);
+    for (int b = 0; b < nb; ++b)
+        if (br[b]) cudaStreamDestroy(br[b]);
+    cudaStreamDestroy(cs);
+    if (!ok) {
+        cudaGetLastError();
+        return st < 0 ? st : HS_ERR_CUDA;
+    }
+    B->have_graph = 1;
+    return HS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -126,6 +280,8 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
     B->tol = 0.0;
     B->resid_mode = HS_RESID_AUTO;
     B->have_graph = 0;
+    B->graph_warm = 0;
+    B->graph_kernels = 0;
     B->graph_stream = nullptr;
     B->bytes = 0;
     B->spin_limit = 20000000;  // ~2 s of 100 ns naps before a wait gives up
@@ -301,6 +457,10 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
     for (int v = 0; v < kNumVariants; ++v) {
         int per = 0;
         B->grid[v] = 0;
+        if (v == kGraphVariant) {
+            B->grid[v] = 1;
+            continue;
+        }
         if (cudaFuncSetAttribute(variant_fn(v), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, variant_fn(v), 256, smem) !=
@@ -336,6 +496,7 @@ hs_status hs_batch_set_io(hs_batch_t B, int k, const void *f, double *u) {
         cudaGetLastError();
         return HS_ERR_CUDA;
     }
+    drop_graph(B);   // the graph mode captures the pointers
     return HS_OK;
 }
 
@@ -373,6 +534,12 @@ hs_status hs_batch_get_variant(hs_batch_t B, int *variant, int *grid) {
     if (!B) return HS_ERR_INVALID_ARG;
     if (variant) *variant = B->variant;
     if (grid) *grid = B->grid[B->variant];
+    return HS_OK;
+}
+
+hs_status hs_batch_graph_kernels(hs_batch_t B, int *kernels) {
+    if (!B || !kernels) return HS_ERR_INVALID_ARG;
+    *kernels = B->have_graph ? B->graph_kernels : 0;
     return HS_OK;
 }
 
@@ -435,45 +602,8 @@ hs_status hs_batch_solve(hs_batch_t B, void *stream, int sync) {
     if (!B->have_graph || B->graph_stream != s) {
         if (B->have_graph) cudaGraphExecDestroy(B->graph);
         B->have_graph = 0;
-        BatchArgs A;
-        A.works = B->d_works;
-        A.items = B->d_items;
-        A.nitems = B->nitems;
-        A.next = B->d_ctr;
-        A.err = B->d_ctr + 1;
-        A.done = B->d_ctr + 2;
-        A.spin_limit = B->spin_limit;
-        A.f_is_f64 = B->f_dtype == HS_F64;
-        A.tol2 = B->tol * B->tol;
-        A.resid_mode = B->resid_mode;
-        A.norms_on = B->sweeps >= 1 && (B->tol > 0.0 ||
-                                         (B->resid_mode == HS_RESID_AUTO && B->sweeps >= 2));
-        A.stages = B->stages;
-        for (int k = 0; k < BMAX_STAGES; ++k) A.sweep_of[k] = B->sweep_of[k];
-        cudaStream_t cs;
-        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            return HS_ERR_CUDA;
-        }
-        cudaGraph_t g = nullptr;
-        bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-        if (ok) {
-            cudaMemsetAsync(B->d_ctr, 0, (2 + (size_t)B->nworks * BMAX_STAGES) * sizeof(int), cs);
-            cudaMemsetAsync(B->d_norms, 0,
-                            (size_t)B->nworks * (HS_INFO_MAX_ITERS + 1) * sizeof(double), cs);
-            void *args[] = {&A};
-            cudaLaunchKernel(variant_fn(B->variant), dim3(B->grid[B->variant]), dim3(256), args,
-                             B->smem, cs);
-            ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && g;
-        }
-        ok = ok && cudaGraphInstantiate(&B->graph, g, 0) == cudaSuccess;
-        if (g) cudaGraphDestroy(g);
-        cudaStreamDestroy(cs);
-        if (!ok) {
-            cudaGetLastError();
-            return HS_ERR_CUDA;
-        }
-        B->have_graph = 1;
+        const hs_status st = B->variant == kGraphVariant ? capture_solves(B) : capture_persistent(B);
+        if (st != HS_OK) return st;
         B->graph_stream = s;
     }
     if (cudaGraphLaunch(B->graph, s) != cudaSuccess) {

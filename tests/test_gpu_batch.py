@@ -213,34 +213,63 @@ def test_batch_residual_precision_auto():
             H.hs_batch_destroy(b)
 
 
+def test_batch_graph_mode_all_rhs_and_tolerance():
+    """The graph execution (variant 4) solves every RHS of every problem like the
+    stand-alone solver, also with a tolerance, and after new output buffers."""
+    torch = pytest.importorskip("torch")
+    specs = _specs(seed=15, n=5)
+    probs, _ = _make(torch, specs)
+    b = H.hs_batch_create(probs, H.HS_F32, 2)
+    try:
+        H.hs_batch_set_variant(b, 4)
+        H.hs_batch_solve(b, sync=True)
+        H.hs_batch_solve(b, sync=True)
+        nsolves = sum(pr["nrhs"] for pr in probs)
+        assert H.hs_batch_graph_kernels(b) >= 12 * nsolves   # >= 12 kernels per 2-sweep solve
+        for k, pr in enumerate(probs):
+            for r in range(pr["nrhs"]):
+                ref = _single(torch, pr, r, 2)
+                d = float((pr["u"][r] - ref).abs().max()) / float(ref.abs().max())
+                assert d <= 1e-14, (k, r, d)
+        u2 = torch.zeros_like(probs[0]["u"])
+        H.hs_batch_set_io(b, 0, probs[0]["f"], u2)
+        H.hs_batch_solve(b, sync=True)
+        assert torch.equal(u2, probs[0]["u"])
+    finally:
+        H.hs_batch_destroy(b)
+
+
 def test_batch_kernel_variants_and_autotune():
-    """Every persistent-kernel variant (register caps for 2 and 3 CTAs per SM,
-    staged or fused transform tiles) gives the stand-alone results; the
-    autotuner times them and keeps one."""
+    """Every execution variant (persistent kernel with register caps for 2 and 3
+    CTAs per SM, staged or fused transform tiles; or the graph of stand-alone
+    solves) gives the stand-alone results; the autotuner times them and keeps
+    one."""
     torch = pytest.importorskip("torch")
     specs = _specs(seed=14, n=4)
     probs, _ = _make(torch, specs)
     b = H.hs_batch_create(probs, H.HS_F32, 1)
     try:
         outs = []
-        for v in (0, 1, 2, 3):
+        for v in (0, 1, 2, 3, 4):
             H.hs_batch_set_variant(b, v)
             assert H.hs_batch_get_variant(b)[0] == v
             assert H.hs_batch_get_variant(b)[1] >= 1
             for p in probs:
                 p["u"].fill_(np.nan)
             H.hs_batch_solve(b, sync=True)
+            if v < 4:
+                assert H.hs_batch_graph_kernels(b) == 1   # the persistent kernel
             outs.append([p["u"].clone() for p in probs])
         for k, pr in enumerate(probs):
             ref = _single(torch, pr, 0, 1)
-            for v in range(4):
+            for v in range(5):
                 x = outs[v][k]
                 d = float((x[0] - ref).abs().max()) / float(ref.abs().max())
                 assert d <= 1e-14, (v, k, d)
         ms = H.hs_batch_autotune(b, reps=1)
         assert ms > 0
-        assert H.hs_batch_get_variant(b)[0] in (0, 1, 2, 3)
+        assert H.hs_batch_get_variant(b)[0] in (0, 1, 2, 3, 4)
         with pytest.raises(H.HsError):
-            H.hs_batch_set_variant(b, 4)
+            H.hs_batch_set_variant(b, 5)
     finally:
         H.hs_batch_destroy(b)
