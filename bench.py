@@ -492,6 +492,10 @@ def main():
     ap.add_argument("--sweeps", type=int, default=-1,
                     help="refinement sweeps; -1 = the fewest whose error is <= 1e-10")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", default="",
+                    help="mixed plan: transform variant x,y[,z-solve mapping] instead of autotuning")
+    ap.add_argument("--variants64", default="",
+                    help="FP64 plan: transform variant x,y instead of autotuning")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "hs":
@@ -541,13 +545,25 @@ def main():
         s.set_coeff(*wk.c, wk.cd)
         if precision == H.HS_MIXED:
             H.hs_set_refinement(s.plan, sweeps)
-        # transform kernel variant per axis, timed on this plan (set-up, untimed)
+        # transform kernel variant per axis, timed on this plan (set-up, untimed);
+        # --variants / --variants64 fix them instead (profiler runs, where the
+        # serialised launches make the autotuner's timings meaningless)
         t0 = time.perf_counter()
-        mx, my = H.hs_autotune(s.plan, stream, 3)
         name = "mixed" if precision == H.HS_MIXED else "fp64"
+        fixed = args.variants if precision == H.HS_MIXED else args.variants64
+        if fixed:
+            vals = [int(x) for x in fixed.split(",")]
+            H.hs_set_transform_variant(s.plan, H.HS_AXIS_X, vals[0])
+            H.hs_set_transform_variant(s.plan, H.HS_AXIS_Y, vals[1])
+            if len(vals) > 2:
+                H.hs_set_thomas_variant(s.plan, vals[2])
+            mx = my = None
+        else:
+            mx, my = H.hs_autotune(s.plan, stream, 3)
         tuning[name] = {"variant_x": H.hs_get_transform_variant(s.plan, H.HS_AXIS_X),
                         "variant_y": H.hs_get_transform_variant(s.plan, H.HS_AXIS_Y),
-                        "pass_ms_x": mx, "pass_ms_y": my,
+                        "thomas_variant": H.hs_get_thomas_variant(s.plan),
+                        "pass_ms_x": mx, "pass_ms_y": my, "fixed": bool(fixed),
                         "autotune_s": time.perf_counter() - t0}
         return s
 

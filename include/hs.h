@@ -64,6 +64,8 @@ enum { HS_RHS_NODAL = 0, HS_RHS_ASSEMBLED = 1 };             /* meaning of f */
 enum { HS_RESID_DF = 0, HS_RESID_F64 = 1, HS_RESID_AUTO = 2 }; /* refinement residual */
 enum { HS_DST_STAGED = 0, HS_DST_FUSED = 1, HS_DST_GENERIC = 2 };  /* transform kernels */
 enum { HS_AXIS_X = 0, HS_AXIS_Y = 1 };                       /* transform axis */
+enum { HS_THOMAS_PIPE16_256 = 0, HS_THOMAS_PIPE8_128 = 1,    /* FP32 z-solve mapping */
+       HS_THOMAS_PLAIN16_256 = 2, HS_THOMAS_PIPE16_128 = 3 };
 
 typedef struct hs_plan_s *hs_plan_t;
 
@@ -190,11 +192,28 @@ hs_status hs_set_transform_variant(hs_plan_t plan, int axis, int variant);
 hs_status hs_get_transform_variant(hs_plan_t plan, int axis, int *variant);
 
 /*
+ * hs_set_thomas_variant / hs_get_thomas_variant -- thread mapping of the FP32
+ * z-solves of an HS_MIXED plan (Section 3.6's per-mode LU; one thread per
+ * (p,q) column, z walked in chunks): HS_THOMAS_PIPE16_256 (default: 16-plane
+ * chunks, the next chunk's loads issued before the current chunk's chain,
+ * 256-thread blocks), HS_THOMAS_PIPE8_128, HS_THOMAS_PLAIN16_256 (no
+ * pipelining, fewer registers), HS_THOMAS_PIPE16_128.  Identical results.
+ * Errors: HS_ERR_INVALID_ARG.
+ */
+hs_status hs_set_thomas_variant(hs_plan_t plan, int variant);
+hs_status hs_get_thomas_variant(hs_plan_t plan, int *variant);
+
+/*
  * hs_autotune -- times one forward transform pass per supported variant and
- * axis (`reps` launches after one untimed) on the plan's own work buffer
- * (overwritten) on `stream`, and keeps the fastest variant of each axis;
- * *ms_x, *ms_y (may be NULL) receive the kept variants' times per pass.
- * Synchronous.  Call after hs_plan, before solves (not during capture).
+ * axis (`reps` rounds after one untimed; for x of an HS_MIXED plan a round is a
+ * forward pass plus the two inverse passes of a refined solve, pair set and
+ * final u) on the plan's own work buffers (overwritten) on `stream`, and keeps
+ * the fastest
+ * variant of each axis; *ms_x, *ms_y (may be NULL) receive the kept variants'
+ * times per round.  For an
+ * HS_MIXED plan whose coefficients are set and whose factors are FP32, the
+ * z-solve mappings are timed the same way and the fastest kept.
+ * Synchronous.  Call after hs_set_coeff, before solves (not during capture).
  */
 hs_status hs_autotune(hs_plan_t plan, void *stream, int reps, float *ms_x, float *ms_y);
 

@@ -37,6 +37,7 @@ HS_RHS_NODAL, HS_RHS_ASSEMBLED = 0, 1
 HS_RESID_DF, HS_RESID_F64, HS_RESID_AUTO = 0, 1, 2
 HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC = 0, 1, 2
 HS_AXIS_X, HS_AXIS_Y = 0, 1
+HS_THOMAS_PIPE16_256, HS_THOMAS_PIPE8_128, HS_THOMAS_PLAIN16_256, HS_THOMAS_PIPE16_128 = 0, 1, 2, 3
 HS_INFO_MAX_ITERS = 8
 HS_INFO_STAGES = 8
 STAGES = ("rhs", "dst_x", "dst_y", "thomas", "idst_y", "idst_x", "residual", "total")
@@ -50,6 +51,7 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_batch_set_variant", "hs_batch_get_variant", "hs_batch_autotune",
             "hs_batch_graph_kernels",
             "hs_set_transform_variant", "hs_get_transform_variant", "hs_autotune",
+            "hs_set_thomas_variant", "hs_get_thomas_variant",
             "hs_batch_workspace_bytes", "hs_batch_destroy")
 HS_STATIC_MAX_NZ = 8192
 
@@ -128,6 +130,10 @@ def load(path: Optional[str] = None):
     lib.hs_batch_solve.restype = ci
     lib.hs_batch_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     lib.hs_batch_set_wait_limit.restype = ci
+    lib.hs_set_thomas_variant.argtypes = [vp, ci]
+    lib.hs_set_thomas_variant.restype = ci
+    lib.hs_get_thomas_variant.argtypes = [vp, ctypes.POINTER(ci)]
+    lib.hs_get_thomas_variant.restype = ci
     lib.hs_set_transform_variant.argtypes = [vp, ci, ci]
     lib.hs_set_transform_variant.restype = ci
     lib.hs_get_transform_variant.argtypes = [vp, ci, ctypes.POINTER(ci)]
@@ -356,6 +362,16 @@ def hs_batch_set_residual_precision(batch, mode):
 def hs_set_transform_variant(plan, axis, variant):
     return _check(load().hs_set_transform_variant(plan, int(axis), int(variant)),
                   "hs_set_transform_variant", plan)
+
+
+def hs_set_thomas_variant(plan, variant):
+    return _check(load().hs_set_thomas_variant(plan, int(variant)), "hs_set_thomas_variant", plan)
+
+
+def hs_get_thomas_variant(plan):
+    v = ctypes.c_int()
+    _check(load().hs_get_thomas_variant(plan, ctypes.byref(v)), "hs_get_thomas_variant", plan)
+    return v.value
 
 
 def hs_get_transform_variant(plan, axis):

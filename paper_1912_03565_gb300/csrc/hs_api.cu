@@ -683,6 +683,19 @@ hs_status hs_set_transform_variant(hs_plan_t P, int axis, int variant) {
     return HS_OK;
 }
 
+hs_status hs_set_thomas_variant(hs_plan_t P, int variant) {
+    if (!P || variant < HS_THOMAS_PIPE16_256 || variant > HS_THOMAS_PIPE16_128)
+        return HS_ERR_INVALID_ARG;
+    P->thomas_variant = variant;
+    return HS_OK;
+}
+
+hs_status hs_get_thomas_variant(hs_plan_t P, int *variant) {
+    if (!P || !variant) return HS_ERR_INVALID_ARG;
+    *variant = P->thomas_variant;
+    return HS_OK;
+}
+
 hs_status hs_get_transform_variant(hs_plan_t P, int axis, int *variant) {
     if (!P || !variant || (axis != HS_AXIS_X && axis != HS_AXIS_Y)) return HS_ERR_INVALID_ARG;
     *variant = P->dst_variant[axis];
@@ -698,6 +711,7 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
     if (!w) return HS_ERR_INVALID_ARG;
     const size_t n = interior_count(P);
     HS_CK(P, cudaMemsetAsync(w, 0, n * (mixed ? sizeof(float) : sizeof(double)), s));
+    if (mixed && P->d_Udf) HS_CK(P, cudaMemsetAsync(P->d_Udf, 0, 2 * n * sizeof(float), s));
     cudaEvent_t e0, e1;
     HS_CK(P, cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -711,12 +725,28 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
         int best = -1;
         for (int v = HS_DST_STAGED; v <= HS_DST_GENERIC && st == HS_OK; ++v) {
             if (hs_set_transform_variant(P, axis, v) != HS_OK) continue;
-            // one untimed pass (first launch, attribute set-up), then `reps` timed
-            st = hs_launch_dst(P, axis, tc, tc, w, tc, w, HS_MODE_WRITE, 1.0, s);
+            // one untimed round (first launch, attribute set-up), then `reps`
+            // timed.  x of a mixed plan: a forward pass and an inverse pass that
+            // adds into the pair iterate (the two uses of the x kernels per sweep)
+            auto one_round = [&]() {
+                hs_status q = hs_launch_dst(P, axis, tc, tc, w, tc, w, HS_MODE_WRITE, 1.0, s);
+                if (q == HS_OK && mixed && axis == HS_AXIS_X && P->d_Udf && P->d_Fdf) {
+                    // the inverse x passes of a refined solve: set the pair iterate, then
+                    // the final u = U + correction (written into F's storage, which
+                    // holds n doubles and is rebuilt by every solve)
+                    q = hs_launch_dst(P, axis, tc, tc, w, HS_T_DF, P->d_Udf, HS_MODE_DF_SET,
+                                      1.0, s);
+                    if (q == HS_OK)
+                        q = hs_launch_dst(P, axis, tc, tc, w, HS_T_DF, P->d_Udf,
+                                          HS_MODE_DF_FINAL, 1.0, s,
+                                          reinterpret_cast<double *>(P->d_Fdf));
+                }
+                return q;
+            };
+            st = one_round();
             if (st != HS_OK) break;
             cudaEventRecord(e0, s);
-            for (int r = 0; r < reps && st == HS_OK; ++r)
-                st = hs_launch_dst(P, axis, tc, tc, w, tc, w, HS_MODE_WRITE, 1.0, s);
+            for (int r = 0; r < reps && st == HS_OK; ++r) st = one_round();
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) st = HS_ERR_CUDA;
             float ms = 0.f;
@@ -728,6 +758,27 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
             }
         }
         P->dst_variant[axis] = best >= 0 ? best : saved;
+    }
+    if (st == HS_OK && mixed && P->have_coeff && P->thomas32) {
+        int best = -1;
+        float best_t = 0.f;
+        for (int v = HS_THOMAS_PIPE16_256; v <= HS_THOMAS_PIPE16_128 && st == HS_OK; ++v) {
+            P->thomas_variant = v;
+            st = hs_launch_thomas(P, HS_T_F32, w, P->d_dscr, s);
+            if (st != HS_OK) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && st == HS_OK; ++r)
+                st = hs_launch_thomas(P, HS_T_F32, w, P->d_dscr, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = HS_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st == HS_OK && (best < 0 || ms < best_t)) {
+                best = v;
+                best_t = ms;
+            }
+        }
+        P->thomas_variant = best >= 0 ? best : HS_THOMAS_PIPE16_256;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

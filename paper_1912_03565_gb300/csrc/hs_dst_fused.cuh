@@ -142,6 +142,20 @@ __device__ __forceinline__ void dst_fused_tile(const Tin *in, Tout *out, double 
             const bool live = inl && s < nel_rows;
             Tout *orow = out + base + (size_t)s * N;
             double *arow = aux ? aux + base + (size_t)s * N : nullptr;
+            constexpr bool RMW = MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL;
+            // read-modify-write modes: every (hi, lo) of this lane's outputs is
+            // loaded before the first store (the stores could alias the loads as
+            // far as the compiler knows, which would serialise them)
+            float uh[RMW ? RL : 1], ul[RMW ? RL : 1];
+            if constexpr (RMW) {
+#pragma unroll
+                for (int r = 0; r < RL; ++r) {
+                    const int K = j + NsL * r;
+                    const bool ok = live && K > 0;
+                    uh[r] = ok ? ldc<COH>(orow + (K - 1)) : 0.f;
+                    ul[r] = ok ? ldc<COH>(orow + (K - 1) + lo_off) : 0.f;
+                }
+            }
 #pragma unroll
             for (int r = 0; r < RL; ++r) {
                 // partner of K = j + NsL r is M - K = (NsL - j) + NsL (RL - 1 - r) (j > 0),
@@ -155,7 +169,20 @@ __device__ __forceinline__ void dst_fused_tile(const Tin *in, Tout *out, double 
                     const float2 cs = half[K];
                     const float X =
                         ((Wm.y - Wk.y) + cs.x * (Wk.x - Wm.x) + cs.y * (Wk.y + Wm.y)) * q;
-                    hs_emit<Tout, MODE>(orow, arow, lo_off, (size_t)(K - 1), (double)X);
+                    if constexpr (RMW) {
+                        dfloat a;
+                        a.hi = uh[r];
+                        a.lo = ul[r];
+                        const dfloat sum = df_add(a, df_of(X));
+                        if constexpr (MODE == HS_MODE_DF_ADD) {
+                            orow[K - 1] = sum.hi;
+                            orow[K - 1 + lo_off] = sum.lo;
+                        } else {
+                            arow[K - 1] = (double)sum.hi + (double)sum.lo;
+                        }
+                    } else {
+                        hs_emit<Tout, MODE>(orow, arow, lo_off, (size_t)(K - 1), (double)X);
+                    }
                 }
             }
         }

@@ -48,6 +48,7 @@ struct hs_plan_s {
     const int *cur_skip;  // the flag the launchers pass on (NULL outside tolerance mode)
     int stage_timing;
     int dst_variant[2];   // per axis: HS_DST_STAGED / HS_DST_FUSED / HS_DST_GENERIC
+    int thomas_variant;   // FP32 z-solve mapping: HS_THOMAS_*
     int resid_mode;       // HS_RESID_DF / HS_RESID_F64 / HS_RESID_AUTO
     int have_coeff;
     int cd_variant;

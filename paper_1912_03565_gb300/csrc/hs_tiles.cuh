@@ -1009,7 +1009,7 @@ constexpr int CH = 16;
 // One z-solve with cached factors.  Td: data type (in place); Tf: factor type;
 // Ts: type of the forward-sweep values (kept in `scratch` when it is not null,
 // else in `data`); Ta: arithmetic type.
-template <typename Td, typename Tf, typename Ta, bool COH = false, bool PIPE = true>
+template <typename Td, typename Tf, typename Ta, bool COH = false, bool PIPE = true, int CH = hs_tiles::CH>
 __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, Td *data,
                                               Ta *scratch, const Tf *cpr, const Tf *alpha,
                                               const Tf *beta) {

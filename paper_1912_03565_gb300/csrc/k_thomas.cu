@@ -117,16 +117,26 @@ __global__ void __launch_bounds__(256) thomas32_kernel(int Nx, int Ny, int Nz,
 // recurrence, in place (Fhat in, W out).  The error this adds to the fast
 // solve, ~2^-24 times the condition of the z-system, is removed by the
 // refinement sweeps like the FP32 transform error.
-__global__ void __launch_bounds__(256) thomas_f32_kernel(int Nx, int Ny, int Nz,
-                                                          float *__restrict__ data,
-                                                          const float *__restrict__ fac,
-                                                          const int *skip) {
+template <int CHK, bool PIPE, int NT>
+__global__ void __launch_bounds__(NT) thomas_f32_kernel(int Nx, int Ny, int Nz,
+                                                        float *__restrict__ data,
+                                                        const float *__restrict__ fac,
+                                                        const int *skip) {
     if (skip && *skip) return;
     const size_t plane = (size_t)Nx * Ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= plane) return;
-    thomas_column<float, float, float>(Nz, plane, idx, data, (float *)nullptr, fac,
-                                       fac + (size_t)Nz * plane, fac + 2 * (size_t)Nz * plane);
+    thomas_column<float, float, float, false, PIPE, CHK>(Nz, plane, idx, data, (float *)nullptr,
+                                                         fac, fac + (size_t)Nz * plane,
+                                                         fac + 2 * (size_t)Nz * plane);
+}
+
+template <int CHK, bool PIPE, int NT>
+void launch_f32(const hs_plan_s *P, float *data, cudaStream_t s) {
+    const size_t plane = (size_t)P->Nx * P->Ny;
+    const unsigned blocks = (unsigned)((plane + NT - 1) / NT);
+    thomas_f32_kernel<CHK, PIPE, NT><<<blocks, NT, 0, s>>>(P->Nx, P->Ny, P->Nz, data, P->d_fac32,
+                                                          P->cur_skip);
 }
 
 }  // namespace
@@ -147,8 +157,14 @@ hs_status hs_launch_thomas(const hs_plan_s *P, int tio, void *data, double *scra
         thomas64_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, static_cast<double *>(data),
                                                P->d_fac, P->cur_skip);
     else if (P->thomas32)
-        thomas_f32_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, static_cast<float *>(data),
-                                                 P->d_fac32, P->cur_skip);
+        switch (P->thomas_variant) {
+            // thread mapping of the FP32 z-solves: one thread per (p,q) column;
+            // chunk depth, software pipelining and block size vary
+            case HS_THOMAS_PIPE8_128: launch_f32<8, true, 128>(P, static_cast<float *>(data), s); break;
+            case HS_THOMAS_PLAIN16_256: launch_f32<16, false, 256>(P, static_cast<float *>(data), s); break;
+            case HS_THOMAS_PIPE16_128: launch_f32<16, true, 128>(P, static_cast<float *>(data), s); break;
+            default: launch_f32<16, true, 256>(P, static_cast<float *>(data), s); break;
+        }
     else
         thomas32_kernel<<<blocks, 256, 0, s>>>(P->Nx, P->Ny, P->Nz, static_cast<float *>(data),
                                                scratch, P->d_fac, P->cur_skip);
