@@ -62,7 +62,8 @@ enum { HS_CD_PAPER = 0, HS_CD_CORRECTED = 1 };               /* CD coefficient v
 enum { HS_F64 = 0, HS_F32 = 1 };                             /* element type of f / faces */
 enum { HS_RHS_NODAL = 0, HS_RHS_ASSEMBLED = 1 };             /* meaning of f */
 enum { HS_RESID_DF = 0, HS_RESID_F64 = 1, HS_RESID_AUTO = 2 }; /* refinement residual */
-enum { HS_DST_STAGED = 0, HS_DST_FUSED = 1, HS_DST_GENERIC = 2 };  /* transform kernels */
+enum { HS_DST_STAGED = 0, HS_DST_FUSED = 1, HS_DST_GENERIC = 2,   /* transform kernels */
+       HS_DST_TWOPASS = 3 };
 enum { HS_AXIS_X = 0, HS_AXIS_Y = 1 };                       /* transform axis */
 enum { HS_THOMAS_PIPE16_256 = 0, HS_THOMAS_PIPE8_128 = 1,    /* FP32 z-solve mapping */
        HS_THOMAS_PLAIN16_256 = 2, HS_THOMAS_PIPE16_128 = 3 };
@@ -183,10 +184,14 @@ hs_status hs_set_refinement_tol(hs_plan_t plan, double tol);
  *                  memory and (x) the last stage paired by warp shuffles
  *                  (HS_MIXED plans only);
  *   HS_DST_GENERIC runtime-sized kernels (any length; the only choice for
- *                  lengths without compiled kernels).
+ *                  lengths without compiled kernels);
+ *   HS_DST_TWOPASS y only, HS_MIXED plans, N + 1 in {512, 768, 1024}: the FFT
+ *                  split M = 32 M2 over two kernels, every access a whole
+ *                  128-byte row segment of 32 columns; allocates a complex
+ *                  scratch of 8 bytes per unknown while selected.
  * Results agree to rounding.  Default: HS_DST_STAGED where compiled.
  * Errors: HS_ERR_INVALID_ARG; HS_ERR_UNSUPPORTED (variant not built for this
- * length or precision).
+ * length, axis or precision); HS_ERR_OOM.
  */
 hs_status hs_set_transform_variant(hs_plan_t plan, int axis, int variant);
 hs_status hs_get_transform_variant(hs_plan_t plan, int axis, int *variant);

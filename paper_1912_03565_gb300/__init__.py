@@ -35,7 +35,7 @@ HS_CD_PAPER, HS_CD_CORRECTED = 0, 1
 HS_F64, HS_F32 = 0, 1
 HS_RHS_NODAL, HS_RHS_ASSEMBLED = 0, 1
 HS_RESID_DF, HS_RESID_F64, HS_RESID_AUTO = 0, 1, 2
-HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC = 0, 1, 2
+HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC, HS_DST_TWOPASS = 0, 1, 2, 3
 HS_AXIS_X, HS_AXIS_Y = 0, 1
 HS_THOMAS_PIPE16_256, HS_THOMAS_PIPE8_128, HS_THOMAS_PLAIN16_256, HS_THOMAS_PIPE16_128 = 0, 1, 2, 3
 HS_INFO_MAX_ITERS = 8

@@ -91,12 +91,19 @@ hs_status dev_alloc(hs_plan_s *P, T **p, size_t n) {
     return HS_OK;
 }
 
+void free_ytmp(hs_plan_s *P) {
+    if (!P->d_ytmp) return;
+    cudaFree(P->d_ytmp);
+    P->bytes -= (size_t)P->Nz * P->axf[HS_AXIS_Y].M * P->Nx * 2 * sizeof(float);
+    P->d_ytmp = nullptr;
+}
+
 void free_plan(hs_plan_s *P) {
     if (!P) return;
     void *ptrs[] = {P->d_coef, P->d_c0, P->d_c1, P->d_cx, P->d_cy, P->d_fac, P->d_red,
                     P->d_tables, P->d_w64, P->d_w32, P->d_dscr, P->d_stage_f, P->d_stage_u,
                     P->d_stage_bnd, P->d_fac32, P->d_coef_df, P->d_Fdf, P->d_Udf, P->d_rhs_df,
-                    P->d_skip};
+                    P->d_skip, P->d_ytmp};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->have_events) {
@@ -674,11 +681,23 @@ hs_status hs_set_residual_precision(hs_plan_t P, int mode) {
 
 hs_status hs_set_transform_variant(hs_plan_t P, int axis, int variant) {
     if (!P || (axis != HS_AXIS_X && axis != HS_AXIS_Y)) return HS_ERR_INVALID_ARG;
-    if (variant != HS_DST_STAGED && variant != HS_DST_FUSED && variant != HS_DST_GENERIC)
-        return HS_ERR_INVALID_ARG;
+    if (variant < HS_DST_STAGED || variant > HS_DST_TWOPASS) return HS_ERR_INVALID_ARG;
     const bool fast = hs_dst_fast_size(P->axd[axis].M) != 0;
     if (variant == HS_DST_FUSED && (!fast || P->precision != HS_MIXED)) return HS_ERR_UNSUPPORTED;
     if (variant == HS_DST_STAGED && !fast) return HS_ERR_UNSUPPORTED;
+    if (variant == HS_DST_TWOPASS) {
+        if (axis != HS_AXIS_Y || P->precision != HS_MIXED ||
+            !hs_dst_twopass_size(P->axf[HS_AXIS_Y].M))
+            return HS_ERR_UNSUPPORTED;
+        if (!P->d_ytmp) {
+            const size_t n = (size_t)P->Nz * P->axf[HS_AXIS_Y].M * P->Nx * 2;   // floats
+            float *t = nullptr;
+            HS_TRY(P, dev_alloc(P, &t, n));
+            P->d_ytmp = t;
+        }
+    } else if (axis == HS_AXIS_Y && P->d_ytmp) {
+        free_ytmp(P);
+    }
     P->dst_variant[axis] = variant;
     return HS_OK;
 }
@@ -723,7 +742,7 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
     for (int axis = 0; axis < 2 && st == HS_OK; ++axis) {
         const int saved = P->dst_variant[axis];
         int best = -1;
-        for (int v = HS_DST_STAGED; v <= HS_DST_GENERIC && st == HS_OK; ++v) {
+        for (int v = HS_DST_STAGED; v <= HS_DST_TWOPASS && st == HS_OK; ++v) {
             if (hs_set_transform_variant(P, axis, v) != HS_OK) continue;
             // one untimed round (first launch, attribute set-up), then `reps`
             // timed.  x of a mixed plan: a forward pass and an inverse pass that
@@ -757,7 +776,9 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
                 best_ms[axis] = ms;
             }
         }
-        P->dst_variant[axis] = best >= 0 ? best : saved;
+        // through the setter: the two-pass scratch is kept only when chosen
+        if (hs_set_transform_variant(P, axis, best >= 0 ? best : saved) != HS_OK)
+            P->dst_variant[axis] = saved;
     }
     if (st == HS_OK && mixed && P->have_coeff && P->thomas32) {
         int best = -1;

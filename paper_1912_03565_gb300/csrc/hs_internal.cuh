@@ -49,6 +49,7 @@ struct hs_plan_s {
     int stage_timing;
     int dst_variant[2];   // per axis: HS_DST_STAGED / HS_DST_FUSED / HS_DST_GENERIC
     int thomas_variant;   // FP32 z-solve mapping: HS_THOMAS_*
+    void *d_ytmp;         // complex scratch of the two-pass y transform (Nz x M x Nx float2)
     int resid_mode;       // HS_RESID_DF / HS_RESID_F64 / HS_RESID_AUTO
     int have_coeff;
     int cd_variant;
@@ -124,6 +125,12 @@ hs_status hs_launch_dst_fused_x(const hs_plan_s *P, int tin, const void *in, int
                                 int mode, double scale, cudaStream_t s, double *aux);
 hs_status hs_launch_dst_fused_y(const hs_plan_s *P, int tin, const void *in, int tout, void *out,
                                 int mode, double scale, cudaStream_t s, double *aux);
+
+// Two-pass y transform for long lines (k_dst_twopass.cu): 1 for M in {512, 768, 1024};
+// needs P->d_ytmp.
+int hs_dst_twopass_size(int M);
+hs_status hs_launch_dst_twopass_y(const hs_plan_s *P, const float *in, float *out, double scale,
+                                  cudaStream_t s);
 
 // 1 when a line of this axis fits the transform kernel's shared memory.
 int hs_dst_fits(const DstAxis &ax, int axis, int tc);

@@ -272,7 +272,8 @@ FAST_N = [31, 63, 95, 127, 191, 255, 383, 511, 767, 1023]
 @pytest.mark.parametrize("N", FAST_N)
 @pytest.mark.parametrize("precision,variant", [(H.HS_FP64, H.HS_DST_STAGED),
                                                (H.HS_MIXED, H.HS_DST_STAGED),
-                                               (H.HS_MIXED, H.HS_DST_FUSED)])
+                                               (H.HS_MIXED, H.HS_DST_FUSED),
+                                               (H.HS_MIXED, H.HS_DST_TWOPASS)])
 def test_transform_lengths(N, precision, variant):
     """Every compile-time-sized transform length and kernel variant, along x and along
     y (ragged tiles: 9 x-lines over 5 planes, 7-column y-tiles).
@@ -294,6 +295,21 @@ def test_transform_lengths(N, precision, variant):
             assert e <= 4 * es + 1e-7 and e <= 1e-4, (e, es)
 
 
+@pytest.mark.parametrize("shape", [(40, 511, 3), (33, 1023, 2), (70, 767, 2)])
+def test_twopass_y_transform(shape):
+    """The two-pass y transform (lines of 512, 768, 1024 points, 32-column blocks
+    with a ragged last block): refined parity with the oracle, and the unrefined
+    FP32 solve as accurate as with the single-pass kernel."""
+    p = random_problem(shape, 6, W.HELMHOLTZ, seed=sum(shape))
+    ref = oracle_solve(p)
+    u, _ = gpu_solve(p, H.HS_MIXED, sweeps=3, variant=H.HS_DST_TWOPASS)
+    assert O.max_rel_diff(u, ref) <= TOLMIX
+    u0, _ = gpu_solve(p, H.HS_MIXED, sweeps=0, variant=H.HS_DST_TWOPASS)
+    u0s, _ = gpu_solve(p, H.HS_MIXED, sweeps=0, variant=H.HS_DST_STAGED)
+    e, es = O.max_rel_diff(u0, ref), O.max_rel_diff(u0s, ref)
+    assert e <= 4 * es + 1e-7 and e <= 1e-4, (e, es)
+
+
 def test_autotune_keeps_a_valid_variant():
     """hs_autotune times the transform variants of each axis and keeps one; solves
     afterwards still meet the parity bar; variants that do not exist are refused."""
@@ -307,7 +323,7 @@ def test_autotune_keeps_a_valid_variant():
         assert mx > 0 and my > 0
         for axis in (H.HS_AXIS_X, H.HS_AXIS_Y):
             assert H.hs_get_transform_variant(s.plan, axis) in (
-                H.HS_DST_STAGED, H.HS_DST_FUSED, H.HS_DST_GENERIC)
+                H.HS_DST_STAGED, H.HS_DST_FUSED, H.HS_DST_GENERIC, H.HS_DST_TWOPASS)
         H.hs_set_refinement(s.plan, 2)
         f = torch.from_numpy(p.f_nodes).cuda()
         faces = [None if a is None else torch.from_numpy(a).cuda() for a in p.faces]
@@ -337,6 +353,8 @@ def test_autotune_keeps_a_valid_variant():
     try:
         with pytest.raises(H.HsError):
             H.hs_set_transform_variant(q.plan, H.HS_AXIS_X, H.HS_DST_FUSED)
+        with pytest.raises(H.HsError):
+            H.hs_set_transform_variant(q.plan, H.HS_AXIS_Y, H.HS_DST_TWOPASS)
         H.hs_set_transform_variant(q.plan, H.HS_AXIS_X, H.HS_DST_GENERIC)
     finally:
         q.close()
