@@ -200,6 +200,13 @@ WORKLOADS = {
              "a~U[0,1], 1-4 right-hand sides each, f ~ U[-1,1] FP32 at interior nodes, "
              "one CUDA graph launch per step; execution autotuned between the persistent "
              "kernel variants and a graph of stand-alone solves on parallel branches"),
+    "precond255_o4": dict(
+        steps=3,
+        desc="preconditioner mode: 4th-order compact Helmholtz with k^2(x,y,z) = "
+             "(20(1+z^2/2))^2 (1 + 0.1 sin(pi x) sin(pi y)) on the unit cube, 255^3 interior, "
+             "zero Dirichlet data, F ~ U[-1,1] h^2 assembled (seed 9); BiCGStab to "
+             "||F - A x|| / ||F|| <= 1e-10 preconditioned by the separable solve for the plane "
+             "means of k^2"),
     "cd511x8": dict(
         steps=10,
         desc="4th-order compact convection-diffusion Lap(u)+b(z)u_z=f, 511^3 interior, "
@@ -295,6 +302,25 @@ def run_reference(args):
     elif name == "cube1023_o6":
         p = W.sine_mode_problem(255, 6, W.k_tanh(), nmodes=16, seed=4)
         n, sample = 255 ** 3, "255^3 instance of the same recipe per step"
+    elif name == "precond255_o4":
+        from oracle import hs_precond_oracle as PC
+        Np = 63
+        K = precond_field(np, Np)
+        F = np.random.RandomState(9).uniform(-1, 1, K.shape) / (Np + 1) ** 2
+        h = (1.0 / (Np + 1),) * 3
+        Kref = PC.reference_from_field(K)
+        run = lambda: PC.precond_solve(4, K, F, h, Kref, tol=1e-10, maxit=200)
+        steps = args.steps if args.steps is not None else 3
+        for _ in range(args.warmup):
+            run()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            run()
+        dt = (time.perf_counter() - t0) / steps
+        emit_reference(args, name, Np ** 3 / dt / 1e9, dt, steps,
+                       f"{Np}^3 instance of the same recipe per step (numpy FP64 BiCGStab, "
+                       "the oracle's O(N^4) solve as preconditioner)", world)
+        return
     elif name == "batch64":
         sp = W.workload_batch_specs(nprob=64, seed=3)[0]
         p = W.batch_problem(sp, 0)
@@ -309,7 +335,11 @@ def run_reference(args):
     for _ in range(steps):
         O.solve(p)
     dt = (time.perf_counter() - t0) / steps
-    val = n / dt / 1e9
+    emit_reference(args, name, n / dt / 1e9, dt, steps,
+                   sample + " (numpy FP64, matmul O(N^4) DSTs, textbook Thomas)", world)
+
+
+def emit_reference(args, name, val, dt, steps, sample, world):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
             "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -317,14 +347,93 @@ def run_reference(args):
             "config": {"workload": f"{name}: {WORKLOADS[name]['desc']}", "global_batch": 1,
                        "parallelism": "cpu oracle, rank 0 only"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                             "sample": sample + " (numpy FP64, matmul O(N^4) DSTs, textbook "
-                                                "Thomas)"},
+                             "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def precond_field(xp, N):
+    """k^2 of the preconditioner workload on the N^3 interior of the unit cube
+    (xp: numpy or torch; input generation only)."""
+    t = xp.arange(1, N + 1, dtype=xp.float64) / (N + 1)
+    kz = (20.0 * (1.0 + 0.5 * t ** 2)) ** 2
+    sx = xp.sin(xp.pi * t) if xp.__name__ == "numpy" else xp.sin(t * 3.141592653589793)
+    return kz[:, None, None] * (1.0 + 0.1 * sx[None, :, None] * sx[None, None, :])
+
+
+def bench_precond(args, torch, H, rank, world, barrier, max_over_ranks):
+    """Preconditioner mode: BiCGStab for k(x,y,z) with the plan's solve as M^-1."""
+    N = 255
+    Kd = precond_field(torch, N).to("cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(9)
+    Fd = (torch.rand((N, N, N), generator=g, dtype=torch.float64, device="cuda") * 2 - 1) \
+        / (N + 1) ** 2
+    Kref = np.concatenate([[0.0], Kd.mean(dim=(1, 2)).cpu().numpy(), [0.0]])
+    Kref[0], Kref[-1] = Kref[1], Kref[-2]
+    stream = torch.cuda.current_stream()
+    res = {}
+    clocks = None
+    for name, prec, sweeps in (("fp64", H.HS_FP64, 0), ("mixed", H.HS_MIXED, 1)):
+        s = H.Solver(N, N, N, 1.0, 1.0, 1.0, 4, H.HS_HELMHOLTZ, prec)
+        s.set_coeff(Kref)
+        if prec == H.HS_MIXED:
+            H.hs_set_refinement(s.plan, sweeps)
+        H.hs_autotune(s.plan, stream, 3)
+        pc = H.hs_precond_create(s.plan, Kd)
+        x = torch.zeros_like(Fd)
+        st, inf = H.hs_precond_solve(pc, Fd, x, 1e-10, 200, stream)   # warm-up + accuracy
+        steps = args.steps
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        its = []
+        clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+        clk.start()
+        e0.record(stream)
+        for _ in range(steps):
+            x.zero_()
+            st, inf = H.hs_precond_solve(pc, Fd, x, 1e-10, 200, stream)
+            its.append(inf["iterations"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c = clk.stop()
+        if name == "mixed":
+            clocks = c
+        ms = max_over_ranks(e0.elapsed_time(e1)) / steps
+        # kernels per solve: operator + init, then per iteration 3 dot products,
+        # 3 vector updates, 2 operator applications and 2 solves of the plan (right-hand
+        # side + 5 transform/z-solve passes, plus the residual and 5 more per sweep)
+        per_solve = 6 + 6 * sweeps
+        launches = sum(2 + k * (8 + 2 * per_solve) for k in its)
+        res[name] = {"ms_per_solve": ms, "iterations": its, "status": st,
+                     "rel_residual": inf["rel_residual"], "gpu_launches": launches,
+                     "x": x.clone()}
+        H.hs_precond_destroy(pc)
+        s.close()
+    x64, xmx = res["fp64"].pop("x"), res["mixed"].pop("x")
+    diff = float((xmx - x64).abs().max() / x64.abs().max())
+    value = world * N ** 3 / (res["mixed"]["ms_per_solve"] * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": 1, "ms_per_step": res["mixed"]["ms_per_solve"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 Krylov, f32 + f32-pair preconditioner",
+            "data": "synthetic",
+            "config": {"workload": f"precond255_o4: {WORKLOADS['precond255_o4']['desc']}",
+                       "global_batch": world, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (8 vectors of 133 MB per solve)"},
+            "fp64_preconditioner": res["fp64"], "mixed_preconditioner": res["mixed"],
+            "accuracy": {"mixed_vs_fp64_preconditioned_solution": diff,
+                         "judged_against": "the same BiCGStab with the FP64 plan as preconditioner"},
+            "cpu_baseline": None, "e2e": None, "roofline": None, "clocks": clocks,
+            "gpu_launches": res["mixed"]["gpu_launches"],
+        }
+        print(json.dumps(line), flush=True)
 
 
 def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
@@ -522,6 +631,12 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    if args.workload == "precond255_o4":
+        bench_precond(args, torch, H, rank, world, barrier,
+                      lambda x: reduce_max(x, dist, "cuda"))
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.workload == "batch64":
         bench_batch(args, torch, H, W, rank, world, barrier,
                     lambda x: reduce_max(x, dist, "cuda"))

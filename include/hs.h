@@ -340,6 +340,49 @@ hs_status hs_batch_solve(hs_batch_t batch, void *stream, int sync);
  * inside the launch gives up (default 2e7). */
 hs_status hs_batch_set_wait_limit(hs_batch_t batch, long long spins);
 
+/*
+ * Preconditioner mode (the use the paper's introduction names): solve
+ * A(K) x = F for a Helmholtz coefficient K = k^2 that varies in x, y and z,
+ * by BiCGStab (van der Vorst) preconditioned from the right with the solve of
+ * a plan whose separable coefficient K_ref(z) approximates K (for instance the
+ * plane means).  A(K) is the compact scheme of the plan's order (2 or 4) for a
+ * general coefficient, zero Dirichlet data, scaled by h_z^2 like the Section
+ * 3.3 coefficients (for K = K(z) it is the plan's own 27-point operator):
+ *   4th order: h_z^2 [ Lap_h x + sum_{a<b} (h_a^2 + h_b^2)/12 d_a^2 d_b^2 x
+ *                      + K_c x_c / 2 + (1/12) sum_{6 face neighbours} K x ]
+ *   2nd order: h_z^2 [ Lap_h x + K_c x_c ]
+ * All vectors are FP64 device arrays of Nx Ny Nz interior values [z][y][x].
+ */
+typedef struct hs_precond_s *hs_precond_t;
+
+#define HS_PRECOND_MAX_HIST 64
+typedef struct {
+    int iterations;                          /* BiCGStab iterations done */
+    double rel_residual;                     /* ||F - A x|| / ||F|| (recurrence) at exit */
+    double history[HS_PRECOND_MAX_HIST];     /* the same after each iteration */
+} hs_precond_info;
+
+/* hs_precond_create -- workspace (8 FP64 vectors) for `plan` (HELMHOLTZ, order
+ * 2 or 4, coefficients set: they are K_ref) and the device coefficient field K
+ * (Nx Ny Nz FP64, not copied: it must outlive the object).
+ * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED (order 6, CD), HS_ERR_NO_COEFF,
+ * HS_ERR_OOM. */
+hs_status hs_precond_create(hs_precond_t *out, hs_plan_t plan, const double *K);
+
+/* hs_precond_apply -- y = A(K) u (device FP64 arrays, asynchronous on stream). */
+hs_status hs_precond_apply(hs_precond_t pc, const double *u, double *y, void *stream);
+
+/* hs_precond_solve -- x (device FP64, in: initial guess, out: solution) for the
+ * assembled right-hand side F; stops at ||F - A x|| / ||F|| <= tol or after maxit
+ * iterations (HS_WARN_NOT_CONVERGED, x valid).  Each iteration applies A twice
+ * and the plan's solve twice (hs_solve with HS_RHS_ASSEMBLED on `stream`) and
+ * synchronises the stream for its four reductions.  HS_ERR_NONFINITE on a
+ * BiCGStab breakdown or a NaN.  info may be NULL. */
+hs_status hs_precond_solve(hs_precond_t pc, const double *F, double *x, double tol, int maxit,
+                           void *stream, hs_precond_info *info);
+
+hs_status hs_precond_destroy(hs_precond_t pc);
+
 /* hs_batch_set_tol -- tolerance-controlled refinement per problem and RHS:
  * each stops once ||F - A U||_2 / ||F||_2 <= tol (decided on the device) or
  * after the batch's sweep count; 0 (default) runs every sweep. */

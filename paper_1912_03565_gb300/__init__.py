@@ -52,6 +52,7 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_batch_graph_kernels",
             "hs_set_transform_variant", "hs_get_transform_variant", "hs_autotune",
             "hs_set_thomas_variant", "hs_get_thomas_variant",
+            "hs_precond_create", "hs_precond_apply", "hs_precond_solve", "hs_precond_destroy",
             "hs_batch_workspace_bytes", "hs_batch_destroy")
 HS_STATIC_MAX_NZ = 8192
 
@@ -66,6 +67,14 @@ class hs_problem_desc(ctypes.Structure):
                 ("order", ctypes.c_int), ("equation", ctypes.c_int), ("cd_variant", ctypes.c_int),
                 ("c0", ctypes.c_void_p), ("c1", ctypes.c_void_p), ("c2", ctypes.c_void_p),
                 ("nrhs", ctypes.c_int), ("f", ctypes.c_void_p), ("u", ctypes.c_void_p)]
+
+
+HS_PRECOND_MAX_HIST = 64
+
+
+class hs_precond_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("history", ctypes.c_double * HS_PRECOND_MAX_HIST)]
 
 
 class hs_info(ctypes.Structure):
@@ -130,6 +139,14 @@ def load(path: Optional[str] = None):
     lib.hs_batch_solve.restype = ci
     lib.hs_batch_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
     lib.hs_batch_set_wait_limit.restype = ci
+    lib.hs_precond_create.argtypes = [ctypes.POINTER(vp), vp, vp]
+    lib.hs_precond_create.restype = ci
+    lib.hs_precond_apply.argtypes = [vp, vp, vp, vp]
+    lib.hs_precond_apply.restype = ci
+    lib.hs_precond_solve.argtypes = [vp, vp, vp, cd, ci, vp, ctypes.POINTER(hs_precond_info)]
+    lib.hs_precond_solve.restype = ci
+    lib.hs_precond_destroy.argtypes = [vp]
+    lib.hs_precond_destroy.restype = ci
     lib.hs_set_thomas_variant.argtypes = [vp, ci]
     lib.hs_set_thomas_variant.restype = ci
     lib.hs_get_thomas_variant.argtypes = [vp, ctypes.POINTER(ci)]
@@ -362,6 +379,34 @@ def hs_batch_set_residual_precision(batch, mode):
 def hs_set_transform_variant(plan, axis, variant):
     return _check(load().hs_set_transform_variant(plan, int(axis), int(variant)),
                   "hs_set_transform_variant", plan)
+
+
+def hs_precond_create(plan, K):
+    """Preconditioner-mode workspace for plan (coefficients = K_ref(z)) and the
+    device FP64 coefficient field K (kept referenced by the caller)."""
+    out = ctypes.c_void_p()
+    _check(load().hs_precond_create(ctypes.byref(out), plan, _ptr(K)), "hs_precond_create", plan)
+    return out
+
+
+def hs_precond_apply(pc, u, y, stream=None):
+    return _check(load().hs_precond_apply(pc, _ptr(u), _ptr(y), _stream_ptr(stream)),
+                  "hs_precond_apply")
+
+
+def hs_precond_solve(pc, F, x, tol=1e-10, maxit=100, stream=None):
+    """Returns (status, info dict); raises on errors (negative status)."""
+    inf = hs_precond_info()
+    st = _check(load().hs_precond_solve(pc, _ptr(F), _ptr(x), float(tol), int(maxit),
+                                        _stream_ptr(stream), ctypes.byref(inf)),
+                "hs_precond_solve")
+    n = min(inf.iterations, HS_PRECOND_MAX_HIST)
+    return st, {"iterations": inf.iterations, "rel_residual": inf.rel_residual,
+                "history": list(inf.history[:n])}
+
+
+def hs_precond_destroy(pc):
+    return _check(load().hs_precond_destroy(pc), "hs_precond_destroy")
 
 
 def hs_set_thomas_variant(plan, variant):
