@@ -178,8 +178,13 @@ hs_status capture_solves(hs_batch_s *B) {
             return st;
     }
     if (!B->graph_warm) {
-        // one solve per problem outside capture: first-launch attributes and any
-        // lazily created buffers exist before the capture
+        // each plan picks its own transform kernels and z-solve mapping (timed on
+        // its work buffers), then solves once outside capture: first-launch
+        // attributes and any lazily created buffers exist before the capture
+        for (int k = 0; k < B->n; ++k) {
+            const hs_status st = hs_autotune(B->plans[k], nullptr, 2, nullptr, nullptr);
+            if (st < 0) return st;
+        }
         for (int k = 0; k < B->n; ++k) {
             const BatchWork &W = B->works[B->work_of[k]];
             const hs_status st = hs_solve(B->plans[k], W.f, B->f_dtype, HS_RHS_NODAL, nullptr,
