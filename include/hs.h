@@ -223,6 +223,19 @@ hs_status hs_get_thomas_variant(hs_plan_t plan, int *variant);
 hs_status hs_autotune(hs_plan_t plan, void *stream, int reps, float *ms_x, float *ms_y);
 
 /*
+ * hs_set_host_io -- how hs_solve treats host buffers f and u.  Pageable host
+ * buffers are always staged (copied into a plan-owned device buffer and
+ * back).  For pinned (page-locked) buffers, `mapped` is a bit mask: bit 0 =
+ * the right-hand-side kernel reads f in place through its device alias, bit 1
+ * = the last transform pass writes u in place; no staging buffer is then
+ * allocated for it.  Default 0 (staged): on GB300 a 255^3 6th-order solve from
+ * pinned host buffers took 2.66 ms staged against 2.94 (u in place), 3.19 (f
+ * in place) and 3.47 ms (both), the kernels' access pattern over the host link
+ * costing more than one bulk copy.  Errors: HS_ERR_INVALID_ARG (mask > 3).
+ */
+hs_status hs_set_host_io(hs_plan_t plan, int mapped);
+
+/*
  * hs_set_stage_timing -- when on (1), solves record CUDA events around each
  * stage launch (no synchronisation is added); hs_stage_times and
  * hs_info.stage_ms report them.  Off (0) by default.

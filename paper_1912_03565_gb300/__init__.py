@@ -51,7 +51,7 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_batch_set_variant", "hs_batch_get_variant", "hs_batch_autotune",
             "hs_batch_graph_kernels",
             "hs_set_transform_variant", "hs_get_transform_variant", "hs_autotune",
-            "hs_set_thomas_variant", "hs_get_thomas_variant",
+            "hs_set_thomas_variant", "hs_get_thomas_variant", "hs_set_host_io",
             "hs_precond_create", "hs_precond_apply", "hs_precond_solve", "hs_precond_destroy",
             "hs_batch_workspace_bytes", "hs_batch_destroy")
 HS_STATIC_MAX_NZ = 8192
@@ -147,6 +147,8 @@ def load(path: Optional[str] = None):
     lib.hs_precond_solve.restype = ci
     lib.hs_precond_destroy.argtypes = [vp]
     lib.hs_precond_destroy.restype = ci
+    lib.hs_set_host_io.argtypes = [vp, ci]
+    lib.hs_set_host_io.restype = ci
     lib.hs_set_thomas_variant.argtypes = [vp, ci]
     lib.hs_set_thomas_variant.restype = ci
     lib.hs_get_thomas_variant.argtypes = [vp, ctypes.POINTER(ci)]
@@ -407,6 +409,10 @@ def hs_precond_solve(pc, F, x, tol=1e-10, maxit=100, stream=None):
 
 def hs_precond_destroy(pc):
     return _check(load().hs_precond_destroy(pc), "hs_precond_destroy")
+
+
+def hs_set_host_io(plan, mapped):
+    return _check(load().hs_set_host_io(plan, int(mapped)), "hs_set_host_io", plan)
 
 
 def hs_set_thomas_variant(plan, variant):

@@ -82,6 +82,16 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device alias of pinned (page-locked, mapped) host memory, else NULL.
+void *mapped_host(const void *p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 template <typename T>
 hs_status dev_alloc(hs_plan_s *P, T **p, size_t n) {
     *p = nullptr;
@@ -526,6 +536,7 @@ hs_status hs_plan(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, 
     P->order = order; P->equation = equation; P->precision = precision; P->max_rhs = max_rhs;
     P->refine_sweeps = 2;
     P->resid_mode = HS_RESID_AUTO;
+    P->host_io_mapped = 0;
     P->cd_variant = HS_CD_CORRECTED;
     if (cudaGetDevice(&P->device) != cudaSuccess) {
         cudaGetLastError();
@@ -812,6 +823,13 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
     return HS_OK;
 }
 
+hs_status hs_set_host_io(hs_plan_t P, int mapped) {
+    if (!P) return HS_ERR_INVALID_ARG;
+    if (mapped < 0 || mapped > 3) return HS_ERR_INVALID_ARG;
+    P->host_io_mapped = mapped;
+    return HS_OK;
+}
+
 hs_status hs_set_stage_timing(hs_plan_t P, int on) {
     if (!P) return HS_ERR_INVALID_ARG;
     P->stage_timing = on ? 1 : 0;
@@ -831,9 +849,15 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
     const size_t fcount = rhs_kind == HS_RHS_NODAL ? node_count(P) : interior_count(P);
     const size_t ucount = interior_count(P);
 
-    // host staging
+    // host buffers: pinned ones are read / written in place through their device
+    // alias when the plan allows it (the kernels then move the bytes over the
+    // host link themselves), pageable ones are staged
     const unsigned char *fd = static_cast<const unsigned char *>(f);
-    if (!is_device_ptr(f)) {
+    const void *f_mapped =
+        (!is_device_ptr(f) && (P->host_io_mapped & 1)) ? mapped_host(f) : nullptr;
+    if (f_mapped) {
+        fd = static_cast<const unsigned char *>(f_mapped);
+    } else if (!is_device_ptr(f)) {
         const size_t nb = fcount * esz * nrhs;
         if (nb > P->stage_f_bytes) {
             if (P->d_stage_f) { cudaFree(P->d_stage_f); P->bytes -= P->stage_f_bytes; }
@@ -846,7 +870,13 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
         fd = static_cast<const unsigned char *>(P->d_stage_f);
     }
     double *ud = u;
-    const bool u_host = !is_device_ptr(u);
+    bool u_host = !is_device_ptr(u);
+    double *u_mapped =
+        (u_host && (P->host_io_mapped & 2)) ? static_cast<double *>(mapped_host(u)) : nullptr;
+    if (u_mapped) {
+        ud = u_mapped;
+        u_host = false;
+    }
     if (u_host) {
         const size_t nb = ucount * sizeof(double) * nrhs;
         if (nb > P->stage_u_bytes) {

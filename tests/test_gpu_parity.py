@@ -189,6 +189,41 @@ def test_host_pointers_match_device():
     assert np.array_equal(ud, uh)
 
 
+@pytest.mark.parametrize("precision", [H.HS_FP64, H.HS_MIXED])
+def test_pinned_host_buffers_in_place_and_staged(precision):
+    """Pinned host f and u are used in place through their device alias (either
+    or both) or staged (default); pageable ones are always staged.  All give the
+    device result."""
+    torch = _torch()
+    p = random_problem((40, 33, 27), 6, W.HELMHOLTZ, seed=9, faces=False)
+    ref = oracle_solve(p)
+    s = H.Solver(p.Nx, p.Ny, p.Nz, p.Lx, p.Ly, p.Lz, 6, H.HS_HELMHOLTZ, precision)
+    try:
+        s.set_coeff(p.c0, p.c1, p.c2)
+        if precision == H.HS_MIXED:
+            H.hs_set_refinement(s.plan, 2)
+        fd = torch.from_numpy(p.f_nodes).cuda()
+        ud = torch.zeros((p.Nz, p.Ny, p.Nx), dtype=torch.float64, device="cuda")
+        s.solve(fd, ud, H.HS_F64, H.HS_RHS_NODAL)
+        torch.cuda.synchronize()
+        outs = []
+        for mapped in (3, 1, 2, 0):
+            H.hs_set_host_io(s.plan, mapped)
+            for pinned in (True, False):
+                fh = torch.from_numpy(p.f_nodes.copy())
+                uh = torch.full((p.Nz, p.Ny, p.Nx), np.nan, dtype=torch.float64)
+                if pinned:
+                    fh, uh = fh.pin_memory(), uh.pin_memory()
+                s.solve(fh, uh, H.HS_F64, H.HS_RHS_NODAL)
+                torch.cuda.synchronize()
+                outs.append(uh.numpy().copy())
+        for o in outs:
+            assert np.array_equal(o, ud.cpu().numpy())
+        assert O.max_rel_diff(outs[0], ref) <= (TOL64 if precision == H.HS_FP64 else TOLMIX)
+    finally:
+        s.close()
+
+
 def test_assembled_rhs_and_multi_rhs():
     torch = _torch()
     Nx, Ny, Nz = 30, 26, 21
