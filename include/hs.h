@@ -65,6 +65,7 @@ enum { HS_RESID_DF = 0, HS_RESID_F64 = 1, HS_RESID_AUTO = 2 }; /* refinement res
 enum { HS_DST_STAGED = 0, HS_DST_FUSED = 1, HS_DST_GENERIC = 2,   /* transform kernels */
        HS_DST_TWOPASS = 3 };
 enum { HS_AXIS_X = 0, HS_AXIS_Y = 1 };                       /* transform axis */
+enum { HS_FACTOR_AUTO = 0, HS_FACTOR_F32 = 1, HS_FACTOR_F64 = 2 }; /* mixed z-solve factors */
 enum { HS_THOMAS_PIPE16_256 = 0, HS_THOMAS_PIPE8_128 = 1,    /* FP32 z-solve mapping */
        HS_THOMAS_PLAIN16_256 = 2, HS_THOMAS_PIPE16_128 = 3 };
 
@@ -221,6 +222,20 @@ hs_status hs_get_thomas_variant(hs_plan_t plan, int *variant);
  * Synchronous.  Call after hs_set_coeff, before solves (not during capture).
  */
 hs_status hs_autotune(hs_plan_t plan, void *stream, int reps, float *ms_x, float *ms_y);
+
+/*
+ * hs_set_factor_precision -- the factors of the mixed path's z-solves
+ * (Section 3.6's LU of each mode's tridiagonal system): HS_FACTOR_F32 (FP32
+ * factors and sweep, 20 bytes moved per unknown), HS_FACTOR_F64 (FP64 factors,
+ * FP64 forward sweep kept in an FP64 scratch: a more accurate correction solve,
+ * which can save a refinement sweep, for 32 more bytes of plan memory per
+ * unknown), HS_FACTOR_AUTO (default: FP32 unless some z-system has min pivot
+ * ratio < 1e-4).  On GB300 at 1023^3 FP64 factors lowered the unrefined error
+ * (9.2e-6 -> 4.2e-7) but not the refined one, which the residual's rounding
+ * bounds.  May be called before or after hs_set_coeff (refactors).
+ * Ignored by the HS_FP64 path.  Errors: HS_ERR_INVALID_ARG, HS_ERR_OOM.
+ */
+hs_status hs_set_factor_precision(hs_plan_t plan, int mode);
 
 /*
  * hs_set_host_io -- how hs_solve treats host buffers f and u.  Pageable host

@@ -37,6 +37,7 @@ HS_RHS_NODAL, HS_RHS_ASSEMBLED = 0, 1
 HS_RESID_DF, HS_RESID_F64, HS_RESID_AUTO = 0, 1, 2
 HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC, HS_DST_TWOPASS = 0, 1, 2, 3
 HS_AXIS_X, HS_AXIS_Y = 0, 1
+HS_FACTOR_AUTO, HS_FACTOR_F32, HS_FACTOR_F64 = 0, 1, 2
 HS_THOMAS_PIPE16_256, HS_THOMAS_PIPE8_128, HS_THOMAS_PLAIN16_256, HS_THOMAS_PIPE16_128 = 0, 1, 2, 3
 HS_INFO_MAX_ITERS = 8
 HS_INFO_STAGES = 8
@@ -52,6 +53,7 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_batch_graph_kernels",
             "hs_set_transform_variant", "hs_get_transform_variant", "hs_autotune",
             "hs_set_thomas_variant", "hs_get_thomas_variant", "hs_set_host_io",
+            "hs_set_factor_precision",
             "hs_precond_create", "hs_precond_apply", "hs_precond_solve", "hs_precond_destroy",
             "hs_batch_workspace_bytes", "hs_batch_destroy")
 HS_STATIC_MAX_NZ = 8192
@@ -147,6 +149,8 @@ def load(path: Optional[str] = None):
     lib.hs_precond_solve.restype = ci
     lib.hs_precond_destroy.argtypes = [vp]
     lib.hs_precond_destroy.restype = ci
+    lib.hs_set_factor_precision.argtypes = [vp, ci]
+    lib.hs_set_factor_precision.restype = ci
     lib.hs_set_host_io.argtypes = [vp, ci]
     lib.hs_set_host_io.restype = ci
     lib.hs_set_thomas_variant.argtypes = [vp, ci]
@@ -409,6 +413,10 @@ def hs_precond_solve(pc, F, x, tol=1e-10, maxit=100, stream=None):
 
 def hs_precond_destroy(pc):
     return _check(load().hs_precond_destroy(pc), "hs_precond_destroy")
+
+
+def hs_set_factor_precision(plan, mode):
+    return _check(load().hs_set_factor_precision(plan, int(mode)), "hs_set_factor_precision", plan)
 
 
 def hs_set_host_io(plan, mapped):

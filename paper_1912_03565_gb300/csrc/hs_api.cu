@@ -501,6 +501,29 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
 
 }  // namespace
 
+namespace {
+
+// Factor precision of the mixed path's z-solves: FP32 factors (the FP32 sweep)
+// when allowed -- by default only when no z-system is close to singular (min
+// pivot ratio >= 1e-4) -- else the FP64 factors are built (and kept) as well
+// and the sweep runs in FP64 with FP32 data.
+hs_status choose_factors(hs_plan_s *P) {
+    const bool f32 = P->factor_mode == HS_FACTOR_F32 ||
+                     (P->factor_mode == HS_FACTOR_AUTO && P->min_pivot_ratio >= 1e-4);
+    P->thomas32 = (P->precision == HS_MIXED && f32) ? 1 : 0;
+    if (P->precision == HS_MIXED && !P->thomas32) {
+        const double init[2] = {__builtin_inf(), 0.0};
+        if (!P->d_fac) HS_TRY(P, dev_alloc(P, &P->d_fac, 3 * interior_count(P)));
+        HS_TRY(P, ensure_f64_work(P));
+        HS_CK(P, cudaMemcpy(P->d_red, init, sizeof(init), cudaMemcpyHostToDevice));
+        HS_TRY(P, hs_launch_factor(P, 0));
+        HS_CK(P, cudaDeviceSynchronize());
+    }
+    return HS_OK;
+}
+
+}  // namespace
+
 // Exposed for the fixed-scratch residual entry point (k_noalloc.cu).
 void hs_stencil_table(const hs_plan_s *P, const double *c0, const double *c1, const double *c2,
                       int cd_variant, double *C) {
@@ -656,16 +679,7 @@ hs_status hs_set_coeff(hs_plan_t P, const double *c0, const double *c1, const do
     double red[2];
     HS_CK(P, cudaMemcpy(red, P->d_red, sizeof(red), cudaMemcpyDeviceToHost));
     P->min_pivot_ratio = red[1] > 0 ? red[0] / red[1] : 0.0;
-    // FP32 z-solves in the mixed path only when no z-system is close to
-    // singular; otherwise the FP64 factors are built (and kept) as well.
-    P->thomas32 = (P->precision == HS_MIXED && P->min_pivot_ratio >= 1e-4) ? 1 : 0;
-    if (P->precision == HS_MIXED && !P->thomas32) {
-        if (!P->d_fac) HS_TRY(P, dev_alloc(P, &P->d_fac, 3 * interior_count(P)));
-        HS_TRY(P, ensure_f64_work(P));
-        HS_CK(P, cudaMemcpy(P->d_red, init, sizeof(init), cudaMemcpyHostToDevice));
-        HS_TRY(P, hs_launch_factor(P, 0));
-        HS_CK(P, cudaDeviceSynchronize());
-    }
+    HS_TRY(P, choose_factors(P));
     P->cd_variant = cd_variant;
     P->have_coeff = 1;
     return P->min_pivot_ratio < 1e-13 ? HS_WARN_NEAR_SINGULAR : HS_OK;
@@ -820,6 +834,13 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
     }
     if (ms_x) *ms_x = best_ms[0];
     if (ms_y) *ms_y = best_ms[1];
+    return HS_OK;
+}
+
+hs_status hs_set_factor_precision(hs_plan_t P, int mode) {
+    if (!P || mode < HS_FACTOR_AUTO || mode > HS_FACTOR_F64) return HS_ERR_INVALID_ARG;
+    P->factor_mode = mode;
+    if (P->have_coeff) HS_TRY(P, choose_factors(P));
     return HS_OK;
 }
 

@@ -51,6 +51,7 @@ struct hs_plan_s {
     int thomas_variant;   // FP32 z-solve mapping: HS_THOMAS_*
     void *d_ytmp;         // complex scratch of the two-pass y transform (Nz x M x Nx float2)
     int resid_mode;       // HS_RESID_DF / HS_RESID_F64 / HS_RESID_AUTO
+    int factor_mode;      // HS_FACTOR_AUTO / F32 / F64 (mixed path z-solves)
     int host_io_mapped;   // bit 0: pinned host f read in place; bit 1: pinned host u written in place
     int have_coeff;
     int cd_variant;
