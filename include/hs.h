@@ -66,6 +66,7 @@ enum { HS_DST_STAGED = 0, HS_DST_FUSED = 1, HS_DST_GENERIC = 2,   /* transform k
        HS_DST_TWOPASS = 3 };
 enum { HS_AXIS_X = 0, HS_AXIS_Y = 1 };                       /* transform axis */
 enum { HS_FACTOR_AUTO = 0, HS_FACTOR_F32 = 1, HS_FACTOR_F64 = 2 }; /* mixed z-solve factors */
+enum { HS_HOST_F_MAPPED = 1, HS_HOST_U_MAPPED = 2, HS_HOST_F_EARLY = 4 };  /* hs_set_host_io */
 enum { HS_THOMAS_PIPE16_256 = 0, HS_THOMAS_PIPE8_128 = 1,    /* FP32 z-solve mapping */
        HS_THOMAS_PLAIN16_256 = 2, HS_THOMAS_PIPE16_128 = 3 };
 
@@ -238,15 +239,23 @@ hs_status hs_autotune(hs_plan_t plan, void *stream, int reps, float *ms_x, float
 hs_status hs_set_factor_precision(hs_plan_t plan, int mode);
 
 /*
- * hs_set_host_io -- how hs_solve treats host buffers f and u.  Pageable host
- * buffers are always staged (copied into a plan-owned device buffer and
- * back).  For pinned (page-locked) buffers, `mapped` is a bit mask: bit 0 =
- * the right-hand-side kernel reads f in place through its device alias, bit 1
- * = the last transform pass writes u in place; no staging buffer is then
- * allocated for it.  Default 0 (staged): on GB300 a 255^3 6th-order solve from
- * pinned host buffers took 2.66 ms staged against 2.94 (u in place), 3.19 (f
- * in place) and 3.47 ms (both), the kernels' access pattern over the host link
- * costing more than one bulk copy.  Errors: HS_ERR_INVALID_ARG (mask > 3).
+ * hs_set_host_io -- how hs_solve moves host buffers f and u (flags, default 0).
+ * Pageable host buffers are staged: f is copied into a plan-owned device buffer
+ * -- a nodal f in z-chunks on a second stream, each slab of the right-hand-side
+ * kernel starting as soon as its planes have arrived, so copy and kernel
+ * overlap -- and u is copied back.  Flags:
+ *   HS_HOST_F_MAPPED  a pinned f is read in place by the right-hand-side kernel
+ *                     through its device alias (no staging);
+ *   HS_HOST_U_MAPPED  a pinned u is written in place by the last transform pass;
+ *   HS_HOST_F_EARLY   the copy of a staged f does not wait for the work queued
+ *                     before the call on the stream, only until the previous
+ *                     solve has finished reading the staging buffer, so it
+ *                     overlaps that solve.  Use only when no work queued on the
+ *                     stream writes the host f (for example f filled by the CPU).
+ * On GB300, 255^3, 6th order, pinned host buffers, back-to-back solves: 2.51 ms
+ * per solve staged (2.66 ms copying f whole), 2.22 ms with HS_HOST_F_EARLY; in
+ * place: 2.94 (u), 3.19 (f), 3.47 ms (both) -- the kernels' access pattern over
+ * the host link costs more than one bulk copy.  Errors: HS_ERR_INVALID_ARG.
  */
 hs_status hs_set_host_io(hs_plan_t plan, int mapped);
 

@@ -38,6 +38,7 @@ HS_RESID_DF, HS_RESID_F64, HS_RESID_AUTO = 0, 1, 2
 HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC, HS_DST_TWOPASS = 0, 1, 2, 3
 HS_AXIS_X, HS_AXIS_Y = 0, 1
 HS_FACTOR_AUTO, HS_FACTOR_F32, HS_FACTOR_F64 = 0, 1, 2
+HS_HOST_F_MAPPED, HS_HOST_U_MAPPED, HS_HOST_F_EARLY = 1, 2, 4
 HS_THOMAS_PIPE16_256, HS_THOMAS_PIPE8_128, HS_THOMAS_PLAIN16_256, HS_THOMAS_PIPE16_128 = 0, 1, 2, 3
 HS_INFO_MAX_ITERS = 8
 HS_INFO_STAGES = 8

@@ -92,6 +92,25 @@ void *mapped_host(const void *p) {
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+// The upload stream and events of the pipelined host-f copy (created once per plan).
+hs_status ensure_upload(hs_plan_s *P) {
+    if (P->have_up) return HS_OK;
+    if (cudaStreamCreateWithFlags(&P->up_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return HS_ERR_CUDA;
+    }
+    for (int k = 0; k < HS_UP_CHUNKS + 3; ++k) {
+        if (cudaEventCreateWithFlags(&P->up_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            for (int j = 0; j < k; ++j) cudaEventDestroy(P->up_ev[j]);
+            cudaStreamDestroy(P->up_stream);
+            return HS_ERR_CUDA;
+        }
+    }
+    P->have_up = 1;
+    return HS_OK;
+}
+
 template <typename T>
 hs_status dev_alloc(hs_plan_s *P, T **p, size_t n) {
     *p = nullptr;
@@ -116,6 +135,10 @@ void free_plan(hs_plan_s *P) {
                     P->d_skip, P->d_ytmp};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    if (P->have_up) {
+        for (int k = 0; k < HS_UP_CHUNKS + 3; ++k) cudaEventDestroy(P->up_ev[k]);
+        cudaStreamDestroy(P->up_stream);
+    }
     if (P->have_events) {
         for (int k = 0; k < 2 * HS_EVENT_PAIRS; ++k) cudaEventDestroy(P->ev[k]);
         cudaEventDestroy(P->ev_total[0]);
@@ -846,7 +869,7 @@ hs_status hs_set_factor_precision(hs_plan_t P, int mode) {
 
 hs_status hs_set_host_io(hs_plan_t P, int mapped) {
     if (!P) return HS_ERR_INVALID_ARG;
-    if (mapped < 0 || mapped > 3) return HS_ERR_INVALID_ARG;
+    if (mapped < 0 || mapped > 7) return HS_ERR_INVALID_ARG;
     P->host_io_mapped = mapped;
     return HS_OK;
 }
@@ -875,7 +898,8 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
     // host link themselves), pageable ones are staged
     const unsigned char *fd = static_cast<const unsigned char *>(f);
     const void *f_mapped =
-        (!is_device_ptr(f) && (P->host_io_mapped & 1)) ? mapped_host(f) : nullptr;
+        (!is_device_ptr(f) && (P->host_io_mapped & HS_HOST_F_MAPPED)) ? mapped_host(f) : nullptr;
+    bool piped = false;   // staged host f uploaded in chunks overlapping the first RHS kernel
     if (f_mapped) {
         fd = static_cast<const unsigned char *>(f_mapped);
     } else if (!is_device_ptr(f)) {
@@ -887,13 +911,15 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
             HS_TRY(P, dev_alloc(P, (unsigned char **)&P->d_stage_f, nb));
             P->stage_f_bytes = nb;
         }
-        HS_CK(P, cudaMemcpyAsync(P->d_stage_f, f, nb, cudaMemcpyHostToDevice, s));
+        piped = rhs_kind == HS_RHS_NODAL && ensure_upload(P) == HS_OK;
+        if (!piped) HS_CK(P, cudaMemcpyAsync(P->d_stage_f, f, nb, cudaMemcpyHostToDevice, s));
         fd = static_cast<const unsigned char *>(P->d_stage_f);
     }
     double *ud = u;
     bool u_host = !is_device_ptr(u);
     double *u_mapped =
-        (u_host && (P->host_io_mapped & 2)) ? static_cast<double *>(mapped_host(u)) : nullptr;
+        (u_host && (P->host_io_mapped & HS_HOST_U_MAPPED)) ? static_cast<double *>(mapped_host(u))
+                                                           : nullptr;
     if (u_mapped) {
         ud = u_mapped;
         u_host = false;
@@ -926,13 +952,31 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
             HS_CK(P, cudaMemsetAsync(P->d_skip, 0, sizeof(int), s));
         }
         T.begin(HS_STAGE_RHS);
-        HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db,
-                                P->precision == HS_MIXED ? (void *)P->d_Fdf : (void *)P->d_w64,
-                                P->precision == HS_MIXED, s, norms ? P->d_red + 4 : nullptr));
+        void *Fout = P->precision == HS_MIXED ? (void *)P->d_Fdf : (void *)P->d_w64;
+        if (piped && r == 0) {
+            HS_TRY(P, hs_upload_rhs(P, f, P->d_stage_f, f_dtype, db, Fout, P->precision == HS_MIXED,
+                                    s, norms ? P->d_red + 4 : nullptr));
+            if (nrhs > 1) {
+                // the other right-hand sides in one copy, overlapping the first solve
+                const size_t one = fcount * esz;
+                HS_CK(P, cudaMemcpyAsync(static_cast<unsigned char *>(P->d_stage_f) + one,
+                                         static_cast<const unsigned char *>(f) + one,
+                                         one * (nrhs - 1), cudaMemcpyHostToDevice,
+                                         P->up_stream));
+                HS_CK(P, cudaEventRecord(P->up_ev[HS_UP_CHUNKS], P->up_stream));
+            }
+        } else {
+            if (piped && r == 1) HS_CK(P, cudaStreamWaitEvent(s, P->up_ev[HS_UP_CHUNKS], 0));
+            HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db, Fout, P->precision == HS_MIXED,
+                                    s, norms ? P->d_red + 4 : nullptr));
+        }
+        // the last reader of the staged f is queued: the next solve's upload may start
+        if (piped && r == nrhs - 1) HS_CK(P, cudaEventRecord(P->up_ev[HS_UP_CHUNKS + 1], s));
         T.end(HS_STAGE_RHS);
         HS_TRY(P, solve_one(P, ur, s, T, ir));
         if (ir && P->precision == HS_FP64) {
             HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db, P->d_w64, 0, s));
+            if (piped) HS_CK(P, cudaEventRecord(P->up_ev[HS_UP_CHUNKS + 1], s));
             double r2, f2;
             HS_TRY(P, residual_norms(P, P->d_w64, ur, s, &r2, &f2));
             ir->rel_residual[0] = f2 > 0 ? sqrt(r2 / f2) : sqrt(r2);

@@ -38,6 +38,9 @@ struct DevBoundary {
     const void *fnn[6];
 };
 
+// Chunks of the pipelined upload of a staged host right-hand side.
+#define HS_UP_CHUNKS 4
+
 struct hs_plan_s {
     int Nx, Ny, Nz;
     double Lx, Ly, Lz, hx, hy, hz;
@@ -52,7 +55,10 @@ struct hs_plan_s {
     void *d_ytmp;         // complex scratch of the two-pass y transform (Nz x M x Nx float2)
     int resid_mode;       // HS_RESID_DF / HS_RESID_F64 / HS_RESID_AUTO
     int factor_mode;      // HS_FACTOR_AUTO / F32 / F64 (mixed path z-solves)
-    int host_io_mapped;   // bit 0: pinned host f read in place; bit 1: pinned host u written in place
+    int host_io_mapped;
+    cudaStream_t up_stream;   // upload stream of the chunked host-f copy (lazily created)
+    cudaEvent_t up_ev[HS_UP_CHUNKS + 3];   // chunks, rest, staging free, call start
+    int have_up;   // bit 0: pinned host f read in place; bit 1: pinned host u written in place
     int have_coeff;
     int cd_variant;
     double min_pivot_ratio;
@@ -139,9 +145,21 @@ int hs_dst_fits(const DstAxis &ax, int axis, int tc);
 
 // Lifted right-hand side F (interior) from f: FP64 (out_df = 0) or a
 // double-float pair in two FP32 planes [2][Nz][Ny][Nx] (out_df = 1).
+// Uploads one node-grid right-hand side from host memory fh into the device
+// staging buffer fd in HS_UP_CHUNKS chunks of z-planes on P->up_stream (after
+// the work already queued on s, or -- with HS_HOST_F_EARLY -- only after the
+// event P->up_ev[HS_UP_CHUNKS + 1], which the caller records on its stream once
+// the staging buffer's last reader is queued), and runs the tiled right-hand-side kernel on
+// stream s slab by slab, each slab waiting only for the chunk that holds its
+// last plane: the copy overlaps the kernel.  Needs P->have_up.
+hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int f_dtype, const DevBoundary &b,
+                        void *F, int out_df, cudaStream_t s, double *f2);
+
+// For a nodal f the tiled kernels can run on a slab of z-tiles [bz0, bz0 + nbz)
+// (nbz < 0: to the last tile; tiles are RZ output planes).
 hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_kind,
                         const DevBoundary &b, void *F, int out_df, cudaStream_t s,
-                        double *f2 = nullptr);
+                        double *f2 = nullptr, int bz0 = 0, int nbz = -1);
 
 // Kernel selectors of the automatic residual precision: launch both kernels;
 // each returns at once unless the rule (residual_use_f64 on norms, sweep m)

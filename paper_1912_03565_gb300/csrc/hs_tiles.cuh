@@ -458,6 +458,7 @@ struct RhsArgs {
     const double *c1;    // [Nz+2]
     const float4 *rc;    // [Nz+2]: per-row double-float RHS weights (see rhs_tiled_df_kernel)
     int has_faces;       // 0: every Dirichlet face is zero, so the lifting vanishes
+    int bz0;             // first z-tile of the launch (slab launches of the tiled kernels)
     DevBoundary b;
 };
 

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_kernel(RhsArgs a, const T 
     __shared__ double pl[5][RHY][RHX];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RTX + tx;
     const int i0 = 1 + blockIdx.x * RTX, j0 = 1 + blockIdx.y * RTY;
-    const int lbeg = 1 + blockIdx.z * RZ;
+    const int lbeg = 1 + (blockIdx.z + a.bz0) * RZ;
     const int lend = min(lbeg + RZ - 1, a.Nz);
     const size_t n = (size_t)a.Nx * a.Ny * a.Nz;
     const double h = a.hz, h2 = h * h;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_df_kernel(RhsArgs a, const
                                                                 float *__restrict__ Fo,
                                                                 double *f2out) {
     __shared__ __align__(16) unsigned char smem[2 * 5 * RHY * RHX * sizeof(float)];
-    rhs_df_tile<T>(a, f, Fo, f2out, smem, blockIdx.x, blockIdx.y, blockIdx.z);
+    rhs_df_tile<T>(a, f, Fo, f2out, smem, blockIdx.x, blockIdx.y, blockIdx.z + a.bz0);
 }
 
 __global__ void __launch_bounds__(QTX *QTY) residual_zmarch_kernel(int Nx, int Ny, int Nz,
@@ -308,8 +308,53 @@ __global__ void __launch_bounds__(256) sumsq_kernel(const T *__restrict__ x, siz
 
 }  // namespace
 
+hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int f_dtype, const DevBoundary &b,
+                        void *F, int out_df, cudaStream_t s, double *f2) {
+    constexpr int K = HS_UP_CHUNKS;
+    const size_t esz = f_dtype == HS_F64 ? 8 : 4;
+    const size_t pb = (size_t)(P->Nx + 2) * (P->Ny + 2) * esz;   // bytes per node plane
+    const int tz = (P->Nz + RZ - 1) / RZ;
+    const unsigned char *src = static_cast<const unsigned char *>(fh);
+    unsigned char *dst = static_cast<unsigned char *>(fd);
+    if (P->host_io_mapped & HS_HOST_F_EARLY) {
+        // the caller vouches that no work queued on s writes fh: the copy only
+        // waits until the previous solve's last right-hand-side kernel has read
+        // the staging buffer (a never-recorded event is complete), so it may
+        // overlap the rest of that solve
+        if (cudaStreamWaitEvent(P->up_stream, P->up_ev[K + 1], 0) != cudaSuccess)
+            return HS_ERR_CUDA;
+    } else {
+        // stream order: the copy starts after everything queued on s so far
+        if (cudaEventRecord(P->up_ev[K + 2], s) != cudaSuccess ||
+            cudaStreamWaitEvent(P->up_stream, P->up_ev[K + 2], 0) != cudaSuccess)
+            return HS_ERR_CUDA;
+    }
+    int copied = 0;   // node planes [0, copied) are on their way
+    for (int k = 0; k < K; ++k) {
+        const int t0 = (k * tz) / K, t1 = ((k + 1) * tz) / K;
+        // the slab's last tile reads node planes up to min(t1 RZ, Nz) + 2 (<= Nz + 1)
+        const int need = k == K - 1 ? P->Nz + 2 : (t1 * RZ + 3 < P->Nz + 2 ? t1 * RZ + 3 : P->Nz + 2);
+        if (need > copied) {
+            if (cudaMemcpyAsync(dst + copied * pb, src + copied * pb, (size_t)(need - copied) * pb,
+                                cudaMemcpyHostToDevice, P->up_stream) != cudaSuccess)
+                return HS_ERR_CUDA;
+            copied = need;
+        }
+        if (cudaEventRecord(P->up_ev[k], P->up_stream) != cudaSuccess ||
+            cudaStreamWaitEvent(s, P->up_ev[k], 0) != cudaSuccess)
+            return HS_ERR_CUDA;
+        if (t1 > t0) {
+            const hs_status st = hs_launch_rhs(P, fd, f_dtype, HS_RHS_NODAL, b, F, out_df, s, f2,
+                                               t0, t1 - t0);
+            if (st != HS_OK) return st;
+        }
+    }
+    return HS_OK;
+}
+
 hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_kind,
-                        const DevBoundary &b, void *F, int out_df, cudaStream_t s, double *f2) {
+                        const DevBoundary &b, void *F, int out_df, cudaStream_t s, double *f2,
+                        int bz0, int nbz) {
     RhsArgs a;
     a.Nx = P->Nx;
     a.Ny = P->Ny;
@@ -327,8 +372,12 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
     for (int k = 0; k < 6; ++k)
         if (b.face[k]) a.has_faces = 1;
     if (rhs_kind == HS_RHS_NODAL) {
+        const int tz = (P->Nz + RZ - 1) / RZ;
+        a.bz0 = bz0 < 0 ? 0 : bz0;
+        const int cnt = nbz < 0 ? tz - a.bz0 : nbz;
+        if (cnt <= 0) return HS_OK;
         dim3 tb(RTX, RTY, 1);
-        dim3 tg((P->Nx + RTX - 1) / RTX, (P->Ny + RTY - 1) / RTY, (P->Nz + RZ - 1) / RZ);
+        dim3 tg((P->Nx + RTX - 1) / RTX, (P->Ny + RTY - 1) / RTY, (unsigned)cnt);
         if (f_dtype == HS_F64) {
             if (out_df)
                 rhs_tiled_df_kernel<double><<<tg, tb, 0, s>>>(a, static_cast<const double *>(f),
@@ -344,6 +393,7 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
         }
         return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
     }
+    a.bz0 = 0;
     dim3 block(32, 8, 1);
     dim3 grid((P->Nx + 31) / 32, (P->Ny + 7) / 8, P->Nz);
     if (f_dtype == HS_F64) {

@@ -190,6 +190,69 @@ def test_host_pointers_match_device():
 
 
 @pytest.mark.parametrize("precision", [H.HS_FP64, H.HS_MIXED])
+def test_host_multi_rhs_chunked_upload(precision):
+    """Staged host f is uploaded in z-chunks overlapping the right-hand-side
+    kernel (slabs of z-tiles), the other right-hand sides in one copy overlapping
+    the first solve: results equal the device-buffer solve, for an Nz that leaves
+    a ragged last tile."""
+    torch = _torch()
+    Nx, Ny, Nz, R = 37, 29, 70, 3
+    probs = [random_problem((Nx, Ny, Nz), 6, W.HELMHOLTZ, seed=20 + r, faces=False)
+             for r in range(R)]
+    p = probs[0]
+    F = np.stack([q.f_nodes for q in probs])
+    s = H.Solver(Nx, Ny, Nz, p.Lx, p.Ly, p.Lz, 6, H.HS_HELMHOLTZ, precision, max_rhs=R)
+    try:
+        s.set_coeff(p.c0, p.c1, p.c2)
+        if precision == H.HS_MIXED:
+            H.hs_set_refinement(s.plan, 2)
+        ud = torch.zeros((R, Nz, Ny, Nx), dtype=torch.float64, device="cuda")
+        s.solve(torch.from_numpy(F).cuda(), ud, H.HS_F64, H.HS_RHS_NODAL, nrhs=R)
+        for pinned in (True, False):
+            fh = torch.from_numpy(F.copy())
+            uh = torch.full((R, Nz, Ny, Nx), np.nan, dtype=torch.float64)
+            if pinned:
+                fh, uh = fh.pin_memory(), uh.pin_memory()
+            for _ in range(2):   # the second call reuses the staging buffer
+                s.solve(fh, uh, H.HS_F64, H.HS_RHS_NODAL, nrhs=R)
+            torch.cuda.synchronize()
+            assert np.array_equal(uh.numpy(), ud.cpu().numpy())
+    finally:
+        s.close()
+
+
+def test_early_upload_back_to_back_solves():
+    """HS_HOST_F_EARLY: each call's f upload may start while the previous solve
+    still runs; three back-to-back calls with different f each give their own
+    device-buffer result."""
+    torch = _torch()
+    shape = (45, 38, 51)
+    probs = [random_problem(shape, 6, W.HELMHOLTZ, seed=30 + r, faces=False) for r in range(3)]
+    p = probs[0]
+    s = H.Solver(p.Nx, p.Ny, p.Nz, p.Lx, p.Ly, p.Lz, 6, H.HS_HELMHOLTZ, H.HS_MIXED)
+    try:
+        s.set_coeff(p.c0, p.c1, p.c2)
+        refs = []
+        for q in probs:
+            ud = torch.zeros((p.Nz, p.Ny, p.Nx), dtype=torch.float64, device="cuda")
+            s.solve(torch.from_numpy(q.f_nodes).cuda(), ud, H.HS_F64, H.HS_RHS_NODAL)
+            refs.append(ud)
+        torch.cuda.synchronize()
+        H.hs_set_host_io(s.plan, H.HS_HOST_F_EARLY)
+        fh = [torch.from_numpy(q.f_nodes.copy()).pin_memory() for q in probs]
+        uh = [torch.full((p.Nz, p.Ny, p.Nx), np.nan, dtype=torch.float64).pin_memory()
+              for _ in probs]
+        for rep in range(2):
+            for k in range(3):
+                s.solve(fh[k], uh[k], H.HS_F64, H.HS_RHS_NODAL)
+        torch.cuda.synchronize()
+        for k in range(3):
+            assert torch.equal(uh[k], refs[k].cpu()), k
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("precision", [H.HS_FP64, H.HS_MIXED])
 def test_pinned_host_buffers_in_place_and_staged(precision):
     """Pinned host f and u are used in place through their device alias (either
     or both) or staged (default); pageable ones are always staged.  All give the
