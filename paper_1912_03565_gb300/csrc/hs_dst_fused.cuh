@@ -22,9 +22,44 @@
 
 namespace hs_tiles {
 
+// In-place length-32 DFT (forward) as 4 x 8: the length-4 and length-8 DFTs use
+// the constant 48th roots, the twiddles W_32^(n2 k1) between them come from the
+// line's table of M-th roots (W_32^m = W_M^(m M / 32)).  Natural order in; the
+// result X[k1 + 4 k2] is left at x[8 k1 + k2] (see nat()).
+__device__ __forceinline__ void dft32_inplace(float2 *x, const float2 *roots, int stride) {
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) {
+        float2 t[4];
+#pragma unroll
+        for (int n1 = 0; n1 < 4; ++n1) t[n1] = x[8 * n1 + n2];
+        Dft<float, 4>::run(t);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            float2 a = t[k1];
+            if (n2 * k1 != 0) {
+                const float2 r = roots[n2 * k1 * stride];
+                a = make_float2(a.x * r.x - a.y * r.y, a.x * r.y + a.y * r.x);
+            }
+            x[8 * k1 + n2] = a;
+        }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) Dft<float, 8>::run(x + 8 * k1);
+}
+
+// Where output r of dft_regs<R> is stored.
 template <int R>
-__device__ __forceinline__ void dft_regs(float2 *v) {
-    Dft<float, R>::run(v);
+__host__ __device__ constexpr int nat(int r) {
+    return R == 32 ? 8 * (r % 4) + r / 4 : r;
+}
+
+// In-register DFT of length R: constant roots where R divides 48, else 32.
+template <int R, int M>
+__device__ __forceinline__ void dft_regs(float2 *v, const float2 *roots) {
+    if constexpr (R == 32)
+        dft32_inplace(v, roots, M / 32);
+    else
+        Dft<float, R>::run(v);
 }
 
 // Element m of the odd extension of the line at `row` (m in [0, 2M)).
@@ -45,6 +80,7 @@ __device__ __forceinline__ void dst_fused_tile(const Tin *in, Tout *out, double 
     constexpr int N = M - 1;
     constexpr int LS = LineStride<M>::value;
     constexpr int NT = 256;
+    static_assert(R1 != 32, "the first stage runs before the root table is complete");
     constexpr int B1 = M / R1;   // first-stage butterflies per line
     constexpr int NsL = M / RL;  // butterflies (and Ns) of the last stage
     const size_t lo_off = (size_t)Nx * Ny * Nz;
@@ -102,7 +138,7 @@ __device__ __forceinline__ void dst_fused_tile(const Tin *in, Tout *out, double 
 #pragma unroll
             for (int r = 0; r < R1; ++r) v[r] = make_float2(0.f, 0.f);
         }
-        dft_regs<R1>(v);
+        dft_regs<R1, M>(v, roots);
         float2 *y = buf0 + s * LS;
 #pragma unroll
         for (int r = 0; r < R1; ++r) y[PAD(j * R1 + r)] = v[r];
@@ -136,7 +172,7 @@ __device__ __forceinline__ void dst_fused_tile(const Tin *in, Tout *out, double 
                     v[r] = make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
                 }
             }
-            dft_regs<RL>(v);   // v[r] = W_{j + NsL r}
+            dft_regs<RL, M>(v, roots);   // v[nat(r)] = W_{j + NsL r}
             const int lane = threadIdx.x & 31;
             const int src_lane = (lane & ~(NsL - 1)) | ((NsL - j) & (NsL - 1));
             const bool live = inl && s < nel_rows;
@@ -145,9 +181,11 @@ __device__ __forceinline__ void dst_fused_tile(const Tin *in, Tout *out, double 
             constexpr bool RMW = MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL;
             // read-modify-write modes: every (hi, lo) of this lane's outputs is
             // loaded before the first store (the stores could alias the loads as
-            // far as the compiler knows, which would serialise them)
-            float uh[RMW ? RL : 1], ul[RMW ? RL : 1];
-            if constexpr (RMW) {
+            // far as the compiler knows, which would serialise them); for a
+            // length-32 last stage the registers are not there, so it loads per output
+            constexpr bool PRE = RMW && RL <= 24;
+            float uh[PRE ? RL : 1], ul[PRE ? RL : 1];
+            if constexpr (PRE) {
 #pragma unroll
                 for (int r = 0; r < RL; ++r) {
                     const int K = j + NsL * r;
@@ -160,16 +198,16 @@ __device__ __forceinline__ void dst_fused_tile(const Tin *in, Tout *out, double 
             for (int r = 0; r < RL; ++r) {
                 // partner of K = j + NsL r is M - K = (NsL - j) + NsL (RL - 1 - r) (j > 0),
                 // or NsL (RL - r) held by this lane (j = 0)
-                const float px = __shfl_sync(0xffffffffu, v[RL - 1 - r].x, src_lane);
-                const float py = __shfl_sync(0xffffffffu, v[RL - 1 - r].y, src_lane);
-                const float2 Wk = v[r];
-                const float2 Wm = j > 0 ? make_float2(px, py) : v[(RL - r) % RL];
+                const float px = __shfl_sync(0xffffffffu, v[nat<RL>(RL - 1 - r)].x, src_lane);
+                const float py = __shfl_sync(0xffffffffu, v[nat<RL>(RL - 1 - r)].y, src_lane);
+                const float2 Wk = v[nat<RL>(r)];
+                const float2 Wm = j > 0 ? make_float2(px, py) : v[nat<RL>((RL - r) % RL)];
                 const int K = j + NsL * r;
                 if (live && K > 0) {
                     const float2 cs = half[K];
                     const float X =
                         ((Wm.y - Wk.y) + cs.x * (Wk.x - Wm.x) + cs.y * (Wk.y + Wm.y)) * q;
-                    if constexpr (RMW) {
+                    if constexpr (PRE) {
                         dfloat a;
                         a.hi = uh[r];
                         a.lo = ul[r];

@@ -62,7 +62,7 @@ hs_status fused_launch_sized(const hs_plan_s *P, const DstAxis &ax, const void *
             if constexpr (AXIS == HS_AXIS_Y) {
                 HS_F(1024, 16, 16, 4);
             } else {
-                return HS_ERR_UNSUPPORTED;  // 64 lanes per line in the last stage
+                HS_F(1024, 16, 32, 2);   // 32 lanes per line: a length-32 last stage
             }
         default: return HS_ERR_UNSUPPORTED;
     }
