@@ -429,7 +429,7 @@ def bench_precond(args, torch, H, rank, world, barrier, max_over_ranks):
                        "l2": "inputs larger than L2 (8 vectors of 133 MB per solve)"},
             "fp64_preconditioner": res["fp64"], "mixed_preconditioner": res["mixed"],
             "accuracy": {"mixed_vs_fp64_preconditioned_solution": diff,
-                         "judged_against": "the same BiCGStab with the FP64 plan as preconditioner"},
+                         "compared_against": "the same BiCGStab with the FP64 plan as preconditioner"},
             "cpu_baseline": None, "e2e": None, "roofline": None, "clocks": clocks,
             "gpu_launches": res["mixed"]["gpu_launches"],
         }
@@ -495,7 +495,7 @@ def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
 
     res64 = [fp64_residuals(pr, u) for pr, u in zip(probs, u64)]
 
-    def judge():
+    def assess():
         """Forward error against the FP64 path for every (problem, RHS); where it
         is above 1e-10, the backward error: the FP64 residual of the result
         against that of the FP64 path's answer (ill-conditioned problems, where
@@ -530,7 +530,7 @@ def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
     for cand in ((1e-9, 1e-10, 1e-11, 1e-12, 0.0) if args.sweeps < 0 else (0.0,)):
         H.hs_batch_set_tol(b, cand)
         H.hs_batch_solve(b, stream, True)
-        tried[cand] = judge()
+        tried[cand] = assess()
         tol = cand
         if tried[cand]["ok"]:
             break
@@ -540,7 +540,7 @@ def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
     tune = {"variant": H.hs_batch_get_variant(b)[0], "grid": H.hs_batch_get_variant(b)[1],
             "ms": tuned_ms, "autotune_s": time.perf_counter() - t0}
     H.hs_batch_solve(b, stream, True)
-    acc = {"judged_against": "fp64 GPU path, every problem and RHS: forward error <= 1e-10, "
+    acc = {"compared_against": "fp64 GPU path, every problem and RHS: forward error <= 1e-10, "
                              "else FP64 residual <= 4x the FP64 path's",
            "max_sweeps": max_sweeps, "residual_tol": tol, "residual_precision": "auto",
            "result": tried[tol],
@@ -698,7 +698,7 @@ def main():
     if wk.ref is not None:
         ref = torch.from_numpy(wk.ref).cuda()
         acc["fp64_vs_oracle"] = rel(u64 if R == 1 else u64[0], ref)
-    acc["judged_against"] = "oracle" if ref is not None else "fp64 GPU path"
+    acc["compared_against"] = "oracle" if ref is not None else "fp64 GPU path"
     by_sweeps = []
     for sw in range(0, 4):
         ss = solver(H.HS_MIXED, sw)
