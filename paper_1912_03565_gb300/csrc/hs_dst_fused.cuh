@@ -70,6 +70,88 @@ __device__ __forceinline__ float ext_x(const Tin *row, int m) {
     return -(float)ldc<COH>(row + (2 * M - m - 1));
 }
 
+// One Stockham stage of radix R done in place: every thread loads the inputs of
+// all its butterflies (CNT of them) into registers, the block synchronises, and
+// the outputs overwrite the same buffer.  One line buffer instead of two: twice
+// the CTAs fit in shared memory where that was the limit.
+template <int M, int S, int R, int Ns>
+__device__ __forceinline__ void fstage_inplace(float2 *buf, const float2 *roots) {
+    constexpr int LS = LineStride<M>::value;
+    constexpr int MR = M / R;
+    constexpr int stride = M / (Ns * R);
+    constexpr int NT = 256;
+    constexpr int TOT = S * MR;
+    constexpr int CNT = (TOT + NT - 1) / NT;
+    float2 v[CNT][R];
+#pragma unroll
+    for (int c = 0; c < CNT; ++c) {
+        const int t = threadIdx.x + c * NT;
+        if (t < TOT) {
+            const int sl = t / MR;
+            const int j = t - sl * MR;
+            const float2 *x = buf + sl * LS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[c][r] = x[PAD(j + r * MR)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < CNT; ++c) {
+        const int t = threadIdx.x + c * NT;
+        if (t < TOT) {
+            const int sl = t / MR;
+            const int j = t - sl * MR;
+            const int k = j % Ns;
+            if (Ns > 1 && k > 0) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const float2 w = roots[k * r * stride];
+                    const float2 a = v[c][r];
+                    v[c][r] = make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+                }
+            }
+            Dft<float, R>::run(v[c]);
+            const int idxD = (j / Ns) * Ns * R + k;
+            float2 *y = buf + sl * LS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) y[PAD(idxD + r * Ns)] = v[c][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int M, int S, int Ns>
+__device__ __forceinline__ void fstages_inplace(float2 *, const float2 *) {}
+
+template <int M, int S, int Ns, int R, int... Rest>
+__device__ __forceinline__ void fstages_inplace(float2 *buf, const float2 *roots) {
+    fstage_inplace<M, S, R, Ns>(buf, roots);
+    fstages_inplace<M, S, Ns * R, Rest...>(buf, roots);
+}
+
+// Registers of the in-place stages: every stage after the first (and the last
+// one of y tiles, which goes back through shared memory) holds at most 32
+// complex values per thread.
+template <int M, int S, int R>
+__host__ __device__ constexpr bool stage_fits() {
+    return ((S * (M / R) + 255) / 256) * R <= 32;
+}
+template <int AXIS, int M, int S, int R1, int RL, int... Rmid>
+__host__ __device__ constexpr bool fused_inplace() {
+    return (stage_fits<M, S, Rmid>() && ... && true) &&
+           (AXIS == HS_AXIS_X || stage_fits<M, S, RL>());
+}
+
+// Shared memory of a fused tile: the two root tables and one line buffer per
+// line (in place) or two.
+template <int AXIS, int M, int S, int R1, int RL, int... Rmid>
+__host__ __device__ constexpr size_t fused_smem() {
+    return sizeof(float2) *
+           ((size_t)2 * M + 1 +
+            (size_t)(fused_inplace<AXIS, M, S, R1, RL, Rmid...>() ? 1 : 2) * S *
+                LineStride<M>::value);
+}
+
 // One CTA: S whole lines.  Radices: R1 first, RL last, Rmid... in between.
 template <typename Tin, typename Tout, int AXIS, int MODE, int M, int S, bool COH, int R1, int RL,
           int... Rmid>
@@ -145,8 +227,12 @@ __device__ __forceinline__ void dst_fused_tile(const Tin *in, Tout *out, double 
     }
     __syncthreads();
 
+    constexpr bool INPL = fused_inplace<AXIS, M, S, R1, RL, Rmid...>();
     float2 *src = buf0, *dst = buf1;
-    fstages<float, M, S, R1, Rmid...>(src, dst, roots);  // middle stages (each ends in a barrier)
+    if constexpr (INPL)
+        fstages_inplace<M, S, R1, Rmid...>(buf0, roots);   // middle stages, one buffer
+    else
+        fstages<float, M, S, R1, Rmid...>(src, dst, roots);  // each ends in a barrier
 
     const float q = scale * 0.25f;
     if constexpr (AXIS == HS_AXIS_X) {
@@ -226,9 +312,14 @@ __device__ __forceinline__ void dst_fused_tile(const Tin *in, Tout *out, double 
         }
     } else {
         // ---- last stage through shared memory, pairing read back per output
-        fstage<float, M, S, RL, NsL>(src, dst, roots);
-        __syncthreads();
-        src = dst;
+        if constexpr (INPL) {
+            fstage_inplace<M, S, RL, NsL>(buf0, roots);
+            src = buf0;
+        } else {
+            fstage<float, M, S, RL, NsL>(src, dst, roots);
+            __syncthreads();
+            src = dst;
+        }
 #pragma unroll 4
         for (int e = threadIdx.x; e < S * N; e += NT) {
             const int kk = e / S;

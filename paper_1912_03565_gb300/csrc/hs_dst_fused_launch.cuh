@@ -23,7 +23,7 @@ template <typename Tin, typename Tout, int AXIS, int MODE, int M, int R1, int RL
 hs_status fused_launch_m(const hs_plan_s *P, const DstAxis &ax, const void *in, void *out,
                          double scale, cudaStream_t st, double *aux) {
     constexpr int S = Lines<float, M, AXIS>::value;
-    constexpr size_t smem = fast_smem<float, M, S>();
+    constexpr size_t smem = fused_smem<AXIS, M, S, R1, RL, Rmid...>();
     static_assert(smem <= 227 * 1024, "transform tile exceeds shared memory");
     static_assert(R1 * RL * (1 * ... * Rmid) == M, "radices must multiply to M");
     auto k = dst_fused_kernel<Tin, Tout, AXIS, MODE, M, S, R1, RL, Rmid...>;
