@@ -63,10 +63,11 @@ enum { HS_F64 = 0, HS_F32 = 1 };                             /* element type of 
 enum { HS_RHS_NODAL = 0, HS_RHS_ASSEMBLED = 1 };             /* meaning of f */
 enum { HS_RESID_DF = 0, HS_RESID_F64 = 1, HS_RESID_AUTO = 2 }; /* refinement residual */
 enum { HS_DST_STAGED = 0, HS_DST_FUSED = 1, HS_DST_GENERIC = 2,   /* transform kernels */
-       HS_DST_TWOPASS = 3 };
+       HS_DST_TWOPASS = 3, HS_DST_FUSED_WIDE = 4 };
 enum { HS_AXIS_X = 0, HS_AXIS_Y = 1 };                       /* transform axis */
 enum { HS_FACTOR_AUTO = 0, HS_FACTOR_F32 = 1, HS_FACTOR_F64 = 2 }; /* mixed z-solve factors */
-enum { HS_HOST_F_MAPPED = 1, HS_HOST_U_MAPPED = 2, HS_HOST_F_EARLY = 4 };  /* hs_set_host_io */
+enum { HS_HOST_F_MAPPED = 1, HS_HOST_U_MAPPED = 2, HS_HOST_F_EARLY = 4,     /* hs_set_host_io */
+       HS_HOST_U_LATE = 8 };
 enum { HS_THOMAS_PIPE16_256 = 0, HS_THOMAS_PIPE8_128 = 1,    /* FP32 z-solve mapping */
        HS_THOMAS_PLAIN16_256 = 2, HS_THOMAS_PIPE16_128 = 3 };
 
@@ -190,7 +191,11 @@ hs_status hs_set_refinement_tol(hs_plan_t plan, double tol);
  *   HS_DST_TWOPASS y only, HS_MIXED plans, N + 1 in {512, 768, 1024}: the FFT
  *                  split M = 32 M2 over two kernels, every access a whole
  *                  128-byte row segment of 32 columns; allocates a complex
- *                  scratch of 8 bytes per unknown while selected.
+ *                  scratch of 8 bytes per unknown while selected;
+ *   HS_DST_FUSED_WIDE  HS_DST_FUSED with twice the lines per CTA (for y,
+ *                  longer row segments per access), for the lengths whose
+ *                  tile then still runs its stages in one shared buffer
+ *                  (HS_ERR_UNSUPPORTED for the others).
  * Results agree to rounding.  Default: HS_DST_STAGED where compiled.
  * Errors: HS_ERR_INVALID_ARG; HS_ERR_UNSUPPORTED (variant not built for this
  * length, axis or precision); HS_ERR_OOM.
@@ -247,17 +252,34 @@ hs_status hs_set_factor_precision(hs_plan_t plan, int mode);
  *   HS_HOST_F_MAPPED  a pinned f is read in place by the right-hand-side kernel
  *                     through its device alias (no staging);
  *   HS_HOST_U_MAPPED  a pinned u is written in place by the last transform pass;
- *   HS_HOST_F_EARLY   the copy of a staged f does not wait for the work queued
- *                     before the call on the stream, only until the previous
- *                     solve has finished reading the staging buffer, so it
- *                     overlaps that solve.  Use only when no work queued on the
- *                     stream writes the host f (for example f filled by the CPU).
+ *   HS_HOST_F_EARLY   the copies of a staged f and of host boundary arrays do
+ *                     not wait for the work queued before the call on the
+ *                     stream, only until the solve before the previous one has
+ *                     read the plan's staging buffers (two sets, used in turn),
+ *                     so they overlap the previous solve; the right-hand-side
+ *                     kernel then runs as one launch after the whole copy.  Use
+ *                     only when no work queued on the stream writes those host
+ *                     arrays (for example arrays filled by the CPU).
+ *   HS_HOST_U_LATE    the copy of a staged u back to the host runs on a
+ *                     plan-owned stream after the solve, so it overlaps the work
+ *                     queued after the call (the next solve); two device staging
+ *                     buffers of u are used in turn.  The host u is complete only
+ *                     once a stream made to wait by hs_host_io_wait has reached
+ *                     that point (or after cudaDeviceSynchronize).  Solves called
+ *                     with an hs_info copy back on the caller's stream as usual.
  * On GB300, 255^3, 6th order, pinned host buffers, back-to-back solves: 2.51 ms
  * per solve staged (2.66 ms copying f whole), 2.22 ms with HS_HOST_F_EARLY; in
  * place: 2.94 (u), 3.19 (f), 3.47 ms (both) -- the kernels' access pattern over
  * the host link costs more than one bulk copy.  Errors: HS_ERR_INVALID_ARG.
  */
 hs_status hs_set_host_io(hs_plan_t plan, int mapped);
+
+/*
+ * hs_host_io_wait -- makes `stream` wait (without blocking the host) until
+ * every copy of u to the host queued by HS_HOST_U_LATE solves of this plan is
+ * done.  A no-op when none was queued.  Errors: HS_ERR_INVALID_ARG, HS_ERR_CUDA.
+ */
+hs_status hs_host_io_wait(hs_plan_t plan, void *stream);
 
 /*
  * hs_set_stage_timing -- when on (1), solves record CUDA events around each

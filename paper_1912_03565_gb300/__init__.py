@@ -35,10 +35,10 @@ HS_CD_PAPER, HS_CD_CORRECTED = 0, 1
 HS_F64, HS_F32 = 0, 1
 HS_RHS_NODAL, HS_RHS_ASSEMBLED = 0, 1
 HS_RESID_DF, HS_RESID_F64, HS_RESID_AUTO = 0, 1, 2
-HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC, HS_DST_TWOPASS = 0, 1, 2, 3
+HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC, HS_DST_TWOPASS, HS_DST_FUSED_WIDE = 0, 1, 2, 3, 4
 HS_AXIS_X, HS_AXIS_Y = 0, 1
 HS_FACTOR_AUTO, HS_FACTOR_F32, HS_FACTOR_F64 = 0, 1, 2
-HS_HOST_F_MAPPED, HS_HOST_U_MAPPED, HS_HOST_F_EARLY = 1, 2, 4
+HS_HOST_F_MAPPED, HS_HOST_U_MAPPED, HS_HOST_F_EARLY, HS_HOST_U_LATE = 1, 2, 4, 8
 HS_THOMAS_PIPE16_256, HS_THOMAS_PIPE8_128, HS_THOMAS_PLAIN16_256, HS_THOMAS_PIPE16_128 = 0, 1, 2, 3
 HS_INFO_MAX_ITERS = 8
 HS_INFO_STAGES = 8
@@ -53,7 +53,7 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_batch_set_variant", "hs_batch_get_variant", "hs_batch_autotune",
             "hs_batch_graph_kernels",
             "hs_set_transform_variant", "hs_get_transform_variant", "hs_autotune",
-            "hs_set_thomas_variant", "hs_get_thomas_variant", "hs_set_host_io",
+            "hs_set_thomas_variant", "hs_get_thomas_variant", "hs_set_host_io", "hs_host_io_wait",
             "hs_set_factor_precision",
             "hs_precond_create", "hs_precond_apply", "hs_precond_solve", "hs_precond_destroy",
             "hs_batch_workspace_bytes", "hs_batch_destroy")
@@ -154,6 +154,8 @@ def load(path: Optional[str] = None):
     lib.hs_set_factor_precision.restype = ci
     lib.hs_set_host_io.argtypes = [vp, ci]
     lib.hs_set_host_io.restype = ci
+    lib.hs_host_io_wait.argtypes = [vp, vp]
+    lib.hs_host_io_wait.restype = ci
     lib.hs_set_thomas_variant.argtypes = [vp, ci]
     lib.hs_set_thomas_variant.restype = ci
     lib.hs_get_thomas_variant.argtypes = [vp, ctypes.POINTER(ci)]
@@ -422,6 +424,11 @@ def hs_set_factor_precision(plan, mode):
 
 def hs_set_host_io(plan, mapped):
     return _check(load().hs_set_host_io(plan, int(mapped)), "hs_set_host_io", plan)
+
+
+def hs_host_io_wait(plan, stream=None):
+    """Make `stream` wait for the plan's queued copies of u to the host (HS_HOST_U_LATE)."""
+    return _check(load().hs_host_io_wait(plan, _stream_ptr(stream)), "hs_host_io_wait", plan)
 
 
 def hs_set_thomas_variant(plan, variant):

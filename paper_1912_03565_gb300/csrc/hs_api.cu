@@ -99,15 +99,57 @@ hs_status ensure_upload(hs_plan_s *P) {
         cudaGetLastError();
         return HS_ERR_CUDA;
     }
-    for (int k = 0; k < HS_UP_CHUNKS + 3; ++k) {
-        if (cudaEventCreateWithFlags(&P->up_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+    const int nev = HS_UP_CHUNKS + 3 + P->max_rhs;
+    P->up_rhs = new (std::nothrow) cudaEvent_t[P->max_rhs];
+    if (!P->up_rhs) {
+        cudaStreamDestroy(P->up_stream);
+        return HS_ERR_OOM;
+    }
+    auto ev = [&](int k) -> cudaEvent_t & {
+        return k < HS_UP_CHUNKS + 3 ? P->up_ev[k] : P->up_rhs[k - HS_UP_CHUNKS - 3];
+    };
+    for (int k = 0; k < nev; ++k) {
+        if (cudaEventCreateWithFlags(&ev(k), cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
-            for (int j = 0; j < k; ++j) cudaEventDestroy(P->up_ev[j]);
+            for (int j = 0; j < k; ++j) cudaEventDestroy(ev(j));
+            delete[] P->up_rhs;
+            P->up_rhs = nullptr;
             cudaStreamDestroy(P->up_stream);
             return HS_ERR_CUDA;
         }
     }
+    P->f_buf = 0;
     P->have_up = 1;
+    return HS_OK;
+}
+
+// The download stream and events of HS_HOST_U_LATE (created once per plan).
+hs_status ensure_download(hs_plan_s *P) {
+    if (P->have_dn) return HS_OK;
+    if (cudaStreamCreateWithFlags(&P->dn_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return HS_ERR_CUDA;
+    }
+    for (int k = 0; k < 3; ++k) {
+        if (cudaEventCreateWithFlags(&P->dn_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            for (int j = 0; j < k; ++j) cudaEventDestroy(P->dn_ev[j]);
+            cudaStreamDestroy(P->dn_stream);
+            return HS_ERR_CUDA;
+        }
+    }
+    P->dn_pending[0] = P->dn_pending[1] = 0;
+    P->dn_last = -1;
+    P->u_buf = 0;
+    P->have_dn = 1;
+    return HS_OK;
+}
+
+// Work queued on s next may overwrite u staging buffer b: it waits for a
+// queued copy of that buffer to the host.
+hs_status guard_stage_u(hs_plan_s *P, int b, cudaStream_t s) {
+    if (P->have_dn && P->dn_pending[b])
+        HS_CK(P, cudaStreamWaitEvent(s, P->dn_ev[b], 0));
     return HS_OK;
 }
 
@@ -132,12 +174,18 @@ void free_plan(hs_plan_s *P) {
     void *ptrs[] = {P->d_coef, P->d_c0, P->d_c1, P->d_cx, P->d_cy, P->d_fac, P->d_red,
                     P->d_tables, P->d_w64, P->d_w32, P->d_dscr, P->d_stage_f, P->d_stage_u,
                     P->d_stage_bnd, P->d_fac32, P->d_coef_df, P->d_Fdf, P->d_Udf, P->d_rhs_df,
-                    P->d_skip, P->d_ytmp};
+                    P->d_skip, P->d_ytmp, P->d_stage_u1, P->d_stage_f1, P->d_stage_bnd1};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->have_up) {
         for (int k = 0; k < HS_UP_CHUNKS + 3; ++k) cudaEventDestroy(P->up_ev[k]);
+        for (int k = 0; k < P->max_rhs; ++k) cudaEventDestroy(P->up_rhs[k]);
+        delete[] P->up_rhs;
         cudaStreamDestroy(P->up_stream);
+    }
+    if (P->have_dn) {
+        for (int k = 0; k < 3; ++k) cudaEventDestroy(P->dn_ev[k]);
+        cudaStreamDestroy(P->dn_stream);
     }
     if (P->have_events) {
         for (int k = 0; k < 2 * HS_EVENT_PAIRS; ++k) cudaEventDestroy(P->ev[k]);
@@ -285,8 +333,10 @@ size_t face_count(const hs_plan_s *P, int k) {
 }
 
 // Copies host-resident boundary arrays to the plan's staging buffer.
+// Host boundary arrays are copied on stream s into boundary staging buffer bb
+// (0 or 1); device ones are used in place.
 hs_status stage_boundary(hs_plan_s *P, const hs_boundary *bnd, size_t esz, cudaStream_t s,
-                         DevBoundary *out) {
+                         DevBoundary *out, int bb = 0) {
     memset(out, 0, sizeof(*out));
     if (!bnd) return HS_OK;
     size_t need = 0;
@@ -294,15 +344,17 @@ hs_status stage_boundary(hs_plan_s *P, const hs_boundary *bnd, size_t esz, cudaS
         const void *p = (k < 6) ? bnd->face[k] : bnd->fnn[k - 6];
         if (p && !is_device_ptr(p)) need += ((face_count(P, k % 6) * esz + 255) & ~(size_t)255);
     }
-    if (need > P->stage_bnd_bytes) {
-        if (P->d_stage_bnd) {
-            cudaFree(P->d_stage_bnd);
-            P->bytes -= P->stage_bnd_bytes;
+    void **buf = bb ? &P->d_stage_bnd1 : &P->d_stage_bnd;
+    size_t *bytes = bb ? &P->stage_bnd1_bytes : &P->stage_bnd_bytes;
+    if (need > *bytes) {
+        if (*buf) {
+            cudaFree(*buf);
+            P->bytes -= *bytes;
         }
-        P->d_stage_bnd = nullptr;
-        P->stage_bnd_bytes = 0;
-        HS_TRY(P, dev_alloc(P, (unsigned char **)&P->d_stage_bnd, need));
-        P->stage_bnd_bytes = need;
+        *buf = nullptr;
+        *bytes = 0;
+        HS_TRY(P, dev_alloc(P, (unsigned char **)buf, need));
+        *bytes = need;
     }
     size_t off = 0;
     for (int k = 0; k < 12; ++k) {
@@ -314,7 +366,7 @@ hs_status stage_boundary(hs_plan_s *P, const hs_boundary *bnd, size_t esz, cudaS
             continue;
         }
         const size_t nb = face_count(P, k % 6) * esz;
-        unsigned char *d = static_cast<unsigned char *>(P->d_stage_bnd) + off;
+        unsigned char *d = static_cast<unsigned char *>(*buf) + off;
         HS_CK(P, cudaMemcpyAsync(d, p, nb, cudaMemcpyHostToDevice, s));
         *dst = d;
         off += (nb + 255) & ~(size_t)255;
@@ -729,9 +781,15 @@ hs_status hs_set_residual_precision(hs_plan_t P, int mode) {
 
 hs_status hs_set_transform_variant(hs_plan_t P, int axis, int variant) {
     if (!P || (axis != HS_AXIS_X && axis != HS_AXIS_Y)) return HS_ERR_INVALID_ARG;
-    if (variant < HS_DST_STAGED || variant > HS_DST_TWOPASS) return HS_ERR_INVALID_ARG;
+    if (variant < HS_DST_STAGED || variant > HS_DST_FUSED_WIDE) return HS_ERR_INVALID_ARG;
     const bool fast = hs_dst_fast_size(P->axd[axis].M) != 0;
     if (variant == HS_DST_FUSED && (!fast || P->precision != HS_MIXED)) return HS_ERR_UNSUPPORTED;
+    if (variant == HS_DST_FUSED_WIDE) {
+        const int M = P->axf[axis].M;
+        if (!fast || P->precision != HS_MIXED ||
+            (axis == HS_AXIS_X ? hs_dst_fused_lines_x(M, 1) : hs_dst_fused_lines_y(M, 1)) == 0)
+            return HS_ERR_UNSUPPORTED;
+    }
     if (variant == HS_DST_STAGED && !fast) return HS_ERR_UNSUPPORTED;
     if (variant == HS_DST_TWOPASS) {
         if (axis != HS_AXIS_Y || P->precision != HS_MIXED ||
@@ -790,7 +848,7 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
     for (int axis = 0; axis < 2 && st == HS_OK; ++axis) {
         const int saved = P->dst_variant[axis];
         int best = -1;
-        for (int v = HS_DST_STAGED; v <= HS_DST_TWOPASS && st == HS_OK; ++v) {
+        for (int v = HS_DST_STAGED; v <= HS_DST_FUSED_WIDE && st == HS_OK; ++v) {
             if (hs_set_transform_variant(P, axis, v) != HS_OK) continue;
             // one untimed round (first launch, attribute set-up), then `reps`
             // timed.  x of a mixed plan: a forward pass and an inverse pass that
@@ -869,8 +927,16 @@ hs_status hs_set_factor_precision(hs_plan_t P, int mode) {
 
 hs_status hs_set_host_io(hs_plan_t P, int mapped) {
     if (!P) return HS_ERR_INVALID_ARG;
-    if (mapped < 0 || mapped > 7) return HS_ERR_INVALID_ARG;
+    if (mapped < 0 || mapped > 15) return HS_ERR_INVALID_ARG;
     P->host_io_mapped = mapped;
+    return HS_OK;
+}
+
+hs_status hs_host_io_wait(hs_plan_t P, void *stream) {
+    if (!P) return HS_ERR_INVALID_ARG;
+    // copies on the download stream run in order: the latest covers the others
+    if (P->have_dn && P->dn_last >= 0)
+        HS_CK(P, cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), P->dn_ev[P->dn_last], 0));
     return HS_OK;
 }
 
@@ -900,20 +966,27 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
     const void *f_mapped =
         (!is_device_ptr(f) && (P->host_io_mapped & HS_HOST_F_MAPPED)) ? mapped_host(f) : nullptr;
     bool piped = false;   // staged host f uploaded in chunks overlapping the first RHS kernel
+    int fb = 0;           // f and boundary staging buffers of this call
     if (f_mapped) {
         fd = static_cast<const unsigned char *>(f_mapped);
     } else if (!is_device_ptr(f)) {
         const size_t nb = fcount * esz * nrhs;
-        if (nb > P->stage_f_bytes) {
-            if (P->d_stage_f) { cudaFree(P->d_stage_f); P->bytes -= P->stage_f_bytes; }
-            P->d_stage_f = nullptr;
-            P->stage_f_bytes = 0;
-            HS_TRY(P, dev_alloc(P, (unsigned char **)&P->d_stage_f, nb));
-            P->stage_f_bytes = nb;
-        }
         piped = rhs_kind == HS_RHS_NODAL && ensure_upload(P) == HS_OK;
-        if (!piped) HS_CK(P, cudaMemcpyAsync(P->d_stage_f, f, nb, cudaMemcpyHostToDevice, s));
-        fd = static_cast<const unsigned char *>(P->d_stage_f);
+        // HS_HOST_F_EARLY: two staging buffers in turn, so a call's upload waits
+        // only for the solve before the previous one
+        if (piped && (P->host_io_mapped & HS_HOST_F_EARLY)) fb = P->f_buf;
+        void **buf = fb ? &P->d_stage_f1 : &P->d_stage_f;
+        size_t *bytes = fb ? &P->stage_f1_bytes : &P->stage_f_bytes;
+        if (nb > *bytes) {
+            if (*buf) { cudaFree(*buf); P->bytes -= *bytes; }
+            *buf = nullptr;
+            *bytes = 0;
+            HS_TRY(P, dev_alloc(P, (unsigned char **)buf, nb));
+            *bytes = nb;
+        }
+        if (!piped) HS_CK(P, cudaMemcpyAsync(*buf, f, nb, cudaMemcpyHostToDevice, s));
+        fd = static_cast<const unsigned char *>(*buf);
+        if (piped) P->f_buf = (P->host_io_mapped & HS_HOST_F_EARLY) ? fb ^ 1 : 0;
     }
     double *ud = u;
     bool u_host = !is_device_ptr(u);
@@ -924,19 +997,49 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
         ud = u_mapped;
         u_host = false;
     }
+    // HS_HOST_U_LATE: the copy back runs on the download stream and overlaps the
+    // work queued after this call; the solves use the staging buffers in turn
+    const bool u_late = u_host && (P->host_io_mapped & HS_HOST_U_LATE) && !info &&
+                        ensure_download(P) == HS_OK;
+    // copies of u per right-hand side on the download stream (late ones, or
+    // several right-hand sides, each copied while the next is solved)
+    const bool u_down = u_late || (u_host && nrhs > 1 && ensure_download(P) == HS_OK);
+    int ub = 0;
     if (u_host) {
         const size_t nb = ucount * sizeof(double) * nrhs;
-        if (nb > P->stage_u_bytes) {
-            if (P->d_stage_u) { cudaFree(P->d_stage_u); P->bytes -= P->stage_u_bytes; }
-            P->d_stage_u = nullptr;
-            P->stage_u_bytes = 0;
-            HS_TRY(P, dev_alloc(P, &P->d_stage_u, ucount * (size_t)nrhs));
-            P->stage_u_bytes = nb;
+        ub = u_late ? P->u_buf : 0;
+        double **buf = ub ? &P->d_stage_u1 : &P->d_stage_u;
+        size_t *bytes = ub ? &P->stage_u1_bytes : &P->stage_u_bytes;
+        if (nb > *bytes) {
+            if (*buf) { cudaFree(*buf); P->bytes -= *bytes; }
+            *buf = nullptr;
+            *bytes = 0;
+            HS_TRY(P, dev_alloc(P, buf, ucount * (size_t)nrhs));
+            *bytes = nb;
         }
-        ud = P->d_stage_u;
+        HS_TRY(P, guard_stage_u(P, ub, s));
+        ud = *buf;
     }
     DevBoundary db;
-    HS_TRY(P, stage_boundary(P, bnd, esz, s, &db));
+    const bool early = piped && (P->host_io_mapped & HS_HOST_F_EARLY);
+    if (piped) {
+        if (early) {
+            // the caller vouches that no work queued on s writes the host f or
+            // boundary arrays: their copies wait only until the last
+            // right-hand-side kernel that read staging buffers fb is done (a
+            // never-recorded event is complete), so they may overlap the solves
+            // before it; the boundary goes first, the f chunks' events cover it
+            HS_CK(P, cudaStreamWaitEvent(P->up_stream, P->up_ev[HS_UP_CHUNKS + 1 + fb], 0));
+            HS_TRY(P, stage_boundary(P, bnd, esz, P->up_stream, &db, fb));
+        } else {
+            // stream order: the copies start after everything queued on s so far
+            HS_CK(P, cudaEventRecord(P->up_ev[HS_UP_CHUNKS], s));
+            HS_CK(P, cudaStreamWaitEvent(P->up_stream, P->up_ev[HS_UP_CHUNKS], 0));
+            HS_TRY(P, stage_boundary(P, bnd, esz, s, &db));
+        }
+    } else {
+        HS_TRY(P, stage_boundary(P, bnd, esz, s, &db));
+    }
 
     StageTimer T(P, s, P->stage_timing != 0 && P->have_events);
     timer_reset(P);
@@ -954,36 +1057,56 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
         T.begin(HS_STAGE_RHS);
         void *Fout = P->precision == HS_MIXED ? (void *)P->d_Fdf : (void *)P->d_w64;
         if (piped && r == 0) {
-            HS_TRY(P, hs_upload_rhs(P, f, P->d_stage_f, f_dtype, db, Fout, P->precision == HS_MIXED,
-                                    s, norms ? P->d_red + 4 : nullptr));
-            if (nrhs > 1) {
-                // the other right-hand sides in one copy, overlapping the first solve
-                const size_t one = fcount * esz;
-                HS_CK(P, cudaMemcpyAsync(static_cast<unsigned char *>(P->d_stage_f) + one,
-                                         static_cast<const unsigned char *>(f) + one,
-                                         one * (nrhs - 1), cudaMemcpyHostToDevice,
-                                         P->up_stream));
-                HS_CK(P, cudaEventRecord(P->up_ev[HS_UP_CHUNKS], P->up_stream));
+            // early uploads usually finish during the previous solve: one chunk,
+            // so the right-hand-side kernel runs as one launch
+            HS_TRY(P, hs_upload_rhs(P, f, const_cast<unsigned char *>(fd),
+                                    early ? 1 : HS_UP_CHUNKS, f_dtype, db, Fout,
+                                    P->precision == HS_MIXED, s, norms ? P->d_red + 4 : nullptr));
+            // the other right-hand sides one copy each, overlapping the solves before them
+            const size_t one = fcount * esz;
+            for (int q = 1; q < nrhs; ++q) {
+                HS_CK(P, cudaMemcpyAsync(const_cast<unsigned char *>(fd) + q * one,
+                                         static_cast<const unsigned char *>(f) + q * one, one,
+                                         cudaMemcpyHostToDevice, P->up_stream));
+                HS_CK(P, cudaEventRecord(P->up_rhs[q], P->up_stream));
             }
         } else {
-            if (piped && r == 1) HS_CK(P, cudaStreamWaitEvent(s, P->up_ev[HS_UP_CHUNKS], 0));
+            if (piped) HS_CK(P, cudaStreamWaitEvent(s, P->up_rhs[r], 0));
             HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db, Fout, P->precision == HS_MIXED,
                                     s, norms ? P->d_red + 4 : nullptr));
         }
-        // the last reader of the staged f is queued: the next solve's upload may start
-        if (piped && r == nrhs - 1) HS_CK(P, cudaEventRecord(P->up_ev[HS_UP_CHUNKS + 1], s));
+        // the last reader of staging buffers fb (f, boundary) is queued: a later
+        // early upload into them may start
+        if (P->have_up && r == nrhs - 1)
+            HS_CK(P, cudaEventRecord(P->up_ev[HS_UP_CHUNKS + 1 + fb], s));
         T.end(HS_STAGE_RHS);
         HS_TRY(P, solve_one(P, ur, s, T, ir));
         if (ir && P->precision == HS_FP64) {
             HS_TRY(P, hs_launch_rhs(P, fr, f_dtype, rhs_kind, db, P->d_w64, 0, s));
-            if (piped) HS_CK(P, cudaEventRecord(P->up_ev[HS_UP_CHUNKS + 1], s));
+            if (P->have_up) HS_CK(P, cudaEventRecord(P->up_ev[HS_UP_CHUNKS + 1 + fb], s));
             double r2, f2;
             HS_TRY(P, residual_norms(P, P->d_w64, ur, s, &r2, &f2));
             ir->rel_residual[0] = f2 > 0 ? sqrt(r2 / f2) : sqrt(r2);
         }
+        if (u_down) {
+            // this right-hand side's u goes back while the next ones are solved
+            HS_CK(P, cudaEventRecord(P->dn_ev[2], s));
+            HS_CK(P, cudaStreamWaitEvent(P->dn_stream, P->dn_ev[2], 0));
+            HS_CK(P, cudaMemcpyAsync(u + (size_t)r * ucount, ur, ucount * sizeof(double),
+                                     cudaMemcpyDeviceToHost, P->dn_stream));
+        }
     }
-    if (u_host)
+    if (u_down) {
+        HS_CK(P, cudaEventRecord(P->dn_ev[ub], P->dn_stream));
+        P->dn_pending[ub] = 1;
+        P->dn_last = ub;
+        if (u_late)
+            P->u_buf = ub ^ 1;
+        else   // the caller's stream is done only when u is on the host
+            HS_CK(P, cudaStreamWaitEvent(s, P->dn_ev[ub], 0));
+    } else if (u_host) {
         HS_CK(P, cudaMemcpyAsync(u, ud, ucount * sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    }
     if (T.on) {
         cudaEventRecord(P->ev_total[1], s);
         P->timer_total_pending = 1;
@@ -1030,6 +1153,7 @@ hs_status hs_residual(hs_plan_t P, const void *f, int f_dtype, int rhs_kind,
             HS_TRY(P, dev_alloc(P, &P->d_stage_u, ucount));
             P->stage_u_bytes = nb;
         }
+        HS_TRY(P, guard_stage_u(P, 0, s));
         HS_CK(P, cudaMemcpyAsync(P->d_stage_u, u, nb, cudaMemcpyHostToDevice, s));
         ud = P->d_stage_u;
     }
@@ -1037,6 +1161,8 @@ hs_status hs_residual(hs_plan_t P, const void *f, int f_dtype, int rhs_kind,
     HS_TRY(P, stage_boundary(P, bnd, esz, s, &db));
     HS_TRY(P, ensure_f64_work(P));
     HS_TRY(P, hs_launch_rhs(P, fd, f_dtype, rhs_kind, db, P->d_w64, 0, s));
+    // staging buffers 0 (f, boundary) read: an early upload of a later solve may reuse them
+    if (P->have_up) HS_CK(P, cudaEventRecord(P->up_ev[HS_UP_CHUNKS + 1], s));
     double r2, f2;
     HS_TRY(P, residual_norms(P, P->d_w64, ud, s, &r2, &f2));
     if (res_norm) *res_norm = sqrt(r2);

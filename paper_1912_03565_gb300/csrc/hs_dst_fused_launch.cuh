@@ -19,10 +19,26 @@ dst_fused_kernel(const Tin *in, Tout *out, double *aux, const float2 *roots_g,
         in, out, aux, roots_g, half_g, Nx, Ny, Nz, scale, smem_raw, blockIdx.x, blockIdx.y);
 }
 
-template <typename Tin, typename Tout, int AXIS, int MODE, int M, int R1, int RL, int... Rmid>
+// Lines per CTA of the fused tiles: as the staged tiles, or twice as many
+// (WIDE) when the stages run in place and the one buffer still fits.
+template <bool WIDE, int AXIS, int M, int R1, int RL, int... Rmid>
+struct FusedLines {
+    static constexpr int base = Lines<float, M, AXIS>::value;
+    static constexpr bool can = fused_inplace<AXIS, M, 2 * base, R1, RL, Rmid...>() &&
+                                fused_smem<AXIS, M, 2 * base, R1, RL, Rmid...>() <= 227 * 1024;
+    static constexpr int value = (WIDE && can) ? 2 * base : base;
+};
+
+template <typename Tin, typename Tout, int AXIS, int MODE, bool WIDE, int M, int R1, int RL,
+          int... Rmid>
 hs_status fused_launch_m(const hs_plan_s *P, const DstAxis &ax, const void *in, void *out,
-                         double scale, cudaStream_t st, double *aux) {
-    constexpr int S = Lines<float, M, AXIS>::value;
+                         double scale, cudaStream_t st, double *aux, int *probe) {
+    constexpr int S = FusedLines<WIDE, AXIS, M, R1, RL, Rmid...>::value;
+    if (WIDE && S == Lines<float, M, AXIS>::value) return HS_ERR_UNSUPPORTED;
+    if (probe) {   // lines per CTA only, nothing launched
+        *probe = S;
+        return HS_OK;
+    }
     constexpr size_t smem = fused_smem<AXIS, M, S, R1, RL, Rmid...>();
     static_assert(smem <= 227 * 1024, "transform tile exceeds shared memory");
     static_assert(R1 * RL * (1 * ... * Rmid) == M, "radices must multiply to M");
@@ -44,10 +60,10 @@ hs_status fused_launch_m(const hs_plan_s *P, const DstAxis &ax, const void *in, 
 
 // Radices per length: first R1, last RL (M / RL lanes per line in the last
 // stage: at most 32 and a divisor of 32, for the shuffle pairing of x-lines).
-template <typename Tin, typename Tout, int AXIS, int MODE>
+template <typename Tin, typename Tout, int AXIS, int MODE, bool WIDE = false>
 hs_status fused_launch_sized(const hs_plan_s *P, const DstAxis &ax, const void *in, void *out,
-                             double scale, cudaStream_t st, double *aux) {
-#define HS_F(...) return fused_launch_m<Tin, Tout, AXIS, MODE, __VA_ARGS__>(P, ax, in, out, scale, st, aux)
+                             double scale, cudaStream_t st, double *aux, int *probe = nullptr) {
+#define HS_F(...) return fused_launch_m<Tin, Tout, AXIS, MODE, WIDE, __VA_ARGS__>(P, ax, in, out, scale, st, aux, probe)
     switch (ax.M) {
         case 32: HS_F(32, 8, 4);
         case 64: HS_F(64, 16, 4);

@@ -50,15 +50,27 @@ struct hs_plan_s {
     int *d_skip;        // device flag: 1 once refinement has converged (later kernels return)
     const int *cur_skip;  // the flag the launchers pass on (NULL outside tolerance mode)
     int stage_timing;
-    int dst_variant[2];   // per axis: HS_DST_STAGED / HS_DST_FUSED / HS_DST_GENERIC
+    int dst_variant[2];   // per axis: one of HS_DST_* (hs.h)
     int thomas_variant;   // FP32 z-solve mapping: HS_THOMAS_*
     void *d_ytmp;         // complex scratch of the two-pass y transform (Nz x M x Nx float2)
     int resid_mode;       // HS_RESID_DF / HS_RESID_F64 / HS_RESID_AUTO
     int factor_mode;      // HS_FACTOR_AUTO / F32 / F64 (mixed path z-solves)
     int host_io_mapped;
     cudaStream_t up_stream;   // upload stream of the chunked host-f copy (lazily created)
-    cudaEvent_t up_ev[HS_UP_CHUNKS + 3];   // chunks, rest, staging free, call start
-    int have_up;   // bit 0: pinned host f read in place; bit 1: pinned host u written in place
+    // [0, K): chunks of the first right-hand side; [K]: call start; [K + 1 + b]:
+    // f staging buffer b free (its last right-hand-side kernel is queued)
+    cudaEvent_t up_ev[HS_UP_CHUNKS + 3];
+    cudaEvent_t *up_rhs;      // [max_rhs]: copy of right-hand side r done
+    int f_buf;                // f staging buffer of the next HS_HOST_F_EARLY solve
+    int have_up;   // up_stream and up_ev exist
+    // HS_HOST_U_LATE: the copy of a staged u to the host runs on dn_stream, out of
+    // one of two staging buffers (d_stage_u, d_stage_u1) used in turn
+    cudaStream_t dn_stream;
+    cudaEvent_t dn_ev[3];   // [b]: copy out of staging buffer b done; [2]: solve queued
+    int dn_pending[2];      // a copy out of buffer b has been queued
+    int dn_last;            // buffer of the latest queued copy (-1: none)
+    int u_buf;              // staging buffer of the next HS_HOST_U_LATE solve
+    int have_dn;
     int have_coeff;
     int cd_variant;
     double min_pivot_ratio;
@@ -93,10 +105,16 @@ struct hs_plan_s {
     // host staging (allocated on first use with host pointers)
     void *d_stage_f;
     size_t stage_f_bytes;
+    void *d_stage_f1;         // second f staging buffer (HS_HOST_F_EARLY)
+    size_t stage_f1_bytes;
     double *d_stage_u;
     size_t stage_u_bytes;
+    double *d_stage_u1;
+    size_t stage_u1_bytes;
     void *d_stage_bnd;
     size_t stage_bnd_bytes;
+    void *d_stage_bnd1;       // second boundary staging buffer (HS_HOST_F_EARLY)
+    size_t stage_bnd1_bytes;
 
     cudaEvent_t ev[2 * HS_EVENT_PAIRS];   // stage timing: begin/end pairs
     cudaEvent_t ev_total[2];
@@ -128,11 +146,15 @@ hs_status hs_launch_dst_fast(const hs_plan_s *P, int axis, int tc, int tin, cons
                              double *aux);
 
 // Fused FP32 transform tiles (k_dst_fused_x.cu, k_dst_fused_y.cu); HS_ERR_UNSUPPORTED
-// for a length or type combination they do not cover.
+// for a length or type combination they do not cover.  wide = 1: twice the
+// staged tile's lines per CTA (lengths whose in-place tile allows it).
 hs_status hs_launch_dst_fused_x(const hs_plan_s *P, int tin, const void *in, int tout, void *out,
-                                int mode, double scale, cudaStream_t s, double *aux);
+                                int mode, double scale, cudaStream_t s, double *aux, int wide);
 hs_status hs_launch_dst_fused_y(const hs_plan_s *P, int tin, const void *in, int tout, void *out,
-                                int mode, double scale, cudaStream_t s, double *aux);
+                                int mode, double scale, cudaStream_t s, double *aux, int wide);
+// Lines per CTA of the fused tile of length M (0: not built for that length).
+int hs_dst_fused_lines_x(int M, int wide);
+int hs_dst_fused_lines_y(int M, int wide);
 
 // Two-pass y transform for long lines (k_dst_twopass.cu): 1 for M in {512, 768, 1024};
 // needs P->d_ytmp.
@@ -146,14 +168,13 @@ int hs_dst_fits(const DstAxis &ax, int axis, int tc);
 // Lifted right-hand side F (interior) from f: FP64 (out_df = 0) or a
 // double-float pair in two FP32 planes [2][Nz][Ny][Nx] (out_df = 1).
 // Uploads one node-grid right-hand side from host memory fh into the device
-// staging buffer fd in HS_UP_CHUNKS chunks of z-planes on P->up_stream (after
-// the work already queued on s, or -- with HS_HOST_F_EARLY -- only after the
-// event P->up_ev[HS_UP_CHUNKS + 1], which the caller records on its stream once
-// the staging buffer's last reader is queued), and runs the tiled right-hand-side kernel on
-// stream s slab by slab, each slab waiting only for the chunk that holds its
-// last plane: the copy overlaps the kernel.  Needs P->have_up.
-hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int f_dtype, const DevBoundary &b,
-                        void *F, int out_df, cudaStream_t s, double *f2);
+// staging buffer fd in `chunks` (1..HS_UP_CHUNKS) chunks of z-planes on
+// P->up_stream, behind whatever the caller queued there before, and runs the
+// tiled right-hand-side kernel on stream s slab by slab, each slab waiting only
+// for the chunk that holds its last plane: the copy overlaps the kernel.
+// Needs P->have_up.
+hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int chunks, int f_dtype,
+                        const DevBoundary &b, void *F, int out_df, cudaStream_t s, double *f2);
 
 // For a nodal f the tiled kernels can run on a slab of z-tiles [bz0, bz0 + nbz)
 // (nbz < 0: to the last tile; tiles are RZ output planes).

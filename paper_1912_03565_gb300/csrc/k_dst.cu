@@ -350,10 +350,13 @@ hs_status hs_launch_dst(const hs_plan_s *P, int axis, int tc, int tin, const voi
         hs_dst_twopass_size(P->axf[HS_AXIS_Y].M))
         return hs_launch_dst_twopass_y(P, static_cast<const float *>(in),
                                        static_cast<float *>(out), scale, s);
-    if (v == HS_DST_FUSED && tc == HS_T_F32 && hs_dst_fast_size(P->axd[axis].M)) {
+    if ((v == HS_DST_FUSED || v == HS_DST_FUSED_WIDE) && tc == HS_T_F32 &&
+        hs_dst_fast_size(P->axd[axis].M)) {
+        const int wide = v == HS_DST_FUSED_WIDE;
         const hs_status st =
-            axis == HS_AXIS_X ? hs_launch_dst_fused_x(P, tin, in, tout, out, mode, scale, s, aux)
-                              : hs_launch_dst_fused_y(P, tin, in, tout, out, mode, scale, s, aux);
+            axis == HS_AXIS_X
+                ? hs_launch_dst_fused_x(P, tin, in, tout, out, mode, scale, s, aux, wide)
+                : hs_launch_dst_fused_y(P, tin, in, tout, out, mode, scale, s, aux, wide);
         if (st != HS_ERR_UNSUPPORTED) return st;
     }
     if (v != HS_DST_GENERIC && hs_dst_fast_size(P->axd[axis].M))

@@ -308,27 +308,14 @@ __global__ void __launch_bounds__(256) sumsq_kernel(const T *__restrict__ x, siz
 
 }  // namespace
 
-hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int f_dtype, const DevBoundary &b,
-                        void *F, int out_df, cudaStream_t s, double *f2) {
-    constexpr int K = HS_UP_CHUNKS;
+hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int chunks, int f_dtype,
+                        const DevBoundary &b, void *F, int out_df, cudaStream_t s, double *f2) {
+    const int K = chunks < 1 ? 1 : (chunks > HS_UP_CHUNKS ? HS_UP_CHUNKS : chunks);
     const size_t esz = f_dtype == HS_F64 ? 8 : 4;
     const size_t pb = (size_t)(P->Nx + 2) * (P->Ny + 2) * esz;   // bytes per node plane
     const int tz = (P->Nz + RZ - 1) / RZ;
     const unsigned char *src = static_cast<const unsigned char *>(fh);
     unsigned char *dst = static_cast<unsigned char *>(fd);
-    if (P->host_io_mapped & HS_HOST_F_EARLY) {
-        // the caller vouches that no work queued on s writes fh: the copy only
-        // waits until the previous solve's last right-hand-side kernel has read
-        // the staging buffer (a never-recorded event is complete), so it may
-        // overlap the rest of that solve
-        if (cudaStreamWaitEvent(P->up_stream, P->up_ev[K + 1], 0) != cudaSuccess)
-            return HS_ERR_CUDA;
-    } else {
-        // stream order: the copy starts after everything queued on s so far
-        if (cudaEventRecord(P->up_ev[K + 2], s) != cudaSuccess ||
-            cudaStreamWaitEvent(P->up_stream, P->up_ev[K + 2], 0) != cudaSuccess)
-            return HS_ERR_CUDA;
-    }
     int copied = 0;   // node planes [0, copied) are on their way
     for (int k = 0; k < K; ++k) {
         const int t0 = (k * tz) / K, t1 = ((k + 1) * tz) / K;

@@ -252,6 +252,66 @@ def test_early_upload_back_to_back_solves():
         s.close()
 
 
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_late_download_back_to_back_solves(nrhs):
+    """HS_HOST_U_LATE (with HS_HOST_F_EARLY): each call's copy of u to the host
+    runs on the plan's download stream while the next solve runs, out of two
+    staging buffers used in turn; after hs_host_io_wait on the caller's stream
+    every host u equals its device-buffer result.  A call without the flag right
+    after late ones (staging buffer 0 again) waits for the copy queued from it."""
+    torch = _torch()
+    shape = (45, 38, 51)
+    probs = [random_problem(shape, 6, W.HELMHOLTZ, seed=40 + r) for r in range(4)]
+    p = probs[0]
+    s = H.Solver(p.Nx, p.Ny, p.Nz, p.Lx, p.Ly, p.Lz, 6, H.HS_HELMHOLTZ, H.HS_MIXED,
+                 max_rhs=nrhs)
+    try:
+        s.set_coeff(p.c0, p.c1, p.c2)
+        # every call has its own Dirichlet faces and face data (staged with f)
+        groups = [np.stack([probs[(k + r) % 4].f_nodes for r in range(nrhs)]) for k in range(4)]
+        refs = []
+        for k, g in enumerate(groups):
+            ud = torch.zeros((nrhs, p.Nz, p.Ny, p.Nx), dtype=torch.float64, device="cuda")
+            faces = [None if a is None else torch.from_numpy(a).cuda() for a in probs[k].faces]
+            fnn = [None if a is None else torch.from_numpy(a).cuda() for a in probs[k].fnn]
+            s.solve(torch.from_numpy(g).cuda(), ud, H.HS_F64, H.HS_RHS_NODAL, faces, fnn,
+                    nrhs=nrhs)
+            refs.append(ud)
+        torch.cuda.synchronize()
+        H.hs_set_host_io(s.plan, H.HS_HOST_F_EARLY | H.HS_HOST_U_LATE)
+        fh = [torch.from_numpy(g.copy()).pin_memory() for g in groups]
+        bh = [([None if a is None else torch.from_numpy(a.copy()).pin_memory() for a in q.faces],
+               [None if a is None else torch.from_numpy(a.copy()).pin_memory() for a in q.fnn])
+              for q in probs]
+        uh = [torch.full((nrhs, p.Nz, p.Ny, p.Nx), np.nan, dtype=torch.float64).pin_memory()
+              for _ in groups]
+        stream = torch.cuda.current_stream()
+        keep = []   # the binding keeps only the last call's arrays alive
+        for rep in range(2):
+            for k in range(4):
+                s.solve(fh[k], uh[k], H.HS_F64, H.HS_RHS_NODAL, *bh[k], nrhs=nrhs)
+                keep.append(bh[k])
+        H.hs_host_io_wait(s.plan, stream)
+        stream.synchronize()
+        for k in range(4):
+            assert torch.equal(uh[k], refs[k].cpu()), k
+        # a call without the flag right after late ones reuses staging buffer 0
+        for k in range(4):
+            uh[k].fill_(np.nan)
+        for k in range(3):
+            s.solve(fh[k], uh[k], H.HS_F64, H.HS_RHS_NODAL, *bh[k], nrhs=nrhs)
+        H.hs_set_host_io(s.plan, H.HS_HOST_F_EARLY)
+        s.solve(fh[3], uh[3], H.HS_F64, H.HS_RHS_NODAL, *bh[3], nrhs=nrhs)
+        stream.synchronize()
+        assert torch.equal(uh[3], refs[3].cpu())
+        H.hs_host_io_wait(s.plan, stream)
+        stream.synchronize()
+        for k in range(3):
+            assert torch.equal(uh[k], refs[k].cpu()), k
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("precision", [H.HS_FP64, H.HS_MIXED])
 def test_pinned_host_buffers_in_place_and_staged(precision):
     """Pinned host f and u are used in place through their device alias (either
@@ -371,6 +431,7 @@ FAST_N = [31, 63, 95, 127, 191, 255, 383, 511, 767, 1023]
 @pytest.mark.parametrize("precision,variant", [(H.HS_FP64, H.HS_DST_STAGED),
                                                (H.HS_MIXED, H.HS_DST_STAGED),
                                                (H.HS_MIXED, H.HS_DST_FUSED),
+                                               (H.HS_MIXED, H.HS_DST_FUSED_WIDE),
                                                (H.HS_MIXED, H.HS_DST_TWOPASS)])
 def test_transform_lengths(N, precision, variant):
     """Every compile-time-sized transform length and kernel variant, along x and along
@@ -421,7 +482,8 @@ def test_autotune_keeps_a_valid_variant():
         assert mx > 0 and my > 0
         for axis in (H.HS_AXIS_X, H.HS_AXIS_Y):
             assert H.hs_get_transform_variant(s.plan, axis) in (
-                H.HS_DST_STAGED, H.HS_DST_FUSED, H.HS_DST_GENERIC, H.HS_DST_TWOPASS)
+                H.HS_DST_STAGED, H.HS_DST_FUSED, H.HS_DST_GENERIC, H.HS_DST_TWOPASS,
+                H.HS_DST_FUSED_WIDE)
         H.hs_set_refinement(s.plan, 2)
         f = torch.from_numpy(p.f_nodes).cuda()
         faces = [None if a is None else torch.from_numpy(a).cuda() for a in p.faces]
