@@ -1,0 +1,272 @@
+"""FP64 CPU oracle for complex k(z) and Robin z-faces.
+
+TEST INFRASTRUCTURE ONLY (same rule as hs_oracle: only the test-suite, the
+smoke check and the benchmark's CPU legs may import it; the solver library
+never calls it and shares no code with it).
+
+Section 1 states the paper's general problem: k is complex and depends on z
+only, u = 0 on the four side faces, and alpha u_z + beta u = g(x, y) on the two
+z-faces with complex alpha, beta.  The schemes and the direct solver of
+Sections 3 and 3.6 are worked out for Dirichlet data; the compact closure of a
+Robin face belongs to a cited work that the paper does not reproduce.  This
+module takes, for orders 2 and 4:
+
+  * interior rows l = 1..Nz: the compact rows of Sections 3.2 / 3.3 with
+    complex K = k^2.  Every coefficient is affine in K, so the complex table is
+    the real table of Re K plus i times the K-part of the real table of Im K;
+  * a Dirichlet z-face: its plane holds g, moved into the next row's right-hand
+    side through the stencil (as for the real problem);
+  * a Robin z-face: its plane is unknown and its row is the second-order
+    7-point scheme h_z^2 (dxx + dyy + dzz + K) u = h_z^2 f, the plane outside
+    eliminated with the central difference of the face condition:
+      lo face (l = 0):      alpha (u_1 - u_-1) / (2 h_z) + beta u_0 = g
+      hi face (l = Nz + 1): alpha (u_Nz+2 - u_Nz) / (2 h_z) + beta u_Nz+1 = g
+    (a second-order closure: the high-order one is out of this module's reach);
+  * right-hand side: the real operator R_h of the order applied to Re f and
+    Im f on interior rows, h_z^2 f plus the ghost's data term on Robin rows.
+
+The unknowns are the planes l0..l1 (l0 = 0 for a Robin lo face, else 1; l1 =
+Nz + 1 for a Robin hi face, else Nz).  Side faces stay Dirichlet, so Section
+3.6's sine transforms in x and y still split the system into N_x N_y complex
+tridiagonal systems in z; these are solved by the textbook recurrence.
+
+Arrays: f on the node grid [Nz+2][Ny+2][Nx+2] (complex; side-face nodes are
+never read by the 2nd-order rows and are 0 for the 4th-order operator as u is
+0 there -- they are read as given); face data g_lo, g_hi on the interior face
+nodes [Ny][Nx] (complex; None = 0); the solution on all planes [Nz+2][Ny][Nx]
+(Dirichlet planes hold g).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import hs_oracle as O
+
+DIRICHLET = 0
+ROBIN = 1
+
+
+class ZFaces:
+    """Kind (DIRICHLET / ROBIN) and Robin parameters of the two z-faces."""
+
+    def __init__(self, lo=DIRICHLET, alpha_lo=1.0, beta_lo=0.0, hi=DIRICHLET, alpha_hi=1.0,
+                 beta_hi=0.0):
+        self.lo, self.hi = lo, hi
+        self.alpha = (complex(alpha_lo), complex(alpha_hi))
+        self.beta = (complex(beta_lo), complex(beta_hi))
+        for kind, a in ((lo, self.alpha[0]), (hi, self.alpha[1])):
+            if kind == ROBIN and a == 0:
+                raise ValueError("a Robin face needs alpha != 0 (alpha = 0 is a Dirichlet face)")
+
+    def unknown_planes(self, Nz):
+        return (0 if self.lo == ROBIN else 1), (Nz + 1 if self.hi == ROBIN else Nz)
+
+
+def complex_coefficients(order, h, K):
+    """C[l-1, nu, m] (complex) for interior rows l = 1..Nz; K complex, length Nz + 2."""
+    if order not in (2, 4):
+        raise ValueError("complex coefficients: orders 2 and 4")
+    K = np.asarray(K, dtype=np.complex128)
+    zero = np.zeros(K.shape)
+    base = O.stencil_coefficients(order, O.HELMHOLTZ, h, zero)
+    re = O.stencil_coefficients(order, O.HELMHOLTZ, h, K.real)
+    im = O.stencil_coefficients(order, O.HELMHOLTZ, h, K.imag)
+    return re + 1j * (im - base)
+
+
+def robin_row(h, K_l, alpha, beta, side):
+    """3 x 4 block (nu = l-1, l, l+1; a, b, c, d) of a Robin face's row (side -1: lo, +1: hi)."""
+    hx, hy, hz = h
+    Rzx, Rzy = hz * hz / (hx * hx), hz * hz / (hy * hy)
+    R = np.zeros((3, 4), dtype=np.complex128)
+    R[O.MID, O.B_] = Rzx
+    R[O.MID, O.C_] = Rzy
+    # d_zz u with the outside plane replaced by the face condition
+    R[O.MID, O.D_] = -2.0 * (Rzx + Rzy + 1.0) + hz * hz * K_l - side * 2.0 * hz * beta / alpha
+    R[O.UPP if side < 0 else O.LOW, O.D_] = 2.0
+    return R
+
+
+def row_table(order, h, K, zf):
+    """Coefficient blocks of the unknown rows l0..l1: array (Nu, 3, 4) complex."""
+    K = np.asarray(K, dtype=np.complex128)
+    Nz = K.shape[0] - 2
+    Ci = complex_coefficients(order, h, K)
+    rows = []
+    if zf.lo == ROBIN:
+        rows.append(robin_row(h, K[0], zf.alpha[0], zf.beta[0], -1))
+    rows.extend(Ci)
+    if zf.hi == ROBIN:
+        rows.append(robin_row(h, K[Nz + 1], zf.alpha[1], zf.beta[1], +1))
+    return np.array(rows)
+
+
+def _face(g, Ny, Nx):
+    return np.zeros((Ny, Nx), dtype=np.complex128) if g is None else np.asarray(g, np.complex128)
+
+
+def _plane_part(block, P):
+    """One plane's part of a row: block (4,) applied to a padded plane P [Ny+2][Nx+2]."""
+    corners = P[:-2, :-2] + P[:-2, 2:] + P[2:, :-2] + P[2:, 2:]
+    xn = P[1:-1, :-2] + P[1:-1, 2:]
+    yn = P[:-2, 1:-1] + P[2:, 1:-1]
+    return (block[O.A_] * corners + block[O.B_] * xn + block[O.C_] * yn
+            + block[O.D_] * P[1:-1, 1:-1])
+
+
+def _pad2(g):
+    Ny, Nx = g.shape
+    P = np.zeros((Ny + 2, Nx + 2), dtype=np.complex128)
+    P[1:-1, 1:-1] = g
+    return P
+
+
+def rhs(order, h, K, zf, f_nodes, g_lo=None, g_hi=None):
+    """Right-hand side of the unknown rows: array (Nu, Ny, Nx) complex."""
+    hz = h[2]
+    f = np.asarray(f_nodes, dtype=np.complex128)
+    Nz, Ny, Nx = f.shape[0] - 2, f.shape[1] - 2, f.shape[2] - 2
+    glo, ghi = _face(g_lo, Ny, Nx), _face(g_hi, Ny, Nx)
+    Fi = (O.rhs_operator(order, O.HELMHOLTZ, h, f.real)
+          + 1j * O.rhs_operator(order, O.HELMHOLTZ, h, f.imag))
+    Ci = complex_coefficients(order, h, K)
+    # Dirichlet faces: their known plane leaves rows 1 / Nz through the stencil
+    if zf.lo == DIRICHLET:
+        Fi[0] -= _plane_part(Ci[0, O.LOW], _pad2(glo))
+    if zf.hi == DIRICHLET:
+        Fi[-1] -= _plane_part(Ci[-1, O.UPP], _pad2(ghi))
+    rows = []
+    if zf.lo == ROBIN:
+        # u_-1 = u_1 - 2 h (g - beta u_0) / alpha: the data part enters the row with weight 1
+        rows.append(hz * hz * f[0, 1:-1, 1:-1] + 2.0 * hz * glo / zf.alpha[0])
+    rows.extend(Fi)
+    if zf.hi == ROBIN:
+        rows.append(hz * hz * f[Nz + 1, 1:-1, 1:-1] - 2.0 * hz * ghi / zf.alpha[1])
+    return np.array(rows)
+
+
+def eigenvalues(R, Nx, Ny):
+    """lambda_nu(p, q) of every unknown row: complex array (3, Nu, Ny, Nx)."""
+    cx = O.mode_cosines(Nx)[None, None, :]
+    cy = O.mode_cosines(Ny)[None, :, None]
+    lam = np.empty((3, R.shape[0], Ny, Nx), dtype=np.complex128)
+    for nu in range(3):
+        cf = R[:, nu, :]
+        lam[nu] = (4.0 * cf[:, O.A_, None, None] * cx * cy + 2.0 * cf[:, O.B_, None, None] * cx
+                   + 2.0 * cf[:, O.C_, None, None] * cy + cf[:, O.D_, None, None])
+    return lam
+
+
+def solve_rows(R, F):
+    """U (Nu, Ny, Nx) = A^-1 F by Section 3.6: 2-D DST, complex tridiagonals in z, inverse."""
+    Nu, Ny, Nx = F.shape
+    Sx, Sy = O.sine_matrix(Nx), O.sine_matrix(Ny)
+    Fhat = O.dst2_forward(F, Sx, Sy)
+    lam = eigenvalues(R, Nx, Ny)
+    W, ratio = O.thomas(lam[O.LOW], lam[O.MID], lam[O.UPP], Fhat)
+    return O.dst2_inverse(W, Sx, Sy), ratio
+
+
+def solve(order, h, K, zf, f_nodes, g_lo=None, g_hi=None):
+    """Solution on every plane l = 0..Nz+1 (interior x, y): complex (Nz+2, Ny, Nx)."""
+    f = np.asarray(f_nodes, dtype=np.complex128)
+    Nz, Ny, Nx = f.shape[0] - 2, f.shape[1] - 2, f.shape[2] - 2
+    R = row_table(order, h, K, zf)
+    F = rhs(order, h, K, zf, f, g_lo, g_hi)
+    Uu, ratio = solve_rows(R, F)
+    l0, l1 = zf.unknown_planes(Nz)
+    U = np.zeros((Nz + 2, Ny, Nx), dtype=np.complex128)
+    U[l0:l1 + 1] = Uu
+    if zf.lo == DIRICHLET:
+        U[0] = _face(g_lo, Ny, Nx)
+    if zf.hi == DIRICHLET:
+        U[Nz + 1] = _face(g_hi, Ny, Nx)
+    return U, {"min_pivot_ratio": ratio}
+
+
+# --------------------------------------------------------------------------
+# direct definitions (for the pins): the operator evaluated from the scheme
+# itself, the face condition imposed through an explicit ghost plane
+
+
+def apply_operator(order, h, K, zf, U_all, g_lo=None, g_hi=None):
+    """Rows l0..l1 of (A U - data terms): U_all on planes 0..Nz+1 (interior x, y).
+
+    Interior rows: the 27-point stencil with the complex table.  Robin rows: the
+    7-point second-order operator h_z^2 (dxx + dyy + dzz + K) u evaluated with an
+    explicit ghost plane built from the face condition (with its data g), so that
+    solving A U = F means operator(U) = rhs without the data terms."""
+    hx, hy, hz = h
+    K = np.asarray(K, dtype=np.complex128)
+    U_all = np.asarray(U_all, dtype=np.complex128)
+    Nz, Ny, Nx = U_all.shape[0] - 2, U_all.shape[1], U_all.shape[2]
+    P = np.zeros((Nz + 2, Ny + 2, Nx + 2), dtype=np.complex128)
+    P[:, 1:-1, 1:-1] = U_all
+    Ci = complex_coefficients(order, h, K)
+    out = []
+    glo, ghi = _face(g_lo, Ny, Nx), _face(g_hi, Ny, Nx)
+
+    def seven_point(l, ghost_below, ghost_above):
+        c = P[l, 1:-1, 1:-1]
+        dxx = (P[l, 1:-1, :-2] - 2 * c + P[l, 1:-1, 2:]) / (hx * hx)
+        dyy = (P[l, :-2, 1:-1] - 2 * c + P[l, 2:, 1:-1]) / (hy * hy)
+        dzz = (ghost_below - 2 * c + ghost_above) / (hz * hz)
+        return hz * hz * (dxx + dyy + dzz + K[l] * c)
+
+    if zf.lo == ROBIN:
+        a, b = zf.alpha[0], zf.beta[0]
+        u1 = P[1, 1:-1, 1:-1]
+        ghost = u1 - 2.0 * hz * (glo - b * P[0, 1:-1, 1:-1]) / a
+        out.append(seven_point(0, ghost, u1))
+    for l in range(1, Nz + 1):
+        row = np.zeros((Ny, Nx), dtype=np.complex128)
+        for nu, dl in ((O.LOW, -1), (O.MID, 0), (O.UPP, 1)):
+            row += _plane_part(Ci[l - 1, nu], P[l + dl])
+        out.append(row)
+    if zf.hi == ROBIN:
+        a, b = zf.alpha[1], zf.beta[1]
+        uN = P[Nz, 1:-1, 1:-1]
+        ghost = uN + 2.0 * hz * (ghi - b * P[Nz + 1, 1:-1, 1:-1]) / a
+        out.append(seven_point(Nz + 1, uN, ghost))
+    return np.array(out)
+
+
+def rhs_direct(order, h, f_nodes):
+    """The scheme's f-side on every plane that can be a row: R_h f on interior rows
+    (real operator on Re f and Im f), h_z^2 f on the two face planes."""
+    hz = h[2]
+    f = np.asarray(f_nodes, dtype=np.complex128)
+    Fi = (O.rhs_operator(order, O.HELMHOLTZ, h, f.real)
+          + 1j * O.rhs_operator(order, O.HELMHOLTZ, h, f.imag))
+    return hz * hz * f[0, 1:-1, 1:-1], Fi, hz * hz * f[-1, 1:-1, 1:-1]
+
+
+def solve_dense(order, h, K, zf, f_nodes, g_lo=None, g_hi=None):
+    """Brute force: the matrix of apply_operator (columns from unit vectors), its data
+    part from the operator at U = 0, and a dense complex LU solve."""
+    f = np.asarray(f_nodes, dtype=np.complex128)
+    Nz, Ny, Nx = f.shape[0] - 2, f.shape[1] - 2, f.shape[2] - 2
+    l0, l1 = zf.unknown_planes(Nz)
+    Nu = l1 - l0 + 1
+    base = np.zeros((Nz + 2, Ny, Nx), dtype=np.complex128)
+    if zf.lo == DIRICHLET:
+        base[0] = _face(g_lo, Ny, Nx)
+    if zf.hi == DIRICHLET:
+        base[Nz + 1] = _face(g_hi, Ny, Nx)
+    data = apply_operator(order, h, K, zf, base, g_lo, g_hi).ravel()
+    n = Nu * Ny * Nx
+    A = np.zeros((n, n), dtype=np.complex128)
+    zero_faces = ZFaces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
+    for k in range(n):
+        e = np.zeros(n, dtype=np.complex128)
+        e[k] = 1.0
+        Ue = np.zeros((Nz + 2, Ny, Nx), dtype=np.complex128)
+        Ue[l0:l1 + 1] = e.reshape(Nu, Ny, Nx)
+        A[:, k] = apply_operator(order, h, K, zero_faces, Ue).ravel()
+    flo, Fi, fhi = rhs_direct(order, h, f)
+    rows = ([flo] if zf.lo == ROBIN else []) + list(Fi) + ([fhi] if zf.hi == ROBIN else [])
+    b = np.array(rows).ravel() - data
+    x = np.linalg.solve(A, b).reshape(Nu, Ny, Nx)
+    U = base.copy()
+    U[l0:l1 + 1] = x
+    return U

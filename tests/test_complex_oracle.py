@@ -1,0 +1,150 @@
+"""Pins of the complex-k / Robin z-face oracle (oracle/hs_complex_oracle.py), CPU only.
+
+What fixes it, independently of its own code paths:
+  (a) the complex coefficient table rests on every coefficient being affine in K
+      (checked on the real table, which tests/test_oracle_pins.py pins to the paper);
+  (b) the separated solve (2-D DST, complex tridiagonals) equals a dense LU solve of
+      the matrix assembled from the scheme itself, with the Robin face imposed by an
+      explicit ghost plane (not the folded row), for every face combination;
+  (c) Dirichlet faces, real K and real data reduce it to the real oracle;
+  (d) alpha -> 0 turns a Robin face into the Dirichlet face u = g / beta;
+  (e) mirroring z maps a Robin face (alpha, beta) on one side to (-alpha, beta) on
+      the other, and the solution mirrors with it;
+  (f) on a manufactured complex solution the error falls at least like h^2 with
+      Robin faces, and like h^4 (4th order) with Dirichlet faces.
+"""
+import numpy as np
+import pytest
+
+from oracle import hs_oracle as O
+from oracle import hs_complex_oracle as CX
+
+D, R = CX.DIRICHLET, CX.ROBIN
+
+
+def _crand(rs, shape, scale=1.0):
+    return scale * (rs.uniform(-1, 1, shape) + 1j * rs.uniform(-1, 1, shape))
+
+
+def _random_case(shape, seed, order):
+    Nx, Ny, Nz = shape
+    rs = np.random.RandomState(seed)
+    h = O.grid_steps(shape, (1.0, 0.9, 1.1))
+    K = (30.0 + 10.0 * rs.uniform(size=Nz + 2)) * (1.0 + 0.3j * rs.uniform(size=Nz + 2))
+    f = _crand(rs, (Nz + 2, Ny + 2, Nx + 2))
+    f[:, 0, :] = f[:, -1, :] = 0.0
+    f[:, :, 0] = f[:, :, -1] = 0.0
+    g_lo, g_hi = _crand(rs, (Ny, Nx)), _crand(rs, (Ny, Nx))
+    return h, K, f, g_lo, g_hi, rs
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_coefficients_affine_in_K(order):
+    rs = np.random.RandomState(order)
+    h = (0.11, 0.13, 0.09)
+    K1, K2 = rs.uniform(-50, 50, 9), rs.uniform(-50, 50, 9)
+    C = lambda K: O.stencil_coefficients(order, O.HELMHOLTZ, h, K)
+    assert np.max(np.abs(C(K1 + K2) - C(K1) - C(K2) + C(np.zeros(9)))) <= 1e-13
+    assert np.array_equal(CX.complex_coefficients(order, h, K1), C(K1).astype(complex))
+    Kc = K1 + 1j * K2
+    t = 0.37
+    assert np.allclose(CX.complex_coefficients(order, h, Kc),
+                       C(K1) + 1j * (C(K2) - C(np.zeros(9))), rtol=0, atol=1e-14)
+    # the imaginary part enters exactly where K does
+    assert np.allclose(CX.complex_coefficients(order, h, K1 + 1j * t * K2).imag,
+                       t * (C(K2) - C(np.zeros(9))), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("faces", [(R, R), (R, D), (D, R), (D, D)])
+def test_separated_solve_equals_dense_solve(order, faces):
+    shape = (5, 4, 6)
+    h, K, f, g_lo, g_hi, rs = _random_case(shape, 7 + order + 2 * faces[0] + faces[1], order)
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    U, info = CX.solve(order, h, K, zf, f, g_lo, g_hi)
+    Ud = CX.solve_dense(order, h, K, zf, f, g_lo, g_hi)
+    assert O.max_rel_diff(U, Ud) <= 1e-11
+    # and it satisfies the scheme: operator(U) reproduces the f-side row by row
+    res = CX.apply_operator(order, h, K, zf, U, g_lo, g_hi)
+    flo, Fi, fhi = CX.rhs_direct(order, h, f)
+    rows = ([flo] if faces[0] == R else []) + list(Fi) + ([fhi] if faces[1] == R else [])
+    want = np.array(rows)
+    assert np.max(np.abs(res - want)) <= 1e-11 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_dirichlet_real_case_is_the_real_oracle(order):
+    Nx, Ny, Nz = 7, 6, 5
+    rs = np.random.RandomState(20 + order)
+    h = O.grid_steps((Nx, Ny, Nz), (1.0, 0.8, 1.2))
+    K = 20.0 + 10.0 * rs.uniform(size=Nz + 2)
+    f = rs.uniform(-1, 1, (Nz + 2, Ny + 2, Nx + 2))
+    f[:, 0, :] = f[:, -1, :] = 0.0
+    f[:, :, 0] = f[:, :, -1] = 0.0
+    g_lo, g_hi = rs.uniform(-1, 1, (Ny, Nx)), rs.uniform(-1, 1, (Ny, Nx))
+    U, _ = CX.solve(order, h, K, CX.ZFaces(), f, g_lo, g_hi)
+    zl = np.zeros((Ny + 2, Nx + 2))
+    zh = np.zeros((Ny + 2, Nx + 2))
+    zl[1:-1, 1:-1], zh[1:-1, 1:-1] = g_lo, g_hi
+    C = O.stencil_coefficients(order, O.HELMHOLTZ, h, K)
+    F = O.assemble_rhs(order, O.HELMHOLTZ, h, f, C, K, None, (None, None, None, None, zl, zh))
+    Ur, _ = O.solve_assembled(C, F)
+    assert np.max(np.abs(U.imag)) == 0.0
+    assert O.max_rel_diff(U[1:-1].real, Ur) <= 1e-13
+    assert np.array_equal(U[0], g_lo) and np.array_equal(U[-1], g_hi)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_robin_face_tends_to_dirichlet_as_alpha_vanishes(order):
+    shape = (6, 5, 7)
+    h, K, f, g_lo, g_hi, rs = _random_case(shape, 31, order)
+    beta = 2.0 + 0.5j
+    Ud, _ = CX.solve(order, h, K, CX.ZFaces(D, 1, 0, D, 1, 0), f, g_lo / beta, g_hi / beta)
+    prev = None
+    for a in (1e-3, 1e-5, 1e-7):
+        Ur, _ = CX.solve(order, h, K, CX.ZFaces(R, a, beta, R, a * (1 - 1j), beta), f, g_lo, g_hi)
+        d = O.max_rel_diff(Ur, Ud)
+        if prev is not None:
+            assert d <= 0.02 * prev + 1e-12   # O(alpha)
+        prev = d
+    assert prev <= 1e-5
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_z_mirror_swaps_the_faces(order):
+    shape = (5, 6, 7)
+    h, K, f, g_lo, g_hi, rs = _random_case(shape, 41, order)
+    a_lo, b_lo, a_hi, b_hi = 1.0 - 0.3j, 0.5 + 1.0j, 0.8 + 0.1j, -1.0 + 0.4j
+    U, _ = CX.solve(order, h, K, CX.ZFaces(R, a_lo, b_lo, R, a_hi, b_hi), f, g_lo, g_hi)
+    # z -> Lz - z: d/dz changes sign, the faces swap
+    Um, _ = CX.solve(order, h, K[::-1], CX.ZFaces(R, -a_hi, b_hi, R, -a_lo, b_lo),
+                     f[::-1], g_hi, g_lo)
+    assert O.max_rel_diff(Um[::-1], U) <= 1e-12
+
+
+def _manufactured(N, order, zf_kind, kappa=2.5, c=(40.0, 8.0)):
+    h = (1.0 / (N + 1),) * 3
+    x = np.arange(N + 2) * h[0]
+    z = x.copy()
+    K = (c[0] + 1j * c[1]) * (1.0 + 0.5 * z)
+    sxy = np.sin(np.pi * x)[None, None, :] * np.sin(2 * np.pi * x)[None, :, None]
+    ez = np.exp(1j * kappa * z)[:, None, None]
+    u = sxy * ez                                      # u = sin(pi x) sin(2 pi y) e^{i kappa z}
+    f = (-5.0 * np.pi ** 2 - kappa ** 2 + K[:, None, None]) * u
+    alpha, beta = 1.0 + 0.5j, 3.0 - 1.0j
+    if zf_kind == R:
+        zf = CX.ZFaces(R, alpha, beta, R, alpha, beta)
+        gfun = (1j * kappa * alpha + beta) * u        # alpha u_z + beta u
+    else:
+        zf = CX.ZFaces()
+        gfun = u
+    g_lo, g_hi = gfun[0, 1:-1, 1:-1], gfun[-1, 1:-1, 1:-1]
+    U, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi)
+    return np.max(np.abs(U - u[:, 1:-1, 1:-1]))
+
+
+@pytest.mark.parametrize("order,kind,lo_ratio", [(2, R, 3.5), (4, R, 3.5), (2, D, 3.5), (4, D, 12.0)])
+def test_manufactured_complex_solution_converges(order, kind, lo_ratio):
+    e = [_manufactured(N, order, kind) for N in (7, 15, 31)]
+    assert e[2] < e[1] < e[0]
+    assert e[1] / e[2] >= lo_ratio, e
