@@ -498,6 +498,62 @@ const char *hs_status_str(hs_status s);
 /* hs_last_error -- text of the last error seen on this plan (never NULL). */
 const char *hs_last_error(hs_plan_t plan);
 
+/* ---------------------------------------------------------------------------
+ * Complex k(z) and Robin z-faces (FP64; Helmholtz, orders 2 and 4).
+ *
+ * The general problem of Section 1 (eqs. (problem), (bc)): K = k^2 complex and
+ * depending on z only, u = 0 on the four side faces, and on each z-face either
+ * u = g (Dirichlet) or alpha u_z + beta u = g (Robin) with complex alpha, beta
+ * and complex face data g(x, y).  Interior rows l = 1..Nz are the compact rows
+ * of Sections 3.2 (order 2) and 3.3 (order 4) with complex K.  The paper gives
+ * no compact closure of a Robin face: a Robin face's plane (l = 0 or Nz + 1)
+ * is unknown and its row is the second-order 7-point scheme
+ * h_z^2 (dxx + dyy + dzz + K) u = h_z^2 f with the plane outside eliminated by
+ * the central difference of the face condition, alpha (u_+1 - u_-1) / (2 h_z) +
+ * beta u_0 = g.  The side faces stay Dirichlet, so Section 3.6 applies: the
+ * real DSTs act on Re and Im, and each sine mode (p, q) is one complex
+ * tridiagonal system in z, solved without pivoting.
+ *
+ * Complex arrays are planar: all real parts, then all imaginary parts.
+ *   f:  [2][Nz+2][Ny+2][Nx+2]  on the node grid (device memory);
+ *   g_lo, g_hi: [2][Ny][Nx]    on the interior nodes of the z-face (device
+ *                              memory; NULL = 0); the side faces are 0;
+ *   u:  [2][Nz+2][Ny][Nx]      every plane (device memory): Dirichlet planes
+ *                              receive g, the others the solution.
+ * Scalars alpha, beta and the coefficient K are host (re, im) pairs.
+ */
+typedef struct hs_zplan_s *hs_zplan_t;
+enum { HS_ZFACE_DIRICHLET = 0, HS_ZFACE_ROBIN = 1 };
+
+/* hs_zplan -- plan for an Nx x Ny x Nz interior grid on [0,Lx]x[0,Ly]x[0,Lz]
+ * (h_a = L_a / (N_a + 1)), order 2 or 4.  Faces start Dirichlet.  Errors:
+ * HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED (transform length), HS_ERR_OOM,
+ * HS_ERR_CUDA. */
+hs_status hs_zplan(hs_zplan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, double Lz,
+                   int order);
+
+/* hs_zplan_set_coeff -- K = k^2 at the nodes l = 0..Nz+1: host array of Nz + 2
+ * (re, im) pairs, copied.  Errors: HS_ERR_INVALID_ARG (NULL, non-finite). */
+hs_status hs_zplan_set_coeff(hs_zplan_t plan, const double *K);
+
+/* hs_zplan_set_faces -- kind (HS_ZFACE_DIRICHLET / HS_ZFACE_ROBIN) of the z-lo
+ * and z-hi faces; alpha, beta: host (re, im) pairs, read for Robin faces only
+ * (alpha != 0 there).  Errors: HS_ERR_INVALID_ARG, HS_ERR_OOM. */
+hs_status hs_zplan_set_faces(hs_zplan_t plan, int lo_kind, const double *alpha_lo,
+                             const double *beta_lo, int hi_kind, const double *alpha_hi,
+                             const double *beta_hi);
+
+/* hs_zsolve -- one solve on `stream` (asynchronous; the caller keeps f, g and
+ * u valid until the stream has passed it).  Errors: HS_ERR_INVALID_ARG (NULL
+ * f or u, host pointers), HS_ERR_NO_COEFF, HS_ERR_CUDA. */
+hs_status hs_zsolve(hs_zplan_t plan, const double *f, const double *g_lo, const double *g_hi,
+                    double *u, void *stream);
+
+/* Device workspace of the plan in bytes, its last error text, and its release. */
+size_t hs_zplan_workspace_bytes(hs_zplan_t plan);
+const char *hs_zplan_last_error(hs_zplan_t plan);
+void hs_zplan_destroy(hs_zplan_t plan);
+
 #ifdef __cplusplus
 }
 #endif

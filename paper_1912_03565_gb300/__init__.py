@@ -39,6 +39,7 @@ HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC, HS_DST_TWOPASS, HS_DST_FUSED_WIDE =
 HS_AXIS_X, HS_AXIS_Y = 0, 1
 HS_FACTOR_AUTO, HS_FACTOR_F32, HS_FACTOR_F64 = 0, 1, 2
 HS_HOST_F_MAPPED, HS_HOST_U_MAPPED, HS_HOST_F_EARLY, HS_HOST_U_LATE = 1, 2, 4, 8
+HS_ZFACE_DIRICHLET, HS_ZFACE_ROBIN = 0, 1
 HS_THOMAS_PIPE16_256, HS_THOMAS_PIPE8_128, HS_THOMAS_PLAIN16_256, HS_THOMAS_PIPE16_128 = 0, 1, 2, 3
 HS_INFO_MAX_ITERS = 8
 HS_INFO_STAGES = 8
@@ -56,7 +57,9 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_set_thomas_variant", "hs_get_thomas_variant", "hs_set_host_io", "hs_host_io_wait",
             "hs_set_factor_precision",
             "hs_precond_create", "hs_precond_apply", "hs_precond_solve", "hs_precond_destroy",
-            "hs_batch_workspace_bytes", "hs_batch_destroy")
+            "hs_batch_workspace_bytes", "hs_batch_destroy",
+            "hs_zplan", "hs_zplan_set_coeff", "hs_zplan_set_faces", "hs_zsolve",
+            "hs_zplan_workspace_bytes", "hs_zplan_last_error", "hs_zplan_destroy")
 HS_STATIC_MAX_NZ = 8192
 
 
@@ -156,6 +159,21 @@ def load(path: Optional[str] = None):
     lib.hs_set_host_io.restype = ci
     lib.hs_host_io_wait.argtypes = [vp, vp]
     lib.hs_host_io_wait.restype = ci
+    dp = ctypes.POINTER(cd)
+    lib.hs_zplan.argtypes = [ctypes.POINTER(vp), ci, ci, ci, cd, cd, cd, ci]
+    lib.hs_zplan.restype = ci
+    lib.hs_zplan_set_coeff.argtypes = [vp, dp]
+    lib.hs_zplan_set_coeff.restype = ci
+    lib.hs_zplan_set_faces.argtypes = [vp, ci, dp, dp, ci, dp, dp]
+    lib.hs_zplan_set_faces.restype = ci
+    lib.hs_zsolve.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.hs_zsolve.restype = ci
+    lib.hs_zplan_workspace_bytes.argtypes = [vp]
+    lib.hs_zplan_workspace_bytes.restype = ctypes.c_size_t
+    lib.hs_zplan_last_error.argtypes = [vp]
+    lib.hs_zplan_last_error.restype = ctypes.c_char_p
+    lib.hs_zplan_destroy.argtypes = [vp]
+    lib.hs_zplan_destroy.restype = None
     lib.hs_set_thomas_variant.argtypes = [vp, ci]
     lib.hs_set_thomas_variant.restype = ci
     lib.hs_get_thomas_variant.argtypes = [vp, ctypes.POINTER(ci)]
@@ -526,6 +544,64 @@ class Solver:
     def close(self):
         if getattr(self, "plan", None):
             hs_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------- complex k(z), Robin z-faces
+
+
+def _pair(z):
+    z = complex(z)
+    return (ctypes.c_double * 2)(z.real, z.imag)
+
+
+class ZSolver:
+    """Complex k(z) and Robin / Dirichlet z-faces on the FP64 path (orders 2, 4).
+
+    Arrays are planar complex float64 device tensors: f [2][Nz+2][Ny+2][Nx+2],
+    g_lo / g_hi [2][Ny][Nx] (None = 0), u [2][Nz+2][Ny][Nx]."""
+
+    def __init__(self, Nx, Ny, Nz, Lx, Ly, Lz, order):
+        out = ctypes.c_void_p()
+        _check(load().hs_zplan(ctypes.byref(out), Nx, Ny, Nz, Lx, Ly, Lz, order), "hs_zplan")
+        self.plan = out
+        self.shape = (Nx, Ny, Nz)
+
+    def _err(self, st, where):
+        if st < 0:
+            raise HsError(st, where, load().hs_zplan_last_error(self.plan).decode())
+        return st
+
+    def set_coeff(self, K):
+        import numpy as np
+        K = np.asarray(K, dtype=np.complex128)
+        buf = np.ascontiguousarray(np.stack([K.real, K.imag], axis=-1).ravel())
+        arr = (ctypes.c_double * buf.size)(*buf.tolist())
+        return self._err(load().hs_zplan_set_coeff(self.plan, arr), "hs_zplan_set_coeff")
+
+    def set_faces(self, lo_kind, alpha_lo=1.0, beta_lo=0.0, hi_kind=HS_ZFACE_DIRICHLET,
+                  alpha_hi=1.0, beta_hi=0.0):
+        return self._err(load().hs_zplan_set_faces(self.plan, int(lo_kind), _pair(alpha_lo),
+                                                   _pair(beta_lo), int(hi_kind), _pair(alpha_hi),
+                                                   _pair(beta_hi)), "hs_zplan_set_faces")
+
+    def solve(self, f, u, g_lo=None, g_hi=None, stream=None):
+        self._keep = (f, u, g_lo, g_hi)
+        return self._err(load().hs_zsolve(self.plan, _ptr(f), _ptr(g_lo), _ptr(g_hi), _ptr(u),
+                                          _stream_ptr(stream)), "hs_zsolve")
+
+    def workspace_bytes(self):
+        return load().hs_zplan_workspace_bytes(self.plan)
+
+    def close(self):
+        if getattr(self, "plan", None):
+            load().hs_zplan_destroy(self.plan)
             self.plan = None
 
     def __del__(self):

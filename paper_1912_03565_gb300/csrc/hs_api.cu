@@ -609,6 +609,11 @@ extern "C" {
 
 hs_status hs_plan(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, double Lz,
                   int order, int equation, int bc, int precision, int max_rhs) {
+    return hs_plan_ex(out, Nx, Ny, Nz, Lx, Ly, Lz, order, equation, bc, precision, max_rhs, 0);
+}
+
+hs_status hs_plan_ex(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, double Lz,
+                     int order, int equation, int bc, int precision, int max_rhs, int lean) {
     if (!out) return HS_ERR_INVALID_ARG;
     *out = nullptr;
     if (Nx < 1 || Ny < 1 || Nz < 1 || !(Lx > 0) || !(Ly > 0) || !(Lz > 0) || max_rhs < 1)
@@ -659,7 +664,7 @@ hs_status hs_plan(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, 
         (st = dev_alloc(P, &P->d_c0, (size_t)Nz + 2)) ||
         (st = dev_alloc(P, &P->d_c1, (size_t)Nz + 2)) ||
         (st = dev_alloc(P, &P->d_cx, (size_t)Nx)) || (st = dev_alloc(P, &P->d_cy, (size_t)Ny)) ||
-        (precision == HS_FP64 && (st = dev_alloc(P, &P->d_fac, 3 * nint))) ||
+        (precision == HS_FP64 && !lean && (st = dev_alloc(P, &P->d_fac, 3 * nint))) ||
         (st = dev_alloc(P, &P->d_red, (size_t)64)) || (st = dev_alloc(P, &P->d_skip, (size_t)1)) ||
         (precision == HS_FP64 && (st = dev_alloc(P, &P->d_w64, nint))) ||
         (precision == HS_FP64 && (st = dev_alloc(P, &P->d_dscr, nint))) ||

@@ -152,6 +152,12 @@ hs_status hs_launch_dst_fused_x(const hs_plan_s *P, int tin, const void *in, int
                                 int mode, double scale, cudaStream_t s, double *aux, int wide);
 hs_status hs_launch_dst_fused_y(const hs_plan_s *P, int tin, const void *in, int tout, void *out,
                                 int mode, double scale, cudaStream_t s, double *aux, int wide);
+// hs_plan with lean = 1: an FP64 plan without the cached z-factorization, used
+// as the transform engine and work arrays of other solvers (d_w64, d_dscr).
+extern "C" hs_status hs_plan_ex(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly,
+                                double Lz, int order, int equation, int bc, int precision,
+                                int max_rhs, int lean);
+
 // Lines per CTA of the fused tile of length M (0: not built for that length).
 int hs_dst_fused_lines_x(int M, int wide);
 int hs_dst_fused_lines_y(int M, int wide);

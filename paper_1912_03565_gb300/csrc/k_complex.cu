@@ -1,0 +1,439 @@
+// Complex k(z) and Robin z-faces on the FP64 path (orders 2 and 4, Helmholtz).
+//
+// Section 1's general problem: K = k^2 complex and depending on z only, u = 0
+// on the side faces, each z-face Dirichlet (u = g) or Robin (alpha u_z + beta u
+// = g, complex alpha, beta).  Interior rows l = 1..Nz are the compact rows of
+// Sections 3.2 / 3.3 with complex K; every coefficient is affine in K, so the
+// complex table is the real table at Re K plus i times its K-part at Im K.  A
+// Robin face's plane is unknown and its row is the second-order 7-point scheme
+// with the outside plane eliminated by the central difference of the face
+// condition (the paper leaves the compact closure to a cited work):
+//   lo face (l = 0):      u_-1    = u_1  - 2 h_z (g - beta u_0) / alpha,
+//   hi face (l = Nz + 1): u_Nz+2  = u_Nz + 2 h_z (g - beta u_Nz+1) / alpha,
+// which gives the row  Rzx dxx + Rzy dyy + 2 u_(inner) + (-2 - 2Rzx - 2Rzy +
+// h_z^2 K -+ 2 h_z beta / alpha) u_face = h_z^2 f +- 2 h_z g / alpha.
+//
+// The solve (Section 3.6 with complex rows): the right-hand side kernel writes
+// the unknown rows l0..l1 as planar complex data [2][Nu][Ny][Nx]; the real FP64
+// sine transforms of an internal plan with 2 Nu planes act on Re and Im; one
+// thread per sine mode (p, q) solves the complex tridiagonal system in z by the
+// textbook recurrence (no pivoting); the inverse transforms follow.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "hs_internal.cuh"
+
+struct hs_zplan_s {
+    int Nx, Ny, Nz, order;
+    double Lx, Ly, Lz, hx, hy, hz;
+    int kind[2];               // HS_ZFACE_* of the lo and hi faces
+    double2 alpha[2], beta[2];
+    std::vector<double2> K;    // Nz + 2 nodes
+    int have_coeff;
+    int Nu, l0;                // unknown planes l0 .. l0 + Nu - 1
+    hs_plan_s *T;              // FP64 transform plan over 2 Nu planes (work: d_w64, d_dscr)
+    double2 *d_rows;           // [Nu][3][4] complex coefficients of the unknown rows
+    int rows_ok;
+    size_t bytes;
+    char last_error[256];
+};
+
+namespace {
+
+void zerr(hs_zplan_s *Z, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(Z->last_error, sizeof(Z->last_error), fmt, ap);
+    va_end(ap);
+}
+
+#define ZCK(Z, call)                                                                     \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            zerr(Z, "%s failed: %s", #call, cudaGetErrorString(e_));                     \
+            return (e_ == cudaErrorMemoryAllocation) ? HS_ERR_OOM : HS_ERR_CUDA;         \
+        }                                                                                \
+    } while (0)
+
+enum { ZA = 0, ZB = 1, ZC = 2, ZD = 3 };          // corner, x-, y-neighbour, centre
+enum { ZLOW = 0, ZMID = 1, ZUPP = 2 };            // planes l - 1, l, l + 1
+
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 cadd(double2 a, double2 b) {
+    return make_double2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ inline double2 csub(double2 a, double2 b) {
+    return make_double2(a.x - b.x, a.y - b.y);
+}
+__host__ __device__ inline double2 cscale(double s, double2 a) {
+    return make_double2(s * a.x, s * a.y);
+}
+__host__ inline double2 cdiv_host(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// Real coefficients of an interior row (Sections 3.2, 3.3) for a real K at the
+// three nodes (Km, K, Kp) = K(z_{l-1}), K(z_l), K(z_{l+1}); blk[nu][m].
+void real_row(int order, double Rzx, double Rzy, double hz2, double Km, double K, double Kp,
+              double blk[3][4]) {
+    memset(blk, 0, sizeof(double) * 12);
+    if (order == 2) {
+        blk[ZMID][ZB] = Rzx;
+        blk[ZMID][ZC] = Rzy;
+        blk[ZLOW][ZD] = 1.0;
+        blk[ZUPP][ZD] = 1.0;
+        blk[ZMID][ZD] = -2.0 * (Rzx + Rzy + 1.0) + hz2 * K;
+    } else {
+        blk[ZLOW][ZB] = blk[ZUPP][ZB] = (1.0 + Rzx) / 12.0;
+        blk[ZLOW][ZC] = blk[ZUPP][ZC] = (1.0 + Rzy) / 12.0;
+        blk[ZLOW][ZD] = 2.0 / 3.0 - (Rzx + Rzy) / 6.0 + hz2 * Km / 12.0;
+        blk[ZUPP][ZD] = 2.0 / 3.0 - (Rzx + Rzy) / 6.0 + hz2 * Kp / 12.0;
+        blk[ZMID][ZA] = (Rzx + Rzy) / 12.0;
+        blk[ZMID][ZB] = (4.0 * Rzx - Rzy - 1.0 + hz2 * K / 2.0) / 6.0;
+        blk[ZMID][ZC] = (4.0 * Rzy - Rzx - 1.0 + hz2 * K / 2.0) / 6.0;
+        blk[ZMID][ZD] = -4.0 * (1.0 + Rzx + Rzy) / 3.0 + hz2 * K / 2.0;
+    }
+}
+
+// Builds the complex rows of the unknown planes and uploads them.
+hs_status build_rows(hs_zplan_s *Z) {
+    const double Rzx = Z->hz * Z->hz / (Z->hx * Z->hx), Rzy = Z->hz * Z->hz / (Z->hy * Z->hy);
+    const double hz2 = Z->hz * Z->hz;
+    std::vector<double2> rows((size_t)Z->Nu * 12);
+    for (int r = 0; r < Z->Nu; ++r) {
+        const int l = Z->l0 + r;
+        double2 *blk = &rows[(size_t)r * 12];
+        if (l == 0 || l == Z->Nz + 1) {   // a Robin face's row
+            const int side = l == 0 ? -1 : 1;
+            const double2 a = Z->alpha[l == 0 ? 0 : 1], b = Z->beta[l == 0 ? 0 : 1];
+            for (int k = 0; k < 12; ++k) blk[k] = make_double2(0.0, 0.0);
+            const double2 ba = cdiv_host(b, a);
+            blk[ZMID * 4 + ZB] = make_double2(Rzx, 0.0);
+            blk[ZMID * 4 + ZC] = make_double2(Rzy, 0.0);
+            blk[ZMID * 4 + ZD] = make_double2(-2.0 * (Rzx + Rzy + 1.0) + hz2 * Z->K[l].x -
+                                                  side * 2.0 * Z->hz * ba.x,
+                                              hz2 * Z->K[l].y - side * 2.0 * Z->hz * ba.y);
+            blk[(side < 0 ? ZUPP : ZLOW) * 4 + ZD] = make_double2(2.0, 0.0);
+            continue;
+        }
+        double re[3][4], im[3][4], z0[3][4];
+        const double2 Km = Z->K[l - 1], K = Z->K[l], Kp = Z->K[l + 1];
+        real_row(Z->order, Rzx, Rzy, hz2, Km.x, K.x, Kp.x, re);
+        real_row(Z->order, Rzx, Rzy, hz2, Km.y, K.y, Kp.y, im);
+        real_row(Z->order, Rzx, Rzy, hz2, 0.0, 0.0, 0.0, z0);
+        for (int nu = 0; nu < 3; ++nu)
+            for (int m = 0; m < 4; ++m)
+                blk[nu * 4 + m] = make_double2(re[nu][m], im[nu][m] - z0[nu][m]);
+    }
+    ZCK(Z, cudaMemcpy(Z->d_rows, rows.data(), rows.size() * sizeof(double2),
+                      cudaMemcpyHostToDevice));
+    Z->rows_ok = 1;
+    return HS_OK;
+}
+
+// (Re)creates the transform plan and row table for the current faces.
+hs_status layout(hs_zplan_s *Z) {
+    const int l0 = Z->kind[0] == HS_ZFACE_ROBIN ? 0 : 1;
+    const int l1 = Z->kind[1] == HS_ZFACE_ROBIN ? Z->Nz + 1 : Z->Nz;
+    const int Nu = l1 - l0 + 1;
+    if (Z->T && Nu == Z->Nu) {
+        Z->l0 = l0;
+        return HS_OK;
+    }
+    if (Z->T) hs_destroy(Z->T);
+    Z->T = nullptr;
+    if (Z->d_rows) cudaFree(Z->d_rows);
+    Z->d_rows = nullptr;
+    Z->Nu = Nu;
+    Z->l0 = l0;
+    Z->rows_ok = 0;
+    hs_plan_t T = nullptr;
+    const hs_status st = hs_plan_ex(&T, Z->Nx, Z->Ny, 2 * Nu, Z->Lx, Z->Ly, 1.0, 2,
+                                    HS_HELMHOLTZ, HS_BC_DIRICHLET, HS_FP64, 1, 1);
+    if (st != HS_OK) {
+        zerr(Z, "transform plan: status %d", st);
+        return st;
+    }
+    Z->T = T;
+    ZCK(Z, cudaMalloc(&Z->d_rows, (size_t)Nu * 12 * sizeof(double2)));
+    return HS_OK;
+}
+
+bool device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct ZRhsArgs {
+    int Nx, Ny, Nz, Nu, l0, order;
+    int kind_lo, kind_hi;
+    double hz;
+    double2 ga_lo, ga_hi;   // 2 h_z / alpha of each face (Robin)
+    const double *f;        // [2][Nz+2][Ny+2][Nx+2]
+    const double *g_lo, *g_hi;   // [2][Ny][Nx] or NULL
+    const double2 *rows;    // [Nu][3][4]
+    double *W;              // [2][Nu][Ny][Nx]
+};
+
+__device__ inline double2 face_val(const double *g, int Ny, int Nx, int j, int i) {
+    if (!g || j < 0 || j >= Ny || i < 0 || i >= Nx) return make_double2(0.0, 0.0);
+    const size_t k = (size_t)j * Nx + i, n = (size_t)Ny * Nx;
+    return make_double2(g[k], g[n + k]);
+}
+
+// One thread per unknown (row r, j, i): the compact right-hand side of the row,
+// minus the known Dirichlet plane next to it, or the Robin row's h_z^2 f plus
+// its face-data term.
+__global__ void zrhs_kernel(ZRhsArgs a) {
+    const size_t plane = (size_t)a.Ny * a.Nx, n = plane * a.Nu;
+    const size_t sy = (size_t)(a.Nx + 2), sz = sy * (a.Ny + 2), nodes = sz * (a.Nz + 2);
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t / plane);
+        const int rem = (int)(t - (size_t)r * plane);
+        const int j = rem / a.Nx, i = rem - j * a.Nx;
+        const int l = a.l0 + r;
+        const size_t c = (size_t)l * sz + (size_t)(j + 1) * sy + (i + 1);
+        const double hz2 = a.hz * a.hz;
+        double2 F;
+        for (int comp = 0; comp < 2; ++comp) {
+            const double *f = a.f + comp * nodes;
+            double v = f[c];
+            if (a.order == 4 && l >= 1 && l <= a.Nz) {
+                const double D = (f[c - 1] + f[c + 1] + f[c - sy] + f[c + sy] + f[c - sz] +
+                                  f[c + sz]) - 6.0 * f[c];
+                v += D / 12.0;
+            }
+            if (comp == 0) F.x = hz2 * v; else F.y = hz2 * v;
+        }
+        if (l == 0) {
+            F = cadd(F, cmul(a.ga_lo, face_val(a.g_lo, a.Ny, a.Nx, j, i)));
+        } else if (l == a.Nz + 1) {
+            F = csub(F, cmul(a.ga_hi, face_val(a.g_hi, a.Ny, a.Nx, j, i)));
+        } else {
+            // a Dirichlet face's plane next to this row: its values leave through the stencil
+            const bool lo = l == 1 && a.kind_lo == HS_ZFACE_DIRICHLET && a.g_lo;
+            const bool hi = l == a.Nz && a.kind_hi == HS_ZFACE_DIRICHLET && a.g_hi;
+            for (int side = 0; side < 2; ++side) {
+                if (!(side == 0 ? lo : hi)) continue;
+                const double *g = side == 0 ? a.g_lo : a.g_hi;
+                const double2 *w = a.rows + (size_t)r * 12 + (side == 0 ? ZLOW : ZUPP) * 4;
+                for (int dj = -1; dj <= 1; ++dj)
+                    for (int di = -1; di <= 1; ++di) {
+                        const int m = (di != 0 && dj != 0) ? ZA : (di != 0 ? ZB : (dj != 0 ? ZC : ZD));
+                        F = csub(F, cmul(w[m], face_val(g, a.Ny, a.Nx, j + dj, i + di)));
+                    }
+            }
+        }
+        a.W[t] = F.x;
+        a.W[n + t] = F.y;
+    }
+}
+
+// One thread per sine mode (p, q): the complex tridiagonal system of the
+// unknown rows, lambda_nu = 4 a cp cq + 2 b cp + 2 c cq + d (Section 3.6), by
+// the textbook recurrence; c' kept in the scratch S [2][Nu][Ny][Nx].
+__global__ void zthomas_kernel(double *W, double *S, const double2 *rows, const double *cx,
+                               const double *cy, int Nx, int Ny, int Nu) {
+    const size_t plane = (size_t)Nx * Ny, n = plane * Nu;
+    const size_t col = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (col >= plane) return;
+    const int q = (int)(col / Nx), p = (int)(col - (size_t)q * Nx);
+    const double cp = cx[p], cq = cy[q];
+    const double w4 = 4.0 * cp * cq, wb = 2.0 * cp, wc = 2.0 * cq;
+    auto lam = [&](const double2 *b) {
+        return make_double2(w4 * b[ZA].x + wb * b[ZB].x + wc * b[ZC].x + b[ZD].x,
+                            w4 * b[ZA].y + wb * b[ZB].y + wc * b[ZC].y + b[ZD].y);
+    };
+    double2 cprev = make_double2(0.0, 0.0), dprev = make_double2(0.0, 0.0);
+    for (int r = 0; r < Nu; ++r) {
+        const double2 *blk = rows + (size_t)r * 12;
+        const double2 lo = lam(blk + ZLOW * 4), di = lam(blk + ZMID * 4), up = lam(blk + ZUPP * 4);
+        const double2 piv = r ? csub(di, cmul(lo, cprev)) : di;
+        const double inv = 1.0 / (piv.x * piv.x + piv.y * piv.y);
+        const double2 ip = make_double2(piv.x * inv, -piv.y * inv);   // 1 / piv
+        const size_t k = (size_t)r * plane + col;
+        double2 rhs = make_double2(W[k], W[n + k]);
+        if (r) rhs = csub(rhs, cmul(lo, dprev));
+        const double2 d = cmul(rhs, ip);
+        const double2 c = cmul(up, ip);
+        S[k] = c.x;
+        S[n + k] = c.y;
+        W[k] = d.x;
+        W[n + k] = d.y;
+        cprev = c;
+        dprev = d;
+    }
+    double2 w = dprev;
+    for (int r = Nu - 2; r >= 0; --r) {
+        const size_t k = (size_t)r * plane + col;
+        w = csub(make_double2(W[k], W[n + k]), cmul(make_double2(S[k], S[n + k]), w));
+        W[k] = w.x;
+        W[n + k] = w.y;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+hs_status hs_zplan(hs_zplan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, double Lz,
+                   int order) {
+    if (!out) return HS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (Nx < 1 || Ny < 1 || Nz < 1 || !(Lx > 0) || !(Ly > 0) || !(Lz > 0)) return HS_ERR_INVALID_ARG;
+    if (order != 2 && order != 4) return HS_ERR_INVALID_ARG;
+    if (2.0 * (Nz + 2) * (double)Nx * Ny > 4.0e9) return HS_ERR_UNSUPPORTED;
+    hs_zplan_s *Z = new (std::nothrow) hs_zplan_s();
+    if (!Z) return HS_ERR_OOM;
+    Z->Nx = Nx; Z->Ny = Ny; Z->Nz = Nz; Z->order = order;
+    Z->Lx = Lx; Z->Ly = Ly; Z->Lz = Lz;
+    Z->hx = Lx / (Nx + 1); Z->hy = Ly / (Ny + 1); Z->hz = Lz / (Nz + 1);
+    Z->kind[0] = Z->kind[1] = HS_ZFACE_DIRICHLET;
+    Z->alpha[0] = Z->alpha[1] = make_double2(1.0, 0.0);
+    Z->beta[0] = Z->beta[1] = make_double2(0.0, 0.0);
+    const hs_status st = layout(Z);
+    if (st != HS_OK) {
+        hs_zplan_destroy(Z);
+        return st;
+    }
+    *out = Z;
+    return HS_OK;
+}
+
+hs_status hs_zplan_set_coeff(hs_zplan_t Z, const double *K) {
+    if (!Z || !K) return HS_ERR_INVALID_ARG;
+    std::vector<double2> k(Z->Nz + 2);
+    for (int l = 0; l < Z->Nz + 2; ++l) {
+        if (!isfinite(K[2 * l]) || !isfinite(K[2 * l + 1])) return HS_ERR_INVALID_ARG;
+        k[l] = make_double2(K[2 * l], K[2 * l + 1]);
+    }
+    Z->K = k;
+    Z->have_coeff = 1;
+    return build_rows(Z);
+}
+
+hs_status hs_zplan_set_faces(hs_zplan_t Z, int lo_kind, const double *alpha_lo,
+                             const double *beta_lo, int hi_kind, const double *alpha_hi,
+                             const double *beta_hi) {
+    if (!Z) return HS_ERR_INVALID_ARG;
+    const int kinds[2] = {lo_kind, hi_kind};
+    const double *al[2] = {alpha_lo, alpha_hi}, *be[2] = {beta_lo, beta_hi};
+    double2 na[2], nb[2];
+    for (int s = 0; s < 2; ++s) {
+        if (kinds[s] != HS_ZFACE_DIRICHLET && kinds[s] != HS_ZFACE_ROBIN) return HS_ERR_INVALID_ARG;
+        na[s] = make_double2(1.0, 0.0);
+        nb[s] = make_double2(0.0, 0.0);
+        if (kinds[s] == HS_ZFACE_ROBIN) {
+            if (!al[s] || !be[s]) return HS_ERR_INVALID_ARG;
+            na[s] = make_double2(al[s][0], al[s][1]);
+            nb[s] = make_double2(be[s][0], be[s][1]);
+            if (!isfinite(na[s].x) || !isfinite(na[s].y) || !isfinite(nb[s].x) ||
+                !isfinite(nb[s].y) || (na[s].x == 0.0 && na[s].y == 0.0))
+                return HS_ERR_INVALID_ARG;
+        }
+    }
+    for (int s = 0; s < 2; ++s) {
+        Z->kind[s] = kinds[s];
+        Z->alpha[s] = na[s];
+        Z->beta[s] = nb[s];
+    }
+    const hs_status st = layout(Z);
+    if (st != HS_OK) return st;
+    return Z->have_coeff ? build_rows(Z) : HS_OK;
+}
+
+hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const double *g_hi,
+                    double *u, void *stream) {
+    if (!Z || !f || !u) return HS_ERR_INVALID_ARG;
+    if (!Z->have_coeff || !Z->rows_ok) return HS_ERR_NO_COEFF;
+    if (!device_ptr(f) || !device_ptr(u) || (g_lo && !device_ptr(g_lo)) ||
+        (g_hi && !device_ptr(g_hi)))
+        return HS_ERR_INVALID_ARG;
+    Z->last_error[0] = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    hs_plan_s *T = Z->T;
+    const size_t plane = (size_t)Z->Nx * Z->Ny;
+    const size_t nu = plane * Z->Nu;
+    double *W = T->d_w64;
+    ZRhsArgs a;
+    a.Nx = Z->Nx; a.Ny = Z->Ny; a.Nz = Z->Nz; a.Nu = Z->Nu; a.l0 = Z->l0; a.order = Z->order;
+    a.kind_lo = Z->kind[0]; a.kind_hi = Z->kind[1];
+    a.hz = Z->hz;
+    a.ga_lo = cscale(2.0 * Z->hz, cdiv_host(make_double2(1.0, 0.0), Z->alpha[0]));
+    a.ga_hi = cscale(2.0 * Z->hz, cdiv_host(make_double2(1.0, 0.0), Z->alpha[1]));
+    a.f = f; a.g_lo = g_lo; a.g_hi = g_hi; a.rows = Z->d_rows; a.W = W;
+    const unsigned blocks = (unsigned)((nu + 255) / 256 < 152 * 16 ? (nu + 255) / 256 : 152 * 16);
+    zrhs_kernel<<<blocks, 256, 0, s>>>(a);
+    ZCK(Z, cudaGetLastError());
+    hs_status st;
+    if ((st = hs_launch_dst(T, HS_AXIS_X, HS_T_F64, HS_T_F64, W, HS_T_F64, W, HS_MODE_WRITE, 1.0,
+                            s)) != HS_OK ||
+        (st = hs_launch_dst(T, HS_AXIS_Y, HS_T_F64, HS_T_F64, W, HS_T_F64, W, HS_MODE_WRITE, 1.0,
+                            s)) != HS_OK) {
+        zerr(Z, "forward transform: status %d", st);
+        return st;
+    }
+    zthomas_kernel<<<(unsigned)((plane + 127) / 128), 128, 0, s>>>(W, T->d_dscr, Z->d_rows,
+                                                                 T->d_cx, T->d_cy, Z->Nx,
+                                                                 Z->Ny, Z->Nu);
+    ZCK(Z, cudaGetLastError());
+    if ((st = hs_launch_dst(T, HS_AXIS_Y, HS_T_F64, HS_T_F64, W, HS_T_F64, W, HS_MODE_WRITE,
+                            2.0 / (Z->Ny + 1), s)) != HS_OK ||
+        (st = hs_launch_dst(T, HS_AXIS_X, HS_T_F64, HS_T_F64, W, HS_T_F64, W, HS_MODE_WRITE,
+                            2.0 / (Z->Nx + 1), s)) != HS_OK) {
+        zerr(Z, "inverse transform: status %d", st);
+        return st;
+    }
+    // unknown planes into u; Dirichlet planes receive their face data
+    const size_t uplanes = (size_t)Z->Nz + 2;
+    for (int comp = 0; comp < 2; ++comp) {
+        double *uc = u + comp * uplanes * plane;
+        ZCK(Z, cudaMemcpyAsync(uc + (size_t)Z->l0 * plane, W + comp * nu, nu * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s));
+        for (int side = 0; side < 2; ++side) {
+            if (Z->kind[side] != HS_ZFACE_DIRICHLET) continue;
+            double *dst = uc + (side == 0 ? 0 : (size_t)(Z->Nz + 1) * plane);
+            const double *g = side == 0 ? g_lo : g_hi;
+            if (g)
+                ZCK(Z, cudaMemcpyAsync(dst, g + comp * plane, plane * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s));
+            else
+                ZCK(Z, cudaMemsetAsync(dst, 0, plane * sizeof(double), s));
+        }
+    }
+    return HS_OK;
+}
+
+size_t hs_zplan_workspace_bytes(hs_zplan_t Z) {
+    if (!Z) return 0;
+    return hs_workspace_bytes(Z->T) + (Z->d_rows ? (size_t)Z->Nu * 12 * sizeof(double2) : 0);
+}
+
+const char *hs_zplan_last_error(hs_zplan_t Z) {
+    if (!Z) return "no plan";
+    if (Z->last_error[0]) return Z->last_error;
+    return Z->T ? hs_last_error(Z->T) : "";
+}
+
+void hs_zplan_destroy(hs_zplan_t Z) {
+    if (!Z) return;
+    if (Z->T) hs_destroy(Z->T);
+    if (Z->d_rows) cudaFree(Z->d_rows);
+    delete Z;
+}
+
+}  // extern "C"

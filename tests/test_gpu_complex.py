@@ -1,0 +1,145 @@
+"""Complex k(z) and Robin z-faces on the GPU (hs_zplan / hs_zsolve), against the oracle.
+
+Parity bar: the FP64 path's 1e-12 (max relative error over the whole complex field),
+on ragged sizes (runtime-sized and compiled transform lengths), every face
+combination, orders 2 and 4, absent face data, Nz = 1, and one 255^3 case.
+"""
+import numpy as np
+import pytest
+
+import paper_1912_03565_gb300 as H
+from oracle import hs_oracle as O
+from oracle import hs_complex_oracle as CX
+
+pytestmark = pytest.mark.gpu
+
+D, R = CX.DIRICHLET, CX.ROBIN
+TOL = 1e-12
+
+
+def _torch():
+    return pytest.importorskip("torch")
+
+
+def _case(shape, L, seed, kscale=40.0):
+    Nx, Ny, Nz = shape
+    rs = np.random.RandomState(seed)
+    z = np.arange(Nz + 2) / (Nz + 1)
+    K = kscale * (1.0 + 0.5 * z) * (1.0 + 0.2j * (1.0 + np.sin(3.0 * z)))
+    f = rs.uniform(-1, 1, (Nz + 2, Ny + 2, Nx + 2)) + 1j * rs.uniform(-1, 1, (Nz + 2, Ny + 2, Nx + 2))
+    f[:, 0, :] = f[:, -1, :] = 0.0
+    f[:, :, 0] = f[:, :, -1] = 0.0
+    g_lo = rs.uniform(-1, 1, (Ny, Nx)) + 1j * rs.uniform(-1, 1, (Ny, Nx))
+    g_hi = rs.uniform(-1, 1, (Ny, Nx)) + 1j * rs.uniform(-1, 1, (Ny, Nx))
+    return O.grid_steps(shape, L), K, f, g_lo, g_hi
+
+
+def _planar(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(np.stack([a.real, a.imag]))).cuda()
+
+
+def _gpu(shape, L, order, K, zf, f, g_lo, g_hi):
+    torch = _torch()
+    Nx, Ny, Nz = shape
+    s = H.ZSolver(Nx, Ny, Nz, *L, order)
+    try:
+        s.set_coeff(K)
+        s.set_faces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
+        u = torch.full((2, Nz + 2, Ny, Nx), np.nan, dtype=torch.float64, device="cuda")
+        s.solve(_planar(torch, f), u, None if g_lo is None else _planar(torch, g_lo),
+                None if g_hi is None else _planar(torch, g_hi))
+        torch.cuda.synchronize()
+        uc = u.cpu().numpy()
+        return uc[0] + 1j * uc[1]
+    finally:
+        s.close()
+
+
+FACES = [(R, R), (R, D), (D, R), (D, D)]
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("faces", FACES)
+@pytest.mark.parametrize("shape", [(13, 9, 7), (31, 20, 17), (63, 40, 12)])
+def test_complex_solve_matches_oracle(order, faces, shape):
+    L = (1.0, 0.9, 1.2)
+    h, K, f, g_lo, g_hi = _case(shape, L, sum(shape) + order)
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    ref, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi)
+    got = _gpu(shape, L, order, K, zf, f, g_lo, g_hi)
+    assert O.max_rel_diff(got, ref) <= TOL
+
+
+@pytest.mark.parametrize("faces", FACES)
+def test_absent_face_data_and_one_plane(faces):
+    """g = NULL (zero face data) and Nz = 1: one interior plane, up to three unknown rows."""
+    shape, L = (15, 11, 1), (1.0, 1.0, 0.3)
+    h, K, f, _, _ = _case(shape, L, 5)
+    zf = CX.ZFaces(faces[0], 0.5 - 1.0j, 1.0 + 0.0j, faces[1], 2.0 + 0.0j, -0.5 + 1.5j)
+    ref, _ = CX.solve(4, h, K, zf, f, None, None)
+    got = _gpu(shape, L, 4, K, zf, f, None, None)
+    assert O.max_rel_diff(got, ref) <= TOL
+
+
+def test_dirichlet_real_data_equals_real_solver():
+    """Dirichlet faces, real K, real f and g: the complex solver gives the real FP64
+    solver's answer in the real part and exactly zero imaginary part."""
+    torch = _torch()
+    shape, L = (33, 27, 21), (1.0, 1.0, 1.0)
+    Nx, Ny, Nz = shape
+    rs = np.random.RandomState(3)
+    K = 25.0 + 10.0 * rs.uniform(size=Nz + 2)
+    f = rs.uniform(-1, 1, (Nz + 2, Ny + 2, Nx + 2))
+    g_lo, g_hi = rs.uniform(-1, 1, (Ny, Nx)), rs.uniform(-1, 1, (Ny, Nx))
+    got = _gpu(shape, L, 4, K.astype(complex), CX.ZFaces(), f.astype(complex),
+               g_lo.astype(complex), g_hi.astype(complex))
+    assert np.max(np.abs(got.imag)) == 0.0
+    s = H.Solver(Nx, Ny, Nz, *L, 4, H.HS_HELMHOLTZ, H.HS_FP64)
+    try:
+        s.set_coeff(K)
+        zl = np.zeros((Ny + 2, Nx + 2))
+        zh = np.zeros((Ny + 2, Nx + 2))
+        zl[1:-1, 1:-1], zh[1:-1, 1:-1] = g_lo, g_hi
+        u = torch.zeros((Nz, Ny, Nx), dtype=torch.float64, device="cuda")
+        faces = [None, None, None, None, torch.from_numpy(zl).cuda(), torch.from_numpy(zh).cuda()]
+        s.solve(torch.from_numpy(f).cuda(), u, H.HS_F64, H.HS_RHS_NODAL, faces, None)
+        torch.cuda.synchronize()
+        assert O.max_rel_diff(got[1:-1].real, u.cpu().numpy()) <= TOL
+    finally:
+        s.close()
+
+
+def test_complex_255_robin_matches_oracle():
+    """The benchmark's size: 255^3, 4th order, Robin on both z-faces."""
+    shape, L = (255, 255, 255), (1.0, 1.0, 1.0)
+    h, K, f, g_lo, g_hi = _case(shape, L, 11)
+    zf = CX.ZFaces(R, 1.0 + 0.5j, 3.0 - 1.0j, R, 1.0 + 0.5j, 3.0 - 1.0j)
+    ref, _ = CX.solve(4, h, K, zf, f, g_lo, g_hi)
+    got = _gpu(shape, L, 4, K, zf, f, g_lo, g_hi)
+    assert O.max_rel_diff(got, ref) <= TOL
+
+
+def test_errors():
+    torch = _torch()
+    with pytest.raises(H.HsError) as e:
+        H.ZSolver(8, 8, 8, 1.0, 1.0, 1.0, 6)
+    assert e.value.status == H.HS_ERR_INVALID_ARG
+    s = H.ZSolver(8, 7, 6, 1.0, 1.0, 1.0, 4)
+    try:
+        f = torch.zeros((2, 8, 9, 10), dtype=torch.float64, device="cuda")
+        u = torch.zeros((2, 8, 7, 8), dtype=torch.float64, device="cuda")
+        with pytest.raises(H.HsError) as e:
+            s.solve(f, u)
+        assert e.value.status == H.HS_ERR_NO_COEFF
+        s.set_coeff(np.full(8, 30.0 + 1.0j))
+        with pytest.raises(H.HsError) as e:
+            s.set_faces(H.HS_ZFACE_ROBIN, 0.0, 1.0, H.HS_ZFACE_DIRICHLET)
+        assert e.value.status == H.HS_ERR_INVALID_ARG
+        with pytest.raises(H.HsError) as e:
+            s.solve(f.cpu(), u)
+        assert e.value.status == H.HS_ERR_INVALID_ARG
+        s.solve(f, u)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(u).item() == 0
+    finally:
+        s.close()
