@@ -207,6 +207,12 @@ WORKLOADS = {
              "zero Dirichlet data, F ~ U[-1,1] h^2 assembled (seed 9); BiCGStab to "
              "||F - A x|| / ||F|| <= 1e-10 preconditioned by the separable solve for the plane "
              "means of k^2"),
+    "zrobin255_o4": dict(
+        steps=5,
+        desc="complex k(z) = 20(1+z^2/2)(1+0.02i), 4th-order compact Helmholtz on the unit "
+             "cube, 255^3 interior, first-order absorbing z-faces u_z +- i k u = 0 (Robin, "
+             "second-order closure, both face planes unknown), zero side faces, "
+             "f = U[-1,1] + i U[-1,1] (seed 12); FP64 path, complex z-solves"),
     "cd511x8": dict(
         steps=10,
         desc="4th-order compact convection-diffusion Lap(u)+b(z)u_z=f, 511^3 interior, "
@@ -321,6 +327,19 @@ def run_reference(args):
                        f"{Np}^3 instance of the same recipe per step (numpy FP64 BiCGStab, "
                        "the oracle's O(N^4) solve as preconditioner)", world)
         return
+    elif name == "zrobin255_o4":
+        wz = W.workload_zrobin(255)
+        steps = args.steps if args.steps is not None else 2
+        for _ in range(args.warmup):
+            zrobin_run_oracle(wz)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            zrobin_run_oracle(wz)
+        dt = (time.perf_counter() - t0) / steps
+        emit_reference(args, name, 255 ** 3 / dt / 1e9, dt, steps,
+                       "full 255^3 complex solve per step (numpy FP64, O(N^4) sine sums, "
+                       "textbook complex Thomas)", world)
+        return
     elif name == "batch64":
         sp = W.workload_batch_specs(nprob=64, seed=3)[0]
         p = W.batch_problem(sp, 0)
@@ -434,6 +453,73 @@ def bench_precond(args, torch, H, rank, world, barrier, max_over_ranks):
             "gpu_launches": res["mixed"]["gpu_launches"],
         }
         print(json.dumps(line), flush=True)
+
+
+def zrobin_run_oracle(w):
+    from oracle import hs_complex_oracle as CX
+    from oracle import hs_oracle as O
+    N = w["N"]
+    zf = CX.ZFaces(CX.ROBIN, w["alpha_lo"], w["beta_lo"], CX.ROBIN, w["alpha_hi"], w["beta_hi"])
+    h = O.grid_steps((N, N, N), w["L"])
+    return CX.solve(w["order"], h, w["K"], zf, w["f"])[0]
+
+
+def bench_zrobin(args, torch, H, W, rank, world, barrier, max_over_ranks):
+    """Complex k(z) with absorbing (Robin) z-faces: one hs_zsolve per step (FP64)."""
+    w = W.workload_zrobin(255)
+    N = w["N"]
+    s = H.ZSolver(N, N, N, *w["L"], w["order"])
+    s.set_coeff(w["K"])
+    s.set_faces(H.HS_ZFACE_ROBIN, w["alpha_lo"], w["beta_lo"], H.HS_ZFACE_ROBIN,
+                w["alpha_hi"], w["beta_hi"])
+    f = torch.from_numpy(np.ascontiguousarray(np.stack([w["f"].real, w["f"].imag]))).cuda()
+    u = torch.empty((2, N + 2, N, N), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        s.solve(f, u, stream=stream)
+    torch.cuda.synchronize()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        s.solve(f, u, stream=stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev)) / args.steps
+    acc, cpu = {"compared_against": "oracle (complex FP64, O(N^4) sine sums)"}, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        ref = zrobin_run_oracle(w)
+        dt = time.perf_counter() - t0
+        got = u.cpu().numpy()
+        got = got[0] + 1j * got[1]
+        acc["max_rel_error"] = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        cpu = {"value": N ** 3 / dt / 1e9, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"one full {N}^3 complex oracle solve (numpy FP64): {dt:.2f} s"}
+    value = world * N ** 3 / (ms * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128 (FP64 re, im)", "data": "synthetic",
+            "config": {"workload": f"zrobin255_o4: {WORKLOADS['zrobin255_o4']['desc']}",
+                       "global_batch": world, "parallelism": f"replicas x{world}",
+                       "l2": "256 MB buffer written between timed steps",
+                       "unknowns": "complex, planes l = 0..N+1 (Robin faces)"},
+            "accuracy": acc, "cpu_baseline": cpu, "e2e": None, "roofline": None,
+            "clocks": clocks,
+            # right-hand side, 4 transform passes, complex z-solve
+            "gpu_launches": 6 * args.steps,
+            "workspace_bytes": s.workspace_bytes(),
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
 
 
 def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
@@ -634,6 +720,12 @@ def main():
     if args.workload == "precond255_o4":
         bench_precond(args, torch, H, rank, world, barrier,
                       lambda x: reduce_max(x, dist, "cuda"))
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    if args.workload == "zrobin255_o4":
+        bench_zrobin(args, torch, H, W, rank, world, barrier,
+                     lambda x: reduce_max(x, dist, "cuda"))
         if dist is not None:
             dist.destroy_process_group()
         return

@@ -413,3 +413,20 @@ def workload_convdiff511(rhs_index: int, seed: int = 5, N: int = 511) -> Problem
     return random_interior_problem((N, N, N), (1.0, 1.0, 1.0), 4, CONVDIFF, gamma_2_sin2pi(),
                                    seed * 1000 + rhs_index, np.float32,
                                    name=f"cd{N}r{rhs_index}")
+
+
+def workload_zrobin(N: int = 255, seed: int = 12) -> dict:
+    """Complex k(z) with first-order absorbing z-faces on the unit cube (N^3 interior).
+
+    k(z) = 20 (1 + z^2 / 2) (1 + 0.02 i) (a weakly absorbing medium), K = k^2 at
+    the nodes z_l; z-faces Robin u_z + i k u = 0 at z = 0 and u_z - i k u = 0 at
+    z = 1 (alpha = 1, beta = +-i k at the face, zero data); side faces zero;
+    f = U[-1,1] + i U[-1,1] at interior nodes (seeded), zero on the faces.
+    Returns the plan parameters and the arrays (numpy complex)."""
+    z = node_coords(N, 1.0)
+    k = 20.0 * (1.0 + 0.5 * z ** 2) * (1.0 + 0.02j)
+    rs = np.random.RandomState(seed)
+    f = np.zeros((N + 2, N + 2, N + 2), dtype=np.complex128)
+    f[1:-1, 1:-1, 1:-1] = (rs.uniform(-1, 1, (N, N, N)) + 1j * rs.uniform(-1, 1, (N, N, N)))
+    return dict(N=N, L=(1.0, 1.0, 1.0), order=4, K=k * k,
+                alpha_lo=1.0, beta_lo=1j * k[0], alpha_hi=1.0, beta_hi=-1j * k[-1], f=f)
