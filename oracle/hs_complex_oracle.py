@@ -30,10 +30,20 @@ Nz + 1 for a Robin hi face, else Nz).  Side faces stay Dirichlet, so Section
 3.6's sine transforms in x and y still split the system into N_x N_y complex
 tridiagonal systems in z; these are solved by the textbook recurrence.
 
-Arrays: f on the node grid [Nz+2][Ny+2][Nx+2] (complex; side-face nodes are
-never read by the 2nd-order rows and are 0 for the 4th-order operator as u is
-0 there -- they are read as given); face data g_lo, g_hi on the interior face
-nodes [Ny][Nx] (complex; None = 0); the solution on all planes [Nz+2][Ny][Nx]
+Neumann side faces (the extension Section 1 names): a side axis may instead
+carry u_n = 0 on both of its faces.  Its boundary nodes become unknowns, the
+operator sees the even reflection u_-1 = u_1 (the central difference of
+u_x = 0), f is reflected the same way, and the sine transform of that axis is
+replaced by the cosine transform DCT-I over the nodes 0..N+1, whose modes
+cos(p pi i / (N+1)), p = 0..N+1, diagonalise the reflected second difference
+with the same eigenvalue formula (Section 3.6) -- the per-row coefficients are
+unchanged.
+
+Arrays: f on the node grid [Nz+2][Ny+2][Nx+2] (complex; side-face nodes of a
+Dirichlet axis are read by the 4th-order operator as given); the unknown grid
+of a plane is [ny][nx] with nx = Nx + 2 for a Neumann x-axis (nodes 0..Nx+1),
+else Nx (nodes 1..Nx), and likewise ny; face data g_lo, g_hi on that grid of
+the z-face (complex; None = 0); the solution on all planes [Nz+2][ny][nx]
 (Dirichlet planes hold g).
 """
 from __future__ import annotations
@@ -60,6 +70,58 @@ class ZFaces:
 
     def unknown_planes(self, Nz):
         return (0 if self.lo == ROBIN else 1), (Nz + 1 if self.hi == ROBIN else Nz)
+
+
+SIDE_DIRICHLET = 0
+SIDE_NEUMANN = 1
+
+
+def _n_unknown(N, kind):
+    return N + 2 if kind == SIDE_NEUMANN else N
+
+
+def cosine_matrix(N):
+    """DCT-I over the nodes 0..N+1 (M = N + 1): C[p, i] = w_i cos(pi p i / M), p, i = 0..M,
+    w_0 = w_M = 1/2, else 1; the argument is reduced as an integer modulo 2M first."""
+    M = N + 1
+    k = np.outer(np.arange(M + 1), np.arange(M + 1)) % (2 * M)
+    C = np.cos(np.pi * k / M)
+    C[:, 0] *= 0.5
+    C[:, M] *= 0.5
+    return C
+
+
+def side_transform(N, kind):
+    """(forward, inverse) matrices of one side axis: DST-I of the interior nodes, or DCT-I
+    of all nodes; inverse(forward(x)) = x."""
+    if kind == SIDE_NEUMANN:
+        # the DCT-I is its own inverse up to 2/M: x_i = (2/M) sum_p w_p X_p cos(pi p i/M)
+        C = cosine_matrix(N)
+        return C, (2.0 / (N + 1)) * C
+    S = O.sine_matrix(N)
+    return S, (2.0 / (N + 1)) * S.T
+
+
+def side_cosines(N, kind):
+    """cos(theta_p) of the modes of one side axis."""
+    if kind == SIDE_NEUMANN:
+        return np.cos(np.pi * np.arange(0, N + 2) / (N + 1))
+    return O.mode_cosines(N)
+
+
+def reflect_pad(U, sides):
+    """Pad a field on the unknown grid [..., ny, nx] by one node per side: zero beyond a
+    Dirichlet axis (its boundary nodes), the even reflection beyond a Neumann axis."""
+    U = np.asarray(U)
+    pad = [(0, 0)] * (U.ndim - 2) + [(1, 1), (1, 1)]
+    P = np.pad(U, pad)
+    if sides[1] == SIDE_NEUMANN:
+        P[..., 0, :] = P[..., 2, :]
+        P[..., -1, :] = P[..., -3, :]
+    if sides[0] == SIDE_NEUMANN:
+        P[..., :, 0] = P[..., :, 2]
+        P[..., :, -1] = P[..., :, -3]
+    return P
 
 
 def complex_coefficients(order, h, K):
@@ -121,35 +183,57 @@ def _pad2(g):
     return P
 
 
-def rhs(order, h, K, zf, f_nodes, g_lo=None, g_hi=None):
-    """Right-hand side of the unknown rows: array (Nu, Ny, Nx) complex."""
+def _f_on_unknowns(f, sides):
+    """f on [Nz+2][ny+2][nx+2]: the unknown grid of every plane plus one node per side
+    (a Dirichlet axis' boundary nodes as given, the even reflection beyond a Neumann one)."""
+    sx = slice(None) if sides[0] == SIDE_NEUMANN else slice(1, -1)
+    sy = slice(None) if sides[1] == SIDE_NEUMANN else slice(1, -1)
+    core = f[:, sy, sx]
+    P = np.zeros((f.shape[0], core.shape[1] + 2, core.shape[2] + 2), dtype=f.dtype)
+    P[:, 1:-1, 1:-1] = core
+    if sides[0] == SIDE_NEUMANN:
+        P[:, :, 0], P[:, :, -1] = P[:, :, 2], P[:, :, -3]
+    else:
+        P[:, 1:-1, 0], P[:, 1:-1, -1] = f[:, sy, 0], f[:, sy, -1]
+    if sides[1] == SIDE_NEUMANN:
+        P[:, 0, :], P[:, -1, :] = P[:, 2, :], P[:, -3, :]
+    else:
+        P[:, 0, 1:-1], P[:, -1, 1:-1] = f[:, 0, sx], f[:, -1, sx]
+    return P
+
+
+def rhs(order, h, K, zf, f_nodes, g_lo=None, g_hi=None, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
+    """Right-hand side of the unknown rows: array (Nu, ny, nx) complex."""
     hz = h[2]
     f = np.asarray(f_nodes, dtype=np.complex128)
-    Nz, Ny, Nx = f.shape[0] - 2, f.shape[1] - 2, f.shape[2] - 2
-    glo, ghi = _face(g_lo, Ny, Nx), _face(g_hi, Ny, Nx)
-    Fi = (O.rhs_operator(order, O.HELMHOLTZ, h, f.real)
-          + 1j * O.rhs_operator(order, O.HELMHOLTZ, h, f.imag))
+    Nz = f.shape[0] - 2
+    fu = _f_on_unknowns(f, sides)
+    ny, nx = fu.shape[1] - 2, fu.shape[2] - 2
+    glo, ghi = _face(g_lo, ny, nx), _face(g_hi, ny, nx)
+    # R_h of the order on the padded unknown grid (interior planes 1..Nz)
+    Fi = (O.rhs_operator(order, O.HELMHOLTZ, h, fu.real)
+          + 1j * O.rhs_operator(order, O.HELMHOLTZ, h, fu.imag))
     Ci = complex_coefficients(order, h, K)
     # Dirichlet faces: their known plane leaves rows 1 / Nz through the stencil
     if zf.lo == DIRICHLET:
-        Fi[0] -= _plane_part(Ci[0, O.LOW], _pad2(glo))
+        Fi[0] -= _plane_part(Ci[0, O.LOW], reflect_pad(glo, sides))
     if zf.hi == DIRICHLET:
-        Fi[-1] -= _plane_part(Ci[-1, O.UPP], _pad2(ghi))
+        Fi[-1] -= _plane_part(Ci[-1, O.UPP], reflect_pad(ghi, sides))
     rows = []
     if zf.lo == ROBIN:
         # u_-1 = u_1 - 2 h (g - beta u_0) / alpha: the data part enters the row with weight 1
-        rows.append(hz * hz * f[0, 1:-1, 1:-1] + 2.0 * hz * glo / zf.alpha[0])
+        rows.append(hz * hz * fu[0, 1:-1, 1:-1] + 2.0 * hz * glo / zf.alpha[0])
     rows.extend(Fi)
     if zf.hi == ROBIN:
-        rows.append(hz * hz * f[Nz + 1, 1:-1, 1:-1] - 2.0 * hz * ghi / zf.alpha[1])
+        rows.append(hz * hz * fu[Nz + 1, 1:-1, 1:-1] - 2.0 * hz * ghi / zf.alpha[1])
     return np.array(rows)
 
 
-def eigenvalues(R, Nx, Ny):
-    """lambda_nu(p, q) of every unknown row: complex array (3, Nu, Ny, Nx)."""
-    cx = O.mode_cosines(Nx)[None, None, :]
-    cy = O.mode_cosines(Ny)[None, :, None]
-    lam = np.empty((3, R.shape[0], Ny, Nx), dtype=np.complex128)
+def eigenvalues(R, Nx, Ny, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
+    """lambda_nu(p, q) of every unknown row: complex array (3, Nu, ny, nx)."""
+    cx = side_cosines(Nx, sides[0])[None, None, :]
+    cy = side_cosines(Ny, sides[1])[None, :, None]
+    lam = np.empty((3, R.shape[0], cy.shape[1], cx.shape[2]), dtype=np.complex128)
     for nu in range(3):
         cf = R[:, nu, :]
         lam[nu] = (4.0 * cf[:, O.A_, None, None] * cx * cy + 2.0 * cf[:, O.B_, None, None] * cx
@@ -157,30 +241,33 @@ def eigenvalues(R, Nx, Ny):
     return lam
 
 
-def solve_rows(R, F):
-    """U (Nu, Ny, Nx) = A^-1 F by Section 3.6: 2-D DST, complex tridiagonals in z, inverse."""
-    Nu, Ny, Nx = F.shape
-    Sx, Sy = O.sine_matrix(Nx), O.sine_matrix(Ny)
-    Fhat = O.dst2_forward(F, Sx, Sy)
-    lam = eigenvalues(R, Nx, Ny)
+def solve_rows(R, F, Nx, Ny, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
+    """U (Nu, ny, nx) = A^-1 F by Section 3.6: 2-D side transforms, complex tridiagonals
+    in z, inverse transforms."""
+    Tx, Txi = side_transform(Nx, sides[0])
+    Ty, Tyi = side_transform(Ny, sides[1])
+    Fhat = np.matmul(Ty, F @ Tx.T)
+    lam = eigenvalues(R, Nx, Ny, sides)
     W, ratio = O.thomas(lam[O.LOW], lam[O.MID], lam[O.UPP], Fhat)
-    return O.dst2_inverse(W, Sx, Sy), ratio
+    return np.matmul(Tyi, W @ Txi.T), ratio
 
 
-def solve(order, h, K, zf, f_nodes, g_lo=None, g_hi=None):
-    """Solution on every plane l = 0..Nz+1 (interior x, y): complex (Nz+2, Ny, Nx)."""
+def solve(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
+          sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
+    """Solution on every plane l = 0..Nz+1 (unknown grid in x, y): complex (Nz+2, ny, nx)."""
     f = np.asarray(f_nodes, dtype=np.complex128)
     Nz, Ny, Nx = f.shape[0] - 2, f.shape[1] - 2, f.shape[2] - 2
+    ny, nx = _n_unknown(Ny, sides[1]), _n_unknown(Nx, sides[0])
     R = row_table(order, h, K, zf)
-    F = rhs(order, h, K, zf, f, g_lo, g_hi)
-    Uu, ratio = solve_rows(R, F)
+    F = rhs(order, h, K, zf, f, g_lo, g_hi, sides)
+    Uu, ratio = solve_rows(R, F, Nx, Ny, sides)
     l0, l1 = zf.unknown_planes(Nz)
-    U = np.zeros((Nz + 2, Ny, Nx), dtype=np.complex128)
+    U = np.zeros((Nz + 2, ny, nx), dtype=np.complex128)
     U[l0:l1 + 1] = Uu
     if zf.lo == DIRICHLET:
-        U[0] = _face(g_lo, Ny, Nx)
+        U[0] = _face(g_lo, ny, nx)
     if zf.hi == DIRICHLET:
-        U[Nz + 1] = _face(g_hi, Ny, Nx)
+        U[Nz + 1] = _face(g_hi, ny, nx)
     return U, {"min_pivot_ratio": ratio}
 
 
@@ -189,7 +276,8 @@ def solve(order, h, K, zf, f_nodes, g_lo=None, g_hi=None):
 # itself, the face condition imposed through an explicit ghost plane
 
 
-def apply_operator(order, h, K, zf, U_all, g_lo=None, g_hi=None):
+def apply_operator(order, h, K, zf, U_all, g_lo=None, g_hi=None,
+                   sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
     """Rows l0..l1 of (A U - data terms): U_all on planes 0..Nz+1 (interior x, y).
 
     Interior rows: the 27-point stencil with the complex table.  Robin rows: the
@@ -200,8 +288,8 @@ def apply_operator(order, h, K, zf, U_all, g_lo=None, g_hi=None):
     K = np.asarray(K, dtype=np.complex128)
     U_all = np.asarray(U_all, dtype=np.complex128)
     Nz, Ny, Nx = U_all.shape[0] - 2, U_all.shape[1], U_all.shape[2]
-    P = np.zeros((Nz + 2, Ny + 2, Nx + 2), dtype=np.complex128)
-    P[:, 1:-1, 1:-1] = U_all
+    # beyond a Neumann side: the ghost u_-1 = u_1 of u_n = 0, built explicitly
+    P = reflect_pad(U_all, sides)
     Ci = complex_coefficients(order, h, K)
     out = []
     glo, ghi = _face(g_lo, Ny, Nx), _face(g_hi, Ny, Nx)
@@ -231,21 +319,25 @@ def apply_operator(order, h, K, zf, U_all, g_lo=None, g_hi=None):
     return np.array(out)
 
 
-def rhs_direct(order, h, f_nodes):
+def rhs_direct(order, h, f_nodes, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
     """The scheme's f-side on every plane that can be a row: R_h f on interior rows
-    (real operator on Re f and Im f), h_z^2 f on the two face planes."""
+    (real operator on Re f and Im f, f reflected beyond a Neumann side), h_z^2 f on the
+    two face planes."""
     hz = h[2]
     f = np.asarray(f_nodes, dtype=np.complex128)
-    Fi = (O.rhs_operator(order, O.HELMHOLTZ, h, f.real)
-          + 1j * O.rhs_operator(order, O.HELMHOLTZ, h, f.imag))
-    return hz * hz * f[0, 1:-1, 1:-1], Fi, hz * hz * f[-1, 1:-1, 1:-1]
+    fu = _f_on_unknowns(f, sides)
+    Fi = (O.rhs_operator(order, O.HELMHOLTZ, h, fu.real)
+          + 1j * O.rhs_operator(order, O.HELMHOLTZ, h, fu.imag))
+    return hz * hz * fu[0, 1:-1, 1:-1], Fi, hz * hz * fu[-1, 1:-1, 1:-1]
 
 
-def solve_dense(order, h, K, zf, f_nodes, g_lo=None, g_hi=None):
+def solve_dense(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
+                sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
     """Brute force: the matrix of apply_operator (columns from unit vectors), its data
     part from the operator at U = 0, and a dense complex LU solve."""
     f = np.asarray(f_nodes, dtype=np.complex128)
-    Nz, Ny, Nx = f.shape[0] - 2, f.shape[1] - 2, f.shape[2] - 2
+    Nz = f.shape[0] - 2
+    Ny, Nx = _n_unknown(f.shape[1] - 2, sides[1]), _n_unknown(f.shape[2] - 2, sides[0])
     l0, l1 = zf.unknown_planes(Nz)
     Nu = l1 - l0 + 1
     base = np.zeros((Nz + 2, Ny, Nx), dtype=np.complex128)
@@ -253,7 +345,7 @@ def solve_dense(order, h, K, zf, f_nodes, g_lo=None, g_hi=None):
         base[0] = _face(g_lo, Ny, Nx)
     if zf.hi == DIRICHLET:
         base[Nz + 1] = _face(g_hi, Ny, Nx)
-    data = apply_operator(order, h, K, zf, base, g_lo, g_hi).ravel()
+    data = apply_operator(order, h, K, zf, base, g_lo, g_hi, sides).ravel()
     n = Nu * Ny * Nx
     A = np.zeros((n, n), dtype=np.complex128)
     zero_faces = ZFaces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
@@ -262,8 +354,8 @@ def solve_dense(order, h, K, zf, f_nodes, g_lo=None, g_hi=None):
         e[k] = 1.0
         Ue = np.zeros((Nz + 2, Ny, Nx), dtype=np.complex128)
         Ue[l0:l1 + 1] = e.reshape(Nu, Ny, Nx)
-        A[:, k] = apply_operator(order, h, K, zero_faces, Ue).ravel()
-    flo, Fi, fhi = rhs_direct(order, h, f)
+        A[:, k] = apply_operator(order, h, K, zero_faces, Ue, sides=sides).ravel()
+    flo, Fi, fhi = rhs_direct(order, h, f, sides)
     rows = ([flo] if zf.lo == ROBIN else []) + list(Fi) + ([fhi] if zf.hi == ROBIN else [])
     b = np.array(rows).ravel() - data
     x = np.linalg.solve(A, b).reshape(Nu, Ny, Nx)

@@ -11,7 +11,12 @@ What fixes it, independently of its own code paths:
   (e) mirroring z maps a Robin face (alpha, beta) on one side to (-alpha, beta) on
       the other, and the solution mirrors with it;
   (f) on a manufactured complex solution the error falls at least like h^2 with
-      Robin faces, and like h^4 (4th order) with Dirichlet faces.
+      Robin faces, and like h^4 (4th order) with Dirichlet faces;
+  (g) Neumann side axes: the DCT-I pair inverts, and it diagonalises the reflected
+      second difference with eigenvalues 2 cos(theta_p) - 2, theta_p = p pi/(N+1),
+      p = 0..N+1; the separated solve equals the dense solve of the operator built
+      with explicit reflected ghosts; swapping x and y swaps the solution; a
+      manufactured cos-cos solution converges.
 """
 import numpy as np
 import pytest
@@ -146,5 +151,88 @@ def _manufactured(N, order, zf_kind, kappa=2.5, c=(40.0, 8.0)):
 @pytest.mark.parametrize("order,kind,lo_ratio", [(2, R, 3.5), (4, R, 3.5), (2, D, 3.5), (4, D, 12.0)])
 def test_manufactured_complex_solution_converges(order, kind, lo_ratio):
     e = [_manufactured(N, order, kind) for N in (7, 15, 31)]
+    assert e[2] < e[1] < e[0]
+    assert e[1] / e[2] >= lo_ratio, e
+
+
+NEU, DIR = CX.SIDE_NEUMANN, CX.SIDE_DIRICHLET
+
+
+@pytest.mark.parametrize("N", [1, 6, 15])
+def test_dct_pair_and_reflected_second_difference(N):
+    C, Ci = CX.side_transform(N, NEU)
+    assert np.max(np.abs(Ci @ C - np.eye(N + 2))) <= 1e-13
+    # second difference over nodes 0..N+1 with the reflected ghosts u_-1 = u_1
+    n = N + 2
+    D = -2.0 * np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
+    D[0, 1] = 2.0
+    D[-1, -2] = 2.0
+    lam = 2.0 * CX.side_cosines(N, NEU) - 2.0
+    assert np.max(np.abs(C @ D @ Ci - np.diag(lam))) <= 1e-12
+    # and the sine pair for comparison (Dirichlet axis)
+    S, Si = CX.side_transform(N, DIR)
+    assert np.max(np.abs(Si @ S - np.eye(N))) <= 1e-13
+
+
+def _neumann_case(shape, seed):
+    Nx, Ny, Nz = shape
+    rs = np.random.RandomState(seed)
+    h = O.grid_steps(shape, (1.0, 0.9, 1.1))
+    K = (30.0 + 10.0 * rs.uniform(size=Nz + 2)) * (1.0 + 0.3j * rs.uniform(size=Nz + 2))
+    f = _crand(rs, (Nz + 2, Ny + 2, Nx + 2))
+    return h, K, f, rs
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("sides", [(NEU, DIR), (DIR, NEU), (NEU, NEU)])
+@pytest.mark.parametrize("faces", [(R, R), (D, D), (R, D)])
+def test_neumann_sides_separated_equals_dense(order, sides, faces):
+    shape = (5, 4, 5)
+    h, K, f, rs = _neumann_case(shape, 50 + order + 3 * sides[0] + sides[1] + 7 * faces[1])
+    nx = shape[0] + 2 if sides[0] == NEU else shape[0]
+    ny = shape[1] + 2 if sides[1] == NEU else shape[1]
+    g_lo, g_hi = _crand(rs, (ny, nx)), _crand(rs, (ny, nx))
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    U, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi, sides)
+    Ud = CX.solve_dense(order, h, K, zf, f, g_lo, g_hi, sides)
+    assert U.shape == (shape[2] + 2, ny, nx)
+    assert O.max_rel_diff(U, Ud) <= 1e-11
+
+
+def test_neumann_x_y_swap():
+    N, Nz = 6, 5
+    rs = np.random.RandomState(61)
+    h = O.grid_steps((N, N, Nz), (1.0, 1.0, 1.2))
+    K = (25.0 + 5.0 * rs.uniform(size=Nz + 2)) * (1.0 + 0.1j)
+    f = _crand(rs, (Nz + 2, N + 2, N + 2))
+    zf = CX.ZFaces(R, 1.0 - 0.5j, 0.5 + 1.0j, D)
+    g_lo = _crand(rs, (N, N + 2))           # unknown grid of (NEU x, DIR y): ny = N, nx = N + 2
+    U1, _ = CX.solve(4, h, K, zf, f, g_lo, None, (NEU, DIR))
+    U2, _ = CX.solve(4, h, K, zf, f.transpose(0, 2, 1), g_lo.T, None, (DIR, NEU))
+    assert O.max_rel_diff(U2.transpose(0, 2, 1), U1) <= 1e-12
+
+
+def _manufactured_neumann(N, order, zkind, kappa=2.0):
+    h = (1.0 / (N + 1),) * 3
+    x = np.arange(N + 2) * h[0]
+    z = x.copy()
+    K = (35.0 + 6.0j) * (1.0 + 0.5 * z)
+    u = (np.cos(np.pi * x)[None, None, :] * np.cos(2 * np.pi * x)[None, :, None]
+         * np.exp(1j * kappa * z)[:, None, None])
+    f = (-5.0 * np.pi ** 2 - kappa ** 2 + K[:, None, None]) * u
+    alpha, beta = 1.0 + 0.5j, 3.0 - 1.0j
+    if zkind == R:
+        zf = CX.ZFaces(R, alpha, beta, R, alpha, beta)
+        gfun = (1j * kappa * alpha + beta) * u
+    else:
+        zf = CX.ZFaces()
+        gfun = u
+    U, _ = CX.solve(order, h, K, zf, f, gfun[0], gfun[-1], (NEU, NEU))
+    return np.max(np.abs(U - u))
+
+
+@pytest.mark.parametrize("order,kind,lo_ratio", [(2, R, 3.5), (4, R, 3.5), (4, D, 12.0)])
+def test_neumann_manufactured_converges(order, kind, lo_ratio):
+    e = [_manufactured_neumann(N, order, kind) for N in (7, 15, 31)]
     assert e[2] < e[1] < e[0]
     assert e[1] / e[2] >= lo_ratio, e
