@@ -514,16 +514,25 @@ const char *hs_last_error(hs_plan_t plan);
  * real DSTs act on Re and Im, and each sine mode (p, q) is one complex
  * tridiagonal system in z, solved without pivoting.
  *
- * Complex arrays are planar: all real parts, then all imaginary parts.
+ * A side axis (x or y) may instead carry u_n = 0 on both of its faces (the
+ * extension Section 1 names): its boundary nodes become unknowns, f and the
+ * face data are reflected evenly beyond them (the central difference of
+ * u_n = 0), and the cosine transform DCT-I over nodes 0..N+1 replaces the sine
+ * transform (modes cos(p pi i/(N+1)), p = 0..N+1, same eigenvalue formula).
+ *
+ * The unknown grid of a plane is [ny][nx]: nx = Nx + 2 (nodes 0..Nx+1) for a
+ * Neumann x-axis, else Nx (nodes 1..Nx); likewise ny.  Complex arrays are
+ * planar: all real parts, then all imaginary parts.
  *   f:  [2][Nz+2][Ny+2][Nx+2]  on the node grid (device memory);
- *   g_lo, g_hi: [2][Ny][Nx]    on the interior nodes of the z-face (device
- *                              memory; NULL = 0); the side faces are 0;
- *   u:  [2][Nz+2][Ny][Nx]      every plane (device memory): Dirichlet planes
+ *   g_lo, g_hi: [2][ny][nx]    on the unknown grid of the z-face (device
+ *                              memory; NULL = 0); Dirichlet side faces are 0;
+ *   u:  [2][Nz+2][ny][nx]      every plane (device memory): Dirichlet planes
  *                              receive g, the others the solution.
  * Scalars alpha, beta and the coefficient K are host (re, im) pairs.
  */
 typedef struct hs_zplan_s *hs_zplan_t;
 enum { HS_ZFACE_DIRICHLET = 0, HS_ZFACE_ROBIN = 1 };
+enum { HS_SIDE_DIRICHLET = 0, HS_SIDE_NEUMANN = 1 };
 
 /* hs_zplan -- plan for an Nx x Ny x Nz interior grid on [0,Lx]x[0,Ly]x[0,Lz]
  * (h_a = L_a / (N_a + 1)), order 2 or 4.  Faces start Dirichlet.  Errors:
@@ -542,6 +551,12 @@ hs_status hs_zplan_set_coeff(hs_zplan_t plan, const double *K);
 hs_status hs_zplan_set_faces(hs_zplan_t plan, int lo_kind, const double *alpha_lo,
                              const double *beta_lo, int hi_kind, const double *alpha_hi,
                              const double *beta_hi);
+
+/* hs_zplan_set_sides -- kind (HS_SIDE_DIRICHLET / HS_SIDE_NEUMANN) of the x and
+ * y side axes (default Dirichlet).  A Neumann axis needs N + 1 with a compiled
+ * transform (N + 1 in {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024}).
+ * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED, HS_ERR_OOM. */
+hs_status hs_zplan_set_sides(hs_zplan_t plan, int x_kind, int y_kind);
 
 /* hs_zsolve -- one solve on `stream` (asynchronous; the caller keeps f, g and
  * u valid until the stream has passed it).  Errors: HS_ERR_INVALID_ARG (NULL

@@ -40,6 +40,7 @@ HS_AXIS_X, HS_AXIS_Y = 0, 1
 HS_FACTOR_AUTO, HS_FACTOR_F32, HS_FACTOR_F64 = 0, 1, 2
 HS_HOST_F_MAPPED, HS_HOST_U_MAPPED, HS_HOST_F_EARLY, HS_HOST_U_LATE = 1, 2, 4, 8
 HS_ZFACE_DIRICHLET, HS_ZFACE_ROBIN = 0, 1
+HS_SIDE_DIRICHLET, HS_SIDE_NEUMANN = 0, 1
 HS_THOMAS_PIPE16_256, HS_THOMAS_PIPE8_128, HS_THOMAS_PLAIN16_256, HS_THOMAS_PIPE16_128 = 0, 1, 2, 3
 HS_INFO_MAX_ITERS = 8
 HS_INFO_STAGES = 8
@@ -58,7 +59,8 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_set_factor_precision",
             "hs_precond_create", "hs_precond_apply", "hs_precond_solve", "hs_precond_destroy",
             "hs_batch_workspace_bytes", "hs_batch_destroy",
-            "hs_zplan", "hs_zplan_set_coeff", "hs_zplan_set_faces", "hs_zsolve",
+            "hs_zplan", "hs_zplan_set_coeff", "hs_zplan_set_faces", "hs_zplan_set_sides",
+            "hs_zsolve",
             "hs_zplan_workspace_bytes", "hs_zplan_last_error", "hs_zplan_destroy")
 HS_STATIC_MAX_NZ = 8192
 
@@ -166,6 +168,8 @@ def load(path: Optional[str] = None):
     lib.hs_zplan_set_coeff.restype = ci
     lib.hs_zplan_set_faces.argtypes = [vp, ci, dp, dp, ci, dp, dp]
     lib.hs_zplan_set_faces.restype = ci
+    lib.hs_zplan_set_sides.argtypes = [vp, ci, ci]
+    lib.hs_zplan_set_sides.restype = ci
     lib.hs_zsolve.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.hs_zsolve.restype = ci
     lib.hs_zplan_workspace_bytes.argtypes = [vp]
@@ -565,7 +569,8 @@ class ZSolver:
     """Complex k(z) and Robin / Dirichlet z-faces on the FP64 path (orders 2, 4).
 
     Arrays are planar complex float64 device tensors: f [2][Nz+2][Ny+2][Nx+2],
-    g_lo / g_hi [2][Ny][Nx] (None = 0), u [2][Nz+2][Ny][Nx]."""
+    g_lo / g_hi [2][ny][nx] (None = 0), u [2][Nz+2][ny][nx], with nx = Nx + 2 on a
+    Neumann x-axis (set_sides) else Nx, and likewise ny."""
 
     def __init__(self, Nx, Ny, Nz, Lx, Ly, Lz, order):
         out = ctypes.c_void_p()
@@ -590,6 +595,10 @@ class ZSolver:
         return self._err(load().hs_zplan_set_faces(self.plan, int(lo_kind), _pair(alpha_lo),
                                                    _pair(beta_lo), int(hi_kind), _pair(alpha_hi),
                                                    _pair(beta_hi)), "hs_zplan_set_faces")
+
+    def set_sides(self, x_kind, y_kind):
+        return self._err(load().hs_zplan_set_sides(self.plan, int(x_kind), int(y_kind)),
+                         "hs_zplan_set_sides")
 
     def solve(self, f, u, g_lo=None, g_hi=None, stream=None):
         self._keep = (f, u, g_lo, g_hi)

@@ -158,6 +158,14 @@ extern "C" hs_status hs_plan_ex(hs_plan_t *out, int Nx, int Ny, int Nz, double L
                                 double Lz, int order, int equation, int bc, int precision,
                                 int max_rhs, int lean);
 
+// FP64 DCT-I of lines of M + 1 nodes (k_dct.cu), in place allowed; roots: M
+// complex exp(-2 pi i k / M), half: M + 1 complex (cos, sin)(pi k / M).  axis X:
+// nrows contiguous rows; axis Y: the nx columns of nplanes planes [M + 1][nx].
+// HS_ERR_UNSUPPORTED unless M has a compiled FFT (hs_dst_fast_size).
+hs_status hs_launch_dct(int axis, int M, const double *in, double *out, const void *roots,
+                        const void *half, long nrows, int nx, int nplanes, double scale,
+                        cudaStream_t s);
+
 // Lines per CTA of the fused tile of length M (0: not built for that length).
 int hs_dst_fused_lines_x(int M, int wide);
 int hs_dst_fused_lines_y(int M, int wide);

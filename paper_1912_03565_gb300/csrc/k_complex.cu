@@ -13,11 +13,17 @@
 // which gives the row  Rzx dxx + Rzy dyy + 2 u_(inner) + (-2 - 2Rzx - 2Rzy +
 // h_z^2 K -+ 2 h_z beta / alpha) u_face = h_z^2 f +- 2 h_z g / alpha.
 //
+// A side axis may instead carry u_n = 0 on both faces: its boundary nodes are
+// unknowns, f and the face data are reflected evenly beyond them, and the
+// cosine transform DCT-I over nodes 0..N+1 (k_dct.cu) replaces the sine
+// transform; the modes cos(p pi i/(N+1)), p = 0..N+1, enter the same eigenvalue
+// formula, and the per-row coefficients are unchanged.
+//
 // The solve (Section 3.6 with complex rows): the right-hand side kernel writes
-// the unknown rows l0..l1 as planar complex data [2][Nu][Ny][Nx]; the real FP64
-// sine transforms of an internal plan with 2 Nu planes act on Re and Im; one
-// thread per sine mode (p, q) solves the complex tridiagonal system in z by the
-// textbook recurrence (no pivoting); the inverse transforms follow.
+// the unknown rows l0..l1 as planar complex data [2][Nu][ny][nx]; the real FP64
+// transforms (sine: an internal plan over 2 Nu planes; cosine: k_dct.cu) act on
+// Re and Im; one thread per mode (p, q) solves the complex tridiagonal system in
+// z by the textbook recurrence (no pivoting); the inverse transforms follow.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -36,7 +42,11 @@ struct hs_zplan_s {
     std::vector<double2> K;    // Nz + 2 nodes
     int have_coeff;
     int Nu, l0;                // unknown planes l0 .. l0 + Nu - 1
-    hs_plan_s *T;              // FP64 transform plan over 2 Nu planes (work: d_w64, d_dscr)
+    int side[2];               // HS_SIDE_* of the x and y axes
+    int nx, ny, i0x, i0y;      // unknown grid of a plane; node index of its first point
+    hs_plan_s *T;              // FP64 transform plan [2 Nu][ny][nx] (work: d_w64, d_dscr)
+    double *d_cos;             // [nx] then [ny]: cos(theta) of each axis' modes
+    double2 *d_dct[2];         // Neumann axis: M roots then M + 1 half-angle pairs
     double2 *d_rows;           // [Nu][3][4] complex coefficients of the unknown rows
     int rows_ok;
     size_t bytes;
@@ -140,32 +150,79 @@ hs_status build_rows(hs_zplan_s *Z) {
     return HS_OK;
 }
 
-// (Re)creates the transform plan and row table for the current faces.
+// cos(pi a / b) with the argument reduced exactly (integers) to [0, pi/2] first.
+double cos_pi_frac(long a, long b) {
+    a %= 2 * b;
+    if (a < 0) a += 2 * b;
+    if (a > b) a = 2 * b - a;           // cos is even about pi
+    if (2 * a > b) return -cos(M_PI * (double)(b - a) / (double)b);
+    return cos(M_PI * (double)a / (double)b);
+}
+double sin_pi_frac(long a, long b) { return cos_pi_frac(2 * a - b, 2 * b); }
+
+// Mode cosines of both axes and the DCT tables of Neumann axes.
+hs_status side_tables(hs_zplan_s *Z) {
+    std::vector<double> c;
+    const int N[2] = {Z->Nx, Z->Ny};
+    for (int a = 0; a < 2; ++a) {
+        if (Z->side[a] == HS_SIDE_NEUMANN)
+            for (int p = 0; p <= N[a] + 1; ++p) c.push_back(cos_pi_frac(p, N[a] + 1));
+        else
+            for (int p = 1; p <= N[a]; ++p) c.push_back(cos_pi_frac(p, N[a] + 1));
+    }
+    if (Z->d_cos) cudaFree(Z->d_cos);
+    Z->d_cos = nullptr;
+    ZCK(Z, cudaMalloc(&Z->d_cos, c.size() * sizeof(double)));
+    ZCK(Z, cudaMemcpy(Z->d_cos, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice));
+    for (int a = 0; a < 2; ++a) {
+        if (Z->d_dct[a]) cudaFree(Z->d_dct[a]);
+        Z->d_dct[a] = nullptr;
+        if (Z->side[a] != HS_SIDE_NEUMANN) continue;
+        const int M = N[a] + 1;
+        std::vector<double2> t(2 * (size_t)M + 1);
+        for (int k = 0; k < M; ++k)   // exp(-2 pi i k / M)
+            t[k] = make_double2(cos_pi_frac(2L * k, M), -sin_pi_frac(2L * k, M));
+        for (int k = 0; k <= M; ++k) t[M + k] = make_double2(cos_pi_frac(k, M), sin_pi_frac(k, M));
+        ZCK(Z, cudaMalloc(&Z->d_dct[a], t.size() * sizeof(double2)));
+        ZCK(Z, cudaMemcpy(Z->d_dct[a], t.data(), t.size() * sizeof(double2),
+                          cudaMemcpyHostToDevice));
+    }
+    return HS_OK;
+}
+
+// (Re)creates the transform plan, row table and side tables for the current
+// faces and side axes.
 hs_status layout(hs_zplan_s *Z) {
     const int l0 = Z->kind[0] == HS_ZFACE_ROBIN ? 0 : 1;
     const int l1 = Z->kind[1] == HS_ZFACE_ROBIN ? Z->Nz + 1 : Z->Nz;
     const int Nu = l1 - l0 + 1;
-    if (Z->T && Nu == Z->Nu) {
-        Z->l0 = l0;
-        return HS_OK;
-    }
-    if (Z->T) hs_destroy(Z->T);
-    Z->T = nullptr;
-    if (Z->d_rows) cudaFree(Z->d_rows);
-    Z->d_rows = nullptr;
-    Z->Nu = Nu;
+    const int nx = Z->side[0] == HS_SIDE_NEUMANN ? Z->Nx + 2 : Z->Nx;
+    const int ny = Z->side[1] == HS_SIDE_NEUMANN ? Z->Ny + 2 : Z->Ny;
+    Z->i0x = Z->side[0] == HS_SIDE_NEUMANN ? 0 : 1;
+    Z->i0y = Z->side[1] == HS_SIDE_NEUMANN ? 0 : 1;
     Z->l0 = l0;
-    Z->rows_ok = 0;
-    hs_plan_t T = nullptr;
-    const hs_status st = hs_plan_ex(&T, Z->Nx, Z->Ny, 2 * Nu, Z->Lx, Z->Ly, 1.0, 2,
-                                    HS_HELMHOLTZ, HS_BC_DIRICHLET, HS_FP64, 1, 1);
-    if (st != HS_OK) {
-        zerr(Z, "transform plan: status %d", st);
-        return st;
+    if (!(Z->T && Nu == Z->Nu && nx == Z->nx && ny == Z->ny)) {
+        if (Z->T) hs_destroy(Z->T);
+        Z->T = nullptr;
+        if (Z->d_rows) cudaFree(Z->d_rows);
+        Z->d_rows = nullptr;
+        Z->Nu = Nu;
+        Z->nx = nx;
+        Z->ny = ny;
+        Z->rows_ok = 0;
+        // the sine transforms of Dirichlet axes, and the work arrays; a Neumann
+        // axis' own table in this plan is never used
+        hs_plan_t T = nullptr;
+        const hs_status st = hs_plan_ex(&T, nx, ny, 2 * Nu, Z->Lx, Z->Ly, 1.0, 2, HS_HELMHOLTZ,
+                                        HS_BC_DIRICHLET, HS_FP64, 1, 1);
+        if (st != HS_OK) {
+            zerr(Z, "transform plan: status %d", st);
+            return st;
+        }
+        Z->T = T;
+        ZCK(Z, cudaMalloc(&Z->d_rows, (size_t)Nu * 12 * sizeof(double2)));
     }
-    Z->T = T;
-    ZCK(Z, cudaMalloc(&Z->d_rows, (size_t)Nu * 12 * sizeof(double2)));
-    return HS_OK;
+    return side_tables(Z);
 }
 
 bool device_ptr(const void *p) {
@@ -179,18 +236,27 @@ bool device_ptr(const void *p) {
 
 struct ZRhsArgs {
     int Nx, Ny, Nz, Nu, l0, order;
+    int nx, ny, i0x, i0y;   // unknown grid of a plane and its first node
+    int neu_x, neu_y;       // Neumann side axes (even reflection)
     int kind_lo, kind_hi;
     double hz;
     double2 ga_lo, ga_hi;   // 2 h_z / alpha of each face (Robin)
     const double *f;        // [2][Nz+2][Ny+2][Nx+2]
-    const double *g_lo, *g_hi;   // [2][Ny][Nx] or NULL
+    const double *g_lo, *g_hi;   // [2][ny][nx] or NULL
     const double2 *rows;    // [Nu][3][4]
-    double *W;              // [2][Nu][Ny][Nx]
+    double *W;              // [2][Nu][ny][nx]
 };
 
-__device__ inline double2 face_val(const double *g, int Ny, int Nx, int j, int i) {
-    if (!g || j < 0 || j >= Ny || i < 0 || i >= Nx) return make_double2(0.0, 0.0);
-    const size_t k = (size_t)j * Nx + i, n = (size_t)Ny * Nx;
+// Index one node beyond [0, n - 1] of a Neumann axis: the even reflection.
+__device__ inline int reflect(int i, int n) { return i < 0 ? -i : (i >= n ? 2 * (n - 1) - i : i); }
+
+// Face data on the unknown grid: beyond a Dirichlet axis 0, beyond a Neumann one reflected.
+__device__ inline double2 face_val(const ZRhsArgs &a, const double *g, int j, int i) {
+    if (!g) return make_double2(0.0, 0.0);
+    if (a.neu_y) j = reflect(j, a.ny);
+    if (a.neu_x) i = reflect(i, a.nx);
+    if (j < 0 || j >= a.ny || i < 0 || i >= a.nx) return make_double2(0.0, 0.0);
+    const size_t k = (size_t)j * a.nx + i, n = (size_t)a.ny * a.nx;
     return make_double2(g[k], g[n + k]);
 }
 
@@ -198,31 +264,38 @@ __device__ inline double2 face_val(const double *g, int Ny, int Nx, int j, int i
 // minus the known Dirichlet plane next to it, or the Robin row's h_z^2 f plus
 // its face-data term.
 __global__ void zrhs_kernel(ZRhsArgs a) {
-    const size_t plane = (size_t)a.Ny * a.Nx, n = plane * a.Nu;
+    const size_t plane = (size_t)a.ny * a.nx, n = plane * a.Nu;
     const size_t sy = (size_t)(a.Nx + 2), sz = sy * (a.Ny + 2), nodes = sz * (a.Nz + 2);
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
          t += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(t / plane);
         const int rem = (int)(t - (size_t)r * plane);
-        const int j = rem / a.Nx, i = rem - j * a.Nx;
+        const int j = rem / a.nx, i = rem - j * a.nx;
         const int l = a.l0 + r;
-        const size_t c = (size_t)l * sz + (size_t)(j + 1) * sy + (i + 1);
+        const int jj = j + a.i0y, ii = i + a.i0x;   // node indices
+        // neighbours on the node grid, reflected beyond a Neumann side's faces
+        const int im = reflect(ii - 1, a.Nx + 2), ip = reflect(ii + 1, a.Nx + 2);
+        const int jm = reflect(jj - 1, a.Ny + 2), jp = reflect(jj + 1, a.Ny + 2);
+        const size_t rowc = (size_t)l * sz + (size_t)jj * sy;
+        const size_t c = rowc + ii;
         const double hz2 = a.hz * a.hz;
         double2 F;
         for (int comp = 0; comp < 2; ++comp) {
             const double *f = a.f + comp * nodes;
             double v = f[c];
             if (a.order == 4 && l >= 1 && l <= a.Nz) {
-                const double D = (f[c - 1] + f[c + 1] + f[c - sy] + f[c + sy] + f[c - sz] +
-                                  f[c + sz]) - 6.0 * f[c];
+                const size_t pl = (size_t)l * sz;
+                const double D = (f[rowc + im] + f[rowc + ip] + f[pl + (size_t)jm * sy + ii] +
+                                  f[pl + (size_t)jp * sy + ii] + f[c - sz] + f[c + sz]) -
+                                 6.0 * f[c];
                 v += D / 12.0;
             }
             if (comp == 0) F.x = hz2 * v; else F.y = hz2 * v;
         }
         if (l == 0) {
-            F = cadd(F, cmul(a.ga_lo, face_val(a.g_lo, a.Ny, a.Nx, j, i)));
+            F = cadd(F, cmul(a.ga_lo, face_val(a, a.g_lo, j, i)));
         } else if (l == a.Nz + 1) {
-            F = csub(F, cmul(a.ga_hi, face_val(a.g_hi, a.Ny, a.Nx, j, i)));
+            F = csub(F, cmul(a.ga_hi, face_val(a, a.g_hi, j, i)));
         } else {
             // a Dirichlet face's plane next to this row: its values leave through the stencil
             const bool lo = l == 1 && a.kind_lo == HS_ZFACE_DIRICHLET && a.g_lo;
@@ -234,7 +307,7 @@ __global__ void zrhs_kernel(ZRhsArgs a) {
                 for (int dj = -1; dj <= 1; ++dj)
                     for (int di = -1; di <= 1; ++di) {
                         const int m = (di != 0 && dj != 0) ? ZA : (di != 0 ? ZB : (dj != 0 ? ZC : ZD));
-                        F = csub(F, cmul(w[m], face_val(g, a.Ny, a.Nx, j + dj, i + di)));
+                        F = csub(F, cmul(w[m], face_val(a, g, j + dj, i + di)));
                     }
             }
         }
@@ -296,7 +369,7 @@ hs_status hs_zplan(hs_zplan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly
     *out = nullptr;
     if (Nx < 1 || Ny < 1 || Nz < 1 || !(Lx > 0) || !(Ly > 0) || !(Lz > 0)) return HS_ERR_INVALID_ARG;
     if (order != 2 && order != 4) return HS_ERR_INVALID_ARG;
-    if (2.0 * (Nz + 2) * (double)Nx * Ny > 4.0e9) return HS_ERR_UNSUPPORTED;
+    if (2.0 * (Nz + 2) * (double)(Nx + 2) * (Ny + 2) > 4.0e9) return HS_ERR_UNSUPPORTED;
     hs_zplan_s *Z = new (std::nothrow) hs_zplan_s();
     if (!Z) return HS_ERR_OOM;
     Z->Nx = Nx; Z->Ny = Ny; Z->Nz = Nz; Z->order = order;
@@ -305,6 +378,7 @@ hs_status hs_zplan(hs_zplan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly
     Z->kind[0] = Z->kind[1] = HS_ZFACE_DIRICHLET;
     Z->alpha[0] = Z->alpha[1] = make_double2(1.0, 0.0);
     Z->beta[0] = Z->beta[1] = make_double2(0.0, 0.0);
+    Z->side[0] = Z->side[1] = HS_SIDE_DIRICHLET;
     const hs_status st = layout(Z);
     if (st != HS_OK) {
         hs_zplan_destroy(Z);
@@ -356,6 +430,20 @@ hs_status hs_zplan_set_faces(hs_zplan_t Z, int lo_kind, const double *alpha_lo,
     return Z->have_coeff ? build_rows(Z) : HS_OK;
 }
 
+hs_status hs_zplan_set_sides(hs_zplan_t Z, int x_kind, int y_kind) {
+    if (!Z) return HS_ERR_INVALID_ARG;
+    const int k[2] = {x_kind, y_kind}, N[2] = {Z->Nx, Z->Ny};
+    for (int a = 0; a < 2; ++a) {
+        if (k[a] != HS_SIDE_DIRICHLET && k[a] != HS_SIDE_NEUMANN) return HS_ERR_INVALID_ARG;
+        if (k[a] == HS_SIDE_NEUMANN && !hs_dst_fast_size(N[a] + 1)) return HS_ERR_UNSUPPORTED;
+    }
+    Z->side[0] = x_kind;
+    Z->side[1] = y_kind;
+    const hs_status st = layout(Z);
+    if (st != HS_OK) return st;
+    return Z->have_coeff ? build_rows(Z) : HS_OK;
+}
+
 hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const double *g_hi,
                     double *u, void *stream) {
     if (!Z || !f || !u) return HS_ERR_INVALID_ARG;
@@ -366,11 +454,14 @@ hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const dou
     Z->last_error[0] = 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     hs_plan_s *T = Z->T;
-    const size_t plane = (size_t)Z->Nx * Z->Ny;
+    const size_t plane = (size_t)Z->nx * Z->ny;
     const size_t nu = plane * Z->Nu;
     double *W = T->d_w64;
     ZRhsArgs a;
     a.Nx = Z->Nx; a.Ny = Z->Ny; a.Nz = Z->Nz; a.Nu = Z->Nu; a.l0 = Z->l0; a.order = Z->order;
+    a.nx = Z->nx; a.ny = Z->ny; a.i0x = Z->i0x; a.i0y = Z->i0y;
+    a.neu_x = Z->side[0] == HS_SIDE_NEUMANN;
+    a.neu_y = Z->side[1] == HS_SIDE_NEUMANN;
     a.kind_lo = Z->kind[0]; a.kind_hi = Z->kind[1];
     a.hz = Z->hz;
     a.ga_lo = cscale(2.0 * Z->hz, cdiv_host(make_double2(1.0, 0.0), Z->alpha[0]));
@@ -379,22 +470,28 @@ hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const dou
     const unsigned blocks = (unsigned)((nu + 255) / 256 < 152 * 16 ? (nu + 255) / 256 : 152 * 16);
     zrhs_kernel<<<blocks, 256, 0, s>>>(a);
     ZCK(Z, cudaGetLastError());
+    // one transform pass along an axis: the cosine kernel on a Neumann axis, else the
+    // plan's sine transform; inverse passes carry 2 / (N + 1) for either
+    auto pass = [&](int axis, double scale) -> hs_status {
+        if (Z->side[axis] == HS_SIDE_NEUMANN) {
+            const int M = (axis == HS_AXIS_X ? Z->Nx : Z->Ny) + 1;
+            const double2 *t = Z->d_dct[axis];
+            return hs_launch_dct(axis, M, W, W, t, t + M, (long)Z->ny * 2 * Z->Nu, Z->nx,
+                                 2 * Z->Nu, scale, s);
+        }
+        return hs_launch_dst(T, axis, HS_T_F64, HS_T_F64, W, HS_T_F64, W, HS_MODE_WRITE, scale, s);
+    };
     hs_status st;
-    if ((st = hs_launch_dst(T, HS_AXIS_X, HS_T_F64, HS_T_F64, W, HS_T_F64, W, HS_MODE_WRITE, 1.0,
-                            s)) != HS_OK ||
-        (st = hs_launch_dst(T, HS_AXIS_Y, HS_T_F64, HS_T_F64, W, HS_T_F64, W, HS_MODE_WRITE, 1.0,
-                            s)) != HS_OK) {
+    if ((st = pass(HS_AXIS_X, 1.0)) != HS_OK || (st = pass(HS_AXIS_Y, 1.0)) != HS_OK) {
         zerr(Z, "forward transform: status %d", st);
         return st;
     }
     zthomas_kernel<<<(unsigned)((plane + 127) / 128), 128, 0, s>>>(W, T->d_dscr, Z->d_rows,
-                                                                 T->d_cx, T->d_cy, Z->Nx,
-                                                                 Z->Ny, Z->Nu);
+                                                                 Z->d_cos, Z->d_cos + Z->nx,
+                                                                 Z->nx, Z->ny, Z->Nu);
     ZCK(Z, cudaGetLastError());
-    if ((st = hs_launch_dst(T, HS_AXIS_Y, HS_T_F64, HS_T_F64, W, HS_T_F64, W, HS_MODE_WRITE,
-                            2.0 / (Z->Ny + 1), s)) != HS_OK ||
-        (st = hs_launch_dst(T, HS_AXIS_X, HS_T_F64, HS_T_F64, W, HS_T_F64, W, HS_MODE_WRITE,
-                            2.0 / (Z->Nx + 1), s)) != HS_OK) {
+    if ((st = pass(HS_AXIS_Y, 2.0 / (Z->Ny + 1))) != HS_OK ||
+        (st = pass(HS_AXIS_X, 2.0 / (Z->Nx + 1))) != HS_OK) {
         zerr(Z, "inverse transform: status %d", st);
         return st;
     }
@@ -420,7 +517,11 @@ hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const dou
 
 size_t hs_zplan_workspace_bytes(hs_zplan_t Z) {
     if (!Z) return 0;
-    return hs_workspace_bytes(Z->T) + (Z->d_rows ? (size_t)Z->Nu * 12 * sizeof(double2) : 0);
+    size_t b = hs_workspace_bytes(Z->T) + (Z->d_rows ? (size_t)Z->Nu * 12 * sizeof(double2) : 0);
+    b += (size_t)(Z->nx + Z->ny) * sizeof(double);
+    if (Z->d_dct[0]) b += (2 * (size_t)Z->Nx + 3) * sizeof(double2);
+    if (Z->d_dct[1]) b += (2 * (size_t)Z->Ny + 3) * sizeof(double2);
+    return b;
 }
 
 const char *hs_zplan_last_error(hs_zplan_t Z) {
@@ -433,6 +534,9 @@ void hs_zplan_destroy(hs_zplan_t Z) {
     if (!Z) return;
     if (Z->T) hs_destroy(Z->T);
     if (Z->d_rows) cudaFree(Z->d_rows);
+    if (Z->d_cos) cudaFree(Z->d_cos);
+    for (int a = 0; a < 2; ++a)
+        if (Z->d_dct[a]) cudaFree(Z->d_dct[a]);
     delete Z;
 }
 

@@ -2,7 +2,8 @@
 
 Parity bar: the FP64 path's 1e-12 (max relative error over the whole complex field),
 on ragged sizes (runtime-sized and compiled transform lengths), every face
-combination, orders 2 and 4, absent face data, Nz = 1, and one 255^3 case.
+combination, orders 2 and 4, absent face data, Nz = 1, and one 255^3 case; and
+with Neumann side axes (cosine transform), every side combination.
 """
 import numpy as np
 import pytest
@@ -38,14 +39,17 @@ def _planar(torch, a):
     return torch.from_numpy(np.ascontiguousarray(np.stack([a.real, a.imag]))).cuda()
 
 
-def _gpu(shape, L, order, K, zf, f, g_lo, g_hi):
+def _gpu(shape, L, order, K, zf, f, g_lo, g_hi, sides=(0, 0)):
     torch = _torch()
     Nx, Ny, Nz = shape
     s = H.ZSolver(Nx, Ny, Nz, *L, order)
     try:
         s.set_coeff(K)
         s.set_faces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
-        u = torch.full((2, Nz + 2, Ny, Nx), np.nan, dtype=torch.float64, device="cuda")
+        s.set_sides(*sides)
+        nx = Nx + 2 if sides[0] == H.HS_SIDE_NEUMANN else Nx
+        ny = Ny + 2 if sides[1] == H.HS_SIDE_NEUMANN else Ny
+        u = torch.full((2, Nz + 2, ny, nx), np.nan, dtype=torch.float64, device="cuda")
         s.solve(_planar(torch, f), u, None if g_lo is None else _planar(torch, g_lo),
                 None if g_hi is None else _planar(torch, g_hi))
         torch.cuda.synchronize()
@@ -141,5 +145,69 @@ def test_errors():
         s.solve(f, u)
         torch.cuda.synchronize()
         assert torch.count_nonzero(u).item() == 0
+    finally:
+        s.close()
+
+
+NEU, DIRS = CX.SIDE_NEUMANN, CX.SIDE_DIRICHLET
+
+
+def _neumann_case(shape, L, sides, seed):
+    Nx, Ny, Nz = shape
+    rs = np.random.RandomState(seed)
+    z = np.arange(Nz + 2) / (Nz + 1)
+    K = 40.0 * (1.0 + 0.5 * z) * (1.0 + 0.2j * (1.0 + np.cos(2.0 * z)))
+    f = rs.uniform(-1, 1, (Nz + 2, Ny + 2, Nx + 2)) + 1j * rs.uniform(-1, 1, (Nz + 2, Ny + 2, Nx + 2))
+    nx = Nx + 2 if sides[0] == NEU else Nx
+    ny = Ny + 2 if sides[1] == NEU else Ny
+    g_lo = rs.uniform(-1, 1, (ny, nx)) + 1j * rs.uniform(-1, 1, (ny, nx))
+    g_hi = rs.uniform(-1, 1, (ny, nx)) + 1j * rs.uniform(-1, 1, (ny, nx))
+    return O.grid_steps(shape, L), K, f, g_lo, g_hi
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("sides", [(NEU, DIRS), (DIRS, NEU), (NEU, NEU)])
+@pytest.mark.parametrize("faces", [(R, R), (D, D), (R, D)])
+@pytest.mark.parametrize("shape", [(31, 63, 9), (63, 31, 4)])
+def test_neumann_sides_match_oracle(order, sides, faces, shape):
+    L = (1.0, 0.8, 1.1)
+    h, K, f, g_lo, g_hi = _neumann_case(shape, L, sides, sum(shape) + 3 * sides[0] + sides[1])
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    ref, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi, sides)
+    got = _gpu(shape, L, order, K, zf, f, g_lo, g_hi, sides)
+    assert O.max_rel_diff(got, ref) <= TOL
+
+
+def test_neumann_beside_runtime_sized_sine_axis():
+    """A Neumann x-axis (compiled cosine transform, 127 + 1 points) beside a Dirichlet
+    y-axis whose length has no compiled transform (runtime-sized sine transform)."""
+    shape, L = (127, 20, 11), (1.0, 1.0, 1.0)
+    sides = (NEU, DIRS)
+    h, K, f, g_lo, g_hi = _neumann_case(shape, L, sides, 77)
+    zf = CX.ZFaces(R, 1.0 + 0.5j, 2.0 - 1.0j, D)
+    ref, _ = CX.solve(4, h, K, zf, f, g_lo, g_hi, sides)
+    got = _gpu(shape, L, 4, K, zf, f, g_lo, g_hi, sides)
+    assert O.max_rel_diff(got, ref) <= TOL
+
+
+def test_neumann_255():
+    shape, L = (255, 255, 127), (1.0, 1.0, 0.5)
+    sides = (NEU, NEU)
+    h, K, f, g_lo, g_hi = _neumann_case(shape, L, sides, 88)
+    zf = CX.ZFaces(R, 1.0 + 0.5j, 3.0 - 1.0j, R, 1.0 + 0.5j, 3.0 - 1.0j)
+    ref, _ = CX.solve(4, h, K, zf, f, g_lo, g_hi, sides)
+    got = _gpu(shape, L, 4, K, zf, f, g_lo, g_hi, sides)
+    assert O.max_rel_diff(got, ref) <= TOL
+
+
+def test_neumann_unsupported_length():
+    s = H.ZSolver(30, 31, 5, 1.0, 1.0, 1.0, 4)
+    try:
+        with pytest.raises(H.HsError) as e:
+            s.set_sides(H.HS_SIDE_NEUMANN, H.HS_SIDE_DIRICHLET)   # 31 points: no compiled FFT
+        assert e.value.status == H.HS_ERR_UNSUPPORTED
+        s.set_sides(H.HS_SIDE_DIRICHLET, H.HS_SIDE_NEUMANN)       # 32 points
+        with pytest.raises(H.HsError):
+            s.set_sides(2, 0)
     finally:
         s.close()
