@@ -213,6 +213,10 @@ WORKLOADS = {
              "cube, 255^3 interior, first-order absorbing z-faces u_z +- i k u = 0 (Robin, "
              "second-order closure, both face planes unknown), zero side faces, "
              "f = U[-1,1] + i U[-1,1] (seed 12); FP64 path, complex z-solves"),
+    "zneumann255_o4": dict(
+        steps=5,
+        desc="zrobin255_o4's complex k(z) and absorbing z-faces with u_n = 0 on the four side "
+             "faces (cosine transforms over the 257 nodes of each side axis; seed 13)"),
     "cd511x8": dict(
         steps=10,
         desc="4th-order compact convection-diffusion Lap(u)+b(z)u_z=f, 511^3 interior, "
@@ -327,8 +331,9 @@ def run_reference(args):
                        f"{Np}^3 instance of the same recipe per step (numpy FP64 BiCGStab, "
                        "the oracle's O(N^4) solve as preconditioner)", world)
         return
-    elif name == "zrobin255_o4":
-        wz = W.workload_zrobin(255)
+    elif name in ("zrobin255_o4", "zneumann255_o4"):
+        wz = W.workload_zneumann(255) if name == "zneumann255_o4" else W.workload_zrobin(255)
+        nu = 257 * (257 if wz["sides"][0] else 255) * (257 if wz["sides"][1] else 255)
         steps = args.steps if args.steps is not None else 2
         for _ in range(args.warmup):
             zrobin_run_oracle(wz)
@@ -336,9 +341,9 @@ def run_reference(args):
         for _ in range(steps):
             zrobin_run_oracle(wz)
         dt = (time.perf_counter() - t0) / steps
-        emit_reference(args, name, 255 ** 3 / dt / 1e9, dt, steps,
-                       "full 255^3 complex solve per step (numpy FP64, O(N^4) sine sums, "
-                       "textbook complex Thomas)", world)
+        emit_reference(args, name, nu / dt / 1e9, dt, steps,
+                       "full 255^3 complex solve per step (numpy FP64, O(N^4) sine / cosine "
+                       "sums, textbook complex Thomas)", world)
         return
     elif name == "batch64":
         sp = W.workload_batch_specs(nprob=64, seed=3)[0]
@@ -461,19 +466,24 @@ def zrobin_run_oracle(w):
     N = w["N"]
     zf = CX.ZFaces(CX.ROBIN, w["alpha_lo"], w["beta_lo"], CX.ROBIN, w["alpha_hi"], w["beta_hi"])
     h = O.grid_steps((N, N, N), w["L"])
-    return CX.solve(w["order"], h, w["K"], zf, w["f"])[0]
+    return CX.solve(w["order"], h, w["K"], zf, w["f"], sides=w["sides"])[0]
 
 
 def bench_zrobin(args, torch, H, W, rank, world, barrier, max_over_ranks):
-    """Complex k(z) with absorbing (Robin) z-faces: one hs_zsolve per step (FP64)."""
-    w = W.workload_zrobin(255)
+    """Complex k(z) with absorbing (Robin) z-faces (and, for zneumann255_o4, u_n = 0 on
+    the side faces): one hs_zsolve per step (FP64)."""
+    name = args.workload
+    w = W.workload_zneumann(255) if name == "zneumann255_o4" else W.workload_zrobin(255)
     N = w["N"]
     s = H.ZSolver(N, N, N, *w["L"], w["order"])
     s.set_coeff(w["K"])
     s.set_faces(H.HS_ZFACE_ROBIN, w["alpha_lo"], w["beta_lo"], H.HS_ZFACE_ROBIN,
                 w["alpha_hi"], w["beta_hi"])
+    s.set_sides(*w["sides"])
+    nx = N + 2 if w["sides"][0] else N
+    ny = N + 2 if w["sides"][1] else N
     f = torch.from_numpy(np.ascontiguousarray(np.stack([w["f"].real, w["f"].imag]))).cuda()
-    u = torch.empty((2, N + 2, N, N), dtype=torch.float64, device="cuda")
+    u = torch.empty((2, N + 2, ny, nx), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -492,7 +502,7 @@ def bench_zrobin(args, torch, H, W, rank, world, barrier, max_over_ranks):
     torch.cuda.synchronize()
     clocks = clk.stop()
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev)) / args.steps
-    acc, cpu = {"compared_against": "oracle (complex FP64, O(N^4) sine sums)"}, None
+    acc, cpu = {"compared_against": "oracle (complex FP64, O(N^4) sine / cosine sums)"}, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
         ref = zrobin_run_oracle(w)
@@ -500,18 +510,20 @@ def bench_zrobin(args, torch, H, W, rank, world, barrier, max_over_ranks):
         got = u.cpu().numpy()
         got = got[0] + 1j * got[1]
         acc["max_rel_error"] = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
-        cpu = {"value": N ** 3 / dt / 1e9, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+        cpu = {"value": (N + 2) * ny * nx / dt / 1e9, "unit": UNIT, "cores": cpu_cores(),
+               "kind": "oracle",
                "sample": f"one full {N}^3 complex oracle solve (numpy FP64): {dt:.2f} s"}
-    value = world * N ** 3 / (ms * 1e-3) / 1e9
+    value = world * (N + 2) * ny * nx / (ms * 1e-3) / 1e9   # unknown (complex) points
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128 (FP64 re, im)", "data": "synthetic",
-            "config": {"workload": f"zrobin255_o4: {WORKLOADS['zrobin255_o4']['desc']}",
+            "config": {"workload": f"{name}: {WORKLOADS[name]['desc']}",
                        "global_batch": world, "parallelism": f"replicas x{world}",
                        "l2": "256 MB buffer written between timed steps",
-                       "unknowns": "complex, planes l = 0..N+1 (Robin faces)"},
+                       "unknowns": f"complex, planes l = 0..N+1 (Robin faces), {ny} x {nx} "
+                                   "per plane"},
             "accuracy": acc, "cpu_baseline": cpu, "e2e": None, "roofline": None,
             "clocks": clocks,
             # right-hand side, 4 transform passes, complex z-solve
@@ -723,7 +735,7 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
-    if args.workload == "zrobin255_o4":
+    if args.workload in ("zrobin255_o4", "zneumann255_o4"):
         bench_zrobin(args, torch, H, W, rank, world, barrier,
                      lambda x: reduce_max(x, dist, "cuda"))
         if dist is not None:

@@ -429,4 +429,13 @@ def workload_zrobin(N: int = 255, seed: int = 12) -> dict:
     f = np.zeros((N + 2, N + 2, N + 2), dtype=np.complex128)
     f[1:-1, 1:-1, 1:-1] = (rs.uniform(-1, 1, (N, N, N)) + 1j * rs.uniform(-1, 1, (N, N, N)))
     return dict(N=N, L=(1.0, 1.0, 1.0), order=4, K=k * k,
-                alpha_lo=1.0, beta_lo=1j * k[0], alpha_hi=1.0, beta_hi=-1j * k[-1], f=f)
+                alpha_lo=1.0, beta_lo=1j * k[0], alpha_hi=1.0, beta_hi=-1j * k[-1], f=f,
+                sides=(0, 0))
+
+
+def workload_zneumann(N: int = 255, seed: int = 13) -> dict:
+    """workload_zrobin's medium and z-faces with u_n = 0 on the four side faces
+    (the side axes' boundary nodes are unknowns; side kinds (1, 1) = Neumann)."""
+    w = workload_zrobin(N, seed)
+    w["sides"] = (1, 1)
+    return w
