@@ -146,6 +146,16 @@ hs_status hs_set_coeff(hs_plan_t plan, const double *c0, const double *c1, const
                        int cd_variant);
 
 /*
+ * hs_set_coeff_fn -- hs_set_coeff from a function: c0, c1, c2 are sampled as
+ * fn(z_l, 0, user), fn(z_l, 1, user), fn(z_l, 2, user) at z_l = l hz,
+ * l = 0..Nz+1 (the coefficient and its first two z-derivatives: k^2 for
+ * Helmholtz, gamma for convection-diffusion), on the calling thread, before
+ * the call returns.  Same results and errors as hs_set_coeff.
+ */
+typedef double (*hs_coeff_fn)(double z, int deriv, void *user);
+hs_status hs_set_coeff_fn(hs_plan_t plan, hs_coeff_fn fn, void *user, int cd_variant);
+
+/*
  * hs_set_refinement -- number of refinement sweeps of the HS_MIXED path
  * after its first solve (default 2; 0..HS_INFO_MAX_ITERS-1).  Each sweep
  * computes the residual r = F - A U (precision: hs_set_residual_precision)

@@ -60,7 +60,7 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_precond_create", "hs_precond_apply", "hs_precond_solve", "hs_precond_destroy",
             "hs_batch_workspace_bytes", "hs_batch_destroy",
             "hs_zplan", "hs_zplan_set_coeff", "hs_zplan_set_faces", "hs_zplan_set_sides",
-            "hs_zsolve",
+            "hs_zsolve", "hs_set_coeff_fn",
             "hs_zplan_workspace_bytes", "hs_zplan_last_error", "hs_zplan_destroy")
 HS_STATIC_MAX_NZ = 8192
 
@@ -98,6 +98,17 @@ class hs_info(ctypes.Structure):
                 "stage_ms": dict(zip(STAGES, list(self.stage_ms)))}
 
 
+# double (*)(double z, int deriv, void *user)
+HS_COEFF_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p)
+
+
+def hs_set_coeff_fn(plan, fn, cd_variant=1):
+    """hs_set_coeff from a Python function fn(z, deriv) -> float (deriv 0, 1, 2)."""
+    cb = HS_COEFF_FN(lambda z, d, _u: float(fn(z, d)))
+    return _check(load().hs_set_coeff_fn(plan, cb, None, int(cd_variant)), "hs_set_coeff_fn",
+                  plan)
+
+
 class HsError(RuntimeError):
     def __init__(self, status, where, detail=""):
         self.status = status
@@ -122,6 +133,8 @@ def load(path: Optional[str] = None):
     lib.hs_plan.restype = ci
     lib.hs_set_coeff.argtypes = [vp, vp, vp, vp, ci]
     lib.hs_set_coeff.restype = ci
+    lib.hs_set_coeff_fn.argtypes = [vp, HS_COEFF_FN, vp, ci]
+    lib.hs_set_coeff_fn.restype = ci
     lib.hs_set_refinement.argtypes = [vp, ci]
     lib.hs_set_refinement.restype = ci
     lib.hs_set_refinement_tol.argtypes = [vp, cd]

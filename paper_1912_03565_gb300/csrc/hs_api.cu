@@ -705,6 +705,19 @@ hs_status hs_plan_ex(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double L
     return HS_OK;
 }
 
+hs_status hs_set_coeff_fn(hs_plan_t P, hs_coeff_fn fn, void *user, int cd_variant) {
+    if (!P || !fn) return HS_ERR_INVALID_ARG;
+    const int n = P->Nz + 2;
+    std::vector<double> c0(n), c1(n), c2(n);
+    for (int l = 0; l < n; ++l) {
+        const double z = l * P->hz;
+        c0[l] = fn(z, 0, user);
+        c1[l] = fn(z, 1, user);
+        c2[l] = fn(z, 2, user);
+    }
+    return hs_set_coeff(P, c0.data(), c1.data(), c2.data(), cd_variant);
+}
+
 hs_status hs_set_coeff(hs_plan_t P, const double *c0, const double *c1, const double *c2,
                        int cd_variant) {
     if (!P || !c0) return HS_ERR_INVALID_ARG;

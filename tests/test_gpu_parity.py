@@ -630,3 +630,39 @@ def test_residual_precision_modes():
         finally:
             s.close()
     assert torch.equal(outs[0], outs[1])
+
+
+def test_coefficient_from_function():
+    """hs_set_coeff_fn samples k^2 and its z-derivatives at z_l = l h_z: the same plan as
+    hs_set_coeff with those arrays, so the same solution bit for bit."""
+    torch = _torch()
+    Nx, Ny, Nz = 31, 27, 23
+    L = (1.0, 1.0, 1.0)
+    hz = L[2] / (Nz + 1)
+    z = np.arange(Nz + 2) * hz
+    k2 = lambda t, d: [(20.0 * (1 + 0.5 * t * t)) ** 2, 800.0 * t * (1 + 0.5 * t * t),
+                       800.0 * (1 + 1.5 * t * t)][d]
+    f = torch.from_numpy(np.random.RandomState(4).uniform(-1, 1, (Nz + 2, Ny + 2, Nx + 2))).cuda()
+    outs = []
+    for via_fn in (False, True):
+        s = H.Solver(Nx, Ny, Nz, *L, 6, H.HS_HELMHOLTZ, H.HS_FP64)
+        try:
+            if via_fn:
+                H.hs_set_coeff_fn(s.plan, k2)
+            else:
+                s.set_coeff(np.array([k2(t, 0) for t in z]), np.array([k2(t, 1) for t in z]),
+                            np.array([k2(t, 2) for t in z]))
+            u = torch.zeros((Nz, Ny, Nx), dtype=torch.float64, device="cuda")
+            s.solve(f, u, H.HS_F64, H.HS_RHS_NODAL)
+            torch.cuda.synchronize()
+            outs.append(u.cpu())
+        finally:
+            s.close()
+    assert torch.equal(outs[0], outs[1])
+    s = H.Solver(8, 8, 8, 1.0, 1.0, 1.0, 4, H.HS_HELMHOLTZ, H.HS_FP64)
+    try:
+        with pytest.raises(H.HsError) as e:
+            H.hs_set_coeff_fn(s.plan, lambda t, d: float("nan"))
+        assert e.value.status == H.HS_ERR_NONFINITE
+    finally:
+        s.close()
