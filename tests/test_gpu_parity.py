@@ -636,7 +636,7 @@ def test_coefficient_from_function():
     """hs_set_coeff_fn samples k^2 and its z-derivatives at z_l = l h_z: the same plan as
     hs_set_coeff with those arrays, so the same solution bit for bit."""
     torch = _torch()
-    Nx, Ny, Nz = 31, 27, 23
+    Nx, Ny, Nz = 31, 31, 31     # order 6 needs one grid step on all axes
     L = (1.0, 1.0, 1.0)
     hz = L[2] / (Nz + 1)
     z = np.arange(Nz + 2) * hz
