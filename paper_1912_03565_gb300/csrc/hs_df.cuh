@@ -85,27 +85,24 @@ __device__ __forceinline__ dfloat df_from_double(double x) {
 
 __device__ __forceinline__ double df_to_double(dfloat x) { return (double)x.hi + (double)x.lo; }
 
-// Splits an FP64 value into hi + lo FP32 parts with integer operations only
-// (no FP64 instruction): hi keeps the top 24 significant bits, lo the next 24
-// (truncated), so |x - (hi + lo)| <= 2^-47 |x|.  Values below 2^-126 in
-// magnitude (FP32's normal range) become 0; inputs are finite.
+// Splits an FP64 value into hi + lo FP32 parts without FP64 arithmetic: hi keeps
+// the top 24 significant bits (integer operations), lo is the remaining 29 bits
+// converted to FP32 (rounded to 24 bits) and scaled by 2^(e - 52) with two exact
+// multiplications, so |x - (hi + lo)| <= 2^-48 |x| (lo may lose bits to FP32's
+// subnormal range when |x| < 2^-74).  |x| outside FP32's normal range gives 0;
+// inputs are finite.
 __device__ __forceinline__ dfloat df_split_bits(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned sign = (unsigned)(b >> 63) << 31;
-    const int e = (int)((b >> 52) & 0x7FF) - 1023;
-    const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+    const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+    const int e = (int)((hw >> 20) & 0x7FFu) - 1023;
     dfloat r;
     r.hi = 0.f;
     r.lo = 0.f;
     if (e < -126 || e > 127) return r;
-    r.hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
-    const unsigned rem = (unsigned)(m & 0x1FFFFFFFULL);  // low 29 bits
-    if (rem == 0) return r;
-    const int p = 31 - __clz(rem);                       // msb position, 0..28
-    const int el = e - 52 + p;                           // exponent of the lo part
-    if (el < -126) return r;
-    const unsigned frac = (p >= 23) ? ((rem >> (p - 23)) & 0x7FFFFFu) : ((rem << (23 - p)) & 0x7FFFFFu);
-    r.lo = __uint_as_float(sign | ((unsigned)(el + 127) << 23) | frac);
+    const unsigned sign = hw & 0x80000000u;
+    const unsigned ebits = (unsigned)(e + 127) << 23;           // 2^e as FP32
+    r.hi = __uint_as_float(sign | ebits | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+    const float rem = __uint2float_rn(lw & 0x1FFFFFFFu) * 0x1p-52f;
+    r.lo = __uint_as_float(__float_as_uint(rem * __uint_as_float(ebits)) | sign);
     return r;
 }
 
