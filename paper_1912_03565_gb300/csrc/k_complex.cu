@@ -49,7 +49,6 @@ struct hs_zplan_s {
     double2 *d_dct[2];         // Neumann axis: M roots then M + 1 half-angle pairs
     double2 *d_rows;           // [Nu][3][4] complex coefficients of the unknown rows
     int rows_ok;
-    size_t bytes;
     char last_error[256];
 };
 
