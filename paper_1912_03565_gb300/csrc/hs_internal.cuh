@@ -144,6 +144,14 @@ int hs_dst_fast_size(int M);
 hs_status hs_launch_dst_fast(const hs_plan_s *P, int axis, int tc, int tin, const void *in,
                              int tout, void *out, int mode, double scale, cudaStream_t s,
                              double *aux);
+// Its three groups of kernel instances (k_dst_fast_f64.cu, k_dst_fast_f32.cu,
+// k_dst_fast_df.cu); HS_ERR_UNSUPPORTED for other type / mode combinations.
+hs_status hs_dst_fast_f64(const hs_plan_s *P, int axis, int tin, const void *in, int tout,
+                          void *out, int mode, double scale, cudaStream_t s, double *aux);
+hs_status hs_dst_fast_f32(const hs_plan_s *P, int axis, int tin, const void *in, int tout,
+                          void *out, int mode, double scale, cudaStream_t s, double *aux);
+hs_status hs_dst_fast_df(const hs_plan_s *P, int axis, int tin, const void *in, int tout,
+                         void *out, int mode, double scale, cudaStream_t s, double *aux);
 
 // Fused FP32 transform tiles (k_dst_fused_x.cu, k_dst_fused_y.cu); HS_ERR_UNSUPPORTED
 // for a length or type combination they do not cover.  wide = 1: twice the
