@@ -61,6 +61,11 @@ NCU_COUNTS = {
 }
 
 
+# FP64 pipe instruction rate of one GB300: the measured FP64 FMA throughput
+# (1.19 TFLOP/s, independent-chain probe) / 2 flops / 32 threads, in G warp-inst/s
+FP64_PIPE_PEAK = 1.19e12 / 2.0 / 32.0 / 1e9
+
+
 def sm_max_mhz():
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
@@ -502,6 +507,30 @@ def bench_zrobin(args, torch, H, W, rank, world, barrier, max_over_ranks):
     torch.cuda.synchronize()
     clocks = clk.stop()
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev)) / args.steps
+    # per-stage times from a separate loop with the plan's stage events on
+    s.set_stage_timing(True)
+    stages = {k: 0.0 for k in H.ZSolver.ZSTAGES}
+    nst = 3
+    for k in range(nst):
+        flush.fill_(float(k))
+        s.solve(f, u, stream=stream)
+        for key, v in s.stage_times().items():
+            stages[key] += v / nst
+    s.set_stage_timing(False)
+    roofline = None
+    counts = NCU_COUNTS.get((name, "transforms"))
+    if counts is not None:
+        # the forward transform stage: one x and one y pass (FP64 sine or cosine tiles,
+        # FP64-pipe bound); FP64-pipe warp instructions of the two passes (ncu) over the
+        # stage's live time, against the FP64 pipe's instruction rate
+        ach = counts["fp64_warp_inst"] / (stages["transforms"] * 1e-3) / 1e9
+        roofline = {"bound": "alu", "kernel": counts["kernel"], "achieved": ach,
+                    "peak": FP64_PIPE_PEAK, "unit": "G fp64 warp-inst/s",
+                    "frac": ach / FP64_PIPE_PEAK, "traffic": counts["dram_bytes"],
+                    "peak_kind": "FP64 pipe: measured FP64 FMA rate 1.19 TFLOP/s = 0.595 T "
+                                 "thread-instructions/s = 18.6 G warp-instructions/s",
+                    "launches": 2, "fp64_warp_inst_per_stage": counts["fp64_warp_inst"],
+                    "stage_ms": stages["transforms"], "profile": counts["profile"]}
     acc, cpu = {"compared_against": "oracle (complex FP64, O(N^4) sine / cosine sums)"}, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
@@ -524,8 +553,8 @@ def bench_zrobin(args, torch, H, W, rank, world, barrier, max_over_ranks):
                        "l2": "256 MB buffer written between timed steps",
                        "unknowns": f"complex, planes l = 0..N+1 (Robin faces), {ny} x {nx} "
                                    "per plane"},
-            "accuracy": acc, "cpu_baseline": cpu, "e2e": None, "roofline": None,
-            "clocks": clocks,
+            "accuracy": acc, "cpu_baseline": cpu, "e2e": None, "roofline": roofline,
+            "stages_ms": stages, "clocks": clocks,
             # right-hand side, 4 transform passes, complex z-solve
             "gpu_launches": 6 * args.steps,
             "workspace_bytes": s.workspace_bytes(),

@@ -574,6 +574,15 @@ hs_status hs_zplan_set_sides(hs_zplan_t plan, int x_kind, int y_kind);
 hs_status hs_zsolve(hs_zplan_t plan, const double *f, const double *g_lo, const double *g_hi,
                     double *u, void *stream);
 
+/* hs_zplan_set_stage_timing -- when on (1), each hs_zsolve records CUDA events
+ * on its stream around its stages; hs_zplan_stage_times then waits for the
+ * last solve's events and writes the milliseconds of its 5 stages to ms[0..4]:
+ * right-hand side, forward transforms (x and y), z-solves, inverse transforms,
+ * output copies.  Errors: HS_ERR_INVALID_ARG (timing never switched on),
+ * HS_ERR_CUDA. */
+hs_status hs_zplan_set_stage_timing(hs_zplan_t plan, int on);
+hs_status hs_zplan_stage_times(hs_zplan_t plan, float *ms);
+
 /* Device workspace of the plan in bytes, its last error text, and its release. */
 size_t hs_zplan_workspace_bytes(hs_zplan_t plan);
 const char *hs_zplan_last_error(hs_zplan_t plan);

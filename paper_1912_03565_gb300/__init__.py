@@ -60,7 +60,8 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_precond_create", "hs_precond_apply", "hs_precond_solve", "hs_precond_destroy",
             "hs_batch_workspace_bytes", "hs_batch_destroy",
             "hs_zplan", "hs_zplan_set_coeff", "hs_zplan_set_faces", "hs_zplan_set_sides",
-            "hs_zsolve", "hs_set_coeff_fn",
+            "hs_zsolve", "hs_set_coeff_fn", "hs_zplan_set_stage_timing",
+            "hs_zplan_stage_times",
             "hs_zplan_workspace_bytes", "hs_zplan_last_error", "hs_zplan_destroy")
 HS_STATIC_MAX_NZ = 8192
 
@@ -181,6 +182,10 @@ def load(path: Optional[str] = None):
     lib.hs_zplan_set_coeff.restype = ci
     lib.hs_zplan_set_faces.argtypes = [vp, ci, dp, dp, ci, dp, dp]
     lib.hs_zplan_set_faces.restype = ci
+    lib.hs_zplan_set_stage_timing.argtypes = [vp, ci]
+    lib.hs_zplan_set_stage_timing.restype = ci
+    lib.hs_zplan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.hs_zplan_stage_times.restype = ci
     lib.hs_zplan_set_sides.argtypes = [vp, ci, ci]
     lib.hs_zplan_set_sides.restype = ci
     lib.hs_zsolve.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -617,6 +622,17 @@ class ZSolver:
         self._keep = (f, u, g_lo, g_hi)
         return self._err(load().hs_zsolve(self.plan, _ptr(f), _ptr(g_lo), _ptr(g_hi), _ptr(u),
                                           _stream_ptr(stream)), "hs_zsolve")
+
+    ZSTAGES = ("rhs", "transforms", "thomas", "inverse_transforms", "output")
+
+    def set_stage_timing(self, on):
+        return self._err(load().hs_zplan_set_stage_timing(self.plan, int(bool(on))),
+                         "hs_zplan_set_stage_timing")
+
+    def stage_times(self):
+        ms = (ctypes.c_float * 5)()
+        self._err(load().hs_zplan_stage_times(self.plan, ms), "hs_zplan_stage_times")
+        return dict(zip(self.ZSTAGES, list(ms)))
 
     def workspace_bytes(self):
         return load().hs_zplan_workspace_bytes(self.plan)

@@ -49,6 +49,9 @@ struct hs_zplan_s {
     double2 *d_dct[2];         // Neumann axis: M roots then M + 1 half-angle pairs
     double2 *d_rows;           // [Nu][3][4] complex coefficients of the unknown rows
     int rows_ok;
+    int timing;                // record events around the stages of each solve
+    int have_ev;
+    cudaEvent_t ev[6];         // rhs | forward transforms | z-solves | inverse | output
     char last_error[256];
 };
 
@@ -467,8 +470,15 @@ hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const dou
     a.ga_hi = cscale(2.0 * Z->hz, cdiv_host(make_double2(1.0, 0.0), Z->alpha[1]));
     a.f = f; a.g_lo = g_lo; a.g_hi = g_hi; a.rows = Z->d_rows; a.W = W;
     const unsigned blocks = (unsigned)((nu + 255) / 256 < 152 * 16 ? (nu + 255) / 256 : 152 * 16);
+    auto mark = [&](int k) -> hs_status {
+        if (Z->timing && Z->have_ev) ZCK(Z, cudaEventRecord(Z->ev[k], s));
+        return HS_OK;
+    };
+    hs_status mk;
+    if ((mk = mark(0)) != HS_OK) return mk;
     zrhs_kernel<<<blocks, 256, 0, s>>>(a);
     ZCK(Z, cudaGetLastError());
+    if ((mk = mark(1)) != HS_OK) return mk;
     // one transform pass along an axis: the cosine kernel on a Neumann axis, else the
     // plan's sine transform; inverse passes carry 2 / (N + 1) for either
     auto pass = [&](int axis, double scale) -> hs_status {
@@ -485,15 +495,18 @@ hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const dou
         zerr(Z, "forward transform: status %d", st);
         return st;
     }
+    if ((mk = mark(2)) != HS_OK) return mk;
     zthomas_kernel<<<(unsigned)((plane + 127) / 128), 128, 0, s>>>(W, T->d_dscr, Z->d_rows,
                                                                  Z->d_cos, Z->d_cos + Z->nx,
                                                                  Z->nx, Z->ny, Z->Nu);
     ZCK(Z, cudaGetLastError());
+    if ((mk = mark(3)) != HS_OK) return mk;
     if ((st = pass(HS_AXIS_Y, 2.0 / (Z->Ny + 1))) != HS_OK ||
         (st = pass(HS_AXIS_X, 2.0 / (Z->Nx + 1))) != HS_OK) {
         zerr(Z, "inverse transform: status %d", st);
         return st;
     }
+    if ((mk = mark(4)) != HS_OK) return mk;
     // unknown planes into u; Dirichlet planes receive their face data
     const size_t uplanes = (size_t)Z->Nz + 2;
     for (int comp = 0; comp < 2; ++comp) {
@@ -511,6 +524,30 @@ hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const dou
                 ZCK(Z, cudaMemsetAsync(dst, 0, plane * sizeof(double), s));
         }
     }
+    return mark(5);
+}
+
+hs_status hs_zplan_set_stage_timing(hs_zplan_t Z, int on) {
+    if (!Z) return HS_ERR_INVALID_ARG;
+    if (on && !Z->have_ev) {
+        for (int k = 0; k < 6; ++k) {
+            if (cudaEventCreate(&Z->ev[k]) != cudaSuccess) {
+                cudaGetLastError();
+                for (int j = 0; j < k; ++j) cudaEventDestroy(Z->ev[j]);
+                return HS_ERR_CUDA;
+            }
+        }
+        Z->have_ev = 1;
+    }
+    Z->timing = on ? 1 : 0;
+    return HS_OK;
+}
+
+hs_status hs_zplan_stage_times(hs_zplan_t Z, float *ms) {
+    if (!Z || !ms) return HS_ERR_INVALID_ARG;
+    if (!Z->have_ev) return HS_ERR_INVALID_ARG;
+    ZCK(Z, cudaEventSynchronize(Z->ev[5]));
+    for (int k = 0; k < 5; ++k) ZCK(Z, cudaEventElapsedTime(&ms[k], Z->ev[k], Z->ev[k + 1]));
     return HS_OK;
 }
 
@@ -536,6 +573,8 @@ void hs_zplan_destroy(hs_zplan_t Z) {
     if (Z->d_cos) cudaFree(Z->d_cos);
     for (int a = 0; a < 2; ++a)
         if (Z->d_dct[a]) cudaFree(Z->d_dct[a]);
+    if (Z->have_ev)
+        for (int k = 0; k < 6; ++k) cudaEventDestroy(Z->ev[k]);
     delete Z;
 }
 
