@@ -58,6 +58,18 @@ NCU_COUNTS = {
     ("cube255_o6", "rhs"): {"bound": "alu", "dram_bytes": 139.350784e6 + 89.349632e6,
                             "warp_inst": 338550643,
                             "profile": "profiles/rhs_df_cube255_o6.md"},
+    # forward transform stage of the complex plan (x and y pass): FP64-pipe warp
+    # instructions and DRAM bytes of the two launches
+    ("zrobin255_o4", "transforms"): {
+        "kernel": "dst_fast_kernel<double> x + y (sine tiles over 2 x 257 planes)",
+        "fp64_warp_inst": 32374688 + 32501248,
+        "dram_bytes": 267439360 + 207346944 + 267740160 + 211877888,
+        "profile": "profiles/fp64_transforms_complex255.md"},
+    ("zneumann255_o4", "transforms"): {
+        "kernel": "dct_kernel x + y (cosine tiles over 2 x 257 planes)",
+        "fp64_warp_inst": 31671646 + 32533116,
+        "dram_bytes": 271669504 + 211579648 + 271651072 + 215605760,
+        "profile": "profiles/fp64_transforms_complex255.md"},
 }
 
 
