@@ -58,3 +58,22 @@ def test_stage_bytes_and_launch_counts():
     assert bench.launches_per_solve("mixed", 1) == 12
     assert bench.launches_per_solve("fp64", 0) == 6
     assert set(bench.WORKLOADS) >= {"cube255_o6", "cube1023_o6", "cd511x8"}
+
+
+def test_complex_workloads_and_fp64_pipe_peak():
+    """The complex-plan workloads, their counters and the FP64 pipe's rate the bench uses;
+    the oracle leg on a small instance of the Neumann recipe (every plane and side node
+    is an unknown: Robin z-faces, Neumann x and y)."""
+    assert {"zrobin255_o4", "zneumann255_o4"} <= set(bench.WORKLOADS)
+    assert abs(bench.FP64_PIPE_PEAK - 1.19e12 / 64 / 1e9) < 1e-9
+    for name in ("zrobin255_o4", "zneumann255_o4"):
+        c = bench.NCU_COUNTS[(name, "transforms")]
+        assert c["fp64_warp_inst"] > 0 and c["dram_bytes"] > 0
+        assert os.path.exists(os.path.join(ROOT, c["profile"]))
+    import numpy as np
+    import workloads as W
+    w = W.workload_zneumann(7)
+    U = bench.zrobin_run_oracle(w)
+    assert U.shape == (9, 9, 9) and np.all(np.isfinite(U))
+    w = W.workload_zrobin(7)
+    assert bench.zrobin_run_oracle(w).shape == (9, 7, 7)
