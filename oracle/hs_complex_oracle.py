@@ -109,18 +109,47 @@ def side_cosines(N, kind):
     return O.mode_cosines(N)
 
 
-def reflect_pad(U, sides):
+def _span(n_nodes, kind):
+    """Node indices covered by a padded unknown grid along a side axis: nodes -1..N+2 of
+    a Neumann axis (folded back into 0..N+1 by the even reflection), 0..N+1 otherwise."""
+    if kind == SIDE_NEUMANN:
+        idx = np.arange(-1, n_nodes + 1)
+        idx[0], idx[-1] = 1, n_nodes - 2
+        return idx
+    return np.arange(0, n_nodes)
+
+
+def reflect_pad(U, sides, side_data=None, h=None):
     """Pad a field on the unknown grid [..., ny, nx] by one node per side: zero beyond a
-    Dirichlet axis (its boundary nodes), the even reflection beyond a Neumann axis."""
+    Dirichlet axis (its boundary nodes), beyond a Neumann axis the ghost of the central
+    difference of u_n = g, i.e. the even reflection plus 2 h g (outward normal, both
+    faces).  side_data = (x-lo, x-hi, y-lo, y-hi) arrays of u_n on the face node grids
+    ([planes][Ny+2] for x-faces, [planes][Nx+2] for y-faces; None = 0), reflected
+    evenly beyond their own edges; x-ghosts are set first, so a corner ghost carries the
+    data of both faces."""
     U = np.asarray(U)
     pad = [(0, 0)] * (U.ndim - 2) + [(1, 1), (1, 1)]
     P = np.pad(U, pad)
-    if sides[1] == SIDE_NEUMANN:
-        P[..., 0, :] = P[..., 2, :]
-        P[..., -1, :] = P[..., -3, :]
+    sd = [None] * 4 if side_data is None else list(side_data)
+    ny, nx = P.shape[-2] - 2, P.shape[-1] - 2
+    Ny = ny - 2 if sides[1] == SIDE_NEUMANN else ny
+    Nx = nx - 2 if sides[0] == SIDE_NEUMANN else nx
     if sides[0] == SIDE_NEUMANN:
         P[..., :, 0] = P[..., :, 2]
         P[..., :, -1] = P[..., :, -3]
+        rows = _span(Ny + 2, sides[1])
+        for k, col in ((0, 0), (1, -1)):
+            if sd[k] is not None:
+                g = np.asarray(sd[k])[..., rows]
+                P[..., :, col] = P[..., :, col] + 2.0 * h[0] * g
+    if sides[1] == SIDE_NEUMANN:
+        P[..., 0, :] = P[..., 2, :]
+        P[..., -1, :] = P[..., -3, :]
+        cols = _span(Nx + 2, sides[0])
+        for k, row in ((2, 0), (3, -1)):
+            if sd[k] is not None:
+                g = np.asarray(sd[k])[..., cols]
+                P[..., row, :] = P[..., row, :] + 2.0 * h[1] * g
     return P
 
 
@@ -202,7 +231,8 @@ def _f_on_unknowns(f, sides):
     return P
 
 
-def rhs(order, h, K, zf, f_nodes, g_lo=None, g_hi=None, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
+def rhs(order, h, K, zf, f_nodes, g_lo=None, g_hi=None, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET),
+        side_data=None):
     """Right-hand side of the unknown rows: array (Nu, ny, nx) complex."""
     hz = h[2]
     f = np.asarray(f_nodes, dtype=np.complex128)
@@ -226,7 +256,12 @@ def rhs(order, h, K, zf, f_nodes, g_lo=None, g_hi=None, sides=(SIDE_DIRICHLET, S
     rows.extend(Fi)
     if zf.hi == ROBIN:
         rows.append(hz * hz * fu[Nz + 1, 1:-1, 1:-1] - 2.0 * hz * ghi / zf.alpha[1])
-    return np.array(rows)
+    F = np.array(rows)
+    if side_data is not None and any(d is not None for d in side_data):
+        # Neumann data: the stencil weights of the ghost nodes times their data parts
+        zero = np.zeros((Nz + 2, ny, nx), dtype=np.complex128)
+        F = F - apply_operator(order, h, K, zf, zero, None, None, sides, side_data)
+    return F
 
 
 def eigenvalues(R, Nx, Ny, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
@@ -253,13 +288,13 @@ def solve_rows(R, F, Nx, Ny, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
 
 
 def solve(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
-          sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
+          sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), side_data=None):
     """Solution on every plane l = 0..Nz+1 (unknown grid in x, y): complex (Nz+2, ny, nx)."""
     f = np.asarray(f_nodes, dtype=np.complex128)
     Nz, Ny, Nx = f.shape[0] - 2, f.shape[1] - 2, f.shape[2] - 2
     ny, nx = _n_unknown(Ny, sides[1]), _n_unknown(Nx, sides[0])
     R = row_table(order, h, K, zf)
-    F = rhs(order, h, K, zf, f, g_lo, g_hi, sides)
+    F = rhs(order, h, K, zf, f, g_lo, g_hi, sides, side_data)
     Uu, ratio = solve_rows(R, F, Nx, Ny, sides)
     l0, l1 = zf.unknown_planes(Nz)
     U = np.zeros((Nz + 2, ny, nx), dtype=np.complex128)
@@ -277,7 +312,7 @@ def solve(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
 
 
 def apply_operator(order, h, K, zf, U_all, g_lo=None, g_hi=None,
-                   sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
+                   sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), side_data=None):
     """Rows l0..l1 of (A U - data terms): U_all on planes 0..Nz+1 (interior x, y).
 
     Interior rows: the 27-point stencil with the complex table.  Robin rows: the
@@ -288,8 +323,8 @@ def apply_operator(order, h, K, zf, U_all, g_lo=None, g_hi=None,
     K = np.asarray(K, dtype=np.complex128)
     U_all = np.asarray(U_all, dtype=np.complex128)
     Nz, Ny, Nx = U_all.shape[0] - 2, U_all.shape[1], U_all.shape[2]
-    # beyond a Neumann side: the ghost u_-1 = u_1 of u_n = 0, built explicitly
-    P = reflect_pad(U_all, sides)
+    # beyond a Neumann side: the ghost u_-1 = u_1 + 2 h g of u_n = g, built explicitly
+    P = reflect_pad(U_all, sides, side_data, h)
     Ci = complex_coefficients(order, h, K)
     out = []
     glo, ghi = _face(g_lo, Ny, Nx), _face(g_hi, Ny, Nx)
@@ -332,7 +367,7 @@ def rhs_direct(order, h, f_nodes, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
 
 
 def solve_dense(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
-                sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
+                sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), side_data=None):
     """Brute force: the matrix of apply_operator (columns from unit vectors), its data
     part from the operator at U = 0, and a dense complex LU solve."""
     f = np.asarray(f_nodes, dtype=np.complex128)
@@ -345,7 +380,7 @@ def solve_dense(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
         base[0] = _face(g_lo, Ny, Nx)
     if zf.hi == DIRICHLET:
         base[Nz + 1] = _face(g_hi, Ny, Nx)
-    data = apply_operator(order, h, K, zf, base, g_lo, g_hi, sides).ravel()
+    data = apply_operator(order, h, K, zf, base, g_lo, g_hi, sides, side_data).ravel()
     n = Nu * Ny * Nx
     A = np.zeros((n, n), dtype=np.complex128)
     zero_faces = ZFaces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])

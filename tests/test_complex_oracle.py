@@ -236,3 +236,75 @@ def test_neumann_manufactured_converges(order, kind, lo_ratio):
     e = [_manufactured_neumann(N, order, kind) for N in (7, 15, 31)]
     assert e[2] < e[1] < e[0]
     assert e[1] / e[2] >= lo_ratio, e
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("sides", [(NEU, DIR), (DIR, NEU), (NEU, NEU)])
+@pytest.mark.parametrize("faces", [(R, R), (D, D)])
+def test_neumann_data_separated_equals_dense(order, sides, faces):
+    """u_n = g on the Neumann faces: the separated solve (data moved to the right-hand
+    side through the ghost nodes' stencil weights) equals the dense solve of the operator
+    whose ghosts carry the data explicitly."""
+    shape = (5, 4, 4)
+    Nx, Ny, Nz = shape
+    h, K, f, rs = _neumann_case(shape, 70 + order + 3 * sides[0] + sides[1] + 7 * faces[1])
+    nx = Nx + 2 if sides[0] == NEU else Nx
+    ny = Ny + 2 if sides[1] == NEU else Ny
+    g_lo, g_hi = _crand(rs, (ny, nx)), _crand(rs, (ny, nx))
+    sd = (_crand(rs, (Nz + 2, Ny + 2)), _crand(rs, (Nz + 2, Ny + 2)),
+          _crand(rs, (Nz + 2, Nx + 2)), _crand(rs, (Nz + 2, Nx + 2)))
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    U, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi, sides, sd)
+    Ud = CX.solve_dense(order, h, K, zf, f, g_lo, g_hi, sides, sd)
+    assert O.max_rel_diff(U, Ud) <= 1e-11
+    U0, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi, sides)
+    assert O.max_rel_diff(U, U0) > 1e-3          # the data matter
+
+
+def _manufactured_neumann_data(N, order, kappa=2.0):
+    """u = sin(pi x / 2) cos(2 pi y) e^{i kappa z}: u_n = -pi/2 cos(2 pi y) e^{i kappa z}
+    on x = 0, 0 on x = 1 and on both y-faces; Dirichlet z-faces."""
+    h = (1.0 / (N + 1),) * 3
+    x = np.arange(N + 2) * h[0]
+    z = x.copy()
+    K = (35.0 + 6.0j) * (1.0 + 0.5 * z)
+    ez = np.exp(1j * kappa * z)
+    u = (np.sin(0.5 * np.pi * x)[None, None, :] * np.cos(2 * np.pi * x)[None, :, None]
+         * ez[:, None, None])
+    f = (-0.25 * np.pi ** 2 - 4 * np.pi ** 2 - kappa ** 2 + K[:, None, None]) * u
+    gx_lo = -0.5 * np.pi * np.cos(2 * np.pi * x)[None, :] * ez[:, None]   # [Nz+2][Ny+2]
+    sd = (gx_lo, None, None, None)
+    U, _ = CX.solve(order, h, K, CX.ZFaces(), f, u[0], u[-1], (NEU, NEU), sd)
+    return np.max(np.abs(U - u))
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_neumann_data_manufactured_converges(order):
+    e = [_manufactured_neumann_data(N, order) for N in (7, 15, 31)]
+    assert e[2] < e[1] < e[0]
+    assert e[1] / e[2] >= 3.5, e
+
+
+def _manufactured_neumann_ydata(N, order, kappa=2.0, Ly=1.3):
+    """u = cos(pi x) sin(pi y / (2 Ly)) e^{i kappa z} on [0,1] x [0,Ly] x [0,1] (h_x != h_y):
+    u_n = -pi/(2 Ly) cos(pi x) e^{i kappa z} on y = 0, 0 on the other side faces."""
+    h = (1.0 / (N + 1), Ly / (N + 1), 1.0 / (N + 1))
+    x = np.arange(N + 2) * h[0]
+    y = np.arange(N + 2) * h[1]
+    z = np.arange(N + 2) * h[2]
+    K = (35.0 + 6.0j) * (1.0 + 0.5 * z)
+    ez = np.exp(1j * kappa * z)
+    u = (np.cos(np.pi * x)[None, None, :] * np.sin(0.5 * np.pi * y / Ly)[None, :, None]
+         * ez[:, None, None])
+    f = (-np.pi ** 2 - (0.5 * np.pi / Ly) ** 2 - kappa ** 2 + K[:, None, None]) * u
+    gy_lo = -(0.5 * np.pi / Ly) * np.cos(np.pi * x)[None, :] * ez[:, None]   # [Nz+2][Nx+2]
+    U, _ = CX.solve(order, h, K, CX.ZFaces(), f, u[0], u[-1], (NEU, NEU),
+                    (None, None, gy_lo, None))
+    return np.max(np.abs(U - u))
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_neumann_ydata_anisotropic_converges(order):
+    e = [_manufactured_neumann_ydata(N, order) for N in (7, 15, 31)]
+    assert e[2] < e[1] < e[0]
+    assert e[1] / e[2] >= 3.5, e
