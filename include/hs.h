@@ -562,6 +562,16 @@ hs_status hs_zplan_set_faces(hs_zplan_t plan, int lo_kind, const double *alpha_l
                              const double *beta_lo, int hi_kind, const double *alpha_hi,
                              const double *beta_hi);
 
+/* hs_zsolve_ex -- hs_zsolve with data on Neumann side faces: side[0..3] are the
+ * outward normal derivative u_n = g on the x-lo, x-hi faces ([2][Nz+2][Ny+2],
+ * planar complex, on the face node grid: planes l, nodes j = 0..Ny+1) and the
+ * y-lo, y-hi faces ([2][Nz+2][Nx+2]); NULL entries (or side = NULL) are 0.  The
+ * ghost beyond such a face is the mirror value plus 2 h g (second-order
+ * central difference), a face's data reflected evenly beyond its own edges.
+ * Data on the faces of a Dirichlet axis are rejected (HS_ERR_INVALID_ARG). */
+hs_status hs_zsolve_ex(hs_zplan_t plan, const double *f, const double *g_lo, const double *g_hi,
+                       const double *const *side, double *u, void *stream);
+
 /* hs_zplan_set_sides -- kind (HS_SIDE_DIRICHLET / HS_SIDE_NEUMANN) of the x and
  * y side axes (default Dirichlet).  A Neumann axis needs N + 1 with a compiled
  * transform (N + 1 in {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024}).

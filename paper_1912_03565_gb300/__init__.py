@@ -60,7 +60,7 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_precond_create", "hs_precond_apply", "hs_precond_solve", "hs_precond_destroy",
             "hs_batch_workspace_bytes", "hs_batch_destroy",
             "hs_zplan", "hs_zplan_set_coeff", "hs_zplan_set_faces", "hs_zplan_set_sides",
-            "hs_zsolve", "hs_set_coeff_fn", "hs_zplan_set_stage_timing",
+            "hs_zsolve", "hs_zsolve_ex", "hs_set_coeff_fn", "hs_zplan_set_stage_timing",
             "hs_zplan_stage_times",
             "hs_zplan_workspace_bytes", "hs_zplan_last_error", "hs_zplan_destroy")
 HS_STATIC_MAX_NZ = 8192
@@ -188,6 +188,8 @@ def load(path: Optional[str] = None):
     lib.hs_zplan_stage_times.restype = ci
     lib.hs_zplan_set_sides.argtypes = [vp, ci, ci]
     lib.hs_zplan_set_sides.restype = ci
+    lib.hs_zsolve_ex.argtypes = [vp, vp, vp, vp, ctypes.POINTER(vp), vp, vp]
+    lib.hs_zsolve_ex.restype = ci
     lib.hs_zsolve.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.hs_zsolve.restype = ci
     lib.hs_zplan_workspace_bytes.argtypes = [vp]
@@ -618,10 +620,16 @@ class ZSolver:
         return self._err(load().hs_zplan_set_sides(self.plan, int(x_kind), int(y_kind)),
                          "hs_zplan_set_sides")
 
-    def solve(self, f, u, g_lo=None, g_hi=None, stream=None):
-        self._keep = (f, u, g_lo, g_hi)
-        return self._err(load().hs_zsolve(self.plan, _ptr(f), _ptr(g_lo), _ptr(g_hi), _ptr(u),
-                                          _stream_ptr(stream)), "hs_zsolve")
+    def solve(self, f, u, g_lo=None, g_hi=None, stream=None, side_data=None):
+        """side_data: u_n on the (x-lo, x-hi, y-lo, y-hi) faces of Neumann axes, planar
+        complex [2][Nz+2][Ny+2] (x-faces) / [2][Nz+2][Nx+2] (y-faces); None entries = 0."""
+        self._keep = (f, u, g_lo, g_hi, side_data)
+        if side_data is None:
+            return self._err(load().hs_zsolve(self.plan, _ptr(f), _ptr(g_lo), _ptr(g_hi),
+                                              _ptr(u), _stream_ptr(stream)), "hs_zsolve")
+        sd = (ctypes.c_void_p * 4)(*[_ptr(a) for a in side_data])
+        return self._err(load().hs_zsolve_ex(self.plan, _ptr(f), _ptr(g_lo), _ptr(g_hi), sd,
+                                             _ptr(u), _stream_ptr(stream)), "hs_zsolve_ex")
 
     ZSTAGES = ("rhs", "transforms", "thomas", "inverse_transforms", "output")
 

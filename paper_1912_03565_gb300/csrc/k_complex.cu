@@ -245,6 +245,9 @@ struct ZRhsArgs {
     double2 ga_lo, ga_hi;   // 2 h_z / alpha of each face (Robin)
     const double *f;        // [2][Nz+2][Ny+2][Nx+2]
     const double *g_lo, *g_hi;   // [2][ny][nx] or NULL
+    const double *side[4];  // u_n on the x-lo, x-hi ([2][Nz+2][Ny+2]), y-lo, y-hi
+                            // ([2][Nz+2][Nx+2]) faces of Neumann axes, or NULL
+    double hx, hy;
     const double2 *rows;    // [Nu][3][4]
     double *W;              // [2][Nu][ny][nx]
 };
@@ -260,6 +263,33 @@ __device__ inline double2 face_val(const ZRhsArgs &a, const double *g, int j, in
     if (j < 0 || j >= a.ny || i < 0 || i >= a.nx) return make_double2(0.0, 0.0);
     const size_t k = (size_t)j * a.nx + i, n = (size_t)a.ny * a.nx;
     return make_double2(g[k], g[n + k]);
+}
+
+// Data part (2 h g) of the value at node (i, j) of plane l when it is a ghost
+// beyond a Neumann face (u_n = g, outward normal): the x-ghost first, then the
+// y-ghost, each face's data read along the face with even reflection.
+__device__ inline double2 ghost_data(const ZRhsArgs &a, int i, int j, int l) {
+    double2 d = make_double2(0.0, 0.0);
+    const size_t nzp = (size_t)a.Nz + 2;
+    if (a.neu_x && (i < 0 || i > a.Nx + 1)) {
+        const double *g = a.side[i < 0 ? 0 : 1];
+        if (g) {
+            const int jr = reflect(j, a.Ny + 2);
+            const size_t k = (size_t)l * (a.Ny + 2) + jr, n = nzp * (a.Ny + 2);
+            d.x += 2.0 * a.hx * g[k];
+            d.y += 2.0 * a.hx * g[n + k];
+        }
+    }
+    if (a.neu_y && (j < 0 || j > a.Ny + 1)) {
+        const double *g = a.side[j < 0 ? 2 : 3];
+        if (g) {
+            const int ir = reflect(i, a.Nx + 2);
+            const size_t k = (size_t)l * (a.Nx + 2) + ir, n = nzp * (a.Nx + 2);
+            d.x += 2.0 * a.hy * g[k];
+            d.y += 2.0 * a.hy * g[n + k];
+        }
+    }
+    return d;
 }
 
 // One thread per unknown (row r, j, i): the compact right-hand side of the row,
@@ -310,6 +340,24 @@ __global__ void zrhs_kernel(ZRhsArgs a) {
                     for (int di = -1; di <= 1; ++di) {
                         const int m = (di != 0 && dj != 0) ? ZA : (di != 0 ? ZB : (dj != 0 ? ZC : ZD));
                         F = csub(F, cmul(w[m], face_val(a, g, j + dj, i + di)));
+                    }
+            }
+        }
+        // rows next to a Neumann face with data: the ghost nodes' stencil weights
+        // times their data parts leave for the right-hand side (planes 0..Nz+1)
+        const bool edge_x = a.neu_x && (ii == 0 || ii == a.Nx + 1) && (a.side[0] || a.side[1]);
+        const bool edge_y = a.neu_y && (jj == 0 || jj == a.Ny + 1) && (a.side[2] || a.side[3]);
+        if (edge_x || edge_y) {
+            for (int dl = -1; dl <= 1; ++dl) {
+                const int ll = l + dl;
+                if (ll < 0 || ll > a.Nz + 1) continue;
+                const double2 *w = a.rows + (size_t)r * 12 + (dl + 1) * 4;
+                for (int dj = -1; dj <= 1; ++dj)
+                    for (int di = -1; di <= 1; ++di) {
+                        const int i2 = ii + di, j2 = jj + dj;
+                        if (i2 >= 0 && i2 <= a.Nx + 1 && j2 >= 0 && j2 <= a.Ny + 1) continue;
+                        const int m = (di != 0 && dj != 0) ? ZA : (di != 0 ? ZB : (dj != 0 ? ZC : ZD));
+                        F = csub(F, cmul(w[m], ghost_data(a, i2, j2, ll)));
                     }
             }
         }
@@ -448,11 +496,23 @@ hs_status hs_zplan_set_sides(hs_zplan_t Z, int x_kind, int y_kind) {
 
 hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const double *g_hi,
                     double *u, void *stream) {
+    return hs_zsolve_ex(Z, f, g_lo, g_hi, nullptr, u, stream);
+}
+
+hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const double *g_hi,
+                       const double *const *side, double *u, void *stream) {
     if (!Z || !f || !u) return HS_ERR_INVALID_ARG;
     if (!Z->have_coeff || !Z->rows_ok) return HS_ERR_NO_COEFF;
     if (!device_ptr(f) || !device_ptr(u) || (g_lo && !device_ptr(g_lo)) ||
         (g_hi && !device_ptr(g_hi)))
         return HS_ERR_INVALID_ARG;
+    const double *sd[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; side && k < 4; ++k) {
+        if (!side[k]) continue;
+        // data on the faces of a Dirichlet axis have no meaning
+        if (Z->side[k / 2] != HS_SIDE_NEUMANN || !device_ptr(side[k])) return HS_ERR_INVALID_ARG;
+        sd[k] = side[k];
+    }
     Z->last_error[0] = 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     hs_plan_s *T = Z->T;
@@ -469,6 +529,9 @@ hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const dou
     a.ga_lo = cscale(2.0 * Z->hz, cdiv_host(make_double2(1.0, 0.0), Z->alpha[0]));
     a.ga_hi = cscale(2.0 * Z->hz, cdiv_host(make_double2(1.0, 0.0), Z->alpha[1]));
     a.f = f; a.g_lo = g_lo; a.g_hi = g_hi; a.rows = Z->d_rows; a.W = W;
+    for (int k = 0; k < 4; ++k) a.side[k] = sd[k];
+    a.hx = Z->hx;
+    a.hy = Z->hy;
     const unsigned blocks = (unsigned)((nu + 255) / 256 < 152 * 16 ? (nu + 255) / 256 : 152 * 16);
     auto mark = [&](int k) -> hs_status {
         if (Z->timing && Z->have_ev) ZCK(Z, cudaEventRecord(Z->ev[k], s));

@@ -211,3 +211,46 @@ def test_neumann_unsupported_length():
             s.set_sides(2, 0)
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("sides", [(NEU, DIRS), (DIRS, NEU), (NEU, NEU)])
+@pytest.mark.parametrize("faces", [(R, R), (D, D), (R, D)])
+def test_neumann_face_data_match_oracle(order, sides, faces):
+    """u_n = g on the Neumann faces (hs_zsolve_ex): every face with its own data, the
+    corner ghosts carrying two faces' data."""
+    torch = _torch()
+    shape, L = (31, 63, 7), (1.0, 1.3, 0.9)
+    Nx, Ny, Nz = shape
+    h, K, f, g_lo, g_hi = _neumann_case(shape, L, sides, 91 + order + 3 * sides[0] + sides[1])
+    rs = np.random.RandomState(5 + order)
+    cr = lambda *sh: rs.uniform(-1, 1, sh) + 1j * rs.uniform(-1, 1, sh)
+    sd = [cr(Nz + 2, Ny + 2) if sides[0] == NEU else None,
+          cr(Nz + 2, Ny + 2) if sides[0] == NEU else None,
+          cr(Nz + 2, Nx + 2) if sides[1] == NEU else None,
+          cr(Nz + 2, Nx + 2) if sides[1] == NEU else None]
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    ref, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi, sides, sd)
+    s = H.ZSolver(Nx, Ny, Nz, *L, order)
+    try:
+        s.set_coeff(K)
+        s.set_faces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
+        s.set_sides(*sides)
+        nx = Nx + 2 if sides[0] == NEU else Nx
+        ny = Ny + 2 if sides[1] == NEU else Ny
+        u = torch.full((2, Nz + 2, ny, nx), np.nan, dtype=torch.float64, device="cuda")
+        sdd = [None if a is None else _planar(torch, a) for a in sd]
+        s.solve(_planar(torch, f), u, _planar(torch, g_lo), _planar(torch, g_hi), side_data=sdd)
+        torch.cuda.synchronize()
+        uc = u.cpu().numpy()
+        got = uc[0] + 1j * uc[1]
+        with pytest.raises(H.HsError):   # data on a Dirichlet axis' faces
+            bad = [None, None, None, None]
+            k = 0 if sides[0] == DIRS else (2 if sides[1] == DIRS else None)
+            if k is None:
+                raise H.HsError(H.HS_ERR_INVALID_ARG, "no Dirichlet axis here")
+            bad[k] = _planar(torch, cr(Nz + 2, (Ny if k < 2 else Nx) + 2))
+            s.solve(_planar(torch, f), u, side_data=bad)
+    finally:
+        s.close()
+    assert O.max_rel_diff(got, ref) <= TOL
