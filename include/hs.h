@@ -522,7 +522,9 @@ const char *hs_last_error(hs_plan_t plan);
  * the central difference of the face condition, alpha (u_+1 - u_-1) / (2 h_z) +
  * beta u_0 = g.  The side faces stay Dirichlet, so Section 3.6 applies: the
  * real DSTs act on Re and Im, and each sine mode (p, q) is one complex
- * tridiagonal system in z, solved without pivoting.
+ * tridiagonal system in z, solved without pivoting; its LU factors are cached
+ * (48 bytes per complex unknown), rebuilt by the first solve after a change of
+ * coefficient, faces or side axes.
  *
  * A side axis (x or y) may instead carry u_n = 0 on both of its faces (the
  * extension Section 1 names): its boundary nodes become unknowns, f and the

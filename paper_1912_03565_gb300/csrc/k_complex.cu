@@ -49,6 +49,8 @@ struct hs_zplan_s {
     double2 *d_dct[2];         // Neumann axis: M roots then M + 1 half-angle pairs
     double2 *d_rows;           // [Nu][3][4] complex coefficients of the unknown rows
     int rows_ok;
+    double *d_fac;             // cached LU factors: 3 planar complex arrays [2][Nu][ny][nx]
+    int fac_ok;                // the factors match the rows and side tables
     int timing;                // record events around the stages of each solve
     int have_ev;
     cudaEvent_t ev[6];         // rhs | forward transforms | z-solves | inverse | output
@@ -149,6 +151,7 @@ hs_status build_rows(hs_zplan_s *Z) {
     ZCK(Z, cudaMemcpy(Z->d_rows, rows.data(), rows.size() * sizeof(double2),
                       cudaMemcpyHostToDevice));
     Z->rows_ok = 1;
+    Z->fac_ok = 0;
     return HS_OK;
 }
 
@@ -164,6 +167,7 @@ double sin_pi_frac(long a, long b) { return cos_pi_frac(2 * a - b, 2 * b); }
 
 // Mode cosines of both axes and the DCT tables of Neumann axes.
 hs_status side_tables(hs_zplan_s *Z) {
+    Z->fac_ok = 0;
     std::vector<double> c;
     const int N[2] = {Z->Nx, Z->Ny};
     for (int a = 0; a < 2; ++a) {
@@ -208,6 +212,8 @@ hs_status layout(hs_zplan_s *Z) {
         Z->T = nullptr;
         if (Z->d_rows) cudaFree(Z->d_rows);
         Z->d_rows = nullptr;
+        if (Z->d_fac) cudaFree(Z->d_fac);
+        Z->d_fac = nullptr;
         Z->Nu = Nu;
         Z->nx = nx;
         Z->ny = ny;
@@ -223,6 +229,7 @@ hs_status layout(hs_zplan_s *Z) {
         }
         Z->T = T;
         ZCK(Z, cudaMalloc(&Z->d_rows, (size_t)Nu * 12 * sizeof(double2)));
+        ZCK(Z, cudaMalloc(&Z->d_fac, (size_t)6 * Nu * nx * ny * sizeof(double)));
     }
     return side_tables(Z);
 }
@@ -343,33 +350,68 @@ __global__ void zrhs_kernel(ZRhsArgs a) {
                     }
             }
         }
-        // rows next to a Neumann face with data: the ghost nodes' stencil weights
-        // times their data parts leave for the right-hand side (planes 0..Nz+1)
-        const bool edge_x = a.neu_x && (ii == 0 || ii == a.Nx + 1) && (a.side[0] || a.side[1]);
-        const bool edge_y = a.neu_y && (jj == 0 || jj == a.Ny + 1) && (a.side[2] || a.side[3]);
-        if (edge_x || edge_y) {
-            for (int dl = -1; dl <= 1; ++dl) {
-                const int ll = l + dl;
-                if (ll < 0 || ll > a.Nz + 1) continue;
-                const double2 *w = a.rows + (size_t)r * 12 + (dl + 1) * 4;
-                for (int dj = -1; dj <= 1; ++dj)
-                    for (int di = -1; di <= 1; ++di) {
-                        const int i2 = ii + di, j2 = jj + dj;
-                        if (i2 >= 0 && i2 <= a.Nx + 1 && j2 >= 0 && j2 <= a.Ny + 1) continue;
-                        const int m = (di != 0 && dj != 0) ? ZA : (di != 0 ? ZB : (dj != 0 ? ZC : ZD));
-                        F = csub(F, cmul(w[m], ghost_data(a, i2, j2, ll)));
-                    }
-            }
-        }
         a.W[t] = F.x;
         a.W[n + t] = F.y;
     }
 }
 
-// One thread per sine mode (p, q): the complex tridiagonal system of the
-// unknown rows, lambda_nu = 4 a cp cq + 2 b cp + 2 c cq + d (Section 3.6), by
-// the textbook recurrence; c' kept in the scratch S [2][Nu][Ny][Nx].
-__global__ void zthomas_kernel(double *W, double *S, const double2 *rows, const double *cx,
+// Rows next to a Neumann face with data: the stencil weight of every ghost
+// neighbour times its data part leaves for the right-hand side (planes
+// 0..Nz+1), added to W after zrhs_kernel.  One thread per face row: x-face rows
+// first (all their ghost neighbours, corners included), then y-face rows not
+// already on a Neumann x-face with data, so each row is written once.
+__global__ void zside_kernel(ZRhsArgs a) {
+    const size_t plane = (size_t)a.ny * a.nx, n = plane * a.Nu;
+    const bool dx = a.neu_x && (a.side[0] || a.side[1]);
+    const bool dy = a.neu_y && (a.side[2] || a.side[3]);
+    const size_t cx = dx ? 2 * (size_t)a.Nu * a.ny : 0;
+    const size_t cy = dy ? 2 * (size_t)a.Nu * a.nx : 0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < cx + cy;
+         t += (size_t)gridDim.x * blockDim.x) {
+        int r, i, j;
+        if (t < cx) {
+            const size_t per = (size_t)a.Nu * a.ny;
+            const int face = (int)(t / per);
+            const size_t rem = t - face * per;
+            r = (int)(rem / a.ny);
+            j = (int)(rem - (size_t)r * a.ny);
+            i = face ? a.nx - 1 : 0;
+        } else {
+            const size_t u = t - cx, per = (size_t)a.Nu * a.nx;
+            const int face = (int)(u / per);
+            const size_t rem = u - face * per;
+            r = (int)(rem / a.nx);
+            i = (int)(rem - (size_t)r * a.nx);
+            j = face ? a.ny - 1 : 0;
+            if (dx && (i == 0 || i == a.nx - 1)) continue;   // written by its x-face thread
+        }
+        const int l = a.l0 + r, ii = i + a.i0x, jj = j + a.i0y;
+        double2 F = make_double2(0.0, 0.0);
+#pragma unroll 1
+        for (int dl = -1; dl <= 1; ++dl) {
+            const int ll = l + dl;
+            if (ll < 0 || ll > a.Nz + 1) continue;
+            const double2 *w = a.rows + (size_t)r * 12 + (dl + 1) * 4;
+#pragma unroll 1
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    const int i2 = ii + di, j2 = jj + dj;
+                    if (i2 >= 0 && i2 <= a.Nx + 1 && j2 >= 0 && j2 <= a.Ny + 1) continue;
+                    const int m = (di != 0 && dj != 0) ? ZA : (di != 0 ? ZB : (dj != 0 ? ZC : ZD));
+                    F = csub(F, cmul(w[m], ghost_data(a, i2, j2, ll)));
+                }
+        }
+        const size_t k = (size_t)r * plane + (size_t)j * a.nx + i;
+        a.W[k] += F.x;
+        a.W[n + k] += F.y;
+    }
+}
+
+// Cached LU of every mode's complex tridiagonal system (one thread per mode
+// (p, q); lambda_nu = 4 a cp cq + 2 b cp + 2 c cq + d, Section 3.6; no
+// pivoting): per row r the planar complex factors 1/m_r, lower_r/m_r and
+// c'_r = upper_r/m_r with m_r = diag_r - lower_r c'_{r-1}, each [2][Nu][ny][nx].
+__global__ void zfactor_kernel(double *fac, const double2 *rows, const double *cx,
                                const double *cy, int Nx, int Ny, int Nu) {
     const size_t plane = (size_t)Nx * Ny, n = plane * Nu;
     const size_t col = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -381,29 +423,46 @@ __global__ void zthomas_kernel(double *W, double *S, const double2 *rows, const 
         return make_double2(w4 * b[ZA].x + wb * b[ZB].x + wc * b[ZC].x + b[ZD].x,
                             w4 * b[ZA].y + wb * b[ZB].y + wc * b[ZC].y + b[ZD].y);
     };
-    double2 cprev = make_double2(0.0, 0.0), dprev = make_double2(0.0, 0.0);
+    double *F0 = fac, *F1 = fac + 2 * n, *F2 = fac + 4 * n;
+    double2 cprev = make_double2(0.0, 0.0);
     for (int r = 0; r < Nu; ++r) {
         const double2 *blk = rows + (size_t)r * 12;
         const double2 lo = lam(blk + ZLOW * 4), di = lam(blk + ZMID * 4), up = lam(blk + ZUPP * 4);
         const double2 piv = r ? csub(di, cmul(lo, cprev)) : di;
         const double inv = 1.0 / (piv.x * piv.x + piv.y * piv.y);
-        const double2 ip = make_double2(piv.x * inv, -piv.y * inv);   // 1 / piv
-        const size_t k = (size_t)r * plane + col;
-        double2 rhs = make_double2(W[k], W[n + k]);
-        if (r) rhs = csub(rhs, cmul(lo, dprev));
-        const double2 d = cmul(rhs, ip);
+        const double2 ip = make_double2(piv.x * inv, -piv.y * inv);   // 1 / m_r
+        const double2 li = r ? cmul(lo, ip) : make_double2(0.0, 0.0);
         const double2 c = cmul(up, ip);
-        S[k] = c.x;
-        S[n + k] = c.y;
+        const size_t k = (size_t)r * plane + col;
+        F0[k] = ip.x;
+        F0[n + k] = ip.y;
+        F1[k] = li.x;
+        F1[n + k] = li.y;
+        F2[k] = c.x;
+        F2[n + k] = c.y;
+        cprev = c;
+    }
+}
+
+// The z-solves with the cached factors, in place on W [2][Nu][ny][nx]:
+// d_r = rhs_r / m_r - (lower_r / m_r) d_{r-1}, then w_r = d_r - c'_r w_{r+1}.
+__global__ void zthomas_kernel(double *W, const double *fac, int Nx, int Ny, int Nu) {
+    const size_t plane = (size_t)Nx * Ny, n = plane * Nu;
+    const size_t col = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (col >= plane) return;
+    const double *F0 = fac, *F1 = fac + 2 * n, *F2 = fac + 4 * n;
+    double2 d = make_double2(0.0, 0.0);
+    for (int r = 0; r < Nu; ++r) {
+        const size_t k = (size_t)r * plane + col;
+        const double2 rhs = make_double2(W[k], W[n + k]);
+        d = csub(cmul(rhs, make_double2(F0[k], F0[n + k])), cmul(make_double2(F1[k], F1[n + k]), d));
         W[k] = d.x;
         W[n + k] = d.y;
-        cprev = c;
-        dprev = d;
     }
-    double2 w = dprev;
+    double2 w = d;
     for (int r = Nu - 2; r >= 0; --r) {
         const size_t k = (size_t)r * plane + col;
-        w = csub(make_double2(W[k], W[n + k]), cmul(make_double2(S[k], S[n + k]), w));
+        w = csub(make_double2(W[k], W[n + k]), cmul(make_double2(F2[k], F2[n + k]), w));
         W[k] = w.x;
         W[n + k] = w.y;
     }
@@ -541,6 +600,11 @@ hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const 
     if ((mk = mark(0)) != HS_OK) return mk;
     zrhs_kernel<<<blocks, 256, 0, s>>>(a);
     ZCK(Z, cudaGetLastError());
+    if ((a.neu_x && (sd[0] || sd[1])) || (a.neu_y && (sd[2] || sd[3]))) {
+        const size_t rows = 2 * (size_t)Z->Nu * (Z->nx + Z->ny);
+        zside_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(a);
+        ZCK(Z, cudaGetLastError());
+    }
     if ((mk = mark(1)) != HS_OK) return mk;
     // one transform pass along an axis: the cosine kernel on a Neumann axis, else the
     // plan's sine transform; inverse passes carry 2 / (N + 1) for either
@@ -559,9 +623,14 @@ hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const 
         return st;
     }
     if ((mk = mark(2)) != HS_OK) return mk;
-    zthomas_kernel<<<(unsigned)((plane + 127) / 128), 128, 0, s>>>(W, T->d_dscr, Z->d_rows,
-                                                                 Z->d_cos, Z->d_cos + Z->nx,
-                                                                 Z->nx, Z->ny, Z->Nu);
+    if (!Z->fac_ok) {   // first solve after a change of coefficients, faces or sides
+        zfactor_kernel<<<(unsigned)((plane + 127) / 128), 128, 0, s>>>(
+            Z->d_fac, Z->d_rows, Z->d_cos, Z->d_cos + Z->nx, Z->nx, Z->ny, Z->Nu);
+        ZCK(Z, cudaGetLastError());
+        Z->fac_ok = 1;
+    }
+    zthomas_kernel<<<(unsigned)((plane + 127) / 128), 128, 0, s>>>(W, Z->d_fac, Z->nx, Z->ny,
+                                                                 Z->Nu);
     ZCK(Z, cudaGetLastError());
     if ((mk = mark(3)) != HS_OK) return mk;
     if ((st = pass(HS_AXIS_Y, 2.0 / (Z->Ny + 1))) != HS_OK ||
@@ -618,6 +687,7 @@ size_t hs_zplan_workspace_bytes(hs_zplan_t Z) {
     if (!Z) return 0;
     size_t b = hs_workspace_bytes(Z->T) + (Z->d_rows ? (size_t)Z->Nu * 12 * sizeof(double2) : 0);
     b += (size_t)(Z->nx + Z->ny) * sizeof(double);
+    if (Z->d_fac) b += (size_t)6 * Z->Nu * Z->nx * Z->ny * sizeof(double);
     if (Z->d_dct[0]) b += (2 * (size_t)Z->Nx + 3) * sizeof(double2);
     if (Z->d_dct[1]) b += (2 * (size_t)Z->Ny + 3) * sizeof(double2);
     return b;
@@ -634,6 +704,7 @@ void hs_zplan_destroy(hs_zplan_t Z) {
     if (Z->T) hs_destroy(Z->T);
     if (Z->d_rows) cudaFree(Z->d_rows);
     if (Z->d_cos) cudaFree(Z->d_cos);
+    if (Z->d_fac) cudaFree(Z->d_fac);
     for (int a = 0; a < 2; ++a)
         if (Z->d_dct[a]) cudaFree(Z->d_dct[a]);
     if (Z->have_ev)
