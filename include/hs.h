@@ -11,6 +11,13 @@
  * discrete sine transform (DST-I) along x then y, one tridiagonal system in z
  * per sine mode (p, q), and the inverse transform.
  *
+ * Entry points: the single-problem plan (hs_plan ... hs_solve; FP64 and mixed
+ * paths, refinement, autotuning, host-buffer staging), an allocation-free
+ * residual (hs_residual_static), batches of uneven problems in one graph launch
+ * (hs_batch_*), the solver as the preconditioner of BiCGStab for k^2(x, y, z)
+ * (hs_precond_*), and the complex plan (hs_zplan_*, hs_zsolve*) for complex
+ * k(z), Robin z-faces and Neumann side faces (the general problem of Section 1).
+ *
  * Conventions shared by every entry point
  *  - Grids.  N_a interior points per axis, h_a = L_a / (N_a + 1) (Section 2).
  *    Interior arrays are C-ordered [l][j][i] (x fastest), the paper's row
