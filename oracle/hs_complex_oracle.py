@@ -74,10 +74,27 @@ class ZFaces:
 
 SIDE_DIRICHLET = 0
 SIDE_NEUMANN = 1
+SIDE_DN = 2   # Dirichlet on the low face, u_n = g on the high face
+SIDE_ND = 3   # u_n = g on the low face, Dirichlet on the high face
+
+
+def _lo_neu(kind):
+    return kind in (SIDE_NEUMANN, SIDE_ND)
+
+
+def _hi_neu(kind):
+    return kind in (SIDE_NEUMANN, SIDE_DN)
+
+
+def _nodes(N, kind):
+    """First and last node index of the unknowns along a side axis of N interior nodes:
+    the boundary node of a Neumann face is an unknown, that of a Dirichlet face is not."""
+    return (0 if _lo_neu(kind) else 1), (N + 1 if _hi_neu(kind) else N)
 
 
 def _n_unknown(N, kind):
-    return N + 2 if kind == SIDE_NEUMANN else N
+    first, last = _nodes(N, kind)
+    return last - first + 1
 
 
 def cosine_matrix(N):
@@ -92,64 +109,81 @@ def cosine_matrix(N):
 
 
 def side_transform(N, kind):
-    """(forward, inverse) matrices of one side axis: DST-I of the interior nodes, or DCT-I
-    of all nodes; inverse(forward(x)) = x."""
+    """(forward, inverse) matrices of one side axis, inverse(forward(x)) = x: DST-I of the
+    interior nodes (Dirichlet faces), DCT-I of all nodes (Neumann faces), or for one face
+    of each kind the quarter-wave transforms with theta_p = (2p - 1) pi / (2M), p = 1..M
+    (M = N + 1): sines over nodes 1..M (Neumann high face), cosines over nodes 0..N
+    (Neumann low face), weight 1/2 at the Neumann node."""
+    M = N + 1
     if kind == SIDE_NEUMANN:
         # the DCT-I is its own inverse up to 2/M: x_i = (2/M) sum_p w_p X_p cos(pi p i/M)
         C = cosine_matrix(N)
-        return C, (2.0 / (N + 1)) * C
+        return C, (2.0 / M) * C
+    if kind in (SIDE_DN, SIDE_ND):
+        p = np.arange(1, M + 1)
+        i = np.arange(1, M + 1) if kind == SIDE_DN else np.arange(0, M)
+        k = np.outer(2 * p - 1, i) % (4 * M)       # theta_p i as an integer multiple of pi/2M
+        Q = np.sin(np.pi * k / (2 * M)) if kind == SIDE_DN else np.cos(np.pi * k / (2 * M))
+        fwd = Q.copy()
+        fwd[:, -1 if kind == SIDE_DN else 0] *= 0.5
+        return fwd, (2.0 / M) * Q.T
     S = O.sine_matrix(N)
-    return S, (2.0 / (N + 1)) * S.T
+    return S, (2.0 / M) * S.T
 
 
 def side_cosines(N, kind):
     """cos(theta_p) of the modes of one side axis."""
     if kind == SIDE_NEUMANN:
         return np.cos(np.pi * np.arange(0, N + 2) / (N + 1))
+    if kind in (SIDE_DN, SIDE_ND):
+        M = N + 1
+        return np.cos(np.pi * (2 * np.arange(1, M + 1) - 1) / (2 * M))
     return O.mode_cosines(N)
 
 
-def _span(n_nodes, kind):
-    """Node indices covered by a padded unknown grid along a side axis: nodes -1..N+2 of
-    a Neumann axis (folded back into 0..N+1 by the even reflection), 0..N+1 otherwise."""
-    if kind == SIDE_NEUMANN:
-        idx = np.arange(-1, n_nodes + 1)
-        idx[0], idx[-1] = 1, n_nodes - 2
-        return idx
-    return np.arange(0, n_nodes)
+def _span(N, kind):
+    """Node indices covered by a padded unknown grid along a side axis (one node beyond
+    the unknowns on each side), nodes beyond a Neumann face folded back by the even
+    reflection (-1 -> 1, N + 2 -> N)."""
+    first, last = _nodes(N, kind)
+    idx = np.arange(first - 1, last + 2)
+    if _lo_neu(kind):
+        idx[0] = 1
+    if _hi_neu(kind):
+        idx[-1] = N
+    return idx
+
+
+def _axis_n(n_unknown, kind):
+    return n_unknown - int(_lo_neu(kind)) - int(_hi_neu(kind))
 
 
 def reflect_pad(U, sides, side_data=None, h=None):
-    """Pad a field on the unknown grid [..., ny, nx] by one node per side: zero beyond a
-    Dirichlet axis (its boundary nodes), beyond a Neumann axis the ghost of the central
-    difference of u_n = g, i.e. the even reflection plus 2 h g (outward normal, both
-    faces).  side_data = (x-lo, x-hi, y-lo, y-hi) arrays of u_n on the face node grids
-    ([planes][Ny+2] for x-faces, [planes][Nx+2] for y-faces; None = 0), reflected
-    evenly beyond their own edges; x-ghosts are set first, so a corner ghost carries the
-    data of both faces."""
+    """Pad a field on the unknown grid [..., ny, nx] by one node per side: beyond a
+    Dirichlet face its boundary node (u = 0), beyond a Neumann face the ghost of the
+    central difference of u_n = g, i.e. the even reflection plus 2 h g (outward normal).
+    side_data = (x-lo, x-hi, y-lo, y-hi) arrays of u_n on the face node grids
+    ([planes][Ny+2] for x-faces, [planes][Nx+2] for y-faces; None = 0, read on Neumann
+    faces only), reflected evenly beyond their own edges; x-ghosts are set first, so a
+    corner ghost carries the data of both faces."""
     U = np.asarray(U)
     pad = [(0, 0)] * (U.ndim - 2) + [(1, 1), (1, 1)]
     P = np.pad(U, pad)
     sd = [None] * 4 if side_data is None else list(side_data)
-    ny, nx = P.shape[-2] - 2, P.shape[-1] - 2
-    Ny = ny - 2 if sides[1] == SIDE_NEUMANN else ny
-    Nx = nx - 2 if sides[0] == SIDE_NEUMANN else nx
-    if sides[0] == SIDE_NEUMANN:
-        P[..., :, 0] = P[..., :, 2]
-        P[..., :, -1] = P[..., :, -3]
-        rows = _span(Ny + 2, sides[1])
-        for k, col in ((0, 0), (1, -1)):
+    Ny = _axis_n(P.shape[-2] - 2, sides[1])
+    Nx = _axis_n(P.shape[-1] - 2, sides[0])
+    rows = _span(Ny, sides[1])
+    for k, col, src, neu in ((0, 0, 2, _lo_neu(sides[0])), (1, -1, -3, _hi_neu(sides[0]))):
+        if neu:
+            P[..., :, col] = P[..., :, src]
             if sd[k] is not None:
-                g = np.asarray(sd[k])[..., rows]
-                P[..., :, col] = P[..., :, col] + 2.0 * h[0] * g
-    if sides[1] == SIDE_NEUMANN:
-        P[..., 0, :] = P[..., 2, :]
-        P[..., -1, :] = P[..., -3, :]
-        cols = _span(Nx + 2, sides[0])
-        for k, row in ((2, 0), (3, -1)):
+                P[..., :, col] = P[..., :, col] + 2.0 * h[0] * np.asarray(sd[k])[..., rows]
+    cols = _span(Nx, sides[0])
+    for k, row, src, neu in ((2, 0, 2, _lo_neu(sides[1])), (3, -1, -3, _hi_neu(sides[1]))):
+        if neu:
+            P[..., row, :] = P[..., src, :]
             if sd[k] is not None:
-                g = np.asarray(sd[k])[..., cols]
-                P[..., row, :] = P[..., row, :] + 2.0 * h[1] * g
+                P[..., row, :] = P[..., row, :] + 2.0 * h[1] * np.asarray(sd[k])[..., cols]
     return P
 
 
@@ -214,21 +248,13 @@ def _pad2(g):
 
 def _f_on_unknowns(f, sides):
     """f on [Nz+2][ny+2][nx+2]: the unknown grid of every plane plus one node per side
-    (a Dirichlet axis' boundary nodes as given, the even reflection beyond a Neumann one)."""
-    sx = slice(None) if sides[0] == SIDE_NEUMANN else slice(1, -1)
-    sy = slice(None) if sides[1] == SIDE_NEUMANN else slice(1, -1)
-    core = f[:, sy, sx]
-    P = np.zeros((f.shape[0], core.shape[1] + 2, core.shape[2] + 2), dtype=f.dtype)
-    P[:, 1:-1, 1:-1] = core
-    if sides[0] == SIDE_NEUMANN:
-        P[:, :, 0], P[:, :, -1] = P[:, :, 2], P[:, :, -3]
-    else:
-        P[:, 1:-1, 0], P[:, 1:-1, -1] = f[:, sy, 0], f[:, sy, -1]
-    if sides[1] == SIDE_NEUMANN:
-        P[:, 0, :], P[:, -1, :] = P[:, 2, :], P[:, -3, :]
-    else:
-        P[:, 0, 1:-1], P[:, -1, 1:-1] = f[:, 0, sx], f[:, -1, sx]
-    return P
+    (beyond a Dirichlet face its boundary node as given, beyond a Neumann face the even
+    reflection)."""
+    Ny, Nx = f.shape[1] - 2, f.shape[2] - 2
+    xs = _span(Nx, sides[0])
+    ys = _span(Ny, sides[1])
+    # every padded node is either a node of the grid or folded back onto one
+    return f[:, ys][:, :, xs]
 
 
 def rhs(order, h, K, zf, f_nodes, g_lo=None, g_hi=None, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET),

@@ -308,3 +308,68 @@ def test_neumann_ydata_anisotropic_converges(order):
     e = [_manufactured_neumann_ydata(N, order) for N in (7, 15, 31)]
     assert e[2] < e[1] < e[0]
     assert e[1] / e[2] >= 3.5, e
+
+
+DN, ND = CX.SIDE_DN, CX.SIDE_ND
+
+
+@pytest.mark.parametrize("kind", [DN, ND])
+@pytest.mark.parametrize("N", [1, 6, 15])
+def test_quarter_wave_pair_and_second_difference(kind, N):
+    """One Dirichlet and one Neumann face on an axis: the quarter-wave pair inverts and
+    diagonalises the second difference over the M = N + 1 unknown nodes with the
+    Dirichlet neighbour 0 at one end and the reflected ghost at the other."""
+    M = N + 1
+    T, Ti = CX.side_transform(N, kind)
+    assert T.shape == (M, M)
+    assert np.max(np.abs(Ti @ T - np.eye(M))) <= 1e-13
+    D = -2.0 * np.eye(M) + np.eye(M, k=1) + np.eye(M, k=-1)
+    if kind == DN:
+        D[-1, -2] = 2.0          # node M (Neumann): ghost M + 1 = node M - 1
+    else:
+        D[0, 1] = 2.0            # node 0 (Neumann): ghost -1 = node 1
+    lam = 2.0 * CX.side_cosines(N, kind) - 2.0
+    assert np.max(np.abs(T @ D @ Ti - np.diag(lam))) <= 1e-12
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("sides", [(DN, DIR), (ND, NEU), (DN, ND), (NEU, DN)])
+@pytest.mark.parametrize("faces", [(R, R), (D, D)])
+def test_mixed_sides_separated_equals_dense(order, sides, faces):
+    shape = (5, 4, 4)
+    Nx, Ny, Nz = shape
+    h, K, f, rs = _neumann_case(shape, 80 + order + 4 * sides[0] + sides[1] + 7 * faces[1])
+    nx, ny = CX._n_unknown(Nx, sides[0]), CX._n_unknown(Ny, sides[1])
+    g_lo, g_hi = _crand(rs, (ny, nx)), _crand(rs, (ny, nx))
+    sd = (_crand(rs, (Nz + 2, Ny + 2)), _crand(rs, (Nz + 2, Ny + 2)),
+          _crand(rs, (Nz + 2, Nx + 2)), _crand(rs, (Nz + 2, Nx + 2)))
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    U, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi, sides, sd)
+    Ud = CX.solve_dense(order, h, K, zf, f, g_lo, g_hi, sides, sd)
+    assert U.shape == (Nz + 2, ny, nx)
+    assert O.max_rel_diff(U, Ud) <= 1e-11
+
+
+def _manufactured_mixed(N, order, kind, kappa=2.0):
+    """x-profile sin(pi x/2) (u = 0 at x = 0, u_x = 0 at x = 1: kind DN) or cos(pi x/2)
+    (u_x = 0 at x = 0, u = 0 at x = 1: kind ND), times cos(2 pi y) (Neumann y) and
+    e^{i kappa z} (Dirichlet z-faces)."""
+    h = (1.0 / (N + 1),) * 3
+    x = np.arange(N + 2) * h[0]
+    z = x.copy()
+    K = (35.0 + 6.0j) * (1.0 + 0.5 * z)
+    px = np.sin(0.5 * np.pi * x) if kind == DN else np.cos(0.5 * np.pi * x)
+    u = (px[None, None, :] * np.cos(2 * np.pi * x)[None, :, None]
+         * np.exp(1j * kappa * z)[:, None, None])
+    f = (-0.25 * np.pi ** 2 - 4 * np.pi ** 2 - kappa ** 2 + K[:, None, None]) * u
+    x0, x1 = CX._nodes(N, kind)
+    ue = u[:, :, x0:x1 + 1]                     # every y node (Neumann y), the unknown x nodes
+    U, _ = CX.solve(order, h, K, CX.ZFaces(), f, ue[0], ue[-1], (kind, NEU))
+    return np.max(np.abs(U - ue))
+
+
+@pytest.mark.parametrize("kind", [DN, ND])
+def test_mixed_sides_manufactured_converges(kind):
+    e = [_manufactured_mixed(N, 4, kind) for N in (7, 15, 31)]
+    assert e[2] < e[1] < e[0]
+    assert e[1] / e[2] >= 12.0, e
