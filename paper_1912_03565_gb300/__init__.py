@@ -557,6 +557,11 @@ class Solver:
                             precision, max_rhs)
 
     def set_coeff(self, c0, c1=None, c2=None, cd_variant=HS_CD_CORRECTED):
+        import numpy as np
+        n = self.shape[0] + 2
+        for name, c in (("c0", c0), ("c1", c1), ("c2", c2)):
+            if c is not None and np.asarray(c).size != n:
+                raise ValueError(f"{name} must hold Nz + 2 = {n} values")
         return hs_set_coeff(self.plan, c0, c1, c2, cd_variant)
 
     def solve(self, f, u, f_dtype=HS_F64, rhs_kind=HS_RHS_NODAL, faces=None, fnn=None, nrhs=1,
@@ -605,7 +610,9 @@ class ZSolver:
 
     def set_coeff(self, K):
         import numpy as np
-        K = np.asarray(K, dtype=np.complex128)
+        K = np.asarray(K, dtype=np.complex128).ravel()
+        if K.size != self.shape[2] + 2:
+            raise ValueError(f"K must hold Nz + 2 = {self.shape[2] + 2} values")
         buf = np.ascontiguousarray(np.stack([K.real, K.imag], axis=-1).ravel())
         arr = (ctypes.c_double * buf.size)(*buf.tolist())
         return self._err(load().hs_zplan_set_coeff(self.plan, arr), "hs_zplan_set_coeff")
