@@ -72,3 +72,28 @@ def test_binding_fails_loudly_without_library(tmp_path):
             H.load(str(tmp_path / "missing.so"))
         finally:
             H._lib = H._lib_backup
+
+
+def test_complex_plan_and_host_io_argument_validation(lib):
+    """The complex plan, host-I/O and callback entry points reject bad arguments before
+    touching the device."""
+    h = ctypes.c_void_p()
+    assert lib.hs_zplan(None, 4, 4, 4, 1.0, 1.0, 1.0, 4) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_zplan(ctypes.byref(h), 0, 4, 4, 1.0, 1.0, 1.0, 4) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_zplan(ctypes.byref(h), 4, 4, 4, 1.0, 1.0, 1.0, 6) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_zplan(ctypes.byref(h), 4, 4, 4, 1.0, -1.0, 1.0, 4) == H.HS_ERR_INVALID_ARG
+    assert h.value is None
+    assert lib.hs_zplan_set_coeff(None, None) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_zplan_set_faces(None, 0, None, None, 0, None, None) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_zplan_set_sides(None, 0, 0) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_zsolve(None, None, None, None, None, None) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_zsolve_ex(None, None, None, None, None, None, None) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_zplan_set_stage_timing(None, 1) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_zplan_stage_times(None, None) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_zplan_workspace_bytes(None) == 0
+    assert lib.hs_zplan_last_error(None).decode() == "no plan"
+    lib.hs_zplan_destroy(None)
+    assert lib.hs_set_host_io(None, 0) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_host_io_wait(None, None) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_set_coeff_fn(None, H.HS_COEFF_FN(lambda z, d, u: 0.0), None, 0) == \
+        H.HS_ERR_INVALID_ARG
