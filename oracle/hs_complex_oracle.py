@@ -187,10 +187,35 @@ def reflect_pad(U, sides, side_data=None, h=None):
     return P
 
 
-def complex_coefficients(order, h, K):
-    """C[l-1, nu, m] (complex) for interior rows l = 1..Nz; K complex, length Nz + 2."""
+def complex_coefficients6(h, K, Kz, Kzz):
+    """6th-order rows (Section 3.4, uniform h) for complex K, K_z, K_zz (length Nz + 2):
+    the printed coefficients are polynomials in K (K^2 in d_l, K_z K in d_{l+-1}), so they
+    are evaluated in complex arithmetic as written."""
+    hh = h[2]
+    K = np.asarray(K, dtype=np.complex128)
+    Kz = np.asarray(Kz, dtype=np.complex128)[1:-1]
+    Kzz = np.asarray(Kzz, dtype=np.complex128)[1:-1]
+    Km, Kc, Kp = K[:-2], K[1:-1], K[2:]
+    h2, h3, h4 = hh ** 2, hh ** 3, hh ** 4
+    C = np.zeros((K.shape[0] - 2, 3, 4), dtype=np.complex128)
+    C[:, O.LOW, O.A_] = C[:, O.UPP, O.A_] = 1.0 / 30.0
+    C[:, O.LOW, O.B_] = C[:, O.LOW, O.C_] = 0.1 + h2 * Km / 90.0 - h3 * Kz / 120.0
+    C[:, O.UPP, O.B_] = C[:, O.UPP, O.C_] = 0.1 + h2 * Kp / 90.0 + h3 * Kz / 120.0
+    C[:, O.LOW, O.D_] = 7.0 / 15.0 - h2 * Km / 90.0 - (h3 * Kz / 20.0) * (1.0 / 3.0 + h2 * Km / 6.0)
+    C[:, O.UPP, O.D_] = 7.0 / 15.0 - h2 * Kp / 90.0 + (h3 * Kz / 20.0) * (1.0 / 3.0 + h2 * Kp / 6.0)
+    C[:, O.MID, O.A_] = 0.1 + h2 * Kc / 90.0
+    C[:, O.MID, O.B_] = C[:, O.MID, O.C_] = 7.0 / 15.0 - h2 * Kc / 90.0
+    C[:, O.MID, O.D_] = -64.0 / 15.0 + 14.0 * h2 * Kc / 15.0 - h4 * Kc * Kc / 20.0 + h4 * Kzz / 20.0
+    return C
+
+
+def complex_coefficients(order, h, K, Kz=None, Kzz=None):
+    """C[l-1, nu, m] (complex) for interior rows l = 1..Nz; K complex, length Nz + 2
+    (order 6 also needs K_z and K_zz)."""
+    if order == 6:
+        return complex_coefficients6(h, K, Kz, Kzz)
     if order not in (2, 4):
-        raise ValueError("complex coefficients: orders 2 and 4")
+        raise ValueError("complex coefficients: orders 2, 4 and 6")
     K = np.asarray(K, dtype=np.complex128)
     zero = np.zeros(K.shape)
     base = O.stencil_coefficients(order, O.HELMHOLTZ, h, zero)
@@ -212,11 +237,11 @@ def robin_row(h, K_l, alpha, beta, side):
     return R
 
 
-def row_table(order, h, K, zf):
+def row_table(order, h, K, zf, Kz=None, Kzz=None):
     """Coefficient blocks of the unknown rows l0..l1: array (Nu, 3, 4) complex."""
     K = np.asarray(K, dtype=np.complex128)
     Nz = K.shape[0] - 2
-    Ci = complex_coefficients(order, h, K)
+    Ci = complex_coefficients(order, h, K, Kz, Kzz)
     rows = []
     if zf.lo == ROBIN:
         rows.append(robin_row(h, K[0], zf.alpha[0], zf.beta[0], -1))
@@ -257,9 +282,32 @@ def _f_on_unknowns(f, sides):
     return f[:, ys][:, :, xs]
 
 
+def _interior_rhs(order, h, fu, K, Kz=None, fnn=None):
+    """R_h f on the interior planes for complex f (padded unknown grid fu).  Orders 2 and 4:
+    the real operator on Re f and Im f.  Order 6 (R6, Dirichlet sides): the K-free part
+    likewise (with the face data f_nn split the same way) plus the complex terms
+    h^2 (-h^2 K f / 20 + h^3 K_z (f_{l+1} - f_{l-1}) / 120)."""
+    if order != 6:
+        return (O.rhs_operator(order, O.HELMHOLTZ, h, fu.real)
+                + 1j * O.rhs_operator(order, O.HELMHOLTZ, h, fu.imag))
+    hh = h[2]
+    zero = np.zeros(fu.shape[0])
+    fnn = [None] * 6 if fnn is None else list(fnn)
+    part = lambda g: [None if a is None else g(np.asarray(a, dtype=np.complex128)) for a in fnn]
+    F = (O.rhs_operator(6, O.HELMHOLTZ, h, fu.real, zero, zero, part(np.real))
+         + 1j * O.rhs_operator(6, O.HELMHOLTZ, h, fu.imag, zero, zero, part(np.imag)))
+    Kc = np.asarray(K, dtype=np.complex128)[1:-1][:, None, None]
+    Kzc = np.asarray(Kz, dtype=np.complex128)[1:-1][:, None, None]
+    fc = fu[1:-1, 1:-1, 1:-1]
+    dz1 = fu[2:, 1:-1, 1:-1] - fu[:-2, 1:-1, 1:-1]
+    return F + hh * hh * (-hh * hh * Kc * fc / 20.0 + hh ** 3 * Kzc * dz1 / 120.0)
+
+
 def rhs(order, h, K, zf, f_nodes, g_lo=None, g_hi=None, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET),
-        side_data=None):
+        side_data=None, Kz=None, Kzz=None, fnn=None):
     """Right-hand side of the unknown rows: array (Nu, ny, nx) complex."""
+    if order == 6 and sides != (SIDE_DIRICHLET, SIDE_DIRICHLET):
+        raise ValueError("6th-order complex rows: Dirichlet side faces")
     hz = h[2]
     f = np.asarray(f_nodes, dtype=np.complex128)
     Nz = f.shape[0] - 2
@@ -267,9 +315,8 @@ def rhs(order, h, K, zf, f_nodes, g_lo=None, g_hi=None, sides=(SIDE_DIRICHLET, S
     ny, nx = fu.shape[1] - 2, fu.shape[2] - 2
     glo, ghi = _face(g_lo, ny, nx), _face(g_hi, ny, nx)
     # R_h of the order on the padded unknown grid (interior planes 1..Nz)
-    Fi = (O.rhs_operator(order, O.HELMHOLTZ, h, fu.real)
-          + 1j * O.rhs_operator(order, O.HELMHOLTZ, h, fu.imag))
-    Ci = complex_coefficients(order, h, K)
+    Fi = _interior_rhs(order, h, fu, K, Kz, fnn)
+    Ci = complex_coefficients(order, h, K, Kz, Kzz)
     # Dirichlet faces: their known plane leaves rows 1 / Nz through the stencil
     if zf.lo == DIRICHLET:
         Fi[0] -= _plane_part(Ci[0, O.LOW], reflect_pad(glo, sides))
@@ -286,7 +333,7 @@ def rhs(order, h, K, zf, f_nodes, g_lo=None, g_hi=None, sides=(SIDE_DIRICHLET, S
     if side_data is not None and any(d is not None for d in side_data):
         # Neumann data: the stencil weights of the ghost nodes times their data parts
         zero = np.zeros((Nz + 2, ny, nx), dtype=np.complex128)
-        F = F - apply_operator(order, h, K, zf, zero, None, None, sides, side_data)
+        F = F - apply_operator(order, h, K, zf, zero, None, None, sides, side_data, Kz, Kzz)
     return F
 
 
@@ -314,13 +361,13 @@ def solve_rows(R, F, Nx, Ny, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
 
 
 def solve(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
-          sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), side_data=None):
+          sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), side_data=None, Kz=None, Kzz=None, fnn=None):
     """Solution on every plane l = 0..Nz+1 (unknown grid in x, y): complex (Nz+2, ny, nx)."""
     f = np.asarray(f_nodes, dtype=np.complex128)
     Nz, Ny, Nx = f.shape[0] - 2, f.shape[1] - 2, f.shape[2] - 2
     ny, nx = _n_unknown(Ny, sides[1]), _n_unknown(Nx, sides[0])
-    R = row_table(order, h, K, zf)
-    F = rhs(order, h, K, zf, f, g_lo, g_hi, sides, side_data)
+    R = row_table(order, h, K, zf, Kz, Kzz)
+    F = rhs(order, h, K, zf, f, g_lo, g_hi, sides, side_data, Kz, Kzz, fnn)
     Uu, ratio = solve_rows(R, F, Nx, Ny, sides)
     l0, l1 = zf.unknown_planes(Nz)
     U = np.zeros((Nz + 2, ny, nx), dtype=np.complex128)
@@ -338,7 +385,7 @@ def solve(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
 
 
 def apply_operator(order, h, K, zf, U_all, g_lo=None, g_hi=None,
-                   sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), side_data=None):
+                   sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), side_data=None, Kz=None, Kzz=None):
     """Rows l0..l1 of (A U - data terms): U_all on planes 0..Nz+1 (interior x, y).
 
     Interior rows: the 27-point stencil with the complex table.  Robin rows: the
@@ -351,7 +398,7 @@ def apply_operator(order, h, K, zf, U_all, g_lo=None, g_hi=None,
     Nz, Ny, Nx = U_all.shape[0] - 2, U_all.shape[1], U_all.shape[2]
     # beyond a Neumann side: the ghost u_-1 = u_1 + 2 h g of u_n = g, built explicitly
     P = reflect_pad(U_all, sides, side_data, h)
-    Ci = complex_coefficients(order, h, K)
+    Ci = complex_coefficients(order, h, K, Kz, Kzz)
     out = []
     glo, ghi = _face(g_lo, Ny, Nx), _face(g_hi, Ny, Nx)
 
@@ -380,20 +427,20 @@ def apply_operator(order, h, K, zf, U_all, g_lo=None, g_hi=None,
     return np.array(out)
 
 
-def rhs_direct(order, h, f_nodes, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
+def rhs_direct(order, h, f_nodes, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), K=None, Kz=None,
+               fnn=None):
     """The scheme's f-side on every plane that can be a row: R_h f on interior rows
-    (real operator on Re f and Im f, f reflected beyond a Neumann side), h_z^2 f on the
-    two face planes."""
+    (f reflected beyond a Neumann side), h_z^2 f on the two face planes."""
     hz = h[2]
     f = np.asarray(f_nodes, dtype=np.complex128)
     fu = _f_on_unknowns(f, sides)
-    Fi = (O.rhs_operator(order, O.HELMHOLTZ, h, fu.real)
-          + 1j * O.rhs_operator(order, O.HELMHOLTZ, h, fu.imag))
+    Fi = _interior_rhs(order, h, fu, K, Kz, fnn)
     return hz * hz * fu[0, 1:-1, 1:-1], Fi, hz * hz * fu[-1, 1:-1, 1:-1]
 
 
 def solve_dense(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
-                sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), side_data=None):
+                sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), side_data=None, Kz=None, Kzz=None,
+                fnn=None):
     """Brute force: the matrix of apply_operator (columns from unit vectors), its data
     part from the operator at U = 0, and a dense complex LU solve."""
     f = np.asarray(f_nodes, dtype=np.complex128)
@@ -406,7 +453,7 @@ def solve_dense(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
         base[0] = _face(g_lo, Ny, Nx)
     if zf.hi == DIRICHLET:
         base[Nz + 1] = _face(g_hi, Ny, Nx)
-    data = apply_operator(order, h, K, zf, base, g_lo, g_hi, sides, side_data).ravel()
+    data = apply_operator(order, h, K, zf, base, g_lo, g_hi, sides, side_data, Kz, Kzz).ravel()
     n = Nu * Ny * Nx
     A = np.zeros((n, n), dtype=np.complex128)
     zero_faces = ZFaces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
@@ -415,8 +462,8 @@ def solve_dense(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
         e[k] = 1.0
         Ue = np.zeros((Nz + 2, Ny, Nx), dtype=np.complex128)
         Ue[l0:l1 + 1] = e.reshape(Nu, Ny, Nx)
-        A[:, k] = apply_operator(order, h, K, zero_faces, Ue, sides=sides).ravel()
-    flo, Fi, fhi = rhs_direct(order, h, f, sides)
+        A[:, k] = apply_operator(order, h, K, zero_faces, Ue, sides=sides, Kz=Kz, Kzz=Kzz).ravel()
+    flo, Fi, fhi = rhs_direct(order, h, f, sides, K, Kz, fnn)
     rows = ([flo] if zf.lo == ROBIN else []) + list(Fi) + ([fhi] if zf.hi == ROBIN else [])
     b = np.array(rows).ravel() - data
     x = np.linalg.solve(A, b).reshape(Nu, Ny, Nx)

@@ -373,3 +373,92 @@ def test_mixed_sides_manufactured_converges(kind):
     e = [_manufactured_mixed(N, 4, kind) for N in (7, 15, 31)]
     assert e[2] < e[1] < e[0]
     assert e[1] / e[2] >= 12.0, e
+
+
+def _case6(shape, seed):
+    """Uniform h (6th order): box ((N_a + 1) h); complex K with K_z, K_zz; f and the six
+    face arrays f_nn complex."""
+    Nx, Ny, Nz = shape
+    rs = np.random.RandomState(seed)
+    hh = 1.0 / (max(shape) + 1)
+    h = (hh, hh, hh)
+    z = np.arange(Nz + 2) * hh
+    c = (30.0 + 5.0 * rs.uniform()) * (1.0 + 0.2j)
+    K = c * (1.0 + 0.5 * z + 0.3 * z * z)
+    Kz = c * (0.5 + 0.6 * z)
+    Kzz = c * 0.6 + 0.0 * z
+    f = _crand(rs, (Nz + 2, Ny + 2, Nx + 2))
+    fnn = [_crand(rs, (Nz + 2, Ny + 2)), _crand(rs, (Nz + 2, Ny + 2)),
+           _crand(rs, (Nz + 2, Nx + 2)), _crand(rs, (Nz + 2, Nx + 2)),
+           _crand(rs, (Ny + 2, Nx + 2)), _crand(rs, (Ny + 2, Nx + 2))]
+    return h, K, Kz, Kzz, f, fnn, rs
+
+
+def test_complex_coefficients6_reduce_to_real():
+    rs = np.random.RandomState(3)
+    h = (0.1, 0.1, 0.1)
+    K, Kz, Kzz = rs.uniform(10, 50, 9), rs.uniform(-20, 20, 9), rs.uniform(-50, 50, 9)
+    C = O.stencil_coefficients(6, O.HELMHOLTZ, h, K, Kz, Kzz)
+    Cc = CX.complex_coefficients(6, h, K, Kz, Kzz)
+    assert np.max(np.abs(Cc.imag)) == 0.0
+    assert np.max(np.abs(Cc.real - C)) <= 1e-15 * np.max(np.abs(C))
+
+
+@pytest.mark.parametrize("faces", [(R, R), (D, D), (R, D)])
+def test_order6_separated_equals_dense(faces):
+    shape = (5, 4, 6)
+    h, K, Kz, Kzz, f, fnn, rs = _case6(shape, 90 + 2 * faces[0] + faces[1])
+    Nx, Ny, Nz = shape
+    g_lo, g_hi = _crand(rs, (Ny, Nx)), _crand(rs, (Ny, Nx))
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    U, _ = CX.solve(6, h, K, zf, f, g_lo, g_hi, Kz=Kz, Kzz=Kzz, fnn=fnn)
+    Ud = CX.solve_dense(6, h, K, zf, f, g_lo, g_hi, Kz=Kz, Kzz=Kzz, fnn=fnn)
+    assert O.max_rel_diff(U, Ud) <= 1e-11
+
+
+def test_order6_real_case_is_the_real_oracle():
+    shape = (7, 6, 5)
+    Nx, Ny, Nz = shape
+    h, K, Kz, Kzz, f, fnn, rs = _case6(shape, 97)
+    K, Kz, Kzz, f = K.real, Kz.real, Kzz.real, f.real
+    fnn = [a.real for a in fnn]
+    f[:, 0, :] = f[:, -1, :] = 0.0
+    f[:, :, 0] = f[:, :, -1] = 0.0
+    g_lo, g_hi = rs.uniform(-1, 1, (Ny, Nx)), rs.uniform(-1, 1, (Ny, Nx))
+    U, _ = CX.solve(6, h, K, CX.ZFaces(), f, g_lo, g_hi, Kz=Kz, Kzz=Kzz, fnn=fnn)
+    zl, zh = np.zeros((Ny + 2, Nx + 2)), np.zeros((Ny + 2, Nx + 2))
+    zl[1:-1, 1:-1], zh[1:-1, 1:-1] = g_lo, g_hi
+    C = O.stencil_coefficients(6, O.HELMHOLTZ, h, K, Kz, Kzz)
+    F = O.assemble_rhs(6, O.HELMHOLTZ, h, f, C, K, Kz, (None, None, None, None, zl, zh), fnn)
+    Ur, _ = O.solve_assembled(C, F)
+    assert np.max(np.abs(U.imag)) == 0.0
+    assert O.max_rel_diff(U[1:-1].real, Ur) <= 1e-12
+
+
+def _manufactured6(N, kappa=2.5, c=(40.0, 8.0)):
+    """u = sin(pi x) sin(2 pi y) e^{i kappa z}, K = c (1 + z/2) (complex): f and its
+    normal second derivatives on the z-faces analytic (zero on the x and y faces)."""
+    hh = 1.0 / (N + 1)
+    h = (hh, hh, hh)
+    x = np.arange(N + 2) * hh
+    z = x.copy()
+    cc = c[0] + 1j * c[1]
+    K, Kz, Kzz = cc * (1.0 + 0.5 * z), cc * 0.5 + 0.0 * z, 0.0 * z + 0.0j
+    s = np.sin(np.pi * x)[None, None, :] * np.sin(2 * np.pi * x)[None, :, None]
+    ez = np.exp(1j * kappa * z)
+    u = s * ez[:, None, None]
+    q = -5.0 * np.pi ** 2 - kappa ** 2
+    f = (q + K[:, None, None]) * u
+    # f = g(z) s(x, y) with g = (q + K) e^{i kappa z}: g'' = (2 i kappa K' - kappa^2 (q + K)) e^{..}
+    g2 = (2j * kappa * Kz - kappa ** 2 * (q + K)) * ez
+    sxy = s[0]
+    fnn = [None, None, None, None, g2[0] * sxy, g2[-1] * sxy]
+    U, _ = CX.solve(6, h, K, CX.ZFaces(), f, u[0, 1:-1, 1:-1], u[-1, 1:-1, 1:-1],
+                    Kz=Kz, Kzz=Kzz, fnn=fnn)
+    return np.max(np.abs(U - u[:, 1:-1, 1:-1]))
+
+
+def test_order6_manufactured_complex_solution_converges():
+    e = [_manufactured6(N) for N in (7, 15, 31)]
+    assert e[2] < e[1] < e[0]
+    assert e[1] / e[2] >= 40.0, e
