@@ -462,3 +462,34 @@ def test_order6_manufactured_complex_solution_converges():
     e = [_manufactured6(N) for N in (7, 15, 31)]
     assert e[2] < e[1] < e[0]
     assert e[1] / e[2] >= 40.0, e
+
+
+@pytest.mark.parametrize("N", [1, 6, 15, 31])
+def test_side_transforms_are_the_library_dst_dct(N):
+    """The four side-axis transforms against scipy's unnormalised trigonometric
+    transforms (an independent implementation): Dirichlet faces = DST-I / 2 over the
+    interior nodes, Neumann faces = DCT-I / 2 over all nodes, Dirichlet low with
+    Neumann high = DST-III / 2 over nodes 1..M, Neumann low with Dirichlet high =
+    DCT-III / 2 over nodes 0..N.  The quarter-wave transform is also the odd outputs
+    of a DST-I of length 2M over the line extended evenly about the Neumann node."""
+    sfft = pytest.importorskip("scipy.fft")
+    M = N + 1
+    g = np.random.default_rng(N)
+    x = g.standard_normal(N)
+    T, _ = CX.side_transform(N, DIR)
+    assert np.max(np.abs(T @ x - sfft.dst(x, type=1) / 2)) <= 1e-12
+    x = g.standard_normal(M + 1)
+    T, _ = CX.side_transform(N, NEU)
+    assert np.max(np.abs(T @ x - sfft.dct(x, type=1) / 2)) <= 1e-12
+    x = g.standard_normal(M)
+    T, _ = CX.side_transform(N, DN)
+    assert np.max(np.abs(T @ x - sfft.dst(x, type=3) / 2)) <= 1e-12
+    ext = np.concatenate([x, x[-2::-1]])              # nodes 1..2M-1, even about node M
+    assert ext.size == 2 * M - 1
+    assert np.max(np.abs(T @ x - sfft.dst(ext, type=1)[0::2] / 4)) <= 1e-12
+    T, _ = CX.side_transform(N, ND)
+    assert np.max(np.abs(T @ x - sfft.dct(x, type=3) / 2)) <= 1e-12
+    # ND is DN of the reversed line (node i -> M - i) with alternating signs
+    TDN, _ = CX.side_transform(N, DN)
+    sign = (-1.0) ** np.arange(M)
+    assert np.max(np.abs(T @ x - sign * (TDN @ x[::-1]))) <= 1e-12
