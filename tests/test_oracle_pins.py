@@ -274,6 +274,37 @@ def test_dst2_roundtrip():
     assert np.allclose(O.dst2_inverse(O.dst2_forward(F)), F, atol=1e-13)
 
 
+def test_dst2_forward_is_the_library_dst():
+    """The plane transform against scipy's unnormalised DST-I (2 sum x_n sin(...)) along
+    the two last axes, for non-square planes (a transposed pair of sine matrices fails)."""
+    sfft = pytest.importorskip("scipy.fft")
+    rs = np.random.RandomState(5)
+    F = rs.standard_normal((3, 11, 6))
+    ref = sfft.dstn(F, type=1, axes=(1, 2)) / 4.0
+    assert np.max(np.abs(O.dst2_forward(F) - ref)) <= 1e-12
+
+
+def test_thomas_is_the_library_banded_solve():
+    """The textbook tridiagonal LU against LAPACK's banded solver (partial pivoting) on
+    diagonally dominant rows, several right-hand sides; and its pivot ratio."""
+    sla = pytest.importorskip("scipy.linalg")
+    rs = np.random.RandomState(8)
+    n, m = 17, 4
+    lower = rs.uniform(-1, 1, (n, m))
+    upper = rs.uniform(-1, 1, (n, m))
+    diag = 2.5 + rs.uniform(0, 1, (n, m))
+    rhs = rs.standard_normal((n, m))
+    w, ratio = O.thomas(lower, diag, upper, rhs)
+    for j in range(m):
+        ab = np.zeros((3, n))
+        ab[0, 1:] = upper[:-1, j]
+        ab[1] = diag[:, j]
+        ab[2, :-1] = lower[1:, j]
+        ref = sla.solve_banded((1, 1), ab, rhs[:, j])
+        assert np.max(np.abs(w[:, j] - ref)) <= 1e-13 * max(1.0, np.abs(ref).max())
+    assert 0 < ratio <= 1
+
+
 def test_single_mode_reduces_to_1d_system():
     """F = sin(p pi x) sin(q pi y) phi(z): U = same mode times T_pq^{-1} phi (dense 1-D solve)."""
     Nx, Ny, Nz = 12, 9, 10
