@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for complex k(z) and Robin z-faces.
+"""FP64 CPU oracle for complex k(z), Robin z-faces and Neumann side faces.
 
 TEST INFRASTRUCTURE ONLY (same rule as hs_oracle: only the test-suite, the
 smoke check and the benchmark's CPU legs may import it; the solver library
@@ -9,11 +9,15 @@ only, u = 0 on the four side faces, and alpha u_z + beta u = g(x, y) on the two
 z-faces with complex alpha, beta.  The schemes and the direct solver of
 Sections 3 and 3.6 are worked out for Dirichlet data; the compact closure of a
 Robin face belongs to a cited work that the paper does not reproduce.  This
-module takes, for orders 2 and 4:
+module takes, for orders 2, 4 and 6:
 
-  * interior rows l = 1..Nz: the compact rows of Sections 3.2 / 3.3 with
-    complex K = k^2.  Every coefficient is affine in K, so the complex table is
-    the real table of Re K plus i times the K-part of the real table of Im K;
+  * interior rows l = 1..Nz: the compact rows of Sections 3.2 - 3.4 with
+    complex K = k^2.  At orders 2 and 4 every coefficient is affine in K, so
+    the complex table is the real table of Re K plus i times the K-part of the
+    real table of Im K; the 6th-order rows (Section 3.4, uniform h) are
+    polynomials in K and K_z and are evaluated in complex arithmetic as
+    printed, as is the K-dependent part of the 6th-order right-hand side
+    (Dirichlet side faces only);
   * a Dirichlet z-face: its plane holds g, moved into the next row's right-hand
     side through the stencil (as for the real problem);
   * a Robin z-face: its plane is unknown and its row is the second-order
@@ -31,18 +35,21 @@ Nz + 1 for a Robin hi face, else Nz).  Side faces stay Dirichlet, so Section
 tridiagonal systems in z; these are solved by the textbook recurrence.
 
 Neumann side faces (the extension Section 1 names): a side axis may instead
-carry u_n = 0 on both of its faces.  Its boundary nodes become unknowns, the
-operator sees the even reflection u_-1 = u_1 (the central difference of
-u_x = 0), f is reflected the same way, and the sine transform of that axis is
-replaced by the cosine transform DCT-I over the nodes 0..N+1, whose modes
-cos(p pi i / (N+1)), p = 0..N+1, diagonalise the reflected second difference
-with the same eigenvalue formula (Section 3.6) -- the per-row coefficients are
-unchanged.
+carry u_n = g on both of its faces (g = 0 or per-face data).  Its boundary
+nodes become unknowns, the operator sees the ghost of the central difference of
+the face condition (the even reflection u_-1 = u_1 plus 2 h g), f is reflected
+evenly, and the sine transform of that axis is replaced by the cosine
+transform DCT-I over the nodes 0..N+1, whose modes cos(p pi i / (N+1)),
+p = 0..N+1, diagonalise the reflected second difference with the same
+eigenvalue formula (Section 3.6) -- the per-row coefficients are unchanged.
+An axis with one face of each kind (SIDE_DN, SIDE_ND) takes the quarter-wave
+transforms, modes of angle (2p - 1) pi / (2 (N + 1)), p = 1..N+1.
 
 Arrays: f on the node grid [Nz+2][Ny+2][Nx+2] (complex; side-face nodes of a
 Dirichlet axis are read by the 4th-order operator as given); the unknown grid
 of a plane is [ny][nx] with nx = Nx + 2 for a Neumann x-axis (nodes 0..Nx+1),
-else Nx (nodes 1..Nx), and likewise ny; face data g_lo, g_hi on that grid of
+Nx + 1 for an axis with one Neumann face (nodes 1..Nx+1 or 0..Nx), else Nx
+(nodes 1..Nx), and likewise ny; face data g_lo, g_hi on that grid of
 the z-face (complex; None = 0); the solution on all planes [Nz+2][ny][nx]
 (Dirichlet planes hold g).
 """
