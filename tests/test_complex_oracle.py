@@ -16,7 +16,10 @@ What fixes it, independently of its own code paths:
       second difference with eigenvalues 2 cos(theta_p) - 2, theta_p = p pi/(N+1),
       p = 0..N+1; the separated solve equals the dense solve of the operator built
       with explicit reflected ghosts; swapping x and y swaps the solution; a
-      manufactured cos-cos solution converges.
+      manufactured cos-cos solution converges;
+  (h) the side transforms equal scipy's DST-I, DCT-I, DST-III and DCT-III;
+  (i) mutations: a mistake planted in the oracle (Robin term sign, quarter-wave
+      weight, Neumann data sign, mode angle, 6th-order K_z sign) makes a pin fail.
 """
 import numpy as np
 import pytest
@@ -493,3 +496,84 @@ def test_side_transforms_are_the_library_dst_dct(N):
     TDN, _ = CX.side_transform(N, DN)
     sign = (-1.0) ** np.arange(M)
     assert np.max(np.abs(T @ x - sign * (TDN @ x[::-1]))) <= 1e-12
+
+
+# ----------------------------------------------------------------- mutations
+# A plausible mistake planted in the oracle (on the CPU, through monkeypatch) must make
+# one of the pins above fail.
+
+
+def test_planted_robin_sign_is_caught(monkeypatch):
+    """Robin row with the sign of the eliminated face term flipped."""
+    orig = CX.robin_row
+
+    def mutated(h, K_l, alpha, beta, side):
+        Rb = orig(h, K_l, alpha, beta, side)
+        Rb[O.MID, O.D_] += side * 4.0 * h[2] * beta / alpha
+        return Rb
+
+    monkeypatch.setattr(CX, "robin_row", mutated)
+    with pytest.raises(AssertionError):
+        test_separated_solve_equals_dense_solve(4, (R, R))
+
+
+def test_planted_quarter_wave_weight_is_caught(monkeypatch):
+    """Quarter-wave forward transform without the weight 1/2 at the Neumann node."""
+    orig = CX.side_transform
+
+    def mutated(N, kind):
+        fwd, inv = orig(N, kind)
+        if kind == DN:
+            fwd = fwd.copy()
+            fwd[:, -1] *= 2.0
+        return fwd, inv
+
+    monkeypatch.setattr(CX, "side_transform", mutated)
+    with pytest.raises(AssertionError):
+        test_quarter_wave_pair_and_second_difference(DN, 6)
+    with pytest.raises(AssertionError):
+        test_mixed_sides_separated_equals_dense(4, (DN, DIR), (R, R))
+
+
+def test_planted_neumann_data_sign_is_caught(monkeypatch):
+    """Ghost of u_n = g built with the inward normal (data sign flipped) in every code
+    path: the separated and dense solves still agree, the manufactured solution does
+    not converge."""
+    orig = CX.reflect_pad
+
+    def mutated(U, sides, side_data=None, h=None):
+        if side_data is not None:
+            side_data = [None if d is None else -np.asarray(d) for d in side_data]
+        return orig(U, sides, side_data, h)
+
+    monkeypatch.setattr(CX, "reflect_pad", mutated)
+    test_neumann_data_separated_equals_dense(4, (NEU, NEU), (D, D))
+    with pytest.raises(AssertionError):
+        test_neumann_data_manufactured_converges(4)
+
+
+def test_planted_mode_angle_is_caught(monkeypatch):
+    """Eigenvalues from cos(p pi / (N + 2)) instead of cos(p pi / (N + 1))."""
+    orig = CX.side_cosines
+
+    def mutated(N, kind):
+        c = orig(N, kind)
+        return orig(N + 1, kind)[:c.size] if kind == DIR else c
+
+    monkeypatch.setattr(CX, "side_cosines", mutated)
+    with pytest.raises(AssertionError):
+        test_separated_solve_equals_dense_solve(2, (D, D))
+
+
+def test_planted_order6_kz_sign_is_caught(monkeypatch):
+    """6th-order rows with the sign of the K_z terms flipped."""
+    orig = CX.complex_coefficients6
+
+    def mutated(h, K, Kz, Kzz):
+        return orig(h, K, -np.asarray(Kz), Kzz)
+
+    monkeypatch.setattr(CX, "complex_coefficients6", mutated)
+    with pytest.raises(AssertionError):
+        test_order6_real_case_is_the_real_oracle()
+    with pytest.raises(AssertionError):
+        test_order6_manufactured_complex_solution_converges()
