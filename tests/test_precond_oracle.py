@@ -9,7 +9,8 @@ compact scheme with K U averaged like f in the right-hand side.  What pins it:
       that node (weight h_z^2 K U_m / 2) and its six face neighbours (h_z^2 K U_m / 12);
   (c) on a uniform grid the operator commutes with every permutation of the axes;
   (d) with K = K(z) the preconditioner is exact: BiCGStab converges in one step;
-  (e) BiCGStab's answer equals a direct solve of the assembled matrix.
+  (e) BiCGStab's answer equals a direct solve of the assembled matrix;
+  (f) mutations: K U taken pointwise, or the preconditioner left out, makes a pin fail.
 """
 import itertools
 
@@ -100,3 +101,35 @@ def test_bicgstab_matches_direct_solve(order):
     assert O.max_rel_diff(x, direct) <= 1e-10
     true_res = np.linalg.norm(PC.apply_general(order, K, x, h) - F) / np.linalg.norm(F)
     assert true_res <= 1e-12
+
+
+# ----------------------------------------------------------------- mutations
+# A plausible mistake planted in the oracle (on the CPU, through monkeypatch) must make
+# one of the pins above fail.
+
+
+def test_planted_pointwise_coefficient_is_caught(monkeypatch):
+    """K U taken pointwise in the 4th-order operator (not averaged like f)."""
+    orig = PC.apply_general
+
+    def mutated(order, K, U, h):
+        K = np.asarray(K, dtype=np.float64)
+        return orig(order, np.zeros_like(K), U, h) + h[2] ** 2 * K * np.asarray(U)
+
+    monkeypatch.setattr(PC, "apply_general", mutated)
+    with pytest.raises(AssertionError):
+        test_general_operator_reduces_to_stencil27_for_kz(4)
+    with pytest.raises(AssertionError):
+        test_coefficient_enters_locally(4, 0.5, 1.0 / 12.0)
+
+
+def test_planted_missing_preconditioner_is_caught(monkeypatch):
+    """BiCGStab run without applying the separable solve."""
+    orig = PC.bicgstab
+
+    def mutated(apply_A, apply_Minv, F, tol=1e-12, maxit=100, x0=None):
+        return orig(apply_A, lambda r: r, F, tol, maxit, x0)
+
+    monkeypatch.setattr(PC, "bicgstab", mutated)
+    with pytest.raises(AssertionError):
+        test_preconditioner_exact_for_z_only_coefficient()
