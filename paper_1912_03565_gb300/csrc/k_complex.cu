@@ -13,11 +13,12 @@
 // which gives the row  Rzx dxx + Rzy dyy + 2 u_(inner) + (-2 - 2Rzx - 2Rzy +
 // h_z^2 K -+ 2 h_z beta / alpha) u_face = h_z^2 f +- 2 h_z g / alpha.
 //
-// A side axis may instead carry u_n = 0 on both faces: its boundary nodes are
-// unknowns, f and the face data are reflected evenly beyond them, and the
-// cosine transform DCT-I over nodes 0..N+1 (k_dct.cu) replaces the sine
-// transform; the modes cos(p pi i/(N+1)), p = 0..N+1, enter the same eigenvalue
-// formula, and the per-row coefficients are unchanged.
+// A side axis may instead carry u_n = g on both faces (g = 0, or per-face data
+// through hs_zsolve_ex): its boundary nodes are unknowns, the ghost beyond a
+// face is the even reflection plus 2 h g, f and the z-face data are reflected
+// evenly, and the cosine transform DCT-I over nodes 0..N+1 (k_dct.cu) replaces
+// the sine transform; the modes cos(p pi i/(N+1)), p = 0..N+1, enter the same
+// eigenvalue formula, and the per-row coefficients are unchanged.
 //
 // The solve (Section 3.6 with complex rows): the right-hand side kernel writes
 // the unknown rows l0..l1 as planar complex data [2][Nu][ny][nx]; the real FP64
@@ -207,7 +208,8 @@ hs_status layout(hs_zplan_s *Z) {
     Z->i0x = Z->side[0] == HS_SIDE_NEUMANN ? 0 : 1;
     Z->i0y = Z->side[1] == HS_SIDE_NEUMANN ? 0 : 1;
     Z->l0 = l0;
-    if (!(Z->T && Nu == Z->Nu && nx == Z->nx && ny == Z->ny)) {
+    // rebuilt after a change of shape, or when an earlier rebuild stopped part-way
+    if (!(Z->T && Z->d_rows && Z->d_fac && Nu == Z->Nu && nx == Z->nx && ny == Z->ny)) {
         if (Z->T) hs_destroy(Z->T);
         Z->T = nullptr;
         if (Z->d_rows) cudaFree(Z->d_rows);
