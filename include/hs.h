@@ -589,7 +589,9 @@ hs_status hs_zplan_set_sides(hs_zplan_t plan, int x_kind, int y_kind);
 
 /* hs_zsolve -- one solve on `stream` (asynchronous; the caller keeps f, g and
  * u valid until the stream has passed it).  Errors: HS_ERR_INVALID_ARG (NULL
- * f or u, host pointers), HS_ERR_NO_COEFF, HS_ERR_CUDA. */
+ * f or u, host pointers), HS_ERR_NO_COEFF (no coefficients yet, or an earlier
+ * hs_zplan_set_faces / hs_zplan_set_sides failed part-way: repeat it),
+ * HS_ERR_CUDA. */
 hs_status hs_zsolve(hs_zplan_t plan, const double *f, const double *g_lo, const double *g_hi,
                     double *u, void *stream);
 

@@ -45,6 +45,7 @@ struct hs_zplan_s {
     int Nu, l0;                // unknown planes l0 .. l0 + Nu - 1
     int side[2];               // HS_SIDE_* of the x and y axes
     int nx, ny, i0x, i0y;      // unknown grid of a plane; node index of its first point
+    int layout_ok;             // transform plan, tables and buffers complete
     hs_plan_s *T;              // FP64 transform plan [2 Nu][ny][nx] (work: d_w64, d_dscr)
     double *d_cos;             // [nx] then [ny]: cos(theta) of each axis' modes
     double2 *d_dct[2];         // Neumann axis: M roots then M + 1 half-angle pairs
@@ -121,6 +122,7 @@ void real_row(int order, double Rzx, double Rzy, double hz2, double Km, double K
 
 // Builds the complex rows of the unknown planes and uploads them.
 hs_status build_rows(hs_zplan_s *Z) {
+    if (!Z->layout_ok) return HS_OK;   // built once a set-up call completes the layout
     const double Rzx = Z->hz * Z->hz / (Z->hx * Z->hx), Rzy = Z->hz * Z->hz / (Z->hy * Z->hy);
     const double hz2 = Z->hz * Z->hz;
     std::vector<double2> rows((size_t)Z->Nu * 12);
@@ -200,6 +202,7 @@ hs_status side_tables(hs_zplan_s *Z) {
 // (Re)creates the transform plan, row table and side tables for the current
 // faces and side axes.
 hs_status layout(hs_zplan_s *Z) {
+    Z->layout_ok = 0;
     const int l0 = Z->kind[0] == HS_ZFACE_ROBIN ? 0 : 1;
     const int l1 = Z->kind[1] == HS_ZFACE_ROBIN ? Z->Nz + 1 : Z->Nz;
     const int Nu = l1 - l0 + 1;
@@ -233,7 +236,9 @@ hs_status layout(hs_zplan_s *Z) {
         ZCK(Z, cudaMalloc(&Z->d_rows, (size_t)Nu * 12 * sizeof(double2)));
         ZCK(Z, cudaMalloc(&Z->d_fac, (size_t)6 * Nu * nx * ny * sizeof(double)));
     }
-    return side_tables(Z);
+    const hs_status st = side_tables(Z);
+    if (st == HS_OK) Z->layout_ok = 1;
+    return st;
 }
 
 bool device_ptr(const void *p) {
@@ -563,6 +568,10 @@ hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const dou
 hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const double *g_hi,
                        const double *const *side, double *u, void *stream) {
     if (!Z || !f || !u) return HS_ERR_INVALID_ARG;
+    if (!Z->layout_ok) {
+        zerr(Z, "plan set-up incomplete: an earlier set-up call failed part-way");
+        return HS_ERR_NO_COEFF;
+    }
     if (!Z->have_coeff || !Z->rows_ok) return HS_ERR_NO_COEFF;
     if (!device_ptr(f) || !device_ptr(u) || (g_lo && !device_ptr(g_lo)) ||
         (g_hi && !device_ptr(g_hi)))
