@@ -147,7 +147,10 @@ hs_status hs_plan(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, 
  *               gamma = gamma(z)) or HS_CD_PAPER (the printed coefficients
  *               with gamma frozen at row l); ignored for Helmholtz.
  * Synchronous.  Returns HS_WARN_NEAR_SINGULAR when some pivot ratio is
- * below 1e-13.  Errors: HS_ERR_INVALID_ARG, HS_ERR_CUDA.
+ * below 1e-13.  Errors: HS_ERR_INVALID_ARG, HS_ERR_NONFINITE (a sample is
+ * NaN or infinite), both leaving the plan as it was; HS_ERR_CUDA, after which
+ * the plan has no coefficients (hs_solve returns HS_ERR_NO_COEFF) until a
+ * call succeeds.
  */
 hs_status hs_set_coeff(hs_plan_t plan, const double *c0, const double *c1, const double *c2,
                        int cd_variant);

@@ -732,6 +732,7 @@ hs_status hs_set_coeff(hs_plan_t P, const double *c0, const double *c1, const do
         if (!isfinite(c0[l]) || (c1 && !isfinite(c1[l])) || (c2 && !isfinite(c2[l])))
             return HS_ERR_NONFINITE;
     P->last_error[0] = 0;
+    P->have_coeff = 0;   // until every table below is in place
     std::vector<double> C((size_t)Nz * 12), c1v(Nz + 2, 0.0);
     stencil_table(P, c0, c1, c2, cd_variant, C.data());
     if (c1)
