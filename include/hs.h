@@ -109,7 +109,7 @@ enum {
     HS_STAGE_THOMAS = 3,     /* z-direction tridiagonal solves */
     HS_STAGE_IDST_Y = 4,     /* inverse DST along y */
     HS_STAGE_IDST_X = 5,     /* inverse DST along x (+ write / update of u) */
-    HS_STAGE_RESIDUAL = 6,   /* FP64 residual F - A U (mixed path) */
+    HS_STAGE_RESIDUAL = 6,   /* refinement residual F - A U (mixed path) */
     HS_STAGE_TOTAL = 7
 };
 
@@ -123,8 +123,11 @@ enum {
  *               needs hx = hy = hz (relative difference <= 1e-12).
  *   equation    HS_HELMHOLTZ or HS_CONVDIFF.
  *   bc          HS_BC_DIRICHLET (the only one).
- *   precision   HS_FP64: every step in FP64.  HS_MIXED: FP32 transforms,
- *               FP64 z-solves, FP64 residual and iterative refinement.
+ *   precision   HS_FP64: every step in FP64.  HS_MIXED: FP32 transforms and
+ *               z-solves (FP64 factors where the pivots call for them, see
+ *               hs_set_factor_precision), the right-hand side and the iterate
+ *               as FP32 pairs, and iterative refinement with an FP32-pair or
+ *               FP64 residual (hs_set_residual_precision).
  *   max_rhs     largest nrhs a solve will pass (>= 1).
  * Allocates the plan's device tables and workspace on the current device.
  * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED, HS_ERR_OOM, HS_ERR_CUDA.
@@ -170,6 +173,7 @@ hs_status hs_set_coeff_fn(hs_plan_t plan, hs_coeff_fn fn, void *user, int cd_var
  * after its first solve (default 2; 0..HS_INFO_MAX_ITERS-1).  Each sweep
  * computes the residual r = F - A U (precision: hs_set_residual_precision)
  * and adds the fast solve of r to U.  Ignored by the HS_FP64 path.
+ * Errors: HS_ERR_INVALID_ARG (sweeps outside that range).
  */
 hs_status hs_set_refinement(hs_plan_t plan, int sweeps);
 
@@ -246,6 +250,7 @@ hs_status hs_get_thomas_variant(hs_plan_t plan, int *variant);
  * HS_MIXED plan whose coefficients are set and whose factors are FP32, the
  * z-solve mappings are timed the same way and the fastest kept.
  * Synchronous.  Call after hs_set_coeff, before solves (not during capture).
+ * Errors: HS_ERR_INVALID_ARG (reps < 1), HS_ERR_CUDA.
  */
 hs_status hs_autotune(hs_plan_t plan, void *stream, int reps, float *ms_x, float *ms_y);
 
@@ -305,6 +310,7 @@ hs_status hs_host_io_wait(hs_plan_t plan, void *stream);
  * hs_set_stage_timing -- when on (1), solves record CUDA events around each
  * stage launch (no synchronisation is added); hs_stage_times and
  * hs_info.stage_ms report them.  Off (0) by default.
+ * Errors: HS_ERR_INVALID_ARG (NULL plan).
  */
 hs_status hs_set_stage_timing(hs_plan_t plan, int on);
 
@@ -330,7 +336,8 @@ hs_status hs_solve(hs_plan_t plan, const void *f, int f_dtype, int rhs_kind,
 /*
  * hs_residual -- ||F - A U||_2 and ||F||_2 of a computed solution, in FP64,
  * for one right-hand side given as in hs_solve (L2-res of Section 5.1).
- * Synchronous.  Device or host pointers.
+ * Synchronous.  Device or host pointers.  Errors: HS_ERR_INVALID_ARG,
+ * HS_ERR_NO_COEFF, HS_ERR_OOM (host staging), HS_ERR_CUDA.
  */
 hs_status hs_residual(hs_plan_t plan, const void *f, int f_dtype, int rhs_kind,
                       const hs_boundary *bnd, const double *u, void *stream,
@@ -340,7 +347,7 @@ hs_status hs_residual(hs_plan_t plan, const void *f, int f_dtype, int rhs_kind,
  * hs_stage_times -- device time per stage (ms[HS_INFO_STAGES], indexed by
  * HS_STAGE_*) summed over the last hs_solve on this plan, when stage timing
  * was on; HS_STAGE_TOTAL is the whole call.  Waits for that solve's events.
- * Errors: HS_ERR_INVALID_ARG.
+ * Errors: HS_ERR_INVALID_ARG (NULL, or timing never on), HS_ERR_CUDA.
  */
 hs_status hs_stage_times(hs_plan_t plan, float *ms);
 
@@ -404,7 +411,8 @@ typedef struct {
 hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int nprob, int f_dtype,
                           int sweeps);
 
-/* hs_batch_set_io -- new f and u device pointers of problem k (same layout). */
+/* hs_batch_set_io -- new f and u device pointers of problem k (same layout).
+ * Errors: HS_ERR_INVALID_ARG (k out of range, NULL), HS_ERR_CUDA. */
 hs_status hs_batch_set_io(hs_batch_t batch, int k, const void *f, double *u);
 
 /*
@@ -412,11 +420,14 @@ hs_status hs_batch_set_io(hs_batch_t batch, int k, const void *f, double *u);
  * `stream` (the graph is built on the first call for a stream).  sync = 0:
  * asynchronous; sync = 1: waits and returns HS_ERR_TIMEOUT if a bounded wait
  * inside the launch gave up (the results are then incomplete).
+ * Errors: HS_ERR_INVALID_ARG, HS_ERR_TIMEOUT, HS_ERR_OOM and HS_ERR_CUDA
+ * (building or launching the graph).
  */
 hs_status hs_batch_solve(hs_batch_t batch, void *stream, int sync);
 
 /* hs_batch_set_wait_limit -- spin iterations (about 100 ns each) before a wait
- * inside the launch gives up (default 2e7). */
+ * inside the launch gives up (default 2e7).  Errors: HS_ERR_INVALID_ARG
+ * (spins < 1). */
 hs_status hs_batch_set_wait_limit(hs_batch_t batch, long long spins);
 
 /*
@@ -448,7 +459,8 @@ typedef struct {
  * HS_ERR_OOM. */
 hs_status hs_precond_create(hs_precond_t *out, hs_plan_t plan, const double *K);
 
-/* hs_precond_apply -- y = A(K) u (device FP64 arrays, asynchronous on stream). */
+/* hs_precond_apply -- y = A(K) u (device FP64 arrays, asynchronous on stream).
+ * Errors: HS_ERR_INVALID_ARG, HS_ERR_CUDA. */
 hs_status hs_precond_apply(hs_precond_t pc, const double *u, double *y, void *stream);
 
 /* hs_precond_solve -- x (device FP64, in: initial guess, out: solution) for the
@@ -456,19 +468,25 @@ hs_status hs_precond_apply(hs_precond_t pc, const double *u, double *y, void *st
  * iterations (HS_WARN_NOT_CONVERGED, x valid).  Each iteration applies A twice
  * and the plan's solve twice (hs_solve with HS_RHS_ASSEMBLED on `stream`) and
  * synchronises the stream for its four reductions.  HS_ERR_NONFINITE on a
- * BiCGStab breakdown or a NaN.  info may be NULL. */
+ * BiCGStab breakdown or a NaN.  info may be NULL.  Errors: HS_ERR_INVALID_ARG
+ * (NULL, tol < 0 or NaN, maxit < 1), HS_ERR_NONFINITE, HS_ERR_CUDA, and those
+ * of hs_solve. */
 hs_status hs_precond_solve(hs_precond_t pc, const double *F, double *x, double tol, int maxit,
                            void *stream, hs_precond_info *info);
 
+/* hs_precond_destroy -- free the workspace (K stays the caller's; NULL is
+ * accepted).  Returns HS_OK. */
 hs_status hs_precond_destroy(hs_precond_t pc);
 
 /* hs_batch_set_tol -- tolerance-controlled refinement per problem and RHS:
  * each stops once ||F - A U||_2 / ||F||_2 <= tol (decided on the device) or
- * after the batch's sweep count; 0 (default) runs every sweep. */
+ * after the batch's sweep count; 0 (default) runs every sweep.  Errors:
+ * HS_ERR_INVALID_ARG (tol < 0 or NaN). */
 hs_status hs_batch_set_tol(hs_batch_t batch, double tol);
 
 /* hs_batch_set_residual_precision -- as hs_set_residual_precision, for every
- * (problem, RHS) of the batch, each deciding on its own (default AUTO). */
+ * (problem, RHS) of the batch, each deciding on its own (default AUTO).
+ * Errors: HS_ERR_INVALID_ARG. */
 hs_status hs_batch_set_residual_precision(hs_batch_t batch, int mode);
 
 /* hs_batch_set_variant / hs_batch_get_variant -- the persistent kernel
@@ -485,18 +503,20 @@ hs_status hs_batch_set_variant(hs_batch_t batch, int variant);
 hs_status hs_batch_get_variant(hs_batch_t batch, int *variant, int *grid);
 
 /* hs_batch_graph_kernels -- kernel launches per hs_batch_solve: the kernel
- * nodes of the captured graph (0 before the first solve of the variant). */
+ * nodes of the captured graph (0 before the first solve of the variant).
+ * Errors: HS_ERR_INVALID_ARG. */
 hs_status hs_batch_graph_kernels(hs_batch_t batch, int *kernels);
 
 /* hs_batch_autotune -- times `reps` solves of the batch (after one warm-up)
  * with each kernel variant on `stream` and keeps the fastest; *ms (may be
  * NULL) receives its mean time per solve.  The solves write the outputs u.
- * Synchronous. */
+ * Synchronous.  Errors: HS_ERR_INVALID_ARG (reps < 1), HS_ERR_UNSUPPORTED (no
+ * variant fits), HS_ERR_TIMEOUT, HS_ERR_OOM, HS_ERR_CUDA. */
 hs_status hs_batch_autotune(hs_batch_t batch, void *stream, int reps, float *ms);
 
 /* hs_batch_debug_stall -- test hook: on = 1 makes one dependency of the first
  * problem unsatisfiable, so the next solve must end with HS_ERR_TIMEOUT; on =
- * 0 restores it. */
+ * 0 restores it.  Errors: HS_ERR_INVALID_ARG, HS_ERR_CUDA. */
 hs_status hs_batch_debug_stall(hs_batch_t batch, int on);
 
 /* hs_batch_workspace_bytes -- device bytes owned by the batch. */
@@ -536,11 +556,13 @@ const char *hs_last_error(hs_plan_t plan);
  * (48 bytes per complex unknown), rebuilt by the first solve after a change of
  * coefficient, faces or side axes.
  *
- * A side axis (x or y) may instead carry u_n = 0 on both of its faces (the
- * extension Section 1 names): its boundary nodes become unknowns, f and the
- * face data are reflected evenly beyond them (the central difference of
- * u_n = 0), and the cosine transform DCT-I over nodes 0..N+1 replaces the sine
- * transform (modes cos(p pi i/(N+1)), p = 0..N+1, same eigenvalue formula).
+ * A side axis (x or y) may instead carry u_n = g on both of its faces (the
+ * extension Section 1 names; g = 0, or per-face data through hs_zsolve_ex):
+ * its boundary nodes become unknowns, the ghost beyond a face is the even
+ * reflection plus 2 h g (the central difference of u_n = g), f and the z-face
+ * data are reflected evenly, and the cosine transform DCT-I over nodes 0..N+1
+ * replaces the sine transform (modes cos(p pi i/(N+1)), p = 0..N+1, same
+ * eigenvalue formula).
  *
  * The unknown grid of a plane is [ny][nx]: nx = Nx + 2 (nodes 0..Nx+1) for a
  * Neumann x-axis, else Nx (nodes 1..Nx); likewise ny.  Complex arrays are
@@ -580,7 +602,8 @@ hs_status hs_zplan_set_faces(hs_zplan_t plan, int lo_kind, const double *alpha_l
  * y-lo, y-hi faces ([2][Nz+2][Nx+2]); NULL entries (or side = NULL) are 0.  The
  * ghost beyond such a face is the mirror value plus 2 h g (second-order
  * central difference), a face's data reflected evenly beyond its own edges.
- * Data on the faces of a Dirichlet axis are rejected (HS_ERR_INVALID_ARG). */
+ * Data on the faces of a Dirichlet axis are rejected (HS_ERR_INVALID_ARG).
+ * Other errors as hs_zsolve. */
 hs_status hs_zsolve_ex(hs_zplan_t plan, const double *f, const double *g_lo, const double *g_hi,
                        const double *const *side, double *u, void *stream);
 
