@@ -7,8 +7,8 @@ manufactured right-hand side of u = sin(pi x) sin(2 pi y) sin(3 pi z) e^z plus
 seeded U[-1, 1] noise at interior nodes, face data d2f/dn2 analytic, FP64 f.
 
 A step is one complete solve of one right-hand side (RHS operator, forward
-DSTs, z-solves, inverse DSTs, and for the mixed path the FP64 residual and
-refinement sweeps) with f and u resident in HBM.  The headline value is the
+DSTs, z-solves, inverse DSTs, and for the mixed path the refinement residual
+and sweeps) with f and u resident in HBM.  The headline value is the
 mixed path (FP32 transforms and z-solves, double-float residual and iterate,
 refinement sweeps: the fewest whose error against the CPU oracle, measured in
 the same run, is <= 1e-10) in Gunknowns/s; the FP64 path is timed beside it.  L2 is flushed

@@ -7,9 +7,11 @@
 //               Fhat = DST_y DST_x F       (k_dst, FP64, in place)
 //               W = T_pq^{-1} Fhat         (k_thomas, FP64, cached LU)
 //               U = 4/((Nx+1)(Ny+1)) DST_x DST_y W
-//   Mixed path: F as above, kept in FP64; U_0 = 0; for m = 0..sweeps:
-//               r = F - A U_m (FP64 27-point; r = F for m = 0), rounded to FP32,
-//               U_{m+1} = U_m + (FP32 DSTs, FP64 z-solves) r.
+//   Mixed path: F as above, kept as FP32 pairs; U_0 = 0; for m = 0..sweeps:
+//               r = F - A U_m (27-point, FP32-pair or FP64 arithmetic; r = F
+//               for m = 0), rounded to FP32,
+//               U_{m+1} = U_m + (FP32 DSTs, FP32 z-solves with FP32 or FP64
+//               factors) r, U held as FP32 pairs.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
