@@ -95,7 +95,9 @@ def _hi_neu(kind):
 
 def _nodes(N, kind):
     """First and last node index of the unknowns along a side axis of N interior nodes:
-    the boundary node of a Neumann face is an unknown, that of a Dirichlet face is not."""
+    the boundary node of a Neumann face is an unknown, that of a Dirichlet face is not.
+
+    Paper: Section 1 (Neumann side faces, the extension it names)."""
     return (0 if _lo_neu(kind) else 1), (N + 1 if _hi_neu(kind) else N)
 
 
@@ -106,7 +108,9 @@ def _n_unknown(N, kind):
 
 def cosine_matrix(N):
     """DCT-I over the nodes 0..N+1 (M = N + 1): C[p, i] = w_i cos(pi p i / M), p, i = 0..M,
-    w_0 = w_M = 1/2, else 1; the argument is reduced as an integer modulo 2M first."""
+    w_0 = w_M = 1/2, else 1; the argument is reduced as an integer modulo 2M first.
+
+    Paper: Section 3.6's transform for Section 1's Neumann side faces."""
     M = N + 1
     k = np.outer(np.arange(M + 1), np.arange(M + 1)) % (2 * M)
     C = np.cos(np.pi * k / M)
@@ -120,7 +124,9 @@ def side_transform(N, kind):
     interior nodes (Dirichlet faces), DCT-I of all nodes (Neumann faces), or for one face
     of each kind the quarter-wave transforms with theta_p = (2p - 1) pi / (2M), p = 1..M
     (M = N + 1): sines over nodes 1..M (Neumann high face), cosines over nodes 0..N
-    (Neumann low face), weight 1/2 at the Neumann node."""
+    (Neumann low face), weight 1/2 at the Neumann node.
+
+    Paper: Section 3.6 with Section 1's side faces."""
     M = N + 1
     if kind == SIDE_NEUMANN:
         # the DCT-I is its own inverse up to 2/M: x_i = (2/M) sum_p w_p X_p cos(pi p i/M)
@@ -139,7 +145,9 @@ def side_transform(N, kind):
 
 
 def side_cosines(N, kind):
-    """cos(theta_p) of the modes of one side axis."""
+    """cos(theta_p) of the modes of one side axis.
+
+    Paper: Section 3.6 with Section 1's side faces."""
     if kind == SIDE_NEUMANN:
         return np.cos(np.pi * np.arange(0, N + 2) / (N + 1))
     if kind in (SIDE_DN, SIDE_ND):
@@ -151,7 +159,9 @@ def side_cosines(N, kind):
 def _span(N, kind):
     """Node indices covered by a padded unknown grid along a side axis (one node beyond
     the unknowns on each side), nodes beyond a Neumann face folded back by the even
-    reflection (-1 -> 1, N + 2 -> N)."""
+    reflection (-1 -> 1, N + 2 -> N).
+
+    Paper: Section 1 (even reflection beyond a Neumann face)."""
     first, last = _nodes(N, kind)
     idx = np.arange(first - 1, last + 2)
     if _lo_neu(kind):
@@ -172,7 +182,9 @@ def reflect_pad(U, sides, side_data=None, h=None):
     side_data = (x-lo, x-hi, y-lo, y-hi) arrays of u_n on the face node grids
     ([planes][Ny+2] for x-faces, [planes][Nx+2] for y-faces; None = 0, read on Neumann
     faces only), reflected evenly beyond their own edges; x-ghosts are set first, so a
-    corner ghost carries the data of both faces."""
+    corner ghost carries the data of both faces.
+
+    Paper: Section 1 (u_n = g faces, central-difference ghost)."""
     U = np.asarray(U)
     pad = [(0, 0)] * (U.ndim - 2) + [(1, 1), (1, 1)]
     P = np.pad(U, pad)
@@ -218,7 +230,9 @@ def complex_coefficients6(h, K, Kz, Kzz):
 
 def complex_coefficients(order, h, K, Kz=None, Kzz=None):
     """C[l-1, nu, m] (complex) for interior rows l = 1..Nz; K complex, length Nz + 2
-    (order 6 also needs K_z and K_zz)."""
+    (order 6 also needs K_z and K_zz).
+
+    Paper: Sections 3.2-3.4 with complex K."""
     if order == 6:
         return complex_coefficients6(h, K, Kz, Kzz)
     if order not in (2, 4):
@@ -232,7 +246,9 @@ def complex_coefficients(order, h, K, Kz=None, Kzz=None):
 
 
 def robin_row(h, K_l, alpha, beta, side):
-    """3 x 4 block (nu = l-1, l, l+1; a, b, c, d) of a Robin face's row (side -1: lo, +1: hi)."""
+    """3 x 4 block (nu = l-1, l, l+1; a, b, c, d) of a Robin face's row (side -1: lo, +1: hi).
+
+    Paper: Section 1's Robin face (eq. bc); a second-order closure, the paper gives none."""
     hx, hy, hz = h
     Rzx, Rzy = hz * hz / (hx * hx), hz * hz / (hy * hy)
     R = np.zeros((3, 4), dtype=np.complex128)
@@ -245,7 +261,9 @@ def robin_row(h, K_l, alpha, beta, side):
 
 
 def row_table(order, h, K, zf, Kz=None, Kzz=None):
-    """Coefficient blocks of the unknown rows l0..l1: array (Nu, 3, 4) complex."""
+    """Coefficient blocks of the unknown rows l0..l1: array (Nu, 3, 4) complex.
+
+    Paper: Sections 3.2-3.4 and Section 1."""
     K = np.asarray(K, dtype=np.complex128)
     Nz = K.shape[0] - 2
     Ci = complex_coefficients(order, h, K, Kz, Kzz)
@@ -263,7 +281,9 @@ def _face(g, Ny, Nx):
 
 
 def _plane_part(block, P):
-    """One plane's part of a row: block (4,) applied to a padded plane P [Ny+2][Nx+2]."""
+    """One plane's part of a row: block (4,) applied to a padded plane P [Ny+2][Nx+2].
+
+    Paper: eq. stencil27 (one plane's part)."""
     corners = P[:-2, :-2] + P[:-2, 2:] + P[2:, :-2] + P[2:, 2:]
     xn = P[1:-1, :-2] + P[1:-1, 2:]
     yn = P[:-2, 1:-1] + P[2:, 1:-1]
@@ -281,7 +301,9 @@ def _pad2(g):
 def _f_on_unknowns(f, sides):
     """f on [Nz+2][ny+2][nx+2]: the unknown grid of every plane plus one node per side
     (beyond a Dirichlet face its boundary node as given, beyond a Neumann face the even
-    reflection)."""
+    reflection).
+
+    Paper: Section 1 (even reflection beyond a Neumann face)."""
     Ny, Nx = f.shape[1] - 2, f.shape[2] - 2
     xs = _span(Nx, sides[0])
     ys = _span(Ny, sides[1])
@@ -293,7 +315,9 @@ def _interior_rhs(order, h, fu, K, Kz=None, fnn=None):
     """R_h f on the interior planes for complex f (padded unknown grid fu).  Orders 2 and 4:
     the real operator on Re f and Im f.  Order 6 (R6, Dirichlet sides): the K-free part
     likewise (with the face data f_nn split the same way) plus the complex terms
-    h^2 (-h^2 K f / 20 + h^3 K_z (f_{l+1} - f_{l-1}) / 120)."""
+    h^2 (-h^2 K f / 20 + h^3 K_z (f_{l+1} - f_{l-1}) / 120).
+
+    Paper: eqs. scheme4 and scheme6."""
     if order != 6:
         return (O.rhs_operator(order, O.HELMHOLTZ, h, fu.real)
                 + 1j * O.rhs_operator(order, O.HELMHOLTZ, h, fu.imag))
@@ -312,7 +336,9 @@ def _interior_rhs(order, h, fu, K, Kz=None, fnn=None):
 
 def rhs(order, h, K, zf, f_nodes, g_lo=None, g_hi=None, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET),
         side_data=None, Kz=None, Kzz=None, fnn=None):
-    """Right-hand side of the unknown rows: array (Nu, ny, nx) complex."""
+    """Right-hand side of the unknown rows: array (Nu, ny, nx) complex.
+
+    Paper: Sections 2 and 3.6."""
     if order == 6 and sides != (SIDE_DIRICHLET, SIDE_DIRICHLET):
         raise ValueError("6th-order complex rows: Dirichlet side faces")
     hz = h[2]
@@ -345,7 +371,9 @@ def rhs(order, h, K, zf, f_nodes, g_lo=None, g_hi=None, sides=(SIDE_DIRICHLET, S
 
 
 def eigenvalues(R, Nx, Ny, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
-    """lambda_nu(p, q) of every unknown row: complex array (3, Nu, ny, nx)."""
+    """lambda_nu(p, q) of every unknown row: complex array (3, Nu, ny, nx).
+
+    Paper: Section 3.6 (lambda_nu(p, q))."""
     cx = side_cosines(Nx, sides[0])[None, None, :]
     cy = side_cosines(Ny, sides[1])[None, :, None]
     lam = np.empty((3, R.shape[0], cy.shape[1], cx.shape[2]), dtype=np.complex128)
@@ -369,7 +397,9 @@ def solve_rows(R, F, Nx, Ny, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET)):
 
 def solve(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
           sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), side_data=None, Kz=None, Kzz=None, fnn=None):
-    """Solution on every plane l = 0..Nz+1 (unknown grid in x, y): complex (Nz+2, ny, nx)."""
+    """Solution on every plane l = 0..Nz+1 (unknown grid in x, y): complex (Nz+2, ny, nx).
+
+    Paper: Section 3.6 (transforms, z-solves, inverse transforms)."""
     f = np.asarray(f_nodes, dtype=np.complex128)
     Nz, Ny, Nx = f.shape[0] - 2, f.shape[1] - 2, f.shape[2] - 2
     ny, nx = _n_unknown(Ny, sides[1]), _n_unknown(Nx, sides[0])
@@ -398,7 +428,10 @@ def apply_operator(order, h, K, zf, U_all, g_lo=None, g_hi=None,
     Interior rows: the 27-point stencil with the complex table.  Robin rows: the
     7-point second-order operator h_z^2 (dxx + dyy + dzz + K) u evaluated with an
     explicit ghost plane built from the face condition (with its data g), so that
-    solving A U = F means operator(U) = rhs without the data terms."""
+    solving A U = F means operator(U) = rhs without the data terms.
+
+    Paper: the scheme written out (eq. stencil27, Section 1's face conditions), for the
+    pins."""
     hx, hy, hz = h
     K = np.asarray(K, dtype=np.complex128)
     U_all = np.asarray(U_all, dtype=np.complex128)
@@ -437,7 +470,9 @@ def apply_operator(order, h, K, zf, U_all, g_lo=None, g_hi=None,
 def rhs_direct(order, h, f_nodes, sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), K=None, Kz=None,
                fnn=None):
     """The scheme's f-side on every plane that can be a row: R_h f on interior rows
-    (f reflected beyond a Neumann side), h_z^2 f on the two face planes."""
+    (f reflected beyond a Neumann side), h_z^2 f on the two face planes.
+
+    Paper: eqs. scheme4 and scheme6 written out, for the pins."""
     hz = h[2]
     f = np.asarray(f_nodes, dtype=np.complex128)
     fu = _f_on_unknowns(f, sides)
@@ -449,7 +484,9 @@ def solve_dense(order, h, K, zf, f_nodes, g_lo=None, g_hi=None,
                 sides=(SIDE_DIRICHLET, SIDE_DIRICHLET), side_data=None, Kz=None, Kzz=None,
                 fnn=None):
     """Brute force: the matrix of apply_operator (columns from unit vectors), its data
-    part from the operator at U = 0, and a dense complex LU solve."""
+    part from the operator at U = 0, and a dense complex LU solve.
+
+    Paper: no paper counterpart (brute-force pin)."""
     f = np.asarray(f_nodes, dtype=np.complex128)
     Nz = f.shape[0] - 2
     Ny, Nx = _n_unknown(f.shape[1] - 2, sides[1]), _n_unknown(f.shape[2] - 2, sides[0])

@@ -76,6 +76,8 @@ def stencil_coefficients(order, equation, h, c0, c1=None, c2=None, cd_variant=CD
     nu = 0, 1, 2 is the plane l-1, l, l+1; m = 0..3 is a (corners), b (x-neighbours),
     c (y-neighbours), d (centre).  c0, c1, c2 have length Nz + 2 (nodes l = 0..Nz+1):
     Helmholtz: K = k^2, K_z, K_zz; CD: gamma, gamma', gamma''.
+    Paper: Sections 3.2 (2nd order), 3.3 (4th), 3.4 (6th) and 3.5 (convection-diffusion):
+    the a, b, c, d of the stencil form, eq. stencil27.
     """
     hx, hy, hz = h
     c0 = np.asarray(c0, dtype=np.float64)
@@ -148,7 +150,9 @@ def stencil_coefficients(order, equation, h, c0, c1=None, c2=None, cd_variant=CD
 
 
 def _undivided_d2(f, axis):
-    """D_a f = f_{+1} - 2 f + f_{-1} along one axis, at interior nodes of that axis."""
+    """D_a f = f_{+1} - 2 f + f_{-1} along one axis, at interior nodes of that axis.
+
+    Paper: h_a^2 delta_a^2 of Section 2."""
     n = f.shape[axis]
     lo = np.take(f, range(0, n - 2), axis=axis)
     mid = np.take(f, range(1, n - 1), axis=axis)
@@ -165,6 +169,8 @@ def _ghost_pad(f, axis, lo_face, hi_face, h):
 
     Ghost f_{-1} = 2 f_0 - f_1 + h^2 (f_nn)_face (and the mirror at the far
     face): second-order Taylor closure, with the face data f_nn = 0 when None.
+    Paper: the face closure of the 6th-order right-hand side, eq. scheme6 (the paper leaves
+    it to the compact scheme it cites).
     """
     f0 = np.take(f, [0], axis=axis)
     f1 = np.take(f, [1], axis=axis)
@@ -255,6 +261,7 @@ def boundary_nodes(shape_interior, faces):
 
     Faces (x-lo, x-hi, y-lo, y-hi, z-lo, z-hi; None = 0) are written in that
     order, so on shared edges and corners the z-face value wins, then y.
+    Paper: the Dirichlet data of eq. bc.
     """
     Nz, Ny, Nx = shape_interior
     G = np.zeros((Nz + 2, Ny + 2, Nx + 2))
@@ -277,7 +284,9 @@ def boundary_nodes(shape_interior, faces):
 
 
 def lift(C, F, faces):
-    """F - (stencil applied to the Dirichlet boundary values): moves known U to the RHS."""
+    """F - (stencil applied to the Dirichlet boundary values): moves known U to the RHS.
+
+    Paper: Section 3.6 (known boundary values carried to the right-hand side)."""
     if faces is None or all(fc is None for fc in faces):
         return F
     return F - apply_stencil(C, boundary_nodes(F.shape, faces))
@@ -289,7 +298,9 @@ def lift(C, F, faces):
 
 def sine_matrix(N):
     """S[p-1, i-1] = sin(pi p i / (N+1)), p, i = 1..N, with the argument reduced
-    exactly as an integer modulo 2(N+1) before the FP64 sine."""
+    exactly as an integer modulo 2(N+1) before the FP64 sine.
+
+    Paper: Section 3.6 (eigenvectors of the second difference)."""
     M = N + 1
     p = np.arange(1, N + 1)
     k = np.outer(p, p) % (2 * M)
@@ -297,7 +308,9 @@ def sine_matrix(N):
 
 
 def dst2_forward(Fi, Sx=None, Sy=None):
-    """Fhat[l, q, p] = sum_i sum_j sin(pi p i/(Nx+1)) sin(pi q j/(Ny+1)) F[l, j, i]."""
+    """Fhat[l, q, p] = sum_i sum_j sin(pi p i/(Nx+1)) sin(pi q j/(Ny+1)) F[l, j, i].
+
+    Paper: Section 3.6 (2-D DST along x, then y)."""
     Nz, Ny, Nx = Fi.shape
     Sx = sine_matrix(Nx) if Sx is None else Sx
     Sy = sine_matrix(Ny) if Sy is None else Sy
@@ -306,7 +319,9 @@ def dst2_forward(Fi, Sx=None, Sy=None):
 
 
 def dst2_inverse(W, Sx=None, Sy=None):
-    """U[l, j, i] = 4/((Nx+1)(Ny+1)) sum_p sum_q sin(.) sin(.) W[l, q, p] (V is orthonormal)."""
+    """U[l, j, i] = 4/((Nx+1)(Ny+1)) sum_p sum_q sin(.) sin(.) W[l, q, p] (V is orthonormal).
+
+    Paper: Section 3.6 (inverse 2-D DST)."""
     Nz, Ny, Nx = W.shape
     Sx = sine_matrix(Nx) if Sx is None else Sx
     Sy = sine_matrix(Ny) if Sy is None else Sy
@@ -314,12 +329,16 @@ def dst2_inverse(W, Sx=None, Sy=None):
 
 
 def mode_cosines(N):
-    """cos(theta_p), theta_p = p pi / (N + 1), p = 1..N."""
+    """cos(theta_p), theta_p = p pi / (N + 1), p = 1..N.
+
+    Paper: Section 3.6."""
     return np.cos(np.pi * np.arange(1, N + 1) / (N + 1))
 
 
 def eigenvalues(C, Nx, Ny):
-    """lambda_nu(p, q) for every row: array (3, Nz, Ny, Nx) for nu = l-1, l, l+1."""
+    """lambda_nu(p, q) for every row: array (3, Nz, Ny, Nx) for nu = l-1, l, l+1.
+
+    Paper: Section 3.6 (lambda_nu(p, q))."""
     cx = mode_cosines(Nx)[None, None, :]
     cy = mode_cosines(Ny)[None, :, None]
     lam = np.empty((3, C.shape[0], Ny, Nx))
@@ -335,6 +354,7 @@ def thomas(lower, diag, upper, rhs):
 
     Row l: lower[l] w[l-1] + diag[l] w[l] + upper[l] w[l+1] = rhs[l]; lower[0] and
     upper[-1] are ignored.  Returns (w, min |pivot| / max |diag|).
+    Paper: Section 3.6 (one tridiagonal system in z per mode).
     """
     n = rhs.shape[0]
     cp = np.empty_like(rhs)
@@ -368,13 +388,17 @@ def solve_assembled(C, F):
 
 
 def assemble_rhs(order, equation, h, f_nodes, C, c0=None, c1=None, faces=None, fnn=None):
-    """Lifted right-hand side: R_h f minus the boundary contributions."""
+    """Lifted right-hand side: R_h f minus the boundary contributions.
+
+    Paper: Sections 2 and 3.6."""
     F = rhs_operator(order, equation, h, f_nodes, c0, c1, fnn)
     return lift(C, F, faces)
 
 
 def solve(prob, cd_variant=CD_CORRECTED, return_all=False):
-    """Full oracle solve of a workloads.Problem-like object (NODAL right-hand side)."""
+    """Full oracle solve of a workloads.Problem-like object (NODAL right-hand side).
+
+    Paper: Section 3.6 (transforms, z-solves, inverse transforms)."""
     N = (prob.Nx, prob.Ny, prob.Nz)
     h = grid_steps(N, (prob.Lx, prob.Ly, prob.Lz))
     C = stencil_coefficients(prob.order, prob.equation, h, prob.c0, prob.c1, prob.c2, cd_variant)
@@ -455,7 +479,9 @@ def solve_sine_modes(modes, amps, N, L, order, c0, c1=None, c2=None, sample=None
 
 
 def pad_boundary(U, faces=None):
-    """Interior U -> node grid with the Dirichlet face data on the boundary."""
+    """Interior U -> node grid with the Dirichlet face data on the boundary.
+
+    Paper: eq. bc."""
     G = boundary_nodes(U.shape, faces)
     G[1:-1, 1:-1, 1:-1] = U
     return G
@@ -467,12 +493,16 @@ def residual_l2(C, U, F_lifted):
 
 
 def error_measures(U, u_nodes):
-    """(max-err, L2-err) = (||u - U||_inf, ||u - U||_2 / ||u||_2) over interior nodes."""
+    """(max-err, L2-err) = (||u - U||_inf, ||u - U||_2 / ||u||_2) over interior nodes.
+
+    Paper: the max-err and L2-err of Section 5.1's tables."""
     u = _interior(np.asarray(u_nodes))
     e = u - U
     return float(np.max(np.abs(e))), float(np.linalg.norm(e) / np.linalg.norm(u))
 
 
 def max_rel_diff(U, V):
-    """||U - V||_inf / ||V||_inf: the parity measure between two solutions."""
+    """||U - V||_inf / ||V||_inf: the parity measure between two solutions.
+
+    Paper: no paper counterpart (the parity measure of the tests)."""
     return float(np.max(np.abs(U - V)) / max(np.max(np.abs(V)), 1e-300))

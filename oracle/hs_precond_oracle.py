@@ -34,7 +34,9 @@ def _pad(U):
 
 
 def _d2(P, axis, h):
-    """Central second difference along an axis of a padded array, on the interior."""
+    """Central second difference along an axis of a padded array, on the interior.
+
+    Paper: delta_a^2 of Section 2."""
     sl = [slice(1, -1)] * 3
     lo, hi = list(sl), list(sl)
     lo[axis] = slice(0, -2)
@@ -44,7 +46,9 @@ def _d2(P, axis, h):
 
 def _d2_full(P, axis, h):
     """Second difference along `axis` keeping the padded shape in the other axes
-    (the padded axis shrinks by 2); used to form mixed differences."""
+    (the padded axis shrinks by 2); used to form mixed differences.
+
+    Paper: delta_a^2 of Section 2."""
     n = P.shape[axis]
     lo = [slice(None)] * 3
     mid = [slice(None)] * 3
@@ -57,7 +61,10 @@ def _d2_full(P, axis, h):
 
 def apply_general(order, K, U, h):
     """(A U) on the interior for a coefficient K = k^2 given on the interior
-    nodes [z][y][x]; h = (hx, hy, hz).  Zero Dirichlet data."""
+    nodes [z][y][x]; h = (hx, hy, hz).  Zero Dirichlet data.
+
+    Paper: Section 2's 4th-order scheme (eq. scheme4) for a coefficient K(x, y, z); Section
+    1 names the preconditioner use."""
     hx, hy, hz = h
     K = np.asarray(K, dtype=np.float64)
     U = np.asarray(U, dtype=np.float64)
@@ -122,7 +129,10 @@ def bicgstab(apply_A, apply_Minv, F, tol=1e-12, maxit=100, x0=None):
 
 def precond_solve(order, K, F, h, Kref, tol=1e-12, maxit=100):
     """Solve A(K) x = F (F assembled, interior) by BiCGStab preconditioned with
-    the separable direct solve for Kref(z) (length Nz + 2, nodes l = 0..Nz+1)."""
+    the separable direct solve for Kref(z) (length Nz + 2, nodes l = 0..Nz+1).
+
+    Paper: Section 1 (the separable solve as preconditioner); BiCGStab of van der Vorst
+    (1992)."""
     C = O.stencil_coefficients(order, O.HELMHOLTZ, h, np.asarray(Kref, dtype=np.float64))
     return bicgstab(lambda u: apply_general(order, K, u, h),
                     lambda r: O.solve_assembled(C, r)[0], F, tol, maxit)
@@ -130,6 +140,8 @@ def precond_solve(order, K, F, h, Kref, tol=1e-12, maxit=100):
 
 def reference_from_field(K):
     """K_ref(z_l) = mean of K over each interior plane, extended to the two
-    boundary planes by the nearest interior plane (length Nz + 2)."""
+    boundary planes by the nearest interior plane (length Nz + 2).
+
+    Paper: no paper counterpart (a choice of K_ref)."""
     m = np.asarray(K, dtype=np.float64).mean(axis=(1, 2))
     return np.concatenate([[m[0]], m, [m[-1]]])
