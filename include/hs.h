@@ -159,7 +159,7 @@ hs_status hs_set_coeff(hs_plan_t plan, const double *c0, const double *c1, const
                        int cd_variant);
 
 /*
- * hs_set_coeff_fn -- hs_set_coeff from a function: c0, c1, c2 are sampled as
+ * hs_set_coeff_fn -- hs_set_coeff (Sections 3.2-3.5) from a function: c0, c1, c2 are sampled as
  * fn(z_l, 0, user), fn(z_l, 1, user), fn(z_l, 2, user) at z_l = l hz,
  * l = 0..Nz+1 (the coefficient and its first two z-derivatives: k^2 for
  * Helmholtz, gamma for convection-diffusion), on the calling thread, before
@@ -169,7 +169,8 @@ typedef double (*hs_coeff_fn)(double z, int deriv, void *user);
 hs_status hs_set_coeff_fn(hs_plan_t plan, hs_coeff_fn fn, void *user, int cd_variant);
 
 /*
- * hs_set_refinement -- number of refinement sweeps of the HS_MIXED path
+ * hs_set_refinement -- number of refinement sweeps of the HS_MIXED path (no
+ * paper counterpart: the paper solves in FP64; each sweep reuses Section 3.6's solve)
  * after its first solve (default 2; 0..HS_INFO_MAX_ITERS-1).  Each sweep
  * computes the residual r = F - A U (precision: hs_set_residual_precision)
  * and adds the fast solve of r to U.  Ignored by the HS_FP64 path.
@@ -178,8 +179,8 @@ hs_status hs_set_coeff_fn(hs_plan_t plan, hs_coeff_fn fn, void *user, int cd_var
 hs_status hs_set_refinement(hs_plan_t plan, int sweeps);
 
 /*
- * hs_set_residual_precision -- arithmetic of the refinement residual of the
- * HS_MIXED path (the iterate U and F are kept as FP32 pairs either way):
+ * hs_set_residual_precision -- arithmetic of the refinement residual (the
+ * 27-point operator of eq. stencil27) of the HS_MIXED path (the iterate U and F are kept as FP32 pairs either way):
  *   HS_RESID_DF   FP32-pair arithmetic, rounding ~2^-47 of the largest term;
  *   HS_RESID_F64  FP64 arithmetic (2^-53), about 2x the time of HS_RESID_DF;
  *   HS_RESID_AUTO (default) FP32-pair residuals while each shrinks the previous
@@ -193,7 +194,7 @@ hs_status hs_set_residual_precision(hs_plan_t plan, int mode);
 
 /*
  * hs_set_refinement_tol -- tolerance-controlled refinement of the HS_MIXED
- * path (iterative refinement U_{m+1} = U_m + M (F - A U_m), stopped once
+ * path (no paper counterpart; L2-res as in Section 5.1; iterative refinement U_{m+1} = U_m + M (F - A U_m), stopped once
  * ||F - A U_m||_2 / ||F||_2 <= tol or after the hs_set_refinement count).
  * tol = 0 (default) runs the fixed count.  The decision is taken on the device
  * (no host synchronisation): the kernels of sweeps after convergence return
@@ -459,11 +460,13 @@ typedef struct {
  * HS_ERR_OOM. */
 hs_status hs_precond_create(hs_precond_t *out, hs_plan_t plan, const double *K);
 
-/* hs_precond_apply -- y = A(K) u (device FP64 arrays, asynchronous on stream).
+/* hs_precond_apply -- y = A(K) u, the operator above (device FP64 arrays,
+ * asynchronous on stream).
  * Errors: HS_ERR_INVALID_ARG, HS_ERR_CUDA. */
 hs_status hs_precond_apply(hs_precond_t pc, const double *u, double *y, void *stream);
 
-/* hs_precond_solve -- x (device FP64, in: initial guess, out: solution) for the
+/* hs_precond_solve -- BiCGStab with the Section 3.6 solve as preconditioner
+ * (Section 1's use): x (device FP64, in: initial guess, out: solution) for the
  * assembled right-hand side F; stops at ||F - A x|| / ||F|| <= tol or after maxit
  * iterations (HS_WARN_NOT_CONVERGED, x valid).  Each iteration applies A twice
  * and the plan's solve twice (hs_solve with HS_RHS_ASSEMBLED on `stream`) and
@@ -585,18 +588,19 @@ enum { HS_SIDE_DIRICHLET = 0, HS_SIDE_NEUMANN = 1 };
 hs_status hs_zplan(hs_zplan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, double Lz,
                    int order);
 
-/* hs_zplan_set_coeff -- K = k^2 at the nodes l = 0..Nz+1: host array of Nz + 2
+/* hs_zplan_set_coeff -- K = k^2 (Sections 3.2, 3.3 with complex K) at the
+ * nodes l = 0..Nz+1: host array of Nz + 2
  * (re, im) pairs, copied.  Errors: HS_ERR_INVALID_ARG (NULL, non-finite). */
 hs_status hs_zplan_set_coeff(hs_zplan_t plan, const double *K);
 
-/* hs_zplan_set_faces -- kind (HS_ZFACE_DIRICHLET / HS_ZFACE_ROBIN) of the z-lo
- * and z-hi faces; alpha, beta: host (re, im) pairs, read for Robin faces only
+/* hs_zplan_set_faces -- kind (HS_ZFACE_DIRICHLET / HS_ZFACE_ROBIN, eq. bc) of
+ * the z-lo and z-hi faces; alpha, beta: host (re, im) pairs, read for Robin faces only
  * (alpha != 0 there).  Errors: HS_ERR_INVALID_ARG, HS_ERR_OOM. */
 hs_status hs_zplan_set_faces(hs_zplan_t plan, int lo_kind, const double *alpha_lo,
                              const double *beta_lo, int hi_kind, const double *alpha_hi,
                              const double *beta_hi);
 
-/* hs_zsolve_ex -- hs_zsolve with data on Neumann side faces: side[0..3] are the
+/* hs_zsolve_ex -- hs_zsolve with data on Neumann side faces (Section 1): side[0..3] are the
  * outward normal derivative u_n = g on the x-lo, x-hi faces ([2][Nz+2][Ny+2],
  * planar complex, on the face node grid: planes l, nodes j = 0..Ny+1) and the
  * y-lo, y-hi faces ([2][Nz+2][Nx+2]); NULL entries (or side = NULL) are 0.  The
@@ -607,13 +611,13 @@ hs_status hs_zplan_set_faces(hs_zplan_t plan, int lo_kind, const double *alpha_l
 hs_status hs_zsolve_ex(hs_zplan_t plan, const double *f, const double *g_lo, const double *g_hi,
                        const double *const *side, double *u, void *stream);
 
-/* hs_zplan_set_sides -- kind (HS_SIDE_DIRICHLET / HS_SIDE_NEUMANN) of the x and
- * y side axes (default Dirichlet).  A Neumann axis needs N + 1 with a compiled
+/* hs_zplan_set_sides -- kind (HS_SIDE_DIRICHLET / HS_SIDE_NEUMANN, Section 1) of
+ * the x and y side axes (default Dirichlet).  A Neumann axis needs N + 1 with a compiled
  * transform (N + 1 in {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024}).
  * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED, HS_ERR_OOM. */
 hs_status hs_zplan_set_sides(hs_zplan_t plan, int x_kind, int y_kind);
 
-/* hs_zsolve -- one solve on `stream` (asynchronous; the caller keeps f, g and
+/* hs_zsolve -- one solve (Section 3.6 with complex rows) on `stream` (asynchronous; the caller keeps f, g and
  * u valid until the stream has passed it).  Errors: HS_ERR_INVALID_ARG (NULL
  * f or u, host pointers), HS_ERR_NO_COEFF (no coefficients yet, or an earlier
  * hs_zplan_set_faces / hs_zplan_set_sides failed part-way: repeat it),
