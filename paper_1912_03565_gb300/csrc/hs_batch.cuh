@@ -1,4 +1,4 @@
-// Device side of the batched persistent solve (shared by the kernel variants,
+// Device side of the batched persistent solve (Section 3.6 per problem) (shared by the kernel variants,
 // one translation unit each, and the host code in k_batch.cu).
 //
 // Many independent problems (uneven sizes, their own k(z), 1..4 right-hand

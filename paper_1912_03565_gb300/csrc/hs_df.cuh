@@ -1,4 +1,5 @@
-// Double-float ("FP32 pair") arithmetic for the mixed path.
+// Double-float ("FP32 pair") arithmetic for the mixed path (no paper
+// counterpart: the paper computes in FP64).
 //
 // GB300 executes FP32 about 62x faster than FP64 (74.5 vs 1.19 TFLOP/s
 // measured), so the mixed path keeps its accuracy-critical quantities -- the

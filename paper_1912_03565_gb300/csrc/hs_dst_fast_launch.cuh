@@ -1,4 +1,4 @@
-// Kernels and launchers of the compile-time-sized DST-I tiles; included by one
+// Kernels and launchers of the compile-time-sized DST-I tiles (Section 3.6); included by one
 // translation unit per group of output modes (k_dst_fast*.cu) so that the
 // kernel instances compile in parallel.
 #pragma once

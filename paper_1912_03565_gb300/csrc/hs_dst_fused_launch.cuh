@@ -1,4 +1,4 @@
-// Kernels and launcher of the fused DST tiles (hs_dst_fused.cuh); included by
+// Kernels and launcher of the fused DST-I tiles (Section 3.6; hs_dst_fused.cuh); included by
 // one translation unit per axis.
 #pragma once
 

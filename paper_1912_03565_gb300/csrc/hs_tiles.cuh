@@ -1,6 +1,7 @@
-// Tile functions shared by the stand-alone kernels and the batched persistent
-// kernel: one CTA's work for the transforms (k_dst_fast.cu), the double-float
-// right-hand side and residual (k_rhs.cu) and the z-solves (k_thomas.cu).
+// Tile functions (Sections 3.2-3.6) shared by the stand-alone kernels and the
+// batched persistent kernel: one CTA's work for the transforms (k_dst_fast.cu),
+// the double-float right-hand side and residual (k_rhs.cu) and the z-solves
+// (k_thomas.cu).
 // Each takes its tile index and, where it needs one, a pointer to the CTA's
 // shared memory instead of reading blockIdx or declaring shared arrays, so a
 // persistent CTA can run tiles of different stages one after another.

@@ -1,6 +1,7 @@
-// Batched solves in one persistent launch: host side (plans, work and item
-// lists, kernel variant and grid, graph capture).  The device side and the
-// scheduling scheme are in hs_batch.cuh.
+// Batched solves in one persistent launch (no paper counterpart; each problem
+// is Section 3.6's solve): host side (plans, work and item lists, kernel
+// variant and grid, graph capture).  The device side and the scheduling scheme
+// are in hs_batch.cuh.
 #include <string.h>
 
 #include <algorithm>

@@ -1,4 +1,4 @@
-// Persistent batch kernel: register cap for 2 resident CTAs of 256 threads per
+// Persistent batch kernel (Section 3.6's solve per work item): register cap for 2 resident CTAs of 256 threads per
 // SM, staged transform tiles.
 #include "hs_batch.cuh"
 

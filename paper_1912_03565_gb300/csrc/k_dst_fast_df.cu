@@ -1,4 +1,4 @@
-// Compile-time-sized DST-I tiles, FP32 compute: the double-float iterate modes
+// Compile-time-sized DST-I tiles (Section 3.6), FP32 compute: the double-float iterate modes
 // of the refined mixed path.
 #include "hs_dst_fast_launch.cuh"
 

@@ -1,4 +1,4 @@
-// Compile-time-sized DST-I tiles, FP32 compute: plain write / add modes.
+// Compile-time-sized DST-I tiles (Section 3.6), FP32 compute: plain write / add modes.
 #include "hs_dst_fast_launch.cuh"
 
 hs_status hs_dst_fast_f32(const hs_plan_s *P, int axis, int tin, const void *in, int tout,

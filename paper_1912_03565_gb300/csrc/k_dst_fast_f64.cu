@@ -1,4 +1,4 @@
-// Compile-time-sized DST-I tiles, FP64 compute (the FP64 path).
+// Compile-time-sized DST-I tiles (Section 3.6), FP64 compute (the FP64 path).
 #include "hs_dst_fast_launch.cuh"
 
 hs_status hs_dst_fast_f64(const hs_plan_s *P, int axis, int tin, const void *in, int tout,

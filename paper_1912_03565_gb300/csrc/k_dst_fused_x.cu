@@ -1,4 +1,4 @@
-// Fused DST tiles along x (FP32 compute): the modes of the mixed path.
+// Fused DST-I tiles (Section 3.6) along x (FP32 compute): the modes of the mixed path.
 #include "hs_dst_fused_launch.cuh"
 
 namespace {

@@ -1,4 +1,4 @@
-// Fused DST tiles along y (FP32 compute, in-place FP32 passes of the mixed path).
+// Fused DST-I tiles (Section 3.6) along y (FP32 compute, in-place FP32 passes of the mixed path).
 #include "hs_dst_fused_launch.cuh"
 
 namespace {

@@ -1,4 +1,4 @@
-// hs_residual_static: the L2 residual ||F - A U||_2 (and ||F||_2) of an
+// hs_residual_static: the L2 residual ||F - A U||_2 (L2-res of Section 5.1) (and ||F||_2) of an
 // assembled right-hand side, for callers that cannot allocate device memory.
 //
 // Who needs it: code that runs where cudaMalloc is not allowed or not
