@@ -159,8 +159,8 @@ hs_status hs_set_coeff(hs_plan_t plan, const double *c0, const double *c1, const
                        int cd_variant);
 
 /*
- * hs_set_coeff_fn -- hs_set_coeff (Sections 3.2-3.5) from a function: c0, c1, c2 are sampled as
- * fn(z_l, 0, user), fn(z_l, 1, user), fn(z_l, 2, user) at z_l = l hz,
+ * hs_set_coeff_fn -- hs_set_coeff (Sections 3.2-3.5) from a function: c0, c1,
+ * c2 are sampled as fn(z_l, 0, user), fn(z_l, 1, user), fn(z_l, 2, user) at z_l = l hz,
  * l = 0..Nz+1 (the coefficient and its first two z-derivatives: k^2 for
  * Helmholtz, gamma for convection-diffusion), on the calling thread, before
  * the call returns.  Same results and errors as hs_set_coeff.
@@ -169,18 +169,19 @@ typedef double (*hs_coeff_fn)(double z, int deriv, void *user);
 hs_status hs_set_coeff_fn(hs_plan_t plan, hs_coeff_fn fn, void *user, int cd_variant);
 
 /*
- * hs_set_refinement -- number of refinement sweeps of the HS_MIXED path (no
- * paper counterpart: the paper solves in FP64; each sweep reuses Section 3.6's solve)
+ * hs_set_refinement -- number of refinement sweeps of the HS_MIXED path
  * after its first solve (default 2; 0..HS_INFO_MAX_ITERS-1).  Each sweep
  * computes the residual r = F - A U (precision: hs_set_residual_precision)
- * and adds the fast solve of r to U.  Ignored by the HS_FP64 path.
+ * and adds the fast solve of r to U.  Ignored by the HS_FP64 path.  No paper
+ * counterpart (the paper solves in FP64); each sweep reuses Section 3.6's solve.
  * Errors: HS_ERR_INVALID_ARG (sweeps outside that range).
  */
 hs_status hs_set_refinement(hs_plan_t plan, int sweeps);
 
 /*
  * hs_set_residual_precision -- arithmetic of the refinement residual (the
- * 27-point operator of eq. stencil27) of the HS_MIXED path (the iterate U and F are kept as FP32 pairs either way):
+ * 27-point operator of eq. stencil27) of the HS_MIXED path (the iterate U and
+ * F are kept as FP32 pairs either way):
  *   HS_RESID_DF   FP32-pair arithmetic, rounding ~2^-47 of the largest term;
  *   HS_RESID_F64  FP64 arithmetic (2^-53), about 2x the time of HS_RESID_DF;
  *   HS_RESID_AUTO (default) FP32-pair residuals while each shrinks the previous
@@ -194,8 +195,9 @@ hs_status hs_set_residual_precision(hs_plan_t plan, int mode);
 
 /*
  * hs_set_refinement_tol -- tolerance-controlled refinement of the HS_MIXED
- * path (no paper counterpart; L2-res as in Section 5.1; iterative refinement U_{m+1} = U_m + M (F - A U_m), stopped once
- * ||F - A U_m||_2 / ||F||_2 <= tol or after the hs_set_refinement count).
+ * path (no paper counterpart; the measure is Section 5.1's L2-res): iterative
+ * refinement U_{m+1} = U_m + M (F - A U_m), stopped once
+ * ||F - A U_m||_2 / ||F||_2 <= tol or after the hs_set_refinement count.
  * tol = 0 (default) runs the fixed count.  The decision is taken on the device
  * (no host synchronisation): the kernels of sweeps after convergence return
  * at once.  With hs_info the same test is made on the host.
@@ -600,8 +602,8 @@ hs_status hs_zplan_set_faces(hs_zplan_t plan, int lo_kind, const double *alpha_l
                              const double *beta_lo, int hi_kind, const double *alpha_hi,
                              const double *beta_hi);
 
-/* hs_zsolve_ex -- hs_zsolve with data on Neumann side faces (Section 1): side[0..3] are the
- * outward normal derivative u_n = g on the x-lo, x-hi faces ([2][Nz+2][Ny+2],
+/* hs_zsolve_ex -- hs_zsolve with data on Neumann side faces (Section 1):
+ * side[0..3] are the outward normal derivative u_n = g on the x-lo, x-hi faces ([2][Nz+2][Ny+2],
  * planar complex, on the face node grid: planes l, nodes j = 0..Ny+1) and the
  * y-lo, y-hi faces ([2][Nz+2][Nx+2]); NULL entries (or side = NULL) are 0.  The
  * ghost beyond such a face is the mirror value plus 2 h g (second-order
@@ -611,14 +613,16 @@ hs_status hs_zplan_set_faces(hs_zplan_t plan, int lo_kind, const double *alpha_l
 hs_status hs_zsolve_ex(hs_zplan_t plan, const double *f, const double *g_lo, const double *g_hi,
                        const double *const *side, double *u, void *stream);
 
-/* hs_zplan_set_sides -- kind (HS_SIDE_DIRICHLET / HS_SIDE_NEUMANN, Section 1) of
- * the x and y side axes (default Dirichlet).  A Neumann axis needs N + 1 with a compiled
- * transform (N + 1 in {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024}).
+/* hs_zplan_set_sides -- kind (HS_SIDE_DIRICHLET / HS_SIDE_NEUMANN, Section 1)
+ * of the x and y side axes (default Dirichlet).  A Neumann axis needs N + 1
+ * with a compiled transform (N + 1 in {32, 64, 96, 128, 192, 256, 384, 512,
+ * 768, 1024}).
  * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED, HS_ERR_OOM. */
 hs_status hs_zplan_set_sides(hs_zplan_t plan, int x_kind, int y_kind);
 
-/* hs_zsolve -- one solve (Section 3.6 with complex rows) on `stream` (asynchronous; the caller keeps f, g and
- * u valid until the stream has passed it).  Errors: HS_ERR_INVALID_ARG (NULL
+/* hs_zsolve -- one solve (Section 3.6 with complex rows) on `stream`
+ * (asynchronous; the caller keeps f, g and u valid until the stream has
+ * passed it).  Errors: HS_ERR_INVALID_ARG (NULL
  * f or u, host pointers), HS_ERR_NO_COEFF (no coefficients yet, or an earlier
  * hs_zplan_set_faces / hs_zplan_set_sides failed part-way: repeat it),
  * HS_ERR_CUDA. */
