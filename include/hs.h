@@ -603,9 +603,10 @@ hs_status hs_zplan_set_faces(hs_zplan_t plan, int lo_kind, const double *alpha_l
                              const double *beta_hi);
 
 /* hs_zsolve_ex -- hs_zsolve with data on Neumann side faces (Section 1):
- * side[0..3] are the outward normal derivative u_n = g on the x-lo, x-hi faces ([2][Nz+2][Ny+2],
- * planar complex, on the face node grid: planes l, nodes j = 0..Ny+1) and the
- * y-lo, y-hi faces ([2][Nz+2][Nx+2]); NULL entries (or side = NULL) are 0.  The
+ * side[0..3] are the outward normal derivative u_n = g on the x-lo, x-hi
+ * faces ([2][Nz+2][Ny+2], planar complex, on the face node grid: planes l,
+ * nodes j = 0..Ny+1) and the y-lo, y-hi faces ([2][Nz+2][Nx+2]); NULL entries
+ * (or side = NULL) are 0.  The
  * ghost beyond such a face is the mirror value plus 2 h g (second-order
  * central difference), a face's data reflected evenly beyond its own edges.
  * Data on the faces of a Dirichlet axis are rejected (HS_ERR_INVALID_ARG).
