@@ -9,7 +9,8 @@ compact scheme with K U averaged like f in the right-hand side.  What pins it:
       that node (weight h_z^2 K U_m / 2) and its six face neighbours (h_z^2 K U_m / 12);
   (c) on a uniform grid the operator commutes with every permutation of the axes;
   (d) with K = K(z) the preconditioner is exact: BiCGStab converges in one step;
-  (e) BiCGStab's answer equals a direct solve of the assembled matrix;
+  (e) BiCGStab's answer equals a direct solve of the assembled matrix, and its
+      iterates equal those of scipy's BiCGStab;
   (f) mutations: K U taken pointwise, or the preconditioner left out, makes a pin fail.
 """
 import itertools
@@ -102,6 +103,30 @@ def test_bicgstab_matches_direct_solve(order):
     true_res = np.linalg.norm(PC.apply_general(order, K, x, h) - F) / np.linalg.norm(F)
     assert true_res <= 1e-12
 
+
+
+def test_bicgstab_steps_are_the_library_bicgstab():
+    """The right-preconditioned BiCGStab of van der Vorst against scipy's implementation
+    of the same recurrence, with the same operator and preconditioner: the iterates after
+    1, 2, 3 and 5 iterations agree (a wrong step of the recurrence changes them)."""
+    spla = pytest.importorskip("scipy.sparse.linalg")
+    Nz, Ny, Nx = 5, 6, 7
+    h = O.grid_steps((Nx, Ny, Nz), (1.0, 1.0, 1.0))
+    rs = np.random.RandomState(6)
+    K = 20.0 * (1.0 + 0.3 * rs.uniform(-1, 1, (Nz, Ny, Nx)))
+    F = rs.uniform(-1, 1, (Nz, Ny, Nx))
+    C = O.stencil_coefficients(4, O.HELMHOLTZ, h, PC.reference_from_field(K))
+    op = lambda u: PC.apply_general(4, K, u, h)
+    pre = lambda r: O.solve_assembled(C, r)[0]
+    n = K.size
+    A = spla.LinearOperator((n, n), matvec=lambda v: op(v.reshape(K.shape)).ravel())
+    M = spla.LinearOperator((n, n), matvec=lambda v: pre(v.reshape(K.shape)).ravel())
+    for it in (1, 2, 3, 5):
+        ref, _ = spla.bicgstab(A, F.ravel(), x0=np.zeros(n), rtol=1e-300, atol=0.0,
+                               maxiter=it, M=M)
+        x, hist = PC.bicgstab(op, pre, F, tol=0.0, maxit=it)
+        assert len(hist) == it
+        assert np.max(np.abs(x.ravel() - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 # ----------------------------------------------------------------- mutations
 # A plausible mistake planted in the oracle (on the CPU, through monkeypatch) must make
