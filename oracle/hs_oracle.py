@@ -32,7 +32,7 @@ What it computes (arXiv 1912.03565, Gonzales, Gryazin, Lee):
 Readings where the paper is garbled (fixed, with the symbolic checks that
 decided them, in the design notes):
   * R6 (6th-order right-hand side, eq. scheme6).  The term k_l^2 U_ijl inside
-    Delta_h(k^2 U) is k^2 f, and "nabla^4 f" is the sum of the pure fourth
+    Delta_h(k^2 U) is k^2 f, and the nabla^4 f term is the sum of the pure fourth
     derivatives.  The f-derivatives are approximated explicitly (the paper's
     implicit compact approximation is not specified):
         F6 / h^2 = f + (1/12)(Dx + Dy + Dz) f - (1/240)(Dx^2 + Dy^2 + Dz^2) f

@@ -2,7 +2,7 @@
 // (N + 1 = M in {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024}).
 //
 // Same algorithm as k_dst.cu (odd extension, length-M complex FFT of the
-// packed line, X_k from W_k and W_{M-k}; Section 3.6's "2D DST by FFT"), but
+// packed line, X_k from W_k and W_{M-k}; Section 3.6's 2-D DST through FFTs), but
 // every size, radix and stride is a template constant: the index arithmetic
 // of the Stockham stages becomes shifts and multiplies, and each thread does
 // one radix-R butterfly (R up to 16) in registers per stage, so a 256-point

@@ -3,8 +3,8 @@
 // Row l of the system of mode (p, q) is
 //     lambda_{l-1}(p,q) w_{l-1} + lambda_l(p,q) w_l + lambda_{l+1}(p,q) w_{l+1} = Fhat_l,
 //     lambda_nu(p,q) = 4 a_nu cos(th_p) cos(th_q) + 2 b_nu cos(th_p) + 2 c_nu cos(th_q) + d_nu,
-// with the coefficients of row l.  It is solved by LU without pivoting (the
-// paper's "LU decomposition"; the systems are indefinite for k^2 above the
+// with the coefficients of row l.  It is solved by LU without pivoting (Section
+// 3.6 names an LU solve and no pivoting; the systems are indefinite for k^2 above the
 // mode's eigenvalue, so small pivots are reported, not avoided).
 //
 // The elimination factors do not depend on the right-hand side, so they are
