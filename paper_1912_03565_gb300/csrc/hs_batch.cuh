@@ -296,7 +296,7 @@ __device__ __forceinline__ void batch_body(const BatchArgs &A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_it, s_wi, s_stage, s_tile, s_bail;
     __shared__ int s_pend_w, s_pend_s, s_ok_w, s_ok_s;  // thread 0's bookkeeping
-    int next_it = 0;  // thread 0: the item claimed for the next round (kept in a register
+    int next_it = 0;  // thread 0: the item claimed for the next loop trip (kept in a register
                       // so the atomic's latency overlaps the current tile)
     if (threadIdx.x == 0) {
         next_it = atomicAdd(A.next, 1);
