@@ -29,8 +29,10 @@ What it computes (arXiv 1912.03565, Gonzales, Gryazin, Lee):
     leaving N_x N_y independent tridiagonal systems in z, solved by LU
     (Thomas, no pivoting), followed by the inverse transform U_l = V W_l.
 
-Readings where the paper is garbled (fixed, with the symbolic checks that
-decided them, in the design notes):
+Readings where the paper is garbled (each one decided by the truncation order
+it gives: with the reading taken, the scheme's local truncation error on a
+smooth solution falls at the scheme's order when h is halved, which the test
+suite checks; with the printed form it does not):
   * R6 (6th-order right-hand side, eq. scheme6).  The term k_l^2 U_ijl inside
     Delta_h(k^2 U) is k^2 f, and the nabla^4 f term is the sum of the pure fourth
     derivatives.  The f-derivatives are approximated explicitly (the paper's
@@ -476,6 +478,76 @@ def solve_sine_modes(modes, amps, N, L, order, c0, c1=None, c2=None, sample=None
 
 # --------------------------------------------------------------------------
 # diagnostics (Section 5.1 error measures)
+
+
+def solve_sine_modes_extended(modes, amps, N, c0, c1, c2, sample):
+    """solve_sine_modes for the 6th-order scheme on a grid of one spacing h =
+    1/(max N_a + 1) (N an int for the cube, or (Nx, Ny, Nz); the box is
+    L_a = (N_a + 1) h and mode m is sin(p pi x / Lx) sin(q pi y / Ly)
+    sin(r pi z / Lz)), with every step in extended precision (numpy longdouble:
+    at least 64 significand bits): the Section 3.4 coefficients, the separable
+    right-hand side of each mode, the cosines of the mode angles, the Thomas sweep
+    of each (p, q) system (Section 3.6) and the sum over modes.  The coefficient
+    samples c0..c2 are taken as exact.  Returns U at the `sample` points (i, j, l
+    arrays of 1-based interior indices), rounded to FP64.
+
+    Purpose: the exact discrete solution when the z-systems are ill conditioned,
+    where any FP64 solve (this oracle's included) carries a rounding error of order
+    eps / (smallest singular value ratio); an FP64 result is then measured against
+    this one, not against another FP64 computation."""
+    LD = np.longdouble
+    if np.finfo(LD).nmant < 63:
+        raise RuntimeError("extended precision (longdouble with >= 64 significand bits) needed")
+    pi = LD("3.14159265358979323846264338327950288419716939937510582097494459")
+    Nx, Ny, Nz = (N, N, N) if np.isscalar(N) else (int(v) for v in N)
+    h = LD(1) / LD(max(Nx, Ny, Nz) + 1)
+    h2, h3, h4 = h * h, h * h * h, h * h * h * h
+    K = np.asarray(c0, dtype=np.float64).astype(LD)
+    Kz = np.asarray(c1, dtype=np.float64).astype(LD)
+    Kzz = np.asarray(c2, dtype=np.float64).astype(LD)
+    Kl, Km, Kp, Kzl, Kzzl = K[1:-1], K[:-2], K[2:], Kz[1:-1], Kzz[1:-1]
+    one = LD(1)
+    # rows nu = l - 1, l, l + 1: (a, b = c, d), Section 3.4
+    rows = ((np.full(Nz, one / 30), one / 10 + h2 * Km / 90 - h3 * Kzl / 120,
+             LD(7) / 15 - h2 * Km / 90 - (h3 * Kzl / 20) * (one / 3 + h2 * Km / 6)),
+            (one / 10 + h2 * Kl / 90, LD(7) / 15 - h2 * Kl / 90,
+             -LD(64) / 15 + 14 * h2 * Kl / 15 - h4 * Kl * Kl / 20 + h4 * Kzzl / 20),
+            (np.full(Nz, one / 30), one / 10 + h2 * Kp / 90 + h3 * Kzl / 120,
+             LD(7) / 15 - h2 * Kp / 90 + (h3 * Kzl / 20) * (one / 3 + h2 * Kp / 6)))
+
+    def sines(m, idx, n):
+        return np.sin(pi * np.asarray((m * idx) % (2 * (n + 1)), dtype=LD) / LD(n + 1))
+
+    lz = np.arange(0, Nz + 2)
+    groups = {}
+    for (p, q, r), A in zip(modes, amps):
+        s = LD(float(A)) * sines(int(r), lz, Nz)
+        mu = [2 * np.cos(pi * LD(int(v)) / LD(n + 1)) - 2 for v, n in ((p, Nx), (q, Ny), (r, Nz))]
+        si = s[1:-1]
+        base = (one + (mu[0] + mu[1] + mu[2]) / 12 - (mu[0] ** 2 + mu[1] ** 2 + mu[2] ** 2) / 240
+                + (mu[0] * mu[1] + mu[0] * mu[2] + mu[1] * mu[2]) / 90)
+        phi = h2 * (base * si - h2 * Kl * si / 20 + h3 * Kzl * (s[2:] - s[:-2]) / 120)
+        key = (int(p), int(q))
+        groups[key] = groups.get(key, LD(0)) + phi
+    si_, sj_, sl_ = (np.asarray(a) for a in sample)
+    U = np.zeros(si_.shape, dtype=LD)
+    for (p, q), phi in groups.items():
+        cp, cq = np.cos(pi * LD(p) / LD(Nx + 1)), np.cos(pi * LD(q) / LD(Ny + 1))
+        lo, di, up = (4 * a * cp * cq + 2 * b * cp + 2 * b * cq + d for (a, b, d) in rows)
+        cpr = np.empty(Nz, dtype=LD)
+        dpr = np.empty(Nz, dtype=LD)
+        cpr[0], dpr[0] = up[0] / di[0], phi[0] / di[0]
+        for l in range(1, Nz):
+            m = di[l] - lo[l] * cpr[l - 1]
+            cpr[l] = up[l] / m
+            dpr[l] = (phi[l] - lo[l] * dpr[l - 1]) / m
+        w = np.empty(Nz, dtype=LD)
+        w[Nz - 1] = dpr[Nz - 1]
+        for l in range(Nz - 2, -1, -1):
+            w[l] = dpr[l] - cpr[l] * w[l + 1]
+        U += (w[sl_ - 1] * sines(q, np.arange(1, Ny + 1), Ny)[sj_ - 1]
+              * sines(p, np.arange(1, Nx + 1), Nx)[si_ - 1])
+    return U.astype(np.float64)
 
 
 def pad_boundary(U, faces=None):

@@ -430,3 +430,92 @@ def test_sine_mode_solution_matches_full_oracle(order):
     pts = (np.array([1, 5, N[0]]), np.array([2, N[1], 7]), np.array([N[2], 3, 1]))
     Us = O.solve_sine_modes(modes, amps, N, L, order, c0, c1, c2, sample=pts)
     assert np.allclose(Us, U[pts[2] - 1, pts[1] - 1, pts[0] - 1], rtol=0, atol=1e-12 * np.abs(U).max())
+
+
+def test_sine_mode_solution_in_extended_precision():
+    """solve_sine_modes_extended (the exact discrete solution for ill-conditioned
+    z-systems) is pinned twice:
+    * where the problem is well conditioned (31^3) it equals the FP64 sine-mode
+      solution, itself pinned against the full oracle, to FP64 rounding;
+    * on a tiny grid (7^3) it equals an independent 40-digit computation: mpmath
+      arithmetic, the z-systems solved by dense LU (not Thomas), the sine modes
+      built as full 3-D fields and projected, so only the Section 3.4 rows are
+      shared; agreement to the FP64 rounding of the output."""
+    mp = pytest.importorskip("mpmath")
+    N = 31
+    modes, amps = W.sine_modes(N, 16, 4)
+    c = W.k_profile_to_k2(W.k_tanh()).sample(N, 1.0)
+    rs = np.random.RandomState(0)
+    pts = tuple(rs.randint(1, N + 1, size=2000) for _ in range(3))
+    ex = O.solve_sine_modes_extended(modes, amps, N, *c, sample=pts)
+    f64 = O.solve_sine_modes(modes, amps, (N, N, N), (1.0, 1.0, 1.0), 6, *c, sample=pts)
+    assert np.abs(ex - f64).max() <= 1e-12 * np.abs(ex).max()
+
+    mp.mp.dps = 40
+    n = 7
+    modes = np.array([[1, 2, 3], [3, 1, 2], [1, 2, 5], [7, 7, 1]])
+    amps = np.array([1.0, -0.5, 0.25, 2.0])
+    k = W.k_profile_to_k2(W.k_tanh(40.0, 20.0))
+    c0, c1, c2 = k.sample(n, 1.0)
+    idx = np.arange(1, n + 1)
+    grid = np.meshgrid(idx, idx, idx, indexing="ij")   # (i, j, l)
+    ex = O.solve_sine_modes_extended(modes, amps, n, c0, c1, c2,
+                                     sample=(grid[0].ravel(), grid[1].ravel(), grid[2].ravel()))
+    h = mp.mpf(1) / (n + 1)
+    m = lambda v: mp.mpf(float(v))
+    K = [m(v) for v in c0]
+    Kz = [m(v) for v in c1]
+    Kzz = [m(v) for v in c2]
+
+    def rows(l):   # (a, b, d) for nu = l-1, l, l+1 of row l (1-based), Section 3.4
+        return ((mp.mpf(1) / 30, mp.mpf(1) / 10 + h**2 * K[l - 1] / 90 - h**3 * Kz[l] / 120,
+                 mp.mpf(7) / 15 - h**2 * K[l - 1] / 90 - (h**3 * Kz[l] / 20) * (mp.mpf(1) / 3 + h**2 * K[l - 1] / 6)),
+                (mp.mpf(1) / 10 + h**2 * K[l] / 90, mp.mpf(7) / 15 - h**2 * K[l] / 90,
+                 -mp.mpf(64) / 15 + 14 * h**2 * K[l] / 15 - h**4 * K[l]**2 / 20 + h**4 * Kzz[l] / 20),
+                (mp.mpf(1) / 30, mp.mpf(1) / 10 + h**2 * K[l + 1] / 90 + h**3 * Kz[l] / 120,
+                 mp.mpf(7) / 15 - h**2 * K[l + 1] / 90 + (h**3 * Kz[l] / 20) * (mp.mpf(1) / 3 + h**2 * K[l + 1] / 6)))
+
+    # f = sum of modes on the node grid; F by the explicit 25-point operator R6
+    # written point by point; projected on each (p, q) sine mode, solved by dense LU
+    S = lambda a, i: mp.sin(mp.pi * a * i / (n + 1))
+    f = {}
+    for i in range(-1, n + 3):
+        for j in range(-1, n + 3):
+            for l in range(-1, n + 3):
+                f[i, j, l] = sum(mp.mpf(float(A)) * S(p, i) * S(q, j) * S(r, l)
+                                 for (p, q, r), A in zip(modes, amps))
+    U = np.zeros((n, n, n))   # [i, j, l]
+    Ump = {}
+    for (p, q) in sorted({(int(a), int(b)) for a, b, _ in modes}):
+        rhs = mp.matrix(n, 1)
+        for l in range(1, n + 1):
+            acc = mp.mpf(0)
+            for i in range(1, n + 1):
+                for j in range(1, n + 1):
+                    c = f[i, j, l]
+                    s1 = sum(f[i + a, j + b, l + g] for a, b, g in
+                             ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)))
+                    s2 = sum(f[i + a, j + b, l + g] for a, b, g in
+                             ((2, 0, 0), (-2, 0, 0), (0, 2, 0), (0, -2, 0), (0, 0, 2), (0, 0, -2)))
+                    e = sum(f[i + a, j + b, l + g] for a, b, g in
+                            ((1, 1, 0), (1, -1, 0), (-1, 1, 0), (-1, -1, 0), (1, 0, 1), (1, 0, -1),
+                             (-1, 0, 1), (-1, 0, -1), (0, 1, 1), (0, 1, -1), (0, -1, 1), (0, -1, -1)))
+                    F6 = h**2 * ((mp.mpf(67) / 120 - h**2 * K[l] / 20) * c + s1 / 18 - s2 / 240 + e / 90
+                                 + h**3 * Kz[l] * (f[i, j, l + 1] - f[i, j, l - 1]) / 120)
+                    acc += F6 * S(p, i) * S(q, j)
+            rhs[l - 1] = acc * 4 / (n + 1) ** 2     # coefficient of sin_p sin_q
+        T = mp.matrix(n, n)
+        cp, cq = mp.cos(mp.pi * p / (n + 1)), mp.cos(mp.pi * q / (n + 1))
+        for l in range(1, n + 1):
+            for nu, (a, b, d) in enumerate(rows(l)):
+                ll = l - 1 + nu
+                if 1 <= ll <= n:
+                    T[l - 1, ll - 1] = 4 * a * cp * cq + 2 * b * cp + 2 * b * cq + d
+        w = mp.lu_solve(T, rhs)
+        for i in range(1, n + 1):
+            for j in range(1, n + 1):
+                for l in range(1, n + 1):
+                    Ump[i, j, l] = Ump.get((i, j, l), mp.mpf(0)) + w[l - 1] * S(p, i) * S(q, j)
+    ref = np.array([float(Ump[i, j, l]) for i, j, l in
+                    zip(grid[0].ravel(), grid[1].ravel(), grid[2].ravel())])
+    assert np.abs(ex - ref).max() <= 4e-16 * np.abs(ref).max()
