@@ -70,7 +70,7 @@ enum { HS_F64 = 0, HS_F32 = 1 };                             /* element type of 
 enum { HS_RHS_NODAL = 0, HS_RHS_ASSEMBLED = 1 };             /* meaning of f */
 enum { HS_RESID_DF = 0, HS_RESID_F64 = 1, HS_RESID_AUTO = 2 }; /* refinement residual */
 enum { HS_DST_STAGED = 0, HS_DST_FUSED = 1, HS_DST_GENERIC = 2,   /* transform kernels */
-       HS_DST_TWOPASS = 3, HS_DST_FUSED_WIDE = 4 };
+       HS_DST_TWOPASS = 3, HS_DST_FUSED_WIDE = 4, HS_DST_GEMM = 5 };
 enum { HS_AXIS_X = 0, HS_AXIS_Y = 1 };                       /* transform axis */
 enum { HS_FACTOR_AUTO = 0, HS_FACTOR_F32 = 1, HS_FACTOR_F64 = 2 }; /* mixed z-solve factors */
 enum { HS_HOST_F_MAPPED = 1, HS_HOST_U_MAPPED = 2, HS_HOST_F_EARLY = 4,     /* hs_set_host_io */
@@ -188,7 +188,11 @@ hs_status hs_set_refinement(hs_plan_t plan, int sweeps);
  *                 one by at least 16x (||r_0|| = ||F||), FP64 from the sweep
  *                 after one that did not: the pair residual has reached its
  *                 floor (an FP32 correction solve contracts far more).
- *                 Decided on the device from the accumulated norms.
+ *                 Decided on the device from the accumulated norms.  A plan
+ *                 whose z-systems are close to singular (min pivot ratio
+ *                 below 1e-4, hs_info) takes FP64 from the first sweep: there
+ *                 the pair residual's rounding, amplified by the conditioning,
+ *                 would limit the refined accuracy.
  * Errors: HS_ERR_INVALID_ARG.
  */
 hs_status hs_set_residual_precision(hs_plan_t plan, int mode);
@@ -222,7 +226,16 @@ hs_status hs_set_refinement_tol(hs_plan_t plan, double tol);
  *   HS_DST_FUSED_WIDE  HS_DST_FUSED with twice the lines per CTA (for y,
  *                  longer row segments per access), for the lengths whose
  *                  tile then still runs its stages in one shared buffer
- *                  (HS_ERR_UNSUPPORTED for the others).
+ *                  (HS_ERR_UNSUPPORTED for the others);
+ *   HS_DST_GEMM    HS_MIXED plans, N + 1 in {32, 64, 96, 128, 192, 256}: the
+ *                  transform as a product with the sine matrix on the tensor
+ *                  cores (Section 3.6's V^T F_l; tcgen05 MMA, FP16 x 2 split
+ *                  operands, FP32 accumulation in tensor memory, each line
+ *                  scaled by a power of two first), accurate to about 2^-22 of
+ *                  each line's largest value like an FP32 FFT; allocates the
+ *                  split sine matrix (at most 256 KB per axis).  A kernel whose
+ *                  bounded internal wait gave up makes the next synchronous
+ *                  call (hs_solve with info, hs_autotune) return HS_ERR_TIMEOUT.
  * Results agree to rounding.  Default: HS_DST_STAGED where compiled.
  * Errors: HS_ERR_INVALID_ARG; HS_ERR_UNSUPPORTED (variant not built for this
  * length, axis or precision); HS_ERR_OOM.
@@ -347,6 +360,21 @@ hs_status hs_residual(hs_plan_t plan, const void *f, int f_dtype, int rhs_kind,
                       double *res_norm, double *rhs_norm);
 
 /*
+ * hs_rhs_apply -- the lifted right-hand side F of one right-hand side exactly
+ * as a solve forms it: the scheme's operator R_h applied to f (eqs. scheme4,
+ * scheme6, cd_rhs; hz^2 f at 2nd order) minus the Dirichlet lifting (problem
+ * statement eq. (bc)), or an assembled F copied (HS_RHS_ASSEMBLED, lifting
+ * still applied).  f, F: DEVICE pointers (host pointers return
+ * HS_ERR_INVALID_ARG); bnd as for hs_solve.  F: FP64 plan -> FP64
+ * [Nz][Ny][Nx]; HS_MIXED plan -> the FP32 pair the mixed path works with, two
+ * planes [2][Nz][Ny][Nx] (hi, then lo; F = hi + lo).  Asynchronous on
+ * `stream`.  Errors: HS_ERR_INVALID_ARG, HS_ERR_NO_COEFF, HS_ERR_OOM (host
+ * boundary staging), HS_ERR_CUDA.
+ */
+hs_status hs_rhs_apply(hs_plan_t plan, const void *f, int f_dtype, int rhs_kind,
+                       const hs_boundary *bnd, void *F, void *stream);
+
+/*
  * hs_stage_times -- device time per stage (ms[HS_INFO_STAGES], indexed by
  * HS_STAGE_*) summed over the last hs_solve on this plan, when stage timing
  * was on; HS_STAGE_TOTAL is the whole call.  Waits for that solve's events.
@@ -371,11 +399,15 @@ hs_status hs_stage_times(hs_plan_t plan, float *ms);
  * of up to HS_STATIC_MAX_NZ rows plus partial sums, about 0.8 MB) that every
  * GPU loading the library holds until exit.  Nz > HS_STATIC_MAX_NZ returns
  * HS_ERR_UNSUPPORTED.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Calls share the array: calls that
+ * device address (cudaGetSymbolAddress) with that device current.  Every call
+ * copies the coefficient table from host memory and synchronises the stream,
+ * so it must not be made on a stream that is being captured (a capturing
+ * stream returns HS_ERR_INVALID_ARG).  Calls share the array: calls that
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  Synchronous: returns after the norms are read.
- * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED, HS_ERR_CUDA.
+ * F and u must be memory of the current device (or managed memory).  Order 6
+ * needs hx = hy = hz (as hs_plan).  Errors: HS_ERR_INVALID_ARG,
+ * HS_ERR_UNSUPPORTED, HS_ERR_NONFINITE (c0..c2), HS_ERR_CUDA.
  */
 #define HS_STATIC_MAX_NZ 8192
 hs_status hs_residual_static(int Nx, int Ny, int Nz, double Lx, double Ly, double Lz, int order,

@@ -35,7 +35,8 @@ HS_CD_PAPER, HS_CD_CORRECTED = 0, 1
 HS_F64, HS_F32 = 0, 1
 HS_RHS_NODAL, HS_RHS_ASSEMBLED = 0, 1
 HS_RESID_DF, HS_RESID_F64, HS_RESID_AUTO = 0, 1, 2
-HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC, HS_DST_TWOPASS, HS_DST_FUSED_WIDE = 0, 1, 2, 3, 4
+HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC, HS_DST_TWOPASS, HS_DST_FUSED_WIDE, HS_DST_GEMM = (
+    0, 1, 2, 3, 4, 5)
 HS_AXIS_X, HS_AXIS_Y = 0, 1
 HS_FACTOR_AUTO, HS_FACTOR_F32, HS_FACTOR_F64 = 0, 1, 2
 HS_HOST_F_MAPPED, HS_HOST_U_MAPPED, HS_HOST_F_EARLY, HS_HOST_U_LATE = 1, 2, 4, 8
@@ -48,7 +49,7 @@ STAGES = ("rhs", "dst_x", "dst_y", "thomas", "idst_y", "idst_x", "residual", "to
 
 EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_tol",
             "hs_set_stage_timing", "hs_solve",
-            "hs_residual", "hs_stage_times", "hs_workspace_bytes", "hs_destroy",
+            "hs_residual", "hs_rhs_apply", "hs_stage_times", "hs_workspace_bytes", "hs_destroy",
             "hs_status_str", "hs_last_error", "hs_residual_static", "hs_batch_create",
             "hs_batch_set_io", "hs_batch_solve", "hs_batch_set_wait_limit", "hs_batch_set_tol",
             "hs_batch_set_residual_precision", "hs_batch_debug_stall", "hs_set_residual_precision",
@@ -148,6 +149,8 @@ def load(path: Optional[str] = None):
     lib.hs_residual.argtypes = [vp, vp, ci, ci, ctypes.POINTER(hs_boundary), vp, vp,
                                 ctypes.POINTER(cd), ctypes.POINTER(cd)]
     lib.hs_residual.restype = ci
+    lib.hs_rhs_apply.argtypes = [vp, vp, ci, ci, ctypes.POINTER(hs_boundary), vp, vp]
+    lib.hs_rhs_apply.restype = ci
     lib.hs_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.hs_stage_times.restype = ci
     lib.hs_residual_static.argtypes = [ci, ci, ci, cd, cd, cd, ci, ci, ci, vp, vp, vp, vp, vp, vp,
@@ -340,6 +343,14 @@ def hs_residual(plan, f, f_dtype, rhs_kind, bnd, u, stream=None):
     return r.value, n.value
 
 
+def hs_rhs_apply(plan, f, f_dtype, rhs_kind, bnd, F, stream=None):
+    """The lifted right-hand side as a solve forms it (device arrays; FP64 plan:
+    F FP64 [Nz][Ny][Nx]; mixed plan: F FP32 [2][Nz][Ny][Nx], hi then lo)."""
+    return _check(load().hs_rhs_apply(plan, _ptr(f), f_dtype, rhs_kind,
+                                      ctypes.byref(bnd) if bnd is not None else None, _ptr(F),
+                                      _stream_ptr(stream)), "hs_rhs_apply", plan)
+
+
 def hs_stage_times(plan):
     """Per-stage device ms of the last solve (stage timing on), keyed by STAGES."""
     arr = (ctypes.c_float * HS_INFO_STAGES)()
@@ -349,9 +360,24 @@ def hs_stage_times(plan):
 
 def hs_residual_static(Nx, Ny, Nz, Lx, Ly, Lz, order, equation, cd_variant, c0, c1, c2, F, u,
                        stream=None):
-    """||F - A U||_2, ||F||_2 without any allocation in the library (F, u device arrays)."""
+    """||F - A U||_2, ||F||_2 without any allocation in the library (F, u device arrays).
+
+    The C side receives bare pointers, so the sizes and types are checked here:
+    c0..c2 hold Nz + 2 values, F and u are contiguous FP64 arrays of Nx Ny Nz
+    elements (torch tensors on the current CUDA device)."""
     import numpy as np
     arrs = [None if c is None else np.ascontiguousarray(c, dtype=np.float64) for c in (c0, c1, c2)]
+    for name, a in zip(("c0", "c1", "c2"), arrs):
+        if a is not None and a.size != Nz + 2:
+            raise ValueError(f"{name} must hold Nz + 2 = {Nz + 2} values, got {a.size}")
+    n = int(Nx) * int(Ny) * int(Nz)
+    for name, a in (("F", F), ("u", u)):
+        dt = getattr(a, "dtype", None)
+        if str(dt) not in ("torch.float64", "float64"):
+            raise ValueError(f"{name} must be float64, got {dt}")
+        numel = a.numel() if hasattr(a, "numel") and callable(a.numel) else int(np.size(a))
+        if numel != n:
+            raise ValueError(f"{name} must hold Nx*Ny*Nz = {n} values, got {numel}")
     r = ctypes.c_double()
     n = ctypes.c_double()
     _check(load().hs_residual_static(Nx, Ny, Nz, Lx, Ly, Lz, order, equation, cd_variant,

@@ -171,12 +171,44 @@ void free_ytmp(hs_plan_s *P) {
     P->d_ytmp = nullptr;
 }
 
+// The tensor-core transform's split sine matrix of one axis (and the plan's
+// error flag of those kernels), built on first use.
+hs_status ensure_gemm_table(hs_plan_s *P, int axis) {
+    if (!P->d_gemm_err) {
+        HS_TRY(P, dev_alloc(P, &P->d_gemm_err, (size_t)1));
+        HS_CK(P, cudaMemset(P->d_gemm_err, 0, sizeof(int)));
+    }
+    if (P->d_gemm[axis]) return HS_OK;
+    const int M = P->axf[axis].M;
+    const size_t bytes = hs_dst_gemm_table_bytes(M);
+    std::vector<uint8_t> h(bytes);
+    hs_dst_gemm_table(M, h.data());
+    uint8_t *d = nullptr;
+    HS_TRY(P, dev_alloc(P, &d, bytes));
+    P->d_gemm[axis] = d;
+    HS_CK(P, cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice));
+    return HS_OK;
+}
+
+// HS_ERR_TIMEOUT (and the flag cleared) when a tensor-core transform gave up a
+// wait since the last check; synchronous.
+hs_status check_gemm_err(hs_plan_s *P) {
+    if (!P->d_gemm_err) return HS_OK;
+    int e = 0;
+    HS_CK(P, cudaMemcpy(&e, P->d_gemm_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!e) return HS_OK;
+    HS_CK(P, cudaMemset(P->d_gemm_err, 0, sizeof(int)));
+    set_err(P, "a tensor-core transform kernel gave up a wait");
+    return HS_ERR_TIMEOUT;
+}
+
 void free_plan(hs_plan_s *P) {
     if (!P) return;
     void *ptrs[] = {P->d_coef, P->d_c0, P->d_c1, P->d_cx, P->d_cy, P->d_fac, P->d_red,
                     P->d_tables, P->d_w64, P->d_w32, P->d_dscr, P->d_stage_f, P->d_stage_u,
                     P->d_stage_bnd, P->d_fac32, P->d_coef_df, P->d_Fdf, P->d_Udf, P->d_rhs_df,
-                    P->d_skip, P->d_ytmp, P->d_stage_u1, P->d_stage_f1, P->d_stage_bnd1};
+                    P->d_skip, P->d_ytmp, P->d_stage_u1, P->d_stage_f1, P->d_stage_bnd1,
+                    P->d_gemm[0], P->d_gemm[1], P->d_gemm_err};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->have_up) {
@@ -456,9 +488,20 @@ hs_status residual_norms(hs_plan_s *P, const double *F, const double *U, cudaStr
 // One right-hand side: F (lifted, FP64) is in P->d_w64 on entry.
 // Does a mixed solve accumulate ||F||^2 and ||r_m||^2 on the device (tolerance
 // stop or the automatic residual precision, without hs_info)?
+// Residual precision the mixed solve uses: the automatic mode takes FP64 from the
+// first sweep on plans whose z-systems are close to singular (min pivot ratio below
+// HS_ILL_PIVOT, where the FP64 factors are kept too): there the pair residual's
+// rounding floor, amplified by the conditioning, is above the refined accuracy.
+int effective_resid_mode(const hs_plan_s *P) {
+    if (P->resid_mode == HS_RESID_AUTO && P->have_coeff && P->min_pivot_ratio < HS_ILL_PIVOT)
+        return HS_RESID_F64;
+    return P->resid_mode;
+}
+
 bool refine_norms_on(const hs_plan_s *P, bool info) {
     if (P->precision != HS_MIXED || info || P->refine_sweeps < 1) return false;
-    return P->refine_tol > 0 || (P->resid_mode == HS_RESID_AUTO && P->refine_sweeps >= 2);
+    return P->refine_tol > 0 ||
+           (effective_resid_mode(P) == HS_RESID_AUTO && P->refine_sweeps >= 2);
 }
 
 hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_info *info) {
@@ -500,9 +543,10 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
     double *nrm = P->d_red + 4;   // [||F||^2, ||r_1||^2, ...] when `norms`
     // info mode takes the automatic residual decision on the host, from the
     // same quantities (relative residuals; rel[-1] = 1)
+    const int rmode = effective_resid_mode(P);
     auto host_use64 = [&](int m) {
-        if (P->resid_mode == HS_RESID_F64) return true;
-        if (P->resid_mode != HS_RESID_AUTO || m < 2) return false;
+        if (rmode == HS_RESID_F64) return true;
+        if (rmode != HS_RESID_AUTO || m < 2) return false;
         const double prev = m >= 3 ? info->rel_residual[m - 3] : 1.0;
         return info->rel_residual[m - 2] > prev / 16.0;
     };
@@ -515,13 +559,13 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
             if (info) {
                 HS_TRY(P, hs_launch_residual_df(P, F, U, w, s, nullptr,
                                                 host_use64(m) ? HS_RESID_F64 : HS_RESID_DF));
-            } else if (P->resid_mode == HS_RESID_AUTO && m >= 2) {
+            } else if (rmode == HS_RESID_AUTO && m >= 2) {
                 HS_TRY(P, hs_launch_residual_df(P, F, U, w, s, r2, HS_RESID_SEL_DF, nrm, m));
                 HS_TRY(P, hs_launch_residual_df(P, F, U, w, s, r2, HS_RESID_SEL_F64, nrm, m));
             } else {
                 HS_TRY(P, hs_launch_residual_df(P, F, U, w, s, r2,
-                                                P->resid_mode == HS_RESID_F64 ? HS_RESID_F64
-                                                                              : HS_RESID_DF));
+                                                rmode == HS_RESID_F64 ? HS_RESID_F64
+                                                                      : HS_RESID_DF));
             }
             T.end(HS_STAGE_RESIDUAL);
             if (tol_mode)
@@ -586,7 +630,7 @@ namespace {
 // and the sweep runs in FP64 with FP32 data.
 hs_status choose_factors(hs_plan_s *P) {
     const bool f32 = P->factor_mode == HS_FACTOR_F32 ||
-                     (P->factor_mode == HS_FACTOR_AUTO && P->min_pivot_ratio >= 1e-4);
+                     (P->factor_mode == HS_FACTOR_AUTO && P->min_pivot_ratio >= HS_ILL_PIVOT);
     P->thomas32 = (P->precision == HS_MIXED && f32) ? 1 : 0;
     if (P->precision == HS_MIXED && !P->thomas32) {
         const double init[2] = {__builtin_inf(), 0.0};
@@ -639,6 +683,13 @@ hs_status hs_plan_ex(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double L
     P->Lx = Lx; P->Ly = Ly; P->Lz = Lz;
     P->hx = hx; P->hy = hy; P->hz = hz;
     P->order = order; P->equation = equation; P->precision = precision; P->max_rhs = max_rhs;
+    {
+        // constant weight of the sum-factorised right-hand side: h^2 / 720 (6th
+        // order), h^2 / 12 (4th order, CD), h^2 (2nd order); h = h_z
+        const double w = hz * hz / (order == 6 ? 720.0 : (order == 2 ? 1.0 : 12.0));
+        const float wh = (float)w;
+        P->rhs_sf_W = make_float2(wh, (float)(w - (double)wh));
+    }
     P->refine_sweeps = 2;
     P->resid_mode = HS_RESID_AUTO;
     P->host_io_mapped = 0;
@@ -675,7 +726,7 @@ hs_status hs_plan_ex(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double L
         (precision == HS_MIXED && (st = dev_alloc(P, &P->d_Udf, 2 * nint))) ||
         (precision == HS_MIXED && (st = dev_alloc(P, &P->d_fac32, 3 * nint))) ||
         (precision == HS_MIXED && (st = dev_alloc(P, &P->d_coef_df, (size_t)Nz * 12))) ||
-        (precision == HS_MIXED && (st = dev_alloc(P, &P->d_rhs_df, (size_t)Nz + 2))) ||
+        (precision == HS_MIXED && (st = dev_alloc(P, &P->d_rhs_df, 2 * ((size_t)Nz + 2)))) ||
         (st = build_tables(P))) {
         free_plan(P);
         return st;
@@ -740,6 +791,10 @@ hs_status hs_set_coeff(hs_plan_t P, const double *c0, const double *c1, const do
     if (c1)
         for (int l = 0; l < Nz + 2; ++l) c1v[l] = c1[l];
     HS_CK(P, cudaMemcpy(P->d_coef, C.data(), C.size() * sizeof(double), cudaMemcpyHostToDevice));
+    P->resid_xy = 1;
+    for (int l = 0; l < Nz; ++l)
+        for (int nu = 0; nu < 3; ++nu)
+            if (C[(size_t)l * 12 + nu * 4 + 1] != C[(size_t)l * 12 + nu * 4 + 2]) P->resid_xy = 0;
     if (P->d_coef_df) {
         std::vector<float2> Cdf(C.size());
         for (size_t k = 0; k < C.size(); ++k) {
@@ -751,8 +806,12 @@ hs_status hs_set_coeff(hs_plan_t P, const double *c0, const double *c1, const do
     }
     if (P->d_rhs_df) {
         // per-row weights of the double-float right-hand side, formed in FP64
-        std::vector<float4> w(Nz + 2);
+        std::vector<float4> w(2 * ((size_t)Nz + 2));
         const double h = P->hz, h2 = h * h;
+        auto pair4 = [](double a, double e) {
+            const float ah = (float)a, eh = (float)e;
+            return make_float4(ah, (float)(a - (double)ah), eh, (float)(e - (double)eh));
+        };
         for (int l = 0; l < Nz + 2; ++l) {
             double a = 0.0, e = 0.0;
             if (P->equation == HS_CONVDIFF) {
@@ -761,8 +820,8 @@ hs_status hs_set_coeff(hs_plan_t P, const double *c0, const double *c1, const do
                 a = 67.0 / 120.0 - h2 * c0[l] / 20.0;
                 e = h2 * h * (c1 ? c1[l] : 0.0) / 120.0;
             }
-            const float ah = (float)a, eh = (float)e;
-            w[l] = make_float4(ah, (float)(a - (double)ah), eh, (float)(e - (double)eh));
+            w[l] = pair4(a, e);
+            w[Nz + 2 + l] = pair4(h2 * a, h2 * e);   // the sum-factorised kernel's weights
         }
         HS_CK(P, cudaMemcpy(P->d_rhs_df, w.data(), w.size() * sizeof(float4),
                             cudaMemcpyHostToDevice));
@@ -802,7 +861,11 @@ hs_status hs_set_residual_precision(hs_plan_t P, int mode) {
 
 hs_status hs_set_transform_variant(hs_plan_t P, int axis, int variant) {
     if (!P || (axis != HS_AXIS_X && axis != HS_AXIS_Y)) return HS_ERR_INVALID_ARG;
-    if (variant < HS_DST_STAGED || variant > HS_DST_FUSED_WIDE) return HS_ERR_INVALID_ARG;
+    if (variant < HS_DST_STAGED || variant > HS_DST_GEMM) return HS_ERR_INVALID_ARG;
+    if (variant == HS_DST_GEMM) {
+        if (P->precision != HS_MIXED || !hs_dst_gemm_size(P->axf[axis].M)) return HS_ERR_UNSUPPORTED;
+        HS_TRY(P, ensure_gemm_table(P, axis));
+    }
     const bool fast = hs_dst_fast_size(P->axd[axis].M) != 0;
     if (variant == HS_DST_FUSED && (!fast || P->precision != HS_MIXED)) return HS_ERR_UNSUPPORTED;
     if (variant == HS_DST_FUSED_WIDE) {
@@ -869,7 +932,7 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
     for (int axis = 0; axis < 2 && st == HS_OK; ++axis) {
         const int saved = P->dst_variant[axis];
         int best = -1;
-        for (int v = HS_DST_STAGED; v <= HS_DST_FUSED_WIDE && st == HS_OK; ++v) {
+        for (int v = HS_DST_STAGED; v <= HS_DST_GEMM && st == HS_OK; ++v) {
             if (hs_set_transform_variant(P, axis, v) != HS_OK) continue;
             // one untimed round (first launch, attribute set-up), then `reps`
             // timed.  x of a mixed plan: a forward pass and an inverse pass that
@@ -895,6 +958,7 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
             for (int r = 0; r < reps && st == HS_OK; ++r) st = one_round();
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) st = HS_ERR_CUDA;
+            if (st == HS_OK && v == HS_DST_GEMM) st = check_gemm_err(P);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
             ms /= reps;
@@ -1134,6 +1198,7 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
     }
     if (info) {
         info->min_pivot_ratio = P->min_pivot_ratio;
+        HS_TRY(P, check_gemm_err(P));
         HS_CK(P, cudaStreamSynchronize(s));
         if (T.on) timer_read(P, info->stage_ms);
     }
@@ -1188,6 +1253,22 @@ hs_status hs_residual(hs_plan_t P, const void *f, int f_dtype, int rhs_kind,
     HS_TRY(P, residual_norms(P, P->d_w64, ud, s, &r2, &f2));
     if (res_norm) *res_norm = sqrt(r2);
     if (rhs_norm) *rhs_norm = sqrt(f2);
+    return HS_OK;
+}
+
+hs_status hs_rhs_apply(hs_plan_t P, const void *f, int f_dtype, int rhs_kind,
+                       const hs_boundary *bnd, void *F, void *stream) {
+    if (!P || !f || !F) return HS_ERR_INVALID_ARG;
+    if (!P->have_coeff) return HS_ERR_NO_COEFF;
+    if (f_dtype != HS_F64 && f_dtype != HS_F32) return HS_ERR_INVALID_ARG;
+    if (rhs_kind != HS_RHS_NODAL && rhs_kind != HS_RHS_ASSEMBLED) return HS_ERR_INVALID_ARG;
+    if (!is_device_ptr(f) || !is_device_ptr(F)) return HS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevBoundary db;
+    HS_TRY(P, stage_boundary(P, bnd, f_dtype == HS_F64 ? 8 : 4, s, &db));
+    HS_TRY(P, hs_launch_rhs(P, f, f_dtype, rhs_kind, db, F, P->precision == HS_MIXED, s));
+    // staging buffers 0 (boundary) read: an early upload of a later solve may reuse them
+    if (P->have_up) HS_CK(P, cudaEventRecord(P->up_ev[HS_UP_CHUNKS + 1], s));
     return HS_OK;
 }
 

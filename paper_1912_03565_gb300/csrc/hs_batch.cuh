@@ -19,6 +19,8 @@
 #pragma once
 
 #include "hs_dst_fused.cuh"
+#include "hs_resid_sf.cuh"
+#include "hs_rhs_sf.cuh"
 #include "hs_tiles.cuh"
 
 namespace hs_batch {
@@ -57,6 +59,10 @@ struct BatchWork {
     int lx;                            // x lines per x-transform tile
     const double *coef64;              // FP64 stencil rows (FP64 residual)
     double *norms;                     // [0] ||F||^2, [m] ||r_m||^2 (when norms_on)
+    const float4 *rw;                  // per-row weights of the sum-factorised right-hand side
+    float2 rhsW;                       // its constant pair weight
+    int resid_xy;                      // b_nu = c_nu on every row (merged residual sums)
+    int ill;                           // z-systems close to singular: FP64 residual (automatic)
     int need[BMAX_STAGES];
 };
 
@@ -228,12 +234,27 @@ __device__ void run_tile(const BatchArgs &A, const BatchWork &W, int stage, int 
         case ST_RHS: {
             const int bx = tile % W.gx, by = (tile / W.gx) % W.gy, bz = tile / (W.gx * W.gy);
             double *f2 = A.norms_on ? W.norms : nullptr;
-            if (A.f_is_f64)
-                rhs_df_tile<double>(W.rhs, static_cast<const double *>(W.f), W.F, f2, smem, bx,
-                                    by, bz);
-            else
-                rhs_df_tile<float>(W.rhs, static_cast<const float *>(W.f), W.F, f2, smem, bx, by,
-                                   bz);
+            // the stand-alone solve's tile (same rounding, so batch and stand-alone
+            // results agree to the last bit of the transforms)
+            const int kind = W.rhs.equation == HS_CONVDIFF ? SF_CD
+                             : (W.rhs.order == 6 ? SF_O6 : (W.rhs.order == 4 ? SF_O4 : SF_O2));
+            if (A.f_is_f64) {
+                const double *f = static_cast<const double *>(W.f);
+                switch (kind) {
+                    case SF_O6: rhs_sf_tile<SF_O6, double>(W.rhs, f, W.F, f2, W.rw, W.rhsW, smem, bx, by, bz); break;
+                    case SF_O4: rhs_sf_tile<SF_O4, double>(W.rhs, f, W.F, f2, W.rw, W.rhsW, smem, bx, by, bz); break;
+                    case SF_CD: rhs_sf_tile<SF_CD, double>(W.rhs, f, W.F, f2, W.rw, W.rhsW, smem, bx, by, bz); break;
+                    default: rhs_sf_tile<SF_O2, double>(W.rhs, f, W.F, f2, W.rw, W.rhsW, smem, bx, by, bz); break;
+                }
+            } else {
+                const float *f = static_cast<const float *>(W.f);
+                switch (kind) {
+                    case SF_O6: rhs_sf_tile<SF_O6, float>(W.rhs, f, W.F, f2, W.rw, W.rhsW, smem, bx, by, bz); break;
+                    case SF_O4: rhs_sf_tile<SF_O4, float>(W.rhs, f, W.F, f2, W.rw, W.rhsW, smem, bx, by, bz); break;
+                    case SF_CD: rhs_sf_tile<SF_CD, float>(W.rhs, f, W.F, f2, W.rw, W.rhsW, smem, bx, by, bz); break;
+                    default: rhs_sf_tile<SF_O2, float>(W.rhs, f, W.F, f2, W.rw, W.rhsW, smem, bx, by, bz); break;
+                }
+            }
             break;
         }
         case ST_RESIDUAL: {
@@ -241,13 +262,22 @@ __device__ void run_tile(const BatchArgs &A, const BatchWork &W, int stage, int 
             const int m = A.sweep_of[stage];
             double *r2 = A.norms_on ? W.norms + m : nullptr;
             const bool f64 = A.resid_mode == HS_RESID_F64 ||
-                             (A.resid_mode == HS_RESID_AUTO && residual_use_f64(W.norms, m));
-            if (f64)
+                             (A.resid_mode == HS_RESID_AUTO &&
+                              (W.ill || residual_use_f64(W.norms, m)));
+            // tiles are RSZ = 2 QZ planes deep: the FP64 tile runs on both halves
+            if (f64) {
                 residual64_tile<true>(W.Nx, W.Ny, W.Nz, W.coef64, W.F, W.U, W.w, r2, smem, bx, by,
-                                      bz);
-            else
-                residual_tile<true>(W.Nx, W.Ny, W.Nz, W.coef_df, W.F, W.U, W.w, r2, smem, bx, by,
-                                    bz);
+                                      2 * bz);
+                __syncthreads();
+                residual64_tile<true>(W.Nx, W.Ny, W.Nz, W.coef64, W.F, W.U, W.w, r2, smem, bx, by,
+                                      2 * bz + 1);
+            } else if (W.resid_xy) {
+                residual_sf_tile<true, true>(W.Nx, W.Ny, W.Nz, W.coef_df, W.F, W.U, W.w, r2,
+                                             reinterpret_cast<float2 *>(smem), bx, by, bz);
+            } else {
+                residual_sf_tile<false, true>(W.Nx, W.Ny, W.Nz, W.coef_df, W.F, W.U, W.w, r2,
+                                              reinterpret_cast<float2 *>(smem), bx, by, bz);
+            }
             break;
         }
         case ST_DSTX_F:

@@ -8,6 +8,9 @@
 #include "hs.h"
 
 #define HS_MAX_STAGES 16
+// Min pivot ratio below which a plan's z-systems count as close to singular: the
+// mixed path then keeps FP64 factors and (automatic mode) an FP64 residual.
+#define HS_ILL_PIVOT 1e-4
 #define HS_EVENT_PAIRS 128
 
 // One transform axis: DST-I of length N computed through a complex FFT of
@@ -53,6 +56,8 @@ struct hs_plan_s {
     int dst_variant[2];   // per axis: one of HS_DST_* (hs.h)
     int thomas_variant;   // FP32 z-solve mapping: HS_THOMAS_*
     void *d_ytmp;         // complex scratch of the two-pass y transform (Nz x M x Nx float2)
+    void *d_gemm[2];      // per axis: FP16 sine-matrix splits of the tensor-core transform
+    int *d_gemm_err;      // set by a tensor-core transform whose bounded wait gave up
     int resid_mode;       // HS_RESID_DF / HS_RESID_F64 / HS_RESID_AUTO
     int factor_mode;      // HS_FACTOR_AUTO / F32 / F64 (mixed path z-solves)
     int host_io_mapped;
@@ -85,8 +90,11 @@ struct hs_plan_s {
     double *d_fac;      // [3][Nz][Ny][Nx]: c'_l, 1/m_l, lower_l/m_l
     float *d_fac32;     // the same rounded to FP32 (mixed path, well-conditioned plans)
     float2 *d_coef_df;  // [Nz][12] coefficients as FP32 pairs (double-float residual)
-    float4 *d_rhs_df;   // [Nz+2] double-float RHS weights: 6th order (67/120 - h^2 K/20,
-                        // h^3 K_z/120); CD (0, h gamma/24)
+    int resid_xy;       // b_nu = c_nu on every row: the residual merges x- and y-neighbour sums
+    float4 *d_rhs_df;   // [2][Nz+2] double-float RHS weights.  [0]: 6th order (67/120 - h^2 K/20,
+                        // h^3 K_z/120); CD (0, h gamma/24).  [1] (sum-factorised kernel):
+                        // 6th order (h^2 (67/120 - h^2 K/20), h^5 K_z/120); CD (0, h^3 gamma/24)
+    float2 rhs_sf_W;    // constant pair weight of the sum-factorised kernel (h^2/720, h^2/12, h^2)
     int thomas32;       // mixed path: 1 = FP32 z-solves (min pivot ratio >= 1e-4)
     double *d_red;      // reduction scratch (64 doubles)
 
@@ -174,6 +182,15 @@ hs_status hs_launch_dct(int axis, int M, const double *in, double *out, const vo
                         const void *half, long nrows, int nx, int nplanes, double scale,
                         cudaStream_t s);
 
+// Tensor-core (tcgen05) sine-matrix GEMM transform (k_dst_gemm.cu), mixed path:
+// line lengths M = N + 1 in {32, 64, 96, 128, 192, 256}.  The table holds the FP16
+// splits of the sine matrix in the kernel's shared-memory layout.
+int hs_dst_gemm_size(int M);
+size_t hs_dst_gemm_table_bytes(int M);
+void hs_dst_gemm_table(int M, uint8_t *host);
+hs_status hs_launch_dst_gemm(const hs_plan_s *P, int axis, int tin, const void *in, int tout,
+                             void *out, int mode, double scale, cudaStream_t s, double *aux);
+
 // Lines per CTA of the fused tile of length M (0: not built for that length).
 int hs_dst_fused_lines_x(int M, int wide);
 int hs_dst_fused_lines_y(int M, int wide);
@@ -200,6 +217,9 @@ hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int chunks, int 
 
 // For a nodal f the tiled kernels can run on a slab of z-tiles [bz0, bz0 + nbz)
 // (nbz < 0: to the last tile; tiles are RZ output planes).
+// z-planes per tile of the nodal right-hand-side kernel (out_df: the mixed path's
+// sum-factorised kernel); slab launches count tiles of this height.
+int hs_rhs_tile_planes(int out_df);
 hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_kind,
                         const DevBoundary &b, void *F, int out_df, cudaStream_t s,
                         double *f2 = nullptr, int bz0 = 0, int nbz = -1);

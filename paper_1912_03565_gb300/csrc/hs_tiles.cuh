@@ -22,112 +22,37 @@ __device__ __forceinline__ T ldc(const T *p) {
 }
 
 // =================================================================== transforms
-__device__ __forceinline__ double cos48(int k) {
-    switch (k) {
+// cos(2 pi k / 48) and sin(2 pi k / 48), the constant twiddles of the compiled
+// radix stages (R divides 48).  The first quadrant cos(pi m / 24), m = 0..12,
+// is tabulated correctly rounded (the exact values rounded to the nearest
+// FP64 number); every other k is mapped onto it by the exact symmetries
+// cos(pi - x) = -cos x, cos(pi + x) = -cos x, cos(2 pi - x) = cos x, and
+// sin x = cos(x - pi / 2).
+__device__ __forceinline__ double cos_q24(int m) {
+    switch (m) {
         case 0: return 1.0;
         case 1: return 0.9914448613738104;
         case 2: return 0.9659258262890683;
         case 3: return 0.9238795325112867;
-        case 4: return 0.8660254037844387;
+        case 4: return 0.8660254037844386;
         case 5: return 0.7933533402912352;
         case 6: return 0.7071067811865476;
         case 7: return 0.6087614290087207;
-        case 8: return 0.5000000000000001;
-        case 9: return 0.38268343236508984;
+        case 8: return 0.5;
+        case 9: return 0.3826834323650898;
         case 10: return 0.25881904510252074;
-        case 11: return 0.1305261922200517;
-        case 12: return 0.0;
-        case 13: return -0.1305261922200516;
-        case 14: return -0.25881904510252063;
-        case 15: return -0.3826834323650895;
-        case 16: return -0.4999999999999998;
-        case 17: return -0.6087614290087207;
-        case 18: return -0.7071067811865475;
-        case 19: return -0.793353340291235;
-        case 20: return -0.8660254037844387;
-        case 21: return -0.9238795325112867;
-        case 22: return -0.9659258262890682;
-        case 23: return -0.9914448613738104;
-        case 24: return -1.0;
-        case 25: return -0.9914448613738104;
-        case 26: return -0.9659258262890683;
-        case 27: return -0.9238795325112868;
-        case 28: return -0.8660254037844388;
-        case 29: return -0.7933533402912352;
-        case 30: return -0.7071067811865479;
-        case 31: return -0.6087614290087209;
-        case 32: return -0.5000000000000004;
-        case 33: return -0.3826834323650895;
-        case 34: return -0.25881904510252063;
-        case 35: return -0.13052619222005163;
-        case 36: return 0.0;
-        case 37: return 0.13052619222005127;
-        case 38: return 0.2588190451025203;
-        case 39: return 0.38268343236508917;
-        case 40: return 0.5000000000000001;
-        case 41: return 0.6087614290087199;
-        case 42: return 0.7071067811865474;
-        case 43: return 0.7933533402912349;
-        case 44: return 0.8660254037844384;
-        case 45: return 0.9238795325112868;
-        case 46: return 0.9659258262890681;
-        case 47: return 0.9914448613738104;
-        default: return 0.0;
+        case 11: return 0.1305261922200516;
+        default: return 0.0;   // m = 12
     }
 }
-__device__ __forceinline__ double sin48(int k) {
-    switch (k) {
-        case 0: return 0.0;
-        case 1: return 0.13052619222005157;
-        case 2: return 0.25881904510252074;
-        case 3: return 0.3826834323650898;
-        case 4: return 0.49999999999999994;
-        case 5: return 0.6087614290087207;
-        case 6: return 0.7071067811865475;
-        case 7: return 0.7933533402912352;
-        case 8: return 0.8660254037844386;
-        case 9: return 0.9238795325112867;
-        case 10: return 0.9659258262890683;
-        case 11: return 0.9914448613738104;
-        case 12: return 1.0;
-        case 13: return 0.9914448613738104;
-        case 14: return 0.9659258262890683;
-        case 15: return 0.9238795325112868;
-        case 16: return 0.8660254037844387;
-        case 17: return 0.7933533402912352;
-        case 18: return 0.7071067811865476;
-        case 19: return 0.6087614290087209;
-        case 20: return 0.49999999999999994;
-        case 21: return 0.3826834323650899;
-        case 22: return 0.258819045102521;
-        case 23: return 0.130526192220052;
-        case 24: return 0.0;
-        case 25: return -0.13052619222005177;
-        case 26: return -0.2588190451025208;
-        case 27: return -0.38268343236508967;
-        case 28: return -0.4999999999999997;
-        case 29: return -0.6087614290087207;
-        case 30: return -0.7071067811865471;
-        case 31: return -0.7933533402912349;
-        case 32: return -0.8660254037844384;
-        case 33: return -0.9238795325112868;
-        case 34: return -0.9659258262890683;
-        case 35: return -0.9914448613738104;
-        case 36: return -1.0;
-        case 37: return -0.9914448613738105;
-        case 38: return -0.9659258262890684;
-        case 39: return -0.923879532511287;
-        case 40: return -0.8660254037844386;
-        case 41: return -0.7933533402912357;
-        case 42: return -0.7071067811865477;
-        case 43: return -0.6087614290087209;
-        case 44: return -0.5000000000000004;
-        case 45: return -0.38268343236508956;
-        case 46: return -0.25881904510252157;
-        case 47: return -0.13052619222005168;
-        default: return 0.0;
-    }
+__device__ __forceinline__ double cos48(int k) {
+    k = ((k % 48) + 48) % 48;
+    if (k <= 12) return cos_q24(k);
+    if (k <= 24) return -cos_q24(24 - k);
+    if (k <= 36) return -cos_q24(k - 24);
+    return cos_q24(48 - k);
 }
+__device__ __forceinline__ double sin48(int k) { return cos48(k - 12); }
 
 template <typename T> struct Cx;
 template <> struct Cx<double> { typedef double2 t; };
@@ -457,7 +382,7 @@ struct RhsArgs {
     const double *coef;  // [Nz][3][4]
     const double *c0;    // [Nz+2]
     const double *c1;    // [Nz+2]
-    const float4 *rc;    // [Nz+2]: per-row double-float RHS weights (see rhs_tiled_df_kernel)
+    const float4 *rc;    // [Nz+2]: per-row double-float RHS weights (hs_api.cu, hs_set_coeff)
     int has_faces;       // 0: every Dirichlet face is zero, so the lifting vanishes
     int bz0;             // first z-tile of the launch (slab launches of the tiled kernels)
     DevBoundary b;
@@ -573,181 +498,11 @@ __device__ double node_or_ghost(const RhsArgs &a, const T *f, int i, int j, int 
     return 0.0;  // never read by an interior point
 }
 
-// The same tiled operator in double-float arithmetic (mixed path): f enters
-// shared memory as (hi, lo) pairs (FP64 f split with integer operations,
-// FP32 f exact), the sums and products use two_sum / two_prod, and F is
-// written as its two FP32 planes.  Ghost values and the Dirichlet lifting
-// (points next to a face only) are formed in FP64 and then split.
-template <typename T>
-__device__ __forceinline__ dfloat node_df(const RhsArgs &a, const T *f, int i, int j, int l) {
-    const bool in = i >= 0 && i <= a.Nx + 1 && j >= 0 && j <= a.Ny + 1 && l >= 0 && l <= a.Nz + 1;
-    if (in) {
-        const size_t sy = (size_t)(a.Nx + 2), sz = sy * (a.Ny + 2);
-        return df_of(__ldg(f + (size_t)l * sz + (size_t)j * sy + i));
-    }
-    return df_split_bits(node_or_ghost<T>(a, f, i, j, l));
-}
-
-__device__ __forceinline__ dfloat dsum(dfloat a, dfloat b) { return df_add(a, b); }
-
-// Sum of double-float terms without renormalising after each one: the hi parts
-// go through two_sum (exact), their errors and the lo parts are added in FP32.
-struct LeanSum {
-    float s, e;
-    __device__ __forceinline__ LeanSum(dfloat a) : s(a.hi), e(a.lo) {}
-    __device__ __forceinline__ void add(dfloat a) {
-        float t, err;
-        df_two_sum(s, a.hi, t, err);
-        s = t;
-        e += err + a.lo;
-    }
-    __device__ __forceinline__ dfloat get() const {
-        dfloat r;
-        df_fast_two_sum(s, e, r.hi, r.lo);
-        return r;
-    }
-};
-
-// One CTA's work of the double-float right-hand side: a RTX x RTY patch and RZ
-// planes; smem holds 2 x 5 planes of (RTY + 4) x (RTX + 4) floats.
-template <typename T>
-__device__ __forceinline__ void rhs_df_tile(const RhsArgs &a, const T *__restrict__ f,
-                                            float *__restrict__ Fo, double *f2out,
-                                            unsigned char *smem, int bx, int by, int bz) {
-    float(*ph)[RHY][RHX] = reinterpret_cast<float(*)[RHY][RHX]>(smem);
-    float(*pq)[RHY][RHX] = ph + 5;
-    constexpr int NT = RTX * RTY;
-    constexpr int PER = (RHX * RHY + NT - 1) / NT;
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int tx = tid & (RTX - 1), ty = tid / RTX;
-    const int i0 = 1 + bx * RTX, j0 = 1 + by * RTY;
-    const int lbeg = 1 + bz * RZ;
-    const int lend = min(lbeg + RZ - 1, a.Nz);
-    const size_t n = (size_t)a.Nx * a.Ny * a.Nz;
-    const dfloat H2 = df_from_double(a.hz * a.hz);
-    const dfloat C18 = df_from_double(1.0 / 18.0), C240 = df_from_double(-1.0 / 240.0);
-    const dfloat C90 = df_from_double(1.0 / 90.0), C12 = df_from_double(1.0 / 12.0);
-    const dfloat HALF = df_of(0.5f);
-
-    dfloat reg[PER];
-    auto fetch = [&](int l) {
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int e = tid + k * NT;
-            const int ey = e / RHX, ex = e - ey * RHX;
-            reg[k] = (e < RHX * RHY) ? node_df<T>(a, f, i0 - 2 + ex, j0 - 2 + ey, l)
-                                     : df_of(0.f);
-        }
-    };
-    auto store = [&](int l) {
-        const int slot = (l + 10) % 5;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int e = tid + k * NT;
-            if (e < RHX * RHY) {
-                const int ey = e / RHX, ex = e - ey * RHX;
-                ph[slot][ey][ex] = reg[k].hi;
-                pq[slot][ey][ex] = reg[k].lo;
-            }
-        }
-    };
-    for (int l = lbeg - 2; l <= lbeg + 1; ++l) {
-        fetch(l);
-        store(l);
-    }
-    fetch(lbeg + 2);
-    float fsq = 0.f;
-    const int i = i0 + tx, j = j0 + ty;
-    const int cx = tx + 2, cy = ty + 2;
-    for (int l = lbeg; l <= lend; ++l) {
-        store(l + 2);               // slot of plane l - 3, last read in the previous step
-        __syncthreads();
-        if (l + 3 <= lend + 2) fetch(l + 3);   // in flight during this plane's arithmetic
-        if (i <= a.Nx && j <= a.Ny) {
-            const int sm2 = (l + 8) % 5, sm = (l + 9) % 5, s0 = (l + 10) % 5, sp = (l + 11) % 5,
-                      sp2 = (l + 12) % 5;
-#define HS_G(S, Y, X) dfloat{ph[S][Y][X], pq[S][Y][X]}
-            const dfloat fc = HS_G(s0, cy, cx);
-            const dfloat fzm = HS_G(sm, cy, cx), fzp = HS_G(sp, cy, cx);
-            LeanSum a1(HS_G(s0, cy, cx - 1));
-            a1.add(HS_G(s0, cy, cx + 1));
-            a1.add(HS_G(s0, cy - 1, cx));
-            a1.add(HS_G(s0, cy + 1, cx));
-            a1.add(fzm);
-            a1.add(fzp);
-            const dfloat S1 = a1.get();
-            dfloat val;
-            const float4 w = a.rc[l];
-            if (a.equation == HS_CONVDIFF) {
-                const dfloat g = dfloat{w.z, w.w};
-                const dfloat dz = df_add_accurate(fzp, df_neg(fzm));
-                val = df_mul(H2, dsum(dsum(df_mul(HALF, fc), df_mul(C12, S1)), df_mul(g, dz)));
-            } else if (a.order == 2) {
-                val = df_mul(H2, fc);
-            } else if (a.order == 4) {
-                val = df_mul(H2, dsum(df_mul(HALF, fc), df_mul(C12, S1)));
-            } else {
-                LeanSum a2(HS_G(s0, cy, cx - 2));
-                a2.add(HS_G(s0, cy, cx + 2));
-                a2.add(HS_G(s0, cy - 2, cx));
-                a2.add(HS_G(s0, cy + 2, cx));
-                a2.add(HS_G(sm2, cy, cx));
-                a2.add(HS_G(sp2, cy, cx));
-                const dfloat S2 = a2.get();
-                LeanSum a3(HS_G(s0, cy - 1, cx - 1));
-                a3.add(HS_G(s0, cy - 1, cx + 1));
-                a3.add(HS_G(s0, cy + 1, cx - 1));
-                a3.add(HS_G(s0, cy + 1, cx + 1));
-                a3.add(HS_G(sm, cy, cx - 1));
-                a3.add(HS_G(sm, cy, cx + 1));
-                a3.add(HS_G(sm, cy - 1, cx));
-                a3.add(HS_G(sm, cy + 1, cx));
-                a3.add(HS_G(sp, cy, cx - 1));
-                a3.add(HS_G(sp, cy, cx + 1));
-                a3.add(HS_G(sp, cy - 1, cx));
-                a3.add(HS_G(sp, cy + 1, cx));
-                const dfloat E = a3.get();
-                const dfloat alpha = dfloat{w.x, w.y};
-                const dfloat eps = dfloat{w.z, w.w};
-                const dfloat dz = df_add_accurate(fzp, df_neg(fzm));
-                dfloat F6 = df_mul(alpha, fc);
-                F6 = dsum(F6, df_mul(C18, S1));
-                F6 = dsum(F6, df_mul(C240, S2));
-                F6 = dsum(F6, df_mul(C90, E));
-                F6 = dsum(F6, df_mul(eps, dz));
-                val = df_mul(H2, F6);
-            }
-#undef HS_G
-            const bool near = (i == 1 || i == a.Nx || j == 1 || j == a.Ny || l == 1 || l == a.Nz);
-            if (a.has_faces && near)
-                val = df_add_accurate(val, df_neg(df_split_bits(lift_terms<T>(a, i, j, l))));
-            const size_t out = ((size_t)(l - 1) * a.Ny + (j - 1)) * a.Nx + (i - 1);
-            Fo[out] = val.hi;
-            Fo[out + n] = val.lo;
-            fsq = fmaf(val.hi, val.hi, fsq);
-        }
-        __syncthreads();
-    }
-    if (f2out) block_sum_to((double)fsq, f2out);
-}
-
-
 // =================================================================== residual
-// z-marching double-float residual.  A CTA owns a RTX x RTY patch and RZ
-// planes; a ring of three U-planes (hi and lo, halo 1) sits in shared memory.
-// For every plane each thread forms the in-plane sums of its column once --
-// corners C, x-neighbours X, y-neighbours Y (exact pair sums of the FP32 hi
-// parts, plain FP32 sums of the lo parts) -- and keeps the last three planes'
-// sums in registers, so output row l costs 12 products
-//     A U_l = sum_nu a_nu C_nu + b_nu X_nu + c_nu Y_nu + d_nu U_nu,
-// accumulated as an unnormalised pair (two_prod into two_sum; cross terms and
-// lo parts in FP32), and one accurate pair subtraction F - A U.
-struct PlaneSums {
-    float C, Ce, X, Xe, Y, Ye, U;   // hi sums with their two_sum errors; U = centre hi
-    float L;                        // lo parts: C_lo etc. folded per coefficient below
-    float Clo, Xlo, Ylo, Ulo;
-};
-
+// One term of the double-float residual's row sum (hs_resid_sf.cuh): the
+// coefficient pair k times the plane sum v (hi sum, its two_sum error ve and
+// the sum of the lo parts vlo) added to the unnormalised pair (S, E): the
+// leading product exactly (two_prod into two_sum), cross terms in FP32.
 __device__ __forceinline__ void acc_term(float &S, float &E, float2 k, float v, float ve,
                                          float vlo) {
     // S + E += (k.x + k.y) * (v + ve + vlo)
@@ -762,127 +517,7 @@ __device__ __forceinline__ void acc_term(float &S, float &E, float2 k, float v, 
 constexpr int QTX = 32, QTY = 8, QZ = 16;
 constexpr int QHX = QTX + 2, QHY = QTY + 2;
 
-// One CTA's work of the double-float residual: a QTX x QTY patch and QZ planes;
-// smem holds 2 x 2 planes of (QTY + 2) x (QTX + 2) floats.
-template <bool COH>
-__device__ __forceinline__ void residual_tile(int Nx, int Ny, int Nz, const float2 *__restrict__ coef,
-                                              const float *__restrict__ F,
-                                              const float *__restrict__ U, float *__restrict__ r,
-                                              double *r2out, unsigned char *smem, int bx, int by,
-                                              int bz) {
-    // two plane slots: the plane whose sums are being formed and the next one,
-    // whose global loads are issued into registers before the current plane's
-    // arithmetic (so their latency overlaps it)
-    float(*uh)[QHY][QHX] = reinterpret_cast<float(*)[QHY][QHX]>(smem);
-    float(*ul)[QHY][QHX] = uh + 2;
-    constexpr int NT = QTX * QTY;
-    constexpr int PER = (QHX * QHY + NT - 1) / NT;
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    const int tx = tid & (QTX - 1), ty = tid / QTX;
-    const int i0 = bx * QTX, j0 = by * QTY;  // 0-based interior indices
-    const int lbeg = bz * QZ;
-    const int lend = min(lbeg + QZ, Nz);                      // exclusive
-    const size_t plane = (size_t)Nx * Ny;
-    const size_t n = plane * Nz;
-    const int i = i0 + tx, j = j0 + ty;
-    const bool active = i < Nx && j < Ny;
-
-    float rh[PER], rl[PER];
-    auto fetch = [&](int l) {
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int e = tid + k * NT;
-            const int ey = e / QHX, ex = e - ey * QHX;
-            const int ii = i0 - 1 + ex, jj = j0 - 1 + ey;
-            rh[k] = 0.f;
-            rl[k] = 0.f;
-            if (e < QHX * QHY && l >= 0 && l < Nz && ii >= 0 && ii < Nx && jj >= 0 && jj < Ny) {
-                const size_t o = (size_t)l * plane + (size_t)jj * Nx + ii;
-                rh[k] = ldc<COH>(U + o);
-                rl[k] = ldc<COH>(U + n + o);
-            }
-        }
-    };
-    auto store = [&](int l) {
-        const int slot = (l + 2) & 1;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int e = tid + k * NT;
-            if (e < QHX * QHY) {
-                const int ey = e / QHX, ex = e - ey * QHX;
-                uh[slot][ey][ex] = rh[k];
-                ul[slot][ey][ex] = rl[k];
-            }
-        }
-    };
-    auto sums = [&](int l, PlaneSums &ps) {
-        const int sl = (l + 2) & 1;
-        const int cx = tx + 1, cy = ty + 1;
-        float s, e, s2, e2;
-        df_two_sum(uh[sl][cy - 1][cx - 1], uh[sl][cy - 1][cx + 1], s, e);
-        df_two_sum(uh[sl][cy + 1][cx - 1], uh[sl][cy + 1][cx + 1], s2, e2);
-        float s3, e3;
-        df_two_sum(s, s2, s3, e3);
-        ps.C = s3;
-        ps.Ce = e3 + (e + e2);
-        df_two_sum(uh[sl][cy][cx - 1], uh[sl][cy][cx + 1], ps.X, ps.Xe);
-        df_two_sum(uh[sl][cy - 1][cx], uh[sl][cy + 1][cx], ps.Y, ps.Ye);
-        ps.U = uh[sl][cy][cx];
-        ps.Clo = (ul[sl][cy - 1][cx - 1] + ul[sl][cy - 1][cx + 1]) +
-                 (ul[sl][cy + 1][cx - 1] + ul[sl][cy + 1][cx + 1]);
-        ps.Xlo = ul[sl][cy][cx - 1] + ul[sl][cy][cx + 1];
-        ps.Ylo = ul[sl][cy - 1][cx] + ul[sl][cy + 1][cx];
-        ps.Ulo = ul[sl][cy][cx];
-    };
-
-    PlaneSums pm, p0, pp;
-    float rsq = 0.f;
-    fetch(lbeg - 1);
-    store(lbeg - 1);
-    __syncthreads();
-    sums(lbeg - 1, pm);
-    fetch(lbeg);
-    __syncthreads();
-    store(lbeg);
-    __syncthreads();
-    sums(lbeg, p0);
-    fetch(lbeg + 1);
-    for (int l = lbeg; l < lend; ++l) {
-        __syncthreads();          // slot of plane l + 1 (= that of l - 1) is free
-        store(l + 1);
-        __syncthreads();
-        fetch(l + 2);             // in flight during the arithmetic below
-        sums(l + 1, pp);
-        if (active) {
-            const float2 *cf = coef + (size_t)l * 12;
-            float S = 0.f, E = 0.f;
-            const PlaneSums *q[3] = {&pm, &p0, &pp};
-#pragma unroll
-            for (int nu = 0; nu < 3; ++nu) {
-                const int ll = l + nu - 1;
-                if (ll < 0 || ll >= Nz) continue;
-                const PlaneSums &ps = *q[nu];
-                acc_term(S, E, cf[nu * 4 + 0], ps.C, ps.Ce, ps.Clo);
-                acc_term(S, E, cf[nu * 4 + 1], ps.X, ps.Xe, ps.Xlo);
-                acc_term(S, E, cf[nu * 4 + 2], ps.Y, ps.Ye, ps.Ylo);
-                acc_term(S, E, cf[nu * 4 + 3], ps.U, 0.f, ps.Ulo);
-            }
-            const size_t o = (size_t)l * plane + (size_t)j * Nx + i;
-            dfloat au;
-            df_fast_two_sum(S, E, au.hi, au.lo);
-            const dfloat res = df_add_accurate(dfloat{ldc<COH>(F + o), ldc<COH>(F + o + n)}, df_neg(au));
-            const float rv = res.hi + res.lo;
-            r[o] = rv;
-            rsq = fmaf(rv, rv, rsq);
-        }
-        pm = p0;
-        p0 = pp;
-    }
-    if (r2out) block_sum_to((double)rsq, r2out);
-}
-
-
-// FP64 residual of a double-float iterate: the same z-march as residual_tile,
+// FP64 residual of a double-float iterate: the same z-march as residual_sf_tile,
 // with U = U_hi + U_lo and F = F_hi + F_lo formed in FP64 and the 12 products
 // and the subtraction in FP64 (rounding 2^-53 instead of the pair's ~2^-47).
 // Used where the double-float residual has stopped the refinement short.

@@ -312,9 +312,10 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
     }
 
     hs_status st = HS_OK;
-    size_t smem = 2 * 5 * RHY * RHX * sizeof(float);
-    const size_t res_smem = 2 * 2 * QHY * QHX * sizeof(float);
+    size_t smem = sf_smem_bytes<2, double>();   // the largest right-hand-side ring
+    const size_t res_smem = 2 * QHY * QHX * sizeof(double);   // FP64 residual tile
     if (res_smem > smem) smem = res_smem;
+    if (2 * RSHX * RSHY * sizeof(float2) > smem) smem = 2 * RSHX * RSHY * sizeof(float2);
     for (int k = 0; k < nprob && st >= 0; ++k) {
         const hs_problem_desc &d = probs[k];
         hs_plan_t P = nullptr;
@@ -393,9 +394,16 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
             }
             W.sx = (float)(2.0 / (d.Nx + 1));
             W.sy = (float)(2.0 / (d.Ny + 1));
-            W.gx = (d.Nx + RTX - 1) / RTX;
-            W.gy = (d.Ny + RTY - 1) / RTY;
-            W.gz = (d.Nz + RZ - 1) / RZ;
+            // right-hand-side and residual tiles share one grid (SFX = RSX, SFY = RSY,
+            // SFZ = RSZ = 2 QZ)
+            static_assert(SFX == RSX && SFY == RSY && SFZ == RSZ && RSZ == 2 * QZ, "tile grids");
+            W.gx = (d.Nx + SFX - 1) / SFX;
+            W.gy = (d.Ny + SFY - 1) / SFY;
+            W.gz = (d.Nz + SFZ - 1) / SFZ;
+            W.rw = P->d_rhs_df + (d.Nz + 2);
+            W.rhsW = P->rhs_sf_W;
+            W.resid_xy = P->resid_xy;
+            W.ill = P->min_pivot_ratio < HS_ILL_PIVOT;
             const int Sx = lines_for(W.Mx, HS_AXIS_X), Sy = lines_for(W.My, HS_AXIS_Y);
             W.dxg = (int)(((long)d.Ny * d.Nz + Sx - 1) / Sx);
             W.lx = Sx;

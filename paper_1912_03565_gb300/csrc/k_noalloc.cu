@@ -60,13 +60,17 @@ hs_status static_scratch(double **out) {
     return HS_OK;
 }
 
-bool on_device(const void *p) {
+// Memory the kernels may dereference: device or managed memory of the current
+// device `dev` (a pointer into another GPU's memory would be a peer access,
+// which faults without peer access enabled).
+bool on_device(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev;
+    return a.type == cudaMemoryTypeManaged;
 }
 
 // Each block adds r^2 = (F - A U)^2 and F^2 over a grid-stride range of
@@ -173,13 +177,38 @@ extern "C" hs_status hs_residual_static(int Nx, int Ny, int Nz, double Lx, doubl
         return HS_ERR_INVALID_ARG;
     if (equation == HS_CONVDIFF && order != 4) return HS_ERR_INVALID_ARG;
     if (equation == HS_HELMHOLTZ && order == 6 && (!c1 || !c2)) return HS_ERR_INVALID_ARG;
+    if (equation == HS_CONVDIFF && cd_variant != HS_CD_PAPER && cd_variant != HS_CD_CORRECTED)
+        return HS_ERR_INVALID_ARG;
     if (Nz > HS_STATIC_MAX_NZ) return HS_ERR_UNSUPPORTED;  // beyond the fixed scratch
-    if (!on_device(F) || !on_device(u)) return HS_ERR_INVALID_ARG;
+    const double hx = Lx / (Nx + 1), hy = Ly / (Ny + 1), hz = Lz / (Nz + 1);
+    if (equation == HS_HELMHOLTZ && order == 6) {
+        // the sixth-order table assumes one spacing (Section 3.4), as hs_plan does
+        const double tol = 1e-12 * hz;
+        if (fabs(hx - hz) > tol || fabs(hy - hz) > tol) return HS_ERR_INVALID_ARG;
+    }
+    for (int l = 0; l < Nz + 2; ++l)
+        if (!isfinite(c0[l]) || (c1 && !isfinite(c1[l])) || (c2 && !isfinite(c2[l])))
+            return HS_ERR_NONFINITE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return HS_ERR_CUDA;
+    }
+    if (!on_device(F, dev) || !on_device(u, dev)) return HS_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        // the synchronous copies below are not allowed on a capturing stream
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+            cudaGetLastError();
+            return HS_ERR_CUDA;
+        }
+        if (cap != cudaStreamCaptureStatusNone) return HS_ERR_INVALID_ARG;
+    }
 
     double *scratch = nullptr;
     hs_status st = static_scratch(&scratch);
     if (st != HS_OK) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     // Coefficient table in chunks of rows built on the host stack and copied
     // into the static array: row l depends on c0..c2 at l-1, l, l+1 only, so a
@@ -188,9 +217,9 @@ extern "C" hs_status hs_residual_static(int Nx, int Ny, int Nz, double Lx, doubl
     memset(&sub, 0, sizeof(sub));
     sub.Nx = Nx;
     sub.Ny = Ny;
-    sub.hx = Lx / (Nx + 1);
-    sub.hy = Ly / (Ny + 1);
-    sub.hz = Lz / (Nz + 1);
+    sub.hx = hx;
+    sub.hy = hy;
+    sub.hz = hz;
     sub.order = order;
     sub.equation = equation;
     const int CH = 128;

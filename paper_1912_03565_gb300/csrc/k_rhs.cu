@@ -17,6 +17,8 @@
 // absent, the zero derivative data the paper mentions).
 // Lifting: every stencil neighbour on a boundary node contributes
 // -coef * g to F (the Dirichlet data of eq. (bc) moved to the right side).
+#include "hs_resid_sf.cuh"
+#include "hs_rhs_sf.cuh"
 #include "hs_tiles.cuh"
 
 namespace {
@@ -197,27 +199,50 @@ __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_kernel(RhsArgs a, const T 
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(RTX *RTY) rhs_tiled_df_kernel(RhsArgs a, const T *__restrict__ f,
-                                                                float *__restrict__ Fo,
-                                                                double *f2out) {
-    __shared__ __align__(16) unsigned char smem[2 * 5 * RHY * RHX * sizeof(float)];
-    rhs_df_tile<T>(a, f, Fo, f2out, smem, blockIdx.x, blockIdx.y, blockIdx.z + a.bz0);
+// Mixed path, nodal f: the sum-factorised double-float tile (hs_rhs_sf.cuh).
+template <int KIND, typename T>
+__global__ void __launch_bounds__(SFX *SFY, 3) rhs_sf_kernel(RhsArgs a, const T *__restrict__ f,
+                                                          float *__restrict__ Fo, double *f2out,
+                                                          const float4 *__restrict__ rw,
+                                                          float2 W) {
+    constexpr int H = KIND == SF_O6 ? 2 : 1;
+    __shared__ __align__(16) unsigned char smem[sf_smem_bytes<H, T>()];
+    rhs_sf_tile<KIND, T>(a, f, Fo, f2out, rw, W, smem, blockIdx.x, blockIdx.y,
+                         blockIdx.z + a.bz0);
 }
 
-__global__ void __launch_bounds__(QTX *QTY) residual_zmarch_kernel(int Nx, int Ny, int Nz,
-                                                                    const float2 *__restrict__ coef,
-                                                                    const float *__restrict__ F,
-                                                                    const float *__restrict__ U,
-                                                                    float *__restrict__ r,
-                                                                    const int *skip, double *r2out,
-                                                                    const double *norms, int m,
-                                                                    int sel) {
+template <typename T>
+void launch_rhs_sf(const hs_plan_s *P, const RhsArgs &a, const T *f, float *Fo, double *f2,
+                   int cnt, cudaStream_t s) {
+    dim3 tg((P->Nx + SFX - 1) / SFX, (P->Ny + SFY - 1) / SFY, (unsigned)cnt);
+    const float4 *rw = P->d_rhs_df + (P->Nz + 2);
+    const float2 W = P->rhs_sf_W;
+    if (P->equation == HS_CONVDIFF)
+        rhs_sf_kernel<SF_CD, T><<<tg, SFX * SFY, 0, s>>>(a, f, Fo, f2, rw, W);
+    else if (P->order == 6)
+        rhs_sf_kernel<SF_O6, T><<<tg, SFX * SFY, 0, s>>>(a, f, Fo, f2, rw, W);
+    else if (P->order == 4)
+        rhs_sf_kernel<SF_O4, T><<<tg, SFX * SFY, 0, s>>>(a, f, Fo, f2, rw, W);
+    else
+        rhs_sf_kernel<SF_O2, T><<<tg, SFX * SFY, 0, s>>>(a, f, Fo, f2, rw, W);
+}
+
+// The lean pair residual (hs_resid_sf.cuh); XY: x- and y-neighbour sums merged
+// (b_nu = c_nu on every row).
+template <bool XY>
+__global__ void __launch_bounds__(RSX *RSY) residual_sf_kernel(int Nx, int Ny, int Nz,
+                                                                const float2 *__restrict__ coef,
+                                                                const float *__restrict__ F,
+                                                                const float *__restrict__ U,
+                                                                float *__restrict__ r,
+                                                                const int *skip, double *r2out,
+                                                                const double *norms, int m,
+                                                                int sel) {
     if (skip && *skip) return;
     if (sel == HS_RESID_SEL_DF && residual_use_f64(norms, m)) return;
-    __shared__ __align__(16) unsigned char smem[2 * 2 * QHY * QHX * sizeof(float)];
-    residual_tile<false>(Nx, Ny, Nz, coef, F, U, r, r2out, smem, blockIdx.x, blockIdx.y,
-                         blockIdx.z);
+    __shared__ __align__(16) float2 ring[resid_async_smem() / sizeof(float2)];
+    residual_sf_tile_async<XY>(Nx, Ny, Nz, coef, F, U, r, r2out, ring, blockIdx.x, blockIdx.y,
+                               blockIdx.z);
 }
 
 __global__ void __launch_bounds__(QTX *QTY) residual64_zmarch_kernel(
@@ -313,14 +338,15 @@ hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int chunks, int 
     const int K = chunks < 1 ? 1 : (chunks > HS_UP_CHUNKS ? HS_UP_CHUNKS : chunks);
     const size_t esz = f_dtype == HS_F64 ? 8 : 4;
     const size_t pb = (size_t)(P->Nx + 2) * (P->Ny + 2) * esz;   // bytes per node plane
-    const int tz = (P->Nz + RZ - 1) / RZ;
+    const int TZ = hs_rhs_tile_planes(out_df);
+    const int tz = (P->Nz + TZ - 1) / TZ;
     const unsigned char *src = static_cast<const unsigned char *>(fh);
     unsigned char *dst = static_cast<unsigned char *>(fd);
     int copied = 0;   // node planes [0, copied) are on their way
     for (int k = 0; k < K; ++k) {
         const int t0 = (k * tz) / K, t1 = ((k + 1) * tz) / K;
         // the slab's last tile reads node planes up to min(t1 RZ, Nz) + 2 (<= Nz + 1)
-        const int need = k == K - 1 ? P->Nz + 2 : (t1 * RZ + 3 < P->Nz + 2 ? t1 * RZ + 3 : P->Nz + 2);
+        const int need = k == K - 1 ? P->Nz + 2 : (t1 * TZ + 3 < P->Nz + 2 ? t1 * TZ + 3 : P->Nz + 2);
         if (need > copied) {
             if (cudaMemcpyAsync(dst + copied * pb, src + copied * pb, (size_t)(need - copied) * pb,
                                 cudaMemcpyHostToDevice, P->up_stream) != cudaSuccess)
@@ -338,6 +364,8 @@ hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int chunks, int 
     }
     return HS_OK;
 }
+
+int hs_rhs_tile_planes(int out_df) { return out_df ? SFZ : RZ; }
 
 hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_kind,
                         const DevBoundary &b, void *F, int out_df, cudaStream_t s, double *f2,
@@ -359,25 +387,26 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
     for (int k = 0; k < 6; ++k)
         if (b.face[k]) a.has_faces = 1;
     if (rhs_kind == HS_RHS_NODAL) {
-        const int tz = (P->Nz + RZ - 1) / RZ;
+        const int TZ = hs_rhs_tile_planes(out_df);
+        const int tz = (P->Nz + TZ - 1) / TZ;
         a.bz0 = bz0 < 0 ? 0 : bz0;
         const int cnt = nbz < 0 ? tz - a.bz0 : nbz;
         if (cnt <= 0) return HS_OK;
+        if (out_df) {
+            if (f_dtype == HS_F64)
+                launch_rhs_sf<double>(P, a, static_cast<const double *>(f), static_cast<float *>(F),
+                                      f2, cnt, s);
+            else
+                launch_rhs_sf<float>(P, a, static_cast<const float *>(f), static_cast<float *>(F),
+                                     f2, cnt, s);
+            return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+        }
         dim3 tb(RTX, RTY, 1);
         dim3 tg((P->Nx + RTX - 1) / RTX, (P->Ny + RTY - 1) / RTY, (unsigned)cnt);
-        if (f_dtype == HS_F64) {
-            if (out_df)
-                rhs_tiled_df_kernel<double><<<tg, tb, 0, s>>>(a, static_cast<const double *>(f),
-                                                              static_cast<float *>(F), f2);
-            else
-                rhs_tiled_kernel<double, 0><<<tg, tb, 0, s>>>(a, static_cast<const double *>(f), F);
-        } else {
-            if (out_df)
-                rhs_tiled_df_kernel<float><<<tg, tb, 0, s>>>(a, static_cast<const float *>(f),
-                                                             static_cast<float *>(F), f2);
-            else
-                rhs_tiled_kernel<float, 0><<<tg, tb, 0, s>>>(a, static_cast<const float *>(f), F);
-        }
+        if (f_dtype == HS_F64)
+            rhs_tiled_kernel<double, 0><<<tg, tb, 0, s>>>(a, static_cast<const double *>(f), F);
+        else
+            rhs_tiled_kernel<float, 0><<<tg, tb, 0, s>>>(a, static_cast<const float *>(f), F);
         return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
     }
     a.bz0 = 0;
@@ -402,9 +431,16 @@ hs_status hs_launch_residual_df(const hs_plan_s *P, const float *F, const float 
                                 int m) {
     dim3 qb(QTX, QTY, 1);
     dim3 qg((P->Nx + QTX - 1) / QTX, (P->Ny + QTY - 1) / QTY, (P->Nz + QZ - 1) / QZ);
-    if (prec == HS_RESID_DF || prec == HS_RESID_SEL_DF)
-        residual_zmarch_kernel<<<qg, qb, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df, F, U, r,
-                                                 P->cur_skip, r2, norms, m, prec);
+    if (prec == HS_RESID_DF || prec == HS_RESID_SEL_DF) {
+        dim3 sg((P->Nx + RSX - 1) / RSX, (P->Ny + RSY - 1) / RSY, (P->Nz + RSZ - 1) / RSZ);
+        if (P->resid_xy)
+            residual_sf_kernel<true><<<sg, RSX * RSY, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df, F,
+                                                              U, r, P->cur_skip, r2, norms, m, prec);
+        else
+            residual_sf_kernel<false><<<sg, RSX * RSY, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df,
+                                                               F, U, r, P->cur_skip, r2, norms, m,
+                                                               prec);
+    }
     if (prec == HS_RESID_F64 || prec == HS_RESID_SEL_F64)
         residual64_zmarch_kernel<<<qg, qb, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef, F, U, r,
                                                    P->cur_skip, r2, norms, m, prec);

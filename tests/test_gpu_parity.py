@@ -443,6 +443,7 @@ def test_error_codes_without_touching_data():
 
 
 FAST_N = [31, 63, 95, 127, 191, 255, 383, 511, 767, 1023]
+GEMM_M = (32, 64, 96, 128, 192, 256)    # line lengths N + 1 of the tensor-core transform
 
 
 @pytest.mark.parametrize("N", FAST_N)
@@ -450,7 +451,8 @@ FAST_N = [31, 63, 95, 127, 191, 255, 383, 511, 767, 1023]
                                                (H.HS_MIXED, H.HS_DST_STAGED),
                                                (H.HS_MIXED, H.HS_DST_FUSED),
                                                (H.HS_MIXED, H.HS_DST_FUSED_WIDE),
-                                               (H.HS_MIXED, H.HS_DST_TWOPASS)])
+                                               (H.HS_MIXED, H.HS_DST_TWOPASS),
+                                               (H.HS_MIXED, H.HS_DST_GEMM)])
 def test_transform_lengths(N, precision, variant):
     """Every compile-time-sized transform length and kernel variant, along x and along
     y (ragged tiles: 9 x-lines over 5 planes, 7-column y-tiles).
@@ -469,7 +471,14 @@ def test_transform_lengths(N, precision, variant):
             u0, _ = gpu_solve(p, precision, sweeps=0, variant=variant)
             u0s, _ = gpu_solve(p, precision, sweeps=0, variant=H.HS_DST_STAGED)
             e, es = O.max_rel_diff(u0, ref), O.max_rel_diff(u0s, ref)
-            assert e <= 4 * es + 1e-7 and e <= 1e-4, (e, es)
+            if variant == H.HS_DST_GEMM and N + 1 in GEMM_M:
+                # the tensor cores round each accumulation step to about 2^-23 of
+                # the running sum: 3 (N + 1) / 16 steps per pass, four passes
+                assert e <= 4 * 3 * (N + 1) / 16 * 2.0 ** -23 + 4 * es, (e, es)
+            else:
+                assert e <= 4 * es + 1e-7 and e <= 1e-4, (e, es)
+            print(f"N={N} shape={shape} variant={variant}: unrefined {e:.3e} "
+                  f"(staged FFT {es:.3e})")
 
 
 @pytest.mark.parametrize("shape", [(40, 511, 3), (33, 1023, 2), (70, 767, 2)])
@@ -501,7 +510,7 @@ def test_autotune_keeps_a_valid_variant():
         for axis in (H.HS_AXIS_X, H.HS_AXIS_Y):
             assert H.hs_get_transform_variant(s.plan, axis) in (
                 H.HS_DST_STAGED, H.HS_DST_FUSED, H.HS_DST_GENERIC, H.HS_DST_TWOPASS,
-                H.HS_DST_FUSED_WIDE)
+                H.HS_DST_FUSED_WIDE, H.HS_DST_GEMM)
         H.hs_set_refinement(s.plan, 2)
         f = torch.from_numpy(p.f_nodes).cuda()
         faces = [None if a is None else torch.from_numpy(a).cuda() for a in p.faces]

@@ -392,13 +392,24 @@ def batch_problem(spec: dict, rhs_index: int, seed: int = 3, dtype=np.float32) -
 def sine_mode_nodes_torch(N: int, modes, amps, dtype=None, device="cuda"):
     """The sum of sine modes on the node grid, built on a torch device (the
     1023^3 FP64 grid is 8.6 GB, too slow to fill with numpy).  Input generation
-    only: f(x,y,z) = sum_m A_m sin(p pi x) sin(q pi y) sin(r pi z) on [0,1]^3."""
+    only: f(x,y,z) = sum_m A_m sin(p pi x) sin(q pi y) sin(r pi z) on [0,1]^3.
+
+    The result equals sine_mode_problem's FP64 f bit for bit: the 1-D sine
+    factors are the same numpy values, and the products and sums are taken in
+    the same order with correctly rounded FP64 operations (no fused
+    multiply-add), so a GPU solve and the oracle see the same input."""
     import torch
-    x = torch.arange(N + 2, dtype=torch.float64, device=device) * (np.pi / (N + 1))
+    x = node_coords(N, 1.0)
     f = torch.zeros((N + 2, N + 2, N + 2), dtype=torch.float64, device=device)
+    t = torch.empty_like(f)
     for (p, q, r), A in zip(modes, amps):
-        zy = torch.outer(torch.sin(float(r) * x), torch.sin(float(q) * x))
-        f.addcmul_(zy[:, :, None], torch.sin(float(p) * x)[None, None, :], value=float(A))
+        sx = torch.from_numpy(np.sin(p * np.pi * x)).to(device)
+        sy = torch.from_numpy(np.sin(q * np.pi * x)).to(device)
+        sz = torch.from_numpy(np.sin(r * np.pi * x)).to(device)
+        torch.mul(sx[None, None, :] * sy[None, :, None], sz[:, None, None], out=t)
+        t.mul_(float(A))
+        f.add_(t)
+    del t
     return f if dtype is None else f.to(dtype)
 
 
