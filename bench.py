@@ -206,12 +206,12 @@ WORKLOADS = {
         desc="4th-order compact Helmholtz on the unit cube, 31^3 interior (h=1/32), "
              "k=10+5 sin(pi z), manufactured u, FP64 f, 1 RHS per step"),
     "cube1023_o6": dict(
-        steps=10,
+        steps=10, steps_in_all=5,
         desc="6th-order compact Helmholtz on the unit cube, 1023^3 interior (h=1/1024), "
              "k=40+20 tanh(10(z-1/2)), f = 16 seeded sine modes, amplitudes N(0,1), "
              "stored FP32, 1 RHS per step"),
     "batch64": dict(
-        steps=5,
+        steps=5, steps_in_all=3,
         desc="64 independent 6th-order Helmholtz problems, N per axis drawn (seed 3) from "
              "{63,95,127,191,255,383}, uniform h=1/(max N+1), k=k0(1+a z) with k0~U[5,60], "
              "a~U[0,1], 1-4 right-hand sides each, f ~ U[-1,1] FP32 at interior nodes, "
@@ -235,11 +235,29 @@ WORKLOADS = {
         desc="zrobin255_o4's complex k(z) and absorbing z-faces with u_n = 0 on the four side "
              "faces (cosine transforms over the 257 nodes of each side axis; seed 13)"),
     "cd511x8": dict(
-        steps=10,
+        steps=10, steps_in_all=4,
         desc="4th-order compact convection-diffusion Lap(u)+b(z)u_z=f, 511^3 interior, "
              "b=2+sin(2pi z) (variable-b corrected coefficients), 8 right-hand sides "
              "U[-1,1] stored FP32 per step, nonsymmetric z-systems"),
 }
+
+
+# timed after the headline workload in the default run ("configs" of the JSON line)
+EXTRA_CONFIGS = ("cube1023_o6", "batch64", "cd511x8")
+
+
+def config_summary(line):
+    """The parts of a workload's line reported under "configs"."""
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "fp64_path",
+            "sequential_fp64_path", "sequential_mixed_path", "stages_ms", "accuracy", "roofline",
+            "cpu_baseline", "clocks", "gpu_launches", "status")
+    out = {k: line[k] for k in keep if k in line}
+    out["workload"] = line["config"]["workload"]
+    for k in ("refinement_sweeps", "refinement_sweeps_max", "refinement_residual_tol",
+              "transform_variants", "batch_kernel", "unknown_solves_per_step"):
+        if k in line["config"]:
+            out[k] = line["config"][k]
+    return out
 
 
 class Work:
@@ -296,11 +314,14 @@ class Work:
             self.f_dtype = 1
             self.nrhs = R
             if want_oracle:
+                # bounded sample: one right-hand side of the same recipe at 255^3 (the
+                # 511^3 oracle takes minutes); parity at 511^3 is in the test suite
+                q = W.workload_convdiff511(0, N=255)
                 t0 = time.perf_counter()
-                self.ref, _ = O.solve(probs[0])
+                O.solve(q)
                 dt = time.perf_counter() - t0
-                self.cpu = (dt, N ** 3, f"bounded sample: the oracle on 1 of the 8 right-hand "
-                                        f"sides (511^3): {dt:.2f} s")
+                self.cpu = (dt, 255 ** 3, f"bounded sample: the oracle on one right-hand side "
+                                          f"of the same recipe at 255^3: {dt:.2f} s")
         else:
             raise ValueError(name)
         Nx, Ny, Nz = self.N
@@ -708,6 +729,34 @@ def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
     value = world * args.steps * total / (ms * 1e-3) / 1e9
     kernels_per_step = H.hs_batch_graph_kernels(b)
     H.hs_batch_destroy(b)
+    # roofline of the whole batch step: the algorithmic bytes of every (problem, RHS)
+    # at one refinement sweep (a lower bound: a solve stopped by the tolerance runs
+    # at least one) over the step's device time
+    hbm_peak, peak_kind = load_peaks()
+    bpu = sum(stage_bytes("mixed", 1).values())
+    achieved = bpu * total / (ms / args.steps * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "whole batch step (one CUDA graph launch)",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                "algorithmic_bytes_per_step": bpu * total,
+                "bytes_per_unknown": bpu,
+                "note": "bytes at one refinement sweep per right-hand side: a lower bound"}
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # bounded sample: the oracle on the first three problems, one RHS each
+        from oracle import hs_oracle as O
+        t0 = time.perf_counter()
+        nsamp = 0
+        for sp in specs[:3]:
+            pb = W.batch_problem(sp, 0)
+            O.solve(pb)
+            nsamp += pb.Nx * pb.Ny * pb.Nz
+        dt = time.perf_counter() - t0
+        cpu_baseline = {"value": nsamp / dt / 1e9, "unit": UNIT, "cores": cpu_cores(),
+                        "kind": "oracle",
+                        "sample": f"bounded sample: problems 0-2 of the batch, one RHS each "
+                                  f"({nsamp} unknowns), numpy FP64 oracle: {dt:.2f} s"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -723,11 +772,12 @@ def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
                                      "ms_per_step": t64},
             "sequential_mixed_path": {"value": total / (tmix * 1e-3) / 1e9, "unit": UNIT,
                                       "ms_per_step": tmix},
-            "accuracy": acc, "status": status, "cpu_baseline": None, "e2e": None,
-            "roofline": None, "clocks": clocks,
+            "accuracy": acc, "status": status, "cpu_baseline": cpu_baseline, "e2e": None,
+            "roofline": roofline, "clocks": clocks,
             "gpu_launches": args.steps * kernels_per_step,
         }
-        print(json.dumps(line), flush=True)
+        return line
+    return None
 
 
 def main():
@@ -736,7 +786,9 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hs", choices=["hs", "reference"])
-    ap.add_argument("--workload", default="cube255_o6", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help="one workload; default: cube255_o6 as the headline line with "
+                         + ", ".join(EXTRA_CONFIGS) + " timed after it under 'configs'")
     ap.add_argument("--sweeps", type=int, default=-1,
                     help="refinement sweeps; -1 = the fewest whose error is <= 1e-10")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -748,6 +800,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "hs":
         args.warmup = 3
+    run_all = args.workload is None and args.impl == "hs"
+    if args.workload is None:
+        args.workload = "cube255_o6"
     if args.impl == "reference":
         run_reference(args)
         return
@@ -783,12 +838,43 @@ def main():
             dist.destroy_process_group()
         return
     if args.workload == "batch64":
-        bench_batch(args, torch, H, W, rank, world, barrier,
-                    lambda x: reduce_max(x, dist, "cuda"))
-        if dist is not None:
-            dist.destroy_process_group()
-        return
+        line = bench_batch(args, torch, H, W, rank, world, barrier,
+                           lambda x: reduce_max(x, dist, "cuda"))
+    else:
+        line = bench_solve(args, torch, H, W, rank, world, local, barrier, dist)
+    if run_all:
+        # the other configurations, timed in the same process and reported under
+        # "configs" (fewer steps; no end-to-end leg)
+        line_configs = {}
+        for name in EXTRA_CONFIGS:
+            sub = argparse.Namespace(**vars(args))
+            sub.workload = name
+            sub.steps = WORKLOADS[name]["steps_in_all"]
+            sub.no_e2e = True
+            sub.variants = ""
+            sub.variants64 = ""
+            sub.sweeps = -1
+            if name == "batch64":
+                sl = bench_batch(sub, torch, H, W, rank, world, barrier,
+                                 lambda x: reduce_max(x, dist, "cuda"))
+            else:
+                sl = bench_solve(sub, torch, H, W, rank, world, local, barrier, dist)
+            torch.cuda.empty_cache()
+            if rank == 0:
+                line_configs[name] = config_summary(sl)
+        if rank == 0:
+            line["configs"] = line_configs
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
+
+def bench_solve(args, torch, H, W, rank, world, local, barrier, dist):
+    """One workload solved by the plan path (the Work recipes): accuracy of both
+    paths, device-timed mixed and FP64 solves, stage breakdown, roofline of the
+    dominant kernel, CPU-oracle baseline and (unless --no-e2e) the end-to-end
+    time through hs_solve with host buffers.  Returns the JSON line (rank 0)."""
     want_oracle = rank == 0 and world == 1 and not args.no_cpu_baseline
     wk = Work(args.workload, torch, W, want_oracle)
     Nx, Ny, Nz = wk.N
@@ -1001,6 +1087,7 @@ def main():
                           "solve (HS_HOST_U_LATE)",
                "host_u_equals_device_u": same}
 
+    line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1022,11 +1109,12 @@ def main():
             "clocks": clocks,
             "gpu_launches": launches_per_solve("mixed", sweeps) * R * args.steps,
         }
-        print(json.dumps(line), flush=True)
     smix.close()
     s64.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    torch.cuda.empty_cache()
+    return line if rank == 0 else None
+
+
 
 
 if __name__ == "__main__":

@@ -200,8 +200,13 @@ __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_kernel(RhsArgs a, const T 
 }
 
 // Mixed path, nodal f: the sum-factorised double-float tile (hs_rhs_sf.cuh).
+// CTAs per SM the register allocation of the sum-factorised kernel is sized for
+#ifndef HS_RHS_SF_MINB
+#define HS_RHS_SF_MINB 3
+#endif
+
 template <int KIND, typename T>
-__global__ void __launch_bounds__(SFX *SFY, 3) rhs_sf_kernel(RhsArgs a, const T *__restrict__ f,
+__global__ void __launch_bounds__(SFX *SFY, HS_RHS_SF_MINB) rhs_sf_kernel(RhsArgs a, const T *__restrict__ f,
                                                           float *__restrict__ Fo, double *f2out,
                                                           const float4 *__restrict__ rw,
                                                           float2 W) {
