@@ -73,9 +73,12 @@ NCU_COUNTS = {
 }
 
 
-# FP64 pipe instruction rate of one GB300: the measured FP64 FMA throughput
-# (1.19 TFLOP/s, independent-chain probe) / 2 flops / 32 threads, in G warp-inst/s
-FP64_PIPE_PEAK = 1.19e12 / 2.0 / 32.0 / 1e9
+def fp64_pipe_peak():
+    """FP64 pipe instruction rate of this GPU, G warp-instructions/s: the FP64 FMA
+    throughput measured now by the library's probe (hs_fp64_fma_rate: 8 independent
+    FMA chains per thread, 152 x 8 blocks of 256 threads), / 2 flops / 32 threads."""
+    rate = max(H.hs_fp64_fma_rate() for _ in range(3))
+    return rate * 1e12 / 2.0 / 32.0 / 1e9, rate
 
 
 def sm_max_mhz():
@@ -557,11 +560,13 @@ def bench_zrobin(args, torch, H, W, rank, world, barrier, max_over_ranks):
         # FP64-pipe bound); FP64-pipe warp instructions of the two passes (ncu) over the
         # stage's live time, against the FP64 pipe's instruction rate
         ach = counts["fp64_warp_inst"] / (stages["transforms"] * 1e-3) / 1e9
+        peak, rate = fp64_pipe_peak()
         roofline = {"bound": "alu", "kernel": counts["kernel"], "achieved": ach,
-                    "peak": FP64_PIPE_PEAK, "unit": "G fp64 warp-inst/s",
-                    "frac": ach / FP64_PIPE_PEAK, "traffic": counts["dram_bytes"],
-                    "peak_kind": "FP64 pipe: measured FP64 FMA rate 1.19 TFLOP/s = 0.595 T "
-                                 "thread-instructions/s = 18.6 G warp-instructions/s",
+                    "peak": peak, "unit": "G fp64 warp-inst/s",
+                    "frac": ach / peak, "traffic": counts["dram_bytes"],
+                    "peak_kind": f"FP64 pipe: FP64 FMA rate {rate:.4f} TFLOP/s measured in this "
+                                 f"run (hs_fp64_fma_rate) / 2 flops / 32 lanes = {peak:.2f} G "
+                                 "warp-instructions/s",
                     "launches": 2, "fp64_warp_inst_per_stage": counts["fp64_warp_inst"],
                     "stage_ms": stages["transforms"], "profile": counts["profile"]}
     acc, cpu = {"compared_against": "oracle (complex FP64, O(N^4) sine / cosine sums)"}, None

@@ -76,7 +76,8 @@ enum { HS_FACTOR_AUTO = 0, HS_FACTOR_F32 = 1, HS_FACTOR_F64 = 2 }; /* mixed z-so
 enum { HS_HOST_F_MAPPED = 1, HS_HOST_U_MAPPED = 2, HS_HOST_F_EARLY = 4,     /* hs_set_host_io */
        HS_HOST_U_LATE = 8 };
 enum { HS_THOMAS_PIPE16_256 = 0, HS_THOMAS_PIPE8_128 = 1,    /* FP32 z-solve mapping */
-       HS_THOMAS_PLAIN16_256 = 2, HS_THOMAS_PIPE16_128 = 3 };
+       HS_THOMAS_PLAIN16_256 = 2, HS_THOMAS_PIPE16_128 = 3, HS_THOMAS_BAL8_512 = 4,
+       HS_THOMAS_BAL16_256 = 5 };
 
 typedef struct hs_plan_s *hs_plan_t;
 
@@ -249,7 +250,10 @@ hs_status hs_get_transform_variant(hs_plan_t plan, int axis, int *variant);
  * (p,q) column, z walked in chunks): HS_THOMAS_PIPE16_256 (default: 16-plane
  * chunks, the next chunk's loads issued before the current chunk's chain,
  * 256-thread blocks), HS_THOMAS_PIPE8_128, HS_THOMAS_PLAIN16_256 (no
- * pipelining, fewer registers), HS_THOMAS_PIPE16_128.  Identical results.
+ * pipelining, fewer registers), HS_THOMAS_PIPE16_128, and the balanced
+ * mappings HS_THOMAS_BAL8_512 / HS_THOMAS_BAL16_256 (8- or 16-plane chunks; a
+ * whole number of blocks per SM with the columns shared evenly among them,
+ * blocks of at most 512 / 256 threads).  Identical results.
  * Errors: HS_ERR_INVALID_ARG.
  */
 hs_status hs_set_thomas_variant(hs_plan_t plan, int variant);
@@ -373,6 +377,15 @@ hs_status hs_residual(hs_plan_t plan, const void *f, int f_dtype, int rhs_kind,
  */
 hs_status hs_rhs_apply(hs_plan_t plan, const void *f, int f_dtype, int rhs_kind,
                        const hs_boundary *bnd, void *F, void *stream);
+
+/*
+ * hs_fp64_fma_rate -- the current device's FP64 fused multiply-add throughput
+ * in TFLOP/s (2 flops per FMA), measured with independent DFMA chains on every
+ * SM and timed with CUDA events on `stream` (synchronous; about 10 ms).  No
+ * paper counterpart: the peak against which the FP64 transforms are reported.
+ * Errors: HS_ERR_INVALID_ARG, HS_ERR_CUDA.
+ */
+hs_status hs_fp64_fma_rate(void *stream, double *tflops);
 
 /*
  * hs_stage_times -- device time per stage (ms[HS_INFO_STAGES], indexed by
@@ -613,7 +626,7 @@ const char *hs_last_error(hs_plan_t plan);
  */
 typedef struct hs_zplan_s *hs_zplan_t;
 enum { HS_ZFACE_DIRICHLET = 0, HS_ZFACE_ROBIN = 1 };
-enum { HS_SIDE_DIRICHLET = 0, HS_SIDE_NEUMANN = 1 };
+enum { HS_SIDE_DIRICHLET = 0, HS_SIDE_NEUMANN = 1, HS_SIDE_DN = 2, HS_SIDE_ND = 3 };
 
 /* hs_zplan -- plan for an Nx x Ny x Nz interior grid on [0,Lx]x[0,Ly]x[0,Lz]
  * (h_a = L_a / (N_a + 1)), order 2 or 4.  Faces start Dirichlet.  Errors:
@@ -641,15 +654,25 @@ hs_status hs_zplan_set_faces(hs_zplan_t plan, int lo_kind, const double *alpha_l
  * (or side = NULL) are 0.  The
  * ghost beyond such a face is the mirror value plus 2 h g (second-order
  * central difference), a face's data reflected evenly beyond its own edges.
- * Data on the faces of a Dirichlet axis are rejected (HS_ERR_INVALID_ARG).
+ * Data on a Dirichlet face (either face of a Dirichlet axis, the low face of an
+ * HS_SIDE_DN axis, the high face of an HS_SIDE_ND axis) are rejected
+ * (HS_ERR_INVALID_ARG).
  * Other errors as hs_zsolve. */
 hs_status hs_zsolve_ex(hs_zplan_t plan, const double *f, const double *g_lo, const double *g_hi,
                        const double *const *side, double *u, void *stream);
 
-/* hs_zplan_set_sides -- kind (HS_SIDE_DIRICHLET / HS_SIDE_NEUMANN, Section 1)
- * of the x and y side axes (default Dirichlet).  A Neumann axis needs N + 1
- * with a compiled transform (N + 1 in {32, 64, 96, 128, 192, 256, 384, 512,
- * 768, 1024}).
+/* hs_zplan_set_sides -- kind of the x and y side axes (Section 1; default
+ * Dirichlet): HS_SIDE_DIRICHLET (u = 0 on both faces, nodes 1..N unknown),
+ * HS_SIDE_NEUMANN (u_n = g on both faces, nodes 0..N+1, cosine transform DCT-I),
+ * HS_SIDE_DN (u = 0 on the low face, u_n = g on the high face, nodes 1..N+1) or
+ * HS_SIDE_ND (u_n = g on the low face, u = 0 on the high face, nodes 0..N);
+ * the last two take the quarter-wave transforms (modes of angle
+ * (2p - 1) pi / (2 (N + 1)), p = 1..N+1), computed as the sine transform of the
+ * line extended evenly about its Neumann node to 2N + 1 points (an internal
+ * plan: about twice the x or y work array).  A Neumann axis needs N + 1, a
+ * mixed axis 2 (N + 1), with a compiled transform (in {32, 64, 96, 128, 192,
+ * 256, 384, 512, 768, 1024}).  The unknown grid is nx = Nx, Nx + 2 or Nx + 1
+ * nodes by the kind, and likewise ny.
  * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED, HS_ERR_OOM. */
 hs_status hs_zplan_set_sides(hs_zplan_t plan, int x_kind, int y_kind);
 

@@ -41,15 +41,16 @@ HS_AXIS_X, HS_AXIS_Y = 0, 1
 HS_FACTOR_AUTO, HS_FACTOR_F32, HS_FACTOR_F64 = 0, 1, 2
 HS_HOST_F_MAPPED, HS_HOST_U_MAPPED, HS_HOST_F_EARLY, HS_HOST_U_LATE = 1, 2, 4, 8
 HS_ZFACE_DIRICHLET, HS_ZFACE_ROBIN = 0, 1
-HS_SIDE_DIRICHLET, HS_SIDE_NEUMANN = 0, 1
+HS_SIDE_DIRICHLET, HS_SIDE_NEUMANN, HS_SIDE_DN, HS_SIDE_ND = 0, 1, 2, 3
 HS_THOMAS_PIPE16_256, HS_THOMAS_PIPE8_128, HS_THOMAS_PLAIN16_256, HS_THOMAS_PIPE16_128 = 0, 1, 2, 3
+HS_THOMAS_BAL8_512, HS_THOMAS_BAL16_256 = 4, 5
 HS_INFO_MAX_ITERS = 8
 HS_INFO_STAGES = 8
 STAGES = ("rhs", "dst_x", "dst_y", "thomas", "idst_y", "idst_x", "residual", "total")
 
 EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_tol",
             "hs_set_stage_timing", "hs_solve",
-            "hs_residual", "hs_rhs_apply", "hs_stage_times", "hs_workspace_bytes", "hs_destroy",
+            "hs_residual", "hs_rhs_apply", "hs_fp64_fma_rate", "hs_stage_times", "hs_workspace_bytes", "hs_destroy",
             "hs_status_str", "hs_last_error", "hs_residual_static", "hs_batch_create",
             "hs_batch_set_io", "hs_batch_solve", "hs_batch_set_wait_limit", "hs_batch_set_tol",
             "hs_batch_set_residual_precision", "hs_batch_debug_stall", "hs_set_residual_precision",
@@ -149,6 +150,8 @@ def load(path: Optional[str] = None):
     lib.hs_residual.argtypes = [vp, vp, ci, ci, ctypes.POINTER(hs_boundary), vp, vp,
                                 ctypes.POINTER(cd), ctypes.POINTER(cd)]
     lib.hs_residual.restype = ci
+    lib.hs_fp64_fma_rate.argtypes = [vp, ctypes.POINTER(cd)]
+    lib.hs_fp64_fma_rate.restype = ci
     lib.hs_rhs_apply.argtypes = [vp, vp, ci, ci, ctypes.POINTER(hs_boundary), vp, vp]
     lib.hs_rhs_apply.restype = ci
     lib.hs_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
@@ -349,6 +352,13 @@ def hs_rhs_apply(plan, f, f_dtype, rhs_kind, bnd, F, stream=None):
     return _check(load().hs_rhs_apply(plan, _ptr(f), f_dtype, rhs_kind,
                                       ctypes.byref(bnd) if bnd is not None else None, _ptr(F),
                                       _stream_ptr(stream)), "hs_rhs_apply", plan)
+
+
+def hs_fp64_fma_rate(stream=None):
+    """Measured FP64 FMA throughput of the current device, TFLOP/s."""
+    t = ctypes.c_double()
+    _check(load().hs_fp64_fma_rate(_stream_ptr(stream), ctypes.byref(t)), "hs_fp64_fma_rate")
+    return t.value
 
 
 def hs_stage_times(plan):
@@ -621,7 +631,8 @@ class ZSolver:
 
     Arrays are planar complex float64 device tensors: f [2][Nz+2][Ny+2][Nx+2],
     g_lo / g_hi [2][ny][nx] (None = 0), u [2][Nz+2][ny][nx], with nx = Nx + 2 on a
-    Neumann x-axis (set_sides) else Nx, and likewise ny."""
+    Neumann x-axis (set_sides), Nx + 1 on an axis with one face of each kind
+    (HS_SIDE_DN: nodes 1..Nx+1; HS_SIDE_ND: nodes 0..Nx), else Nx; likewise ny."""
 
     def __init__(self, Nx, Ny, Nz, Lx, Ly, Lz, order):
         out = ctypes.c_void_p()
@@ -654,8 +665,10 @@ class ZSolver:
                          "hs_zplan_set_sides")
 
     def solve(self, f, u, g_lo=None, g_hi=None, stream=None, side_data=None):
-        """side_data: u_n on the (x-lo, x-hi, y-lo, y-hi) faces of Neumann axes, planar
-        complex [2][Nz+2][Ny+2] (x-faces) / [2][Nz+2][Nx+2] (y-faces); None entries = 0."""
+        """side_data: u_n on the (x-lo, x-hi, y-lo, y-hi) faces, planar complex
+        [2][Nz+2][Ny+2] (x-faces) / [2][Nz+2][Nx+2] (y-faces); None entries = 0.
+        Only Neumann faces take data (both faces of HS_SIDE_NEUMANN, the high face
+        of HS_SIDE_DN, the low face of HS_SIDE_ND)."""
         self._keep = (f, u, g_lo, g_hi, side_data)
         if side_data is None:
             return self._err(load().hs_zsolve(self.plan, _ptr(f), _ptr(g_lo), _ptr(g_hi),

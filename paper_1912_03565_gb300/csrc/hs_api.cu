@@ -893,7 +893,7 @@ hs_status hs_set_transform_variant(hs_plan_t P, int axis, int variant) {
 }
 
 hs_status hs_set_thomas_variant(hs_plan_t P, int variant) {
-    if (!P || variant < HS_THOMAS_PIPE16_256 || variant > HS_THOMAS_PIPE16_128)
+    if (!P || variant < HS_THOMAS_PIPE16_256 || variant > HS_THOMAS_BAL16_256)
         return HS_ERR_INVALID_ARG;
     P->thomas_variant = variant;
     return HS_OK;
@@ -974,7 +974,7 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
     if (st == HS_OK && mixed && P->have_coeff && P->thomas32) {
         int best = -1;
         float best_t = 0.f;
-        for (int v = HS_THOMAS_PIPE16_256; v <= HS_THOMAS_PIPE16_128 && st == HS_OK; ++v) {
+        for (int v = HS_THOMAS_PIPE16_256; v <= HS_THOMAS_BAL16_256 && st == HS_OK; ++v) {
             P->thomas_variant = v;
             st = hs_launch_thomas(P, HS_T_F32, w, P->d_dscr, s);
             if (st != HS_OK) break;

@@ -219,7 +219,9 @@ hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int chunks, int 
 // (nbz < 0: to the last tile; tiles are RZ output planes).
 // z-planes per tile of the nodal right-hand-side kernel (out_df: the mixed path's
 // sum-factorised kernel); slab launches count tiles of this height.
-int hs_rhs_tile_planes(int out_df);
+int hs_rhs_tile_planes(const hs_plan_s *P, int out_df);
+// planes per z-tile of the mixed path's right-hand-side and residual kernels
+int hs_sf_zdepth(const hs_plan_s *P);
 hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_kind,
                         const DevBoundary &b, void *F, int out_df, cudaStream_t s,
                         double *f2 = nullptr, int bz0 = 0, int nbz = -1);

@@ -25,6 +25,7 @@
 
 namespace hs_tiles {
 
+// tile: x, y columns; z planes at most (a launch may use fewer: zt)
 constexpr int RSX = 32, RSY = 8, RSZ = 32;
 constexpr int RSHX = RSX + 2, RSHY = RSY + 2;
 
@@ -97,15 +98,16 @@ __device__ __forceinline__ void residual_sf_tile(int Nx, int Ny, int Nz,
                                                  const float *__restrict__ F,
                                                  const float *__restrict__ U,
                                                  float *__restrict__ r, double *r2out,
-                                                 float2 *ring, int bx, int by, int bz) {
+                                                 float2 *ring, int bx, int by, int bz,
+                                                 int zt = RSZ) {
     // ring: 2 plane slots of RSHY x RSHX pairs (the plane being summed, the next)
     constexpr int NT = RSX * RSY;
     constexpr int PER = (RSHX * RSHY + NT - 1) / NT;
     const int tid = threadIdx.x;
     const int tx = tid & (RSX - 1), ty = tid / RSX;
     const int i0 = bx * RSX, j0 = by * RSY;   // 0-based interior indices
-    const int lbeg = bz * RSZ;
-    const int lend = min(lbeg + RSZ, Nz);     // exclusive
+    const int lbeg = bz * zt;
+    const int lend = min(lbeg + zt, Nz);     // exclusive
     const size_t plane = (size_t)Nx * Ny;
     const size_t n = plane * Nz;
     const int i = i0 + tx, j = j0 + ty;
@@ -195,7 +197,8 @@ __device__ __forceinline__ void residual_sf_tile_async(int Nx, int Ny, int Nz,
                                                        const float *__restrict__ F,
                                                        const float *__restrict__ U,
                                                        float *__restrict__ r, double *r2out,
-                                                       float2 *smem, int bx, int by, int bz) {
+                                                       float2 *smem, int bx, int by, int bz,
+                                                       int zt) {
     constexpr int NT = RSX * RSY;
     constexpr int PER = (RSHX * RSHY + NT - 1) / NT;
     constexpr int HALO = RSHX * RSHY;
@@ -205,8 +208,8 @@ __device__ __forceinline__ void residual_sf_tile_async(int Nx, int Ny, int Nz,
     const int tid = threadIdx.x;
     const int tx = tid & (RSX - 1), ty = tid / RSX;
     const int i0 = bx * RSX, j0 = by * RSY;
-    const int lbeg = bz * RSZ;
-    const int lend = min(lbeg + RSZ, Nz);    // exclusive
+    const int lbeg = bz * zt;
+    const int lend = min(lbeg + zt, Nz);    // exclusive
     const size_t plane = (size_t)Nx * Ny;
     const size_t n = plane * Nz;
     const int i = i0 + tx, j = j0 + ty;

@@ -74,7 +74,9 @@ __device__ __forceinline__ LPair lp_sub(LPair x, LPair y) {
 
 enum { SF_O2 = 0, SF_O4 = 1, SF_CD = 2, SF_O6 = 3 };
 
-constexpr int SFX = 32, SFY = 8, SFZ = 32;   // tile: x, y columns, z planes
+// tile: x, y columns; z planes at most (the depth of a launch, RhsArgs::zt, is
+// SFZ or a smaller power of two when the problem is too small to fill the GPU)
+constexpr int SFX = 32, SFY = 8, SFZ = 32;
 
 template <int H>
 struct SfGeom {
@@ -170,8 +172,8 @@ __device__ __forceinline__ void rhs_sf_tile(const RhsArgs &a, const T *__restric
     const int tid = threadIdx.x;
     const int tx = tid & (SFX - 1), ty = tid / SFX;
     const int i0 = 1 + bx * SFX, j0 = 1 + by * SFY;    // node indices of the first column
-    const int lbeg = 1 + bz * SFZ;
-    const int lend = min(lbeg + SFZ - 1, a.Nz);
+    const int lbeg = 1 + bz * a.zt;
+    const int lend = min(lbeg + a.zt - 1, a.Nz);
     const size_t n = (size_t)a.Nx * a.Ny * a.Nz;
     const size_t sy = (size_t)(a.Nx + 2), sz = sy * (a.Ny + 2);
     // every halo node of the tile is a node of the grid (no ghost in x, y)

@@ -385,6 +385,7 @@ struct RhsArgs {
     const float4 *rc;    // [Nz+2]: per-row double-float RHS weights (hs_api.cu, hs_set_coeff)
     int has_faces;       // 0: every Dirichlet face is zero, so the lifting vanishes
     int bz0;             // first z-tile of the launch (slab launches of the tiled kernels)
+    int zt;              // planes per z-tile of the sum-factorised kernel (runtime depth)
     DevBoundary b;
 };
 

@@ -18,7 +18,16 @@
 // face is the even reflection plus 2 h g, f and the z-face data are reflected
 // evenly, and the cosine transform DCT-I over nodes 0..N+1 (k_dct.cu) replaces
 // the sine transform; the modes cos(p pi i/(N+1)), p = 0..N+1, enter the same
-// eigenvalue formula, and the per-row coefficients are unchanged.
+// eigenvalue formula, and the per-row coefficients are unchanged.  An axis
+// with one face of each kind (HS_SIDE_DN: Dirichlet low face, u_n = g on the
+// high face; HS_SIDE_ND the reverse) has N + 1 unknowns (nodes 1..N+1, or
+// 0..N) and takes the quarter-wave modes of angle (2p - 1) pi / (2 (N + 1)),
+// p = 1..N+1: sines of the nodes 1..N+1 (weight 1/2 at the Neumann node), or
+// for HS_SIDE_ND the cosines of the nodes 0..N, which are those sines of the
+// reversed line times (-1)^(p+1).  Each such pass runs as the sine transform
+// of length 2N + 1 of the line extended evenly about its Neumann node (an
+// internal FP64 plan): the forward modes are half its odd outputs, and the
+// inverse is that transform of the modes placed at the odd points.
 //
 // The solve (Section 3.6 with complex rows): the right-hand side kernel writes
 // the unknown rows l0..l1 as planar complex data [2][Nu][ny][nx]; the real FP64
@@ -47,6 +56,7 @@ struct hs_zplan_s {
     int nx, ny, i0x, i0y;      // unknown grid of a plane; node index of its first point
     int layout_ok;             // transform plan, tables and buffers complete
     hs_plan_s *T;              // FP64 transform plan [2 Nu][ny][nx] (work: d_w64, d_dscr)
+    hs_plan_s *TQ[2];          // quarter-wave axis: plan of its lines extended to 2N + 1
     double *d_cos;             // [nx] then [ny]: cos(theta) of each axis' modes
     double2 *d_dct[2];         // Neumann axis: M roots then M + 1 half-angle pairs
     double2 *d_rows;           // [Nu][3][4] complex coefficients of the unknown rows
@@ -176,6 +186,8 @@ hs_status side_tables(hs_zplan_s *Z) {
     for (int a = 0; a < 2; ++a) {
         if (Z->side[a] == HS_SIDE_NEUMANN)
             for (int p = 0; p <= N[a] + 1; ++p) c.push_back(cos_pi_frac(p, N[a] + 1));
+        else if (Z->side[a] == HS_SIDE_DN || Z->side[a] == HS_SIDE_ND)   // quarter-wave modes
+            for (int p = 1; p <= N[a] + 1; ++p) c.push_back(cos_pi_frac(2 * p - 1, 2 * (N[a] + 1)));
         else
             for (int p = 1; p <= N[a]; ++p) c.push_back(cos_pi_frac(p, N[a] + 1));
     }
@@ -206,10 +218,14 @@ hs_status layout(hs_zplan_s *Z) {
     const int l0 = Z->kind[0] == HS_ZFACE_ROBIN ? 0 : 1;
     const int l1 = Z->kind[1] == HS_ZFACE_ROBIN ? Z->Nz + 1 : Z->Nz;
     const int Nu = l1 - l0 + 1;
-    const int nx = Z->side[0] == HS_SIDE_NEUMANN ? Z->Nx + 2 : Z->Nx;
-    const int ny = Z->side[1] == HS_SIDE_NEUMANN ? Z->Ny + 2 : Z->Ny;
-    Z->i0x = Z->side[0] == HS_SIDE_NEUMANN ? 0 : 1;
-    Z->i0y = Z->side[1] == HS_SIDE_NEUMANN ? 0 : 1;
+    // unknowns of a side axis: N (Dirichlet faces), N + 2 (Neumann faces), N + 1
+    // (one of each); the first is node 0 when the low face is a Neumann face
+    auto count = [](int kind, int N) {
+        return kind == HS_SIDE_NEUMANN ? N + 2 : (kind == HS_SIDE_DIRICHLET ? N : N + 1);
+    };
+    const int nx = count(Z->side[0], Z->Nx), ny = count(Z->side[1], Z->Ny);
+    Z->i0x = (Z->side[0] == HS_SIDE_NEUMANN || Z->side[0] == HS_SIDE_ND) ? 0 : 1;
+    Z->i0y = (Z->side[1] == HS_SIDE_NEUMANN || Z->side[1] == HS_SIDE_ND) ? 0 : 1;
     Z->l0 = l0;
     // rebuilt after a change of shape, or when an earlier rebuild stopped part-way
     if (!(Z->T && Z->d_rows && Z->d_fac && Nu == Z->Nu && nx == Z->nx && ny == Z->ny)) {
@@ -236,6 +252,27 @@ hs_status layout(hs_zplan_s *Z) {
         ZCK(Z, cudaMalloc(&Z->d_rows, (size_t)Nu * 12 * sizeof(double2)));
         ZCK(Z, cudaMalloc(&Z->d_fac, (size_t)6 * Nu * nx * ny * sizeof(double)));
     }
+    // the extended-line plans of quarter-wave axes (their work array holds the
+    // lines of length 2N + 1)
+    for (int a = 0; a < 2; ++a) {
+        const bool q = Z->side[a] == HS_SIDE_DN || Z->side[a] == HS_SIDE_ND;
+        const int ex = a == 0 ? 2 * Z->Nx + 1 : nx, ey = a == 1 ? 2 * Z->Ny + 1 : ny;
+        hs_plan_s *Q = Z->TQ[a];
+        if (Q && (!q || Q->Nx != ex || Q->Ny != ey || Q->Nz != 2 * Nu)) {
+            hs_destroy(Q);
+            Z->TQ[a] = nullptr;
+        }
+        if (q && !Z->TQ[a]) {
+            hs_plan_t Tq = nullptr;
+            const hs_status sq = hs_plan_ex(&Tq, ex, ey, 2 * Nu, 1.0, 1.0, 1.0, 2, HS_HELMHOLTZ,
+                                            HS_BC_DIRICHLET, HS_FP64, 1, 1);
+            if (sq != HS_OK) {
+                zerr(Z, "quarter-wave transform plan: status %d", sq);
+                return sq;
+            }
+            Z->TQ[a] = Tq;
+        }
+    }
     const hs_status st = side_tables(Z);
     if (st == HS_OK) Z->layout_ok = 1;
     return st;
@@ -253,7 +290,8 @@ bool device_ptr(const void *p) {
 struct ZRhsArgs {
     int Nx, Ny, Nz, Nu, l0, order;
     int nx, ny, i0x, i0y;   // unknown grid of a plane and its first node
-    int neu_x, neu_y;       // Neumann side axes (even reflection)
+    int neu_x, neu_y;       // side axes with a Neumann face (even reflection there)
+    int nlo_x, nhi_x, nlo_y, nhi_y;   // which faces of each axis are Neumann faces
     int kind_lo, kind_hi;
     double hz;
     double2 ga_lo, ga_hi;   // 2 h_z / alpha of each face (Robin)
@@ -272,8 +310,8 @@ __device__ inline int reflect(int i, int n) { return i < 0 ? -i : (i >= n ? 2 * 
 // Face data on the unknown grid: beyond a Dirichlet axis 0, beyond a Neumann one reflected.
 __device__ inline double2 face_val(const ZRhsArgs &a, const double *g, int j, int i) {
     if (!g) return make_double2(0.0, 0.0);
-    if (a.neu_y) j = reflect(j, a.ny);
-    if (a.neu_x) i = reflect(i, a.nx);
+    if ((j < 0 && a.nlo_y) || (j >= a.ny && a.nhi_y)) j = reflect(j, a.ny);
+    if ((i < 0 && a.nlo_x) || (i >= a.nx && a.nhi_x)) i = reflect(i, a.nx);
     if (j < 0 || j >= a.ny || i < 0 || i >= a.nx) return make_double2(0.0, 0.0);
     const size_t k = (size_t)j * a.nx + i, n = (size_t)a.ny * a.nx;
     return make_double2(g[k], g[n + k]);
@@ -418,6 +456,90 @@ __global__ void zside_kernel(ZRhsArgs a) {
 // (p, q); lambda_nu = 4 a cp cq + 2 b cp + 2 c cq + d, Section 3.6; no
 // pivoting): per row r the planar complex factors 1/m_r, lower_r/m_r and
 // c'_r = upper_r/m_r with m_r = diag_r - lower_r c'_{r-1}, each [2][Nu][ny][nx].
+// Quarter-wave pass of one side axis (HS_SIDE_DN / HS_SIDE_ND) through the
+// sine transform of length 2n - 1 (n = N + 1 unknowns per line).  W holds the
+// 2 Nu planes [ny][nx]; E the extended lines ([2 Nu][ny][2n - 1] along x,
+// [2 Nu][2n - 1][nx] along y).  rev: HS_SIDE_ND, whose nodes 0..N are the
+// reversed nodes 1..N+1 of the DN form and whose modes carry (-1)^(p+1).
+struct QArgs {
+    int axis, n, nx, ny, rev;
+    long lines;          // 2 Nu ny (x) or 2 Nu nx (y)
+    double scale;        // inverse: 2 / n
+};
+
+__device__ inline void q_line(const QArgs &q, long line, size_t &wb, size_t &eb, size_t &st) {
+    if (q.axis == HS_AXIS_X) {
+        wb = (size_t)line * q.n;
+        eb = (size_t)line * (2 * q.n - 1);
+        st = 1;
+    } else {
+        const long c = line / q.nx, i = line - c * q.nx;
+        wb = (size_t)c * q.n * q.nx + i;
+        eb = (size_t)c * (2 * q.n - 1) * q.nx + i;
+        st = q.nx;
+    }
+}
+
+// forward: the line extended evenly about its Neumann node (DN form, nodes 1..2n-1)
+__global__ void zq_gather_fwd(QArgs q, const double *__restrict__ W, double *__restrict__ E) {
+    const long m = 2 * q.n - 1;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < q.lines * m;
+         t += (long)gridDim.x * blockDim.x) {
+        const long line = t / m;
+        const int k = (int)(t - line * m) + 1;   // node of the extended line
+        const int kk = k <= q.n ? k : 2 * q.n - k;   // folded onto 1..n
+        const int a = q.rev ? q.n - kk : kk - 1;      // index in W's line
+        size_t wb, eb, st;
+        q_line(q, line, wb, eb, st);
+        E[eb + (size_t)(k - 1) * st] = W[wb + (size_t)a * st];
+    }
+}
+
+// forward: mode p = half the odd output 2p - 1 (times (-1)^(p+1) for ND)
+__global__ void zq_scatter_fwd(QArgs q, const double *__restrict__ E, double *__restrict__ W) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < q.lines * q.n;
+         t += (long)gridDim.x * blockDim.x) {
+        const long line = t / q.n;
+        const int p = (int)(t - line * q.n) + 1;
+        size_t wb, eb, st;
+        q_line(q, line, wb, eb, st);
+        const double sg = (q.rev && !(p & 1)) ? -0.5 : 0.5;
+        W[wb + (size_t)(p - 1) * st] = sg * E[eb + (size_t)(2 * p - 2) * st];
+    }
+}
+
+// inverse: the modes at the odd points 2p - 1 of the extended line, zeros between
+__global__ void zq_gather_inv(QArgs q, const double *__restrict__ W, double *__restrict__ E) {
+    const long m = 2 * q.n - 1;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < q.lines * m;
+         t += (long)gridDim.x * blockDim.x) {
+        const long line = t / m;
+        const int k = (int)(t - line * m) + 1;
+        size_t wb, eb, st;
+        q_line(q, line, wb, eb, st);
+        double v = 0.0;
+        if (k & 1) {
+            const int p = (k + 1) / 2;
+            v = W[wb + (size_t)(p - 1) * st];
+            if (q.rev && !(p & 1)) v = -v;
+        }
+        E[eb + (size_t)(k - 1) * st] = v;
+    }
+}
+
+// inverse: node i of the DN form is output i of the transform, times 2 / n
+__global__ void zq_scatter_inv(QArgs q, const double *__restrict__ E, double *__restrict__ W) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < q.lines * q.n;
+         t += (long)gridDim.x * blockDim.x) {
+        const long line = t / q.n;
+        const int a = (int)(t - line * q.n);
+        size_t wb, eb, st;
+        q_line(q, line, wb, eb, st);
+        const int e = q.rev ? q.n - 1 - a : a;
+        W[wb + (size_t)a * st] = q.scale * E[eb + (size_t)e * st];
+    }
+}
+
 __global__ void zfactor_kernel(double *fac, const double2 *rows, const double *cx,
                                const double *cy, int Nx, int Ny, int Nu) {
     const size_t plane = (size_t)Nx * Ny, n = plane * Nu;
@@ -550,8 +672,11 @@ hs_status hs_zplan_set_sides(hs_zplan_t Z, int x_kind, int y_kind) {
     if (!Z) return HS_ERR_INVALID_ARG;
     const int k[2] = {x_kind, y_kind}, N[2] = {Z->Nx, Z->Ny};
     for (int a = 0; a < 2; ++a) {
-        if (k[a] != HS_SIDE_DIRICHLET && k[a] != HS_SIDE_NEUMANN) return HS_ERR_INVALID_ARG;
+        if (k[a] < HS_SIDE_DIRICHLET || k[a] > HS_SIDE_ND) return HS_ERR_INVALID_ARG;
         if (k[a] == HS_SIDE_NEUMANN && !hs_dst_fast_size(N[a] + 1)) return HS_ERR_UNSUPPORTED;
+        // one face of each kind: the sine transform of the lines extended to 2N + 1
+        if ((k[a] == HS_SIDE_DN || k[a] == HS_SIDE_ND) && !hs_dst_fast_size(2 * (N[a] + 1)))
+            return HS_ERR_UNSUPPORTED;
     }
     Z->side[0] = x_kind;
     Z->side[1] = y_kind;
@@ -579,8 +704,11 @@ hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const 
     const double *sd[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int k = 0; side && k < 4; ++k) {
         if (!side[k]) continue;
-        // data on the faces of a Dirichlet axis have no meaning
-        if (Z->side[k / 2] != HS_SIDE_NEUMANN || !device_ptr(side[k])) return HS_ERR_INVALID_ARG;
+        // data on a Dirichlet face have no meaning
+        const int kind = Z->side[k / 2];
+        const bool neu = kind == HS_SIDE_NEUMANN || (kind == HS_SIDE_ND && k % 2 == 0) ||
+                         (kind == HS_SIDE_DN && k % 2 == 1);
+        if (!neu || !device_ptr(side[k])) return HS_ERR_INVALID_ARG;
         sd[k] = side[k];
     }
     Z->last_error[0] = 0;
@@ -592,8 +720,12 @@ hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const 
     ZRhsArgs a;
     a.Nx = Z->Nx; a.Ny = Z->Ny; a.Nz = Z->Nz; a.Nu = Z->Nu; a.l0 = Z->l0; a.order = Z->order;
     a.nx = Z->nx; a.ny = Z->ny; a.i0x = Z->i0x; a.i0y = Z->i0y;
-    a.neu_x = Z->side[0] == HS_SIDE_NEUMANN;
-    a.neu_y = Z->side[1] == HS_SIDE_NEUMANN;
+    a.neu_x = Z->side[0] != HS_SIDE_DIRICHLET;
+    a.neu_y = Z->side[1] != HS_SIDE_DIRICHLET;
+    a.nlo_x = Z->side[0] == HS_SIDE_NEUMANN || Z->side[0] == HS_SIDE_ND;
+    a.nhi_x = Z->side[0] == HS_SIDE_NEUMANN || Z->side[0] == HS_SIDE_DN;
+    a.nlo_y = Z->side[1] == HS_SIDE_NEUMANN || Z->side[1] == HS_SIDE_ND;
+    a.nhi_y = Z->side[1] == HS_SIDE_NEUMANN || Z->side[1] == HS_SIDE_DN;
     a.kind_lo = Z->kind[0]; a.kind_hi = Z->kind[1];
     a.hz = Z->hz;
     a.ga_lo = cscale(2.0 * Z->hz, cdiv_host(make_double2(1.0, 0.0), Z->alpha[0]));
@@ -617,9 +749,36 @@ hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const 
         ZCK(Z, cudaGetLastError());
     }
     if ((mk = mark(1)) != HS_OK) return mk;
-    // one transform pass along an axis: the cosine kernel on a Neumann axis, else the
-    // plan's sine transform; inverse passes carry 2 / (N + 1) for either
-    auto pass = [&](int axis, double scale) -> hs_status {
+    // one transform pass along an axis: the cosine kernel on a Neumann axis, the
+    // quarter-wave gather / extended sine transform / scatter on a mixed one, else
+    // the plan's sine transform; inverse passes carry 2 / (N + 1) for each kind
+    auto pass = [&](int axis, bool fwd, double scale) -> hs_status {
+        if (Z->side[axis] == HS_SIDE_DN || Z->side[axis] == HS_SIDE_ND) {
+            hs_plan_s *Q = Z->TQ[axis];
+            QArgs q;
+            q.axis = axis;
+            q.n = axis == HS_AXIS_X ? Z->nx : Z->ny;
+            q.nx = Z->nx;
+            q.ny = Z->ny;
+            q.rev = Z->side[axis] == HS_SIDE_ND;
+            q.lines = (long)2 * Z->Nu * (axis == HS_AXIS_X ? Z->ny : Z->nx);
+            q.scale = scale;
+            const long work = q.lines * (2 * q.n - 1);
+            const unsigned qb = (unsigned)((work + 255) / 256 < 152 * 16 ? (work + 255) / 256 : 152 * 16);
+            if (fwd)
+                zq_gather_fwd<<<qb, 256, 0, s>>>(q, W, Q->d_w64);
+            else
+                zq_gather_inv<<<qb, 256, 0, s>>>(q, W, Q->d_w64);
+            if (cudaGetLastError() != cudaSuccess) return HS_ERR_CUDA;
+            const hs_status sq = hs_launch_dst(Q, axis, HS_T_F64, HS_T_F64, Q->d_w64, HS_T_F64,
+                                               Q->d_w64, HS_MODE_WRITE, 1.0, s);
+            if (sq != HS_OK) return sq;
+            if (fwd)
+                zq_scatter_fwd<<<qb, 256, 0, s>>>(q, Q->d_w64, W);
+            else
+                zq_scatter_inv<<<qb, 256, 0, s>>>(q, Q->d_w64, W);
+            return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+        }
         if (Z->side[axis] == HS_SIDE_NEUMANN) {
             const int M = (axis == HS_AXIS_X ? Z->Nx : Z->Ny) + 1;
             const double2 *t = Z->d_dct[axis];
@@ -629,7 +788,7 @@ hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const 
         return hs_launch_dst(T, axis, HS_T_F64, HS_T_F64, W, HS_T_F64, W, HS_MODE_WRITE, scale, s);
     };
     hs_status st;
-    if ((st = pass(HS_AXIS_X, 1.0)) != HS_OK || (st = pass(HS_AXIS_Y, 1.0)) != HS_OK) {
+    if ((st = pass(HS_AXIS_X, true, 1.0)) != HS_OK || (st = pass(HS_AXIS_Y, true, 1.0)) != HS_OK) {
         zerr(Z, "forward transform: status %d", st);
         return st;
     }
@@ -644,8 +803,8 @@ hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const 
                                                                  Z->Nu);
     ZCK(Z, cudaGetLastError());
     if ((mk = mark(3)) != HS_OK) return mk;
-    if ((st = pass(HS_AXIS_Y, 2.0 / (Z->Ny + 1))) != HS_OK ||
-        (st = pass(HS_AXIS_X, 2.0 / (Z->Nx + 1))) != HS_OK) {
+    if ((st = pass(HS_AXIS_Y, false, 2.0 / (Z->Ny + 1))) != HS_OK ||
+        (st = pass(HS_AXIS_X, false, 2.0 / (Z->Nx + 1))) != HS_OK) {
         zerr(Z, "inverse transform: status %d", st);
         return st;
     }
@@ -697,6 +856,7 @@ hs_status hs_zplan_stage_times(hs_zplan_t Z, float *ms) {
 size_t hs_zplan_workspace_bytes(hs_zplan_t Z) {
     if (!Z) return 0;
     size_t b = hs_workspace_bytes(Z->T) + (Z->d_rows ? (size_t)Z->Nu * 12 * sizeof(double2) : 0);
+    for (int a = 0; a < 2; ++a) b += hs_workspace_bytes(Z->TQ[a]);
     b += (size_t)(Z->nx + Z->ny) * sizeof(double);
     if (Z->d_fac) b += (size_t)6 * Z->Nu * Z->nx * Z->ny * sizeof(double);
     if (Z->d_dct[0]) b += (2 * (size_t)Z->Nx + 3) * sizeof(double2);
@@ -713,6 +873,8 @@ const char *hs_zplan_last_error(hs_zplan_t Z) {
 void hs_zplan_destroy(hs_zplan_t Z) {
     if (!Z) return;
     if (Z->T) hs_destroy(Z->T);
+    for (int a = 0; a < 2; ++a)
+        if (Z->TQ[a]) hs_destroy(Z->TQ[a]);
     if (Z->d_rows) cudaFree(Z->d_rows);
     if (Z->d_cos) cudaFree(Z->d_cos);
     if (Z->d_fac) cudaFree(Z->d_fac);

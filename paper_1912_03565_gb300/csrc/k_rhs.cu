@@ -242,12 +242,12 @@ __global__ void __launch_bounds__(RSX *RSY) residual_sf_kernel(int Nx, int Ny, i
                                                                 float *__restrict__ r,
                                                                 const int *skip, double *r2out,
                                                                 const double *norms, int m,
-                                                                int sel) {
+                                                                int sel, int zt) {
     if (skip && *skip) return;
     if (sel == HS_RESID_SEL_DF && residual_use_f64(norms, m)) return;
     __shared__ __align__(16) float2 ring[resid_async_smem() / sizeof(float2)];
     residual_sf_tile_async<XY>(Nx, Ny, Nz, coef, F, U, r, r2out, ring, blockIdx.x, blockIdx.y,
-                               blockIdx.z);
+                               blockIdx.z, zt);
 }
 
 __global__ void __launch_bounds__(QTX *QTY) residual64_zmarch_kernel(
@@ -343,7 +343,7 @@ hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int chunks, int 
     const int K = chunks < 1 ? 1 : (chunks > HS_UP_CHUNKS ? HS_UP_CHUNKS : chunks);
     const size_t esz = f_dtype == HS_F64 ? 8 : 4;
     const size_t pb = (size_t)(P->Nx + 2) * (P->Ny + 2) * esz;   // bytes per node plane
-    const int TZ = hs_rhs_tile_planes(out_df);
+    const int TZ = hs_rhs_tile_planes(P, out_df);
     const int tz = (P->Nz + TZ - 1) / TZ;
     const unsigned char *src = static_cast<const unsigned char *>(fh);
     unsigned char *dst = static_cast<unsigned char *>(fd);
@@ -370,7 +370,24 @@ hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int chunks, int 
     return HS_OK;
 }
 
-int hs_rhs_tile_planes(int out_df) { return out_df ? SFZ : RZ; }
+// Planes per z-tile of the mixed path's z-marching kernels: 32, or fewer when the
+// problem would give less than two waves of CTAs (3 per SM) at that depth -- small
+// problems (batches of 63^3 ... 127^3) need the parallelism more than the shorter
+// z-halo overhead.
+int hs_sf_zdepth(const hs_plan_s *P) {
+    static int sms = 0;
+    if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device) !=
+                        cudaSuccess) {
+        cudaGetLastError();
+        sms = 148;
+    }
+    const long xy = (long)((P->Nx + SFX - 1) / SFX) * ((P->Ny + SFY - 1) / SFY);
+    int zt = SFZ;
+    while (zt > 4 && xy * ((P->Nz + zt - 1) / zt) < 2L * 3 * sms) zt /= 2;
+    return zt;
+}
+
+int hs_rhs_tile_planes(const hs_plan_s *P, int out_df) { return out_df ? hs_sf_zdepth(P) : RZ; }
 
 hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_kind,
                         const DevBoundary &b, void *F, int out_df, cudaStream_t s, double *f2,
@@ -392,8 +409,9 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
     for (int k = 0; k < 6; ++k)
         if (b.face[k]) a.has_faces = 1;
     if (rhs_kind == HS_RHS_NODAL) {
-        const int TZ = hs_rhs_tile_planes(out_df);
+        const int TZ = hs_rhs_tile_planes(P, out_df);
         const int tz = (P->Nz + TZ - 1) / TZ;
+        a.zt = TZ;
         a.bz0 = bz0 < 0 ? 0 : bz0;
         const int cnt = nbz < 0 ? tz - a.bz0 : nbz;
         if (cnt <= 0) return HS_OK;
@@ -437,14 +455,16 @@ hs_status hs_launch_residual_df(const hs_plan_s *P, const float *F, const float 
     dim3 qb(QTX, QTY, 1);
     dim3 qg((P->Nx + QTX - 1) / QTX, (P->Ny + QTY - 1) / QTY, (P->Nz + QZ - 1) / QZ);
     if (prec == HS_RESID_DF || prec == HS_RESID_SEL_DF) {
-        dim3 sg((P->Nx + RSX - 1) / RSX, (P->Ny + RSY - 1) / RSY, (P->Nz + RSZ - 1) / RSZ);
+        const int zt = hs_sf_zdepth(P);
+        dim3 sg((P->Nx + RSX - 1) / RSX, (P->Ny + RSY - 1) / RSY, (P->Nz + zt - 1) / zt);
         if (P->resid_xy)
             residual_sf_kernel<true><<<sg, RSX * RSY, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df, F,
-                                                              U, r, P->cur_skip, r2, norms, m, prec);
+                                                              U, r, P->cur_skip, r2, norms, m, prec,
+                                                              zt);
         else
             residual_sf_kernel<false><<<sg, RSX * RSY, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df,
                                                                F, U, r, P->cur_skip, r2, norms, m,
-                                                               prec);
+                                                               prec, zt);
     }
     if (prec == HS_RESID_F64 || prec == HS_RESID_SEL_F64)
         residual64_zmarch_kernel<<<qg, qb, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef, F, U, r,

@@ -139,6 +139,27 @@ void launch_f32(const hs_plan_s *P, float *data, cudaStream_t s) {
                                                           P->cur_skip);
 }
 
+// Balanced mapping: a whole number of blocks per SM and the columns shared
+// evenly among them (block size rounded up to a warp, at most NTMAX), so that
+// no SM runs a second round of blocks while others idle -- at 255^2 columns the
+// fixed 256-thread blocks give 254 blocks for 152 SMs.
+template <int CHK, int NTMAX>
+void launch_f32_bal(const hs_plan_s *P, float *data, cudaStream_t s) {
+    static int sms = 0;
+    if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device) !=
+                        cudaSuccess) {
+        cudaGetLastError();
+        sms = 148;
+    }
+    const size_t plane = (size_t)P->Nx * P->Ny;
+    const size_t per_sm = (plane + sms - 1) / sms;
+    const size_t k = (per_sm + NTMAX - 1) / NTMAX;               // blocks per SM
+    const unsigned blocks = (unsigned)(sms * k);
+    const unsigned nt = (unsigned)(((plane + blocks - 1) / blocks + 31) / 32 * 32);
+    thomas_f32_kernel<CHK, true, NTMAX><<<blocks, nt, 0, s>>>(P->Nx, P->Ny, P->Nz, data,
+                                                             P->d_fac32, P->cur_skip);
+}
+
 }  // namespace
 
 hs_status hs_launch_factor(const hs_plan_s *P, cudaStream_t s) {
@@ -163,6 +184,8 @@ hs_status hs_launch_thomas(const hs_plan_s *P, int tio, void *data, double *scra
             case HS_THOMAS_PIPE8_128: launch_f32<8, true, 128>(P, static_cast<float *>(data), s); break;
             case HS_THOMAS_PLAIN16_256: launch_f32<16, false, 256>(P, static_cast<float *>(data), s); break;
             case HS_THOMAS_PIPE16_128: launch_f32<16, true, 128>(P, static_cast<float *>(data), s); break;
+            case HS_THOMAS_BAL8_512: launch_f32_bal<8, 512>(P, static_cast<float *>(data), s); break;
+            case HS_THOMAS_BAL16_256: launch_f32_bal<16, 256>(P, static_cast<float *>(data), s); break;
             default: launch_f32<16, true, 256>(P, static_cast<float *>(data), s); break;
         }
     else

@@ -2,8 +2,9 @@
 
 Parity bar: the FP64 path's 1e-12 (max relative error over the whole complex field),
 on ragged sizes (runtime-sized and compiled transform lengths), every face
-combination, orders 2 and 4, absent face data, Nz = 1, and one 255^3 case; and
-with Neumann side axes (cosine transform), every side combination.
+combination, orders 2 and 4, absent face data, Nz = 1, and one 255^3 case; with
+Neumann side axes (cosine transform), every side combination; and with axes that
+have one face of each kind (quarter-wave transforms), beside every other kind.
 """
 import numpy as np
 import pytest
@@ -35,6 +36,12 @@ def _case(shape, L, seed, kscale=40.0):
     return O.grid_steps(shape, L), K, f, g_lo, g_hi
 
 
+def _nu(N, kind):
+    """Unknowns of a side axis: N (Dirichlet faces), N + 2 (Neumann faces), N + 1 (one
+    of each)."""
+    return {H.HS_SIDE_DIRICHLET: N, H.HS_SIDE_NEUMANN: N + 2}.get(kind, N + 1)
+
+
 def _planar(torch, a):
     return torch.from_numpy(np.ascontiguousarray(np.stack([a.real, a.imag]))).cuda()
 
@@ -47,8 +54,7 @@ def _gpu(shape, L, order, K, zf, f, g_lo, g_hi, sides=(0, 0)):
         s.set_coeff(K)
         s.set_faces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
         s.set_sides(*sides)
-        nx = Nx + 2 if sides[0] == H.HS_SIDE_NEUMANN else Nx
-        ny = Ny + 2 if sides[1] == H.HS_SIDE_NEUMANN else Ny
+        nx, ny = _nu(Nx, sides[0]), _nu(Ny, sides[1])
         u = torch.full((2, Nz + 2, ny, nx), np.nan, dtype=torch.float64, device="cuda")
         s.solve(_planar(torch, f), u, None if g_lo is None else _planar(torch, g_lo),
                 None if g_hi is None else _planar(torch, g_hi))
@@ -158,8 +164,7 @@ def _neumann_case(shape, L, sides, seed):
     z = np.arange(Nz + 2) / (Nz + 1)
     K = 40.0 * (1.0 + 0.5 * z) * (1.0 + 0.2j * (1.0 + np.cos(2.0 * z)))
     f = rs.uniform(-1, 1, (Nz + 2, Ny + 2, Nx + 2)) + 1j * rs.uniform(-1, 1, (Nz + 2, Ny + 2, Nx + 2))
-    nx = Nx + 2 if sides[0] == NEU else Nx
-    ny = Ny + 2 if sides[1] == NEU else Ny
+    nx, ny = _nu(Nx, sides[0]), _nu(Ny, sides[1])
     g_lo = rs.uniform(-1, 1, (ny, nx)) + 1j * rs.uniform(-1, 1, (ny, nx))
     g_hi = rs.uniform(-1, 1, (ny, nx)) + 1j * rs.uniform(-1, 1, (ny, nx))
     return O.grid_steps(shape, L), K, f, g_lo, g_hi
@@ -207,8 +212,13 @@ def test_neumann_unsupported_length():
             s.set_sides(H.HS_SIDE_NEUMANN, H.HS_SIDE_DIRICHLET)   # 31 points: no compiled FFT
         assert e.value.status == H.HS_ERR_UNSUPPORTED
         s.set_sides(H.HS_SIDE_DIRICHLET, H.HS_SIDE_NEUMANN)       # 32 points
-        with pytest.raises(H.HsError):
-            s.set_sides(2, 0)
+        with pytest.raises(H.HsError) as e:
+            s.set_sides(H.HS_SIDE_DN, H.HS_SIDE_DIRICHLET)   # extended line 62: none compiled
+        assert e.value.status == H.HS_ERR_UNSUPPORTED
+        s.set_sides(H.HS_SIDE_DIRICHLET, H.HS_SIDE_ND)        # extended line 64
+        with pytest.raises(H.HsError) as e:
+            s.set_sides(4, 0)
+        assert e.value.status == H.HS_ERR_INVALID_ARG
     finally:
         s.close()
 
@@ -236,8 +246,7 @@ def test_neumann_face_data_match_oracle(order, sides, faces):
         s.set_coeff(K)
         s.set_faces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
         s.set_sides(*sides)
-        nx = Nx + 2 if sides[0] == NEU else Nx
-        ny = Ny + 2 if sides[1] == NEU else Ny
+        nx, ny = _nu(Nx, sides[0]), _nu(Ny, sides[1])
         u = torch.full((2, Nz + 2, ny, nx), np.nan, dtype=torch.float64, device="cuda")
         sdd = [None if a is None else _planar(torch, a) for a in sd]
         s.solve(_planar(torch, f), u, _planar(torch, g_lo), _planar(torch, g_hi), side_data=sdd)
@@ -254,3 +263,92 @@ def test_neumann_face_data_match_oracle(order, sides, faces):
     finally:
         s.close()
     assert O.max_rel_diff(got, ref) <= TOL
+
+
+DN, ND = CX.SIDE_DN, CX.SIDE_ND
+MIXED = [(DN, DIRS), (ND, DIRS), (DIRS, DN), (DIRS, ND), (DN, ND), (ND, DN), (DN, NEU),
+         (NEU, ND)]
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("sides", MIXED)
+@pytest.mark.parametrize("faces", [(R, R), (D, D), (D, R)])
+@pytest.mark.parametrize("shape", [(31, 63, 9), (63, 31, 4)])
+def test_mixed_sides_match_oracle(order, sides, faces, shape):
+    """One Dirichlet and one Neumann face on an axis: quarter-wave transforms (the
+    extended lines of 2N + 1 points: 127 and 63 here) beside every other kind."""
+    L = (1.0, 0.8, 1.1)
+    h, K, f, g_lo, g_hi = _neumann_case(shape, L, sides, sum(shape) + 5 * sides[0] + sides[1])
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    ref, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi, sides)
+    got = _gpu(shape, L, order, K, zf, f, g_lo, g_hi, sides)
+    assert O.max_rel_diff(got, ref) <= TOL
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("sides", [(DN, ND), (ND, NEU), (NEU, DN), (DIRS, ND)])
+def test_mixed_face_data_match_oracle(order, sides):
+    """u_n = g on the Neumann face of each mixed axis (the high face of DN, the low face
+    of ND) with data; data on its Dirichlet face are rejected."""
+    torch = _torch()
+    shape, L = (31, 63, 7), (1.0, 1.3, 0.9)
+    Nx, Ny, Nz = shape
+    h, K, f, g_lo, g_hi = _neumann_case(shape, L, sides, 17 + order + 5 * sides[0] + sides[1])
+    rs = np.random.RandomState(9 + order)
+    cr = lambda *sh: rs.uniform(-1, 1, sh) + 1j * rs.uniform(-1, 1, sh)
+    neu_face = [sides[0] in (NEU, ND), sides[0] in (NEU, DN), sides[1] in (NEU, ND),
+                sides[1] in (NEU, DN)]
+    sd = [cr(Nz + 2, (Ny if k < 2 else Nx) + 2) if neu_face[k] else None for k in range(4)]
+    zf = CX.ZFaces(R, 1.0 + 0.5j, 2.0 - 1.0j, D)
+    ref, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi, sides, sd)
+    s = H.ZSolver(Nx, Ny, Nz, *L, order)
+    try:
+        s.set_coeff(K)
+        s.set_faces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
+        s.set_sides(*sides)
+        nx, ny = _nu(Nx, sides[0]), _nu(Ny, sides[1])
+        u = torch.full((2, Nz + 2, ny, nx), np.nan, dtype=torch.float64, device="cuda")
+        sdd = [None if a is None else _planar(torch, a) for a in sd]
+        s.solve(_planar(torch, f), u, _planar(torch, g_lo), _planar(torch, g_hi), side_data=sdd)
+        torch.cuda.synchronize()
+        uc = u.cpu().numpy()
+        got = uc[0] + 1j * uc[1]
+        for k in range(4):   # every Dirichlet face rejects data
+            if neu_face[k]:
+                continue
+            bad = [None, None, None, None]
+            bad[k] = _planar(torch, cr(Nz + 2, (Ny if k < 2 else Nx) + 2))
+            with pytest.raises(H.HsError) as e:
+                s.solve(_planar(torch, f), u, side_data=bad)
+            assert e.value.status == H.HS_ERR_INVALID_ARG
+    finally:
+        s.close()
+    assert O.max_rel_diff(got, ref) <= TOL
+
+
+def test_mixed_255():
+    """255 x 255 x 127 with a DN x-axis and an ND y-axis (extended lines of 511 points),
+    Robin z-faces, face data on both Neumann faces."""
+    torch = _torch()
+    shape, L = (255, 255, 127), (1.0, 1.0, 0.5)
+    Nx, Ny, Nz = shape
+    sides = (DN, ND)
+    h, K, f, g_lo, g_hi = _neumann_case(shape, L, sides, 99)
+    rs = np.random.RandomState(12)
+    cr = lambda *sh: rs.uniform(-1, 1, sh) + 1j * rs.uniform(-1, 1, sh)
+    sd = [None, cr(Nz + 2, Ny + 2), cr(Nz + 2, Nx + 2), None]
+    zf = CX.ZFaces(R, 1.0 + 0.5j, 3.0 - 1.0j, R, 1.0 + 0.5j, 3.0 - 1.0j)
+    ref, _ = CX.solve(4, h, K, zf, f, g_lo, g_hi, sides, sd)
+    s = H.ZSolver(Nx, Ny, Nz, *L, 4)
+    try:
+        s.set_coeff(K)
+        s.set_faces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
+        s.set_sides(*sides)
+        u = torch.full((2, Nz + 2, Ny + 1, Nx + 1), np.nan, dtype=torch.float64, device="cuda")
+        s.solve(_planar(torch, f), u, _planar(torch, g_lo), _planar(torch, g_hi),
+                side_data=[None if a is None else _planar(torch, a) for a in sd])
+        torch.cuda.synchronize()
+        uc = u.cpu().numpy()
+    finally:
+        s.close()
+    assert O.max_rel_diff(uc[0] + 1j * uc[1], ref) <= TOL

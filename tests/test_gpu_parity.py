@@ -521,10 +521,10 @@ def test_autotune_keeps_a_valid_variant():
         assert O.max_rel_diff(u.cpu().numpy(), ref) <= TOLMIX
         with pytest.raises(H.HsError):
             H.hs_set_transform_variant(s.plan, H.HS_AXIS_X, 7)
-        assert H.hs_get_thomas_variant(s.plan) in range(4)
+        assert H.hs_get_thomas_variant(s.plan) in range(6)
         # every z-solve mapping runs the same recurrence in the same order
         outs = []
-        for v in range(4):
+        for v in range(6):
             H.hs_set_thomas_variant(s.plan, v)
             uu = torch.zeros_like(u)
             s.solve(f, uu, H.HS_F64, H.HS_RHS_NODAL, faces, fnn)
@@ -533,7 +533,7 @@ def test_autotune_keeps_a_valid_variant():
         for uu in outs[1:]:
             assert torch.equal(uu, outs[0])
         with pytest.raises(H.HsError):
-            H.hs_set_thomas_variant(s.plan, 4)
+            H.hs_set_thomas_variant(s.plan, 6)
     finally:
         s.close()
     q = H.Solver(100, 20, 10, 1.0, 1.0, 1.0, 4, H.HS_HELMHOLTZ, H.HS_MIXED)   # N + 1 = 101
