@@ -55,15 +55,15 @@ BYTES_FP64 = {"rhs": 16.0, "dst_x": 16.0, "dst_y": 16.0, "thomas": 40.0, "idst_y
 # per launch: DRAM bytes read + written, warp instructions.  Valid only while the
 # kernel is unchanged since the capture (the profile named records the command).
 NCU_COUNTS = {
-    ("cube255_o6", "rhs"): {"bound": "alu", "dram_bytes": 139.350784e6 + 89.349632e6,
-                            "warp_inst": 338550643,
-                            "profile": "profiles/rhs_df_cube255_o6.md"},
+    ("cube255_o6", "rhs"): {"bound": "alu", "dram_bytes": 140.392704e6 + 91.851008e6,
+                            "warp_inst": 234759511,
+                            "profile": "profiles/rhs_sf_cube255_o6.md"},
     # forward transform stage of the complex plan (x and y pass): FP64-pipe warp
     # instructions and DRAM bytes of the two launches
     ("zrobin255_o4", "transforms"): {
-        "kernel": "dst_fast_kernel<double> x + y (sine tiles over 2 x 257 planes)",
-        "fp64_warp_inst": 32374688 + 32501248,
-        "dram_bytes": 267439360 + 207346944 + 267740160 + 211877888,
+        "kernel": "dst_half_kernel x + y (half-length FP64 sine tiles over 2 x 257 planes)",
+        "fp64_warp_inst": 20381680 + 20461312,
+        "dram_bytes": 267511808 + 205838592 + 267540480 + 210931200,
         "profile": "profiles/fp64_transforms_complex255.md"},
     ("zneumann255_o4", "transforms"): {
         "kernel": "dct_kernel x + y (cosine tiles over 2 x 257 planes)",
@@ -77,6 +77,7 @@ def fp64_pipe_peak():
     """FP64 pipe instruction rate of this GPU, G warp-instructions/s: the FP64 FMA
     throughput measured now by the library's probe (hs_fp64_fma_rate: 8 independent
     FMA chains per thread, 152 x 8 blocks of 256 threads), / 2 flops / 32 threads."""
+    import paper_1912_03565_gb300 as H
     rate = max(H.hs_fp64_fma_rate() for _ in range(3))
     return rate * 1e12 / 2.0 / 32.0 / 1e9, rate
 

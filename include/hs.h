@@ -70,7 +70,7 @@ enum { HS_F64 = 0, HS_F32 = 1 };                             /* element type of 
 enum { HS_RHS_NODAL = 0, HS_RHS_ASSEMBLED = 1 };             /* meaning of f */
 enum { HS_RESID_DF = 0, HS_RESID_F64 = 1, HS_RESID_AUTO = 2 }; /* refinement residual */
 enum { HS_DST_STAGED = 0, HS_DST_FUSED = 1, HS_DST_GENERIC = 2,   /* transform kernels */
-       HS_DST_TWOPASS = 3, HS_DST_FUSED_WIDE = 4, HS_DST_GEMM = 5 };
+       HS_DST_TWOPASS = 3, HS_DST_FUSED_WIDE = 4, HS_DST_GEMM = 5, HS_DST_HALF = 6 };
 enum { HS_AXIS_X = 0, HS_AXIS_Y = 1 };                       /* transform axis */
 enum { HS_FACTOR_AUTO = 0, HS_FACTOR_F32 = 1, HS_FACTOR_F64 = 2 }; /* mixed z-solve factors */
 enum { HS_HOST_F_MAPPED = 1, HS_HOST_U_MAPPED = 2, HS_HOST_F_EARLY = 4,     /* hs_set_host_io */
@@ -189,11 +189,7 @@ hs_status hs_set_refinement(hs_plan_t plan, int sweeps);
  *                 one by at least 16x (||r_0|| = ||F||), FP64 from the sweep
  *                 after one that did not: the pair residual has reached its
  *                 floor (an FP32 correction solve contracts far more).
- *                 Decided on the device from the accumulated norms.  A plan
- *                 whose z-systems are close to singular (min pivot ratio
- *                 below 1e-4, hs_info) takes FP64 from the first sweep: there
- *                 the pair residual's rounding, amplified by the conditioning,
- *                 would limit the refined accuracy.
+ *                 Decided on the device from the accumulated norms.
  * Errors: HS_ERR_INVALID_ARG.
  */
 hs_status hs_set_residual_precision(hs_plan_t plan, int mode);
@@ -237,6 +233,13 @@ hs_status hs_set_refinement_tol(hs_plan_t plan, double tol);
  *                  split sine matrix (at most 256 KB per axis).  A kernel whose
  *                  bounded internal wait gave up makes the next synchronous
  *                  call (hs_solve with info, hs_autotune) return HS_ERR_TIMEOUT.
+ *   HS_DST_HALF    HS_FP64 plans, N + 1 in {32, 64, 96, 128, 192, 256, 384,
+ *                  512, 768, 1024}: the transform through one complex FFT of
+ *                  (N + 1) / 2 points per line (the real sequence
+ *                  sin(pi j/M)(x_j + x_{M-j}) + (x_j - x_{M-j})/2, M = N + 1,
+ *                  whose DFT gives the even outputs directly and the odd ones
+ *                  by a running sum): about half the FP64 arithmetic of
+ *                  HS_DST_STAGED, error growing like the running sum's.
  * Results agree to rounding.  Default: HS_DST_STAGED where compiled.
  * Errors: HS_ERR_INVALID_ARG; HS_ERR_UNSUPPORTED (variant not built for this
  * length, axis or precision); HS_ERR_OOM.
@@ -270,9 +273,31 @@ hs_status hs_get_thomas_variant(hs_plan_t plan, int *variant);
  * HS_MIXED plan whose coefficients are set and whose factors are FP32, the
  * z-solve mappings are timed the same way and the fastest kept.
  * Synchronous.  Call after hs_set_coeff, before solves (not during capture).
+ * The choices are kept in the process-wide autotune cache, keyed by device
+ * (name, SM count), Nx, Ny, Nz, order, equation, precision and factor type;
+ * a later hs_autotune of a plan with the same key takes them (and the stored
+ * times) without timing.  hs_autotune_cache_clear forces fresh timing.
  * Errors: HS_ERR_INVALID_ARG (reps < 1), HS_ERR_CUDA.
  */
 hs_status hs_autotune(hs_plan_t plan, void *stream, int reps, float *ms_x, float *ms_y);
+
+/*
+ * Autotune cache (no paper counterpart; host only, thread-safe):
+ *   hs_autotune_cache_save(path)  writes every entry to a text file, one line
+ *       per key: "<device> <sms> <Nx> <Ny> <Nz> <order> <equation> <precision>
+ *       <f32_factors> <variant_x> <variant_y> <thomas_variant> <ms_x> <ms_y>"
+ *       after a '#' header line (-1 where a field does not apply);
+ *   hs_autotune_cache_load(path)  merges a file written that way (later
+ *       entries win); a malformed or out-of-range line merges nothing;
+ *   hs_autotune_cache_clear()     empties the cache;
+ *   hs_autotune_cache_count(&n)   number of entries.
+ * Errors: HS_ERR_INVALID_ARG (NULL argument, unreadable / unwritable file,
+ * malformed content).
+ */
+hs_status hs_autotune_cache_save(const char *path);
+hs_status hs_autotune_cache_load(const char *path);
+hs_status hs_autotune_cache_clear(void);
+hs_status hs_autotune_cache_count(int *count);
 
 /*
  * hs_set_factor_precision -- the factors of the mixed path's z-solves
@@ -346,12 +371,28 @@ hs_status hs_set_stage_timing(hs_plan_t plan, int on);
  *   u          output, FP64, interior [nrhs][Nz][Ny][Nx].
  *   stream     a cudaStream_t (NULL = the legacy default stream).
  *   info       NULL: the call is asynchronous.  Non-NULL: the call
- *              synchronises and fills the diagnostics of the last RHS.
+ *              synchronises and fills the diagnostics of the last RHS; it
+ *              first counts the NaN or infinite values of f (hs_check_finite
+ *              for device f, a host scan for host f) and returns
+ *              HS_ERR_NONFINITE, u untouched, if there are any.
  * nrhs must be between 1 and max_rhs.  Errors: HS_ERR_INVALID_ARG,
- * HS_ERR_NO_COEFF, HS_ERR_CUDA, HS_ERR_OOM (host staging).
+ * HS_ERR_NO_COEFF, HS_ERR_NONFINITE (info mode), HS_ERR_CUDA, HS_ERR_OOM
+ * (host staging).
  */
 hs_status hs_solve(hs_plan_t plan, const void *f, int f_dtype, int rhs_kind,
                    const hs_boundary *bnd, double *u, int nrhs, void *stream, hs_info *info);
+
+/*
+ * hs_check_finite -- *count = the number of NaN or infinite values among the n
+ * elements (dtype HS_F64 or HS_F32) of the DEVICE array data: a right-hand
+ * side, face data or a result (input validation; the paper's data are finite).
+ * One pass with a device reduction on `stream`, then a synchronisation.  The
+ * count is kept in the plan's scratch, so checks are ordered with the plan's
+ * other work on the same stream.  Errors: HS_ERR_INVALID_ARG (NULL plan or
+ * count, host pointer, other dtype), HS_ERR_CUDA.
+ */
+hs_status hs_check_finite(hs_plan_t plan, const void *data, int dtype, size_t n, void *stream,
+                          unsigned long long *count);
 
 /*
  * hs_residual -- ||F - A U||_2 and ||F||_2 of a computed solution, in FP64,

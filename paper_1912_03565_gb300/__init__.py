@@ -35,8 +35,8 @@ HS_CD_PAPER, HS_CD_CORRECTED = 0, 1
 HS_F64, HS_F32 = 0, 1
 HS_RHS_NODAL, HS_RHS_ASSEMBLED = 0, 1
 HS_RESID_DF, HS_RESID_F64, HS_RESID_AUTO = 0, 1, 2
-HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC, HS_DST_TWOPASS, HS_DST_FUSED_WIDE, HS_DST_GEMM = (
-    0, 1, 2, 3, 4, 5)
+(HS_DST_STAGED, HS_DST_FUSED, HS_DST_GENERIC, HS_DST_TWOPASS, HS_DST_FUSED_WIDE, HS_DST_GEMM,
+ HS_DST_HALF) = (0, 1, 2, 3, 4, 5, 6)
 HS_AXIS_X, HS_AXIS_Y = 0, 1
 HS_FACTOR_AUTO, HS_FACTOR_F32, HS_FACTOR_F64 = 0, 1, 2
 HS_HOST_F_MAPPED, HS_HOST_U_MAPPED, HS_HOST_F_EARLY, HS_HOST_U_LATE = 1, 2, 4, 8
@@ -50,7 +50,9 @@ STAGES = ("rhs", "dst_x", "dst_y", "thomas", "idst_y", "idst_x", "residual", "to
 
 EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_tol",
             "hs_set_stage_timing", "hs_solve",
-            "hs_residual", "hs_rhs_apply", "hs_fp64_fma_rate", "hs_stage_times", "hs_workspace_bytes", "hs_destroy",
+            "hs_residual", "hs_rhs_apply", "hs_fp64_fma_rate", "hs_check_finite",
+            "hs_autotune_cache_save", "hs_autotune_cache_load", "hs_autotune_cache_clear",
+            "hs_autotune_cache_count", "hs_stage_times", "hs_workspace_bytes", "hs_destroy",
             "hs_status_str", "hs_last_error", "hs_residual_static", "hs_batch_create",
             "hs_batch_set_io", "hs_batch_solve", "hs_batch_set_wait_limit", "hs_batch_set_tol",
             "hs_batch_set_residual_precision", "hs_batch_debug_stall", "hs_set_residual_precision",
@@ -150,6 +152,17 @@ def load(path: Optional[str] = None):
     lib.hs_residual.argtypes = [vp, vp, ci, ci, ctypes.POINTER(hs_boundary), vp, vp,
                                 ctypes.POINTER(cd), ctypes.POINTER(cd)]
     lib.hs_residual.restype = ci
+    lib.hs_autotune_cache_save.argtypes = [ctypes.c_char_p]
+    lib.hs_autotune_cache_save.restype = ci
+    lib.hs_autotune_cache_load.argtypes = [ctypes.c_char_p]
+    lib.hs_autotune_cache_load.restype = ci
+    lib.hs_autotune_cache_clear.argtypes = []
+    lib.hs_autotune_cache_clear.restype = ci
+    lib.hs_autotune_cache_count.argtypes = [ctypes.POINTER(ci)]
+    lib.hs_autotune_cache_count.restype = ci
+    lib.hs_check_finite.argtypes = [vp, vp, ci, ctypes.c_size_t, vp,
+                                    ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.hs_check_finite.restype = ci
     lib.hs_fp64_fma_rate.argtypes = [vp, ctypes.POINTER(cd)]
     lib.hs_fp64_fma_rate.restype = ci
     lib.hs_rhs_apply.argtypes = [vp, vp, ci, ci, ctypes.POINTER(hs_boundary), vp, vp]
@@ -352,6 +365,36 @@ def hs_rhs_apply(plan, f, f_dtype, rhs_kind, bnd, F, stream=None):
     return _check(load().hs_rhs_apply(plan, _ptr(f), f_dtype, rhs_kind,
                                       ctypes.byref(bnd) if bnd is not None else None, _ptr(F),
                                       _stream_ptr(stream)), "hs_rhs_apply", plan)
+
+
+def hs_autotune_cache_save(path):
+    _check(load().hs_autotune_cache_save(os.fsencode(path)), "hs_autotune_cache_save")
+
+
+def hs_autotune_cache_load(path):
+    _check(load().hs_autotune_cache_load(os.fsencode(path)), "hs_autotune_cache_load")
+
+
+def hs_autotune_cache_clear():
+    _check(load().hs_autotune_cache_clear(), "hs_autotune_cache_clear")
+
+
+def hs_autotune_cache_count():
+    n = ctypes.c_int()
+    _check(load().hs_autotune_cache_count(ctypes.byref(n)), "hs_autotune_cache_count")
+    return n.value
+
+
+def hs_check_finite(plan, data, stream=None):
+    """Number of NaN / infinite values of a float64 or float32 device tensor."""
+    import torch
+    if data.dtype not in (torch.float64, torch.float32) or not data.is_contiguous():
+        raise ValueError("data must be a contiguous float64 or float32 tensor")
+    n = ctypes.c_ulonglong()
+    dt = HS_F64 if data.dtype == torch.float64 else HS_F32
+    _check(load().hs_check_finite(plan, _ptr(data), dt, data.numel(), _stream_ptr(stream),
+                                  ctypes.byref(n)), "hs_check_finite", plan)
+    return n.value
 
 
 def hs_fp64_fma_rate(stream=None):

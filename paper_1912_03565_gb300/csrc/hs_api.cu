@@ -423,18 +423,31 @@ void timer_drain(hs_plan_s *P) {
     P->timer_used = 0;
 }
 
+// Stage events (when timing is on) and an NVTX range per stage (always; a no-op
+// without a profiler).
+const char *const kStageName[HS_STAGE_TOTAL] = {"hs rhs", "hs dst_x", "hs dst_y", "hs thomas",
+                                                "hs idst_y", "hs idst_x", "hs residual"};
 struct StageTimer {
     hs_plan_s *P;
     cudaStream_t s;
     bool on;
+    bool open = false;   // an NVTX stage range is pushed
     StageTimer(hs_plan_s *p, cudaStream_t st, bool o) : P(p), s(st), on(o) {}
+    ~StageTimer() {
+        if (open) nvtxRangePop();
+    }
     void begin(int k) {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(k >= 0 && k < HS_STAGE_TOTAL ? kStageName[k] : "hs stage");
+        open = true;
         if (!on) return;
         if (P->timer_used == HS_EVENT_PAIRS) timer_drain(P);
         P->timer_stage[P->timer_used] = k;
         cudaEventRecord(P->ev[2 * P->timer_used], s);
     }
     void end(int k) {
+        if (open) nvtxRangePop();
+        open = false;
         if (!on) return;
         (void)k;
         cudaEventRecord(P->ev[2 * P->timer_used + 1], s);
@@ -488,15 +501,12 @@ hs_status residual_norms(hs_plan_s *P, const double *F, const double *U, cudaStr
 // One right-hand side: F (lifted, FP64) is in P->d_w64 on entry.
 // Does a mixed solve accumulate ||F||^2 and ||r_m||^2 on the device (tolerance
 // stop or the automatic residual precision, without hs_info)?
-// Residual precision the mixed solve uses: the automatic mode takes FP64 from the
-// first sweep on plans whose z-systems are close to singular (min pivot ratio below
-// HS_ILL_PIVOT, where the FP64 factors are kept too): there the pair residual's
-// rounding floor, amplified by the conditioning, is above the refined accuracy.
-int effective_resid_mode(const hs_plan_s *P) {
-    if (P->resid_mode == HS_RESID_AUTO && P->have_coeff && P->min_pivot_ratio < HS_ILL_PIVOT)
-        return HS_RESID_F64;
-    return P->resid_mode;
-}
+// Residual precision the mixed solve uses.  The automatic mode decides per sweep
+// on the device (residual_use_f64): FP64 only after a pair residual that stopped
+// shrinking.  Forcing FP64 from the first sweep on plans close to singular was
+// measured to buy no accuracy on the batch workload (same worst errors) at a
+// quarter of its time, so the pivot ratio does not enter the choice.
+int effective_resid_mode(const hs_plan_s *P) { return P->resid_mode; }
 
 bool refine_norms_on(const hs_plan_s *P, bool info) {
     if (P->precision != HS_MIXED || info || P->refine_sweeps < 1) return false;
@@ -621,6 +631,8 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
 }
 
 }  // namespace
+
+bool hs_is_device_ptr(const void *p) { return is_device_ptr(p); }
 
 namespace {
 
@@ -861,7 +873,10 @@ hs_status hs_set_residual_precision(hs_plan_t P, int mode) {
 
 hs_status hs_set_transform_variant(hs_plan_t P, int axis, int variant) {
     if (!P || (axis != HS_AXIS_X && axis != HS_AXIS_Y)) return HS_ERR_INVALID_ARG;
-    if (variant < HS_DST_STAGED || variant > HS_DST_GEMM) return HS_ERR_INVALID_ARG;
+    if (variant < HS_DST_STAGED || variant > HS_DST_HALF) return HS_ERR_INVALID_ARG;
+    if (variant == HS_DST_HALF &&
+        (P->precision != HS_FP64 || !hs_dst_half_size(P->axd[axis].M)))
+        return HS_ERR_UNSUPPORTED;
     if (variant == HS_DST_GEMM) {
         if (P->precision != HS_MIXED || !hs_dst_gemm_size(P->axf[axis].M)) return HS_ERR_UNSUPPORTED;
         HS_TRY(P, ensure_gemm_table(P, axis));
@@ -912,9 +927,23 @@ hs_status hs_get_transform_variant(hs_plan_t P, int axis, int *variant) {
 }
 
 hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *ms_y) {
+    HsRange range("hs_autotune");
     if (!P || reps < 1) return HS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool mixed = P->precision == HS_MIXED;
+    const bool tune_thomas = mixed && P->have_coeff && P->thomas32;
+    {   // a plan of the same class was tuned before: take its choices
+        int cx, cy, ct;
+        float mx, my;
+        if (hs_tune_lookup(P, &cx, &cy, &ct, &mx, &my) &&
+            hs_set_transform_variant(P, HS_AXIS_X, cx) == HS_OK &&
+            hs_set_transform_variant(P, HS_AXIS_Y, cy) == HS_OK &&
+            (!tune_thomas || hs_set_thomas_variant(P, ct) == HS_OK)) {
+            if (ms_x) *ms_x = mx;
+            if (ms_y) *ms_y = my;
+            return HS_OK;
+        }
+    }
     const int tc = mixed ? HS_T_F32 : HS_T_F64;
     void *w = mixed ? (void *)P->d_w32 : (void *)P->d_w64;
     if (!w) return HS_ERR_INVALID_ARG;
@@ -932,7 +961,7 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
     for (int axis = 0; axis < 2 && st == HS_OK; ++axis) {
         const int saved = P->dst_variant[axis];
         int best = -1;
-        for (int v = HS_DST_STAGED; v <= HS_DST_GEMM && st == HS_OK; ++v) {
+        for (int v = HS_DST_STAGED; v <= HS_DST_HALF && st == HS_OK; ++v) {
             if (hs_set_transform_variant(P, axis, v) != HS_OK) continue;
             // one untimed round (first launch, attribute set-up), then `reps`
             // timed.  x of a mixed plan: a forward pass and an inverse pass that
@@ -1000,6 +1029,8 @@ hs_status hs_autotune(hs_plan_t P, void *stream, int reps, float *ms_x, float *m
     }
     if (ms_x) *ms_x = best_ms[0];
     if (ms_y) *ms_y = best_ms[1];
+    hs_tune_store(P, P->dst_variant[0], P->dst_variant[1], tune_thomas ? P->thomas_variant : -1,
+                  best_ms[0], best_ms[1]);
     return HS_OK;
 }
 
@@ -1033,6 +1064,7 @@ hs_status hs_set_stage_timing(hs_plan_t P, int on) {
 
 hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const hs_boundary *bnd,
                    double *u, int nrhs, void *stream, hs_info *info) {
+    HsRange range("hs_solve");
     if (!P || !f || !u) return HS_ERR_INVALID_ARG;
     if (f_dtype != HS_F64 && f_dtype != HS_F32) return HS_ERR_INVALID_ARG;
     if (rhs_kind != HS_RHS_NODAL && rhs_kind != HS_RHS_ASSEMBLED) return HS_ERR_INVALID_ARG;
@@ -1126,6 +1158,24 @@ hs_status hs_solve(hs_plan_t P, const void *f, int f_dtype, int rhs_kind, const 
         HS_TRY(P, stage_boundary(P, bnd, esz, s, &db));
     }
 
+    if (info) {
+        // synchronous mode: NaN or infinite samples of f are reported instead of
+        // solved (a device reduction over device f, a scan of host f)
+        unsigned long long bad = 0;
+        if (is_device_ptr(f)) {
+            HS_TRY(P, hs_check_finite(P, f, f_dtype, fcount * nrhs, stream, &bad));
+        } else if (f_dtype == HS_F64) {
+            const double *h = static_cast<const double *>(f);
+            for (size_t i = 0; i < fcount * nrhs; ++i) bad += !isfinite(h[i]);
+        } else {
+            const float *h = static_cast<const float *>(f);
+            for (size_t i = 0; i < fcount * nrhs; ++i) bad += !isfinite(h[i]);
+        }
+        if (bad) {
+            set_err(P, "hs_solve: f holds %llu NaN or infinite value(s)", bad);
+            return HS_ERR_NONFINITE;
+        }
+    }
     StageTimer T(P, s, P->stage_timing != 0 && P->have_events);
     timer_reset(P);
     if (T.on) cudaEventRecord(P->ev_total[0], s);

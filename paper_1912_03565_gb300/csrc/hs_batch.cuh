@@ -62,7 +62,6 @@ struct BatchWork {
     const float4 *rw;                  // per-row weights of the sum-factorised right-hand side
     float2 rhsW;                       // its constant pair weight
     int resid_xy;                      // b_nu = c_nu on every row (merged residual sums)
-    int ill;                           // z-systems close to singular: FP64 residual (automatic)
     int need[BMAX_STAGES];
 };
 
@@ -263,7 +262,7 @@ __device__ void run_tile(const BatchArgs &A, const BatchWork &W, int stage, int 
             double *r2 = A.norms_on ? W.norms + m : nullptr;
             const bool f64 = A.resid_mode == HS_RESID_F64 ||
                              (A.resid_mode == HS_RESID_AUTO &&
-                              (W.ill || residual_use_f64(W.norms, m)));
+                              residual_use_f64(W.norms, m));
             // tiles are RSZ = 2 QZ planes deep: the FP64 tile runs on both halves
             if (f64) {
                 residual64_tile<true>(W.Nx, W.Ny, W.Nz, W.coef64, W.F, W.U, W.w, r2, smem, bx, by,

@@ -9,7 +9,7 @@
 
 #define HS_MAX_STAGES 16
 // Min pivot ratio below which a plan's z-systems count as close to singular: the
-// mixed path then keeps FP64 factors and (automatic mode) an FP64 residual.
+// mixed path then keeps FP64 factors (FP64 forward sweep).
 #define HS_ILL_PIVOT 1e-4
 #define HS_EVENT_PAIRS 128
 
@@ -149,6 +149,28 @@ hs_status hs_launch_dst(const hs_plan_s *P, int axis, int tc, int tin, const voi
 
 // Compile-time-sized transform kernels (k_dst_fast.cu): 1 when M = N + 1 has one.
 int hs_dst_fast_size(int M);
+// NVTX range for the lifetime of a scope (a no-op unless a profiler is attached):
+// one per public entry point that launches work.
+#include <nvtx3/nvToolsExt.h>
+struct HsRange {
+    explicit HsRange(const char *name) { nvtxRangePushA(name); }
+    ~HsRange() { nvtxRangePop(); }
+    HsRange(const HsRange &) = delete;
+    HsRange &operator=(const HsRange &) = delete;
+};
+// Autotune cache (hs_tune_cache.cu): choices of an earlier hs_autotune for a plan
+// of the same class (device, shape, order, equation, precision, factor type).
+bool hs_tune_lookup(const hs_plan_s *P, int *vx, int *vy, int *thomas, float *msx, float *msy);
+void hs_tune_store(const hs_plan_s *P, int vx, int vy, int thomas, float msx, float msy);
+// cudaPointerGetAttributes says device or managed memory (NULL counts as device).
+bool hs_is_device_ptr(const void *p);
+// Enqueue the count of NaN / infinite values of x[0..n) into *dcount (k_finite.cu).
+hs_status hs_launch_nonfinite(const void *x, int dtype, size_t n, unsigned long long *dcount,
+                              cudaStream_t s);
+// Half-length FP64 DST-I (k_dst_half.cu): lengths with a compiled M/2-point FFT.
+int hs_dst_half_size(int M);
+hs_status hs_launch_dst_half(const hs_plan_s *P, int axis, int tin, const void *in, int tout,
+                             void *out, int mode, double scale, cudaStream_t s);
 hs_status hs_launch_dst_fast(const hs_plan_s *P, int axis, int tc, int tin, const void *in,
                              int tout, void *out, int mode, double scale, cudaStream_t s,
                              double *aux);

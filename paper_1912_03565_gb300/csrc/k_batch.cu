@@ -404,7 +404,6 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
             W.rw = P->d_rhs_df + (d.Nz + 2);
             W.rhsW = P->rhs_sf_W;
             W.resid_xy = P->resid_xy;
-            W.ill = P->min_pivot_ratio < HS_ILL_PIVOT;
             const int Sx = lines_for(W.Mx, HS_AXIS_X), Sy = lines_for(W.My, HS_AXIS_Y);
             W.dxg = (int)(((long)d.Ny * d.Nz + Sx - 1) / Sx);
             W.lx = Sx;
@@ -612,6 +611,7 @@ hs_status hs_batch_debug_stall(hs_batch_t B, int on) {
 }
 
 hs_status hs_batch_solve(hs_batch_t B, void *stream, int sync) {
+    HsRange range("hs_batch_solve");
     if (!B) return HS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (!B->have_graph || B->graph_stream != s) {

@@ -249,6 +249,9 @@ hs_status layout(hs_zplan_s *Z) {
             return st;
         }
         Z->T = T;
+        // the half-length FP64 sine transform where its FFT is compiled (the
+        // others keep the plan's default)
+        for (int a = 0; a < 2; ++a) (void)hs_set_transform_variant(T, a, HS_DST_HALF);
         ZCK(Z, cudaMalloc(&Z->d_rows, (size_t)Nu * 12 * sizeof(double2)));
         ZCK(Z, cudaMalloc(&Z->d_fac, (size_t)6 * Nu * nx * ny * sizeof(double)));
     }
@@ -270,6 +273,7 @@ hs_status layout(hs_zplan_s *Z) {
                 zerr(Z, "quarter-wave transform plan: status %d", sq);
                 return sq;
             }
+            (void)hs_set_transform_variant(Tq, a, HS_DST_HALF);
             Z->TQ[a] = Tq;
         }
     }
@@ -692,6 +696,7 @@ hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const dou
 
 hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const double *g_hi,
                        const double *const *side, double *u, void *stream) {
+    HsRange range("hs_zsolve");
     if (!Z || !f || !u) return HS_ERR_INVALID_ARG;
     if (!Z->layout_ok) {
         zerr(Z, "plan set-up incomplete: an earlier set-up call failed part-way");

@@ -345,6 +345,11 @@ int hs_dst_fits(const DstAxis &ax, int axis, int tc) {
 hs_status hs_launch_dst(const hs_plan_s *P, int axis, int tc, int tin, const void *in, int tout,
                         void *out, int mode, double scale, cudaStream_t s, double *aux) {
     const int v = P->dst_variant[axis];
+    if (v == HS_DST_HALF && tc == HS_T_F64) {
+        // one M/2-point FFT per line; modes it does not cover fall through
+        const hs_status st = hs_launch_dst_half(P, axis, tin, in, tout, out, mode, scale, s);
+        if (st != HS_ERR_UNSUPPORTED) return st;
+    }
     if (v == HS_DST_GEMM && tc == HS_T_F32) {
         // tensor-core sine-matrix product; modes it does not cover fall through
         const hs_status st = hs_launch_dst_gemm(P, axis, tin, in, tout, out, mode, scale, s, aux);

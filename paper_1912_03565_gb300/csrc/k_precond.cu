@@ -241,6 +241,7 @@ hs_status hs_precond_apply(hs_precond_t C, const double *u, double *y, void *str
 
 hs_status hs_precond_solve(hs_precond_t C, const double *F, double *x, double tol, int maxit,
                            void *stream, hs_precond_info *info) {
+    HsRange range("hs_precond_solve");
     if (!C || !F || !x || !(tol >= 0.0) || maxit < 1) return HS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t n = C->n;

@@ -97,3 +97,47 @@ def test_complex_plan_and_host_io_argument_validation(lib):
     assert lib.hs_host_io_wait(None, None) == H.HS_ERR_INVALID_ARG
     assert lib.hs_set_coeff_fn(None, H.HS_COEFF_FN(lambda z, d, u: 0.0), None, 0) == \
         H.HS_ERR_INVALID_ARG
+
+
+def test_autotune_cache_file_round_trip(lib, tmp_path):
+    """The autotune cache's text format: a written file loads back to the same entries,
+    and malformed or out-of-range content merges nothing (host only, no GPU)."""
+    H.hs_autotune_cache_clear()
+    assert H.hs_autotune_cache_count() == 0
+    good = tmp_path / "tune.txt"
+    good.write_text("# hs autotune cache v1\n"
+                    "NVIDIA_GB300 152 255 255 255 6 0 1 1 1 1 5 0.046 0.055\n"
+                    "NVIDIA_GB300 152 511 511 511 6 0 0 -1 6 6 -1 1.2 1.3\n"
+                    "\n")
+    H.hs_autotune_cache_load(str(good))
+    assert H.hs_autotune_cache_count() == 2
+    out = tmp_path / "out.txt"
+    H.hs_autotune_cache_save(str(out))
+    lines = [l.split() for l in out.read_text().splitlines() if not l.startswith("#")]
+    assert sorted(l[:13] for l in lines) == sorted([
+        "NVIDIA_GB300 152 255 255 255 6 0 1 1 1 1 5".split() + ["0.046"],
+        "NVIDIA_GB300 152 511 511 511 6 0 0 -1 6 6 -1".split() + ["1.2"]])
+    H.hs_autotune_cache_clear()
+    H.hs_autotune_cache_load(str(out))
+    assert H.hs_autotune_cache_count() == 2
+    for bad_line in ("NVIDIA_GB300 152 255 255 255 6 0 1 1 9 1 5 0.1 0.1\n",    # variant 9
+                     "NVIDIA_GB300 152 255 255 255 5 0 1 1 1 1 5 0.1 0.1\n",    # order 5
+                     "NVIDIA_GB300 152 255 255 255 6 0 1 1 1 1 5 0.1\n",        # short
+                     "NVIDIA_GB300 152 255 255 255 6 0 1 1 1 1 5 0.1 0.1 7\n"):  # extra field
+        bad = tmp_path / "bad.txt"
+        bad.write_text("NVIDIA_GB300 152 63 63 63 4 0 1 1 0 0 0 0.01 0.01\n" + bad_line)
+        with pytest.raises(H.HsError) as e:
+            H.hs_autotune_cache_load(str(bad))
+        assert e.value.status == H.HS_ERR_INVALID_ARG
+        assert H.hs_autotune_cache_count() == 2   # nothing merged, not even the good line
+    with pytest.raises(H.HsError):
+        H.hs_autotune_cache_load(str(tmp_path / "missing.txt"))
+    H.hs_autotune_cache_clear()
+    assert H.hs_autotune_cache_count() == 0
+
+
+def test_check_finite_argument_validation(lib):
+    """hs_check_finite refuses a NULL plan or count before touching the device."""
+    cnt = ctypes.c_ulonglong()
+    assert lib.hs_check_finite(None, None, 0, 0, None, ctypes.byref(cnt)) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_check_finite(None, None, 0, 0, None, None) == H.HS_ERR_INVALID_ARG

@@ -63,7 +63,7 @@ def test_complex_workloads_and_fp64_pipe_peak():
     the oracle leg on a small instance of the Neumann recipe (every plane and side node
     is an unknown: Robin z-faces, Neumann x and y)."""
     assert {"zrobin255_o4", "zneumann255_o4"} <= set(bench.WORKLOADS)
-    assert abs(bench.FP64_PIPE_PEAK - 1.19e12 / 64 / 1e9) < 1e-9
+    assert callable(bench.fp64_pipe_peak)   # measured on the GPU by hs_fp64_fma_rate
     for name in ("zrobin255_o4", "zneumann255_o4"):
         c = bench.NCU_COUNTS[(name, "transforms")]
         assert c["fp64_warp_inst"] > 0 and c["dram_bytes"] > 0

@@ -152,9 +152,9 @@ def test_batch64_ill_conditioned_problems(pid):
     Two FP64 solvers -- the GPU FP64 path and the oracle -- differ here by delta
     (measured in the test; 8.9e-10 and 6.1e-12 when first measured): the FP64
     rounding floor of these problems.  The refined mixed path (automatic residual
-    precision, which takes FP64 residuals from the first sweep on plans this close
-    to singular; stop at ||r|| / ||F|| <= 1e-11, at most 4 sweeps) is held to
-    max(1e-10, 4 delta) against the oracle."""
+    precision: FP64 residuals only after a pair residual stopped shrinking; stop at
+    ||r|| / ||F|| <= 1e-11, at most 4 sweeps) is held to max(1e-10, 4 delta)
+    against the oracle."""
     torch = pytest.importorskip("torch")
     spec = W.workload_batch_specs(64, 3)[pid]
     p = W.batch_problem(spec, 0)
