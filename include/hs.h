@@ -670,7 +670,9 @@ enum { HS_ZFACE_DIRICHLET = 0, HS_ZFACE_ROBIN = 1 };
 enum { HS_SIDE_DIRICHLET = 0, HS_SIDE_NEUMANN = 1, HS_SIDE_DN = 2, HS_SIDE_ND = 3 };
 
 /* hs_zplan -- plan for an Nx x Ny x Nz interior grid on [0,Lx]x[0,Ly]x[0,Lz]
- * (h_a = L_a / (N_a + 1)), order 2 or 4.  Faces start Dirichlet.  Errors:
+ * (h_a = L_a / (N_a + 1)), order 2, 4 or 6 (6: Section 3.4's rows, uniform h,
+ * |h_x - h_z| and |h_y - h_z| <= 1e-12 h_z, Dirichlet side faces, coefficients
+ * through hs_zplan_set_coeff6).  Faces start Dirichlet.  Errors:
  * HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED (transform length), HS_ERR_OOM,
  * HS_ERR_CUDA. */
 hs_status hs_zplan(hs_zplan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly, double Lz,
@@ -678,8 +680,19 @@ hs_status hs_zplan(hs_zplan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly
 
 /* hs_zplan_set_coeff -- K = k^2 (Sections 3.2, 3.3 with complex K) at the
  * nodes l = 0..Nz+1: host array of Nz + 2
- * (re, im) pairs, copied.  Errors: HS_ERR_INVALID_ARG (NULL, non-finite). */
+ * (re, im) pairs, copied.  Errors: HS_ERR_INVALID_ARG (NULL, non-finite, or an
+ * order-6 plan, which needs hs_zplan_set_coeff6). */
 hs_status hs_zplan_set_coeff(hs_zplan_t plan, const double *K);
+
+/* hs_zplan_set_coeff6 -- K, K_z and K_zz at the nodes l = 0..Nz+1 (host arrays
+ * of Nz + 2 (re, im) pairs each, copied).  Order 6: the rows of Section 3.4
+ * evaluated in complex arithmetic (their coefficients are polynomials in K:
+ * K^2 and K_z K terms), and the right-hand side's K terms
+ * h^2 (-h^2 K_l f / 20 + h^3 K_z,l (f_{l+1} - f_{l-1}) / 120) (eq. scheme6 with
+ * complex K).  Orders 2 and 4 read K only (K_z, K_zz may be NULL).
+ * Errors: HS_ERR_INVALID_ARG (NULL where needed, non-finite). */
+hs_status hs_zplan_set_coeff6(hs_zplan_t plan, const double *K, const double *Kz,
+                              const double *Kzz);
 
 /* hs_zplan_set_faces -- kind (HS_ZFACE_DIRICHLET / HS_ZFACE_ROBIN, eq. bc) of
  * the z-lo and z-hi faces; alpha, beta: host (re, im) pairs, read for Robin faces only
@@ -702,6 +715,19 @@ hs_status hs_zplan_set_faces(hs_zplan_t plan, int lo_kind, const double *alpha_l
 hs_status hs_zsolve_ex(hs_zplan_t plan, const double *f, const double *g_lo, const double *g_hi,
                        const double *const *side, double *u, void *stream);
 
+/* hs_zsolve_full -- hs_zsolve_ex with the face data of the 6th-order
+ * right-hand side: fnn[0..5] are the normal second derivatives f_nn on the
+ * x-lo, x-hi ([2][Nz+2][Ny+2]), y-lo, y-hi ([2][Nz+2][Nx+2]) and z-lo, z-hi
+ * ([2][Ny+2][Nx+2]) faces, planar complex device arrays on the face node grids
+ * (NULL entries, or fnn = NULL, are 0).  They enter the ghost nodes one step
+ * beyond a face, f_{-1} = 2 f_0 - f_1 + h^2 (f_nn)_face, that the R6 operator's
+ * second neighbours reach (eq. scheme6; the paper's cited compact closure is
+ * replaced by this explicit one).  Orders 2 and 4 ignore fnn.
+ * Errors: as hs_zsolve_ex. */
+hs_status hs_zsolve_full(hs_zplan_t plan, const double *f, const double *g_lo,
+                         const double *g_hi, const double *const *side,
+                         const double *const *fnn, double *u, void *stream);
+
 /* hs_zplan_set_sides -- kind of the x and y side axes (Section 1; default
  * Dirichlet): HS_SIDE_DIRICHLET (u = 0 on both faces, nodes 1..N unknown),
  * HS_SIDE_NEUMANN (u_n = g on both faces, nodes 0..N+1, cosine transform DCT-I),
@@ -710,11 +736,13 @@ hs_status hs_zsolve_ex(hs_zplan_t plan, const double *f, const double *g_lo, con
  * the last two take the quarter-wave transforms (modes of angle
  * (2p - 1) pi / (2 (N + 1)), p = 1..N+1), computed as the sine transform of the
  * line extended evenly about its Neumann node to 2N + 1 points (an internal
- * plan: about twice the x or y work array).  A Neumann axis needs N + 1, a
- * mixed axis 2 (N + 1), with a compiled transform (in {32, 64, 96, 128, 192,
- * 256, 384, 512, 768, 1024}).  The unknown grid is nx = Nx, Nx + 2 or Nx + 1
- * nodes by the kind, and likewise ny.
- * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED, HS_ERR_OOM. */
+ * plan: about twice the x or y work array).  N + 1 (Neumann) or 2 (N + 1)
+ * (mixed) in {32, 64, 96, 128, 192, 256, 384, 512, 768, 1024} run the compiled
+ * FFT tiles; other lengths run runtime-sized transforms (the cosine transform
+ * by direct sums, O(N^2) per line, lines of at most about 3000 nodes).  The
+ * unknown grid is nx = Nx, Nx + 2 or Nx + 1 nodes by the kind, and likewise ny.
+ * Errors: HS_ERR_INVALID_ARG (kind), HS_ERR_UNSUPPORTED (no transform for the
+ * length), HS_ERR_OOM; on error the previous kinds stay in effect. */
 hs_status hs_zplan_set_sides(hs_zplan_t plan, int x_kind, int y_kind);
 
 /* hs_zsolve -- one solve (Section 3.6 with complex rows) on `stream`

@@ -64,7 +64,7 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_precond_create", "hs_precond_apply", "hs_precond_solve", "hs_precond_destroy",
             "hs_batch_workspace_bytes", "hs_batch_destroy",
             "hs_zplan", "hs_zplan_set_coeff", "hs_zplan_set_faces", "hs_zplan_set_sides",
-            "hs_zsolve", "hs_zsolve_ex", "hs_set_coeff_fn", "hs_zplan_set_stage_timing",
+            "hs_zsolve", "hs_zsolve_ex", "hs_zsolve_full", "hs_zplan_set_coeff6", "hs_set_coeff_fn", "hs_zplan_set_stage_timing",
             "hs_zplan_stage_times",
             "hs_zplan_workspace_bytes", "hs_zplan_last_error", "hs_zplan_destroy")
 HS_STATIC_MAX_NZ = 8192
@@ -209,6 +209,10 @@ def load(path: Optional[str] = None):
     lib.hs_zplan_set_sides.restype = ci
     lib.hs_zsolve_ex.argtypes = [vp, vp, vp, vp, ctypes.POINTER(vp), vp, vp]
     lib.hs_zsolve_ex.restype = ci
+    lib.hs_zsolve_full.argtypes = [vp, vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]
+    lib.hs_zsolve_full.restype = ci
+    lib.hs_zplan_set_coeff6.argtypes = [vp, dp, dp, dp]
+    lib.hs_zplan_set_coeff6.restype = ci
     lib.hs_zsolve.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.hs_zsolve.restype = ci
     lib.hs_zplan_workspace_bytes.argtypes = [vp]
@@ -697,6 +701,20 @@ class ZSolver:
         arr = (ctypes.c_double * buf.size)(*buf.tolist())
         return self._err(load().hs_zplan_set_coeff(self.plan, arr), "hs_zplan_set_coeff")
 
+    def set_coeff6(self, K, Kz, Kzz):
+        """K, K_z, K_zz at the Nz + 2 nodes (order 6; orders 2 and 4 read K only)."""
+        import numpy as np
+
+        def arr(v):
+            v = np.asarray(v, dtype=np.complex128).ravel()
+            if v.size != self.shape[2] + 2:
+                raise ValueError(f"coefficients must hold Nz + 2 = {self.shape[2] + 2} values")
+            buf = np.ascontiguousarray(np.stack([v.real, v.imag], axis=-1).ravel())
+            return (ctypes.c_double * buf.size)(*buf.tolist())
+
+        return self._err(load().hs_zplan_set_coeff6(self.plan, arr(K), arr(Kz), arr(Kzz)),
+                         "hs_zplan_set_coeff6")
+
     def set_faces(self, lo_kind, alpha_lo=1.0, beta_lo=0.0, hi_kind=HS_ZFACE_DIRICHLET,
                   alpha_hi=1.0, beta_hi=0.0):
         return self._err(load().hs_zplan_set_faces(self.plan, int(lo_kind), _pair(alpha_lo),
@@ -707,12 +725,20 @@ class ZSolver:
         return self._err(load().hs_zplan_set_sides(self.plan, int(x_kind), int(y_kind)),
                          "hs_zplan_set_sides")
 
-    def solve(self, f, u, g_lo=None, g_hi=None, stream=None, side_data=None):
+    def solve(self, f, u, g_lo=None, g_hi=None, stream=None, side_data=None, fnn=None):
         """side_data: u_n on the (x-lo, x-hi, y-lo, y-hi) faces, planar complex
         [2][Nz+2][Ny+2] (x-faces) / [2][Nz+2][Nx+2] (y-faces); None entries = 0.
         Only Neumann faces take data (both faces of HS_SIDE_NEUMANN, the high face
-        of HS_SIDE_DN, the low face of HS_SIDE_ND)."""
-        self._keep = (f, u, g_lo, g_hi, side_data)
+        of HS_SIDE_DN, the low face of HS_SIDE_ND).  fnn (order 6): f_nn on the six
+        faces, planar complex [2][Nz+2][Ny+2] (x), [2][Nz+2][Nx+2] (y),
+        [2][Ny+2][Nx+2] (z); None entries = 0."""
+        self._keep = (f, u, g_lo, g_hi, side_data, fnn)
+        if fnn is not None:
+            sd = None if side_data is None else (ctypes.c_void_p * 4)(*[_ptr(a) for a in side_data])
+            fa = (ctypes.c_void_p * 6)(*[_ptr(a) for a in fnn])
+            return self._err(load().hs_zsolve_full(self.plan, _ptr(f), _ptr(g_lo), _ptr(g_hi), sd,
+                                                   fa, _ptr(u), _stream_ptr(stream)),
+                             "hs_zsolve_full")
         if side_data is None:
             return self._err(load().hs_zsolve(self.plan, _ptr(f), _ptr(g_lo), _ptr(g_hi),
                                               _ptr(u), _stream_ptr(stream)), "hs_zsolve")

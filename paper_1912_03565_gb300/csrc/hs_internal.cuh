@@ -200,6 +200,8 @@ extern "C" hs_status hs_plan_ex(hs_plan_t *out, int Nx, int Ny, int Nz, double L
 // complex exp(-2 pi i k / M), half: M + 1 complex (cos, sin)(pi k / M).  axis X:
 // nrows contiguous rows; axis Y: the nx columns of nplanes planes [M + 1][nx].
 // HS_ERR_UNSUPPORTED unless M has a compiled FFT (hs_dst_fast_size).
+hs_status hs_launch_dct_generic(int axis, int M, const double *in, double *out, const void *half,
+                                long nrows, int nx, int nplanes, double scale, cudaStream_t s);
 hs_status hs_launch_dct(int axis, int M, const double *in, double *out, const void *roots,
                         const void *half, long nrows, int nx, int nplanes, double scale,
                         cudaStream_t s);

@@ -1,10 +1,15 @@
-// Complex k(z) and Robin z-faces on the FP64 path (orders 2 and 4, Helmholtz).
+// Complex k(z) and Robin z-faces on the FP64 path (orders 2, 4 and 6, Helmholtz).
 //
 // Section 1's general problem: K = k^2 complex and depending on z only, u = 0
 // on the side faces, each z-face Dirichlet (u = g) or Robin (alpha u_z + beta u
 // = g, complex alpha, beta).  Interior rows l = 1..Nz are the compact rows of
 // Sections 3.2 / 3.3 with complex K; every coefficient is affine in K, so the
-// complex table is the real table at Re K plus i times its K-part at Im K.  A
+// complex table is the real table at Re K plus i times its K-part at Im K.  The
+// 6th-order rows (Section 3.4, uniform h, Dirichlet side faces) are polynomials
+// in K, K_z and K_zz and are evaluated in complex arithmetic; their right-hand
+// side is R6 of eq. scheme6 (K-free part on Re f and Im f, with ghosts
+// 2 f_0 - f_1 + h^2 (f_nn)_face one step beyond a face) plus the complex
+// h^2 (-h^2 K f / 20 + h^3 K_z (f_{l+1} - f_{l-1}) / 120).  A
 // Robin face's plane is unknown and its row is the second-order 7-point scheme
 // with the outside plane eliminated by the central difference of the face
 // condition (the paper leaves the compact closure to a cited work):
@@ -50,6 +55,8 @@ struct hs_zplan_s {
     int kind[2];               // HS_ZFACE_* of the lo and hi faces
     double2 alpha[2], beta[2];
     std::vector<double2> K;    // Nz + 2 nodes
+    std::vector<double2> Kz, Kzz;   // order 6: K_z, K_zz at the nodes
+    double2 *d_kk;             // order 6: [2][Nz + 2] K and K_z for the right-hand side
     int have_coeff;
     int Nu, l0;                // unknown planes l0 .. l0 + Nu - 1
     int side[2];               // HS_SIDE_* of the x and y axes
@@ -130,6 +137,33 @@ void real_row(int order, double Rzx, double Rzy, double hz2, double Km, double K
     }
 }
 
+// Complex coefficients of a 6th-order interior row (Section 3.4, uniform h): the
+// printed coefficients are polynomials in K (K_{l-1}, K_l, K_{l+1}), K_z and K_zz,
+// so they are evaluated in complex arithmetic as printed; blk[nu * 4 + m].
+void six_row(double h, double2 Km, double2 K, double2 Kp, double2 Kz, double2 Kzz,
+             double2 *blk) {
+    const double h2 = h * h, h3 = h2 * h, h4 = h2 * h2;
+    auto lin = [](double c, double s, double2 x) {   // c + s x
+        return make_double2(c + s * x.x, s * x.y);
+    };
+    for (int k = 0; k < 12; ++k) blk[k] = make_double2(0.0, 0.0);
+    blk[ZLOW * 4 + ZA] = blk[ZUPP * 4 + ZA] = make_double2(1.0 / 30.0, 0.0);
+    // 1/10 + h^2 K_{l-+1} / 90 -+ h^3 K_z / 120
+    const double2 bl = csub(lin(0.1, h2 / 90.0, Km), cscale(h3 / 120.0, Kz));
+    const double2 bu = cadd(lin(0.1, h2 / 90.0, Kp), cscale(h3 / 120.0, Kz));
+    blk[ZLOW * 4 + ZB] = blk[ZLOW * 4 + ZC] = bl;
+    blk[ZUPP * 4 + ZB] = blk[ZUPP * 4 + ZC] = bu;
+    // 7/15 - h^2 K_{l-+1} / 90 -+ (h^3 K_z / 20) (1/3 + h^2 K_{l-+1} / 6)
+    const double2 tz = cscale(h3 / 20.0, Kz);
+    blk[ZLOW * 4 + ZD] = csub(lin(7.0 / 15.0, -h2 / 90.0, Km), cmul(tz, lin(1.0 / 3.0, h2 / 6.0, Km)));
+    blk[ZUPP * 4 + ZD] = cadd(lin(7.0 / 15.0, -h2 / 90.0, Kp), cmul(tz, lin(1.0 / 3.0, h2 / 6.0, Kp)));
+    blk[ZMID * 4 + ZA] = lin(0.1, h2 / 90.0, K);
+    blk[ZMID * 4 + ZB] = blk[ZMID * 4 + ZC] = lin(7.0 / 15.0, -h2 / 90.0, K);
+    // -64/15 + 14 h^2 K / 15 - h^4 K^2 / 20 + h^4 K_zz / 20
+    blk[ZMID * 4 + ZD] = cadd(csub(lin(-64.0 / 15.0, 14.0 * h2 / 15.0, K), cscale(h4 / 20.0, cmul(K, K))),
+                              cscale(h4 / 20.0, Kzz));
+}
+
 // Builds the complex rows of the unknown planes and uploads them.
 hs_status build_rows(hs_zplan_s *Z) {
     if (!Z->layout_ok) return HS_OK;   // built once a set-up call completes the layout
@@ -150,6 +184,10 @@ hs_status build_rows(hs_zplan_s *Z) {
                                                   side * 2.0 * Z->hz * ba.x,
                                               hz2 * Z->K[l].y - side * 2.0 * Z->hz * ba.y);
             blk[(side < 0 ? ZUPP : ZLOW) * 4 + ZD] = make_double2(2.0, 0.0);
+            continue;
+        }
+        if (Z->order == 6) {
+            six_row(Z->hz, Z->K[l - 1], Z->K[l], Z->K[l + 1], Z->Kz[l], Z->Kzz[l], blk);
             continue;
         }
         double re[3][4], im[3][4], z0[3][4];
@@ -306,7 +344,37 @@ struct ZRhsArgs {
     double hx, hy;
     const double2 *rows;    // [Nu][3][4]
     double *W;              // [2][Nu][ny][nx]
+    const double *fnn[6];   // order 6: f_nn on the x-lo, x-hi ([2][Nz+2][Ny+2]), y-lo, y-hi
+                            // ([2][Nz+2][Nx+2]), z-lo, z-hi ([2][Ny+2][Nx+2]) faces, or NULL
+    const double2 *kk;      // order 6: [2][Nz+2] K and K_z at the nodes
 };
+
+// Order 6: f (component comp) at node (i, j, l) of the node grid, or one step
+// beyond a face the ghost 2 f_0 - f_1 + h^2 (f_nn)_face (the R6 operator's
+// second neighbours; one coordinate at a time leaves the grid).
+__device__ inline double f6_node(const ZRhsArgs &a, int comp, int i, int j, int l) {
+    const size_t sy = (size_t)a.Nx + 2, sz = sy * (a.Ny + 2);
+    const double *fc = a.f + (size_t)comp * sz * (a.Nz + 2);
+    int face = -1, i0 = i, j0 = j, l0 = l, di = 0, dj = 0, dl = 0;
+    if (i < 0) { face = 0; i0 = 0; di = 1; }
+    else if (i > a.Nx + 1) { face = 1; i0 = a.Nx + 1; di = -1; }
+    else if (j < 0) { face = 2; j0 = 0; dj = 1; }
+    else if (j > a.Ny + 1) { face = 3; j0 = a.Ny + 1; dj = -1; }
+    else if (l < 0) { face = 4; l0 = 0; dl = 1; }
+    else if (l > a.Nz + 1) { face = 5; l0 = a.Nz + 1; dl = -1; }
+    if (face < 0) return fc[(size_t)l * sz + (size_t)j * sy + i];
+    double g = 2.0 * fc[(size_t)l0 * sz + (size_t)j0 * sy + i0] -
+               fc[(size_t)(l0 + dl) * sz + (size_t)(j0 + dj) * sy + (i0 + di)];
+    const double *d = a.fnn[face];
+    if (d) {
+        size_t k;
+        if (face < 2) k = (size_t)comp * (a.Nz + 2) * (a.Ny + 2) + (size_t)l0 * (a.Ny + 2) + j0;
+        else if (face < 4) k = (size_t)comp * (a.Nz + 2) * (a.Nx + 2) + (size_t)l0 * (a.Nx + 2) + i0;
+        else k = (size_t)comp * (a.Ny + 2) * (a.Nx + 2) + (size_t)j0 * (a.Nx + 2) + i0;
+        g += a.hz * a.hz * d[k];
+    }
+    return g;
+}
 
 // Index one node beyond [0, n - 1] of a Neumann axis: the even reflection.
 __device__ inline int reflect(int i, int n) { return i < 0 ? -i : (i >= n ? 2 * (n - 1) - i : i); }
@@ -377,8 +445,35 @@ __global__ void zrhs_kernel(ZRhsArgs a) {
                                   f[pl + (size_t)jp * sy + ii] + f[c - sz] + f[c + sz]) -
                                  6.0 * f[c];
                 v += D / 12.0;
+            } else if (a.order == 6 && l >= 1 && l <= a.Nz) {
+                // K-free part of R6 / h^2: 67/120 f + (40 S1 - 3 S2 + 8 E) / 720 with
+                // S1 the 6 face neighbours, S2 the 6 second neighbours (ghosts beyond
+                // a face), E the 12 edge mid-points
+                const size_t pl = (size_t)l * sz;
+                const double S1 = f[rowc + ii - 1] + f[rowc + ii + 1] + f[c - sy] + f[c + sy] +
+                                  f[c - sz] + f[c + sz];
+                const double S2 = f6_node(a, comp, ii - 2, jj, l) + f6_node(a, comp, ii + 2, jj, l) +
+                                  f6_node(a, comp, ii, jj - 2, l) + f6_node(a, comp, ii, jj + 2, l) +
+                                  f6_node(a, comp, ii, jj, l - 2) + f6_node(a, comp, ii, jj, l + 2);
+                double E = 0.0;
+                for (int s1 = -1; s1 <= 1; s1 += 2)
+                    for (int s2 = -1; s2 <= 1; s2 += 2) {
+                        E += f[pl + (size_t)(jj + s1) * sy + (ii + s2)];   // x-y edges
+                        E += f[c + s1 * (long)sz + s2];                     // x-z edges
+                        E += f[c + s1 * (long)sz + s2 * (long)sy];          // y-z edges
+                    }
+                v = (67.0 / 120.0) * f[c] + (40.0 * S1 - 3.0 * S2 + 8.0 * E) / 720.0;
             }
             if (comp == 0) F.x = hz2 * v; else F.y = hz2 * v;
+        }
+        if (a.order == 6 && l >= 1 && l <= a.Nz) {
+            // the complex K terms h^2 (-h^2 K_l f / 20 + h^3 K_z,l (f_{l+1} - f_{l-1}) / 120)
+            const size_t nn = nodes;
+            const double2 fcv = make_double2(a.f[c], a.f[nn + c]);
+            const double2 dz = make_double2(a.f[c + sz] - a.f[c - sz], a.f[nn + c + sz] - a.f[nn + c - sz]);
+            const double2 Kc = a.kk[l], Kzc = a.kk[a.Nz + 2 + l];
+            F = cadd(F, cscale(-hz2 * hz2 / 20.0, cmul(Kc, fcv)));
+            F = cadd(F, cscale(hz2 * hz2 * a.hz / 120.0, cmul(Kzc, dz)));
         }
         if (l == 0) {
             F = cadd(F, cmul(a.ga_lo, face_val(a, a.g_lo, j, i)));
@@ -610,7 +705,11 @@ hs_status hs_zplan(hs_zplan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly
     if (!out) return HS_ERR_INVALID_ARG;
     *out = nullptr;
     if (Nx < 1 || Ny < 1 || Nz < 1 || !(Lx > 0) || !(Ly > 0) || !(Lz > 0)) return HS_ERR_INVALID_ARG;
-    if (order != 2 && order != 4) return HS_ERR_INVALID_ARG;
+    if (order != 2 && order != 4 && order != 6) return HS_ERR_INVALID_ARG;
+    if (order == 6) {   // Section 3.4's rows assume one step in every direction
+        const double hx = Lx / (Nx + 1), hy = Ly / (Ny + 1), hz = Lz / (Nz + 1);
+        if (fabs(hx - hz) > 1e-12 * hz || fabs(hy - hz) > 1e-12 * hz) return HS_ERR_INVALID_ARG;
+    }
     if (2.0 * (Nz + 2) * (double)(Nx + 2) * (Ny + 2) > 4.0e9) return HS_ERR_UNSUPPORTED;
     hs_zplan_s *Z = new (std::nothrow) hs_zplan_s();
     if (!Z) return HS_ERR_OOM;
@@ -630,16 +729,42 @@ hs_status hs_zplan(hs_zplan_t *out, int Nx, int Ny, int Nz, double Lx, double Ly
     return HS_OK;
 }
 
-hs_status hs_zplan_set_coeff(hs_zplan_t Z, const double *K) {
-    if (!Z || !K) return HS_ERR_INVALID_ARG;
-    std::vector<double2> k(Z->Nz + 2);
-    for (int l = 0; l < Z->Nz + 2; ++l) {
+hs_status hs_zplan_set_coeff6(hs_zplan_t Z, const double *K, const double *Kz,
+                              const double *Kzz) {
+    if (!Z || !K || (Z->order == 6 && (!Kz || !Kzz))) return HS_ERR_INVALID_ARG;
+    const int n = Z->Nz + 2;
+    std::vector<double2> k(n), kz(n, make_double2(0.0, 0.0)), kzz(n, make_double2(0.0, 0.0));
+    for (int l = 0; l < n; ++l) {
         if (!isfinite(K[2 * l]) || !isfinite(K[2 * l + 1])) return HS_ERR_INVALID_ARG;
         k[l] = make_double2(K[2 * l], K[2 * l + 1]);
+        if (Z->order == 6) {
+            if (!isfinite(Kz[2 * l]) || !isfinite(Kz[2 * l + 1]) || !isfinite(Kzz[2 * l]) ||
+                !isfinite(Kzz[2 * l + 1]))
+                return HS_ERR_INVALID_ARG;
+            kz[l] = make_double2(Kz[2 * l], Kz[2 * l + 1]);
+            kzz[l] = make_double2(Kzz[2 * l], Kzz[2 * l + 1]);
+        }
+    }
+    if (Z->order == 6) {   // K and K_z for the right-hand side's K terms
+        std::vector<double2> kk(2 * (size_t)n);
+        for (int l = 0; l < n; ++l) {
+            kk[l] = k[l];
+            kk[n + l] = kz[l];
+        }
+        if (!Z->d_kk) ZCK(Z, cudaMalloc(&Z->d_kk, kk.size() * sizeof(double2)));
+        ZCK(Z, cudaMemcpy(Z->d_kk, kk.data(), kk.size() * sizeof(double2),
+                          cudaMemcpyHostToDevice));
     }
     Z->K = k;
+    Z->Kz = kz;
+    Z->Kzz = kzz;
     Z->have_coeff = 1;
     return build_rows(Z);
+}
+
+hs_status hs_zplan_set_coeff(hs_zplan_t Z, const double *K) {
+    if (!Z || !K || Z->order == 6) return HS_ERR_INVALID_ARG;   // order 6 needs K_z, K_zz
+    return hs_zplan_set_coeff6(Z, K, nullptr, nullptr);
 }
 
 hs_status hs_zplan_set_faces(hs_zplan_t Z, int lo_kind, const double *alpha_lo,
@@ -674,18 +799,25 @@ hs_status hs_zplan_set_faces(hs_zplan_t Z, int lo_kind, const double *alpha_lo,
 
 hs_status hs_zplan_set_sides(hs_zplan_t Z, int x_kind, int y_kind) {
     if (!Z) return HS_ERR_INVALID_ARG;
-    const int k[2] = {x_kind, y_kind}, N[2] = {Z->Nx, Z->Ny};
-    for (int a = 0; a < 2; ++a) {
+    const int k[2] = {x_kind, y_kind};
+    for (int a = 0; a < 2; ++a)
         if (k[a] < HS_SIDE_DIRICHLET || k[a] > HS_SIDE_ND) return HS_ERR_INVALID_ARG;
-        if (k[a] == HS_SIDE_NEUMANN && !hs_dst_fast_size(N[a] + 1)) return HS_ERR_UNSUPPORTED;
-        // one face of each kind: the sine transform of the lines extended to 2N + 1
-        if ((k[a] == HS_SIDE_DN || k[a] == HS_SIDE_ND) && !hs_dst_fast_size(2 * (N[a] + 1)))
-            return HS_ERR_UNSUPPORTED;
-    }
+    // the 6th-order right-hand side's ghosts are defined for Dirichlet side faces
+    if (Z->order == 6 && (x_kind != HS_SIDE_DIRICHLET || y_kind != HS_SIDE_DIRICHLET))
+        return HS_ERR_UNSUPPORTED;
+    // lengths without a compiled FFT take the runtime-sized transforms (direct sums
+    // for a cosine axis, the sine plan's own fallback for the extended lines of a
+    // mixed axis); a layout that cannot be built leaves the previous kinds in place
+    const int old[2] = {Z->side[0], Z->side[1]};
     Z->side[0] = x_kind;
     Z->side[1] = y_kind;
     const hs_status st = layout(Z);
-    if (st != HS_OK) return st;
+    if (st != HS_OK) {
+        Z->side[0] = old[0];
+        Z->side[1] = old[1];
+        if (layout(Z) == HS_OK && Z->have_coeff) (void)build_rows(Z);
+        return st;
+    }
     return Z->have_coeff ? build_rows(Z) : HS_OK;
 }
 
@@ -696,6 +828,12 @@ hs_status hs_zsolve(hs_zplan_t Z, const double *f, const double *g_lo, const dou
 
 hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const double *g_hi,
                        const double *const *side, double *u, void *stream) {
+    return hs_zsolve_full(Z, f, g_lo, g_hi, side, nullptr, u, stream);
+}
+
+hs_status hs_zsolve_full(hs_zplan_t Z, const double *f, const double *g_lo, const double *g_hi,
+                         const double *const *side, const double *const *fnn, double *u,
+                         void *stream) {
     HsRange range("hs_zsolve");
     if (!Z || !f || !u) return HS_ERR_INVALID_ARG;
     if (!Z->layout_ok) {
@@ -715,6 +853,11 @@ hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const 
                          (kind == HS_SIDE_DN && k % 2 == 1);
         if (!neu || !device_ptr(side[k])) return HS_ERR_INVALID_ARG;
         sd[k] = side[k];
+    }
+    const double *fd[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; fnn && Z->order == 6 && k < 6; ++k) {
+        if (fnn[k] && !device_ptr(fnn[k])) return HS_ERR_INVALID_ARG;
+        fd[k] = fnn[k];
     }
     Z->last_error[0] = 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -737,6 +880,8 @@ hs_status hs_zsolve_ex(hs_zplan_t Z, const double *f, const double *g_lo, const 
     a.ga_hi = cscale(2.0 * Z->hz, cdiv_host(make_double2(1.0, 0.0), Z->alpha[1]));
     a.f = f; a.g_lo = g_lo; a.g_hi = g_hi; a.rows = Z->d_rows; a.W = W;
     for (int k = 0; k < 4; ++k) a.side[k] = sd[k];
+    for (int k = 0; k < 6; ++k) a.fnn[k] = fd[k];
+    a.kk = Z->d_kk;
     a.hx = Z->hx;
     a.hy = Z->hy;
     const unsigned blocks = (unsigned)((nu + 255) / 256 < 152 * 16 ? (nu + 255) / 256 : 152 * 16);
@@ -880,6 +1025,7 @@ void hs_zplan_destroy(hs_zplan_t Z) {
     if (Z->T) hs_destroy(Z->T);
     for (int a = 0; a < 2; ++a)
         if (Z->TQ[a]) hs_destroy(Z->TQ[a]);
+    if (Z->d_kk) cudaFree(Z->d_kk);
     if (Z->d_rows) cudaFree(Z->d_rows);
     if (Z->d_cos) cudaFree(Z->d_cos);
     if (Z->d_fac) cudaFree(Z->d_fac);

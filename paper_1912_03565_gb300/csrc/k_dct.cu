@@ -1,4 +1,5 @@
-// DCT-I of lines of M + 1 nodes (FP64): the transform of a side axis with
+// DCT-I of lines of M + 1 nodes (FP64; compiled FFT lengths, direct sums for the
+// others): the transform of a side axis with
 // u_n = 0 on both faces, whose modes cos(pi p i / M), p = 0..M, diagonalise
 // the reflected second difference (Section 3.6's separation with cosines in
 // place of sines).
@@ -139,7 +140,93 @@ hs_status launch_dct_m(int axis, const double *in, double *out, const double2 *r
     return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
 }
 
+// Runtime-sized DCT-I (any M, for the lengths without a compiled FFT): direct
+// sums X_k = sum_i w_i x_i cos(pi k i / M), w_0 = w_M = 1/2, with the argument
+// reduced exactly (k i mod 2M) into the table of cos(pi m / M), m = 0..M.  One
+// CTA owns S whole lines, read into shared memory before any output is written
+// (so the transform may run in place); O(M^2) FP64 operations per line.
+constexpr int GDCT_S = 8;
+
+template <int AXIS>
+__global__ void __launch_bounds__(256)
+dct_generic_kernel(const double *in, double *out, const double2 *half_g, int M, long nrows,
+                   int nx, double scale) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = M + 1;
+    double *cs = reinterpret_cast<double *>(smem_raw);   // [M + 1]: cos(pi m / M)
+    double *x = cs + L;                                   // [GDCT_S][L], weights applied
+    for (int t = threadIdx.x; t < L; t += blockDim.x) cs[t] = half_g[t].x;
+    size_t base;
+    int nvalid;
+    if (AXIS == HS_AXIS_X) {
+        const long r0 = (long)blockIdx.x * GDCT_S;
+        nvalid = (int)min((long)GDCT_S, nrows - r0);
+        base = (size_t)r0 * L;
+        for (int e = threadIdx.x; e < nvalid * L; e += blockDim.x) {
+            const int s = e / L, i = e - s * L;
+            x[s * L + i] = (i == 0 || i == M ? 0.5 : 1.0) * in[base + e];
+        }
+    } else {
+        const int p0 = blockIdx.x * GDCT_S;
+        nvalid = min(GDCT_S, nx - p0);
+        base = (size_t)blockIdx.y * L * nx + p0;
+        for (int e = threadIdx.x; e < GDCT_S * L; e += blockDim.x) {
+            const int i = e / GDCT_S, s = e - i * GDCT_S;
+            if (s < nvalid)
+                x[s * L + i] = (i == 0 || i == M ? 0.5 : 1.0) * in[base + (size_t)i * nx + s];
+        }
+    }
+    __syncthreads();
+    const int twoM = 2 * M;
+    for (int e = threadIdx.x; e < nvalid * L; e += blockDim.x) {
+        int s, k;
+        if (AXIS == HS_AXIS_X) {
+            s = e / L;
+            k = e - s * L;
+        } else {   // consecutive threads take consecutive columns: coalesced stores
+            k = e / nvalid;
+            s = e - k * nvalid;
+        }
+        const double *xs = x + s * L;
+        double acc = 0.0;
+        int m = 0;   // k i mod 2M
+        for (int i = 0; i < L; ++i) {
+            acc = fma(xs[i], cs[m <= M ? m : twoM - m], acc);
+            m += k;
+            if (m >= twoM) m -= twoM;
+        }
+        if (AXIS == HS_AXIS_X)
+            out[base + (size_t)s * L + k] = scale * acc;
+        else
+            out[base + (size_t)k * nx + s] = scale * acc;
+    }
+}
+
 }  // namespace
+
+// DCT-I for a length without a compiled FFT (direct sums; see dct_generic_kernel).
+hs_status hs_launch_dct_generic(int axis, int M, const double *in, double *out, const void *half,
+                                long nrows, int nx, int nplanes, double scale, cudaStream_t s) {
+    if (M < 1) return HS_ERR_INVALID_ARG;
+    const size_t smem = sizeof(double) * ((size_t)(M + 1) * (1 + GDCT_S));
+    if (smem > 227 * 1024) return HS_ERR_UNSUPPORTED;
+    const double2 *h = static_cast<const double2 *>(half);
+    if (axis == HS_AXIS_X) {
+        if (cudaFuncSetAttribute(dct_generic_kernel<HS_AXIS_X>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return HS_ERR_CUDA;
+        dct_generic_kernel<HS_AXIS_X><<<(unsigned)((nrows + GDCT_S - 1) / GDCT_S), 256, smem, s>>>(
+            in, out, h, M, nrows, nx, scale);
+    } else {
+        if (cudaFuncSetAttribute(dct_generic_kernel<HS_AXIS_Y>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return HS_ERR_CUDA;
+        dct_generic_kernel<HS_AXIS_Y>
+            <<<dim3((unsigned)((nx + GDCT_S - 1) / GDCT_S), (unsigned)nplanes, 1), 256, smem, s>>>(
+                in, out, h, M, nrows, nx, scale);
+    }
+    return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ERR_CUDA;
+}
 
 hs_status hs_launch_dct(int axis, int M, const double *in, double *out, const void *roots,
                         const void *half, long nrows, int nx, int nplanes, double scale,
@@ -158,7 +245,7 @@ hs_status hs_launch_dct(int axis, int M, const double *in, double *out, const vo
         case 512: HS_D(512, 16, 16, 2);
         case 768: HS_D(768, 16, 16, 3);
         case 1024: HS_D(1024, 16, 16, 4);
-        default: return HS_ERR_UNSUPPORTED;
+        default: return hs_launch_dct_generic(axis, M, in, out, half, nrows, nx, nplanes, scale, s);
     }
 #undef HS_D
 }

@@ -80,7 +80,8 @@ def test_complex_plan_and_host_io_argument_validation(lib):
     h = ctypes.c_void_p()
     assert lib.hs_zplan(None, 4, 4, 4, 1.0, 1.0, 1.0, 4) == H.HS_ERR_INVALID_ARG
     assert lib.hs_zplan(ctypes.byref(h), 0, 4, 4, 1.0, 1.0, 1.0, 4) == H.HS_ERR_INVALID_ARG
-    assert lib.hs_zplan(ctypes.byref(h), 4, 4, 4, 1.0, 1.0, 1.0, 6) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_zplan(ctypes.byref(h), 4, 4, 4, 1.0, 1.0, 1.0, 5) == H.HS_ERR_INVALID_ARG
+    assert lib.hs_zplan(ctypes.byref(h), 4, 4, 4, 1.0, 1.0, 1.3, 6) == H.HS_ERR_INVALID_ARG
     assert lib.hs_zplan(ctypes.byref(h), 4, 4, 4, 1.0, -1.0, 1.0, 4) == H.HS_ERR_INVALID_ARG
     assert h.value is None
     assert lib.hs_zplan_set_coeff(None, None) == H.HS_ERR_INVALID_ARG

@@ -132,7 +132,10 @@ def test_complex_255_robin_matches_oracle():
 def test_errors():
     torch = _torch()
     with pytest.raises(H.HsError) as e:
-        H.ZSolver(8, 8, 8, 1.0, 1.0, 1.0, 6)
+        H.ZSolver(8, 8, 8, 1.0, 1.0, 1.0, 5)
+    assert e.value.status == H.HS_ERR_INVALID_ARG
+    with pytest.raises(H.HsError) as e:   # order 6 needs one step in every direction
+        H.ZSolver(8, 8, 8, 1.0, 1.0, 1.2, 6)
     assert e.value.status == H.HS_ERR_INVALID_ARG
     s = H.ZSolver(8, 7, 6, 1.0, 1.0, 1.0, 4)
     try:
@@ -205,22 +208,54 @@ def test_neumann_255():
     assert O.max_rel_diff(got, ref) <= TOL
 
 
-def test_neumann_unsupported_length():
+def test_side_kinds_and_invalid_kinds():
+    """Lengths without a compiled FFT are accepted (runtime-sized transforms); an
+    unknown kind is refused and leaves the previous kinds in effect."""
     s = H.ZSolver(30, 31, 5, 1.0, 1.0, 1.0, 4)
     try:
-        with pytest.raises(H.HsError) as e:
-            s.set_sides(H.HS_SIDE_NEUMANN, H.HS_SIDE_DIRICHLET)   # 31 points: no compiled FFT
-        assert e.value.status == H.HS_ERR_UNSUPPORTED
-        s.set_sides(H.HS_SIDE_DIRICHLET, H.HS_SIDE_NEUMANN)       # 32 points
-        with pytest.raises(H.HsError) as e:
-            s.set_sides(H.HS_SIDE_DN, H.HS_SIDE_DIRICHLET)   # extended line 62: none compiled
-        assert e.value.status == H.HS_ERR_UNSUPPORTED
-        s.set_sides(H.HS_SIDE_DIRICHLET, H.HS_SIDE_ND)        # extended line 64
+        s.set_sides(H.HS_SIDE_NEUMANN, H.HS_SIDE_DIRICHLET)   # 31 + 1 nodes: direct sums
+        s.set_sides(H.HS_SIDE_DN, H.HS_SIDE_ND)               # extended lines of 61 and 63
         with pytest.raises(H.HsError) as e:
             s.set_sides(4, 0)
         assert e.value.status == H.HS_ERR_INVALID_ARG
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("sides", [(NEU, DIRS), (DIRS, NEU), (NEU, NEU), (CX.SIDE_DN, NEU),
+                                   (NEU, CX.SIDE_ND), (CX.SIDE_ND, CX.SIDE_DN)])
+@pytest.mark.parametrize("shape", [(30, 20, 6), (21, 44, 5)])
+def test_runtime_sized_side_transforms(order, sides, shape):
+    """Side axes whose transform length has no compiled FFT: the cosine transform by
+    direct sums (N + 1 = 31, 21, 45, ...) and the quarter-wave transforms through the
+    runtime-sized sine transform of the extended line (2 (N + 1) = 62, 42, 90), with
+    face data on every Neumann face, against the oracle at the FP64 bar."""
+    torch = _torch()
+    L = (1.0, 0.8, 1.1)
+    Nx, Ny, Nz = shape
+    h, K, f, g_lo, g_hi = _neumann_case(shape, L, sides, 3 * sum(shape) + order)
+    rs = np.random.RandomState(order + sides[0])
+    cr = lambda *sh: rs.uniform(-1, 1, sh) + 1j * rs.uniform(-1, 1, sh)
+    neu = [sides[0] in (NEU, CX.SIDE_ND), sides[0] in (NEU, CX.SIDE_DN),
+           sides[1] in (NEU, CX.SIDE_ND), sides[1] in (NEU, CX.SIDE_DN)]
+    sd = [cr(Nz + 2, (Ny if k < 2 else Nx) + 2) if neu[k] else None for k in range(4)]
+    zf = CX.ZFaces(R, 1.0 + 0.5j, 2.0 - 1.0j, D)
+    ref, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi, sides, sd)
+    s = H.ZSolver(Nx, Ny, Nz, *L, order)
+    try:
+        s.set_coeff(K)
+        s.set_faces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
+        s.set_sides(*sides)
+        nx, ny = _nu(Nx, sides[0]), _nu(Ny, sides[1])
+        u = torch.full((2, Nz + 2, ny, nx), np.nan, dtype=torch.float64, device="cuda")
+        s.solve(_planar(torch, f), u, _planar(torch, g_lo), _planar(torch, g_hi),
+                side_data=[None if a is None else _planar(torch, a) for a in sd])
+        torch.cuda.synchronize()
+        uc = u.cpu().numpy()
+    finally:
+        s.close()
+    assert O.max_rel_diff(uc[0] + 1j * uc[1], ref) <= TOL
 
 
 @pytest.mark.parametrize("order", [2, 4])
@@ -352,3 +387,89 @@ def test_mixed_255():
     finally:
         s.close()
     assert O.max_rel_diff(uc[0] + 1j * uc[1], ref) <= TOL
+
+
+
+def _case6(shape, seed):
+    """Order 6 (uniform h): box ((N_a + 1) h); complex K(z) with its derivatives K_z,
+    K_zz; complex f and six face arrays f_nn."""
+    Nx, Ny, Nz = shape
+    rs = np.random.RandomState(seed)
+    hh = 1.0 / (max(shape) + 1)
+    L = tuple((n + 1) * hh for n in shape)
+    z = np.arange(Nz + 2) * hh
+    c = (30.0 + 5.0 * rs.uniform()) * (1.0 + 0.2j)
+    K = c * (1.0 + 0.5 * z + 0.3 * z * z)
+    Kz = c * (0.5 + 0.6 * z)
+    Kzz = c * 0.6 + 0.0 * z
+    cr = lambda *sh: rs.uniform(-1, 1, sh) + 1j * rs.uniform(-1, 1, sh)
+    f = cr(Nz + 2, Ny + 2, Nx + 2)
+    fnn = [cr(Nz + 2, Ny + 2), cr(Nz + 2, Ny + 2), cr(Nz + 2, Nx + 2), cr(Nz + 2, Nx + 2),
+           cr(Ny + 2, Nx + 2), cr(Ny + 2, Nx + 2)]
+    return (hh, hh, hh), L, K, Kz, Kzz, f, fnn, cr
+
+
+def _gpu6(shape, L, K, Kz, Kzz, zf, f, g_lo, g_hi, fnn):
+    torch = _torch()
+    Nx, Ny, Nz = shape
+    s = H.ZSolver(Nx, Ny, Nz, *L, 6)
+    try:
+        s.set_coeff6(K, Kz, Kzz)
+        s.set_faces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
+        u = torch.full((2, Nz + 2, Ny, Nx), np.nan, dtype=torch.float64, device="cuda")
+        s.solve(_planar(torch, f), u, _planar(torch, g_lo), _planar(torch, g_hi),
+                fnn=None if fnn is None else [None if a is None else _planar(torch, a) for a in fnn])
+        torch.cuda.synchronize()
+        uc = u.cpu().numpy()
+        return uc[0] + 1j * uc[1]
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("faces", [(R, R), (D, D), (R, D), (D, R)])
+@pytest.mark.parametrize("shape", [(15, 15, 15), (31, 23, 13), (9, 40, 27)])
+def test_order6_complex_matches_oracle(faces, shape):
+    """6th-order rows (Section 3.4) in complex arithmetic, R6 with the complex K terms
+    and f_nn ghosts on all six faces, Robin or Dirichlet z-faces: GPU vs oracle."""
+    h, L, K, Kz, Kzz, f, fnn, cr = _case6(shape, sum(shape) + 7 * faces[0] + faces[1])
+    Nx, Ny, Nz = shape
+    g_lo, g_hi = cr(Ny, Nx), cr(Ny, Nx)
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    ref, _ = CX.solve(6, h, K, zf, f, g_lo, g_hi, Kz=Kz, Kzz=Kzz, fnn=fnn)
+    got = _gpu6(shape, L, K, Kz, Kzz, zf, f, g_lo, g_hi, fnn)
+    assert O.max_rel_diff(got, ref) <= TOL
+
+
+def test_order6_complex_without_face_data_and_errors():
+    """fnn absent (zero face data) at 63 x 63 x 31 with Robin faces; the order-6 plan
+    refuses K without its derivatives and Neumann side faces."""
+    torch = _torch()
+    shape = (63, 63, 31)
+    h, L, K, Kz, Kzz, f, _, cr = _case6(shape, 5)
+    Nx, Ny, Nz = shape
+    g_lo, g_hi = cr(Ny, Nx), cr(Ny, Nx)
+    zf = CX.ZFaces(R, 1.0 + 0.5j, 3.0 - 1.0j, R, 1.0 + 0.5j, 3.0 - 1.0j)
+    ref, _ = CX.solve(6, h, K, zf, f, g_lo, g_hi, Kz=Kz, Kzz=Kzz)
+    got = _gpu6(shape, L, K, Kz, Kzz, zf, f, g_lo, g_hi, None)
+    assert O.max_rel_diff(got, ref) <= TOL
+    s = H.ZSolver(Nx, Ny, Nz, *L, 6)
+    try:
+        with pytest.raises(H.HsError) as e:
+            s.set_coeff(K)
+        assert e.value.status == H.HS_ERR_INVALID_ARG
+        with pytest.raises(H.HsError) as e:
+            s.set_sides(H.HS_SIDE_NEUMANN, H.HS_SIDE_DIRICHLET)
+        assert e.value.status == H.HS_ERR_UNSUPPORTED
+    finally:
+        s.close()
+
+
+def test_order6_complex_127():
+    """127^3, 6th order, Robin faces, face data on all six faces."""
+    shape = (127, 127, 127)
+    h, L, K, Kz, Kzz, f, fnn, cr = _case6(shape, 127)
+    g_lo, g_hi = cr(127, 127), cr(127, 127)
+    zf = CX.ZFaces(R, 1.0 + 0.5j, 3.0 - 1.0j, D)
+    ref, _ = CX.solve(6, h, K, zf, f, g_lo, g_hi, Kz=Kz, Kzz=Kzz, fnn=fnn)
+    got = _gpu6(shape, L, K, Kz, Kzz, zf, f, g_lo, g_hi, fnn)
+    assert O.max_rel_diff(got, ref) <= TOL
