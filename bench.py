@@ -66,9 +66,9 @@ NCU_COUNTS = {
         "dram_bytes": 267511808 + 205838592 + 267540480 + 210931200,
         "profile": "profiles/fp64_transforms_complex255.md"},
     ("zneumann255_o4", "transforms"): {
-        "kernel": "dct_kernel x + y (cosine tiles over 2 x 257 planes)",
-        "fp64_warp_inst": 31671646 + 32533116,
-        "dram_bytes": 271669504 + 211579648 + 271651072 + 215605760,
+        "kernel": "dct_half_kernel x + y (half-length FP64 cosine tiles over 2 x 257 planes)",
+        "fp64_warp_inst": 23326000 + 24684850,
+        "dram_bytes": 271667200 + 210036224 + 271682048 + 215204096,
         "profile": "profiles/fp64_transforms_complex255.md"},
 }
 
