@@ -116,7 +116,9 @@ struct GemmLayout {
     static constexpr uint32_t NACC = NPAD <= 32 ? 32 : (NPAD <= 64 ? 64 : (NPAD <= 128 ? 128 : 256));
     static constexpr uint32_t TMEM_COLS = 2 * NACC;
     static constexpr uint32_t CTRL = 2048;
-    static constexpr uint32_t BYTES = GSTAGES * STAGE + CTRL + 1024;   // + alignment slack
+    // x epilogue: a 32 x 33 FP32 transposition tile per epilogue warp
+    static constexpr uint32_t EPI = NEPI * 32 * 33 * 4;
+    static constexpr uint32_t BYTES = GSTAGES * STAGE + CTRL + EPI + 1024;   // + alignment slack
 };
 
 enum { B_FULL = 0, B_BFULL = 2, B_EMPTY = 4, B_ACCFULL = 6, B_ACCEMPTY = 8, B_EXP = 10,
@@ -179,20 +181,35 @@ __global__ void __launch_bounds__(NTHR, 1) dst_gemm_kernel(GemmArgs g) {
             const float *lp[4];
             bool lv[4];
             if (AXIS == HS_AXIS_X) {
-                // lines m = 16 warp + i; the lane converts lines 16 warp + (lane >> 3) + 4q
-                for (int i = 0; i < 16; ++i) {
-                    const int m = 16 * warp + i;
-                    const long r = (long)t * GM + m;
-                    float mx = 0.f;
-                    if (r < g.nlines) {
-                        const float *row = g.in + (size_t)r * g.N;
-                        for (int k = lane; k < g.N; k += 32) mx = fmaxf(mx, fabsf(row[k]));
+                // lines m = 16 warp + i; the lane converts lines 16 warp + (lane >> 3) + 4q.
+                // Four lines at a time, every load of a group issued before its
+                // maxima (a line of N <= 255 is at most 8 loads per lane)
+#pragma unroll
+                for (int i0 = 0; i0 < 16; i0 += 4) {
+                    float v[4][8];
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        const long r = (long)t * GM + 16 * warp + i0 + d;
+                        const float *row = g.in + (size_t)(r < g.nlines ? r : 0) * g.N;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int k = lane + 32 * u;
+                            v[d][u] = (r < g.nlines && k < g.N) ? row[k] : 0.f;
+                        }
                     }
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                    const int e = line_exponent(mx);
-                    if (lane == 0) sexp[buf * GM + m] = e;
-                    if ((i & 3) == (lane >> 3)) ex[i >> 2] = e;
+                    for (int d = 0; d < 4; ++d) {
+                        float mx = 0.f;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) mx = fmaxf(mx, fabsf(v[d][u]));
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1)
+                            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                        const int i = i0 + d, m = 16 * warp + i;
+                        const int e = line_exponent(mx);
+                        if (lane == 0) sexp[buf * GM + m] = e;
+                        if ((i & 3) == (lane >> 3)) ex[i >> 2] = e;
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -211,9 +228,19 @@ __global__ void __launch_bounds__(NTHR, 1) dst_gemm_kernel(GemmArgs g) {
                 const float *col = g.in + (size_t)l * g.Ny * g.Nx + (valid ? p : 0);
                 float mx = 0.f;
                 if (valid) {
+                    // 16 independent loads per group: the column's latency is paid
+                    // once per 16 rows, not once per row
                     const int half = (g.N + 1) / 2;
                     const int j0 = (lane >> 4) * half, j1 = min(g.N, j0 + half);
-                    for (int j = j0; j < j1; ++j) mx = fmaxf(mx, fabsf(col[(size_t)j * g.Nx]));
+                    int j = j0;
+                    for (; j + 16 <= j1; j += 16) {
+                        float v[16];
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) v[u] = col[(size_t)(j + u) * g.Nx];
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) mx = fmaxf(mx, fabsf(v[u]));
+                    }
+                    for (; j < j1; ++j) mx = fmaxf(mx, fabsf(col[(size_t)j * g.Nx]));
                 }
                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
                 const int e = line_exponent(mx);
@@ -248,6 +275,21 @@ __global__ void __launch_bounds__(NTHR, 1) dst_gemm_kernel(GemmArgs g) {
                              2 * LY::B_BYTES, &bar[B_BFULL + s]);
                     last_v[s] = (int)v;
                 }
+                // all 32 loads of this lane's chunk pieces first (one memory latency
+                // per chunk), then the splits and the swizzled stores
+                float x[4][8];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c8 = AXIS == HS_AXIS_X ? (lane & 7) : (lane >> 4) + 2 * q;
+                    const int k0 = kc * GKC + c8 * 8;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int k = k0 + i;
+                        x[q][i] = 0.f;
+                        if (lv[q] && k < g.N)
+                            x[q][i] = AXIS == HS_AXIS_X ? lp[q][k] : lp[q][(size_t)k * g.Nx];
+                    }
+                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     int m, c8;
@@ -258,20 +300,11 @@ __global__ void __launch_bounds__(NTHR, 1) dst_gemm_kernel(GemmArgs g) {
                         m = 16 * warp + (lane & 15);
                         c8 = (lane >> 4) + 2 * q;
                     }
-                    const int k0 = kc * GKC + c8 * 8;
-                    float x[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int k = k0 + i;
-                        x[i] = 0.f;
-                        if (lv[q] && k < g.N)
-                            x[i] = AXIS == HS_AXIS_X ? lp[q][k] : lp[q][(size_t)k * g.Nx];
-                    }
                     uint4 h0, h1;
-                    split_pair(x[0], x[1], s1[q], s2[q], h0.x, h1.x);
-                    split_pair(x[2], x[3], s1[q], s2[q], h0.y, h1.y);
-                    split_pair(x[4], x[5], s1[q], s2[q], h0.z, h1.z);
-                    split_pair(x[6], x[7], s1[q], s2[q], h0.w, h1.w);
+                    split_pair(x[q][0], x[q][1], s1[q], s2[q], h0.x, h1.x);
+                    split_pair(x[q][2], x[q][3], s1[q], s2[q], h0.y, h1.y);
+                    split_pair(x[q][4], x[q][5], s1[q], s2[q], h0.z, h1.z);
+                    split_pair(x[q][6], x[q][7], s1[q], s2[q], h0.w, h1.w);
                     const uint32_t off = swz(m, c8);
                     *reinterpret_cast<uint4 *>(st + off) = h0;
                     *reinterpret_cast<uint4 *>(st + LY::A_BYTES + off) = h1;
@@ -319,6 +352,69 @@ __global__ void __launch_bounds__(NTHR, 1) dst_gemm_kernel(GemmArgs g) {
                 ostep = (size_t)g.Nx;
             }
             const uint32_t tl = tbase + ((uint32_t)(32 * w) << 16) + (uint32_t)buf * LY::NACC;
+            if (AXIS == HS_AXIS_X) {
+                // lane = line in TMEM; through a transposition tile so that a warp's
+                // stores cover 32 consecutive modes of one line (coalesced)
+                float *T = reinterpret_cast<float *>(ctrl + LY::CTRL) + w * 32 * 33;
+#pragma unroll 1
+                for (int c0 = 0; c0 < NPAD; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tl + (uint32_t)c0, v);
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) T[lane * 33 + k] = ((v[k] * f1) * f2) * g.scale;
+                    __syncwarp();
+                    const int n = c0 + lane;
+                    if constexpr (MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL) {
+                        // read-modify-write of the pair iterate: 8 lines' (hi, lo) loaded
+                        // before any is updated
+                        float *o = reinterpret_cast<float *>(g.out);
+#pragma unroll 1
+                        for (int k0 = 0; k0 < 32; k0 += 8) {
+                            float hi[8], lo[8];
+#pragma unroll
+                            for (int d = 0; d < 8; ++d) {
+                                const long r = (long)t * GM + 32 * w + k0 + d;
+                                const bool ok = r < g.nlines && n < g.N;
+                                const size_t idx = (size_t)(ok ? r : 0) * g.N + (ok ? n : 0);
+                                hi[d] = ok ? o[idx] : 0.f;
+                                lo[d] = ok ? o[idx + g.lo_off] : 0.f;
+                            }
+#pragma unroll
+                            for (int d = 0; d < 8; ++d) {
+                                const long r = (long)t * GM + 32 * w + k0 + d;
+                                if (r < g.nlines && n < g.N) {
+                                    const size_t idx = (size_t)r * g.N + n;
+                                    dfloat a;
+                                    a.hi = hi[d];
+                                    a.lo = lo[d];
+                                    dfloat b;
+                                    b.hi = T[(k0 + d) * 33 + lane];
+                                    b.lo = 0.f;
+                                    const dfloat sum = df_add(a, b);
+                                    if constexpr (MODE == HS_MODE_DF_ADD) {
+                                        o[idx] = sum.hi;
+                                        o[idx + g.lo_off] = sum.lo;
+                                    } else {
+                                        g.aux[idx] = (double)sum.hi + (double)sum.lo;
+                                    }
+                                }
+                            }
+                        }
+                    } else {
+#pragma unroll 4
+                        for (int kk = 0; kk < 32; ++kk) {
+                            const long r = (long)t * GM + 32 * w + kk;
+                            if (r < g.nlines && n < g.N)
+                                hs_emit<Tout, MODE>(static_cast<Tout *>(g.out), g.aux, g.lo_off,
+                                                    (size_t)r * g.N + n, (double)T[kk * 33 + lane]);
+                        }
+                    }
+                    __syncwarp();
+                }
+                tc_fence_before();
+                mbar_arrive(&bar[B_ACCEMPTY + buf]);
+                continue;
+            }
 #pragma unroll 1
             for (int c0 = 0; c0 < NPAD; c0 += 32) {
                 float v[32];
