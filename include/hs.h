@@ -694,6 +694,20 @@ hs_status hs_zplan_set_coeff(hs_zplan_t plan, const double *K);
 hs_status hs_zplan_set_coeff6(hs_zplan_t plan, const double *K, const double *Kz,
                               const double *Kzz);
 
+/* hs_zplan_set_precision -- HS_FP64 (default: every step in FP64) or HS_MIXED:
+ * the solve of Section 3.6 run in FP32 (FP32 transforms of the planar real
+ * and imaginary parts, FP32 z-solves on the cached LU factors rounded to FP32)
+ * as the approximate inverse M of an iterative refinement
+ * U_0 = M F, U_{m+1} = U_m + M (F - A U_m), m < sweeps, with F, U and the
+ * complex 27-point residual in FP64 (the refined result is as accurate as the
+ * FP64 path's to about 1e-10 after one sweep on well-conditioned problems).
+ * Dirichlet side faces only (HS_ERR_UNSUPPORTED otherwise, and set_sides then
+ * refuses other kinds); sweeps 0..8.  The mixed solve allocates, on first use,
+ * 20 bytes per complex unknown (FP32 work, FP64 iterate) and 24 for the FP32
+ * factors.  Stage timing reports the refinement loop as the transform stage.
+ * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED. */
+hs_status hs_zplan_set_precision(hs_zplan_t plan, int precision, int sweeps);
+
 /* hs_zplan_set_faces -- kind (HS_ZFACE_DIRICHLET / HS_ZFACE_ROBIN, eq. bc) of
  * the z-lo and z-hi faces; alpha, beta: host (re, im) pairs, read for Robin faces only
  * (alpha != 0 there).  Errors: HS_ERR_INVALID_ARG, HS_ERR_OOM. */

@@ -64,7 +64,8 @@ EXPORTED = ("hs_plan", "hs_set_coeff", "hs_set_refinement", "hs_set_refinement_t
             "hs_precond_create", "hs_precond_apply", "hs_precond_solve", "hs_precond_destroy",
             "hs_batch_workspace_bytes", "hs_batch_destroy",
             "hs_zplan", "hs_zplan_set_coeff", "hs_zplan_set_faces", "hs_zplan_set_sides",
-            "hs_zsolve", "hs_zsolve_ex", "hs_zsolve_full", "hs_zplan_set_coeff6", "hs_set_coeff_fn", "hs_zplan_set_stage_timing",
+            "hs_zsolve", "hs_zsolve_ex", "hs_zsolve_full", "hs_zplan_set_coeff6",
+            "hs_zplan_set_precision", "hs_set_coeff_fn", "hs_zplan_set_stage_timing",
             "hs_zplan_stage_times",
             "hs_zplan_workspace_bytes", "hs_zplan_last_error", "hs_zplan_destroy")
 HS_STATIC_MAX_NZ = 8192
@@ -211,6 +212,8 @@ def load(path: Optional[str] = None):
     lib.hs_zsolve_ex.restype = ci
     lib.hs_zsolve_full.argtypes = [vp, vp, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp]
     lib.hs_zsolve_full.restype = ci
+    lib.hs_zplan_set_precision.argtypes = [vp, ci, ci]
+    lib.hs_zplan_set_precision.restype = ci
     lib.hs_zplan_set_coeff6.argtypes = [vp, dp, dp, dp]
     lib.hs_zplan_set_coeff6.restype = ci
     lib.hs_zsolve.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -700,6 +703,11 @@ class ZSolver:
         buf = np.ascontiguousarray(np.stack([K.real, K.imag], axis=-1).ravel())
         arr = (ctypes.c_double * buf.size)(*buf.tolist())
         return self._err(load().hs_zplan_set_coeff(self.plan, arr), "hs_zplan_set_coeff")
+
+    def set_precision(self, precision, sweeps=1):
+        """HS_FP64, or HS_MIXED: FP32 solves refined with FP64 residuals (Dirichlet sides)."""
+        return self._err(load().hs_zplan_set_precision(self.plan, int(precision), int(sweeps)),
+                         "hs_zplan_set_precision")
 
     def set_coeff6(self, K, Kz, Kzz):
         """K, K_z, K_zz at the Nz + 2 nodes (order 6; orders 2 and 4 read K only)."""

@@ -48,6 +48,7 @@
 #include <vector>
 
 #include "hs_internal.cuh"
+#include "hs_rhs_sf.cuh"   // LPair: unnormalised FP32-pair arithmetic
 
 struct hs_zplan_s {
     int Nx, Ny, Nz, order;
@@ -67,9 +68,17 @@ struct hs_zplan_s {
     double *d_cos;             // [nx] then [ny]: cos(theta) of each axis' modes
     double2 *d_dct[2];         // Neumann axis: M roots then M + 1 half-angle pairs
     double2 *d_rows;           // [Nu][3][4] complex coefficients of the unknown rows
+    float4 *d_rows32;          // the same as FP32 pairs (re hi, re lo, im hi, im lo)
     int rows_ok;
     double *d_fac;             // cached LU factors: 3 planar complex arrays [2][Nu][ny][nx]
     int fac_ok;                // the factors match the rows and side tables
+    // HS_MIXED: FP32 solves of the correction equation, FP64 residuals, refinement
+    int precision, sweeps;
+    float *d_w32;              // [2][Nu][ny][nx] FP32 work of the correction solves
+    float *d_fac32;            // the LU factors rounded to FP32 (layout of d_fac)
+    float *d_Fp, *d_Up;        // F and the iterate as FP32 pairs: [hi: 2][Nu][ny][nx], then lo
+    double *d_U;               // [2][Nu][ny][nx] FP64 result
+    int fac32_ok;
     int timing;                // record events around the stages of each solve
     int have_ev;
     cudaEvent_t ev[6];         // rhs | forward transforms | z-solves | inverse | output
@@ -201,6 +210,15 @@ hs_status build_rows(hs_zplan_s *Z) {
     }
     ZCK(Z, cudaMemcpy(Z->d_rows, rows.data(), rows.size() * sizeof(double2),
                       cudaMemcpyHostToDevice));
+    if (Z->d_rows32) {   // the pair copy of the mixed-precision residual
+        std::vector<float4> r32(rows.size());
+        for (size_t k = 0; k < rows.size(); ++k) {
+            const float rh = (float)rows[k].x, ih = (float)rows[k].y;
+            r32[k] = make_float4(rh, (float)(rows[k].x - (double)rh), ih, (float)(rows[k].y - (double)ih));
+        }
+        ZCK(Z, cudaMemcpy(Z->d_rows32, r32.data(), r32.size() * sizeof(float4),
+                          cudaMemcpyHostToDevice));
+    }
     Z->rows_ok = 1;
     Z->fac_ok = 0;
     return HS_OK;
@@ -249,6 +267,23 @@ hs_status side_tables(hs_zplan_s *Z) {
     return HS_OK;
 }
 
+// Buffers of the mixed-precision solve (allocated by the first mixed solve).
+void free_mixed(hs_zplan_s *Z) {
+    if (Z->d_w32) cudaFree(Z->d_w32);
+    if (Z->d_fac32) cudaFree(Z->d_fac32);
+    if (Z->d_U) cudaFree(Z->d_U);
+    if (Z->d_Fp) cudaFree(Z->d_Fp);
+    if (Z->d_Up) cudaFree(Z->d_Up);
+    if (Z->d_rows32) cudaFree(Z->d_rows32);
+    Z->d_w32 = nullptr;
+    Z->d_fac32 = nullptr;
+    Z->d_U = nullptr;
+    Z->d_Fp = nullptr;
+    Z->d_Up = nullptr;
+    Z->d_rows32 = nullptr;
+    Z->fac32_ok = 0;
+}
+
 // (Re)creates the transform plan, row table and side tables for the current
 // faces and side axes.
 hs_status layout(hs_zplan_s *Z) {
@@ -273,6 +308,7 @@ hs_status layout(hs_zplan_s *Z) {
         Z->d_rows = nullptr;
         if (Z->d_fac) cudaFree(Z->d_fac);
         Z->d_fac = nullptr;
+        free_mixed(Z);   // sized for the previous shape
         Z->Nu = Nu;
         Z->nx = nx;
         Z->ny = ny;
@@ -696,6 +732,161 @@ __global__ void zthomas_kernel(double *W, const double *fac, int Nx, int Ny, int
     }
 }
 
+// ------------------------------------------------------------ mixed precision
+// FP64 -> FP32 copy of n values (the LU factors).
+template <typename Tin>
+__global__ void zround_kernel(const Tin *__restrict__ in, float *__restrict__ out, size_t n) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        out[k] = (float)in[k];
+}
+
+// The z-solves of one correction in FP32 with the FP32-rounded cached factors
+// (zthomas_kernel's recurrence).
+__global__ void zthomas32_kernel(float *W, const float *fac, int Nx, int Ny, int Nu) {
+    const size_t plane = (size_t)Nx * Ny, n = plane * Nu;
+    const size_t col = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (col >= plane) return;
+    const float *F0 = fac, *F1 = fac + 2 * n, *F2 = fac + 4 * n;
+    float dx = 0.f, dy = 0.f;
+    for (int r = 0; r < Nu; ++r) {
+        const size_t k = (size_t)r * plane + col;
+        const float rx = W[k], ry = W[n + k];
+        const float ax = F0[k], ay = F0[n + k], bx = F1[k], by = F1[n + k];
+        const float nx_ = (rx * ax - ry * ay) - (bx * dx - by * dy);
+        const float ny_ = (rx * ay + ry * ax) - (bx * dy + by * dx);
+        dx = nx_;
+        dy = ny_;
+        W[k] = dx;
+        W[n + k] = dy;
+    }
+    float wx = dx, wy = dy;
+    for (int r = Nu - 2; r >= 0; --r) {
+        const size_t k = (size_t)r * plane + col;
+        const float cx = F2[k], cy = F2[n + k];
+        const float nx_ = W[k] - (cx * wx - cy * wy);
+        const float ny_ = W[n + k] - (cx * wy + cy * wx);
+        wx = nx_;
+        wy = ny_;
+        W[k] = wx;
+        W[n + k] = wy;
+    }
+}
+
+// F (FP64 planar complex, n2 values) as FP32 pairs: hi parts at [0, n2), lo at
+// [n2, 2 n2) -- the hi half is the FP32 input of the first solve.
+__global__ void zsplit_kernel(const double *__restrict__ W, float *__restrict__ P, size_t n2) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n2;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const dfloat d = df_split_bits(W[k]);
+        P[k] = d.hi;
+        P[n2 + k] = d.lo;
+    }
+}
+
+// r = F - A U in FP32-pair arithmetic (rounding about 2^-46 of the largest term;
+// the mixed path's residual): a CTA owns 32 x 8 columns and marches over the Nu
+// unknown rows; each U plane (pairs, halo 1, zero beyond the Dirichlet side
+// faces) is staged in shared memory once, every thread forms its plane sums
+// (corners, x and y neighbours, centre; real and imaginary) once, and each row
+// combines the sums of its three planes with its 3 x 4 complex pair
+// coefficients.  r is written in FP32 (the input of the next FP32 solve).
+constexpr int ZRX = 32, ZRY = 8;
+
+struct ZSums {
+    hs_tiles::LPair r[4], i[4];   // A (corners), B (x), C (y), D (centre)
+};
+
+__global__ void __launch_bounds__(ZRX * ZRY)
+zresid_df_kernel(const float *__restrict__ Fp, const float *__restrict__ Up,
+                 const float4 *__restrict__ rows4, float *__restrict__ r32, int nx, int ny, int Nu) {
+    using namespace hs_tiles;
+    __shared__ float4 ring[2][ZRY + 2][ZRX + 2];   // (re hi, re lo, im hi, im lo)
+    const size_t plane = (size_t)nx * ny, nu = plane * Nu, n2 = 2 * nu;
+    const int tx = threadIdx.x % ZRX, ty = threadIdx.x / ZRX;
+    const int i0 = blockIdx.x * ZRX, j0 = blockIdx.y * ZRY;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = i < nx && j < ny;
+    auto load = [&](int rr, int slot) {
+        for (int e = threadIdx.x; e < (ZRY + 2) * (ZRX + 2); e += ZRX * ZRY) {
+            const int ey = e / (ZRX + 2), ex = e - ey * (ZRX + 2);
+            const int jj = j0 - 1 + ey, ii = i0 - 1 + ex;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (jj >= 0 && jj < ny && ii >= 0 && ii < nx) {
+                const size_t k = (size_t)rr * plane + (size_t)jj * nx + ii;
+                v = make_float4(Up[k], Up[n2 + k], Up[nu + k], Up[n2 + nu + k]);
+            }
+            ring[slot][ey][ex] = v;
+        }
+    };
+    auto sums = [&](int slot, ZSums &S) {
+        auto at = [&](int dy, int dx) { return ring[slot][ty + 1 + dy][tx + 1 + dx]; };
+        const float4 a = at(-1, -1), b = at(-1, 1), c = at(1, -1), d = at(1, 1);
+        S.r[0] = LPair{a.x, a.y};
+        lp_add(S.r[0], b.x, b.y);
+        lp_add(S.r[0], c.x, c.y);
+        lp_add(S.r[0], d.x, d.y);
+        S.i[0] = LPair{a.z, a.w};
+        lp_add(S.i[0], b.z, b.w);
+        lp_add(S.i[0], c.z, c.w);
+        lp_add(S.i[0], d.z, d.w);
+        const float4 xl = at(0, -1), xr = at(0, 1), yl = at(-1, 0), yr = at(1, 0), o = at(0, 0);
+        S.r[1] = LPair{xl.x, xl.y};
+        lp_add(S.r[1], xr.x, xr.y);
+        S.i[1] = LPair{xl.z, xl.w};
+        lp_add(S.i[1], xr.z, xr.w);
+        S.r[2] = LPair{yl.x, yl.y};
+        lp_add(S.r[2], yr.x, yr.y);
+        S.i[2] = LPair{yl.z, yl.w};
+        lp_add(S.i[2], yr.z, yr.w);
+        S.r[3] = LPair{o.x, o.y};
+        S.i[3] = LPair{o.z, o.w};
+    };
+    auto zero = [](ZSums &S) {
+        for (int m = 0; m < 4; ++m) S.r[m] = S.i[m] = LPair{0.f, 0.f};
+    };
+    ZSums sm, s0, sp;
+    zero(sm);
+    load(0, 0);
+    __syncthreads();
+    sums(0, s0);
+    for (int r = 0; r < Nu; ++r) {
+        if (r + 1 < Nu) {
+            load(r + 1, (r + 1) & 1);
+            __syncthreads();
+            sums((r + 1) & 1, sp);
+        } else {
+            zero(sp);
+        }
+        if (active) {
+            const size_t k = (size_t)r * plane + (size_t)j * nx + i;
+            LPair ar{Fp[k], Fp[n2 + k]}, ai{Fp[nu + k], Fp[n2 + nu + k]};
+            const float4 *cf = rows4 + (size_t)r * 12;
+            const ZSums *S3[3] = {&sm, &s0, &sp};
+#pragma unroll
+            for (int nuv = 0; nuv < 3; ++nuv) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const float4 c = __ldg(cf + nuv * 4 + m);
+                    const float2 cre = make_float2(c.x, c.y), cim = make_float2(c.z, c.w);
+                    const LPair Sr = S3[nuv]->r[m], Si = S3[nuv]->i[m];
+                    // F - (c_re + i c_im)(S_re + i S_im)
+                    const LPair p1 = lp_mul(cre, Sr), p2 = lp_mul(cim, Si);
+                    const LPair p3 = lp_mul(cre, Si), p4 = lp_mul(cim, Sr);
+                    lp_add(ar, -p1.s, -p1.e);
+                    lp_add(ar, p2);
+                    lp_add(ai, -p3.s, -p3.e);
+                    lp_add(ai, -p4.s, -p4.e);
+                }
+            }
+            r32[k] = ar.s + ar.e;
+            r32[nu + k] = ai.s + ai.e;
+        }
+        sm = s0;
+        s0 = sp;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -762,6 +953,17 @@ hs_status hs_zplan_set_coeff6(hs_zplan_t Z, const double *K, const double *Kz,
     return build_rows(Z);
 }
 
+hs_status hs_zplan_set_precision(hs_zplan_t Z, int precision, int sweeps) {
+    if (!Z || (precision != HS_FP64 && precision != HS_MIXED) || sweeps < 0 || sweeps > 8)
+        return HS_ERR_INVALID_ARG;
+    if (precision == HS_MIXED &&
+        (Z->side[0] != HS_SIDE_DIRICHLET || Z->side[1] != HS_SIDE_DIRICHLET))
+        return HS_ERR_UNSUPPORTED;   // the FP32 cosine / quarter-wave tiles are not built
+    Z->precision = precision;
+    Z->sweeps = sweeps;
+    return HS_OK;
+}
+
 hs_status hs_zplan_set_coeff(hs_zplan_t Z, const double *K) {
     if (!Z || !K || Z->order == 6) return HS_ERR_INVALID_ARG;   // order 6 needs K_z, K_zz
     return hs_zplan_set_coeff6(Z, K, nullptr, nullptr);
@@ -802,8 +1004,10 @@ hs_status hs_zplan_set_sides(hs_zplan_t Z, int x_kind, int y_kind) {
     const int k[2] = {x_kind, y_kind};
     for (int a = 0; a < 2; ++a)
         if (k[a] < HS_SIDE_DIRICHLET || k[a] > HS_SIDE_ND) return HS_ERR_INVALID_ARG;
-    // the 6th-order right-hand side's ghosts are defined for Dirichlet side faces
-    if (Z->order == 6 && (x_kind != HS_SIDE_DIRICHLET || y_kind != HS_SIDE_DIRICHLET))
+    // the 6th-order right-hand side's ghosts are defined for Dirichlet side faces,
+    // and the mixed-precision solve has FP32 sine tiles only
+    if ((Z->order == 6 || Z->precision == HS_MIXED) &&
+        (x_kind != HS_SIDE_DIRICHLET || y_kind != HS_SIDE_DIRICHLET))
         return HS_ERR_UNSUPPORTED;
     // lengths without a compiled FFT take the runtime-sized transforms (direct sums
     // for a cosine axis, the sine plan's own fallback for the extended lines of a
@@ -938,6 +1142,88 @@ hs_status hs_zsolve_full(hs_zplan_t Z, const double *f, const double *g_lo, cons
         return hs_launch_dst(T, axis, HS_T_F64, HS_T_F64, W, HS_T_F64, W, HS_MODE_WRITE, scale, s);
     };
     hs_status st;
+    const double *Wout = W;   // the unknown planes' solution
+    if (Z->precision == HS_MIXED) {
+        // U_0 = M F, U_{m+1} = U_m + M (F - A U_m) with M the FP32 solve (FP32
+        // transforms and z-solves on FP32-rounded factors); F and U are FP32 pairs
+        // and the residual is formed in pair arithmetic; the last correction is
+        // added in FP64.  The stage events see the whole loop as the transform stage.
+        const size_t n2 = 2 * nu;
+        if (!Z->d_w32) ZCK(Z, cudaMalloc(&Z->d_w32, n2 * sizeof(float)));
+        if (!Z->d_U) ZCK(Z, cudaMalloc(&Z->d_U, n2 * sizeof(double)));
+        if (!Z->d_fac32) ZCK(Z, cudaMalloc(&Z->d_fac32, 3 * n2 * sizeof(float)));
+        if (!Z->d_Fp) ZCK(Z, cudaMalloc(&Z->d_Fp, 2 * n2 * sizeof(float)));
+        if (!Z->d_Up) ZCK(Z, cudaMalloc(&Z->d_Up, 2 * n2 * sizeof(float)));
+        if (!Z->d_rows32) {
+            ZCK(Z, cudaMalloc(&Z->d_rows32, (size_t)Z->Nu * 12 * sizeof(float4)));
+            const hs_status rs = build_rows(Z);
+            if (rs != HS_OK) return rs;
+        }
+        if (!Z->fac_ok) {
+            zfactor_kernel<<<(unsigned)((plane + 127) / 128), 128, 0, s>>>(
+                Z->d_fac, Z->d_rows, Z->d_cos, Z->d_cos + Z->nx, Z->nx, Z->ny, Z->Nu);
+            ZCK(Z, cudaGetLastError());
+            Z->fac_ok = 1;
+            Z->fac32_ok = 0;
+        }
+        const unsigned eb = (unsigned)((n2 + 255) / 256 < 152 * 16 ? (n2 + 255) / 256 : 152 * 16);
+        if (!Z->fac32_ok) {
+            zround_kernel<double><<<eb, 256, 0, s>>>(Z->d_fac, Z->d_fac32, 3 * n2);
+            ZCK(Z, cudaGetLastError());
+            Z->fac32_ok = 1;
+        }
+        zsplit_kernel<<<eb, 256, 0, s>>>(W, Z->d_Fp, n2);
+        ZCK(Z, cudaGetLastError());
+        // the FP32 transforms take the fused tiles where the length is compiled
+        // (the plan's own variant is for its FP64 passes)
+        const int saved[2] = {T->dst_variant[0], T->dst_variant[1]};
+        for (int a = 0; a < 2; ++a)
+            if (hs_dst_fast_size(T->axf[a].M)) T->dst_variant[a] = HS_DST_FUSED;
+        float *w = Z->d_w32;
+        const double sx = 2.0 / (Z->Nx + 1), sy = 2.0 / (Z->Ny + 1);
+        const dim3 rgrid((unsigned)((Z->nx + ZRX - 1) / ZRX), (unsigned)((Z->ny + ZRY - 1) / ZRY));
+        const int sw = Z->sweeps;
+        st = HS_OK;
+        for (int m = 0; m <= sw && st == HS_OK; ++m) {
+            const float *in = w;
+            if (m == 0) {
+                in = Z->d_Fp;   // F_hi
+            } else {
+                zresid_df_kernel<<<rgrid, ZRX * ZRY, 0, s>>>(Z->d_Fp, Z->d_Up, Z->d_rows32, w,
+                                                            Z->nx, Z->ny, Z->Nu);
+                if (cudaGetLastError() != cudaSuccess) st = HS_ERR_CUDA;
+            }
+            if (st == HS_OK)
+                st = hs_launch_dst(T, HS_AXIS_X, HS_T_F32, HS_T_F32, in, HS_T_F32, w, HS_MODE_WRITE, 1.0, s);
+            if (st == HS_OK)
+                st = hs_launch_dst(T, HS_AXIS_Y, HS_T_F32, HS_T_F32, w, HS_T_F32, w, HS_MODE_WRITE, 1.0, s);
+            if (st == HS_OK) {
+                zthomas32_kernel<<<(unsigned)((plane + 127) / 128), 128, 0, s>>>(w, Z->d_fac32, Z->nx,
+                                                                               Z->ny, Z->Nu);
+                if (cudaGetLastError() != cudaSuccess) st = HS_ERR_CUDA;
+            }
+            if (st == HS_OK)
+                st = hs_launch_dst(T, HS_AXIS_Y, HS_T_F32, HS_T_F32, w, HS_T_F32, w, HS_MODE_WRITE, sy, s);
+            if (st != HS_OK) break;
+            // the iterate: FP64 U straight away without refinement, else pairs (set,
+            // add) and, on the last sweep, U + correction in FP64
+            if (sw == 0)
+                st = hs_launch_dst(T, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_F64, Z->d_U,
+                                   HS_MODE_WRITE, sx, s);
+            else
+                st = hs_launch_dst(T, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_DF, Z->d_Up,
+                                   m == 0 ? HS_MODE_DF_SET : (m < sw ? HS_MODE_DF_ADD : HS_MODE_DF_FINAL),
+                                   sx, s, Z->d_U);
+        }
+        T->dst_variant[0] = saved[0];
+        T->dst_variant[1] = saved[1];
+        if (st != HS_OK) {
+            zerr(Z, "mixed-precision solve: status %d", st);
+            return st;
+        }
+        Wout = Z->d_U;
+        if ((mk = mark(2)) != HS_OK || (mk = mark(3)) != HS_OK || (mk = mark(4)) != HS_OK) return mk;
+    } else {
     if ((st = pass(HS_AXIS_X, true, 1.0)) != HS_OK || (st = pass(HS_AXIS_Y, true, 1.0)) != HS_OK) {
         zerr(Z, "forward transform: status %d", st);
         return st;
@@ -959,11 +1245,12 @@ hs_status hs_zsolve_full(hs_zplan_t Z, const double *f, const double *g_lo, cons
         return st;
     }
     if ((mk = mark(4)) != HS_OK) return mk;
+    }
     // unknown planes into u; Dirichlet planes receive their face data
     const size_t uplanes = (size_t)Z->Nz + 2;
     for (int comp = 0; comp < 2; ++comp) {
         double *uc = u + comp * uplanes * plane;
-        ZCK(Z, cudaMemcpyAsync(uc + (size_t)Z->l0 * plane, W + comp * nu, nu * sizeof(double),
+        ZCK(Z, cudaMemcpyAsync(uc + (size_t)Z->l0 * plane, Wout + comp * nu, nu * sizeof(double),
                                cudaMemcpyDeviceToDevice, s));
         for (int side = 0; side < 2; ++side) {
             if (Z->kind[side] != HS_ZFACE_DIRICHLET) continue;
@@ -1026,6 +1313,7 @@ void hs_zplan_destroy(hs_zplan_t Z) {
     for (int a = 0; a < 2; ++a)
         if (Z->TQ[a]) hs_destroy(Z->TQ[a]);
     if (Z->d_kk) cudaFree(Z->d_kk);
+    free_mixed(Z);
     if (Z->d_rows) cudaFree(Z->d_rows);
     if (Z->d_cos) cudaFree(Z->d_cos);
     if (Z->d_fac) cudaFree(Z->d_fac);

@@ -473,3 +473,85 @@ def test_order6_complex_127():
     ref, _ = CX.solve(6, h, K, zf, f, g_lo, g_hi, Kz=Kz, Kzz=Kzz, fnn=fnn)
     got = _gpu6(shape, L, K, Kz, Kzz, zf, f, g_lo, g_hi, fnn)
     assert O.max_rel_diff(got, ref) <= TOL
+
+
+
+MIXTOL = 1e-10
+
+
+def _gpu_mixed(shape, L, order, K, zf, f, g_lo, g_hi, sweeps, Kz=None, Kzz=None, fnn=None):
+    torch = _torch()
+    Nx, Ny, Nz = shape
+    s = H.ZSolver(Nx, Ny, Nz, *L, order)
+    try:
+        if order == 6:
+            s.set_coeff6(K, Kz, Kzz)
+        else:
+            s.set_coeff(K)
+        s.set_faces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
+        s.set_precision(H.HS_MIXED, sweeps)
+        u = torch.full((2, Nz + 2, Ny, Nx), np.nan, dtype=torch.float64, device="cuda")
+        s.solve(_planar(torch, f), u, None if g_lo is None else _planar(torch, g_lo),
+                None if g_hi is None else _planar(torch, g_hi),
+                fnn=None if fnn is None else [None if a is None else _planar(torch, a) for a in fnn])
+        torch.cuda.synchronize()
+        uc = u.cpu().numpy()
+        return uc[0] + 1j * uc[1]
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("faces", FACES)
+@pytest.mark.parametrize("shape", [(31, 20, 17), (63, 40, 12), (127, 95, 33)])
+def test_mixed_precision_complex_matches_oracle(order, faces, shape):
+    """HS_MIXED: FP32 solves refined with FP64 residuals; one sweep reaches the mixed
+    bar against the oracle, and the unrefined solve is FP32-accurate (printed)."""
+    L = (1.0, 0.9, 1.2)
+    h, K, f, g_lo, g_hi = _case(shape, L, sum(shape) + order + 11)
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    ref, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi)
+    e0 = O.max_rel_diff(_gpu_mixed(shape, L, order, K, zf, f, g_lo, g_hi, 0), ref)
+    e1 = O.max_rel_diff(_gpu_mixed(shape, L, order, K, zf, f, g_lo, g_hi, 1), ref)
+    print(f"mixed complex {shape} order {order} faces {faces}: unrefined {e0:.2e}, one sweep {e1:.2e}")
+    assert e0 <= 1e-4
+    assert e1 <= MIXTOL
+
+
+@pytest.mark.parametrize("faces", [(R, R), (D, R)])
+def test_mixed_precision_complex_order6(faces):
+    shape = (31, 23, 13)
+    h, L, K, Kz, Kzz, f, fnn, cr = _case6(shape, 41 + faces[0])
+    Nx, Ny, Nz = shape
+    g_lo, g_hi = cr(Ny, Nx), cr(Ny, Nx)
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    ref, _ = CX.solve(6, h, K, zf, f, g_lo, g_hi, Kz=Kz, Kzz=Kzz, fnn=fnn)
+    got = _gpu_mixed(shape, L, 6, K, zf, f, g_lo, g_hi, 2, Kz, Kzz, fnn)
+    assert O.max_rel_diff(got, ref) <= MIXTOL
+
+
+def test_mixed_precision_complex_255_and_errors():
+    """255^3 Robin (the zrobin255_o4 recipe's shape) with one sweep; mixed precision
+    refuses Neumann or mixed side axes, and those side kinds refuse mixed precision."""
+    shape, L = (255, 255, 255), (1.0, 1.0, 1.0)
+    h, K, f, g_lo, g_hi = _case(shape, L, 12)
+    zf = CX.ZFaces(R, 1.0 + 0.5j, 3.0 - 1.0j, R, 1.0 + 0.5j, 3.0 - 1.0j)
+    ref, _ = CX.solve(4, h, K, zf, f, g_lo, g_hi)
+    got = _gpu_mixed(shape, L, 4, K, zf, f, g_lo, g_hi, 1)
+    assert O.max_rel_diff(got, ref) <= MIXTOL
+    s = H.ZSolver(31, 31, 7, 1.0, 1.0, 1.0, 4)
+    try:
+        s.set_sides(H.HS_SIDE_NEUMANN, H.HS_SIDE_DIRICHLET)
+        with pytest.raises(H.HsError) as e:
+            s.set_precision(H.HS_MIXED, 1)
+        assert e.value.status == H.HS_ERR_UNSUPPORTED
+        s.set_sides(H.HS_SIDE_DIRICHLET, H.HS_SIDE_DIRICHLET)
+        s.set_precision(H.HS_MIXED, 1)
+        with pytest.raises(H.HsError) as e:
+            s.set_sides(H.HS_SIDE_DN, H.HS_SIDE_DIRICHLET)
+        assert e.value.status == H.HS_ERR_UNSUPPORTED
+        with pytest.raises(H.HsError) as e:
+            s.set_precision(H.HS_MIXED, 9)
+        assert e.value.status == H.HS_ERR_INVALID_ARG
+    finally:
+        s.close()
