@@ -25,7 +25,7 @@ from oracle import hs_oracle as O
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(37, 13, 70), (70, 20, 33), (5, 4, 3), (1, 2, 1)]
+SHAPES = [(37, 13, 70), (70, 20, 33), (70, 40, 9), (5, 4, 3), (1, 2, 1)]
 CASES = [(6, W.HELMHOLTZ), (4, W.HELMHOLTZ), (2, W.HELMHOLTZ), (4, W.CONVDIFF)]
 
 
