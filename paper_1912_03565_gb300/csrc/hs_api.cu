@@ -208,7 +208,7 @@ void free_plan(hs_plan_s *P) {
                     P->d_tables, P->d_w64, P->d_w32, P->d_dscr, P->d_stage_f, P->d_stage_u,
                     P->d_stage_bnd, P->d_fac32, P->d_coef_df, P->d_Fdf, P->d_Udf, P->d_rhs_df,
                     P->d_skip, P->d_ytmp, P->d_stage_u1, P->d_stage_f1, P->d_stage_bnd1,
-                    P->d_gemm[0], P->d_gemm[1], P->d_gemm_err};
+                    P->d_gemm[0], P->d_gemm[1], P->d_gemm_err, P->d_ghost};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->have_up) {
@@ -739,6 +739,10 @@ hs_status hs_plan_ex(hs_plan_t *out, int Nx, int Ny, int Nz, double Lx, double L
         (precision == HS_MIXED && (st = dev_alloc(P, &P->d_fac32, 3 * nint))) ||
         (precision == HS_MIXED && (st = dev_alloc(P, &P->d_coef_df, (size_t)Nz * 12))) ||
         (precision == HS_MIXED && (st = dev_alloc(P, &P->d_rhs_df, 2 * ((size_t)Nz + 2)))) ||
+        (precision == HS_MIXED && order == 6 &&
+         (st = dev_alloc(P, &P->d_ghost,
+                         2 * (((size_t)Nz + 2) * (Ny + 2) + ((size_t)Nz + 2) * (Nx + 2) +
+                              ((size_t)Ny + 2) * (Nx + 2))))) ||
         (st = build_tables(P))) {
         free_plan(P);
         return st;

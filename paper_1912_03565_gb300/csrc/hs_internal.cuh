@@ -91,6 +91,8 @@ struct hs_plan_s {
     float *d_fac32;     // the same rounded to FP32 (mixed path, well-conditioned plans)
     float2 *d_coef_df;  // [Nz][12] coefficients as FP32 pairs (double-float residual)
     int resid_xy;       // b_nu = c_nu on every row: the residual merges x- and y-neighbour sums
+    double *d_ghost;    // ghost nodes of the 6th-order mixed right-hand side (FP64 f):
+                        // [2][Nz+2][Ny+2] (x faces), [2][Nz+2][Nx+2] (y), [2][Ny+2][Nx+2] (z)
     float4 *d_rhs_df;   // [2][Nz+2] double-float RHS weights.  [0]: 6th order (67/120 - h^2 K/20,
                         // h^3 K_z/120); CD (0, h gamma/24).  [1] (sum-factorised kernel):
                         // 6th order (h^2 (67/120 - h^2 K/20), h^5 K_z/120); CD (0, h^3 gamma/24)

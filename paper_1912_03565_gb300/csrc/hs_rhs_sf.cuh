@@ -114,7 +114,6 @@ template <typename T, typename E, int H, int PER, int HX>
 __device__ __noinline__ void sf_convert_edge(const RhsArgs &a, const T *f, const T *rs, E *dst,
                                              const int *soff, const int *kind, int pl, int i0,
                                              int j0) {
-    const double h2 = a.hz * a.hz;
     const bool zghost = pl < 0 || pl > a.Nz + 1;
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
@@ -136,12 +135,48 @@ __device__ __noinline__ void sf_convert_edge(const RhsArgs &a, const T *f, const
             const T *fnn = static_cast<const T *>(a.b.fnn[face]);
             const size_t fi = face < 2 ? (size_t)pl * (a.Ny + 2) + (j0 - H + ey)
                                        : (size_t)pl * (a.Nx + 2) + (i0 - H + ex);
+            // (h^2 formed here: FP64 issues at a small fraction of the FP32 rate,
+            // and every thread of a face tile converts a plane at every step)
             v = 2.0 * (double)rs[e + step] - (double)rs[e + 2 * step] +
-                (fnn ? h2 * (double)__ldg(fnn + fi) : 0.0);
+                (fnn ? (a.hz * a.hz) * (double)__ldg(fnn + fi) : 0.0);
         }
         const dfloat d = df_split_bits(v);
         if constexpr (sizeof(E) == 8) dst[e] = make_float2(d.hi, d.lo);
         else dst[e] = d.hi;
+    }
+}
+
+// Raw-plane loads of one node plane for a tile that touches an x or y face, or
+// of a ghost plane beyond a z face, when the ghost nodes were precomputed
+// (RhsArgs::ghost, FP64 f): nodes from f, ghost nodes from the ghost arrays,
+// zeros where the stencil never reads (corners).  The raw plane then holds
+// every value the march reads, so it takes the plain conversion.
+template <typename T, int H, int PER, int HX>
+__device__ __noinline__ void sf_issue_ghost(const RhsArgs &a, const T *f, T *dst,
+                                            const int *soff, const int *goff, const int *kind,
+                                            int pl, int i0, int j0) {
+    const size_t sy = (size_t)(a.Nx + 2), sz = sy * (a.Ny + 2);
+    const double *gx = a.ghost;
+    const double *gy = gx + 2 * (size_t)(a.Nz + 2) * (a.Ny + 2);
+    const double *gz = gy + 2 * (size_t)(a.Nz + 2) * (a.Nx + 2);
+    const bool zghost = pl < 0 || pl > a.Nz + 1;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int kq = kind[q];
+        if (kq == SF_K_SKIP) continue;
+        const int e = soff[q];
+        const int ey = e / HX, ex = e - ey * HX;
+        const void *src = nullptr;
+        if (zghost) {
+            if (kq == SF_K_NODE) src = gz + (pl < 0 ? 0 : sz) + goff[q];
+        } else if (kq == SF_K_NODE) {
+            src = f + (size_t)pl * sz + goff[q];
+        } else if (kq == SF_K_XLO || kq == SF_K_XHI) {
+            src = gx + ((size_t)(kq == SF_K_XHI ? a.Nz + 2 : 0) + pl) * (a.Ny + 2) + (j0 - H + ey);
+        } else if (kq == SF_K_YLO || kq == SF_K_YHI) {
+            src = gy + ((size_t)(kq == SF_K_YHI ? a.Nz + 2 : 0) + pl) * (a.Nx + 2) + (i0 - H + ex);
+        }
+        cp_async<sizeof(T)>(dst + e, src ? src : static_cast<const void *>(f), src != nullptr);
     }
 }
 
@@ -156,7 +191,11 @@ __device__ __noinline__ void sf_convert_edge(const RhsArgs &a, const T *f, const
 // into the pair ring (FP64 values split into pairs with integer operations).
 // Ghost nodes beyond an x or y face, 2 f_0 - f_1 + h^2 (f_nn)_face, are formed
 // during that conversion from the raw plane; the ghost planes beyond a z face
-// are formed node by node (node_df).  f is never written during a launch, so
+// are formed node by node (node_or_ghost).  When RhsArgs::ghost holds them
+// precomputed (6th order, FP64 f; stand-alone solves) they are loaded like
+// nodes instead, and every plane takes the plain conversion: face tiles then
+// cost about what interior tiles do (the in-tile formation is FP64 work on the
+// critical path of every plane step).  f is never written during a launch, so
 // the L1-cached copy is safe in the persistent batch kernel too.
 template <int KIND, typename T>
 __device__ __forceinline__ void rhs_sf_tile(const RhsArgs &a, const T *__restrict__ f,
@@ -164,6 +203,7 @@ __device__ __forceinline__ void rhs_sf_tile(const RhsArgs &a, const T *__restric
                                             const float4 *__restrict__ rw, float2 W,
                                             unsigned char *smem, int bx, int by, int bz) {
     constexpr int H = KIND == SF_O6 ? 2 : 1;
+    constexpr bool GHOSTS = H == 2 && sizeof(T) == 8;
     typedef SfGeom<H> G;
     constexpr bool PAIR = sf_pair_ring<H, T>();
     typedef typename std::conditional<PAIR, float2, float>::type E;
@@ -202,16 +242,24 @@ __device__ __forceinline__ void rhs_sf_tile(const RhsArgs &a, const T *__restric
     constexpr int HALO = G::HX * G::HY;
     // stream index k: node plane lbeg - H + k; kend: last index
     const int kend = lend - lbeg + 2 * H;
+    // precomputed ghost nodes (6th order, FP64 f): every plane takes the plain
+    // conversion, face tiles and z-ghost planes load through sf_issue_ghost
+    const bool ghosts = GHOSTS && a.ghost != nullptr;
     auto issue = [&](int k) {
         const int pl = lbeg - H + k;
-        if (k <= kend && pl >= 0 && pl <= a.Nz + 1) {
+        const bool zin = pl >= 0 && pl <= a.Nz + 1;
+        if (k <= kend && (zin || ghosts)) {
             T *dst = raw + (k & (SF_RAW - 1)) * HALO;
-            const T *src = f + (size_t)pl * sz;
+            if (ghosts && (!xy_in || !zin)) {
+                sf_issue_ghost<T, H, G::PER, G::HX>(a, f, dst, soff, goff, kind, pl, i0, j0);
+            } else {
+                const T *src = f + (size_t)pl * sz;
 #pragma unroll
-            for (int q = 0; q < G::PER; ++q) {
-                if (kind[q] == SF_K_SKIP) continue;
-                const bool v = kind[q] == SF_K_NODE;
-                cp_async<sizeof(T)>(dst + soff[q], v ? src + goff[q] : f, v);
+                for (int q = 0; q < G::PER; ++q) {
+                    if (kind[q] == SF_K_SKIP) continue;
+                    const bool v = kind[q] == SF_K_NODE;
+                    cp_async<sizeof(T)>(dst + soff[q], v ? src + goff[q] : f, v);
+                }
             }
         }
         cp_async_commit();
@@ -221,7 +269,7 @@ __device__ __forceinline__ void rhs_sf_tile(const RhsArgs &a, const T *__restric
         const int pl = lbeg - H + k;
         E *dst = &ring[slot][0][0];
         const T *rs = raw + (k & (SF_RAW - 1)) * HALO;
-        if (!xy_in || pl < 0 || pl > a.Nz + 1) {
+        if (!ghosts && (!xy_in || pl < 0 || pl > a.Nz + 1)) {
             sf_convert_edge<T, E, H, G::PER, G::HX>(a, f, rs, dst, soff, kind, pl, i0, j0);
             return;
         }

@@ -386,6 +386,7 @@ struct RhsArgs {
     int has_faces;       // 0: every Dirichlet face is zero, so the lifting vanishes
     int bz0;             // first z-tile of the launch (slab launches of the tiled kernels)
     int zt;              // planes per z-tile of the sum-factorised kernel (runtime depth)
+    const double *ghost; // precomputed ghost nodes (layout of hs_plan_s::d_ghost), or null
     DevBoundary b;
 };
 
@@ -471,7 +472,6 @@ template <typename T>
 __device__ double node_or_ghost(const RhsArgs &a, const T *f, int i, int j, int l) {
     const int Nx = a.Nx, Ny = a.Ny, Nz = a.Nz;
     const size_t sy = (size_t)(Nx + 2), sz = sy * (Ny + 2);
-    const double h2 = a.hz * a.hz;
     const bool xin = i >= 0 && i <= Nx + 1, yin = j >= 0 && j <= Ny + 1, zin = l >= 0 && l <= Nz + 1;
     if (xin && yin && zin) return ld(f, (size_t)l * sz + (size_t)j * sy + i);
     // ghosts exist one node beyond a face, along that face's normal only
@@ -480,21 +480,21 @@ __device__ double node_or_ghost(const RhsArgs &a, const T *f, int i, int j, int 
         const T *fnn = static_cast<const T *>(a.b.fnn[i == -1 ? 0 : 1]);
         const size_t r = (size_t)l * sz + (size_t)j * sy;
         return 2.0 * ld(f, r + i0) - ld(f, r + i1) +
-               (fnn ? h2 * ld(fnn, (size_t)l * (Ny + 2) + j) : 0.0);
+               (fnn ? (a.hz * a.hz) * ld(fnn, (size_t)l * (Ny + 2) + j) : 0.0);
     }
     if (xin && !yin && zin && (j == -1 || j == Ny + 2)) {
         const int j0 = (j == -1) ? 0 : Ny + 1, j1 = (j == -1) ? 1 : Ny;
         const T *fnn = static_cast<const T *>(a.b.fnn[j == -1 ? 2 : 3]);
         const size_t r = (size_t)l * sz + i;
         return 2.0 * ld(f, r + (size_t)j0 * sy) - ld(f, r + (size_t)j1 * sy) +
-               (fnn ? h2 * ld(fnn, (size_t)l * (Nx + 2) + i) : 0.0);
+               (fnn ? (a.hz * a.hz) * ld(fnn, (size_t)l * (Nx + 2) + i) : 0.0);
     }
     if (xin && yin && !zin && (l == -1 || l == Nz + 2)) {
         const int l0 = (l == -1) ? 0 : Nz + 1, l1 = (l == -1) ? 1 : Nz;
         const T *fnn = static_cast<const T *>(a.b.fnn[l == -1 ? 4 : 5]);
         const size_t r = (size_t)j * sy + i;
         return 2.0 * ld(f, (size_t)l0 * sz + r) - ld(f, (size_t)l1 * sz + r) +
-               (fnn ? h2 * ld(fnn, (size_t)j * (Nx + 2) + i) : 0.0);
+               (fnn ? (a.hz * a.hz) * ld(fnn, (size_t)j * (Nx + 2) + i) : 0.0);
     }
     return 0.0;  // never read by an interior point
 }

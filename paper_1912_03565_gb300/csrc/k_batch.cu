@@ -364,6 +364,7 @@ hs_status hs_batch_create(hs_batch_t *out, const hs_problem_desc *probs, int npr
             ra.rc = P->d_rhs_df;
             ra.has_faces = 0;
             ra.zt = SFZ;   // the persistent kernel's tile grid (W.gz) uses full-depth tiles
+            ra.ghost = nullptr;   // ghost nodes formed in the tile (same values)
             W.f = static_cast<const unsigned char *>(d.f) + (size_t)r * fcount * esz;
             W.u = d.u + (size_t)r * n;
             if (r == 0) {

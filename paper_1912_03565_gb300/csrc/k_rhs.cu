@@ -199,6 +199,46 @@ __global__ void __launch_bounds__(RTX *RTY) rhs_tiled_kernel(RhsArgs a, const T 
     }
 }
 
+// Ghost nodes of the 6th-order right-hand side (one node beyond a face along
+// its normal, 2 f_0 - f_1 + h^2 (f_nn)_face: node_or_ghost), into the layout
+// of hs_plan_s::d_ghost: x faces for node planes pl0 .. pl1, y faces likewise,
+// and the z-lo / z-hi ghost planes when zlo / zhi.
+template <typename T>
+__global__ void __launch_bounds__(256) ghost_kernel(RhsArgs a, const T *__restrict__ f,
+                                                    double *__restrict__ g, int pl0, int pl1,
+                                                    int zlo, int zhi) {
+    const long np = pl1 - pl0 + 1;
+    const long nyx = (long)(a.Ny + 2), nxx = (long)(a.Nx + 2);
+    const long cx = 2 * np * nyx, cy = 2 * np * nxx, cz = nyx * nxx;
+    double *gx = g;
+    double *gy = gx + 2 * (size_t)(a.Nz + 2) * nyx;
+    double *gz = gy + 2 * (size_t)(a.Nz + 2) * nxx;
+    const long nzs = (long)(zlo != 0) + (zhi != 0);   // z faces to form
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < cx + cy + nzs * cz;
+         t += (long)gridDim.x * blockDim.x) {
+        if (t < cx) {
+            const int side = (int)(t / (np * nyx));
+            const long r = t - side * np * nyx;
+            const int pl = pl0 + (int)(r / nyx), j = (int)(r % nyx);
+            gx[((size_t)side * (a.Nz + 2) + pl) * nyx + j] =
+                node_or_ghost<T>(a, f, side ? a.Nx + 2 : -1, j, pl);
+        } else if (t < cx + cy) {
+            const long u = t - cx;
+            const int side = (int)(u / (np * nxx));
+            const long r = u - side * np * nxx;
+            const int pl = pl0 + (int)(r / nxx), i = (int)(r % nxx);
+            gy[((size_t)side * (a.Nz + 2) + pl) * nxx + i] =
+                node_or_ghost<T>(a, f, i, side ? a.Ny + 2 : -1, pl);
+        } else {
+            const long u = t - cx - cy;
+            const int side = (zlo && u < cz) ? 0 : 1;
+            const long r = u - (u < cz ? 0 : cz);
+            const int j = (int)(r / nxx), i = (int)(r % nxx);
+            gz[(size_t)side * cz + r] = node_or_ghost<T>(a, f, i, j, side ? a.Nz + 2 : -1);
+        }
+    }
+}
+
 // Mixed path, nodal f: the sum-factorised double-float tile (hs_rhs_sf.cuh).
 // CTAs per SM the register allocation of the sum-factorised kernel is sized for
 #ifndef HS_RHS_SF_MINB
@@ -370,24 +410,83 @@ hs_status hs_upload_rhs(hs_plan_s *P, const void *fh, void *fd, int chunks, int 
     return HS_OK;
 }
 
-// Planes per z-tile of the mixed path's z-marching kernels: 32, or fewer when the
-// problem would give less than two waves of CTAs (3 per SM) at that depth -- small
-// problems (batches of 63^3 ... 127^3) need the parallelism more than the shorter
-// z-halo overhead.
-int hs_sf_zdepth(const hs_plan_s *P) {
+namespace {
+
+// Planes per z-slab of a z-marching kernel launched as (xy tiles) x (slabs)
+// CTAs: the depth whose CTAs fill whole waves best.  A CTA's time is taken as
+// its slab's planes plus `halo` planes on each side and about two planes of
+// prologue, and a launch as (waves of CTAs) x (one CTA's time), waves =
+// ceil(CTAs / (resident CTAs per SM x SMs)).  Slabs hold 4 to 64 planes: short
+// CTAs let the block scheduler even out tiles that cost more (those touching a
+// face form ghost nodes in FP64), so of two depths within 2 % of each other the
+// shorter is taken.  At 255^3 this gives 7 slabs of 37 planes (4 waves of the
+// right-hand side, 3 of the residual) instead of 8 of 32 (4.5 and 3.4 waves).
+int zmarch_depth(long tiles, int Nz, int halo, int resident, int sms) {
+    const long slots = (long)(resident > 0 ? resident : 1) * (sms > 0 ? sms : 1);
+    const int zmin = Nz < 4 ? Nz : 4;
+    int best = Nz < 64 ? Nz : 64;
+    long best_cost = -1;
+    for (int ns = 1; ns <= Nz; ++ns) {
+        const int zt = (Nz + ns - 1) / ns;
+        if (zt > 64) continue;
+        if (zt < zmin) break;
+        const long ctas = tiles * ((Nz + zt - 1) / zt);
+        const long cost = ((ctas + slots - 1) / slots) * (zt + 2 * halo + 2);
+        if (best_cost < 0 || cost * 50 <= best_cost * 51) {
+            if (best_cost < 0 || cost < best_cost) best_cost = cost;
+            best = zt;
+        }
+    }
+    return best;
+}
+
+int sm_count(const hs_plan_s *P) {
     static int sms = 0;
     if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device) !=
                         cudaSuccess) {
         cudaGetLastError();
         sms = 148;
     }
-    const long xy = (long)((P->Nx + SFX - 1) / SFX) * ((P->Ny + SFY - 1) / SFY);
-    int zt = SFZ;
-    while (zt > 4 && xy * ((P->Nz + zt - 1) / zt) < 2L * 3 * sms) zt /= 2;
-    return zt;
+    return sms;
 }
 
-int hs_rhs_tile_planes(const hs_plan_s *P, int out_df) { return out_df ? hs_sf_zdepth(P) : RZ; }
+template <typename K>
+int resident_ctas(K kernel, int threads) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 2;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+// depth of the mixed right-hand side (rhs_sf_kernel; the FP64-f instance)
+int sf_rhs_depth(const hs_plan_s *P) {
+    static int res[4] = {0, 0, 0, 0};
+    const int kind = P->equation == HS_CONVDIFF ? SF_CD
+                                                : (P->order == 6 ? SF_O6 : (P->order == 4 ? SF_O4 : SF_O2));
+    if (res[kind] == 0)
+        res[kind] = kind == SF_CD   ? resident_ctas(rhs_sf_kernel<SF_CD, double>, SFX * SFY)
+                    : kind == SF_O6 ? resident_ctas(rhs_sf_kernel<SF_O6, double>, SFX * SFY)
+                    : kind == SF_O4 ? resident_ctas(rhs_sf_kernel<SF_O4, double>, SFX * SFY)
+                                    : resident_ctas(rhs_sf_kernel<SF_O2, double>, SFX * SFY);
+    const long tiles = (long)((P->Nx + SFX - 1) / SFX) * ((P->Ny + SFY - 1) / SFY);
+    return zmarch_depth(tiles, P->Nz, kind == SF_O6 ? 2 : 1, res[kind], sm_count(P));
+}
+
+// depth of the pair residual (residual_sf_kernel)
+int sf_resid_depth(const hs_plan_s *P) {
+    static int res = 0;
+    if (res == 0) res = resident_ctas(residual_sf_kernel<true>, RSX * RSY);
+    const long tiles = (long)((P->Nx + RSX - 1) / RSX) * ((P->Ny + RSY - 1) / RSY);
+    return zmarch_depth(tiles, P->Nz, 1, res, sm_count(P));
+}
+
+}  // namespace
+
+int hs_sf_zdepth(const hs_plan_s *P) { return sf_resid_depth(P); }
+
+int hs_rhs_tile_planes(const hs_plan_s *P, int out_df) { return out_df ? sf_rhs_depth(P) : RZ; }
 
 hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_kind,
                         const DevBoundary &b, void *F, int out_df, cudaStream_t s, double *f2,
@@ -405,6 +504,7 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
     a.c1 = P->d_c1;
     a.rc = P->d_rhs_df;
     a.b = b;
+    a.ghost = nullptr;
     a.has_faces = 0;
     for (int k = 0; k < 6; ++k)
         if (b.face[k]) a.has_faces = 1;
@@ -416,6 +516,21 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
         const int cnt = nbz < 0 ? tz - a.bz0 : nbz;
         if (cnt <= 0) return HS_OK;
         if (out_df) {
+            a.ghost = nullptr;
+            if (f_dtype == HS_F64 && P->d_ghost && P->order == 6 &&
+                P->equation == HS_HELMHOLTZ) {
+                // the ghost nodes of the node planes these z-tiles read
+                const int lo = 1 + a.bz0 * TZ - 2;
+                const int hi = (a.bz0 + cnt) * TZ + 2;
+                const int pl0 = lo < 0 ? 0 : lo, pl1 = hi > P->Nz + 1 ? P->Nz + 1 : hi;
+                const long work = 2L * (pl1 - pl0 + 1) * (P->Nx + P->Ny + 4) +
+                                  (long)((lo < 0) + (hi > P->Nz + 1)) * (P->Nx + 2) * (P->Ny + 2);
+                const unsigned gb = (unsigned)((work + 255) / 256 < 4096 ? (work + 255) / 256 : 4096);
+                ghost_kernel<double><<<gb, 256, 0, s>>>(a, static_cast<const double *>(f),
+                                                        P->d_ghost, pl0, pl1, lo < 0,
+                                                        hi > P->Nz + 1);
+                a.ghost = P->d_ghost;
+            }
             if (f_dtype == HS_F64)
                 launch_rhs_sf<double>(P, a, static_cast<const double *>(f), static_cast<float *>(F),
                                       f2, cnt, s);

@@ -55,6 +55,7 @@ def test_stage_bytes_and_launch_counts():
     assert bench.stage_bytes("mixed", 1, thomas_fp32=False)["thomas"] == 64.0
     assert bench.launches_per_solve("mixed", 1) == 12
     assert bench.launches_per_solve("fp64", 0) == 6
+    assert bench.launches_per_solve("mixed", 1, ghost=True) == 13
     assert set(bench.WORKLOADS) >= {"cube255_o6", "cube1023_o6", "cd511x8"}
 
 
