@@ -644,6 +644,14 @@ __device__ __forceinline__ bool residual_use_f64(const double *norms, int m) {
 // 2-3 x CH loads in flight.
 constexpr int CH = 16;
 
+// Loads of the cached factors in the pipelined sweeps: each factor is read once
+// per solve, so it is loaded with the streaming (evict-first) policy and does not
+// push the forward sweep's values, which the backward sweep reads again, out of L2.
+template <typename Tf>
+__device__ __forceinline__ Tf ldfac(const Tf *p) {
+    return __ldcs(p);
+}
+
 // One z-solve with cached factors.  Td: data type (in place); Tf: factor type;
 // Ts: type of the forward-sweep values (kept in `scratch` when it is not null,
 // else in `data`); Ta: arithmetic type.
@@ -725,8 +733,8 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
                 for (int k = 0; k < CH; ++k) {
                     const size_t o = (size_t)k * plane + idx;
                     r[k] = (Ta)ldc<COH>(data + o);
-                    a[k] = (Ta)alpha[o];
-                    b[k] = (Ta)beta[o];
+                    a[k] = (Ta)ldfac(alpha + o);
+                    b[k] = (Ta)ldfac(beta + o);
                 }
             }
             for (int c = 0; c < nfull; ++c) {
@@ -736,8 +744,8 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
                 for (int k = 0; k < CH; ++k) {
                     const size_t o = (size_t)((c + 1) * CH + k) * plane + idx;
                     r2[k] = more ? (Ta)ldc<COH>(data + o) : (Ta)0;
-                    a2[k] = more ? (Ta)alpha[o] : (Ta)0;
-                    b2[k] = more ? (Ta)beta[o] : (Ta)0;
+                    a2[k] = more ? (Ta)ldfac(alpha + o) : (Ta)0;
+                    b2[k] = more ? (Ta)ldfac(beta + o) : (Ta)0;
                 }
     #pragma unroll
                 for (int k = 0; k < CH; ++k) {
@@ -762,7 +770,7 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
         }
         for (int l = nfull * CH; l < Nz; ++l) {
             const size_t o = (size_t)l * plane + idx;
-            d = (Ta)alpha[o] * (Ta)ldc<COH>(data + o) - (Ta)beta[o] * d;
+            d = (Ta)ldfac(alpha + o) * (Ta)ldc<COH>(data + o) - (Ta)ldfac(beta + o) * d;
             if (scratch)
                 scratch[o] = d;
             else
@@ -777,7 +785,7 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
         for (int t = 0; t < ntail; ++t, --top) {
             const size_t o = (size_t)top * plane + idx;
             const Ta dd = scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o);
-            w = dd - (Ta)cpr[o] * w;
+            w = dd - (Ta)ldfac(cpr + o) * w;
             data[o] = (Td)w;
         }
         const int nbf = nb / CH;           // full chunks, top planes first
@@ -788,7 +796,7 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
                 for (int k = 0; k < CH; ++k) {
                     const size_t o = (size_t)(top - k) * plane + idx;
                     dv[k] = scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o);
-                    cc[k] = (Ta)cpr[o];
+                    cc[k] = (Ta)ldfac(cpr + o);
                 }
             }
             for (int c = 0; c < nbf; ++c, top -= CH) {
@@ -798,7 +806,7 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
                 for (int k = 0; k < CH; ++k) {
                     const size_t o = (size_t)(more ? top - CH - k : top - k) * plane + idx;
                     dv2[k] = more ? (scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o)) : (Ta)0;
-                    cc2[k] = more ? (Ta)cpr[o] : (Ta)0;
+                    cc2[k] = more ? (Ta)ldfac(cpr + o) : (Ta)0;
                 }
     #pragma unroll
                 for (int k = 0; k < CH; ++k) {
