@@ -30,9 +30,8 @@ constexpr int RSX = 32, RSY = 8, RSZ = 32;
 constexpr int RSHX = RSX + 2, RSHY = RSY + 2;
 
 struct PSum {
-    float C, Ce, X, Xe, Y, Ye;   // hi sums and their two_sum errors (X: X + Y when merged)
-    float U;                     // centre hi
-    float Clo, Xlo, Ylo, Ulo;    // sums of the lo parts
+    float C, X, Y, U;   // hi sums (X: X + Y when merged) and the centre hi
+    float Cl, Xl, Yl, Ul;   // the rest: two_sum errors plus the sums of the lo parts
 };
 
 // In-plane sums of the column at tile position (tx, ty) of one plane slot.
@@ -48,23 +47,22 @@ __device__ __forceinline__ void resid_plane_sums(const float2 *sl, int tx, int t
     df_two_sum(g.x, d.x, s2, e2);
     df_two_sum(s, s2, s3, e3);
     ps.C = s3;
-    ps.Ce = e3 + (e + e2);
-    ps.Clo = (a.y + b.y) + (g.y + d.y);
+    ps.Cl = (e3 + (e + e2)) + ((a.y + b.y) + (g.y + d.y));
     if (XY) {
         df_two_sum(xm.x, xp.x, s, e);
         df_two_sum(ym.x, yp.x, s2, e2);
         df_two_sum(s, s2, s3, e3);
         ps.X = s3;
-        ps.Xe = e3 + (e + e2);
-        ps.Xlo = (xm.y + xp.y) + (ym.y + yp.y);
+        ps.Xl = (e3 + (e + e2)) + ((xm.y + xp.y) + (ym.y + yp.y));
     } else {
-        df_two_sum(xm.x, xp.x, ps.X, ps.Xe);
-        df_two_sum(ym.x, yp.x, ps.Y, ps.Ye);
-        ps.Xlo = xm.y + xp.y;
-        ps.Ylo = ym.y + yp.y;
+        float xe, ye;
+        df_two_sum(xm.x, xp.x, ps.X, xe);
+        df_two_sum(ym.x, yp.x, ps.Y, ye);
+        ps.Xl = xe + (xm.y + xp.y);
+        ps.Yl = ye + (ym.y + yp.y);
     }
     ps.U = u.x;
-    ps.Ulo = u.y;
+    ps.Ul = u.y;
 }
 
 // r_l = F_l - A U_l at one point from the plane sums of rows l - 1, l, l + 1.
@@ -79,10 +77,10 @@ __device__ __forceinline__ float resid_point(const float2 *__restrict__ cf, int 
         const int ll = l + nu - 1;
         if (ll < 0 || ll >= Nz) continue;
         const PSum &ps = *q[nu];
-        acc_term(S, E, cf[nu * 4 + 0], ps.C, ps.Ce, ps.Clo);
-        acc_term(S, E, cf[nu * 4 + 1], ps.X, ps.Xe, ps.Xlo);
-        if (!XY) acc_term(S, E, cf[nu * 4 + 2], ps.Y, ps.Ye, ps.Ylo);
-        acc_term(S, E, cf[nu * 4 + 3], ps.U, 0.f, ps.Ulo);
+        acc_term(S, E, cf[nu * 4 + 0], ps.C, ps.Cl);
+        acc_term(S, E, cf[nu * 4 + 1], ps.X, ps.Xl);
+        if (!XY) acc_term(S, E, cf[nu * 4 + 2], ps.Y, ps.Yl);
+        acc_term(S, E, cf[nu * 4 + 3], ps.U, ps.Ul);
     }
     dfloat au;
     df_fast_two_sum(S, E, au.hi, au.lo);

@@ -501,18 +501,18 @@ __device__ double node_or_ghost(const RhsArgs &a, const T *f, int i, int j, int 
 
 // =================================================================== residual
 // One term of the double-float residual's row sum (hs_resid_sf.cuh): the
-// coefficient pair k times the plane sum v (hi sum, its two_sum error ve and
-// the sum of the lo parts vlo) added to the unnormalised pair (S, E): the
-// leading product exactly (two_prod into two_sum), cross terms in FP32.
-__device__ __forceinline__ void acc_term(float &S, float &E, float2 k, float v, float ve,
-                                         float vlo) {
-    // S + E += (k.x + k.y) * (v + ve + vlo)
+// coefficient pair k times the plane sum v + vl (hi sum v; vl its two_sum error
+// plus the sum of the lo parts, formed once per plane) added to the
+// unnormalised pair (S, E): the leading product exactly (two_prod into two_sum),
+// cross terms in FP32.
+__device__ __forceinline__ void acc_term(float &S, float &E, float2 k, float v, float vl) {
+    // S + E += (k.x + k.y) * (v + vl)
     const float p = k.x * v;
     const float pe = fmaf(k.x, v, -p);
     float s, t;
     df_two_sum(S, p, s, t);
     S = s;
-    E += t + pe + fmaf(k.x, ve + vlo, k.y * v);
+    E += t + pe + fmaf(k.x, vl, k.y * v);
 }
 
 constexpr int QTX = 32, QTY = 8, QZ = 16;
@@ -644,18 +644,22 @@ __device__ __forceinline__ bool residual_use_f64(const double *norms, int m) {
 // 2-3 x CH loads in flight.
 constexpr int CH = 16;
 
-// Loads of the cached factors in the pipelined sweeps: each factor is read once
-// per solve, so it is loaded with the streaming (evict-first) policy and does not
-// push the forward sweep's values, which the backward sweep reads again, out of L2.
-template <typename Tf>
+// Loads of the cached factors in the pipelined sweeps.  STREAM: each factor is
+// read once per solve, so it is loaded with the streaming (evict-first) policy and
+// does not push the forward sweep's values, which the backward sweep reads again,
+// out of L2 -- worth it where those values fit in L2 (255^3: 405 -> 299 MB of DRAM
+// traffic per launch); at 511^3 and above they cannot, and plain loads are faster.
+template <bool STREAM, typename Tf>
 __device__ __forceinline__ Tf ldfac(const Tf *p) {
-    return __ldcs(p);
+    if constexpr (STREAM) return __ldcs(p);
+    else return *p;
 }
 
 // One z-solve with cached factors.  Td: data type (in place); Tf: factor type;
 // Ts: type of the forward-sweep values (kept in `scratch` when it is not null,
 // else in `data`); Ta: arithmetic type.
-template <typename Td, typename Tf, typename Ta, bool COH = false, bool PIPE = true, int CH = hs_tiles::CH>
+template <typename Td, typename Tf, typename Ta, bool COH = false, bool PIPE = true, int CH = hs_tiles::CH,
+          bool STREAM = false>
 __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, Td *data,
                                               Ta *scratch, const Tf *cpr, const Tf *alpha,
                                               const Tf *beta) {
@@ -733,8 +737,8 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
                 for (int k = 0; k < CH; ++k) {
                     const size_t o = (size_t)k * plane + idx;
                     r[k] = (Ta)ldc<COH>(data + o);
-                    a[k] = (Ta)ldfac(alpha + o);
-                    b[k] = (Ta)ldfac(beta + o);
+                    a[k] = (Ta)ldfac<STREAM>(alpha + o);
+                    b[k] = (Ta)ldfac<STREAM>(beta + o);
                 }
             }
             for (int c = 0; c < nfull; ++c) {
@@ -744,8 +748,8 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
                 for (int k = 0; k < CH; ++k) {
                     const size_t o = (size_t)((c + 1) * CH + k) * plane + idx;
                     r2[k] = more ? (Ta)ldc<COH>(data + o) : (Ta)0;
-                    a2[k] = more ? (Ta)ldfac(alpha + o) : (Ta)0;
-                    b2[k] = more ? (Ta)ldfac(beta + o) : (Ta)0;
+                    a2[k] = more ? (Ta)ldfac<STREAM>(alpha + o) : (Ta)0;
+                    b2[k] = more ? (Ta)ldfac<STREAM>(beta + o) : (Ta)0;
                 }
     #pragma unroll
                 for (int k = 0; k < CH; ++k) {
@@ -770,7 +774,7 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
         }
         for (int l = nfull * CH; l < Nz; ++l) {
             const size_t o = (size_t)l * plane + idx;
-            d = (Ta)ldfac(alpha + o) * (Ta)ldc<COH>(data + o) - (Ta)ldfac(beta + o) * d;
+            d = (Ta)ldfac<STREAM>(alpha + o) * (Ta)ldc<COH>(data + o) - (Ta)ldfac<STREAM>(beta + o) * d;
             if (scratch)
                 scratch[o] = d;
             else
@@ -785,7 +789,7 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
         for (int t = 0; t < ntail; ++t, --top) {
             const size_t o = (size_t)top * plane + idx;
             const Ta dd = scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o);
-            w = dd - (Ta)ldfac(cpr + o) * w;
+            w = dd - (Ta)ldfac<STREAM>(cpr + o) * w;
             data[o] = (Td)w;
         }
         const int nbf = nb / CH;           // full chunks, top planes first
@@ -796,7 +800,7 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
                 for (int k = 0; k < CH; ++k) {
                     const size_t o = (size_t)(top - k) * plane + idx;
                     dv[k] = scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o);
-                    cc[k] = (Ta)ldfac(cpr + o);
+                    cc[k] = (Ta)ldfac<STREAM>(cpr + o);
                 }
             }
             for (int c = 0; c < nbf; ++c, top -= CH) {
@@ -806,7 +810,7 @@ __device__ __forceinline__ void thomas_column(int Nz, size_t plane, size_t idx, 
                 for (int k = 0; k < CH; ++k) {
                     const size_t o = (size_t)(more ? top - CH - k : top - k) * plane + idx;
                     dv2[k] = more ? (scratch ? ldc<COH>(scratch + o) : (Ta)ldc<COH>(data + o)) : (Ta)0;
-                    cc2[k] = more ? (Ta)ldfac(cpr + o) : (Ta)0;
+                    cc2[k] = more ? (Ta)ldfac<STREAM>(cpr + o) : (Ta)0;
                 }
     #pragma unroll
                 for (int k = 0; k < CH; ++k) {

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) thomas32_kernel(int Nx, int Ny, int Nz,
 // recurrence, in place (Fhat in, W out).  The error this adds to the fast
 // solve, ~2^-24 times the condition of the z-system, is removed by the
 // refinement sweeps like the FP32 transform error.
-template <int CHK, bool PIPE, int NT>
+template <int CHK, bool PIPE, int NT, bool STREAM>
 __global__ void __launch_bounds__(NT) thomas_f32_kernel(int Nx, int Ny, int Nz,
                                                         float *__restrict__ data,
                                                         const float *__restrict__ fac,
@@ -126,17 +126,27 @@ __global__ void __launch_bounds__(NT) thomas_f32_kernel(int Nx, int Ny, int Nz,
     const size_t plane = (size_t)Nx * Ny;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= plane) return;
-    thomas_column<float, float, float, false, PIPE, CHK>(Nz, plane, idx, data, (float *)nullptr,
-                                                         fac, fac + (size_t)Nz * plane,
-                                                         fac + 2 * (size_t)Nz * plane);
+    thomas_column<float, float, float, false, PIPE, CHK, STREAM>(
+        Nz, plane, idx, data, (float *)nullptr, fac, fac + (size_t)Nz * plane,
+        fac + 2 * (size_t)Nz * plane);
+}
+
+// Streaming factor loads where the forward sweep's values (the whole data array,
+// FP32) fit in about three quarters of the 129 MB L2.
+bool stream_factors(const hs_plan_s *P) {
+    return (size_t)P->Nx * P->Ny * P->Nz * sizeof(float) <= ((size_t)96 << 20);
 }
 
 template <int CHK, bool PIPE, int NT>
 void launch_f32(const hs_plan_s *P, float *data, cudaStream_t s) {
     const size_t plane = (size_t)P->Nx * P->Ny;
     const unsigned blocks = (unsigned)((plane + NT - 1) / NT);
-    thomas_f32_kernel<CHK, PIPE, NT><<<blocks, NT, 0, s>>>(P->Nx, P->Ny, P->Nz, data, P->d_fac32,
-                                                          P->cur_skip);
+    if (stream_factors(P))
+        thomas_f32_kernel<CHK, PIPE, NT, true><<<blocks, NT, 0, s>>>(P->Nx, P->Ny, P->Nz, data,
+                                                                    P->d_fac32, P->cur_skip);
+    else
+        thomas_f32_kernel<CHK, PIPE, NT, false><<<blocks, NT, 0, s>>>(P->Nx, P->Ny, P->Nz, data,
+                                                                     P->d_fac32, P->cur_skip);
 }
 
 // Balanced mapping: a whole number of blocks per SM and the columns shared
@@ -156,8 +166,12 @@ void launch_f32_bal(const hs_plan_s *P, float *data, cudaStream_t s) {
     const size_t k = (per_sm + NTMAX - 1) / NTMAX;               // blocks per SM
     const unsigned blocks = (unsigned)(sms * k);
     const unsigned nt = (unsigned)(((plane + blocks - 1) / blocks + 31) / 32 * 32);
-    thomas_f32_kernel<CHK, true, NTMAX><<<blocks, nt, 0, s>>>(P->Nx, P->Ny, P->Nz, data,
-                                                             P->d_fac32, P->cur_skip);
+    if (stream_factors(P))
+        thomas_f32_kernel<CHK, true, NTMAX, true><<<blocks, nt, 0, s>>>(P->Nx, P->Ny, P->Nz, data,
+                                                                       P->d_fac32, P->cur_skip);
+    else
+        thomas_f32_kernel<CHK, true, NTMAX, false><<<blocks, nt, 0, s>>>(P->Nx, P->Ny, P->Nz, data,
+                                                                        P->d_fac32, P->cur_skip);
 }
 
 }  // namespace
