@@ -66,26 +66,31 @@ __device__ __forceinline__ void resid_plane_sums(const float2 *sl, int tx, int t
 }
 
 // r_l = F_l - A U_l at one point from the plane sums of rows l - 1, l, l + 1.
+// The row's coefficient pairs are read two at a time (16-byte loads).  r only
+// feeds the FP32 correction solve: it is formed as the exact difference of the
+// hi parts (two_sum) plus the low-order terms, rounded once to FP32 -- the same
+// error bound (about 2^-47 |F| + 2^-24 |r|) as a full pair subtraction.
 template <bool XY>
 __device__ __forceinline__ float resid_point(const float2 *__restrict__ cf, int l, int Nz,
                                              const PSum &pm, const PSum &p0, const PSum &pp,
                                              float2 Fl) {
     float S = 0.f, E = 0.f;
     const PSum *q[3] = {&pm, &p0, &pp};
+    const float4 *cf4 = reinterpret_cast<const float4 *>(cf);
 #pragma unroll
     for (int nu = 0; nu < 3; ++nu) {
         const int ll = l + nu - 1;
         if (ll < 0 || ll >= Nz) continue;
         const PSum &ps = *q[nu];
-        acc_term(S, E, cf[nu * 4 + 0], ps.C, ps.Cl);
-        acc_term(S, E, cf[nu * 4 + 1], ps.X, ps.Xl);
-        if (!XY) acc_term(S, E, cf[nu * 4 + 2], ps.Y, ps.Yl);
-        acc_term(S, E, cf[nu * 4 + 3], ps.U, ps.Ul);
+        const float4 ab = cf4[2 * nu], cd = cf4[2 * nu + 1];
+        acc_term(S, E, make_float2(ab.x, ab.y), ps.C, ps.Cl);
+        acc_term(S, E, make_float2(ab.z, ab.w), ps.X, ps.Xl);
+        if (!XY) acc_term(S, E, make_float2(cd.x, cd.y), ps.Y, ps.Yl);
+        acc_term(S, E, make_float2(cd.z, cd.w), ps.U, ps.Ul);
     }
-    dfloat au;
-    df_fast_two_sum(S, E, au.hi, au.lo);
-    const dfloat res = df_add_accurate(dfloat{Fl.x, Fl.y}, df_neg(au));
-    return res.hi + res.lo;
+    float d, de;
+    df_two_sum(Fl.x, -S, d, de);   // F_hi - S exactly
+    return d + (de + (Fl.y - E));
 }
 
 // Register-prefetch loader.  COH: F and U were written earlier in the same
