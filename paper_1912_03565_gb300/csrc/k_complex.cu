@@ -383,6 +383,7 @@ struct ZRhsArgs {
     const double *fnn[6];   // order 6: f_nn on the x-lo, x-hi ([2][Nz+2][Ny+2]), y-lo, y-hi
                             // ([2][Nz+2][Nx+2]), z-lo, z-hi ([2][Ny+2][Nx+2]) faces, or NULL
     const double2 *kk;      // order 6: [2][Nz+2] K and K_z at the nodes
+    double k20, k120;       // order 6: -h_z^4 / 20 and h_z^5 / 120 (the K-term weights)
 };
 
 // Order 6: f (component comp) at node (i, j, l) of the node grid, or one step
@@ -452,16 +453,19 @@ __device__ inline double2 ghost_data(const ZRhsArgs &a, int i, int j, int l) {
     return d;
 }
 
-// One thread per unknown (row r, j, i): the compact right-hand side of the row,
-// minus the known Dirichlet plane next to it, or the Robin row's h_z^2 f plus
-// its face-data term.
+// One thread per unknown (row r = blockIdx.y, (j, i) along x): the compact
+// right-hand side of the row, minus the known Dirichlet plane next to it, or the
+// Robin row's h_z^2 f plus its face-data term.  FP64 divisions by constants are
+// multiplications by the folded reciprocals (an FP64 division costs about ten
+// FP64-pipe operations on this GPU).
 __global__ void zrhs_kernel(ZRhsArgs a) {
     const size_t plane = (size_t)a.ny * a.nx, n = plane * a.Nu;
     const size_t sy = (size_t)(a.Nx + 2), sz = sy * (a.Ny + 2), nodes = sz * (a.Nz + 2);
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
-         t += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(t / plane);
-        const int rem = (int)(t - (size_t)r * plane);
+    {
+        const int r = blockIdx.y;
+        const int rem = blockIdx.x * blockDim.x + threadIdx.x;
+        if (rem >= (int)plane) return;
+        const size_t t = (size_t)r * plane + rem;
         const int j = rem / a.nx, i = rem - j * a.nx;
         const int l = a.l0 + r;
         const int jj = j + a.i0y, ii = i + a.i0x;   // node indices
@@ -480,7 +484,7 @@ __global__ void zrhs_kernel(ZRhsArgs a) {
                 const double D = (f[rowc + im] + f[rowc + ip] + f[pl + (size_t)jm * sy + ii] +
                                   f[pl + (size_t)jp * sy + ii] + f[c - sz] + f[c + sz]) -
                                  6.0 * f[c];
-                v += D / 12.0;
+                v = fma(D, 1.0 / 12.0, v);
             } else if (a.order == 6 && l >= 1 && l <= a.Nz) {
                 // K-free part of R6 / h^2: 67/120 f + (40 S1 - 3 S2 + 8 E) / 720 with
                 // S1 the 6 face neighbours, S2 the 6 second neighbours (ghosts beyond
@@ -498,7 +502,7 @@ __global__ void zrhs_kernel(ZRhsArgs a) {
                         E += f[c + s1 * (long)sz + s2];                     // x-z edges
                         E += f[c + s1 * (long)sz + s2 * (long)sy];          // y-z edges
                     }
-                v = (67.0 / 120.0) * f[c] + (40.0 * S1 - 3.0 * S2 + 8.0 * E) / 720.0;
+                v = fma(40.0 * S1 - 3.0 * S2 + 8.0 * E, 1.0 / 720.0, (67.0 / 120.0) * f[c]);
             }
             if (comp == 0) F.x = hz2 * v; else F.y = hz2 * v;
         }
@@ -508,8 +512,8 @@ __global__ void zrhs_kernel(ZRhsArgs a) {
             const double2 fcv = make_double2(a.f[c], a.f[nn + c]);
             const double2 dz = make_double2(a.f[c + sz] - a.f[c - sz], a.f[nn + c + sz] - a.f[nn + c - sz]);
             const double2 Kc = a.kk[l], Kzc = a.kk[a.Nz + 2 + l];
-            F = cadd(F, cscale(-hz2 * hz2 / 20.0, cmul(Kc, fcv)));
-            F = cadd(F, cscale(hz2 * hz2 * a.hz / 120.0, cmul(Kzc, dz)));
+            F = cadd(F, cscale(a.k20, cmul(Kc, fcv)));
+            F = cadd(F, cscale(a.k120, cmul(Kzc, dz)));
         }
         if (l == 0) {
             F = cadd(F, cmul(a.ga_lo, face_val(a, a.g_lo, j, i)));
@@ -710,13 +714,41 @@ __global__ void zfactor_kernel(double *fac, const double2 *rows, const double *c
 
 // The z-solves with the cached factors, in place on W [2][Nu][ny][nx]:
 // d_r = rhs_r / m_r - (lower_r / m_r) d_{r-1}, then w_r = d_r - c'_r w_{r+1}.
-__global__ void zthomas_kernel(double *W, const double *fac, int Nx, int Ny, int Nu) {
+// The sweeps walk each column ZCH rows at a time: a chunk's loads are all
+// issued before its dependent chain and its in-place stores (which would
+// otherwise keep the next row's loads from starting early).
+constexpr int ZCH = 8;
+
+__global__ void zthomas_kernel(double *__restrict__ W, const double *__restrict__ fac, int Nx,
+                               int Ny, int Nu) {
     const size_t plane = (size_t)Nx * Ny, n = plane * Nu;
     const size_t col = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (col >= plane) return;
     const double *F0 = fac, *F1 = fac + 2 * n, *F2 = fac + 4 * n;
     double2 d = make_double2(0.0, 0.0);
-    for (int r = 0; r < Nu; ++r) {
+    int r = 0;
+    for (; r + ZCH <= Nu; r += ZCH) {
+        double2 rhs[ZCH], a[ZCH], b[ZCH];
+#pragma unroll
+        for (int c = 0; c < ZCH; ++c) {
+            const size_t k = (size_t)(r + c) * plane + col;
+            rhs[c] = make_double2(W[k], W[n + k]);
+            a[c] = make_double2(F0[k], F0[n + k]);
+            b[c] = make_double2(F1[k], F1[n + k]);
+        }
+#pragma unroll
+        for (int c = 0; c < ZCH; ++c) {
+            d = csub(cmul(rhs[c], a[c]), cmul(b[c], d));
+            rhs[c] = d;
+        }
+#pragma unroll
+        for (int c = 0; c < ZCH; ++c) {
+            const size_t k = (size_t)(r + c) * plane + col;
+            W[k] = rhs[c].x;
+            W[n + k] = rhs[c].y;
+        }
+    }
+    for (; r < Nu; ++r) {
         const size_t k = (size_t)r * plane + col;
         const double2 rhs = make_double2(W[k], W[n + k]);
         d = csub(cmul(rhs, make_double2(F0[k], F0[n + k])), cmul(make_double2(F1[k], F1[n + k]), d));
@@ -724,7 +756,28 @@ __global__ void zthomas_kernel(double *W, const double *fac, int Nx, int Ny, int
         W[n + k] = d.y;
     }
     double2 w = d;
-    for (int r = Nu - 2; r >= 0; --r) {
+    r = Nu - 2;
+    for (; r - ZCH + 1 >= 0; r -= ZCH) {
+        double2 dv[ZCH], cc[ZCH];
+#pragma unroll
+        for (int c = 0; c < ZCH; ++c) {
+            const size_t k = (size_t)(r - c) * plane + col;
+            dv[c] = make_double2(W[k], W[n + k]);
+            cc[c] = make_double2(F2[k], F2[n + k]);
+        }
+#pragma unroll
+        for (int c = 0; c < ZCH; ++c) {
+            w = csub(dv[c], cmul(cc[c], w));
+            dv[c] = w;
+        }
+#pragma unroll
+        for (int c = 0; c < ZCH; ++c) {
+            const size_t k = (size_t)(r - c) * plane + col;
+            W[k] = dv[c].x;
+            W[n + k] = dv[c].y;
+        }
+    }
+    for (; r >= 0; --r) {
         const size_t k = (size_t)r * plane + col;
         w = csub(make_double2(W[k], W[n + k]), cmul(make_double2(F2[k], F2[n + k]), w));
         W[k] = w.x;
@@ -743,31 +796,85 @@ __global__ void zround_kernel(const Tin *__restrict__ in, float *__restrict__ ou
 
 // The z-solves of one correction in FP32 with the FP32-rounded cached factors
 // (zthomas_kernel's recurrence).
-__global__ void zthomas32_kernel(float *W, const float *fac, int Nx, int Ny, int Nu) {
+__global__ void zthomas32_kernel(float *__restrict__ W, const float *__restrict__ fac, int Nx,
+                                 int Ny, int Nu) {
     const size_t plane = (size_t)Nx * Ny, n = plane * Nu;
     const size_t col = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (col >= plane) return;
     const float *F0 = fac, *F1 = fac + 2 * n, *F2 = fac + 4 * n;
     float dx = 0.f, dy = 0.f;
-    for (int r = 0; r < Nu; ++r) {
-        const size_t k = (size_t)r * plane + col;
-        const float rx = W[k], ry = W[n + k];
-        const float ax = F0[k], ay = F0[n + k], bx = F1[k], by = F1[n + k];
+    auto fwd = [&](float rx, float ry, float ax, float ay, float bx, float by) {
         const float nx_ = (rx * ax - ry * ay) - (bx * dx - by * dy);
         const float ny_ = (rx * ay + ry * ax) - (bx * dy + by * dx);
         dx = nx_;
         dy = ny_;
+    };
+    int r = 0;
+    for (; r + ZCH <= Nu; r += ZCH) {
+        float rx[ZCH], ry[ZCH], ax[ZCH], ay[ZCH], bx[ZCH], by[ZCH];
+#pragma unroll
+        for (int c = 0; c < ZCH; ++c) {
+            const size_t k = (size_t)(r + c) * plane + col;
+            rx[c] = W[k];
+            ry[c] = W[n + k];
+            ax[c] = F0[k];
+            ay[c] = F0[n + k];
+            bx[c] = F1[k];
+            by[c] = F1[n + k];
+        }
+#pragma unroll
+        for (int c = 0; c < ZCH; ++c) {
+            fwd(rx[c], ry[c], ax[c], ay[c], bx[c], by[c]);
+            rx[c] = dx;
+            ry[c] = dy;
+        }
+#pragma unroll
+        for (int c = 0; c < ZCH; ++c) {
+            const size_t k = (size_t)(r + c) * plane + col;
+            W[k] = rx[c];
+            W[n + k] = ry[c];
+        }
+    }
+    for (; r < Nu; ++r) {
+        const size_t k = (size_t)r * plane + col;
+        fwd(W[k], W[n + k], F0[k], F0[n + k], F1[k], F1[n + k]);
         W[k] = dx;
         W[n + k] = dy;
     }
     float wx = dx, wy = dy;
-    for (int r = Nu - 2; r >= 0; --r) {
-        const size_t k = (size_t)r * plane + col;
-        const float cx = F2[k], cy = F2[n + k];
-        const float nx_ = W[k] - (cx * wx - cy * wy);
-        const float ny_ = W[n + k] - (cx * wy + cy * wx);
+    auto bwd = [&](float vx, float vy, float cx, float cy) {
+        const float nx_ = vx - (cx * wx - cy * wy);
+        const float ny_ = vy - (cx * wy + cy * wx);
         wx = nx_;
         wy = ny_;
+    };
+    r = Nu - 2;
+    for (; r - ZCH + 1 >= 0; r -= ZCH) {
+        float vx[ZCH], vy[ZCH], cx[ZCH], cy[ZCH];
+#pragma unroll
+        for (int c = 0; c < ZCH; ++c) {
+            const size_t k = (size_t)(r - c) * plane + col;
+            vx[c] = W[k];
+            vy[c] = W[n + k];
+            cx[c] = F2[k];
+            cy[c] = F2[n + k];
+        }
+#pragma unroll
+        for (int c = 0; c < ZCH; ++c) {
+            bwd(vx[c], vy[c], cx[c], cy[c]);
+            vx[c] = wx;
+            vy[c] = wy;
+        }
+#pragma unroll
+        for (int c = 0; c < ZCH; ++c) {
+            const size_t k = (size_t)(r - c) * plane + col;
+            W[k] = vx[c];
+            W[n + k] = vy[c];
+        }
+    }
+    for (; r >= 0; --r) {
+        const size_t k = (size_t)r * plane + col;
+        bwd(W[k], W[n + k], F2[k], F2[n + k]);
         W[k] = wx;
         W[n + k] = wy;
     }
@@ -1088,7 +1195,13 @@ hs_status hs_zsolve_full(hs_zplan_t Z, const double *f, const double *g_lo, cons
     a.kk = Z->d_kk;
     a.hx = Z->hx;
     a.hy = Z->hy;
-    const unsigned blocks = (unsigned)((nu + 255) / 256 < 152 * 16 ? (nu + 255) / 256 : 152 * 16);
+    {
+        const double h2 = Z->hz * Z->hz;
+        a.k20 = -h2 * h2 / 20.0;
+        a.k120 = h2 * h2 * Z->hz / 120.0;
+    }
+    (void)nu;
+    const dim3 blocks((unsigned)((plane + 255) / 256), (unsigned)Z->Nu, 1);
     auto mark = [&](int k) -> hs_status {
         if (Z->timing && Z->have_ev) ZCK(Z, cudaEventRecord(Z->ev[k], s));
         return HS_OK;
