@@ -207,33 +207,37 @@ template <typename T>
 __global__ void __launch_bounds__(256) ghost_kernel(RhsArgs a, const T *__restrict__ f,
                                                     double *__restrict__ g, int pl0, int pl1,
                                                     int zlo, int zhi) {
-    const long np = pl1 - pl0 + 1;
-    const long nyx = (long)(a.Ny + 2), nxx = (long)(a.Nx + 2);
-    const long cx = 2 * np * nyx, cy = 2 * np * nxx, cz = nyx * nxx;
+    // 32-bit index arithmetic: at most 2 (Nz + 2)(Nx + Ny + 4) + 2 (Nx + 2)(Ny + 2)
+    // items, far below 2^31 for any grid that fits in memory
+    const int np = pl1 - pl0 + 1;
+    const int nyx = a.Ny + 2, nxx = a.Nx + 2;
+    const int cx = 2 * np * nyx, cy = 2 * np * nxx, cz = nyx * nxx;
     double *gx = g;
     double *gy = gx + 2 * (size_t)(a.Nz + 2) * nyx;
     double *gz = gy + 2 * (size_t)(a.Nz + 2) * nxx;
-    const long nzs = (long)(zlo != 0) + (zhi != 0);   // z faces to form
-    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < cx + cy + nzs * cz;
-         t += (long)gridDim.x * blockDim.x) {
+    const int nzs = (zlo != 0) + (zhi != 0);   // z faces to form
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cx + cy + nzs * cz;
+         t += gridDim.x * blockDim.x) {
         if (t < cx) {
-            const int side = (int)(t / (np * nyx));
-            const long r = t - side * np * nyx;
-            const int pl = pl0 + (int)(r / nyx), j = (int)(r % nyx);
+            const int side = t >= np * nyx;
+            const int r = t - side * np * nyx;
+            const int q = r / nyx;
+            const int pl = pl0 + q, j = r - q * nyx;
             gx[((size_t)side * (a.Nz + 2) + pl) * nyx + j] =
                 node_or_ghost<T>(a, f, side ? a.Nx + 2 : -1, j, pl);
         } else if (t < cx + cy) {
-            const long u = t - cx;
-            const int side = (int)(u / (np * nxx));
-            const long r = u - side * np * nxx;
-            const int pl = pl0 + (int)(r / nxx), i = (int)(r % nxx);
+            const int u = t - cx;
+            const int side = u >= np * nxx;
+            const int r = u - side * np * nxx;
+            const int q = r / nxx;
+            const int pl = pl0 + q, i = r - q * nxx;
             gy[((size_t)side * (a.Nz + 2) + pl) * nxx + i] =
                 node_or_ghost<T>(a, f, i, side ? a.Ny + 2 : -1, pl);
         } else {
-            const long u = t - cx - cy;
+            const int u = t - cx - cy;
             const int side = (zlo && u < cz) ? 0 : 1;
-            const long r = u - (u < cz ? 0 : cz);
-            const int j = (int)(r / nxx), i = (int)(r % nxx);
+            const int r = u - (u < cz ? 0 : cz);
+            const int j = r / nxx, i = r - j * nxx;
             gz[(size_t)side * cz + r] = node_or_ghost<T>(a, f, i, j, side ? a.Nz + 2 : -1);
         }
     }
