@@ -69,6 +69,7 @@ struct hs_zplan_s {
     double2 *d_dct[2];         // Neumann axis: M roots then M + 1 half-angle pairs
     double2 *d_rows;           // [Nu][3][4] complex coefficients of the unknown rows
     float4 *d_rows32;          // the same as FP32 pairs (re hi, re lo, im hi, im lo)
+    int resid_xy;              // d_rows32's x and y coefficients agree on every row
     int rows_ok;
     double *d_fac;             // cached LU factors: 3 planar complex arrays [2][Nu][ny][nx]
     int fac_ok;                // the factors match the rows and side tables
@@ -215,6 +216,11 @@ hs_status build_rows(hs_zplan_s *Z) {
         for (size_t k = 0; k < rows.size(); ++k) {
             const float rh = (float)rows[k].x, ih = (float)rows[k].y;
             r32[k] = make_float4(rh, (float)(rows[k].x - (double)rh), ih, (float)(rows[k].y - (double)ih));
+        }
+        Z->resid_xy = 1;
+        for (size_t k = 0; k < rows.size(); k += 4) {   // (A, B, C, D) of one (row, nu)
+            const float4 b = r32[k + 1], c = r32[k + 2];
+            if (b.x != c.x || b.y != c.y || b.z != c.z || b.w != c.w) Z->resid_xy = 0;
         }
         ZCK(Z, cudaMemcpy(Z->d_rows32, r32.data(), r32.size() * sizeof(float4),
                           cudaMemcpyHostToDevice));
@@ -901,30 +907,62 @@ __global__ void zsplit_kernel(const double *__restrict__ W, float *__restrict__ 
 constexpr int ZRX = 32, ZRY = 8;
 
 struct ZSums {
-    hs_tiles::LPair r[4], i[4];   // A (corners), B (x), C (y), D (centre)
+    hs_tiles::LPair r[4], i[4];   // A (corners), B (x), C (y; with XY: x + y in B), D (centre)
 };
 
+// XY: the x and y coefficient pairs agree on every row (equal steps in x and y),
+// so the x- and y-neighbour sums are added first and multiplied once (nine
+// complex pair products per row instead of twelve).  Loading: the U plane two
+// ahead and the F of the next row are fetched into registers before the
+// current row's arithmetic, so their latency overlaps it; one barrier per plane
+// (the slot a plane is stored into was last read two planes earlier).
+template <bool XY>
 __global__ void __launch_bounds__(ZRX * ZRY)
 zresid_df_kernel(const float *__restrict__ Fp, const float *__restrict__ Up,
                  const float4 *__restrict__ rows4, float *__restrict__ r32, int nx, int ny, int Nu) {
     using namespace hs_tiles;
-    __shared__ float4 ring[2][ZRY + 2][ZRX + 2];   // (re hi, re lo, im hi, im lo)
+    constexpr int HX = ZRX + 2, HY = ZRY + 2, NT = ZRX * ZRY;
+    constexpr int PER = (HX * HY + NT - 1) / NT;
+    __shared__ float4 ring[2][HY][HX];   // (re hi, re lo, im hi, im lo)
     const size_t plane = (size_t)nx * ny, nu = plane * Nu, n2 = 2 * nu;
-    const int tx = threadIdx.x % ZRX, ty = threadIdx.x / ZRX;
+    const int tid = threadIdx.x;
+    const int tx = tid % ZRX, ty = tid / ZRX;
     const int i0 = blockIdx.x * ZRX, j0 = blockIdx.y * ZRY;
     const int i = i0 + tx, j = j0 + ty;
     const bool active = i < nx && j < ny;
-    auto load = [&](int rr, int slot) {
-        for (int e = threadIdx.x; e < (ZRY + 2) * (ZRX + 2); e += ZRX * ZRY) {
-            const int ey = e / (ZRX + 2), ex = e - ey * (ZRX + 2);
-            const int jj = j0 - 1 + ey, ii = i0 - 1 + ex;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (jj >= 0 && jj < ny && ii >= 0 && ii < nx) {
-                const size_t k = (size_t)rr * plane + (size_t)jj * nx + ii;
-                v = make_float4(Up[k], Up[n2 + k], Up[nu + k], Up[n2 + nu + k]);
+    // this thread's halo elements: in-plane offset, -1 outside the unknown grid
+    // (zero there: Dirichlet side faces), -2 past the halo tile
+    int goff[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int e = tid + q * NT;
+        const int ey = e / HX, ex = e - ey * HX;
+        const int jj = j0 - 1 + ey, ii = i0 - 1 + ex;
+        goff[q] = e >= HX * HY ? -2 : ((jj >= 0 && jj < ny && ii >= 0 && ii < nx) ? jj * nx + ii : -1);
+    }
+    float4 reg[PER];
+    float4 fnext = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto fetch = [&](int rr) {   // U plane rr (zeros past the last plane)
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            reg[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rr < Nu && goff[q] >= 0) {
+                const size_t k = (size_t)rr * plane + goff[q];
+                reg[q] = make_float4(Up[k], Up[n2 + k], Up[nu + k], Up[n2 + nu + k]);
             }
-            ring[slot][ey][ex] = v;
         }
+    };
+    auto fetchF = [&](int rr) {
+        if (active && rr < Nu) {
+            const size_t k = (size_t)rr * plane + (size_t)j * nx + i;
+            fnext = make_float4(Fp[k], Fp[n2 + k], Fp[nu + k], Fp[n2 + nu + k]);
+        }
+    };
+    auto store = [&](int slot) {
+        float4 *dst = &ring[slot][0][0];
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+            if (goff[q] != -2) dst[tid + q * NT] = reg[q];
     };
     auto sums = [&](int slot, ZSums &S) {
         auto at = [&](int dy, int dx) { return ring[slot][ty + 1 + dy][tx + 1 + dx]; };
@@ -942,10 +980,17 @@ zresid_df_kernel(const float *__restrict__ Fp, const float *__restrict__ Up,
         lp_add(S.r[1], xr.x, xr.y);
         S.i[1] = LPair{xl.z, xl.w};
         lp_add(S.i[1], xr.z, xr.w);
-        S.r[2] = LPair{yl.x, yl.y};
-        lp_add(S.r[2], yr.x, yr.y);
-        S.i[2] = LPair{yl.z, yl.w};
-        lp_add(S.i[2], yr.z, yr.w);
+        if constexpr (XY) {
+            lp_add(S.r[1], yl.x, yl.y);
+            lp_add(S.r[1], yr.x, yr.y);
+            lp_add(S.i[1], yl.z, yl.w);
+            lp_add(S.i[1], yr.z, yr.w);
+        } else {
+            S.r[2] = LPair{yl.x, yl.y};
+            lp_add(S.r[2], yr.x, yr.y);
+            S.i[2] = LPair{yl.z, yl.w};
+            lp_add(S.i[2], yr.z, yr.w);
+        }
         S.r[3] = LPair{o.x, o.y};
         S.i[3] = LPair{o.z, o.w};
     };
@@ -954,26 +999,31 @@ zresid_df_kernel(const float *__restrict__ Fp, const float *__restrict__ Up,
     };
     ZSums sm, s0, sp;
     zero(sm);
-    load(0, 0);
+    zero(s0);
+    zero(sp);
+    fetch(0);
+    store(0);
     __syncthreads();
     sums(0, s0);
+    fetch(1);
+    fetchF(0);
     for (int r = 0; r < Nu; ++r) {
-        if (r + 1 < Nu) {
-            load(r + 1, (r + 1) & 1);
-            __syncthreads();
-            sums((r + 1) & 1, sp);
-        } else {
-            zero(sp);
-        }
+        const float4 Fr = fnext;
+        store((r + 1) & 1);   // plane r + 1 (zeros past the last)
+        __syncthreads();
+        fetch(r + 2);         // in flight during the arithmetic below
+        fetchF(r + 1);
+        sums((r + 1) & 1, sp);
         if (active) {
             const size_t k = (size_t)r * plane + (size_t)j * nx + i;
-            LPair ar{Fp[k], Fp[n2 + k]}, ai{Fp[nu + k], Fp[n2 + nu + k]};
+            LPair ar{Fr.x, Fr.y}, ai{Fr.z, Fr.w};
             const float4 *cf = rows4 + (size_t)r * 12;
             const ZSums *S3[3] = {&sm, &s0, &sp};
 #pragma unroll
             for (int nuv = 0; nuv < 3; ++nuv) {
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
+                    if (XY && m == 2) continue;
                     const float4 c = __ldg(cf + nuv * 4 + m);
                     const float2 cre = make_float2(c.x, c.y), cim = make_float2(c.z, c.w);
                     const LPair Sr = S3[nuv]->r[m], Si = S3[nuv]->i[m];
@@ -1302,8 +1352,14 @@ hs_status hs_zsolve_full(hs_zplan_t Z, const double *f, const double *g_lo, cons
             if (m == 0) {
                 in = Z->d_Fp;   // F_hi
             } else {
-                zresid_df_kernel<<<rgrid, ZRX * ZRY, 0, s>>>(Z->d_Fp, Z->d_Up, Z->d_rows32, w,
-                                                            Z->nx, Z->ny, Z->Nu);
+                if (Z->resid_xy)
+                    zresid_df_kernel<true><<<rgrid, ZRX * ZRY, 0, s>>>(Z->d_Fp, Z->d_Up,
+                                                                      Z->d_rows32, w, Z->nx,
+                                                                      Z->ny, Z->Nu);
+                else
+                    zresid_df_kernel<false><<<rgrid, ZRX * ZRY, 0, s>>>(Z->d_Fp, Z->d_Up,
+                                                                       Z->d_rows32, w, Z->nx,
+                                                                       Z->ny, Z->Nu);
                 if (cudaGetLastError() != cudaSuccess) st = HS_ERR_CUDA;
             }
             if (st == HS_OK)
