@@ -390,6 +390,7 @@ struct ZRhsArgs {
                             // ([2][Nz+2][Nx+2]), z-lo, z-hi ([2][Ny+2][Nx+2]) faces, or NULL
     const double2 *kk;      // order 6: [2][Nz+2] K and K_z at the nodes
     double k20, k120;       // order 6: -h_z^4 / 20 and h_z^5 / 120 (the K-term weights)
+    int rbase;              // first unknown row of the launch (row rbase + blockIdx.y)
 };
 
 // Order 6: f (component comp) at node (i, j, l) of the node grid, or one step
@@ -468,7 +469,7 @@ __global__ void zrhs_kernel(ZRhsArgs a) {
     const size_t plane = (size_t)a.ny * a.nx, n = plane * a.Nu;
     const size_t sy = (size_t)(a.Nx + 2), sz = sy * (a.Ny + 2), nodes = sz * (a.Nz + 2);
     {
-        const int r = blockIdx.y;
+        const int r = a.rbase + blockIdx.y;
         const int rem = blockIdx.x * blockDim.x + threadIdx.x;
         if (rem >= (int)plane) return;
         const size_t t = (size_t)r * plane + rem;
@@ -594,6 +595,50 @@ __global__ void zside_kernel(ZRhsArgs a) {
         const size_t k = (size_t)r * plane + (size_t)j * a.nx + i;
         a.W[k] += F.x;
         a.W[n + k] += F.y;
+    }
+}
+
+// Mixed precision, orders 2 and 4, rows whose right-hand side is the plain
+// interior formula (no face term; Dirichlet side faces): F = h_z^2 f at order 2,
+// F = (h_z^2 / 2) f + (h_z^2 / 12) S1 at order 4 (S1 the six face neighbours;
+// the same operator as f + (S1 - 6 f) / 12), for the real and the imaginary
+// part alike, in FP32-pair arithmetic (FP64 f split into pairs with integer
+// operations, hi parts summed exactly) and written straight into the pair
+// planes the refinement works on.  wc, w12: the pair weights h_z^2 / 2 (order 4)
+// or h_z^2 (order 2), and h_z^2 / 12.
+__global__ void __launch_bounds__(256) zrhs_pair_kernel(ZRhsArgs a, float *__restrict__ Fp,
+                                                        float2 wc, float2 w12) {
+    using namespace hs_tiles;
+    const int plane = a.ny * a.nx;
+    const size_t nu = (size_t)plane * a.Nu, n2 = 2 * nu;
+    const size_t sy = (size_t)(a.Nx + 2), sz = sy * (a.Ny + 2), nodes = sz * (a.Nz + 2);
+    const int r = a.rbase + blockIdx.y;
+    const int rem = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rem >= plane) return;
+    const int j = rem / a.nx, i = rem - j * a.nx;
+    const size_t c = (size_t)(a.l0 + r) * sz + (size_t)(j + a.i0y) * sy + (i + a.i0x);
+    const size_t k = (size_t)r * plane + rem;
+    auto pr = [](double x) {
+        const dfloat d = df_split_bits(x);
+        return LPair{d.hi, d.lo};
+    };
+#pragma unroll
+    for (int comp = 0; comp < 2; ++comp) {
+        const double *f = a.f + comp * nodes;
+        LPair v = lp_mul(wc, pr(f[c]));
+        if (a.order == 4) {
+            LPair s1 = pr(f[c - 1]);
+            lp_add(s1, pr(f[c + 1]));
+            lp_add(s1, pr(f[c - sy]));
+            lp_add(s1, pr(f[c + sy]));
+            lp_add(s1, pr(f[c - sz]));
+            lp_add(s1, pr(f[c + sz]));
+            lp_add(v, lp_mul(w12, s1));
+        }
+        float hi, lo;
+        df_two_sum(v.s, v.e, hi, lo);
+        Fp[comp * nu + k] = hi;
+        Fp[n2 + comp * nu + k] = lo;
     }
 }
 
@@ -894,6 +939,20 @@ __global__ void zsplit_kernel(const double *__restrict__ W, float *__restrict__ 
         const dfloat d = df_split_bits(W[k]);
         P[k] = d.hi;
         P[n2 + k] = d.lo;
+    }
+}
+
+// zsplit_kernel for the unknown rows r0 .. r0 + nr - 1 only (real and imaginary
+// planes; nu values per component).
+__global__ void zsplit_rows_kernel(const double *__restrict__ W, float *__restrict__ P, size_t nu,
+                                   int plane, int r0, int nr) {
+    const int per = nr * plane;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * per; t += gridDim.x * blockDim.x) {
+        const int comp = t >= per;
+        const size_t k = comp * nu + (size_t)r0 * plane + (t - comp * per);
+        const dfloat d = df_split_bits(W[k]);
+        P[k] = d.hi;
+        P[2 * nu + k] = d.lo;
     }
 }
 
@@ -1258,8 +1317,38 @@ hs_status hs_zsolve_full(hs_zplan_t Z, const double *f, const double *g_lo, cons
     };
     hs_status mk;
     if ((mk = mark(0)) != HS_OK) return mk;
-    zrhs_kernel<<<blocks, 256, 0, s>>>(a);
-    ZCK(Z, cudaGetLastError());
+    // mixed precision at orders 2 and 4 with Dirichlet sides: the rows past the
+    // first two and before the last two take the plain interior formula, formed
+    // in pair arithmetic straight into the pair planes; the edge rows (Robin
+    // rows, rows next to a Dirichlet face) in FP64 as usual, split afterwards
+    const bool pair_rhs = Z->precision == HS_MIXED && Z->order <= 4 && !a.neu_x && !a.neu_y;
+    const int e0 = Z->Nu < 2 ? Z->Nu : 2, e1 = Z->Nu - 2 > e0 ? Z->Nu - 2 : e0;
+    a.rbase = 0;
+    if (!pair_rhs) {
+        zrhs_kernel<<<blocks, 256, 0, s>>>(a);
+        ZCK(Z, cudaGetLastError());
+    } else {
+        if (!Z->d_Fp) ZCK(Z, cudaMalloc(&Z->d_Fp, 4 * nu * sizeof(float)));
+        zrhs_kernel<<<dim3(blocks.x, (unsigned)e0, 1), 256, 0, s>>>(a);
+        ZCK(Z, cudaGetLastError());
+        if (Z->Nu > e1) {
+            a.rbase = e1;
+            zrhs_kernel<<<dim3(blocks.x, (unsigned)(Z->Nu - e1), 1), 256, 0, s>>>(a);
+            ZCK(Z, cudaGetLastError());
+        }
+        if (e1 > e0) {
+            const double h2 = Z->hz * Z->hz;
+            auto pair = [](double x) {
+                const float hi = (float)x;
+                return make_float2(hi, (float)(x - (double)hi));
+            };
+            a.rbase = e0;
+            zrhs_pair_kernel<<<dim3(blocks.x, (unsigned)(e1 - e0), 1), 256, 0, s>>>(
+                a, Z->d_Fp, pair(Z->order == 4 ? 0.5 * h2 : h2), pair(h2 / 12.0));
+            ZCK(Z, cudaGetLastError());
+        }
+        a.rbase = 0;
+    }
     if ((a.neu_x && (sd[0] || sd[1])) || (a.neu_y && (sd[2] || sd[3]))) {
         const size_t rows = 2 * (size_t)Z->Nu * (Z->nx + Z->ny);
         zside_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(a);
@@ -1335,8 +1424,20 @@ hs_status hs_zsolve_full(hs_zplan_t Z, const double *f, const double *g_lo, cons
             ZCK(Z, cudaGetLastError());
             Z->fac32_ok = 1;
         }
-        zsplit_kernel<<<eb, 256, 0, s>>>(W, Z->d_Fp, n2);
-        ZCK(Z, cudaGetLastError());
+        if (!pair_rhs) {
+            zsplit_kernel<<<eb, 256, 0, s>>>(W, Z->d_Fp, n2);
+            ZCK(Z, cudaGetLastError());
+        } else {
+            // the edge rows formed in FP64 (the others are pairs already)
+            for (int side = 0; side < 2; ++side) {
+                const int r0 = side == 0 ? 0 : e1, nr = side == 0 ? e0 : Z->Nu - e1;
+                if (nr <= 0) continue;
+                const int work = 2 * nr * (int)plane;
+                zsplit_rows_kernel<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(
+                    W, Z->d_Fp, nu, (int)plane, r0, nr);
+                ZCK(Z, cudaGetLastError());
+            }
+        }
         // the FP32 transforms take the fused tiles where the length is compiled
         // (the plan's own variant is for its FP64 passes)
         const int saved[2] = {T->dst_variant[0], T->dst_variant[1]};
