@@ -584,10 +584,11 @@ def bench_zrobin(args, torch, H, W, rank, world, barrier, max_over_ranks):
                "kind": "oracle",
                "sample": f"one full {N}^3 complex oracle solve (numpy FP64): {dt:.2f} s"}
     value = world * (N + 2) * ny * nx / (ms * 1e-3) / 1e9   # unknown (complex) points
-    # the mixed-precision plan (Dirichlet side faces only): FP32 solves refined with a
-    # pair residual, one sweep, timed the same way and checked against the FP64 result
+    # the mixed-precision plan (Dirichlet side faces: FP32 sine tiles; Neumann side
+    # faces: FP32 cosine tiles): FP32 solves refined with a pair residual, one
+    # sweep, timed the same way and checked against the FP64 result
     mixed = None
-    if name == "zrobin255_o4":
+    if name in ("zrobin255_o4", "zneumann255_o4"):
         u64 = u.clone()
         s.set_precision(H.HS_MIXED, 1)
         for _ in range(args.warmup):

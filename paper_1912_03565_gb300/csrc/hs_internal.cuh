@@ -207,6 +207,13 @@ hs_status hs_launch_dct_generic(int axis, int M, const double *in, double *out, 
 hs_status hs_launch_dct(int axis, int M, const double *in, double *out, const void *roots,
                         const void *half, long nrows, int nx, int nplanes, double scale,
                         cudaStream_t s);
+// FP32 DCT-I of the same lines (k_dct32.cu): roots / half as above in FP32;
+// tout / mode as hs_launch_dst's (axis Y: FP32 write only); lo_off and aux as
+// hs_emit's.  hs_dct32_size: M has a compiled FFT; else HS_ERR_UNSUPPORTED.
+int hs_dct32_size(int M);
+hs_status hs_launch_dct32(int axis, int M, int tout, int mode, const float *in, void *out,
+                          double *aux, size_t lo_off, const void *roots, const void *half,
+                          long nrows, int nx, int nplanes, double scale, cudaStream_t s);
 
 // Tensor-core (tcgen05) sine-matrix GEMM transform (k_dst_gemm.cu), mixed path:
 // line lengths M = N + 1 in {32, 64, 96, 128, 192, 256}.  The table holds the FP16

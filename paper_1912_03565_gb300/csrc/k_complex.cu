@@ -67,6 +67,7 @@ struct hs_zplan_s {
     hs_plan_s *TQ[2];          // quarter-wave axis: plan of its lines extended to 2N + 1
     double *d_cos;             // [nx] then [ny]: cos(theta) of each axis' modes
     double2 *d_dct[2];         // Neumann axis: M roots then M + 1 half-angle pairs
+    float2 *d_dct32[2];        // the same in FP32 (mixed precision)
     double2 *d_rows;           // [Nu][3][4] complex coefficients of the unknown rows
     float4 *d_rows32;          // the same as FP32 pairs (re hi, re lo, im hi, im lo)
     int resid_xy;              // d_rows32's x and y coefficients agree on every row
@@ -260,6 +261,8 @@ hs_status side_tables(hs_zplan_s *Z) {
     for (int a = 0; a < 2; ++a) {
         if (Z->d_dct[a]) cudaFree(Z->d_dct[a]);
         Z->d_dct[a] = nullptr;
+        if (Z->d_dct32[a]) cudaFree(Z->d_dct32[a]);
+        Z->d_dct32[a] = nullptr;
         if (Z->side[a] != HS_SIDE_NEUMANN) continue;
         const int M = N[a] + 1;
         std::vector<double2> t(2 * (size_t)M + 1);
@@ -268,6 +271,11 @@ hs_status side_tables(hs_zplan_s *Z) {
         for (int k = 0; k <= M; ++k) t[M + k] = make_double2(cos_pi_frac(k, M), sin_pi_frac(k, M));
         ZCK(Z, cudaMalloc(&Z->d_dct[a], t.size() * sizeof(double2)));
         ZCK(Z, cudaMemcpy(Z->d_dct[a], t.data(), t.size() * sizeof(double2),
+                          cudaMemcpyHostToDevice));
+        std::vector<float2> t32(t.size());
+        for (size_t k = 0; k < t.size(); ++k) t32[k] = make_float2((float)t[k].x, (float)t[k].y);
+        ZCK(Z, cudaMalloc(&Z->d_dct32[a], t32.size() * sizeof(float2)));
+        ZCK(Z, cudaMemcpy(Z->d_dct32[a], t32.data(), t32.size() * sizeof(float2),
                           cudaMemcpyHostToDevice));
     }
     return HS_OK;
@@ -978,7 +986,8 @@ struct ZSums {
 template <bool XY>
 __global__ void __launch_bounds__(ZRX * ZRY)
 zresid_df_kernel(const float *__restrict__ Fp, const float *__restrict__ Up,
-                 const float4 *__restrict__ rows4, float *__restrict__ r32, int nx, int ny, int Nu) {
+                 const float4 *__restrict__ rows4, float *__restrict__ r32, int nx, int ny, int Nu,
+                 int rx, int ry) {
     using namespace hs_tiles;
     constexpr int HX = ZRX + 2, HY = ZRY + 2, NT = ZRX * ZRY;
     constexpr int PER = (HX * HY + NT - 1) / NT;
@@ -990,13 +999,19 @@ zresid_df_kernel(const float *__restrict__ Fp, const float *__restrict__ Up,
     const int i = i0 + tx, j = j0 + ty;
     const bool active = i < nx && j < ny;
     // this thread's halo elements: in-plane offset, -1 outside the unknown grid
-    // (zero there: Dirichlet side faces), -2 past the halo tile
+    // (zero there: Dirichlet side faces), -2 past the halo tile.  rx / ry: the x / y
+    // sides are Neumann faces, whose unknown grid includes the face nodes and
+    // whose ghost beyond a face is the even reflection (the face data sit in F)
     int goff[PER];
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
         const int e = tid + q * NT;
         const int ey = e / HX, ex = e - ey * HX;
-        const int jj = j0 - 1 + ey, ii = i0 - 1 + ex;
+        int jj = j0 - 1 + ey, ii = i0 - 1 + ex;
+        if (rx && ii == -1) ii = 1;
+        if (rx && ii == nx) ii = nx - 2;
+        if (ry && jj == -1) jj = 1;
+        if (ry && jj == ny) jj = ny - 2;
         goff[q] = e >= HX * HY ? -2 : ((jj >= 0 && jj < ny && ii >= 0 && ii < nx) ? jj * nx + ii : -1);
     }
     float4 reg[PER];
@@ -1103,6 +1118,19 @@ zresid_df_kernel(const float *__restrict__ Fp, const float *__restrict__ Up,
     }
 }
 
+// Side kinds the mixed-precision solve takes: Dirichlet (FP32 sine tiles) and
+// Neumann on both faces of an axis (FP32 cosine tile, lengths with a compiled
+// FFT); the quarter-wave axes have no FP32 tile.
+bool mixed_sides_ok(const hs_zplan_s *Z, int x_kind, int y_kind) {
+    const int k[2] = {x_kind, y_kind};
+    const int N[2] = {Z->Nx, Z->Ny};
+    for (int a = 0; a < 2; ++a) {
+        if (k[a] == HS_SIDE_DIRICHLET) continue;
+        if (k[a] != HS_SIDE_NEUMANN || !hs_dct32_size(N[a] + 1)) return false;
+    }
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1172,9 +1200,8 @@ hs_status hs_zplan_set_coeff6(hs_zplan_t Z, const double *K, const double *Kz,
 hs_status hs_zplan_set_precision(hs_zplan_t Z, int precision, int sweeps) {
     if (!Z || (precision != HS_FP64 && precision != HS_MIXED) || sweeps < 0 || sweeps > 8)
         return HS_ERR_INVALID_ARG;
-    if (precision == HS_MIXED &&
-        (Z->side[0] != HS_SIDE_DIRICHLET || Z->side[1] != HS_SIDE_DIRICHLET))
-        return HS_ERR_UNSUPPORTED;   // the FP32 cosine / quarter-wave tiles are not built
+    if (precision == HS_MIXED && !mixed_sides_ok(Z, Z->side[0], Z->side[1]))
+        return HS_ERR_UNSUPPORTED;   // no FP32 quarter-wave tile; cosine lines need a compiled FFT
     Z->precision = precision;
     Z->sweeps = sweeps;
     return HS_OK;
@@ -1221,10 +1248,10 @@ hs_status hs_zplan_set_sides(hs_zplan_t Z, int x_kind, int y_kind) {
     for (int a = 0; a < 2; ++a)
         if (k[a] < HS_SIDE_DIRICHLET || k[a] > HS_SIDE_ND) return HS_ERR_INVALID_ARG;
     // the 6th-order right-hand side's ghosts are defined for Dirichlet side faces,
-    // and the mixed-precision solve has FP32 sine tiles only
-    if ((Z->order == 6 || Z->precision == HS_MIXED) &&
-        (x_kind != HS_SIDE_DIRICHLET || y_kind != HS_SIDE_DIRICHLET))
+    // and the mixed-precision solve has FP32 sine and cosine tiles (no quarter-wave)
+    if (Z->order == 6 && (x_kind != HS_SIDE_DIRICHLET || y_kind != HS_SIDE_DIRICHLET))
         return HS_ERR_UNSUPPORTED;
+    if (Z->precision == HS_MIXED && !mixed_sides_ok(Z, x_kind, y_kind)) return HS_ERR_UNSUPPORTED;
     // lengths without a compiled FFT take the runtime-sized transforms (direct sums
     // for a cosine axis, the sine plan's own fallback for the extended lines of a
     // mixed axis); a layout that cannot be built leaves the previous kinds in place
@@ -1448,6 +1475,19 @@ hs_status hs_zsolve_full(hs_zplan_t Z, const double *f, const double *g_lo, cons
         const dim3 rgrid((unsigned)((Z->nx + ZRX - 1) / ZRX), (unsigned)((Z->ny + ZRY - 1) / ZRY));
         const int sw = Z->sweeps;
         st = HS_OK;
+        // one FP32 pass: the cosine tile on a Neumann axis, else the sine tiles
+        auto pass32 = [&](int axis, const float *pin, int tout, void *pout, int mode,
+                          double scale, double *paux) -> hs_status {
+            if (Z->side[axis] == HS_SIDE_NEUMANN) {
+                const int M = (axis == HS_AXIS_X ? Z->Nx : Z->Ny) + 1;
+                const float2 *t = Z->d_dct32[axis];
+                return hs_launch_dct32(axis, M, tout, mode, pin, pout, paux, n2, t, t + M,
+                                       (long)Z->ny * 2 * Z->Nu, Z->nx, 2 * Z->Nu, scale, s);
+            }
+            return hs_launch_dst(T, axis, HS_T_F32, HS_T_F32, pin, tout, pout, mode, scale, s,
+                                 paux);
+        };
+        const int rx = Z->side[0] == HS_SIDE_NEUMANN, ry = Z->side[1] == HS_SIDE_NEUMANN;
         for (int m = 0; m <= sw && st == HS_OK; ++m) {
             const float *in = w;
             if (m == 0) {
@@ -1456,34 +1496,30 @@ hs_status hs_zsolve_full(hs_zplan_t Z, const double *f, const double *g_lo, cons
                 if (Z->resid_xy)
                     zresid_df_kernel<true><<<rgrid, ZRX * ZRY, 0, s>>>(Z->d_Fp, Z->d_Up,
                                                                       Z->d_rows32, w, Z->nx,
-                                                                      Z->ny, Z->Nu);
+                                                                      Z->ny, Z->Nu, rx, ry);
                 else
                     zresid_df_kernel<false><<<rgrid, ZRX * ZRY, 0, s>>>(Z->d_Fp, Z->d_Up,
                                                                        Z->d_rows32, w, Z->nx,
-                                                                       Z->ny, Z->Nu);
+                                                                       Z->ny, Z->Nu, rx, ry);
                 if (cudaGetLastError() != cudaSuccess) st = HS_ERR_CUDA;
             }
-            if (st == HS_OK)
-                st = hs_launch_dst(T, HS_AXIS_X, HS_T_F32, HS_T_F32, in, HS_T_F32, w, HS_MODE_WRITE, 1.0, s);
-            if (st == HS_OK)
-                st = hs_launch_dst(T, HS_AXIS_Y, HS_T_F32, HS_T_F32, w, HS_T_F32, w, HS_MODE_WRITE, 1.0, s);
+            if (st == HS_OK) st = pass32(HS_AXIS_X, in, HS_T_F32, w, HS_MODE_WRITE, 1.0, nullptr);
+            if (st == HS_OK) st = pass32(HS_AXIS_Y, w, HS_T_F32, w, HS_MODE_WRITE, 1.0, nullptr);
             if (st == HS_OK) {
                 zthomas32_kernel<<<(unsigned)((plane + 127) / 128), 128, 0, s>>>(w, Z->d_fac32, Z->nx,
                                                                                Z->ny, Z->Nu);
                 if (cudaGetLastError() != cudaSuccess) st = HS_ERR_CUDA;
             }
-            if (st == HS_OK)
-                st = hs_launch_dst(T, HS_AXIS_Y, HS_T_F32, HS_T_F32, w, HS_T_F32, w, HS_MODE_WRITE, sy, s);
+            if (st == HS_OK) st = pass32(HS_AXIS_Y, w, HS_T_F32, w, HS_MODE_WRITE, sy, nullptr);
             if (st != HS_OK) break;
             // the iterate: FP64 U straight away without refinement, else pairs (set,
             // add) and, on the last sweep, U + correction in FP64
             if (sw == 0)
-                st = hs_launch_dst(T, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_F64, Z->d_U,
-                                   HS_MODE_WRITE, sx, s);
+                st = pass32(HS_AXIS_X, w, HS_T_F64, Z->d_U, HS_MODE_WRITE, sx, nullptr);
             else
-                st = hs_launch_dst(T, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_DF, Z->d_Up,
-                                   m == 0 ? HS_MODE_DF_SET : (m < sw ? HS_MODE_DF_ADD : HS_MODE_DF_FINAL),
-                                   sx, s, Z->d_U);
+                st = pass32(HS_AXIS_X, w, HS_T_DF, Z->d_Up,
+                            m == 0 ? HS_MODE_DF_SET : (m < sw ? HS_MODE_DF_ADD : HS_MODE_DF_FINAL),
+                            sx, Z->d_U);
         }
         T->dst_variant[0] = saved[0];
         T->dst_variant[1] = saved[1];
@@ -1566,8 +1602,8 @@ size_t hs_zplan_workspace_bytes(hs_zplan_t Z) {
     for (int a = 0; a < 2; ++a) b += hs_workspace_bytes(Z->TQ[a]);
     b += (size_t)(Z->nx + Z->ny) * sizeof(double);
     if (Z->d_fac) b += (size_t)6 * Z->Nu * Z->nx * Z->ny * sizeof(double);
-    if (Z->d_dct[0]) b += (2 * (size_t)Z->Nx + 3) * sizeof(double2);
-    if (Z->d_dct[1]) b += (2 * (size_t)Z->Ny + 3) * sizeof(double2);
+    if (Z->d_dct[0]) b += (2 * (size_t)Z->Nx + 3) * (sizeof(double2) + sizeof(float2));
+    if (Z->d_dct[1]) b += (2 * (size_t)Z->Ny + 3) * (sizeof(double2) + sizeof(float2));
     return b;
 }
 
@@ -1587,8 +1623,10 @@ void hs_zplan_destroy(hs_zplan_t Z) {
     if (Z->d_rows) cudaFree(Z->d_rows);
     if (Z->d_cos) cudaFree(Z->d_cos);
     if (Z->d_fac) cudaFree(Z->d_fac);
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 2; ++a) {
         if (Z->d_dct[a]) cudaFree(Z->d_dct[a]);
+        if (Z->d_dct32[a]) cudaFree(Z->d_dct32[a]);
+    }
     if (Z->have_ev)
         for (int k = 0; k < 6; ++k) cudaEventDestroy(Z->ev[k]);
     delete Z;

@@ -479,7 +479,8 @@ def test_order6_complex_127():
 MIXTOL = 1e-10
 
 
-def _gpu_mixed(shape, L, order, K, zf, f, g_lo, g_hi, sweeps, Kz=None, Kzz=None, fnn=None):
+def _gpu_mixed(shape, L, order, K, zf, f, g_lo, g_hi, sweeps, Kz=None, Kzz=None, fnn=None,
+               sides=(0, 0), sd=None):
     torch = _torch()
     Nx, Ny, Nz = shape
     s = H.ZSolver(Nx, Ny, Nz, *L, order)
@@ -489,11 +490,15 @@ def _gpu_mixed(shape, L, order, K, zf, f, g_lo, g_hi, sweeps, Kz=None, Kzz=None,
         else:
             s.set_coeff(K)
         s.set_faces(zf.lo, zf.alpha[0], zf.beta[0], zf.hi, zf.alpha[1], zf.beta[1])
+        s.set_sides(*sides)
         s.set_precision(H.HS_MIXED, sweeps)
-        u = torch.full((2, Nz + 2, Ny, Nx), np.nan, dtype=torch.float64, device="cuda")
+        nx, ny = _nu(Nx, sides[0]), _nu(Ny, sides[1])
+        u = torch.full((2, Nz + 2, ny, nx), np.nan, dtype=torch.float64, device="cuda")
         s.solve(_planar(torch, f), u, None if g_lo is None else _planar(torch, g_lo),
                 None if g_hi is None else _planar(torch, g_hi),
-                fnn=None if fnn is None else [None if a is None else _planar(torch, a) for a in fnn])
+                fnn=None if fnn is None else [None if a is None else _planar(torch, a) for a in fnn],
+                side_data=None if sd is None else [None if a is None else _planar(torch, a)
+                                                   for a in sd])
         torch.cuda.synchronize()
         uc = u.cpu().numpy()
         return uc[0] + 1j * uc[1]
@@ -518,6 +523,53 @@ def test_mixed_precision_complex_matches_oracle(order, faces, shape):
     assert e1 <= MIXTOL
 
 
+@pytest.mark.parametrize("faces", FACES)
+@pytest.mark.parametrize("Nz", [1, 2, 3, 4])
+def test_mixed_precision_complex_thin(faces, Nz):
+    """Thin boxes, where the mixed plan's right-hand side has no rows away from both
+    z ends (those rows are formed in pair arithmetic, the two rows at each end in
+    FP64): one sweep still meets the mixed bar against the oracle."""
+    shape, L = (15, 12, Nz), (1.0, 0.9, 0.3)
+    h, K, f, g_lo, g_hi = _case(shape, L, 7 * Nz + faces[0] + 2 * faces[1])
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    ref, _ = CX.solve(4, h, K, zf, f, g_lo, g_hi)
+    got = _gpu_mixed(shape, L, 4, K, zf, f, g_lo, g_hi, 1)
+    assert O.max_rel_diff(got, ref) <= MIXTOL
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("sides", [(NEU, DIRS), (DIRS, NEU), (NEU, NEU)])
+@pytest.mark.parametrize("faces", [(R, R), (D, R)])
+@pytest.mark.parametrize("shape", [(31, 63, 9), (63, 31, 4)])
+def test_mixed_precision_neumann_sides(order, sides, faces, shape):
+    """HS_MIXED with u_n = 0 on Neumann side faces: FP32 cosine tiles for those axes
+    and even reflection in the pair residual; one sweep meets the mixed bar against
+    the oracle."""
+    L = (1.0, 0.8, 1.1)
+    h, K, f, g_lo, g_hi = _neumann_case(shape, L, sides, sum(shape) + 3 * sides[0] + sides[1] + order)
+    zf = CX.ZFaces(faces[0], 1.0 + 0.5j, 2.0 - 1.0j, faces[1], -0.7 + 0.2j, 1.5 + 0.4j)
+    ref, _ = CX.solve(order, h, K, zf, f, g_lo, g_hi, sides)
+    got = _gpu_mixed(shape, L, order, K, zf, f, g_lo, g_hi, 1, sides=sides)
+    assert O.max_rel_diff(got, ref) <= MIXTOL
+
+
+@pytest.mark.parametrize("sides", [(NEU, DIRS), (NEU, NEU)])
+def test_mixed_precision_neumann_face_data(sides):
+    """HS_MIXED with u_n = g data on the Neumann side faces (the data enter F in FP64;
+    the refinement's residual reflects U): one sweep meets the mixed bar."""
+    shape, L = (31, 63, 7), (1.0, 1.3, 0.9)
+    Nx, Ny, Nz = shape
+    h, K, f, g_lo, g_hi = _neumann_case(shape, L, sides, 23 + 5 * sides[0] + sides[1])
+    rs = np.random.RandomState(29)
+    cr = lambda *sh: rs.uniform(-1, 1, sh) + 1j * rs.uniform(-1, 1, sh)
+    neu_face = [sides[0] == NEU, sides[0] == NEU, sides[1] == NEU, sides[1] == NEU]
+    sd = [cr(Nz + 2, (Ny if k < 2 else Nx) + 2) if neu_face[k] else None for k in range(4)]
+    zf = CX.ZFaces(R, 1.0 + 0.5j, 2.0 - 1.0j, D)
+    ref, _ = CX.solve(4, h, K, zf, f, g_lo, g_hi, sides, sd)
+    got = _gpu_mixed(shape, L, 4, K, zf, f, g_lo, g_hi, 1, sides=sides, sd=sd)
+    assert O.max_rel_diff(got, ref) <= MIXTOL
+
+
 @pytest.mark.parametrize("faces", [(R, R), (D, R)])
 def test_mixed_precision_complex_order6(faces):
     shape = (31, 23, 13)
@@ -532,21 +584,30 @@ def test_mixed_precision_complex_order6(faces):
 
 def test_mixed_precision_complex_255_and_errors():
     """255^3 Robin (the zrobin255_o4 recipe's shape) with one sweep; mixed precision
-    refuses Neumann or mixed side axes, and those side kinds refuse mixed precision."""
+    refuses mixed side axes (no FP32 quarter-wave tile) and Neumann axes whose
+    length has no compiled cosine tile, and those side kinds refuse mixed precision."""
     shape, L = (255, 255, 255), (1.0, 1.0, 1.0)
     h, K, f, g_lo, g_hi = _case(shape, L, 12)
     zf = CX.ZFaces(R, 1.0 + 0.5j, 3.0 - 1.0j, R, 1.0 + 0.5j, 3.0 - 1.0j)
     ref, _ = CX.solve(4, h, K, zf, f, g_lo, g_hi)
     got = _gpu_mixed(shape, L, 4, K, zf, f, g_lo, g_hi, 1)
     assert O.max_rel_diff(got, ref) <= MIXTOL
-    s = H.ZSolver(31, 31, 7, 1.0, 1.0, 1.0, 4)
+    s = H.ZSolver(31, 30, 7, 1.0, 1.0, 1.0, 4)
     try:
-        s.set_sides(H.HS_SIDE_NEUMANN, H.HS_SIDE_DIRICHLET)
+        s.set_sides(H.HS_SIDE_DN, H.HS_SIDE_DIRICHLET)
         with pytest.raises(H.HsError) as e:
             s.set_precision(H.HS_MIXED, 1)
         assert e.value.status == H.HS_ERR_UNSUPPORTED
-        s.set_sides(H.HS_SIDE_DIRICHLET, H.HS_SIDE_DIRICHLET)
+        s.set_sides(H.HS_SIDE_DIRICHLET, H.HS_SIDE_NEUMANN)   # 31 + 1 points: no cosine tile
+        with pytest.raises(H.HsError) as e:
+            s.set_precision(H.HS_MIXED, 1)
+        assert e.value.status == H.HS_ERR_UNSUPPORTED
+        s.set_sides(H.HS_SIDE_NEUMANN, H.HS_SIDE_DIRICHLET)   # 32 + 1 points: compiled
         s.set_precision(H.HS_MIXED, 1)
+        with pytest.raises(H.HsError) as e:
+            s.set_sides(H.HS_SIDE_DIRICHLET, H.HS_SIDE_NEUMANN)
+        assert e.value.status == H.HS_ERR_UNSUPPORTED
+        s.set_sides(H.HS_SIDE_DIRICHLET, H.HS_SIDE_DIRICHLET)
         with pytest.raises(H.HsError) as e:
             s.set_sides(H.HS_SIDE_DN, H.HS_SIDE_DIRICHLET)
         assert e.value.status == H.HS_ERR_UNSUPPORTED
