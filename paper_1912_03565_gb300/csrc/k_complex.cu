@@ -607,7 +607,8 @@ __global__ void zside_kernel(ZRhsArgs a) {
 }
 
 // Mixed precision, orders 2 and 4, rows whose right-hand side is the plain
-// interior formula (no face term; Dirichlet side faces): F = h_z^2 f at order 2,
+// interior formula (no z-face term, no u_n data on the side faces; neighbours
+// beyond a Neumann side face reflected evenly): F = h_z^2 f at order 2,
 // F = (h_z^2 / 2) f + (h_z^2 / 12) S1 at order 4 (S1 the six face neighbours;
 // the same operator as f + (S1 - 6 f) / 12), for the real and the imaginary
 // part alike, in FP32-pair arithmetic (FP64 f split into pairs with integer
@@ -624,7 +625,13 @@ __global__ void __launch_bounds__(256) zrhs_pair_kernel(ZRhsArgs a, float *__res
     const int rem = blockIdx.x * blockDim.x + threadIdx.x;
     if (rem >= plane) return;
     const int j = rem / a.nx, i = rem - j * a.nx;
-    const size_t c = (size_t)(a.l0 + r) * sz + (size_t)(j + a.i0y) * sy + (i + a.i0x);
+    const int jj = j + a.i0y, ii = i + a.i0x;   // node indices
+    const size_t rowc = (size_t)(a.l0 + r) * sz + (size_t)jj * sy;
+    const size_t c = rowc + ii;
+    // in-plane neighbours, reflected beyond a Neumann side's faces
+    const size_t xm = rowc + reflect(ii - 1, a.Nx + 2), xp = rowc + reflect(ii + 1, a.Nx + 2);
+    const size_t ym = (size_t)(a.l0 + r) * sz + (size_t)reflect(jj - 1, a.Ny + 2) * sy + ii;
+    const size_t yp = (size_t)(a.l0 + r) * sz + (size_t)reflect(jj + 1, a.Ny + 2) * sy + ii;
     const size_t k = (size_t)r * plane + rem;
     auto pr = [](double x) {
         const dfloat d = df_split_bits(x);
@@ -635,10 +642,10 @@ __global__ void __launch_bounds__(256) zrhs_pair_kernel(ZRhsArgs a, float *__res
         const double *f = a.f + comp * nodes;
         LPair v = lp_mul(wc, pr(f[c]));
         if (a.order == 4) {
-            LPair s1 = pr(f[c - 1]);
-            lp_add(s1, pr(f[c + 1]));
-            lp_add(s1, pr(f[c - sy]));
-            lp_add(s1, pr(f[c + sy]));
+            LPair s1 = pr(f[xm]);
+            lp_add(s1, pr(f[xp]));
+            lp_add(s1, pr(f[ym]));
+            lp_add(s1, pr(f[yp]));
             lp_add(s1, pr(f[c - sz]));
             lp_add(s1, pr(f[c + sz]));
             lp_add(v, lp_mul(w12, s1));
@@ -1344,11 +1351,12 @@ hs_status hs_zsolve_full(hs_zplan_t Z, const double *f, const double *g_lo, cons
     };
     hs_status mk;
     if ((mk = mark(0)) != HS_OK) return mk;
-    // mixed precision at orders 2 and 4 with Dirichlet sides: the rows past the
+    // mixed precision at orders 2 and 4 without side-face data: the rows past the
     // first two and before the last two take the plain interior formula, formed
     // in pair arithmetic straight into the pair planes; the edge rows (Robin
     // rows, rows next to a Dirichlet face) in FP64 as usual, split afterwards
-    const bool pair_rhs = Z->precision == HS_MIXED && Z->order <= 4 && !a.neu_x && !a.neu_y;
+    const bool pair_rhs = Z->precision == HS_MIXED && Z->order <= 4 && !sd[0] && !sd[1] &&
+                          !sd[2] && !sd[3];
     const int e0 = Z->Nu < 2 ? Z->Nu : 2, e1 = Z->Nu - 2 > e0 ? Z->Nu - 2 : e0;
     a.rbase = 0;
     if (!pair_rhs) {
