@@ -699,10 +699,12 @@ hs_status hs_zplan_set_coeff6(hs_zplan_t plan, const double *K, const double *Kz
  * and imaginary parts, FP32 z-solves on the cached LU factors rounded to FP32)
  * as the approximate inverse M of an iterative refinement
  * U_0 = M F, U_{m+1} = U_m + M (F - A U_m), m < sweeps, with F, U and the
- * complex 27-point residual in FP64 (the refined result is as accurate as the
- * FP64 path's to about 1e-10 after one sweep on well-conditioned problems).
- * Dirichlet side faces only (HS_ERR_UNSUPPORTED otherwise, and set_sides then
- * refuses other kinds); sweeps 0..8.  The mixed solve allocates, on first use,
+ * complex 27-point residual in FP32-pair arithmetic (the refined result is as
+ * accurate as the FP64 path's to about 1e-10 after one sweep on well-conditioned
+ * problems).  Side axes: Dirichlet (FP32 sine tiles), or Neumann on both faces
+ * when N + 1 is a compiled length (32, 64, 96, 128, 192, 256, 384, 512, 768,
+ * 1024; FP32 cosine tile); one face of each kind has no FP32 tile
+ * (HS_ERR_UNSUPPORTED, and set_sides then refuses such kinds); sweeps 0..8.  The mixed solve allocates, on first use,
  * 20 bytes per complex unknown (FP32 work, FP64 iterate) and 24 for the FP32
  * factors.  Stage timing reports the refinement loop as the transform stage.
  * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED. */
@@ -756,7 +758,9 @@ hs_status hs_zsolve_full(hs_zplan_t plan, const double *f, const double *g_lo,
  * by direct sums, O(N^2) per line, lines of at most about 3000 nodes).  The
  * unknown grid is nx = Nx, Nx + 2 or Nx + 1 nodes by the kind, and likewise ny.
  * Errors: HS_ERR_INVALID_ARG (kind), HS_ERR_UNSUPPORTED (no transform for the
- * length), HS_ERR_OOM; on error the previous kinds stay in effect. */
+ * length; an order-6 plan with other than Dirichlet sides; an HS_MIXED plan with
+ * kinds hs_zplan_set_precision refuses), HS_ERR_OOM; on error the previous kinds
+ * stay in effect. */
 hs_status hs_zplan_set_sides(hs_zplan_t plan, int x_kind, int y_kind);
 
 /* hs_zsolve -- one solve (Section 3.6 with complex rows) on `stream`
