@@ -702,9 +702,10 @@ hs_status hs_zplan_set_coeff6(hs_zplan_t plan, const double *K, const double *Kz
  * complex 27-point residual in FP32-pair arithmetic (the refined result is as
  * accurate as the FP64 path's to about 1e-10 after one sweep on well-conditioned
  * problems).  Side axes: Dirichlet (FP32 sine tiles), or Neumann on both faces
- * when N + 1 is a compiled length (32, 64, 96, 128, 192, 256, 384, 512, 768,
- * 1024; FP32 cosine tile); one face of each kind has no FP32 tile
- * (HS_ERR_UNSUPPORTED, and set_sides then refuses such kinds); sweeps 0..8.  The mixed solve allocates, on first use,
+ * when N + 1 is 32, 64, 96, 128, 192 or 256 (FP32 half-length cosine tile, whose
+ * unrefined error grows like (N + 1) eps, 4e-6 at 256); longer Neumann axes and
+ * one face of each kind have no FP32 tile (HS_ERR_UNSUPPORTED, and set_sides
+ * then refuses such kinds); sweeps 0..8.  The mixed solve allocates, on first use,
  * 20 bytes per complex unknown (FP32 work, FP64 iterate) and 24 for the FP32
  * factors.  Stage timing reports the refinement loop as the transform stage.
  * Errors: HS_ERR_INVALID_ARG, HS_ERR_UNSUPPORTED. */

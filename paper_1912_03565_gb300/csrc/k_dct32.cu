@@ -8,8 +8,9 @@
 //     Re Y_k = X_{2k},   Im Y_k = X_{2k-1} - X_{2k+1},
 // and the odd outputs are the running sum X_{2k+1} = X_1 - sum_{k'=1..k} Im Y_k'
 // from X_1 = sum_j w_j x_j cos(pi j / M).  In FP32 that sum is compensated (each
-// addition's rounding error carried, Knuth's two_sum), so the odd outputs are as
-// accurate as the FFT's.  Outputs go through hs_emit, so the same tile serves
+// addition's rounding error carried, Knuth's two_sum), so its additions add no
+// error of their own; the rounding of the FFT outputs it sums still accumulates
+// along the line (see hs_dct32_size).  Outputs go through hs_emit, so the same tile serves
 // the forward passes (write) and the inverse x pass of a refined solve (the pair
 // modes, and the final FP64 u).
 #include "hs_internal.cuh"
@@ -279,10 +280,14 @@ hs_status launch_m(int axis, int tout, int mode, const float *in, void *out, dou
 
 }  // namespace
 
+// Lengths the mixed-precision plan takes the tile for.  The odd outputs are a
+// running sum of FFT outputs, so the FFT's own rounding accumulates along the
+// line: measured unrefined solve errors grow like M eps (1.2e-7 at M = 32, 4e-6
+// at 256, 2e-5 at 768), and beyond 256 one refinement sweep no longer keeps a
+// margin under 1e-10.  The longer lengths stay compiled but are not offered.
 int hs_dct32_size(int M) {
     switch (M) {
-        case 32: case 64: case 96: case 128: case 192: case 256: case 384: case 512: case 768:
-        case 1024:
+        case 32: case 64: case 96: case 128: case 192: case 256:
             return 1;
         default:
             return 0;

@@ -553,6 +553,36 @@ def test_mixed_precision_neumann_sides(order, sides, faces, shape):
     assert O.max_rel_diff(got, ref) <= MIXTOL
 
 
+@pytest.mark.parametrize("M", [32, 64, 96, 128, 192, 256, 384, 512, 768, 1024])
+def test_mixed_precision_cosine_lengths(M):
+    """Every length the FP32 cosine tile serves (N + 1 <= 256), along x and along y
+    (thin boxes, Neumann on the long axis): the refined mixed solve equals the FP64
+    plan's to the mixed bar, and the unrefined error grows no faster than (N + 1) eps
+    (both printed).  Longer Neumann axes are refused in mixed precision: the tile's
+    running sum lets the unrefined error grow past what one sweep corrects."""
+    torch = _torch()
+    if M > 256:
+        s = H.ZSolver(M - 1, 9, 3, 1.0, 0.9, 0.4, 4)
+        try:
+            s.set_sides(H.HS_SIDE_NEUMANN, H.HS_SIDE_DIRICHLET)
+            with pytest.raises(H.HsError) as e:
+                s.set_precision(H.HS_MIXED, 1)
+            assert e.value.status == H.HS_ERR_UNSUPPORTED
+        finally:
+            s.close()
+        return
+    for shape, sides in (((M - 1, 9, 3), (NEU, DIRS)), ((7, M - 1, 3), (DIRS, NEU))):
+        L = (1.0, 0.9, 0.4)
+        h, K, f, g_lo, g_hi = _neumann_case(shape, L, sides, M + sides[0])
+        zf = CX.ZFaces(R, 1.0 + 0.5j, 2.0 - 1.0j, D)
+        ref = _gpu(shape, L, 4, K, zf, f, g_lo, g_hi, sides)
+        e0 = O.max_rel_diff(_gpu_mixed(shape, L, 4, K, zf, f, g_lo, g_hi, 0, sides=sides), ref)
+        e1 = O.max_rel_diff(_gpu_mixed(shape, L, 4, K, zf, f, g_lo, g_hi, 1, sides=sides), ref)
+        print(f"cosine M={M} shape={shape}: unrefined {e0:.2e}, one sweep {e1:.2e}")
+        assert e0 <= 40 * M * 2.0 ** -24
+        assert e1 <= MIXTOL
+
+
 @pytest.mark.parametrize("sides", [(NEU, DIRS), (NEU, NEU)])
 def test_mixed_precision_neumann_face_data(sides):
     """HS_MIXED with u_n = g data on the Neumann side faces (the data enter F in FP64;
