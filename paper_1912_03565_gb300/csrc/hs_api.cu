@@ -554,6 +554,10 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
     // info mode takes the automatic residual decision on the host, from the
     // same quantities (relative residuals; rel[-1] = 1)
     const int rmode = effective_resid_mode(P);
+    // one fixed sweep: the FP32 solve writes only U's hi plane, and the
+    // residual and the final update read only that (U's lo parts are zero until
+    // a correction is added); results are those of the pair iterate bit for bit
+    const bool hi_only = sweeps == 1 && !tol_mode && !info && rmode != HS_RESID_F64;
     auto host_use64 = [&](int m) {
         if (rmode == HS_RESID_F64) return true;
         if (rmode != HS_RESID_AUTO || m < 2) return false;
@@ -575,7 +579,8 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
             } else {
                 HS_TRY(P, hs_launch_residual_df(P, F, U, w, s, r2,
                                                 rmode == HS_RESID_F64 ? HS_RESID_F64
-                                                                      : HS_RESID_DF));
+                                                                      : HS_RESID_DF,
+                                                nullptr, 0, hi_only));
             }
             T.end(HS_STAGE_RESIDUAL);
             if (tol_mode)
@@ -602,6 +607,13 @@ hs_status solve_one(hs_plan_s *P, double *u, cudaStream_t s, StageTimer &T, hs_i
         } else if (sweeps == 0 && !info) {
             HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_F64, u,
                                     HS_MODE_WRITE, sx, s));
+        } else if (hi_only) {
+            if (m == 0)
+                HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_F32, U,
+                                        HS_MODE_WRITE, sx, s));
+            else
+                HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_DF, U,
+                                        HS_MODE_DF_FINAL_HI, sx, s, u));
         } else if (last && !info) {
             HS_TRY(P, hs_launch_dst(P, HS_AXIS_X, HS_T_F32, HS_T_F32, w, HS_T_DF, U,
                                     HS_MODE_DF_FINAL, sx, s, u));

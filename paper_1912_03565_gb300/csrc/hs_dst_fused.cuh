@@ -264,7 +264,8 @@ __device__ __forceinline__ void dst_fused_tile(const Tin *in, Tout *out, double 
             const bool live = inl && s < nel_rows;
             Tout *orow = out + base + (size_t)s * N;
             double *arow = aux ? aux + base + (size_t)s * N : nullptr;
-            constexpr bool RMW = MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL;
+            constexpr bool RMW = MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL ||
+                                 MODE == HS_MODE_DF_FINAL_HI;
             // read-modify-write modes: every (hi, lo) of this lane's outputs is
             // loaded before the first store (the stores could alias the loads as
             // far as the compiler knows, which would serialise them); for a
@@ -277,7 +278,8 @@ __device__ __forceinline__ void dst_fused_tile(const Tin *in, Tout *out, double 
                     const int K = j + NsL * r;
                     const bool ok = live && K > 0;
                     uh[r] = ok ? ldc<COH>(orow + (K - 1)) : 0.f;
-                    ul[r] = ok ? ldc<COH>(orow + (K - 1) + lo_off) : 0.f;
+                    ul[r] = ok && MODE != HS_MODE_DF_FINAL_HI ? ldc<COH>(orow + (K - 1) + lo_off)
+                                                              : 0.f;
                 }
             }
 #pragma unroll

@@ -31,9 +31,11 @@ struct DstAxis {
 enum { HS_T_F64 = 0, HS_T_F32 = 1, HS_T_DF = 2 };
 // Output modes of the inverse x-transform: write, accumulate, and the
 // double-float iterate updates of the mixed path (set hi = X, lo = 0; add X
-// to (hi, lo); add X and write hi + lo as FP64 to the auxiliary array u).
+// to (hi, lo); add X and write hi + lo as FP64 to the auxiliary array u; the
+// same final step for an iterate whose lo plane is zero and was never written:
+// only hi is read).
 enum { HS_MODE_WRITE = 0, HS_MODE_ADD = 1, HS_MODE_DF_SET = 2, HS_MODE_DF_ADD = 3,
-       HS_MODE_DF_FINAL = 4 };
+       HS_MODE_DF_FINAL = 4, HS_MODE_DF_FINAL_HI = 5 };
 
 // Device views of the boundary data of one solve (pointers already on device).
 struct DevBoundary {
@@ -267,10 +269,12 @@ enum { HS_RESID_SEL_DF = 3, HS_RESID_SEL_F64 = 4 };
 // r = F - A U (F, U double-float pairs; r FP32) in the arithmetic `prec`
 // (HS_RESID_DF, HS_RESID_F64, or both selectors in one call for the automatic
 // rule with the squared norms `norms` [||F||^2, ||r_1||^2, ...] and sweep m);
-// adds ||r||^2 to *r2 when r2 is not NULL.
+// adds ||r||^2 to *r2 when r2 is not NULL.  u_lo_zero: the lo plane of U is
+// zero and was never written (the first residual after the FP32 solve wrote
+// U's hi plane only); only HS_RESID_DF takes it.
 hs_status hs_launch_residual_df(const hs_plan_s *P, const float *F, const float *U, float *r,
                                 cudaStream_t s, double *r2 = nullptr, int prec = HS_RESID_DF,
-                                const double *norms = nullptr, int m = 0);
+                                const double *norms = nullptr, int m = 0, bool u_lo_zero = false);
 
 // Sets *skip = 1 when *r2 <= tol^2 * *f2 (refinement converged).
 hs_status hs_launch_gate(const double *r2, const double *f2, double tol, int *skip, cudaStream_t s);
@@ -321,7 +325,7 @@ __device__ __forceinline__ void hs_emit(Tout *out, double *aux, size_t lo_off, s
     } else {
         dfloat a;
         a.hi = out[idx];
-        a.lo = out[idx + lo_off];
+        a.lo = MODE == HS_MODE_DF_FINAL_HI ? 0.f : out[idx + lo_off];
         dfloat b;
         b.hi = (float)v;
         b.lo = 0.f;

@@ -65,12 +65,41 @@ __device__ __forceinline__ void resid_plane_sums(const float2 *sl, int tx, int t
     ps.Ul = u.y;
 }
 
+// The same sums for an iterate whose lo parts are all zero (the first residual
+// after the FP32 solve), from a plane of hi values: the sums of the lo parts
+// vanish, Ul = 0.
+template <bool XY>
+__device__ __forceinline__ void resid_plane_sums_hi(const float *sl, int tx, int ty, PSum &ps) {
+    const int c = (ty + 1) * RSHX + tx + 1;
+    const float a = sl[c - RSHX - 1], b = sl[c - RSHX + 1];
+    const float g = sl[c + RSHX - 1], d = sl[c + RSHX + 1];
+    const float xm = sl[c - 1], xp = sl[c + 1], ym = sl[c - RSHX], yp = sl[c + RSHX];
+    float s, e, s2, e2, s3, e3;
+    df_two_sum(a, b, s, e);
+    df_two_sum(g, d, s2, e2);
+    df_two_sum(s, s2, s3, e3);
+    ps.C = s3;
+    ps.Cl = e3 + (e + e2);
+    if (XY) {
+        df_two_sum(xm, xp, s, e);
+        df_two_sum(ym, yp, s2, e2);
+        df_two_sum(s, s2, s3, e3);
+        ps.X = s3;
+        ps.Xl = e3 + (e + e2);
+    } else {
+        df_two_sum(xm, xp, ps.X, ps.Xl);
+        df_two_sum(ym, yp, ps.Y, ps.Yl);
+    }
+    ps.U = sl[c];
+    ps.Ul = 0.f;
+}
+
 // r_l = F_l - A U_l at one point from the plane sums of rows l - 1, l, l + 1.
 // The row's coefficient pairs are read two at a time (16-byte loads).  r only
 // feeds the FP32 correction solve: it is formed as the exact difference of the
 // hi parts (two_sum) plus the low-order terms, rounded once to FP32 -- the same
 // error bound (about 2^-47 |F| + 2^-24 |r|) as a full pair subtraction.
-template <bool XY>
+template <bool XY, bool ULO = true>
 __device__ __forceinline__ float resid_point(const float2 *__restrict__ cf, int l, int Nz,
                                              const PSum &pm, const PSum &p0, const PSum &pp,
                                              float2 Fl) {
@@ -86,7 +115,8 @@ __device__ __forceinline__ float resid_point(const float2 *__restrict__ cf, int 
         acc_term(S, E, make_float2(ab.x, ab.y), ps.C, ps.Cl);
         acc_term(S, E, make_float2(ab.z, ab.w), ps.X, ps.Xl);
         if (!XY) acc_term(S, E, make_float2(cd.x, cd.y), ps.Y, ps.Yl);
-        acc_term(S, E, make_float2(cd.z, cd.w), ps.U, ps.Ul);
+        if (ULO) acc_term(S, E, make_float2(cd.z, cd.w), ps.U, ps.Ul);
+        else acc_term_hi(S, E, make_float2(cd.z, cd.w), ps.U);
     }
     float d, de;
     df_two_sum(Fl.x, -S, d, de);   // F_hi - S exactly
@@ -194,7 +224,7 @@ constexpr size_t resid_async_smem() {
     return (size_t)RQ_SLOTS * (RSHX * RSHY + RSX * RSY) * sizeof(float2);
 }
 
-template <bool XY>
+template <bool XY, bool ULO = true>
 __device__ __forceinline__ void residual_sf_tile_async(int Nx, int Ny, int Nz,
                                                        const float2 *__restrict__ coef,
                                                        const float *__restrict__ F,
@@ -208,6 +238,8 @@ __device__ __forceinline__ void residual_sf_tile_async(int Nx, int Ny, int Nz,
     constexpr int D = RQ_SLOTS - 1;          // stream indices in flight ahead
     float2 *uring = smem;                    // [RQ_SLOTS][HALO]
     float2 *fring = smem + RQ_SLOTS * HALO;  // [RQ_SLOTS][NT]
+    // !ULO: the lo plane of U is zero and is not read; the U slots hold hi values
+    float *uring_hi = reinterpret_cast<float *>(smem);
     const int tid = threadIdx.x;
     const int tx = tid & (RSX - 1), ty = tid / RSX;
     const int i0 = bx * RSX, j0 = by * RSY;
@@ -234,14 +266,19 @@ __device__ __forceinline__ void residual_sf_tile_async(int Nx, int Ny, int Nz,
         const int slot = k & (RQ_SLOTS - 1);
         if (p <= lend) {
             float2 *us = uring + slot * HALO;
+            float *uh = uring_hi + slot * HALO;
             const bool zin = p >= 0 && p < Nz;
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
                 if (soff[q] < 0) continue;
                 const bool v = zin && goff[q] >= 0;
                 const float *src = v ? U + (size_t)p * plane + goff[q] : U;
-                cp_async<4>(&us[soff[q]].x, src, v);
-                cp_async<4>(&us[soff[q]].y, v ? src + n : U, v);
+                if (ULO) {
+                    cp_async<4>(&us[soff[q]].x, src, v);
+                    cp_async<4>(&us[soff[q]].y, v ? src + n : U, v);
+                } else {
+                    cp_async<4>(&uh[soff[q]], src, v);
+                }
             }
         }
         const int lf = p - 1;                // output plane whose F rides with U plane p
@@ -252,27 +289,30 @@ __device__ __forceinline__ void residual_sf_tile_async(int Nx, int Ny, int Nz,
         }
         cp_async_commit();
     };
-    auto take = [&](int k) -> const float2 * {
+    // wait for stream index k and take the plane sums of its U plane
+    auto take = [&](int k, PSum &ps) {
         cp_async_wait<D - 1>();
         __syncthreads();
-        return uring + (k & (RQ_SLOTS - 1)) * HALO;
+        const int slot = k & (RQ_SLOTS - 1);
+        if (ULO) resid_plane_sums<XY>(uring + slot * HALO, tx, ty, ps);
+        else resid_plane_sums_hi<XY>(uring_hi + slot * HALO, tx, ty, ps);
     };
 
 #pragma unroll
     for (int k = 0; k < D; ++k) issue(k);
     PSum pm, p0, pp;
-    resid_plane_sums<XY>(take(0), tx, ty, pm);
+    take(0, pm);
     issue(D);
-    resid_plane_sums<XY>(take(1), tx, ty, p0);
+    take(1, p0);
     issue(D + 1);
     float rsq = 0.f;
     for (int l = lbeg; l < lend; ++l) {
         const int k = l - lbeg + 2;
-        resid_plane_sums<XY>(take(k), tx, ty, pp);
+        take(k, pp);
         issue(k + D);
         if (active) {
-            const float rv = resid_point<XY>(coef + (size_t)l * 12, l, Nz, pm, p0, pp,
-                                             fring[(k & (RQ_SLOTS - 1)) * NT + tid]);
+            const float rv = resid_point<XY, ULO>(coef + (size_t)l * 12, l, Nz, pm, p0, pp,
+                                                  fring[(k & (RQ_SLOTS - 1)) * NT + tid]);
             r[(size_t)l * plane + col] = rv;
             rsq = fmaf(rv, rv, rsq);
         }

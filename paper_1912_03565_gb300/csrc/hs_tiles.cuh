@@ -289,14 +289,16 @@ __device__ __forceinline__ void dst_fast_tile(const Tin *in, Tout *out, double *
     const Tc q = scale * (Tc)0.25;
     if (AXIS == HS_AXIS_X) {
         const int nel = nvalid * N;
-        if constexpr (MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL) {
+        if constexpr (MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL ||
+                      MODE == HS_MODE_DF_FINAL_HI) {
             // read every (hi, lo) of the tile before any store
             float uh[ITER], ul[ITER];
 #pragma unroll
             for (int it = 0; it < ITER; ++it) {
                 const int e = threadIdx.x + it * NT;
                 uh[it] = (e < nel) ? ldc<COH>(out + base + e) : 0.f;
-                ul[it] = (e < nel) ? ldc<COH>(out + base + e + lo_off) : 0.f;
+                ul[it] = (e < nel && MODE != HS_MODE_DF_FINAL_HI) ? ldc<COH>(out + base + e + lo_off)
+                                                                  : 0.f;
             }
 #pragma unroll
             for (int it = 0; it < ITER; ++it) {
@@ -513,6 +515,18 @@ __device__ __forceinline__ void acc_term(float &S, float &E, float2 k, float v, 
     df_two_sum(S, p, s, t);
     S = s;
     E += t + pe + fmaf(k.x, vl, k.y * v);
+}
+
+// The same term for a plane sum with no low-order part (vl = 0): the cross
+// term k.y v is rounded on its own (not contracted into the sum), so the result
+// is acc_term's with vl = 0 bit for bit.
+__device__ __forceinline__ void acc_term_hi(float &S, float &E, float2 k, float v) {
+    const float p = k.x * v;
+    const float pe = fmaf(k.x, v, -p);
+    float s, t;
+    df_two_sum(S, p, s, t);
+    S = s;
+    E += t + pe + __fmul_rn(k.y, v);
 }
 
 constexpr int QTX = 32, QTY = 8, QZ = 16;

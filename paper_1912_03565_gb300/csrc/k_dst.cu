@@ -392,5 +392,7 @@ hs_status hs_launch_dst(const hs_plan_s *P, int axis, int tc, int tin, const voi
         return launch_typed<float, float, float, HS_MODE_DF_ADD>(P, axis, in, out, scale, s, aux);
     if (tin == HS_T_F32 && tout == HS_T_DF && mode == HS_MODE_DF_FINAL)
         return launch_typed<float, float, float, HS_MODE_DF_FINAL>(P, axis, in, out, scale, s, aux);
+    if (tin == HS_T_F32 && tout == HS_T_DF && mode == HS_MODE_DF_FINAL_HI)
+        return launch_typed<float, float, float, HS_MODE_DF_FINAL_HI>(P, axis, in, out, scale, s, aux);
     return HS_ERR_UNSUPPORTED;
 }

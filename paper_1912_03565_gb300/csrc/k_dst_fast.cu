@@ -26,7 +26,8 @@ hs_status hs_launch_dst_fast(const hs_plan_s *P, int axis, int tc, int tin, cons
                              int tout, void *out, int mode, double scale, cudaStream_t s,
                              double *aux) {
     if (tc == HS_T_F64) return hs_dst_fast_f64(P, axis, tin, in, tout, out, mode, scale, s, aux);
-    if (mode == HS_MODE_DF_SET || mode == HS_MODE_DF_ADD || mode == HS_MODE_DF_FINAL)
+    if (mode == HS_MODE_DF_SET || mode == HS_MODE_DF_ADD || mode == HS_MODE_DF_FINAL ||
+        mode == HS_MODE_DF_FINAL_HI)
         return hs_dst_fast_df(P, axis, tin, in, tout, out, mode, scale, s, aux);
     return hs_dst_fast_f32(P, axis, tin, in, tout, out, mode, scale, s, aux);
 }

@@ -12,5 +12,7 @@ hs_status hs_dst_fast_df(const hs_plan_s *P, int axis, int tin, const void *in, 
         return launch_sized<float, float, float, HS_MODE_DF_ADD>(P, axis, ax, in, out, scale, s, aux);
     if (mode == HS_MODE_DF_FINAL)
         return launch_sized<float, float, float, HS_MODE_DF_FINAL>(P, axis, ax, in, out, scale, s, aux);
+    if (mode == HS_MODE_DF_FINAL_HI)
+        return launch_sized<float, float, float, HS_MODE_DF_FINAL_HI>(P, axis, ax, in, out, scale, s, aux);
     return HS_ERR_UNSUPPORTED;
 }

@@ -18,6 +18,8 @@ hs_status launch_x(const hs_plan_s *P, int tin, const void *in, int tout, void *
         return fused_launch_sized<float, float, HS_AXIS_X, HS_MODE_DF_ADD, W>(P, ax, in, out, scale, s, aux);
     if (tout == HS_T_DF && mode == HS_MODE_DF_FINAL)
         return fused_launch_sized<float, float, HS_AXIS_X, HS_MODE_DF_FINAL, W>(P, ax, in, out, scale, s, aux);
+    if (tout == HS_T_DF && mode == HS_MODE_DF_FINAL_HI)
+        return fused_launch_sized<float, float, HS_AXIS_X, HS_MODE_DF_FINAL_HI, W>(P, ax, in, out, scale, s, aux);
     return HS_ERR_UNSUPPORTED;
 }
 

@@ -364,7 +364,8 @@ __global__ void __launch_bounds__(NTHR, 1) dst_gemm_kernel(GemmArgs g) {
                     for (int k = 0; k < 32; ++k) T[lane * 33 + k] = ((v[k] * f1) * f2) * g.scale;
                     __syncwarp();
                     const int n = c0 + lane;
-                    if constexpr (MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL) {
+                    if constexpr (MODE == HS_MODE_DF_ADD || MODE == HS_MODE_DF_FINAL ||
+                                  MODE == HS_MODE_DF_FINAL_HI) {
                         // read-modify-write of the pair iterate: 8 lines' (hi, lo) loaded
                         // before any is updated
                         float *o = reinterpret_cast<float *>(g.out);
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(NTHR, 1) dst_gemm_kernel(GemmArgs g) {
                                 const bool ok = r < g.nlines && n < g.N;
                                 const size_t idx = (size_t)(ok ? r : 0) * g.N + (ok ? n : 0);
                                 hi[d] = ok ? o[idx] : 0.f;
-                                lo[d] = ok ? o[idx + g.lo_off] : 0.f;
+                                lo[d] = ok && MODE != HS_MODE_DF_FINAL_HI ? o[idx + g.lo_off] : 0.f;
                             }
 #pragma unroll
                             for (int d = 0; d < 8; ++d) {
@@ -624,6 +625,8 @@ hs_status hs_launch_dst_gemm(const hs_plan_s *P, int axis, int tin, const void *
             k = gemm_pick<HS_AXIS_X, HS_MODE_DF_ADD, float>(M);
         else if (tout == HS_T_DF && mode == HS_MODE_DF_FINAL)
             k = gemm_pick<HS_AXIS_X, HS_MODE_DF_FINAL, float>(M);
+        else if (tout == HS_T_DF && mode == HS_MODE_DF_FINAL_HI)
+            k = gemm_pick<HS_AXIS_X, HS_MODE_DF_FINAL_HI, float>(M);
     } else if (tout == HS_T_F32 && mode == HS_MODE_WRITE) {
         k = gemm_pick<HS_AXIS_Y, HS_MODE_WRITE, float>(M);
     }

@@ -277,8 +277,9 @@ void launch_rhs_sf(const hs_plan_s *P, const RhsArgs &a, const T *f, float *Fo, 
 }
 
 // The lean pair residual (hs_resid_sf.cuh); XY: x- and y-neighbour sums merged
-// (b_nu = c_nu on every row).
-template <bool XY>
+// (b_nu = c_nu on every row); ULO: U has a lo plane (else only its hi plane
+// is read, the lo parts being zero).
+template <bool XY, bool ULO = true>
 __global__ void __launch_bounds__(RSX *RSY) residual_sf_kernel(int Nx, int Ny, int Nz,
                                                                 const float2 *__restrict__ coef,
                                                                 const float *__restrict__ F,
@@ -290,8 +291,8 @@ __global__ void __launch_bounds__(RSX *RSY) residual_sf_kernel(int Nx, int Ny, i
     if (skip && *skip) return;
     if (sel == HS_RESID_SEL_DF && residual_use_f64(norms, m)) return;
     __shared__ __align__(16) float2 ring[resid_async_smem() / sizeof(float2)];
-    residual_sf_tile_async<XY>(Nx, Ny, Nz, coef, F, U, r, r2out, ring, blockIdx.x, blockIdx.y,
-                               blockIdx.z, zt);
+    residual_sf_tile_async<XY, ULO>(Nx, Ny, Nz, coef, F, U, r, r2out, ring, blockIdx.x,
+                                    blockIdx.y, blockIdx.z, zt);
 }
 
 __global__ void __launch_bounds__(QTX *QTY) residual64_zmarch_kernel(
@@ -570,13 +571,20 @@ hs_status hs_launch_rhs(const hs_plan_s *P, const void *f, int f_dtype, int rhs_
 
 hs_status hs_launch_residual_df(const hs_plan_s *P, const float *F, const float *U, float *r,
                                 cudaStream_t s, double *r2, int prec, const double *norms,
-                                int m) {
+                                int m, bool u_lo_zero) {
     dim3 qb(QTX, QTY, 1);
     dim3 qg((P->Nx + QTX - 1) / QTX, (P->Ny + QTY - 1) / QTY, (P->Nz + QZ - 1) / QZ);
+    if (u_lo_zero && prec != HS_RESID_DF) return HS_ERR_UNSUPPORTED;
     if (prec == HS_RESID_DF || prec == HS_RESID_SEL_DF) {
         const int zt = hs_sf_zdepth(P);
         dim3 sg((P->Nx + RSX - 1) / RSX, (P->Ny + RSY - 1) / RSY, (P->Nz + zt - 1) / zt);
-        if (P->resid_xy)
+        if (u_lo_zero && P->resid_xy)
+            residual_sf_kernel<true, false><<<sg, RSX * RSY, 0, s>>>(
+                P->Nx, P->Ny, P->Nz, P->d_coef_df, F, U, r, P->cur_skip, r2, norms, m, prec, zt);
+        else if (u_lo_zero)
+            residual_sf_kernel<false, false><<<sg, RSX * RSY, 0, s>>>(
+                P->Nx, P->Ny, P->Nz, P->d_coef_df, F, U, r, P->cur_skip, r2, norms, m, prec, zt);
+        else if (P->resid_xy)
             residual_sf_kernel<true><<<sg, RSX * RSY, 0, s>>>(P->Nx, P->Ny, P->Nz, P->d_coef_df, F,
                                                               U, r, P->cur_skip, r2, norms, m, prec,
                                                               zt);

@@ -146,6 +146,23 @@ def test_random_problems_mixed(shape, order, eq):
     assert O.max_rel_diff(u, ref) <= TOLMIX, inf
 
 
+@pytest.mark.parametrize("variant", [H.HS_DST_STAGED, H.HS_DST_FUSED, H.HS_DST_GENERIC,
+                                     H.HS_DST_GEMM])
+@pytest.mark.parametrize("shape,order,eq", [((31, 40, 9), 6, W.HELMHOLTZ),
+                                            ((63, 17, 20), 4, W.CONVDIFF)])
+def test_one_sweep_hi_only_matches_pair_sequence(shape, order, eq, variant):
+    """One fixed refinement sweep writes only the hi plane of the iterate in the
+    first solve and reads only that in the residual and the final update (its lo
+    parts are zero until a correction is added).  The info-mode solve runs the
+    full pair sequence (lo planes written and read); the two must agree bit for
+    bit for every x-transform variant, and both match the oracle."""
+    p = random_problem(shape, order, eq, seed=sum(shape) + order)
+    u1, _ = gpu_solve(p, H.HS_MIXED, sweeps=1, variant=variant)
+    u2, inf = gpu_solve(p, H.HS_MIXED, sweeps=1, info=True, variant=variant)
+    assert np.array_equal(u1, u2), float(np.abs(u1 - u2).max())
+    assert O.max_rel_diff(u1, oracle_solve(p)) <= TOLMIX, inf
+
+
 @pytest.mark.parametrize("variant", [H.HS_CD_PAPER, H.HS_CD_CORRECTED])
 def test_convdiff_variants(variant):
     p = random_problem((20, 18, 22), 4, W.CONVDIFF, seed=3)
