@@ -47,6 +47,9 @@ BYTES_MIXED = {
     "idst_x": None,            # 4 + 8 (set U pair) first sweep, 4 + 16 (U pair += / u) after
     "residual": 20.0,          # read F pair, U pair (27-point), write r (FP32)
 }
+# One fixed sweep: the first solve writes U's hi plane only (4 + 4), the residual
+# reads F pair + U hi (+ r: 16) and the final update reads U hi (4 + 4 + 8 u).
+BYTES_MIXED_HI_ONLY = {"idst_x": 8.0 + 16.0, "residual": 16.0}
 BYTES_FP64 = {"rhs": 16.0, "dst_x": 16.0, "dst_y": 16.0, "thomas": 40.0, "idst_y": 16.0,
               "idst_x": 16.0, "residual": 0.0}
 
@@ -91,9 +94,14 @@ def sm_max_mhz():
         return 2070.0
 
 
-def stage_bytes(path: str, sweeps: int, thomas_fp32: bool = True):
+def stage_bytes(path: str, sweeps: int, thomas_fp32: bool = True, hi_only: bool = None):
+    """Algorithmic bytes per unknown of each stage of one solve.  hi_only: the
+    one-sweep sequence that keeps the first iterate's lo plane implicit (the
+    stand-alone solve with one fixed sweep; default: sweeps == 1)."""
     if path == "fp64":
         return dict(BYTES_FP64)
+    if hi_only is None:
+        hi_only = sweeps == 1
     b = dict(BYTES_MIXED)
     n = sweeps + 1
     if not thomas_fp32:
@@ -104,6 +112,8 @@ def stage_bytes(path: str, sweeps: int, thomas_fp32: bool = True):
     b["thomas"] *= n
     b["idst_y"] *= n
     b["residual"] *= sweeps
+    if hi_only and sweeps == 1:
+        b.update(BYTES_MIXED_HI_ONLY)
     return b
 
 
@@ -770,7 +780,7 @@ def bench_batch(args, torch, H, W, rank, world, barrier, max_over_ranks_dev):
     # at one refinement sweep (a lower bound: a solve stopped by the tolerance runs
     # at least one) over the step's device time
     hbm_peak, peak_kind = load_peaks()
-    bpu = sum(stage_bytes("mixed", 1).values())
+    bpu = sum(stage_bytes("mixed", 1, hi_only=False).values())
     achieved = bpu * total / (ms / args.steps * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": "whole batch step (one CUDA graph launch)",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

@@ -50,8 +50,13 @@ def test_reference_arm_two_ranks_prints_one_line():
 
 
 def test_stage_bytes_and_launch_counts():
-    b = bench.stage_bytes("mixed", 1)
+    b = bench.stage_bytes("mixed", 1, hi_only=False)
     assert b["residual"] == 20.0 and b["dst_x"] == 16.0 and b["idst_x"] == 32.0
+    # one fixed sweep: the first iterate's lo plane is never stored
+    h = bench.stage_bytes("mixed", 1)
+    assert h["residual"] == 16.0 and h["idst_x"] == 24.0
+    assert sum(b.values()) - sum(h.values()) == 12.0
+    assert bench.stage_bytes("mixed", 2)["residual"] == 40.0
     assert bench.stage_bytes("mixed", 1, thomas_fp32=False)["thomas"] == 64.0
     assert bench.launches_per_solve("mixed", 1) == 12
     assert bench.launches_per_solve("fp64", 0) == 6
