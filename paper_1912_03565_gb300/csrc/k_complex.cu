@@ -990,7 +990,9 @@ struct ZSums {
 // ahead and the F of the next row are fetched into registers before the
 // current row's arithmetic, so their latency overlaps it; one barrier per plane
 // (the slot a plane is stored into was last read two planes earlier).
-template <bool XY>
+// ULO: U has lo planes; else only its hi planes are read (the first residual of
+// a one-sweep solve: the lo parts are zero and were never written).
+template <bool XY, bool ULO = true>
 __global__ void __launch_bounds__(ZRX * ZRY)
 zresid_df_kernel(const float *__restrict__ Fp, const float *__restrict__ Up,
                  const float4 *__restrict__ rows4, float *__restrict__ r32, int nx, int ny, int Nu,
@@ -1029,7 +1031,8 @@ zresid_df_kernel(const float *__restrict__ Fp, const float *__restrict__ Up,
             reg[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (rr < Nu && goff[q] >= 0) {
                 const size_t k = (size_t)rr * plane + goff[q];
-                reg[q] = make_float4(Up[k], Up[n2 + k], Up[nu + k], Up[n2 + nu + k]);
+                reg[q] = make_float4(Up[k], ULO ? Up[n2 + k] : 0.f, Up[nu + k],
+                                     ULO ? Up[n2 + nu + k] : 0.f);
             }
         }
     };
@@ -1496,19 +1499,21 @@ hs_status hs_zsolve_full(hs_zplan_t Z, const double *f, const double *g_lo, cons
                                  paux);
         };
         const int rx = Z->side[0] == HS_SIDE_NEUMANN, ry = Z->side[1] == HS_SIDE_NEUMANN;
+        // one sweep: the first solve writes only U's hi planes, and the residual and
+        // the final update read only those (the lo parts are zero until the
+        // correction is added); the results are those of the pair sequence
+        const bool hi_only = sw == 1;
         for (int m = 0; m <= sw && st == HS_OK; ++m) {
             const float *in = w;
             if (m == 0) {
                 in = Z->d_Fp;   // F_hi
             } else {
-                if (Z->resid_xy)
-                    zresid_df_kernel<true><<<rgrid, ZRX * ZRY, 0, s>>>(Z->d_Fp, Z->d_Up,
-                                                                      Z->d_rows32, w, Z->nx,
-                                                                      Z->ny, Z->Nu, rx, ry);
-                else
-                    zresid_df_kernel<false><<<rgrid, ZRX * ZRY, 0, s>>>(Z->d_Fp, Z->d_Up,
-                                                                       Z->d_rows32, w, Z->nx,
-                                                                       Z->ny, Z->Nu, rx, ry);
+                auto kern = Z->resid_xy ? (hi_only ? zresid_df_kernel<true, false>
+                                                   : zresid_df_kernel<true, true>)
+                                        : (hi_only ? zresid_df_kernel<false, false>
+                                                   : zresid_df_kernel<false, true>);
+                kern<<<rgrid, ZRX * ZRY, 0, s>>>(Z->d_Fp, Z->d_Up, Z->d_rows32, w, Z->nx, Z->ny,
+                                                 Z->Nu, rx, ry);
                 if (cudaGetLastError() != cudaSuccess) st = HS_ERR_CUDA;
             }
             if (st == HS_OK) st = pass32(HS_AXIS_X, in, HS_T_F32, w, HS_MODE_WRITE, 1.0, nullptr);
@@ -1524,6 +1529,10 @@ hs_status hs_zsolve_full(hs_zplan_t Z, const double *f, const double *g_lo, cons
             // add) and, on the last sweep, U + correction in FP64
             if (sw == 0)
                 st = pass32(HS_AXIS_X, w, HS_T_F64, Z->d_U, HS_MODE_WRITE, sx, nullptr);
+            else if (hi_only && m == 0)
+                st = pass32(HS_AXIS_X, w, HS_T_F32, Z->d_Up, HS_MODE_WRITE, sx, nullptr);
+            else if (hi_only)
+                st = pass32(HS_AXIS_X, w, HS_T_DF, Z->d_Up, HS_MODE_DF_FINAL_HI, sx, Z->d_U);
             else
                 st = pass32(HS_AXIS_X, w, HS_T_DF, Z->d_Up,
                             m == 0 ? HS_MODE_DF_SET : (m < sw ? HS_MODE_DF_ADD : HS_MODE_DF_FINAL),

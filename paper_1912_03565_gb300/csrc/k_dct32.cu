@@ -274,6 +274,7 @@ hs_status launch_m(int axis, int tout, int mode, const float *in, void *out, dou
     if (tout == HS_T_DF && mode == HS_MODE_DF_SET) HS_A(HS_AXIS_X, HS_MODE_DF_SET, float);
     if (tout == HS_T_DF && mode == HS_MODE_DF_ADD) HS_A(HS_AXIS_X, HS_MODE_DF_ADD, float);
     if (tout == HS_T_DF && mode == HS_MODE_DF_FINAL) HS_A(HS_AXIS_X, HS_MODE_DF_FINAL, float);
+    if (tout == HS_T_DF && mode == HS_MODE_DF_FINAL_HI) HS_A(HS_AXIS_X, HS_MODE_DF_FINAL_HI, float);
 #undef HS_A
     return HS_ERR_UNSUPPORTED;
 }
