@@ -438,6 +438,10 @@ def hs_residual_static(Nx, Ny, Nz, Lx, Ly, Lz, order, equation, cd_variant, c0, 
         numel = a.numel() if hasattr(a, "numel") and callable(a.numel) else int(np.size(a))
         if numel != n:
             raise ValueError(f"{name} must hold Nx*Ny*Nz = {n} values, got {numel}")
+        contig = a.is_contiguous() if hasattr(a, "is_contiguous") else bool(
+            getattr(getattr(a, "flags", None), "c_contiguous", False))
+        if not contig:
+            raise ValueError(f"{name} must be contiguous")
     r = ctypes.c_double()
     n = ctypes.c_double()
     _check(load().hs_residual_static(Nx, Ny, Nz, Lx, Ly, Lz, order, equation, cd_variant,

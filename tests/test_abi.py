@@ -142,3 +142,21 @@ def test_check_finite_argument_validation(lib):
     cnt = ctypes.c_ulonglong()
     assert lib.hs_check_finite(None, None, 0, 0, None, ctypes.byref(cnt)) == H.HS_ERR_INVALID_ARG
     assert lib.hs_check_finite(None, None, 0, 0, None, None) == H.HS_ERR_INVALID_ARG
+
+
+def test_static_residual_binding_checks_layout_on_cpu():
+    """The allocation-free residual's binding rejects, before any library call,
+    arrays the bare pointers cannot describe: wrong dtype, wrong size, strided."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    c4 = np.full(4, 25.0)
+    good = torch.zeros((2, 2, 2), dtype=torch.float64)
+    strided = torch.zeros((2, 2, 4), dtype=torch.float64)[:, :, ::2]
+    assert strided.numel() == 8 and not strided.is_contiguous()
+    cases = [(torch.zeros((2, 2, 2), dtype=torch.float32), good),
+             (torch.zeros((2, 2, 3), dtype=torch.float64), good),
+             (strided, good), (good, strided)]
+    for F, u in cases:
+        with pytest.raises(ValueError):
+            H.hs_residual_static(2, 2, 2, 1.0, 1.0, 1.0, 4, H.HS_HELMHOLTZ, H.HS_CD_CORRECTED,
+                                 c4, None, None, F, u)
